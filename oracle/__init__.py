@@ -1,0 +1,209 @@
+"""CPU oracle for spiking-network connectivity construction.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU-baseline leg, never by the library.  The arithmetic lives in
+snc_oracle.c (plain C, double precision, no CUDA); this module only marshals
+numpy arrays through ctypes.
+
+Parity status (see the pins in tests/test_oracle_*.py):
+  philox            pinned against cuRAND's host PHILOX4_32_10 generator
+  delay_table       pinned against scipy.stats.norm.cdf + chi-square of samples
+  binom_table       pinned against scipy.stats.binom.cdf + chi-square of counts
+  normal_weight     pinned by closed-form values and a Kolmogorov-Smirnov test
+  generate          pinned by brute-force enumeration (one_to_one, all_to_all,
+                    the paper's Fig. 1 example), exact per-node counts,
+                    autapse/multapse prohibitions, uniformity tests and
+                    exhaustive subset-frequency tests on tiny ranges
+  build             pinned against numpy's stable lexsort, bincount and a
+                    per-source distinct-delay count
+"""
+from __future__ import annotations
+
+import ctypes
+import numpy as np
+
+from .build import build_oracle
+
+RULE_ID = {"one_to_one": 0, "all_to_all": 1, "fixed_indegree": 2, "fixed_outdegree": 3,
+           "fixed_total_number": 4, "pairwise_bernoulli": 5}
+DIST_ID = {"const": 0, "normal": 1}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
+          6: "UNSUPPORTED"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"oracle {what}: {STATUS.get(status, status)}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class _Proj(ctypes.Structure):
+    _fields_ = [("src_first", ctypes.c_uint32), ("src_n", ctypes.c_uint32),
+                ("tgt_first", ctypes.c_uint32), ("tgt_n", ctypes.c_uint32),
+                ("rule", ctypes.c_int32), ("allow_autapses", ctypes.c_int32),
+                ("allow_multapses", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("k", ctypes.c_uint64), ("p", ctypes.c_double),
+                ("w_kind", ctypes.c_int32), ("d_kind", ctypes.c_int32),
+                ("w_mean", ctypes.c_double), ("w_std", ctypes.c_double),
+                ("d_mean", ctypes.c_double), ("d_std", ctypes.c_double)]
+
+
+class _Net(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("dt", ctypes.c_double),
+                ("n_nodes", ctypes.c_uint32), ("n_proj", ctypes.c_uint32)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = ctypes.CDLL(build_oracle())
+        _LIB.or_normal_weight.restype = ctypes.c_float
+    return _LIB
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+
+def _marshal(spec):
+    net = _Net(seed=int(spec.seed) & 0xFFFFFFFFFFFFFFFF, dt=float(spec.dt),
+               n_nodes=int(spec.n_nodes), n_proj=len(spec.projections))
+    arr = (_Proj * max(1, len(spec.projections)))()
+    for i, pj in enumerate(spec.projections):
+        arr[i] = _Proj(src_first=pj.src[0], src_n=pj.src[1], tgt_first=pj.tgt[0],
+                       tgt_n=pj.tgt[1], rule=RULE_ID[pj.rule],
+                       allow_autapses=int(bool(pj.autapses)),
+                       allow_multapses=int(bool(pj.multapses)), pad0=0, k=int(pj.k),
+                       p=float(pj.p), w_kind=DIST_ID[pj.weight.kind],
+                       d_kind=DIST_ID[pj.delay.kind], w_mean=float(pj.weight.mean),
+                       w_std=float(pj.weight.std), d_mean=float(pj.delay.mean),
+                       d_std=float(pj.delay.std))
+    return net, arr
+
+
+def _check(st, what):
+    if st != 0:
+        raise OracleError(st, what)
+
+
+def philox(counters, key):
+    """Philox4x32-10 of each row of `counters` (n x 4 uint32) under key (k0, k1)."""
+    c = np.ascontiguousarray(counters, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(c)
+    _lib().or_philox(_ptr(c), ctypes.c_uint32(key[0]), ctypes.c_uint32(key[1]),
+                     ctypes.c_uint64(c.shape[0]), _ptr(out))
+    return out
+
+
+def delay_table(mu, sigma, dt):
+    """(base, thresholds): step(u) = base + #{T <= u}."""
+    thr = np.zeros(16384, dtype=np.uint32)
+    base = ctypes.c_uint32(0)
+    n = ctypes.c_int(0)
+    _check(_lib().or_delay_table(ctypes.c_double(mu), ctypes.c_double(sigma),
+                                 ctypes.c_double(dt), _ptr(thr), ctypes.c_int(thr.size),
+                                 ctypes.byref(base), ctypes.byref(n)), "delay_table")
+    return int(base.value), thr[:n.value].copy()
+
+
+def binom_table(n, p):
+    """(base, thresholds) of Binomial(n, p): count(u) = base + #{T <= u}."""
+    thr = np.zeros(16384, dtype=np.uint32)
+    base = ctypes.c_uint64(0)
+    ln = ctypes.c_int(0)
+    _check(_lib().or_binom_table(ctypes.c_uint64(n), ctypes.c_double(p), _ptr(thr),
+                                 ctypes.c_int(thr.size), ctypes.byref(base),
+                                 ctypes.byref(ln)), "binom_table")
+    return int(base.value), thr[:ln.value].copy()
+
+
+def normal_weight(mu, sigma, w2, w3):
+    return float(_lib().or_normal_weight(ctypes.c_double(mu), ctypes.c_double(sigma),
+                                         ctypes.c_uint32(w2), ctypes.c_uint32(w3)))
+
+
+def normal_weights(mu, sigma, w2, w3):
+    w2 = np.ascontiguousarray(w2, dtype=np.uint32)
+    w3 = np.ascontiguousarray(w3, dtype=np.uint32)
+    out = np.empty(w2.size, dtype=np.float32)
+    _lib().or_normal_weights(ctypes.c_double(mu), ctypes.c_double(sigma), _ptr(w2), _ptr(w3),
+                             ctypes.c_uint64(w2.size), _ptr(out))
+    return out
+
+
+def check_projection(spec, index):
+    """Status code Connect gives projection `index` (0 = accepted)."""
+    net, arr = _marshal(spec)
+    return int(_lib().or_check_projection(ctypes.byref(net), ctypes.byref(arr[index])))
+
+
+def count(spec):
+    """(total connections, per-projection counts) without storing them."""
+    net, arr = _marshal(spec)
+    per = np.zeros(max(1, len(spec.projections)), dtype=np.uint64)
+    n = ctypes.c_uint64(0)
+    _check(_lib().or_generate(ctypes.byref(net), arr, None, None, None, None,
+                              ctypes.c_uint64(0), ctypes.byref(n), _ptr(per)), "count")
+    return int(n.value), per[:len(spec.projections)].astype(np.int64)
+
+
+def generate(spec):
+    """All connections in generation order (before the sort)."""
+    total, per = count(spec)
+    net, arr = _marshal(spec)
+    out = {"src": np.empty(total, np.uint32), "tgt": np.empty(total, np.uint32),
+           "delay": np.empty(total, np.uint16), "weight": np.empty(total, np.float32)}
+    n = ctypes.c_uint64(0)
+    _check(_lib().or_generate(ctypes.byref(net), arr, _ptr(out["src"]), _ptr(out["tgt"]),
+                              _ptr(out["delay"]), _ptr(out["weight"]), ctypes.c_uint64(total),
+                              ctypes.byref(n), None), "generate")
+    out["per_proj"] = per
+    return out
+
+
+def sort_index(n_nodes, src, tgt, delay, weight):
+    """Stable sort by (source, delay, target) and the CSR / group index."""
+    src = np.array(src, dtype=np.uint32)
+    tgt = np.array(tgt, dtype=np.uint32)
+    delay = np.array(delay, dtype=np.uint16)
+    weight = np.array(weight, dtype=np.float32)
+    n = src.size
+    row_ptr = np.zeros(n_nodes + 1, np.uint64)
+    group_ptr = np.zeros(n_nodes + 1, np.uint64)
+    group_first = np.zeros(max(1, n), np.uint64)
+    ng = ctypes.c_uint64(0)
+    _check(_lib().or_sort_index(ctypes.c_uint32(n_nodes), ctypes.c_uint64(n), _ptr(src),
+                                _ptr(tgt), _ptr(delay), _ptr(weight), _ptr(row_ptr),
+                                _ptr(group_ptr), _ptr(group_first), ctypes.byref(ng)),
+           "sort_index")
+    return {"src": src, "tgt": tgt, "delay": delay, "weight": weight, "row_ptr": row_ptr,
+            "group_ptr": group_ptr, "group_first": group_first[:ng.value].copy(),
+            "n_groups": int(ng.value)}
+
+
+def build(spec):
+    """The finished network: generate, sort, index."""
+    g = generate(spec)
+    out = sort_index(spec.n_nodes, g["src"], g["tgt"], g["delay"], g["weight"])
+    out["per_proj"] = g["per_proj"]
+    return out
+
+
+def generate_primary(spec, proj, primary):
+    """Connections of one primary node of projection `proj`, in slot order."""
+    net, arr = _marshal(spec)
+    pj = spec.projections[proj]
+    cap = max(1, int(pj.src[1]) + int(pj.tgt[1]) + int(pj.k) + 1)
+    out = {"src": np.empty(cap, np.uint32), "tgt": np.empty(cap, np.uint32),
+           "delay": np.empty(cap, np.uint16), "weight": np.empty(cap, np.float32)}
+    n = ctypes.c_uint64(0)
+    _check(_lib().or_generate_primary(ctypes.byref(net), arr, ctypes.c_uint32(proj),
+                                      ctypes.c_uint32(primary), _ptr(out["src"]),
+                                      _ptr(out["tgt"]), _ptr(out["delay"]),
+                                      _ptr(out["weight"]), ctypes.c_uint64(cap),
+                                      ctypes.byref(n)), "generate_primary")
+    return {k: v[:n.value].copy() for k, v in out.items()}
