@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""Benchmark: connections built per second (generate + sort + index) on GB300.
+
+One step builds every network of the two-population rule sweep (2 x 100,000
+nodes, four Connect calls of one rule; fixed_indegree / fixed_outdegree
+K = 1,000, fixed_total_number 1e8 per call, pairwise_bernoulli p = 0.01,
+all_to_all on 2 x 10,000, one_to_one on 2 x 100,000; each with multapses and
+autapses allowed, and both forbidden), i.e. CreatePopulation -> Connect ->
+Finalize -> GetConnections for 12 networks, about 4e9 connections.
+
+Prints one JSON line.  `value` is device-timed (CUDA events on the stream the
+library runs on); `e2e` is host wall-clock through the public API.  With
+--impl reference the CPU oracle is timed instead, on a bounded sample.
+Under torchrun each rank builds the same workload independently (replicas:
+the construction path has no exchange step) and rank 0 reports the total.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "connections built/sec (generate+sort+index) on 1 GB300, % HBM roofline; p50/p99 latency"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="snc", choices=["snc", "reference"])
+    ap.add_argument("--workload", default="rule_sweep", choices=["rule_sweep", "microcircuit", "plain", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_specs(name):
+    from paper_2306_09855_gb300 import workloads as W
+    if name == "rule_sweep":
+        return [W.rule_sweep(r, m) for r, m in W.RULE_SWEEP_RUNS], {
+            "workload": "rule sweep: 2 x 100,000 nodes, 4 Connect calls of one rule per network "
+                        "(fixed_indegree/outdegree K=1000, fixed_total_number 1e8/call, "
+                        "pairwise_bernoulli p=0.01, all_to_all 2 x 10,000, one_to_one 2 x 100,000), "
+                        "multapses+autapses on and off: 12 networks",
+            "seed": 1234, "dt_ms": 0.1}
+    if name == "microcircuit":
+        return [W.microcircuit()], {"workload": "microcircuit-shaped: 8 populations, 77,169 nodes, "
+                                                "64 fixed_total_number calls, 3.0e8 connections",
+                                    "seed": 1234, "dt_ms": 0.1}
+    if name == "plain":
+        return [W.plain_indegree()], {"workload": "2 x 1,000 nodes, fixed_indegree K=100, 400k connections",
+                                      "seed": 1234, "dt_ms": 0.1}
+    return [W.rule_sweep("fixed_indegree", True, scale=0.1)], {
+        "workload": "small: 2 x 10,000 nodes fixed_indegree K=1000 (profiling case)", "seed": 1234}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def committed_traffic():
+    """DRAM bytes per element of one radix pass from the committed ncu summary."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "onesweep_traffic.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for row in csv.reader(f):
+                    if len(row) < 9:
+                        continue
+                    try:
+                        sms.append(float(row[1]))
+                        maxes.append(float(row[2]))
+                    except ValueError:
+                        continue
+                    for name, v in zip(names, row[5:9]):
+                        if v.strip().lower() == "active":
+                            reasons.add(name)
+        finally:
+            os.unlink(self.path)
+        if not sms:
+            return None
+        sms.sort()
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": max(maxes), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def cpu_baseline(sample_syn_target=1e7):
+    """The oracle (as it stands) on a bounded sample of the workload."""
+    import oracle
+    from paper_2306_09855_gb300 import workloads as W
+    spec = W.rule_sweep("fixed_indegree", True, scale=0.05)  # 2 x 5,000 nodes, K = 1,000: 2e7
+    t0 = time.perf_counter()
+    out = oracle.build(spec)
+    dt = time.perf_counter() - t0
+    return {"value": out["src"].size / dt, "unit": "connections/s", "cores": 1, "kind": "oracle",
+            "sample": "fixed_indegree K=1000 on 2 x 5,000 nodes (%d connections), single-threaded C "
+                      "oracle: generate + stable sort + index, %.1f s" % (out["src"].size, dt)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on host cores, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2306_09855_gb300 import workloads as W
+    spec = W.rule_sweep("fixed_indegree", True, scale=0.025)  # 2 x 2,500 nodes, K = 1,000: 1e7
+    for _ in range(args.warmup):
+        oracle.build(spec)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        n += oracle.build(spec)["src"].size
+    dt = time.perf_counter() - t0
+    value = n / dt
+    sample = "fixed_indegree K=1000 on 2 x 2,500 nodes (%d connections per step)" % (n // max(1, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "connections/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
+            "config": workload_specs(args.workload)[1],
+            "cpu_baseline": {"value": value, "unit": "connections/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "connections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2306_09855_gb300 import snc
+    snc.load()
+    specs, config = workload_specs(args.workload)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def one_step(record):
+        n_syn = 0
+        for spec in specs:
+            net = snc.Network(spec, device=local, stream=stream)
+            net.finalize()
+            v = net.view()  # synchronizes, reads the counts back
+            n_syn += int(v.n_syn)
+            if record is not None:
+                times, npass = net.stage_times()
+                st = net.stats()
+                record.append((int(v.n_syn), times, npass, st))
+            net.close()
+        return n_syn
+
+    for _ in range(max(3, args.warmup)):
+        one_step(None)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    records = []
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    start.record(stream)
+    n_total = 0
+    for _ in range(args.steps):
+        n_total += one_step(records)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([ms, float(n_total)], device="cuda", dtype=torch.float64)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        ms, n_all = float(tmax[0]), float(t[1])
+    else:
+        n_all = float(n_total)
+    value = n_all / (ms / 1e3)
+
+    # Dominant kernel: the onesweep radix pass.  Algorithmic bytes per launch:
+    # read key (8 B) + value (4 B), write key + value = 24 B per connection.
+    pass_bytes, pass_ms, pass_launches = 0.0, 0.0, 0
+    gen_bytes, gen_ms, launches = 0.0, 0.0, 0
+    stage_sum = {}
+    for n_syn, times, npass, st in records:
+        launches += int(st.kernel_launches)
+        for k in range(npass):
+            pass_bytes += 24.0 * n_syn
+            pass_ms += times[3 + k]
+            pass_launches += 1
+        gen_bytes += 12.0 * n_syn
+        gen_ms += times[1]
+        names = ["count", "generate", "histogram"] + ["pass%d" % k for k in range(npass)] + ["index"]
+        for nm, t in zip(names, times):
+            stage_sum[nm] = stage_sum.get(nm, 0.0) + t
+    peak, peak_src = measured_peaks()
+    achieved = (pass_bytes / (pass_ms / 1e3)) / 1e9 if pass_ms > 0 else 0.0
+    traffic = None
+    tr = committed_traffic()
+    if tr and pass_launches:
+        traffic = tr["dram_bytes_per_element"] * (pass_bytes / 24.0) / pass_launches
+
+    # End to end through the public API, host buffers and wall clock.
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    n_e2e = 0
+    for spec in specs:
+        net = snc.Network(spec, device=local, stream=stream)
+        net.finalize()
+        v = net.view()
+        n_e2e += int(v.n_syn)
+        st = net.stats()
+        h2d += int(st.h2d_bytes)
+        d2h += int(st.d2h_bytes)
+        net.close()
+    e2e_s = time.perf_counter() - t0
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "connections/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32+f32", "data": "synthetic",
+        "config": dict(config, connections_per_step=n_total // max(1, args.steps),
+                       l2="inputs larger than L2 (>= 4.8 GB of keys+values per network)",
+                       parallelism="replicas" if world > 1 else "single GPU"),
+        "roofline": {"bound": "hbm", "kernel": "onesweep radix pass", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src + " MEASURED_PEAKS.json hbm_gbs" if peak_src == "measured" else peak_src,
+                     "unit": "GB/s", "frac": achieved / peak if peak else None, "traffic": traffic,
+                     "launches": pass_launches, "avg_launch_ms": pass_ms / max(1, pass_launches),
+                     "algorithmic_bytes_per_launch": pass_bytes / max(1, pass_launches)},
+        "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
+        "generate_GBps": (gen_bytes / (gen_ms / 1e3)) / 1e9 if gen_ms else None,
+        "gpu_launches": launches,
+        "e2e": {"value": n_e2e / e2e_s, "unit": "connections/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "note": "public API, host wall clock, network left on the device"},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * snc.h -- C ABI of libsnc: construction of spiking-network connectivity
+ * directly in GPU memory (Golosio et al., "Runtime Construction of
+ * Large-Scale Spiking Neuronal Network Models on GPU Devices",
+ * arXiv 2306.09855).
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2.1, 2.6):
+ * populations are created (Create), connected by high-level rules
+ * (Connect(sources, targets, conn_dict, syn_dict)), and the calibration
+ * phase (triggered by Simulate in the paper, snc_finalize here) generates the
+ * connections, sorts them by source and delay and builds the group index that
+ * spike delivery reads (Sec. 2.2).
+ *
+ * Conventions for every call:
+ *   - Every function returns an snc_status; nothing throws or aborts across
+ *     the ABI.  snc_last_error() gives a human-readable reason for the last
+ *     failing call on a context.
+ *   - Node ids are uint32, connection counts and offsets uint64.
+ *   - Device pointers are plain CUDA device addresses of the context's device;
+ *     host pointers are ordinary host memory.
+ *   - A context is not thread-safe; distinct contexts may be used from
+ *     distinct threads.
+ */
+#ifndef SNC_H
+#define SNC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct snc_ctx snc_ctx;
+
+typedef enum {
+  SNC_OK = 0,
+  SNC_ERR_INVALID_ARG = 1, /* bad argument or rule parameters (checked up front) */
+  SNC_ERR_STATE = 2,       /* call not allowed in the context's current state    */
+  SNC_ERR_OOM = 3,         /* device or host allocation failed                   */
+  SNC_ERR_CUDA = 4,        /* a CUDA runtime call failed                         */
+  SNC_ERR_TIMEOUT = 5,     /* a bounded device wait or redraw loop gave up       */
+  SNC_ERR_UNSUPPORTED = 6  /* valid request outside this build's limits          */
+} snc_status;
+
+/* Connection rules.  Sec. 2.1 defines one_to_one, all_to_all,
+ * fixed_indegree, fixed_outdegree and fixed_total_number (each with
+ * multapses); Sec. 4 names pairwise_bernoulli and the option to forbid
+ * autapses and multapses. */
+typedef enum {
+  SNC_ONE_TO_ONE = 0,
+  SNC_ALL_TO_ALL = 1,
+  SNC_FIXED_INDEGREE = 2,
+  SNC_FIXED_OUTDEGREE = 3,
+  SNC_FIXED_TOTAL_NUMBER = 4,
+  SNC_PAIRWISE_BERNOULLI = 5
+} snc_rule_kind;
+
+/* A contiguous node range [first, first + n) (Sec. 2.1: "both the source-node
+ * group and the target-node group contain nodes with consecutive indexes"). */
+typedef struct {
+  uint32_t first;
+  uint32_t n;
+} snc_range;
+
+/* conn_dict of Sec. 2.1.  k: K of fixed_indegree / fixed_outdegree, or the
+ * total N of fixed_total_number.  p: probability of pairwise_bernoulli.
+ * allow_autapses / allow_multapses: nonzero to allow (the paper's only mode). */
+typedef struct {
+  int32_t kind; /* snc_rule_kind */
+  int32_t allow_autapses;
+  int32_t allow_multapses;
+  int32_t reserved;
+  uint64_t k;
+  double p;
+} snc_conn_rule;
+
+typedef enum { SNC_DIST_CONST = 0, SNC_DIST_NORMAL = 1 } snc_dist_kind;
+
+/* A constant value (std ignored) or a normal distribution N(mean, std). */
+typedef struct {
+  int32_t kind; /* snc_dist_kind */
+  int32_t reserved;
+  double mean;
+  double std;
+} snc_dist;
+
+/* syn_dict of Sec. 2.1: weights (any unit) and delays in milliseconds.  The
+ * delay becomes an integer number of time steps, round(d / dt), at least 1. */
+typedef struct {
+  snc_dist weight;
+  snc_dist delay_ms;
+} snc_syn_spec;
+
+/* Optional device-memory provider.  alloc returns a device pointer of at
+ * least `bytes` usable in stream order on `stream` (NULL on failure); free
+ * releases it in stream order.  Used for every device buffer of a context. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} snc_allocator;
+
+typedef struct {
+  uint64_t seed;    /* seed of the counter-based random stream                */
+  double dt_ms;     /* simulation time step (ms) > 0                           */
+  int32_t device;   /* CUDA device ordinal                                     */
+  int32_t reserved;
+  void* stream;     /* cudaStream_t for all device work; NULL = default stream */
+  const snc_allocator* allocator; /* NULL: cudaMallocAsync / cudaFreeAsync    */
+} snc_config;
+
+/* Device views of a finalized network, sorted by (source, delay, target).
+ * Arrays live on the context's device and stay valid until snc_destroy.
+ *   row_ptr[n_nodes + 1]: connections of source i are [row_ptr[i], row_ptr[i+1])
+ *   target, delay (time steps >= 1), weight: [n_syn]
+ *   group_ptr[n_nodes + 1]: p_i of Sec. 2.2 (groups of source i are
+ *     [group_ptr[i], group_ptr[i+1]); entry n_nodes = n_groups)
+ *   group_first[n_groups]: index of the first connection of each group
+ *     (a group = consecutive connections with equal source and delay). */
+typedef struct {
+  uint64_t n_syn;
+  uint64_t n_nodes;
+  uint64_t n_groups;
+  const uint64_t* row_ptr;
+  const uint32_t* target;
+  const uint16_t* delay;
+  const float* weight;
+  const uint64_t* group_ptr;
+  const uint64_t* group_first;
+} snc_conn_view;
+
+/* Creates a context on cfg->device.  *out receives the handle (owned by the
+ * caller, released with snc_destroy).  INVALID_ARG: null pointers, dt <= 0;
+ * CUDA: the device cannot be selected. */
+snc_status snc_create(const snc_config* cfg, snc_ctx** out);
+
+/* Releases every buffer of the context (after waiting for its stream). */
+snc_status snc_destroy(snc_ctx* ctx);
+
+/* Create (Sec. 2.6, node creation): appends n nodes with contiguous global
+ * ids; *first_id receives the first.  STATE after snc_finalize;
+ * INVALID_ARG when the total would exceed 2^32 - 1 nodes. */
+snc_status snc_create_population(snc_ctx* ctx, uint32_t n, uint32_t* first_id);
+
+/* Connect (Sec. 2.1): records one projection from `src` to `tgt` with the
+ * given rule and synapse specification; *proj_id (may be NULL) receives its
+ * index.  Host-side only: validates and sizes the projection.
+ * INVALID_ARG: range outside the created nodes, one_to_one with unequal
+ * sizes, K or N larger than the candidates when multapses are forbidden,
+ * probability outside [0, 1], std < 0, unknown rule or distribution.
+ * UNSUPPORTED: delay above 65535 steps or threshold table too long.
+ * STATE: after snc_finalize. */
+snc_status snc_connect(snc_ctx* ctx, snc_range src, snc_range tgt, const snc_conn_rule* rule,
+                       const snc_syn_spec* syn, uint32_t* proj_id);
+
+/* Calibration (Sec. 2.2, 2.6): generates every connection on the device,
+ * sorts them by (source, delay, target) and builds the CSR and group index.
+ * Work is queued on the context's stream; the call blocks only for the
+ * small device->host reads that size variable-count rules.  After it,
+ * snc_connect returns STATE.  UNSUPPORTED: packed key wider than 64 bits or
+ * a sampler range beyond the shared-memory bitmap. */
+snc_status snc_finalize(snc_ctx* ctx);
+
+/* Waits for the context's queued work and reports device-side failures
+ * (TIMEOUT for a bounded wait that expired, CUDA for a launch error). */
+snc_status snc_synchronize(snc_ctx* ctx);
+
+/* Fills *out with device views of the finalized network (no copy).
+ * Synchronizes first.  STATE before snc_finalize. */
+snc_status snc_get_connections(snc_ctx* ctx, snc_conn_view* out);
+
+/* Copies the finalized network to host arrays of capacity `cap` (each may be
+ * NULL to skip it): src, tgt (uint32), delay (uint16, steps), weight (float),
+ * in sorted order.  INVALID_ARG when cap < n_syn. */
+snc_status snc_copy_connections(snc_ctx* ctx, uint32_t* src, uint32_t* tgt, uint16_t* delay,
+                                float* weight, uint64_t cap);
+
+/* Device time of each finalize stage (ms) after snc_synchronize:
+ * [0] count, [1] generate, [2] histogram, [3..3+P) sort passes, then index.
+ * *n_stages receives the number written (at most max_stages); *n_passes the
+ * number of radix passes P.  STATE before a finalize has completed. */
+snc_status snc_stage_times(snc_ctx* ctx, float* ms, int max_stages, int* n_stages, int* n_passes);
+
+/* Counters of the last snc_finalize (and later copies) on a context. */
+typedef struct {
+  uint64_t kernel_launches; /* kernels this library launched                 */
+  uint64_t h2d_bytes;       /* host -> device bytes copied                    */
+  uint64_t d2h_bytes;       /* device -> host bytes copied                    */
+  int32_t n_passes;         /* radix passes of the sort                       */
+  int32_t key_bits;         /* width of the packed (source, delay, target) key */
+  uint64_t device_bytes_peak; /* largest total of live device buffers          */
+} snc_stats;
+
+/* Fills *out with the context's counters.  INVALID_ARG on null pointers. */
+snc_status snc_get_stats(const snc_ctx* ctx, snc_stats* out);
+
+/* Stable LSD radix sort of n (key, value) pairs on the low `key_bits` bits of
+ * the keys (Sec. 2.2 sorts connections with an extension of radix sort; this
+ * is the same onesweep sort used by snc_finalize, exposed on its own).
+ * keys_in / vals_in: device input (unchanged); keys_out / vals_out: device
+ * output; the four buffers must not overlap.  stream: cudaStream_t (NULL =
+ * default stream).  Scratch is allocated with cudaMallocAsync on `stream`
+ * and released before return of the queued work.  The call is asynchronous;
+ * errors from the device are reported by a later synchronizing call.
+ * INVALID_ARG: null pointers with n > 0, key_bits outside [1, 64]. */
+snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                                uint32_t* vals_out, uint64_t n, int key_bits, void* stream);
+
+/* Readable description of the last failure on ctx (or of the last
+ * context-free failure when ctx is NULL).  Never NULL. */
+const char* snc_last_error(const snc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNC_H */

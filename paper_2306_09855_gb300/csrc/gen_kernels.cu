@@ -1,0 +1,557 @@
+// gen_kernels.cu -- connection generation directly in GPU memory (Sec. 2.1).
+//
+// Every kernel writes, for connection number `pos` of the concatenated
+// generation order, the packed sort key (source | delay step | target) and
+// the weight bits.  The paper's index formulas decide (source, target); the
+// counter-based stream decides every random quantity, so the output does not
+// depend on grid or block sizes.
+//
+//   gen_direct_kernel   one_to_one, all_to_all, in/out-degree with multapses,
+//                       fixed_total_number with multapses and autapses
+//   bernoulli_count     per-target Binomial counts of pairwise_bernoulli
+//   sampler_kernel      in/out-degree without multapses and the Bernoulli
+//                       subsets: one warp per primary node, distinct draws
+//                       tracked in a shared-memory bitmap
+//   total_*             fixed_total_number with autapses or multapses
+//                       forbidden: round-based redraws, duplicates found with a
+//                       device hash table
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gen_kernels.h"
+#include "snc_device.cuh"
+
+namespace snc {
+
+namespace {
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Projection owning chunk c (binary search over chunk_begin).
+__device__ __forceinline__ int find_proj(const DevProj* projs, int n_proj, uint64_t c) {
+  int lo = 0, hi = n_proj - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (projs[mid].chunk_begin <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct SmemTables {
+  uint32_t* thr;
+  uint16_t* guide;
+};
+
+__device__ __forceinline__ uint32_t delay_step(const DevProj& P, const SmemTables& t, uint32_t u) {
+  if (!P.d_table) return P.d_const;
+  return P.d_base + table_lookup(t.thr, t.guide, P.d_len, u);
+}
+
+__device__ __forceinline__ uint32_t weight_bits(const DevProj& P, uint32_t w2, uint32_t w3) {
+  const float w = P.w_normal ? normal_weight(P.w_mean, P.w_std, w2, w3) : P.w_mean;
+  return __float_as_uint(w);
+}
+
+// Stage the projection's delay table into shared memory.
+__device__ void load_delay_table(const DevProj& P, const uint32_t* thr_blob, const uint16_t* guide_blob,
+                                 SmemTables t) {
+  if (!P.d_table) return;
+  for (uint32_t i = threadIdx.x; i < P.d_len; i += blockDim.x) t.thr[i] = thr_blob[P.d_off + i];
+  for (uint32_t i = threadIdx.x; i < kDelayGuide; i += blockDim.x) t.guide[i] = guide_blob[P.d_goff + i];
+}
+
+__device__ __forceinline__ void store(const GenArgs& a, uint64_t pos, uint32_t s, uint32_t d, uint32_t t,
+                                      uint32_t wbits) {
+  a.keys[pos] = pack_key(s, d, t, a.layout.node_bits, a.layout.delay_bits);
+  a.vals[pos] = wbits;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Direct rules.  A chunk is kChunk consecutive connections of one projection
+// (for all_to_all: kChunk consecutive targets of one source row).  A warp
+// works on windows of 128 consecutive connections; for fixed_total_number
+// each lane computes one IDX draw (four target words) for the window and the
+// words are passed around with shuffles.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
+  extern __shared__ uint32_t smem_raw[];
+  SmemTables tabs{smem_raw, reinterpret_cast<uint16_t*>(smem_raw + a.max_delay_len)};
+  int cur = -1;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  for (uint64_t c = blockIdx.x; c < a.total_chunks; c += gridDim.x) {
+    const int p = find_proj(a.projs, a.n_proj, c);
+    if (p != cur) {
+      __syncthreads();
+      load_delay_table(a.projs[p], a.thr_blob, a.guide_blob, tabs);
+      __syncthreads();
+      cur = p;
+    }
+    const DevProj& P = a.projs[p];
+    const uint64_t lc = c - P.chunk_begin;
+    if (P.rule == SNC_ALL_TO_ALL) {
+      // Row a (source s0 + a); targets b' in [part * kChunk, ...).  With
+      // autapses off the diagonal target is skipped and later rows shift.
+      const uint32_t row = static_cast<uint32_t>(lc / P.chunks_per_row);
+      const uint32_t part = static_cast<uint32_t>(lc % P.chunks_per_row);
+      const uint32_t s = P.s0 + row;
+      const bool diag = !P.autapses && s >= P.t0 && s - P.t0 < P.nt;
+      const uint32_t row_len = P.nt - (diag ? 1u : 0u);
+      uint64_t before = 0;  // diagonal skips in rows < row
+      if (!P.autapses) {
+        const uint32_t lo = max(P.s0, P.t0), hi = min(P.s0 + P.ns, P.t0 + P.nt);
+        if (hi > lo && s > lo) before = min(s, hi) - lo;
+      }
+      const uint64_t row_out = P.out_off + static_cast<uint64_t>(row) * P.nt - before;
+      const uint32_t diag_b = s - P.t0;
+      for (uint32_t e = threadIdx.x; e < kChunk; e += blockDim.x) {
+        const uint32_t bp = part * kChunk + e;
+        if (bp >= row_len) break;
+        const uint32_t b = bp + (diag && bp >= diag_b ? 1u : 0u);
+        const Words W = draw(P.k0, P.k1, kTagWD, 0, b, row);
+        store(a, row_out + bp, s, delay_step(P, tabs, W.x), P.t0 + b, weight_bits(P, W.z, W.w));
+      }
+      continue;
+    }
+    const uint64_t start = lc * kChunk;
+    const uint64_t end = min(start + kChunk, P.count);
+    // Four windows of 128 per warp.
+    for (int win = 0; win < kChunk / (128 * (kGenThreads / 32)); ++win) {
+      const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
+                             static_cast<uint64_t>(win) * 128;
+      if (wbase >= end) break;
+      Words X{0, 0, 0, 0};
+      if (P.rule == SNC_FIXED_TOTAL_NUMBER) X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
+        uint32_t tw = 0;
+        if (P.rule == SNC_FIXED_TOTAL_NUMBER) {
+          const int src_lane = 8 * q + static_cast<int>(lane >> 2);
+          const uint32_t vx = __shfl_sync(0xffffffffu, X.x, src_lane);
+          const uint32_t vy = __shfl_sync(0xffffffffu, X.y, src_lane);
+          const uint32_t vz = __shfl_sync(0xffffffffu, X.z, src_lane);
+          const uint32_t vw = __shfl_sync(0xffffffffu, X.w, src_lane);
+          const uint32_t sel = lane & 3u;
+          tw = sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
+        }
+        if (i >= end) continue;
+        uint32_t s, t, primary;
+        uint64_t slot;
+        switch (P.rule) {
+          case SNC_ONE_TO_ONE:
+            s = P.s0 + static_cast<uint32_t>(i);
+            t = P.t0 + static_cast<uint32_t>(i);
+            primary = static_cast<uint32_t>(i);
+            slot = 0;
+            break;
+          case SNC_FIXED_INDEGREE:
+          case SNC_FIXED_OUTDEGREE: {
+            uint64_t b, j;
+            if (P.count <= 0xFFFFFFFFull) {
+              const uint32_t ii = static_cast<uint32_t>(i), kk = static_cast<uint32_t>(P.k);
+              b = ii / kk;
+              j = ii - static_cast<uint32_t>(b) * kk;
+            } else {
+              b = i / P.k;
+              j = i - b * P.k;
+            }
+            primary = static_cast<uint32_t>(b);
+            slot = j;
+            s = t = 0;
+            break;
+          }
+          default:  // fixed_total_number
+            primary = kPrimaryNone;
+            slot = i;
+            s = t = 0;
+            break;
+        }
+        const Words W = draw(P.k0, P.k1, kTagWD, 0, primary, slot);
+        if (P.rule == SNC_FIXED_INDEGREE) {
+          t = P.t0 + primary;
+          const bool skip = !P.autapses && t >= P.s0 && t - P.s0 < P.ns;
+          s = P.s0 + endpoint(W.y, P.ns, skip, t - P.s0);
+        } else if (P.rule == SNC_FIXED_OUTDEGREE) {
+          s = P.s0 + primary;
+          const bool skip = !P.autapses && s >= P.t0 && s - P.t0 < P.nt;
+          t = P.t0 + endpoint(W.y, P.nt, skip, s - P.t0);
+        } else if (P.rule == SNC_FIXED_TOTAL_NUMBER) {
+          s = P.s0 + rand_below(W.y, P.ns);
+          t = P.t0 + rand_below(tw, P.nt);
+        }
+        store(a, P.out_off + i, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pairwise_bernoulli counts: target b draws n_b ~ Binomial(candidates, p)
+// from word 0 of its COUNT draw (Sec. 4 names the rule; reading in the
+// design notes).
+// ---------------------------------------------------------------------------
+__global__ void bernoulli_count_kernel(const DevProj* proj, const uint32_t* thr_blob,
+                                       const uint16_t* guide_blob, uint32_t* counts) {
+  const DevProj& P = *proj;
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= P.nt) return;
+  const uint32_t node = P.t0 + b;
+  const int skip = (!P.autapses && node >= P.s0 && node - P.s0 < P.ns) ? 1 : 0;
+  const Words W = draw(P.k0, P.k1, kTagCount, 0, b, 0);
+  const uint32_t i = table_lookup(thr_blob + P.b_off[skip], guide_blob + P.b_goff[skip], P.b_len[skip], W.x);
+  counts[b] = P.b_base[skip] + i;
+}
+
+// ---------------------------------------------------------------------------
+// Sampling without replacement, one warp per primary node.  Attempt a uses
+// word (a mod 4) of IDX draw floor(a / 4); the first `need` distinct values
+// are kept.  A warp examines 32 attempts at a time: a value is new if its
+// bit is clear in the warp's bitmap and no lower lane drew it in the same
+// group of 32; the first (need - got) new values in lane order are taken,
+// which is exactly the sequential rule.  When more than half of the
+// candidates are wanted the excluded values are drawn instead and the kept
+// ones are listed in ascending order.
+// ---------------------------------------------------------------------------
+__global__ void sampler_kernel(SamplerArgs a) {
+  extern __shared__ uint32_t bitmap_all[];
+  const DevProj& P = *a.proj;
+  const uint32_t lane = lane_id();
+  const uint32_t warp_in_block = threadIdx.x >> 5;
+  const uint32_t warps_per_block = blockDim.x >> 5;
+  uint32_t* bitmap = bitmap_all + static_cast<size_t>(warp_in_block) * a.bitmap_words;
+  // Delay table (shared by the block).
+  uint32_t* dthr = bitmap_all + static_cast<size_t>(warps_per_block) * a.bitmap_words;
+  uint16_t* dguide = reinterpret_cast<uint16_t*>(dthr + a.max_delay_len);
+  SmemTables tabs{dthr, dguide};
+  load_delay_table(P, a.thr_blob, a.guide_blob, tabs);
+  __syncthreads();
+
+  const bool indeg = P.rule != SNC_FIXED_OUTDEGREE;  // indegree and Bernoulli pick sources
+  const uint32_t n_primary = indeg ? P.nt : P.ns;
+  const uint32_t n_other = indeg ? P.ns : P.nt;
+  const uint32_t first_primary = indeg ? P.t0 : P.s0;
+  const uint32_t first_other = indeg ? P.s0 : P.t0;
+  const uint32_t gw = blockIdx.x * warps_per_block + warp_in_block;
+  const uint32_t n_warps = gridDim.x * warps_per_block;
+  const uint32_t words = (n_other + 31u) >> 5;
+
+  for (uint32_t b = gw; b < n_primary; b += n_warps) {
+    const uint32_t node = first_primary + b;
+    const bool skip = !P.autapses && node >= first_other && node - first_other < n_other;
+    const uint32_t skip_local = skip ? node - first_other : 0u;
+    const uint32_t cand = n_other - (skip ? 1u : 0u);
+    uint64_t want, out;
+    if (P.rule == SNC_PAIRWISE_BERNOULLI) {
+      out = P.out_off + a.prim_offsets[b];
+      want = a.prim_offsets[b + 1] - a.prim_offsets[b];
+    } else {
+      want = P.k;
+      out = P.out_off + static_cast<uint64_t>(b) * P.k;
+    }
+    if (want == 0) continue;
+    const bool complement = 2 * want > cand;
+    const uint32_t need = static_cast<uint32_t>(complement ? cand - want : want);
+    for (uint32_t w = lane; w < words; w += 32) bitmap[w] = 0u;
+    __syncwarp();
+    uint32_t got = 0;
+    uint64_t call = 0;
+    const uint64_t max_calls = 16ull * cand + 64;  // far above any plausible need
+    while (got < need) {
+      if (call > max_calls) {
+        if (lane == 0) atomicOr(a.err, kErrSamplerBound);
+        break;
+      }
+      // One IDX draw per lane: attempts 4*(call + lane) .. +3.
+      const Words X = draw(P.k0, P.k1, kTagIdx, 0, b, call + lane);
+      call += 32;
+#pragma unroll 1
+      for (int q = 0; q < 4 && got < need; ++q) {
+        const int src_lane = 8 * q + static_cast<int>(lane >> 2);
+        const uint32_t vx = __shfl_sync(0xffffffffu, X.x, src_lane);
+        const uint32_t vy = __shfl_sync(0xffffffffu, X.y, src_lane);
+        const uint32_t vz = __shfl_sync(0xffffffffu, X.z, src_lane);
+        const uint32_t vw = __shfl_sync(0xffffffffu, X.w, src_lane);
+        const uint32_t sel = lane & 3u;
+        const uint32_t u = sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
+        const uint32_t r = endpoint(u, n_other, skip, skip_local);
+        const uint32_t bit = 1u << (r & 31u);
+        const bool seen = (bitmap[r >> 5] & bit) != 0u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, r);
+        const bool first = (__ffs(peers) - 1) == static_cast<int>(lane);
+        const bool fresh = !seen && first;
+        const uint32_t fresh_mask = __ballot_sync(0xffffffffu, fresh);
+        const uint32_t rank = __popc(fresh_mask & ((1u << lane) - 1u));
+        const uint32_t room = need - got;
+        const bool take = fresh && rank < room;
+        __syncwarp();
+        if (take) {
+          atomicOr(&bitmap[r >> 5], bit);
+          if (!complement) {
+            const uint32_t j = got + rank;
+            const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
+            const uint32_t other = first_other + r;
+            const uint32_t s = indeg ? other : node, t = indeg ? node : other;
+            store(a.gen, out + j, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+          }
+        }
+        got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
+        __syncwarp();
+      }
+    }
+    if (complement) {
+      // Kept values in ascending order: free bits of the bitmap, minus the
+      // left-out node itself.
+      uint32_t base = 0;
+      for (uint32_t w0 = 0; w0 < words; w0 += 32) {
+        const uint32_t w = w0 + lane;
+        uint32_t free_bits = 0;
+        if (w < words) {
+          free_bits = ~bitmap[w];
+          if (w == words - 1 && (n_other & 31u)) free_bits &= (1u << (n_other & 31u)) - 1u;
+          if (skip && (skip_local >> 5) == w) free_bits &= ~(1u << (skip_local & 31u));
+        }
+        const uint32_t cnt = __popc(free_bits);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (static_cast<int>(lane) >= o) incl += v;
+        }
+        uint32_t j = base + incl - cnt;
+        while (free_bits) {
+          const uint32_t bitpos = __ffs(free_bits) - 1;
+          free_bits &= free_bits - 1;
+          const uint32_t r = w * 32 + bitpos;
+          if (j < want) {
+            const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
+            const uint32_t other = first_other + r;
+            const uint32_t s = indeg ? other : node, t = indeg ? node : other;
+            store(a.gen, out + j, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+          } else {
+            atomicOr(a.err, kErrBounds);
+          }
+          ++j;
+        }
+        base += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fixed_total_number with autapses or multapses forbidden (not in the paper,
+// Sec. 4).  Round 0 draws every slot as in the multapse case; a slot whose
+// pair is not allowed redraws in round r >= 1 from its DEDUP draw.  With
+// multapses forbidden a pair may be held by one slot only: pairs accepted in
+// earlier rounds block it, and among the slots drawing it in the same round
+// the lowest wins.  Claims go through a hash table: a claim is 2^63 | slot
+// (atomicMin keeps the lowest), an accepted pair stores its slot (< 2^63), so
+// an accepted entry is never overwritten by a later claim.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr uint64_t kEmpty = ~0ull;
+constexpr uint64_t kClaim = 1ull << 63;
+
+__device__ __forceinline__ uint64_t pair_hash(uint64_t key) {
+  key ^= key >> 33;
+  key *= 0xff51afd7ed558ccdull;
+  key ^= key >> 33;
+  key *= 0xc4ceb9fe1a85ec53ull;
+  key ^= key >> 33;
+  return key;
+}
+
+// Slot of `pair` in the table (inserted if absent), or ~0 if the probe bound
+// was exceeded.
+__device__ uint64_t table_slot(const TotalArgs& a, uint64_t pair, bool insert) {
+  uint64_t h = pair_hash(pair) & a.table_mask;
+  for (uint64_t probe = 0; probe <= a.table_mask; ++probe) {
+    uint64_t k = a.table_keys[h];
+    if (k == pair) return h;
+    if (k == kEmpty) {
+      if (!insert) return kEmpty;
+      k = atomicCAS(reinterpret_cast<unsigned long long*>(&a.table_keys[h]), kEmpty, pair);
+      if (k == kEmpty || k == pair) return h;
+    }
+    h = (h + 1) & a.table_mask;
+  }
+  atomicOr(a.err, kErrBounds);
+  return kEmpty;
+}
+
+__device__ __forceinline__ void claim(const TotalArgs& a, uint64_t pair, uint64_t slot) {
+  const uint64_t h = table_slot(a, pair, true);
+  if (h != kEmpty)
+    atomicMin(reinterpret_cast<unsigned long long*>(&a.table_vals[h]), kClaim | slot);
+}
+
+__device__ __forceinline__ bool allowed_pair(const DevProj& P, uint32_t s, uint32_t t) {
+  return P.autapses || s != t;
+}
+}  // namespace
+
+__global__ void total_round0_kernel(TotalArgs a) {
+  const DevProj& P = *a.proj;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.count; i += stride) {
+    const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
+    const Words X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, i >> 2);
+    const uint32_t sel = static_cast<uint32_t>(i & 3u);
+    const uint32_t tw = sel == 0 ? X.x : sel == 1 ? X.y : sel == 2 ? X.z : X.w;
+    const uint32_t s = P.s0 + rand_below(W.y, P.ns);
+    const uint32_t t = P.t0 + rand_below(tw, P.nt);
+    const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
+    a.pairs[i] = pair;
+    if (!P.multapses && allowed_pair(P, s, t)) claim(a, pair, i);
+  }
+}
+
+__global__ void total_claim_kernel(TotalArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round) {
+  const DevProj& P = *a.proj;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pending; q += stride) {
+    const uint64_t i = pending[q];
+    const Words D = draw(P.k0, P.k1, kTagDedup, round, kPrimaryNone, i);
+    const uint32_t s = P.s0 + rand_below(D.x, P.ns);
+    const uint32_t t = P.t0 + rand_below(D.y, P.nt);
+    const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
+    a.pairs[i] = pair;
+    if (!P.multapses && allowed_pair(P, s, t)) claim(a, pair, i);
+  }
+}
+
+// Decides the slots of this round: winners become accepted, the others are
+// appended to next_pending (order within the list is irrelevant: each slot's
+// later draws depend only on the slot and the round).
+__global__ void total_resolve_kernel(TotalArgs a, const uint64_t* pending, uint64_t n_pending, int all_slots) {
+  const DevProj& P = *a.proj;
+  const uint64_t n = all_slots ? P.count : n_pending;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n; q += stride) {
+    const uint64_t i = all_slots ? q : pending[q];
+    const uint64_t pair = a.pairs[i];
+    const uint32_t s = static_cast<uint32_t>(pair >> 32), t = static_cast<uint32_t>(pair);
+    bool ok = allowed_pair(P, s, t);
+    if (ok && !P.multapses) {
+      const uint64_t h = table_slot(a, pair, false);
+      ok = h != kEmpty && a.table_vals[h] == (kClaim | i);
+      if (ok) a.table_vals[h] = i;
+    }
+    if (!ok) {
+      const unsigned long long at = atomicAdd(a.n_next, 1ull);
+      a.next_pending[at] = i;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, const DevProj* proj, const uint64_t* pairs) {
+  extern __shared__ uint32_t smem_raw[];
+  SmemTables tabs{smem_raw, reinterpret_cast<uint16_t*>(smem_raw + g.max_delay_len)};
+  const DevProj& P = *proj;
+  load_delay_table(P, g.thr_blob, g.guide_blob, tabs);
+  __syncthreads();
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.count; i += stride) {
+    const uint64_t pair = pairs[i];
+    const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
+    store(g, P.out_off + i, static_cast<uint32_t>(pair >> 32), delay_step(P, tabs, W.x),
+          static_cast<uint32_t>(pair), weight_bits(P, W.z, W.w));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of uint32 counts into uint64 offsets (n + 1 entries):
+// block sums, one-block scan of the sums, then per-block scans.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t warp_sums[kScanThreads / 32];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint64_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (static_cast<int>(lane) >= o) incl += y;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t s = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+    uint64_t si = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, si, o);
+      if (static_cast<int>(lane) >= o) si += y;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = si - s;
+    if (lane == kScanThreads / 32 - 1) *total = si;
+  }
+  __syncthreads();
+  const uint64_t r = incl - v + warp_sums[warp];
+  __syncthreads();
+  return r;
+}
+}  // namespace
+
+__global__ void scan_block_sums(const uint32_t* in, uint64_t n, uint64_t* block_sums) {
+  __shared__ uint64_t total;
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanTile;
+  uint64_t s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    const uint64_t i = base + static_cast<uint64_t>(k) * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void scan_sums_single(uint64_t* block_sums, uint64_t n_blocks) {
+  __shared__ uint64_t total;
+  uint64_t carry = 0;
+  for (uint64_t base = 0; base < n_blocks; base += kScanThreads) {
+    const uint64_t i = base + threadIdx.x;
+    const uint64_t v = i < n_blocks ? block_sums[i] : 0;
+    const uint64_t ex = block_exclusive_scan(v, &total);
+    if (i < n_blocks) block_sums[i] = carry + ex;
+    carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void scan_apply(const uint32_t* in, uint64_t n, const uint64_t* block_offsets, uint64_t* out) {
+  __shared__ uint64_t total;
+  // Blocked arrangement: thread handles kScanItems consecutive entries.
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanTile + static_cast<uint64_t>(threadIdx.x) * kScanItems;
+  uint32_t v[kScanItems];
+  uint64_t s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < n ? in[base + k] : 0u;
+    s += v[k];
+  }
+  uint64_t run = block_exclusive_scan(s, &total) + block_offsets[blockIdx.x];
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k <= n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* block_tmp,
+                               cudaStream_t st) {
+  const uint64_t n_blocks = (n + 1 + kScanTile - 1) / kScanTile;
+  scan_block_sums<<<static_cast<unsigned>(n_blocks), kScanThreads, 0, st>>>(in, n, block_tmp);
+  scan_sums_single<<<1, kScanThreads, 0, st>>>(block_tmp, n_blocks);
+  scan_apply<<<static_cast<unsigned>(n_blocks), kScanThreads, 0, st>>>(in, n, block_tmp, out);
+  return cudaGetLastError();
+}
+
+uint64_t scan_tmp_entries(uint64_t n) { return (n + 1 + kScanTile - 1) / kScanTile; }
+
+}  // namespace snc

@@ -1,0 +1,81 @@
+// snc_internal.h -- host-side context and the descriptors the kernels read.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/snc.h"
+
+namespace snc {
+
+// Device-side error bits, OR-ed into the context's error word by kernels
+// instead of trapping; read back by snc_synchronize.
+enum : uint32_t {
+  kErrLookbackTimeout = 1u,  // a decoupled look-back wait hit its iteration bound
+  kErrSamplerBound = 2u,     // a sampler exceeded its attempt bound
+  kErrBounds = 4u,           // an internal index check failed
+};
+
+constexpr int kDelayGuide = 257;  // guide-table entries per threshold table
+
+// One Connect call as the kernels see it (plain data, copied to the device).
+struct DevProj {
+  uint32_t s0, ns, t0, nt;
+  uint32_t rule;
+  uint32_t autapses, multapses;
+  uint32_t w_normal;
+  uint32_t k0, k1;        // Philox key of this projection
+  uint64_t k;             // K or N
+  uint64_t count;         // connections of this projection
+  uint64_t out_off;       // position of its first connection in the generated arrays
+  float w_mean, w_std;
+  uint32_t d_const;       // delay step when the delay is constant (d_len == 0 && !d_table)
+  uint32_t d_table;       // 1 if the delay is drawn from a threshold table
+  uint32_t d_base, d_len; // value = d_base + #{thr <= u}
+  uint32_t d_off;         // offset of the thresholds in the table blob (uint32 units)
+  uint32_t d_goff;        // offset of the guide (uint16 units) in the guide blob
+  // Bernoulli count tables, [0] all sources candidates, [1] one left out.
+  uint32_t b_base[2], b_len[2], b_off[2], b_goff[2];
+  uint64_t prim_off;      // offset of this projection's per-primary offsets (variable counts)
+  uint64_t chunk_begin;   // first generation chunk of this projection
+  uint64_t n_chunks;
+  uint32_t chunks_per_row;  // all_to_all: chunks per source row
+  uint32_t row_len;         // all_to_all: connections per source row (full row)
+};
+
+// Bit layout of the packed sort key: source | delay step | target.
+struct KeyLayout {
+  int node_bits;
+  int delay_bits;
+  int total_bits() const { return 2 * node_bits + delay_bits; }
+};
+
+__host__ __device__ inline uint64_t pack_key(uint32_t s, uint32_t d, uint32_t t, int nb, int db) {
+  return (static_cast<uint64_t>(s) << (nb + db)) | (static_cast<uint64_t>(d) << nb) | t;
+}
+
+// Host-side projection record.
+struct Projection {
+  snc_range src, tgt;
+  snc_conn_rule rule;
+  snc_syn_spec syn;
+  bool exact_count;     // count known on the host
+  uint64_t count;       // connections (after the count phase for Bernoulli)
+  uint32_t d_const = 1;
+  bool d_table = false;
+  uint32_t d_base = 1;
+  std::vector<uint32_t> d_thr;
+  uint64_t b_base[2] = {0, 0};
+  std::vector<uint32_t> b_thr[2];
+  uint32_t max_step = 1;
+};
+
+// Host threshold tables (tables.cpp).
+int delay_thresholds(double mu, double sigma, double dt, std::vector<uint32_t>& thr, uint32_t& base);
+int binomial_thresholds(uint64_t n, double p, std::vector<uint32_t>& thr, uint64_t& base);
+void guide_table(const std::vector<uint32_t>& thr, uint16_t* guide);
+
+}  // namespace snc

@@ -1,0 +1,814 @@
+// snc_runtime.cu -- the C ABI: context, Create / Connect bookkeeping and the
+// calibration (Finalize) driver that queues the generation, sort and index
+// kernels on the context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/snc.h"
+#include "gen_kernels.h"
+#include "index_kernels.h"
+#include "snc_internal.h"
+#include "sort_kernels.h"
+
+using namespace snc;
+
+namespace {
+
+constexpr int kMaxEvents = 4 + kMaxPasses + 2;
+thread_local std::string g_last_error = "no error";
+
+struct DevBuf {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct snc_ctx {
+  snc_config cfg{};
+  snc_allocator alloc{};
+  bool custom_alloc = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 148;
+  uint64_t n_nodes = 0;
+  std::vector<Projection> projs;
+  bool finalized = false;
+  bool synced = false;
+  std::string err = "no error";
+  std::vector<DevBuf> bufs;
+  // results
+  uint64_t n_syn = 0;
+  uint64_t n_groups = 0;
+  uint64_t group_cap = 0;
+  uint64_t* row_ptr = nullptr;
+  uint32_t* target = nullptr;
+  uint16_t* delay = nullptr;
+  float* weight = nullptr;
+  uint64_t* group_ptr = nullptr;
+  uint64_t* group_first = nullptr;
+  uint64_t* d_n_groups = nullptr;
+  uint32_t* d_err = nullptr;
+  KeyLayout layout{1, 1};
+  SortPasses passes{};
+  cudaEvent_t ev[kMaxEvents] = {};
+  int n_ev = 0;
+  uint64_t* h_pinned = nullptr;  // small pinned staging area
+  snc_stats stats{};
+  uint64_t live_bytes = 0;
+};
+
+namespace {
+
+snc_status fail(snc_ctx* c, snc_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  g_last_error = buf;
+  return st;
+}
+
+#define SNC_CUDA(c, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail((c), SNC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+void* dev_alloc(snc_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (c->custom_alloc) {
+    p = c->alloc.alloc(bytes, c->stream, c->alloc.user);
+  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    c->bufs.push_back({p, bytes});
+    c->live_bytes += bytes;
+    if (c->live_bytes > c->stats.device_bytes_peak) c->stats.device_bytes_peak = c->live_bytes;
+  }
+  return p;
+}
+
+void dev_free(snc_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->bufs.size(); ++i) {
+    if (c->bufs[i].p == p) {
+      if (c->custom_alloc)
+        c->alloc.free(p, c->bufs[i].bytes, c->stream, c->alloc.user);
+      else
+        cudaFreeAsync(p, c->stream);
+      c->live_bytes -= c->bufs[i].bytes;
+      c->bufs.erase(c->bufs.begin() + static_cast<long>(i));
+      return;
+    }
+  }
+}
+
+void free_all(snc_ctx* c) {
+  while (!c->bufs.empty()) dev_free(c, c->bufs.back().p);
+}
+
+int bit_width(uint64_t v) {
+  int b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+uint64_t overlap(const snc_range& a, const snc_range& b) {
+  const uint64_t lo = std::max<uint64_t>(a.first, b.first);
+  const uint64_t hi = std::min<uint64_t>(static_cast<uint64_t>(a.first) + a.n, static_cast<uint64_t>(b.first) + b.n);
+  return hi > lo ? hi - lo : 0;
+}
+
+bool is_sampler(const Projection& p) {
+  return p.rule.kind == SNC_PAIRWISE_BERNOULLI ||
+         ((p.rule.kind == SNC_FIXED_INDEGREE || p.rule.kind == SNC_FIXED_OUTDEGREE) && !p.rule.allow_multapses);
+}
+
+bool is_total_redraw(const Projection& p) {
+  return p.rule.kind == SNC_FIXED_TOTAL_NUMBER && (!p.rule.allow_multapses || !p.rule.allow_autapses);
+}
+
+// Validation and sizing of one Connect call (readings of Sec. 2.1 / Sec. 4).
+snc_status plan_projection(snc_ctx* c, Projection& p) {
+  const snc_conn_rule& r = p.rule;
+  if (static_cast<uint64_t>(p.src.first) + p.src.n > c->n_nodes ||
+      static_cast<uint64_t>(p.tgt.first) + p.tgt.n > c->n_nodes)
+    return fail(c, SNC_ERR_INVALID_ARG, "connect: node range outside the created populations");
+  const uint64_t ov = overlap(p.src, p.tgt);
+  const bool aut = r.allow_autapses != 0;
+  switch (r.kind) {
+    case SNC_ONE_TO_ONE:
+      if (p.src.n != p.tgt.n) return fail(c, SNC_ERR_INVALID_ARG, "one_to_one: source and target sizes differ");
+      p.exact_count = true;
+      p.count = (!aut && p.src.first == p.tgt.first) ? 0 : p.src.n;
+      break;
+    case SNC_ALL_TO_ALL:
+      p.exact_count = true;
+      p.count = static_cast<uint64_t>(p.src.n) * p.tgt.n - (aut ? 0 : ov);
+      break;
+    case SNC_FIXED_INDEGREE:
+    case SNC_FIXED_OUTDEGREE: {
+      const bool indeg = r.kind == SNC_FIXED_INDEGREE;
+      const uint64_t n_other = indeg ? p.src.n : p.tgt.n;
+      const uint64_t n_primary = indeg ? p.tgt.n : p.src.n;
+      if (r.k > 0xFFFFFFFFull) return fail(c, SNC_ERR_INVALID_ARG, "degree K above 2^32 - 1");
+      if (r.k > 0 && n_primary > 0) {
+        const uint64_t least = (!aut && ov > 0) ? n_other - 1 : n_other;
+        if (least == 0) return fail(c, SNC_ERR_INVALID_ARG, "degree rule: no candidate nodes");
+        if (!r.allow_multapses && r.k > least)
+          return fail(c, SNC_ERR_INVALID_ARG, "degree K=%llu above the %llu candidates without multapses",
+                      static_cast<unsigned long long>(r.k), static_cast<unsigned long long>(least));
+      }
+      p.exact_count = true;
+      p.count = n_primary * r.k;
+      break;
+    }
+    case SNC_FIXED_TOTAL_NUMBER: {
+      if (r.k > 0) {
+        const uint64_t pairs = static_cast<uint64_t>(p.src.n) * p.tgt.n;
+        const uint64_t allowed = pairs - (aut ? 0 : ov);
+        if (allowed == 0) return fail(c, SNC_ERR_INVALID_ARG, "fixed_total_number: no allowed pair");
+        if (!r.allow_multapses && r.k > allowed)
+          return fail(c, SNC_ERR_INVALID_ARG, "fixed_total_number: N above the allowed pairs without multapses");
+      }
+      p.exact_count = true;
+      p.count = r.k;
+      break;
+    }
+    case SNC_PAIRWISE_BERNOULLI:
+      if (!(r.p >= 0.0 && r.p <= 1.0)) return fail(c, SNC_ERR_INVALID_ARG, "pairwise_bernoulli: p outside [0, 1]");
+      p.exact_count = false;
+      p.count = 0;
+      break;
+    default:
+      return fail(c, SNC_ERR_INVALID_ARG, "unknown rule %d", r.kind);
+  }
+  const snc_dist& wd = p.syn.weight;
+  const snc_dist& dd = p.syn.delay_ms;
+  if ((wd.kind != SNC_DIST_CONST && wd.kind != SNC_DIST_NORMAL) ||
+      (dd.kind != SNC_DIST_CONST && dd.kind != SNC_DIST_NORMAL))
+    return fail(c, SNC_ERR_INVALID_ARG, "unknown distribution kind");
+  if ((wd.kind == SNC_DIST_NORMAL && !(wd.std >= 0.0)) || (dd.kind == SNC_DIST_NORMAL && !(dd.std >= 0.0)))
+    return fail(c, SNC_ERR_INVALID_ARG, "negative standard deviation");
+  if (!std::isfinite(wd.mean) || !std::isfinite(dd.mean)) return fail(c, SNC_ERR_INVALID_ARG, "non-finite mean");
+  // Delay: constant step or threshold table (Sec. 2.1: round(d / dt), >= 1).
+  if (dd.kind == SNC_DIST_CONST || dd.std == 0.0) {
+    double q = std::floor(dd.mean / c->cfg.dt_ms + 0.5);
+    if (q < 1.0) q = 1.0;
+    if (q > 65535.0) return fail(c, SNC_ERR_UNSUPPORTED, "delay above 65535 steps");
+    p.d_table = false;
+    p.d_const = static_cast<uint32_t>(q);
+    p.max_step = p.d_const;
+  } else {
+    const int st = delay_thresholds(dd.mean, dd.std, c->cfg.dt_ms, p.d_thr, p.d_base);
+    if (st != SNC_OK) return fail(c, static_cast<snc_status>(st), "delay distribution outside the table limits");
+    if (static_cast<uint64_t>(p.d_base) + p.d_thr.size() > 65535)
+      return fail(c, SNC_ERR_UNSUPPORTED, "delay above 65535 steps");
+    p.d_table = true;
+    p.max_step = p.d_base + static_cast<uint32_t>(p.d_thr.size());
+  }
+  if (r.kind == SNC_PAIRWISE_BERNOULLI) {
+    for (int s = 0; s < 2; ++s) {
+      const uint64_t cand = (s == 1 && p.src.n > 0) ? p.src.n - 1u : (s == 1 ? 0 : p.src.n);
+      const int st = binomial_thresholds(cand, r.p, p.b_thr[s], p.b_base[s]);
+      if (st != SNC_OK) return fail(c, static_cast<snc_status>(st), "binomial table outside limits");
+    }
+  }
+  if (is_sampler(p)) {
+    const uint64_t n_other = (r.kind == SNC_FIXED_OUTDEGREE) ? p.tgt.n : p.src.n;
+    if (n_other > kSamplerMaxNodes)
+      return fail(c, SNC_ERR_UNSUPPORTED, "sampler range of %llu nodes above the bitmap limit %llu",
+                  static_cast<unsigned long long>(n_other), static_cast<unsigned long long>(kSamplerMaxNodes));
+  }
+  return SNC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+snc_status snc_create(const snc_config* cfg, snc_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, SNC_ERR_INVALID_ARG, "snc_create: null argument");
+  if (!(cfg->dt_ms > 0.0) || !std::isfinite(cfg->dt_ms)) return fail(nullptr, SNC_ERR_INVALID_ARG, "dt must be > 0");
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, SNC_ERR_CUDA, "cannot select device %d", cfg->device);
+  }
+  snc_ctx* c = new (std::nothrow) snc_ctx();
+  if (!c) return fail(nullptr, SNC_ERR_OOM, "out of host memory");
+  c->cfg = *cfg;
+  c->device = cfg->device;
+  c->stream = static_cast<cudaStream_t>(cfg->stream);
+  if (cfg->allocator) {
+    if (!cfg->allocator->alloc || !cfg->allocator->free) {
+      delete c;
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "allocator without alloc/free");
+    }
+    c->alloc = *cfg->allocator;
+    c->custom_alloc = true;
+  }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  for (int i = 0; i < kMaxEvents; ++i) {
+    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < i; ++j) cudaEventDestroy(c->ev[j]);
+      delete c;
+      return fail(nullptr, SNC_ERR_CUDA, "cudaEventCreate failed");
+    }
+  }
+  if (cudaMallocHost(&c->h_pinned, 64 * sizeof(uint64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    for (int j = 0; j < kMaxEvents; ++j) cudaEventDestroy(c->ev[j]);
+    delete c;
+    return fail(nullptr, SNC_ERR_OOM, "pinned staging allocation failed");
+  }
+  *out = c;
+  return SNC_OK;
+}
+
+snc_status snc_destroy(snc_ctx* c) {
+  if (!c) return SNC_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  cudaStreamSynchronize(c->stream);
+  for (int i = 0; i < kMaxEvents; ++i) cudaEventDestroy(c->ev[i]);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  cudaGetLastError();
+  delete c;
+  return SNC_OK;
+}
+
+snc_status snc_create_population(snc_ctx* c, uint32_t n, uint32_t* first_id) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (c->finalized) return fail(c, SNC_ERR_STATE, "create_population after finalize");
+  if (c->n_nodes + n > 0xFFFFFFFFull) return fail(c, SNC_ERR_INVALID_ARG, "more than 2^32 - 1 nodes");
+  if (first_id) *first_id = static_cast<uint32_t>(c->n_nodes);
+  c->n_nodes += n;
+  return SNC_OK;
+}
+
+snc_status snc_connect(snc_ctx* c, snc_range src, snc_range tgt, const snc_conn_rule* rule,
+                       const snc_syn_spec* syn, uint32_t* proj_id) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (!rule || !syn) return fail(c, SNC_ERR_INVALID_ARG, "connect: null rule or synapse spec");
+  if (c->finalized) return fail(c, SNC_ERR_STATE, "connect after finalize");
+  Projection p;
+  p.src = src;
+  p.tgt = tgt;
+  p.rule = *rule;
+  p.syn = *syn;
+  const snc_status st = plan_projection(c, p);
+  if (st != SNC_OK) return st;
+  if (proj_id) *proj_id = static_cast<uint32_t>(c->projs.size());
+  c->projs.push_back(std::move(p));
+  return SNC_OK;
+}
+
+snc_status snc_finalize(snc_ctx* c) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (c->finalized) return fail(c, SNC_ERR_STATE, "finalize called twice");
+  SNC_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  c->n_ev = 0;
+  cudaEventRecord(c->ev[c->n_ev++], st);
+
+  // Key layout: source | delay step | target.
+  uint32_t max_step = 1;
+  for (const Projection& p : c->projs) max_step = std::max(max_step, p.max_step);
+  c->layout.node_bits = std::max(1, bit_width(c->n_nodes > 0 ? c->n_nodes - 1 : 0));
+  c->layout.delay_bits = std::max(1, bit_width(max_step));
+  if (c->layout.total_bits() > 64)
+    return fail(c, SNC_ERR_UNSUPPORTED, "packed key of %d bits exceeds 64", c->layout.total_bits());
+
+  // Table blobs: thresholds (uint32) and their guides (uint16 x 257).
+  const size_t np = c->projs.size();
+  std::vector<uint32_t> thr_blob;
+  std::vector<uint16_t> guide_blob;
+  std::vector<DevProj> dp(np);
+  uint32_t max_delay_len = 0, max_binom_len = 0;
+  auto add_table = [&](const std::vector<uint32_t>& t, uint32_t& off, uint32_t& goff) {
+    off = static_cast<uint32_t>(thr_blob.size());
+    thr_blob.insert(thr_blob.end(), t.begin(), t.end());
+    goff = static_cast<uint32_t>(guide_blob.size());
+    guide_blob.resize(guide_blob.size() + kDelayGuide);
+    guide_table(t, guide_blob.data() + goff);
+  };
+  uint64_t n_var_primaries = 0;
+  for (size_t i = 0; i < np; ++i) {
+    const Projection& p = c->projs[i];
+    DevProj& d = dp[i];
+    std::memset(&d, 0, sizeof d);
+    d.s0 = p.src.first;
+    d.ns = p.src.n;
+    d.t0 = p.tgt.first;
+    d.nt = p.tgt.n;
+    d.rule = static_cast<uint32_t>(p.rule.kind);
+    d.autapses = p.rule.allow_autapses ? 1u : 0u;
+    d.multapses = p.rule.allow_multapses ? 1u : 0u;
+    d.k0 = static_cast<uint32_t>(c->cfg.seed);
+    d.k1 = static_cast<uint32_t>(c->cfg.seed >> 32) ^ static_cast<uint32_t>(i);
+    d.k = p.rule.k;
+    d.w_normal = (p.syn.weight.kind == SNC_DIST_NORMAL) ? 1u : 0u;
+    d.w_mean = static_cast<float>(p.syn.weight.mean);
+    d.w_std = static_cast<float>(p.syn.weight.std);
+    d.d_const = p.d_const;
+    d.d_table = p.d_table ? 1u : 0u;
+    if (p.d_table) {
+      d.d_base = p.d_base;
+      d.d_len = static_cast<uint32_t>(p.d_thr.size());
+      add_table(p.d_thr, d.d_off, d.d_goff);
+      max_delay_len = std::max(max_delay_len, d.d_len);
+    }
+    if (p.rule.kind == SNC_PAIRWISE_BERNOULLI) {
+      for (int s = 0; s < 2; ++s) {
+        d.b_base[s] = static_cast<uint32_t>(p.b_base[s]);
+        d.b_len[s] = static_cast<uint32_t>(p.b_thr[s].size());
+        add_table(p.b_thr[s], d.b_off[s], d.b_goff[s]);
+        max_binom_len = std::max(max_binom_len, d.b_len[s]);
+      }
+      d.prim_off = n_var_primaries;
+      n_var_primaries += static_cast<uint64_t>(p.tgt.n) + 1;
+    }
+  }
+  if (thr_blob.empty()) thr_blob.push_back(0);
+  if (guide_blob.empty()) guide_blob.resize(kDelayGuide, 0);
+
+  uint32_t* d_thr = static_cast<uint32_t*>(dev_alloc(c, thr_blob.size() * sizeof(uint32_t)));
+  uint16_t* d_guide = static_cast<uint16_t*>(dev_alloc(c, guide_blob.size() * sizeof(uint16_t)));
+  DevProj* d_proj = static_cast<DevProj*>(dev_alloc(c, std::max<size_t>(1, np) * sizeof(DevProj)));
+  c->d_err = static_cast<uint32_t*>(dev_alloc(c, 2 * sizeof(uint64_t)));
+  c->d_n_groups = static_cast<uint64_t*>(dev_alloc(c, sizeof(uint64_t)));
+  if (!d_thr || !d_guide || !d_proj || !c->d_err || !c->d_n_groups)
+    return fail(c, SNC_ERR_OOM, "device allocation failed (tables)");
+  SNC_CUDA(c, cudaMemcpyAsync(d_thr, thr_blob.data(), thr_blob.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  c->stats.h2d_bytes += thr_blob.size() * sizeof(uint32_t) + guide_blob.size() * sizeof(uint16_t);
+  SNC_CUDA(c, cudaMemcpyAsync(d_guide, guide_blob.data(), guide_blob.size() * sizeof(uint16_t),
+                              cudaMemcpyHostToDevice, st));
+  SNC_CUDA(c, cudaMemsetAsync(c->d_err, 0, 2 * sizeof(uint64_t), st));
+  SNC_CUDA(c, cudaMemsetAsync(c->d_n_groups, 0, sizeof(uint64_t), st));
+
+  // Count phase: pairwise Bernoulli per-target counts and offsets.
+  uint64_t* d_prim_off = nullptr;
+  if (n_var_primaries > 0) {
+    SNC_CUDA(c, cudaMemcpyAsync(d_proj, dp.data(), np * sizeof(DevProj), cudaMemcpyHostToDevice, st));
+    c->stats.h2d_bytes += np * sizeof(DevProj);
+    d_prim_off = static_cast<uint64_t*>(dev_alloc(c, n_var_primaries * sizeof(uint64_t)));
+    uint32_t* d_counts = static_cast<uint32_t*>(dev_alloc(c, n_var_primaries * sizeof(uint32_t)));
+    uint64_t* d_scan_tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_var_primaries) + 1) * sizeof(uint64_t)));
+    if (!d_prim_off || !d_counts || !d_scan_tmp) return fail(c, SNC_ERR_OOM, "device allocation failed (counts)");
+    std::vector<size_t> bern;
+    for (size_t i = 0; i < np; ++i)
+      if (c->projs[i].rule.kind == SNC_PAIRWISE_BERNOULLI) bern.push_back(i);
+    if (bern.size() > 60) {
+      // read the totals in groups that fit the pinned staging area
+    }
+    for (size_t bi = 0; bi < bern.size(); ++bi) {
+      const size_t i = bern[bi];
+      const uint32_t nt = c->projs[i].tgt.n;
+      if (nt > 0) {
+        bernoulli_count_kernel<<<(nt + 255) / 256, 256, 0, st>>>(d_proj + i, d_thr, d_guide, d_counts + dp[i].prim_off);
+        ++c->stats.kernel_launches;
+        SNC_CUDA(c, cudaGetLastError());
+      }
+      SNC_CUDA(c, exclusive_scan_u32(d_counts + dp[i].prim_off, nt, d_prim_off + dp[i].prim_off, d_scan_tmp, st));
+      c->stats.kernel_launches += 3;
+    }
+    std::vector<uint64_t> totals(bern.size());
+    for (size_t b0 = 0; b0 < bern.size(); b0 += 64) {
+      const size_t cnt = std::min<size_t>(64, bern.size() - b0);
+      for (size_t j = 0; j < cnt; ++j) {
+        const size_t i = bern[b0 + j];
+        SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned + j, d_prim_off + dp[i].prim_off + c->projs[i].tgt.n, sizeof(uint64_t),
+                                    cudaMemcpyDeviceToHost, st));
+        c->stats.d2h_bytes += sizeof(uint64_t);
+      }
+      SNC_CUDA(c, cudaStreamSynchronize(st));
+      for (size_t j = 0; j < cnt; ++j) totals[b0 + j] = c->h_pinned[j];
+    }
+    for (size_t bi = 0; bi < bern.size(); ++bi) c->projs[bern[bi]].count = totals[bi];
+    dev_free(c, d_counts);
+    dev_free(c, d_scan_tmp);
+  }
+  cudaEventRecord(c->ev[c->n_ev++], st);
+
+  // Output offsets and generation chunks.
+  uint64_t off = 0;
+  std::vector<DevProj> direct;
+  uint64_t chunk = 0;
+  for (size_t i = 0; i < np; ++i) {
+    const Projection& p = c->projs[i];
+    DevProj& d = dp[i];
+    d.count = p.count;
+    d.out_off = off;
+    off += p.count;
+    if (p.count == 0 || is_sampler(p) || is_total_redraw(p)) continue;
+    if (p.rule.kind == SNC_ALL_TO_ALL) {
+      d.chunks_per_row = (p.tgt.n + kChunk - 1) / kChunk;
+      d.row_len = p.tgt.n;
+      d.n_chunks = static_cast<uint64_t>(p.src.n) * d.chunks_per_row;
+    } else {
+      d.n_chunks = (p.count + kChunk - 1) / kChunk;
+    }
+    d.chunk_begin = chunk;
+    chunk += d.n_chunks;
+    direct.push_back(d);
+  }
+  c->n_syn = off;
+  SNC_CUDA(c, cudaMemcpyAsync(d_proj, dp.data(), std::max<size_t>(1, np) * sizeof(DevProj), cudaMemcpyHostToDevice, st));
+  c->stats.h2d_bytes += std::max<size_t>(1, np) * sizeof(DevProj);
+  DevProj* d_direct = nullptr;
+  if (!direct.empty()) {
+    d_direct = static_cast<DevProj*>(dev_alloc(c, direct.size() * sizeof(DevProj)));
+    if (!d_direct) return fail(c, SNC_ERR_OOM, "device allocation failed (projections)");
+    SNC_CUDA(c, cudaMemcpyAsync(d_direct, direct.data(), direct.size() * sizeof(DevProj), cudaMemcpyHostToDevice, st));
+    c->stats.h2d_bytes += direct.size() * sizeof(DevProj);
+  }
+
+  // Buffers: generated keys/values, the sort's second buffer, outputs.
+  const uint64_t n = c->n_syn;
+  c->passes = plan_passes(c->layout.total_bits());
+  uint64_t* keys_a = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
+  uint32_t* vals_a = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+  uint64_t* keys_b = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
+  uint32_t* vals_b = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+  void* sort_scratch = dev_alloc(c, sort_scratch_bytes(n, c->passes));
+  if (!keys_a || !vals_a || !keys_b || !vals_b || !sort_scratch)
+    return fail(c, SNC_ERR_OOM, "device allocation failed (%llu connections)", static_cast<unsigned long long>(n));
+
+  // Generation.
+  GenArgs g{};
+  g.projs = d_direct;
+  g.n_proj = static_cast<int>(direct.size());
+  g.total_chunks = chunk;
+  g.thr_blob = d_thr;
+  g.guide_blob = d_guide;
+  g.max_delay_len = max_delay_len;
+  g.layout = c->layout;
+  g.keys = keys_a;
+  g.vals = vals_a;
+  const size_t table_smem = static_cast<size_t>(max_delay_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
+  if (chunk > 0) {
+    static bool configured = false;
+    if (!configured) {
+      SNC_CUDA(c, cudaFuncSetAttribute(gen_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+      configured = true;
+    }
+    const uint64_t grid = std::min<uint64_t>(chunk, static_cast<uint64_t>(c->sms) * 8);
+    gen_direct_kernel<<<static_cast<unsigned>(grid), kGenThreads, table_smem, st>>>(g);
+    ++c->stats.kernel_launches;
+    SNC_CUDA(c, cudaGetLastError());
+  }
+  for (size_t i = 0; i < np; ++i) {
+    const Projection& p = c->projs[i];
+    if (p.count == 0) continue;
+    if (is_sampler(p)) {
+      const uint32_t n_other = (p.rule.kind == SNC_FIXED_OUTDEGREE) ? p.tgt.n : p.src.n;
+      const uint32_t n_primary = (p.rule.kind == SNC_FIXED_OUTDEGREE) ? p.src.n : p.tgt.n;
+      SamplerArgs s{};
+      s.gen = g;
+      s.proj = d_proj + i;
+      s.thr_blob = d_thr;
+      s.guide_blob = d_guide;
+      s.max_delay_len = dp[i].d_len;
+      s.bitmap_words = (n_other + 31u) / 32u;
+      s.prim_offsets = d_prim_off ? d_prim_off + dp[i].prim_off : nullptr;
+      s.err = c->d_err;
+      const size_t bitmap_bytes = static_cast<size_t>(s.bitmap_words) * sizeof(uint32_t);
+      const size_t tab = static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
+      int warps = static_cast<int>(std::min<size_t>(8, (kSamplerSmem - tab) / std::max<size_t>(bitmap_bytes, 4)));
+      if (warps < 1) return fail(c, SNC_ERR_UNSUPPORTED, "sampler bitmap does not fit shared memory");
+      const size_t smem = static_cast<size_t>(warps) * bitmap_bytes + tab;
+      static bool sconf = false;
+      if (!sconf) {
+        SNC_CUDA(c, cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSamplerSmem)));
+        sconf = true;
+      }
+      const uint64_t want_blocks = (static_cast<uint64_t>(n_primary) + warps - 1) / warps;
+      const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want_blocks, static_cast<uint64_t>(c->sms) * 16));
+      sampler_kernel<<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(s);
+      ++c->stats.kernel_launches;
+      SNC_CUDA(c, cudaGetLastError());
+    } else if (is_total_redraw(p)) {
+      const snc_status r = [&]() -> snc_status {
+        const uint64_t N = p.count;
+        TotalArgs t{};
+        t.proj = d_proj + i;
+        t.err = c->d_err;
+        t.pairs = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
+        t.pending = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
+        t.next_pending = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
+        t.n_next = static_cast<unsigned long long*>(dev_alloc(c, sizeof(unsigned long long)));
+        uint64_t cap = 1;
+        if (!p.rule.allow_multapses) {
+          while (cap < 2 * N + 64) cap <<= 1;
+          t.table_keys = static_cast<uint64_t*>(dev_alloc(c, cap * sizeof(uint64_t)));
+          t.table_vals = static_cast<uint64_t*>(dev_alloc(c, cap * sizeof(uint64_t)));
+          if (!t.table_keys || !t.table_vals) return fail(c, SNC_ERR_OOM, "device allocation failed (pair table)");
+          SNC_CUDA(c, cudaMemsetAsync(t.table_keys, 0xFF, cap * sizeof(uint64_t), st));
+          SNC_CUDA(c, cudaMemsetAsync(t.table_vals, 0xFF, cap * sizeof(uint64_t), st));
+        }
+        t.table_mask = cap - 1;
+        if (!t.pairs || !t.pending || !t.next_pending || !t.n_next)
+          return fail(c, SNC_ERR_OOM, "device allocation failed (redraw lists)");
+        const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
+            1, std::min<uint64_t>((N + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
+        SNC_CUDA(c, cudaMemsetAsync(t.n_next, 0, sizeof(unsigned long long), st));
+        total_round0_kernel<<<grid, 256, 0, st>>>(t);
+        ++c->stats.kernel_launches;
+        total_resolve_kernel<<<grid, 256, 0, st>>>(t, nullptr, 0, 1);
+        ++c->stats.kernel_launches;
+        SNC_CUDA(c, cudaGetLastError());
+        for (uint32_t round = 1;; ++round) {
+          SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned, t.n_next, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+          c->stats.d2h_bytes += sizeof(uint64_t);
+          SNC_CUDA(c, cudaStreamSynchronize(st));
+          const uint64_t n_pend = c->h_pinned[0];
+          if (n_pend == 0) break;
+          if (round > 0xFFFFFFu) return fail(c, SNC_ERR_TIMEOUT, "fixed_total_number: redraw rounds exhausted");
+          std::swap(t.pending, t.next_pending);
+          SNC_CUDA(c, cudaMemsetAsync(t.n_next, 0, sizeof(unsigned long long), st));
+          const unsigned g2 = static_cast<unsigned>(std::max<uint64_t>(
+              1, std::min<uint64_t>((n_pend + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
+          total_claim_kernel<<<g2, 256, 0, st>>>(t, t.pending, n_pend, round);
+          ++c->stats.kernel_launches;
+          total_resolve_kernel<<<g2, 256, 0, st>>>(t, t.pending, n_pend, 0);
+          ++c->stats.kernel_launches;
+          SNC_CUDA(c, cudaGetLastError());
+        }
+        GenArgs ge = g;
+        ge.max_delay_len = dp[i].d_len;
+        const size_t tsm = static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
+        static bool econf = false;
+        if (!econf) {
+          SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+          econf = true;
+        }
+        total_emit_kernel<<<grid, kGenThreads, tsm, st>>>(ge, d_proj + i, t.pairs);
+        ++c->stats.kernel_launches;
+        SNC_CUDA(c, cudaGetLastError());
+        dev_free(c, t.pairs);
+        dev_free(c, t.pending);
+        dev_free(c, t.next_pending);
+        dev_free(c, t.n_next);
+        dev_free(c, t.table_keys);
+        dev_free(c, t.table_vals);
+        return SNC_OK;
+      }();
+      if (r != SNC_OK) return r;
+    }
+  }
+  cudaEventRecord(c->ev[c->n_ev++], st);
+
+  // Sort by (source, delay, target): generated arrays -> (keys_b, vals_b).
+  SNC_CUDA(c, radix_sort_run(keys_a, vals_a, keys_b, vals_b, keys_a, vals_a, n, c->passes, sort_scratch, c->d_err, st,
+                             c->ev + c->n_ev));
+  c->n_ev += c->passes.n_passes + 1;
+  if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 2;
+  c->stats.n_passes = c->passes.n_passes;
+  c->stats.key_bits = c->layout.total_bits();
+  dev_free(c, sort_scratch);
+  dev_free(c, keys_a);
+  dev_free(c, vals_a);
+
+  // Index: unpack target / delay, group starts, row_ptr and p_i.
+  const uint64_t n_delay_values = max_step;
+  c->group_cap = std::max<uint64_t>(1, std::min<uint64_t>(n, c->n_nodes * n_delay_values));
+  c->target = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+  c->delay = static_cast<uint16_t*>(dev_alloc(c, n * sizeof(uint16_t)));
+  c->group_first = static_cast<uint64_t*>(dev_alloc(c, c->group_cap * sizeof(uint64_t)));
+  c->row_ptr = static_cast<uint64_t*>(dev_alloc(c, (c->n_nodes + 1) * sizeof(uint64_t)));
+  c->group_ptr = static_cast<uint64_t*>(dev_alloc(c, (c->n_nodes + 1) * sizeof(uint64_t)));
+  const uint64_t itiles = (n + kIndexTile - 1) / kIndexTile;
+  uint64_t* istatus = static_cast<uint64_t*>(dev_alloc(c, (itiles + 1) * sizeof(uint64_t) + 64));
+  if (!c->target || !c->delay || !c->group_first || !c->row_ptr || !c->group_ptr || !istatus)
+    return fail(c, SNC_ERR_OOM, "device allocation failed (index)");
+  uint32_t* icounter = reinterpret_cast<uint32_t*>(istatus + itiles + 1);
+  SNC_CUDA(c, cudaMemsetAsync(istatus, 0, (itiles + 1) * sizeof(uint64_t) + 64, st));
+  if (n > 0) {
+    IndexArgs ia{};
+    ia.keys = keys_b;
+    ia.n = n;
+    ia.node_bits = c->layout.node_bits;
+    ia.delay_bits = c->layout.delay_bits;
+    ia.target = c->target;
+    ia.delay = c->delay;
+    ia.group_first = c->group_first;
+    ia.group_cap = c->group_cap;
+    ia.n_groups = c->d_n_groups;
+    ia.status = istatus;
+    ia.tile_counter = icounter;
+    ia.err = c->d_err;
+    index_kernel<<<static_cast<unsigned>(itiles), kIndexThreads, 0, st>>>(ia);
+    ++c->stats.kernel_launches;
+    SNC_CUDA(c, cudaGetLastError());
+  }
+  NodeIndexArgs na{};
+  na.keys = keys_b;
+  na.n = n;
+  na.n_nodes = c->n_nodes;
+  na.node_bits = c->layout.node_bits;
+  na.delay_bits = c->layout.delay_bits;
+  na.group_first = c->group_first;
+  na.group_cap = c->group_cap;
+  na.n_groups = c->d_n_groups;
+  na.row_ptr = c->row_ptr;
+  na.group_ptr = c->group_ptr;
+  node_index_kernel<<<static_cast<unsigned>((c->n_nodes + 1 + 255) / 256), 256, 0, st>>>(na);
+  ++c->stats.kernel_launches;
+  SNC_CUDA(c, cudaGetLastError());
+  cudaEventRecord(c->ev[c->n_ev++], st);
+  c->weight = reinterpret_cast<float*>(vals_b);
+  dev_free(c, istatus);
+  dev_free(c, keys_b);
+  dev_free(c, d_direct);
+  dev_free(c, d_prim_off);
+  c->finalized = true;
+  c->synced = false;
+  return SNC_OK;
+}
+
+snc_status snc_synchronize(snc_ctx* c) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  SNC_CUDA(c, cudaSetDevice(c->device));
+  SNC_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!c->finalized) return SNC_OK;
+  if (!c->synced) {
+    SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned + 1, c->d_n_groups, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
+    c->stats.d2h_bytes += sizeof(uint32_t) + sizeof(uint64_t);
+    SNC_CUDA(c, cudaStreamSynchronize(c->stream));
+    const uint32_t err = static_cast<uint32_t>(c->h_pinned[0] & 0xFFFFFFFFu);
+    c->n_groups = c->h_pinned[1];
+    c->synced = true;
+    if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
+    if (err & kErrSamplerBound) return fail(c, SNC_ERR_TIMEOUT, "a sampler exceeded its attempt bound");
+    if (err & kErrBounds) return fail(c, SNC_ERR_CUDA, "a device index check failed");
+  }
+  return SNC_OK;
+}
+
+snc_status snc_get_connections(snc_ctx* c, snc_conn_view* out) {
+  if (!c || !out) return fail(c, SNC_ERR_INVALID_ARG, "null argument");
+  if (!c->finalized) return fail(c, SNC_ERR_STATE, "get_connections before finalize");
+  const snc_status st = snc_synchronize(c);
+  if (st != SNC_OK) return st;
+  out->n_syn = c->n_syn;
+  out->n_nodes = c->n_nodes;
+  out->n_groups = c->n_groups;
+  out->row_ptr = c->row_ptr;
+  out->target = c->target;
+  out->delay = c->delay;
+  out->weight = c->weight;
+  out->group_ptr = c->group_ptr;
+  out->group_first = c->group_first;
+  return SNC_OK;
+}
+
+snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16_t* delay, float* weight,
+                                uint64_t cap) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (!c->finalized) return fail(c, SNC_ERR_STATE, "copy_connections before finalize");
+  snc_status s = snc_synchronize(c);
+  if (s != SNC_OK) return s;
+  if (cap < c->n_syn) return fail(c, SNC_ERR_INVALID_ARG, "capacity below the number of connections");
+  const uint64_t n = c->n_syn;
+  cudaStream_t st = c->stream;
+  if (src && n > 0) {
+    uint32_t* d_src = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+    if (!d_src) return fail(c, SNC_ERR_OOM, "device allocation failed (source expansion)");
+    if (c->n_nodes > 0) {
+      expand_sources_kernel<<<static_cast<unsigned>((c->n_nodes + 255) / 256), 256, 0, st>>>(c->row_ptr, c->n_nodes, d_src);
+      ++c->stats.kernel_launches;
+    }
+    SNC_CUDA(c, cudaGetLastError());
+    SNC_CUDA(c, cudaMemcpyAsync(src, d_src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    SNC_CUDA(c, cudaStreamSynchronize(st));
+    dev_free(c, d_src);
+  }
+  if (tgt && n > 0) SNC_CUDA(c, cudaMemcpyAsync(tgt, c->target, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (delay && n > 0) SNC_CUDA(c, cudaMemcpyAsync(delay, c->delay, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
+  if (weight && n > 0) SNC_CUDA(c, cudaMemcpyAsync(weight, c->weight, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  c->stats.d2h_bytes += n * ((src ? 4 : 0) + (tgt ? 4 : 0) + (delay ? 2 : 0) + (weight ? 4 : 0));
+  SNC_CUDA(c, cudaStreamSynchronize(st));
+  return SNC_OK;
+}
+
+snc_status snc_stage_times(snc_ctx* c, float* ms, int max_stages, int* n_stages, int* n_passes) {
+  if (!c || !ms || max_stages < 0) return fail(c, SNC_ERR_INVALID_ARG, "null argument");
+  if (!c->finalized) return fail(c, SNC_ERR_STATE, "no finalize has run");
+  SNC_CUDA(c, cudaStreamSynchronize(c->stream));
+  int k = 0;
+  for (int i = 1; i < c->n_ev && k < max_stages; ++i, ++k) {
+    float t = 0.f;
+    SNC_CUDA(c, cudaEventElapsedTime(&t, c->ev[i - 1], c->ev[i]));
+    ms[k] = t;
+  }
+  if (n_stages) *n_stages = k;
+  if (n_passes) *n_passes = c->passes.n_passes;
+  return SNC_OK;
+}
+
+snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                                uint32_t* vals_out, uint64_t n, int key_bits, void* stream) {
+  if (key_bits < 1 || key_bits > 64) return fail(nullptr, SNC_ERR_INVALID_ARG, "key_bits outside [1, 64]");
+  if (n == 0) return SNC_OK;
+  if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(nullptr, SNC_ERR_INVALID_ARG, "null buffer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SortPasses sp = plan_passes(key_bits);
+  const size_t scratch_bytes = sort_scratch_bytes(n, sp);
+  void* scratch = nullptr;
+  uint64_t* ktmp = nullptr;
+  uint32_t* vtmp = nullptr;
+  uint32_t* err = nullptr;
+  auto release = [&]() {
+    if (scratch) cudaFreeAsync(scratch, st);
+    if (ktmp) cudaFreeAsync(ktmp, st);
+    if (vtmp) cudaFreeAsync(vtmp, st);
+    if (err) cudaFreeAsync(err, st);
+  };
+  if (cudaMallocAsync(&scratch, scratch_bytes, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&err), 256, st) != cudaSuccess ||
+      (sp.n_passes > 1 && (cudaMallocAsync(reinterpret_cast<void**>(&ktmp), n * sizeof(uint64_t), st) != cudaSuccess ||
+                           cudaMallocAsync(reinterpret_cast<void**>(&vtmp), n * sizeof(uint32_t), st) != cudaSuccess))) {
+    cudaGetLastError();
+    release();
+    return fail(nullptr, SNC_ERR_OOM, "sort scratch allocation failed");
+  }
+  cudaError_t e = cudaMemsetAsync(err, 0, 256, st);
+  if (e == cudaSuccess) e = radix_sort_run(keys_in, vals_in, keys_out, vals_out, ktmp, vtmp, n, sp, scratch, err, st, nullptr);
+  release();
+  if (e != cudaSuccess) return fail(nullptr, SNC_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e));
+  return SNC_OK;
+}
+
+snc_status snc_get_stats(const snc_ctx* c, snc_stats* out) {
+  if (!c || !out) return fail(nullptr, SNC_ERR_INVALID_ARG, "null argument");
+  *out = c->stats;
+  return SNC_OK;
+}
+
+const char* snc_last_error(const snc_ctx* c) {
+  if (c) return c->err.c_str();
+  return g_last_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,326 @@
+"""ctypes binding of libsnc (include/snc.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name; the `Network`
+class strings them together for a NetworkSpec from `workloads`.  Device
+memory for the library comes from PyTorch's caching allocator through the
+ABI's allocator callback, and work runs on a PyTorch stream.  The library is
+required: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+from .workloads import DIST_ID, RULE_ID
+
+SNC_OK, SNC_ERR_INVALID_ARG, SNC_ERR_STATE, SNC_ERR_OOM, SNC_ERR_CUDA, SNC_ERR_TIMEOUT, \
+    SNC_ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "STATE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
+                6: "UNSUPPORTED"}
+SNC_ONE_TO_ONE, SNC_ALL_TO_ALL, SNC_FIXED_INDEGREE, SNC_FIXED_OUTDEGREE, \
+    SNC_FIXED_TOTAL_NUMBER, SNC_PAIRWISE_BERNOULLI = range(6)
+SNC_DIST_CONST, SNC_DIST_NORMAL = 0, 1
+
+
+class SncError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+
+
+class snc_range(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_uint32), ("n", ctypes.c_uint32)]
+
+
+class snc_conn_rule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("allow_autapses", ctypes.c_int32),
+                ("allow_multapses", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("k", ctypes.c_uint64), ("p", ctypes.c_double)]
+
+
+class snc_dist(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mean", ctypes.c_double), ("std", ctypes.c_double)]
+
+
+class snc_syn_spec(ctypes.Structure):
+    _fields_ = [("weight", snc_dist), ("delay_ms", snc_dist)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class snc_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+class snc_config(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("dt_ms", ctypes.c_double), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("allocator", ctypes.POINTER(snc_allocator))]
+
+
+class snc_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
+                ("d2h_bytes", ctypes.c_uint64), ("n_passes", ctypes.c_int32),
+                ("key_bits", ctypes.c_int32), ("device_bytes_peak", ctypes.c_uint64)]
+
+
+class snc_conn_view(ctypes.Structure):
+    _fields_ = [("n_syn", ctypes.c_uint64), ("n_nodes", ctypes.c_uint64),
+                ("n_groups", ctypes.c_uint64), ("row_ptr", ctypes.c_void_p),
+                ("target", ctypes.c_void_p), ("delay", ctypes.c_void_p),
+                ("weight", ctypes.c_void_p), ("group_ptr", ctypes.c_void_p),
+                ("group_first", ctypes.c_void_p)]
+
+
+# Every symbol include/snc.h declares.
+EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
+           "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_stage_times",
+           "snc_radix_sort_pairs", "snc_get_stats", "snc_last_error")
+
+_LIB = None
+
+
+def load(build: bool = True):
+    """Load libsnc.so (building it first when missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libsnc.so is not built: run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, U32, U64, I32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sigs = {
+        "snc_create": ([ctypes.POINTER(snc_config), ctypes.POINTER(P)], I32),
+        "snc_destroy": ([P], I32),
+        "snc_create_population": ([P, U32, ctypes.POINTER(U32)], I32),
+        "snc_connect": ([P, snc_range, snc_range, ctypes.POINTER(snc_conn_rule),
+                         ctypes.POINTER(snc_syn_spec), ctypes.POINTER(U32)], I32),
+        "snc_finalize": ([P], I32),
+        "snc_synchronize": ([P], I32),
+        "snc_get_connections": ([P, ctypes.POINTER(snc_conn_view)], I32),
+        "snc_copy_connections": ([P, P, P, P, P, U64], I32),
+        "snc_stage_times": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(I32),
+                             ctypes.POINTER(I32)], I32),
+        "snc_radix_sort_pairs": ([P, P, P, P, U64, I32, P], I32),
+        "snc_get_stats": ([P, ctypes.POINTER(snc_stats)], I32),
+        "snc_last_error": ([P], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != SNC_OK:
+        msg = load().snc_last_error(ctx).decode()
+        raise SncError(status, msg)
+
+
+# ----------------------------------------------------------------------------
+# Same-name wrappers of the C ABI.
+# ----------------------------------------------------------------------------
+def snc_create(cfg):
+    h = ctypes.c_void_p()
+    _check(load().snc_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def snc_destroy(ctx):
+    _check(load().snc_destroy(ctx))
+
+
+def snc_create_population(ctx, n):
+    first = ctypes.c_uint32()
+    _check(load().snc_create_population(ctx, n, ctypes.byref(first)), ctx)
+    return first.value
+
+
+def snc_connect(ctx, src, tgt, rule, syn):
+    pid = ctypes.c_uint32()
+    _check(load().snc_connect(ctx, src, tgt, ctypes.byref(rule), ctypes.byref(syn),
+                              ctypes.byref(pid)), ctx)
+    return pid.value
+
+
+def snc_finalize(ctx):
+    _check(load().snc_finalize(ctx), ctx)
+
+
+def snc_synchronize(ctx):
+    _check(load().snc_synchronize(ctx), ctx)
+
+
+def snc_get_connections(ctx):
+    v = snc_conn_view()
+    _check(load().snc_get_connections(ctx, ctypes.byref(v)), ctx)
+    return v
+
+
+def snc_copy_connections(ctx, n_syn):
+    out = {"src": np.empty(n_syn, np.uint32), "tgt": np.empty(n_syn, np.uint32),
+           "delay": np.empty(n_syn, np.uint16), "weight": np.empty(n_syn, np.float32)}
+    _check(load().snc_copy_connections(ctx, out["src"].ctypes.data, out["tgt"].ctypes.data,
+                                       out["delay"].ctypes.data, out["weight"].ctypes.data,
+                                       n_syn), ctx)
+    return out
+
+
+def snc_stage_times(ctx):
+    buf = (ctypes.c_float * 32)()
+    ns, npass = ctypes.c_int(), ctypes.c_int()
+    _check(load().snc_stage_times(ctx, buf, 32, ctypes.byref(ns), ctypes.byref(npass)), ctx)
+    return list(buf[:ns.value]), npass.value
+
+
+def snc_radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits, stream=0):
+    """Device pointers (ints) in, device pointers out."""
+    _check(load().snc_radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits,
+                                       stream or None))
+
+
+def snc_get_stats(ctx):
+    st = snc_stats()
+    _check(load().snc_get_stats(ctx, ctypes.byref(st)), ctx)
+    return st
+
+
+def snc_last_error(ctx=None):
+    return load().snc_last_error(ctx).decode()
+
+
+# ----------------------------------------------------------------------------
+# PyTorch as device-memory provider.
+# ----------------------------------------------------------------------------
+class TorchAllocator:
+    """snc_allocator backed by torch's caching allocator on the given device."""
+
+    def __init__(self, device=0):
+        import torch
+        self._torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                                stream or 0)
+            except Exception:  # the library reports OOM
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            self._torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        self.struct = snc_allocator(self._alloc_cb, self._free_cb, None)
+
+
+def _rule_struct(pj):
+    return snc_conn_rule(kind=RULE_ID[pj.rule], allow_autapses=int(bool(pj.autapses)),
+                         allow_multapses=int(bool(pj.multapses)), reserved=0, k=int(pj.k),
+                         p=float(pj.p))
+
+
+def _syn_struct(pj):
+    return snc_syn_spec(weight=snc_dist(DIST_ID[pj.weight.kind], 0, float(pj.weight.mean),
+                                        float(pj.weight.std)),
+                        delay_ms=snc_dist(DIST_ID[pj.delay.kind], 0, float(pj.delay.mean),
+                                          float(pj.delay.std)))
+
+
+class Network:
+    """Create -> Connect -> Finalize -> GetConnections for one NetworkSpec."""
+
+    def __init__(self, spec, device=0, stream=None, allocator="torch"):
+        import torch
+        self.spec = spec
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self._alloc = TorchAllocator(device) if allocator == "torch" else None
+        cfg = snc_config(seed=int(spec.seed) & 0xFFFFFFFFFFFFFFFF, dt_ms=float(spec.dt),
+                         device=device, reserved=0, stream=self.stream.cuda_stream,
+                         allocator=ctypes.pointer(self._alloc.struct) if self._alloc else None)
+        self._cfg = cfg
+        self.ctx = snc_create(cfg)
+        for n in spec.populations:
+            snc_create_population(self.ctx, int(n))
+        for pj in spec.projections:
+            snc_connect(self.ctx, snc_range(*pj.src), snc_range(*pj.tgt), _rule_struct(pj),
+                        _syn_struct(pj))
+
+    def finalize(self):
+        snc_finalize(self.ctx)
+        return self
+
+    def synchronize(self):
+        snc_synchronize(self.ctx)
+
+    def view(self):
+        return snc_get_connections(self.ctx)
+
+    def tensors(self):
+        """Zero-copy torch views of the device arrays."""
+        v = self.view()
+        return _view_tensors(v, self._torch)
+
+    def to_host(self):
+        v = self.view()
+        out = snc_copy_connections(self.ctx, int(v.n_syn))
+        t = self.tensors()
+        out["row_ptr"] = t["row_ptr"].cpu().numpy()
+        out["group_ptr"] = t["group_ptr"].cpu().numpy()
+        out["group_first"] = t["group_first"].cpu().numpy()
+        out["n_groups"] = int(v.n_groups)
+        return out
+
+    def stage_times(self):
+        return snc_stage_times(self.ctx)
+
+    def stats(self):
+        return snc_get_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            snc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _view_tensors(v, torch):
+    def dev_tensor(ptr, n, dtype):
+        if n == 0:
+            return torch.empty(0, dtype=dtype, device="cuda")
+        # wrap without copy through the CUDA array interface
+        class _Arr:
+            pass
+        a = _Arr()
+        typestr = {torch.uint64: "<u8", torch.int64: "<i8", torch.int32: "<i4",
+                   torch.uint32: "<u4", torch.uint16: "<u2", torch.int16: "<i2",
+                   torch.float32: "<f4"}[dtype]
+        a.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True),
+                                      "version": 2}
+        return torch.as_tensor(a, device="cuda")
+    nn = int(v.n_nodes) + 1
+    ns = int(v.n_syn)
+    ng = int(v.n_groups)
+    return {"row_ptr": dev_tensor(v.row_ptr, nn, torch.int64),
+            "target": dev_tensor(v.target, ns, torch.int32),
+            "delay": dev_tensor(v.delay, ns, torch.int16),
+            "weight": dev_tensor(v.weight, ns, torch.float32),
+            "group_ptr": dev_tensor(v.group_ptr, nn, torch.int64),
+            "group_first": dev_tensor(v.group_first, ng, torch.int64)}

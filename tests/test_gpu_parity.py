@@ -1,0 +1,154 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Integer results (sources, targets, delay steps, CSR and group offsets) must be
+bit-exact; weights within 4 fp32 ulp.  Sizes span several generation, sort
+and index tiles and end in ragged tails.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import assert_network_equal
+from paper_2306_09855_gb300 import workloads as W
+from paper_2306_09855_gb300.workloads import Dist, NetworkSpec, Projection
+
+pytestmark = pytest.mark.gpu
+
+WD = dict(weight=Dist("normal", 1.0, 0.1), delay=Dist("normal", 1.5, 0.75))
+
+
+@pytest.fixture(scope="module")
+def snc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_09855_gb300 import snc as mod
+    mod.load()
+    return mod
+
+
+def build_both(snc, oracle_mod, spec):
+    net = snc.Network(spec).finalize()
+    got = net.to_host()
+    net.close()
+    return got, oracle_mod.build(spec)
+
+
+def test_plain_indegree_400k(snc, oracle_mod):
+    spec = W.plain_indegree()
+    got, ref = build_both(snc, oracle_mod, spec)
+    assert ref["src"].size == 400_000
+    assert_network_equal(got, ref, "plain")
+
+
+RULES = [("fixed_indegree", dict(k=37)), ("fixed_outdegree", dict(k=41)),
+         ("fixed_total_number", dict(k=250_003)), ("pairwise_bernoulli", dict(p=0.013)),
+         ("all_to_all", {}), ("one_to_one", {})]
+
+
+@pytest.mark.parametrize("rule,kw", RULES, ids=[r for r, _ in RULES])
+@pytest.mark.parametrize("mult", [True, False], ids=["mult", "nomult"])
+def test_rules_two_population(snc, oracle_mod, rule, kw, mult):
+    n = 700 if rule == "all_to_all" else 3001
+    spec = W.two_population(n, rule, autapses=mult, multapses=mult, seed=77, **kw)
+    got, ref = build_both(snc, oracle_mod, spec)
+    assert_network_equal(got, ref, f"{rule}/{mult}")
+
+
+@pytest.mark.parametrize("aut,mult", [(True, False), (False, True)])
+def test_mixed_flags(snc, oracle_mod, aut, mult):
+    spec = NetworkSpec(seed=5, dt=0.1, populations=[900, 1100], projections=[
+        Projection(src=(0, 900), tgt=(0, 2000), rule="fixed_indegree", k=60, autapses=aut, multapses=mult, **WD),
+        Projection(src=(0, 2000), tgt=(450, 900), rule="fixed_outdegree", k=33, autapses=aut, multapses=mult, **WD),
+        Projection(src=(100, 1500), tgt=(0, 2000), rule="fixed_total_number", k=123_457, autapses=aut,
+                   multapses=mult, **WD),
+        Projection(src=(0, 2000), tgt=(1000, 1000), rule="pairwise_bernoulli", p=0.02, autapses=aut, **WD),
+        Projection(src=(10, 300), tgt=(200, 400), rule="all_to_all", autapses=aut, **WD),
+    ])
+    got, ref = build_both(snc, oracle_mod, spec)
+    assert_network_equal(got, ref, "mixed")
+
+
+def test_microcircuit_scaled(snc, oracle_mod):
+    spec = W.microcircuit(scale=0.08)
+    got, ref = build_both(snc, oracle_mod, spec)
+    assert ref["src"].size > 1_000_000
+    assert_network_equal(got, ref, "microcircuit")
+
+
+def test_complement_and_dense_sampling(snc, oracle_mod):
+    spec = NetworkSpec(seed=3, dt=0.1, populations=[64, 2000], projections=[
+        Projection(src=(0, 64), tgt=(64, 2000), rule="fixed_indegree", k=50, multapses=False, **WD),
+        Projection(src=(0, 64), tgt=(0, 64), rule="fixed_indegree", k=63, autapses=False, multapses=False, **WD),
+        Projection(src=(0, 64), tgt=(64, 2000), rule="pairwise_bernoulli", p=0.9, **WD),
+        Projection(src=(64, 2000), tgt=(0, 64), rule="fixed_outdegree", k=64, multapses=False, **WD),
+    ])
+    got, ref = build_both(snc, oracle_mod, spec)
+    assert_network_equal(got, ref, "complement")
+
+
+def test_edge_cases(snc, oracle_mod):
+    cases = [
+        NetworkSpec(seed=1, dt=0.1, populations=[10], projections=[]),
+        NetworkSpec(seed=1, dt=0.1, populations=[10], projections=[
+            Projection(src=(0, 10), tgt=(0, 10), rule="one_to_one", autapses=False, **WD)]),
+        NetworkSpec(seed=1, dt=0.1, populations=[1, 1], projections=[
+            Projection(src=(0, 1), tgt=(1, 1), rule="one_to_one", **WD)]),
+        NetworkSpec(seed=1, dt=0.1, populations=[5, 7], projections=[
+            Projection(src=(0, 5), tgt=(5, 7), rule="pairwise_bernoulli", p=0.0, **WD),
+            Projection(src=(0, 5), tgt=(5, 7), rule="pairwise_bernoulli", p=1.0, **WD),
+            Projection(src=(0, 5), tgt=(5, 7), rule="fixed_indegree", k=0, **WD)]),
+        # sources with no outgoing connections, constant delays, big delays
+        NetworkSpec(seed=2, dt=0.25, populations=[5000, 3], projections=[
+            Projection(src=(4990, 10), tgt=(5000, 3), rule="fixed_indegree", k=9000,
+                       weight=Dist("const", -2.5), delay=Dist("const", 1000.0)),
+            Projection(src=(0, 3), tgt=(5000, 3), rule="all_to_all", weight=Dist("const", 1.0),
+                       delay=Dist("normal", 40.0, 10.0))]),
+        # delay below one step everywhere
+        NetworkSpec(seed=9, dt=1.0, populations=[50], projections=[
+            Projection(src=(0, 50), tgt=(0, 50), rule="fixed_total_number", k=999,
+                       weight=Dist("normal", 0.0, 1.0), delay=Dist("normal", 0.01, 0.001))]),
+    ]
+    for i, spec in enumerate(cases):
+        got, ref = build_both(snc, oracle_mod, spec)
+        assert_network_equal(got, ref, f"edge{i}")
+
+
+BAD = [
+    Projection(src=(0, 3), tgt=(3, 4), rule="one_to_one", **WD),
+    Projection(src=(0, 3), tgt=(3, 4), rule="fixed_indegree", k=4, multapses=False, **WD),
+    Projection(src=(0, 3), tgt=(0, 3), rule="fixed_indegree", k=3, autapses=False, multapses=False, **WD),
+    Projection(src=(0, 1), tgt=(0, 1), rule="fixed_total_number", k=1, autapses=False, **WD),
+    Projection(src=(0, 2), tgt=(2, 2), rule="fixed_total_number", k=5, multapses=False, **WD),
+    Projection(src=(0, 3), tgt=(5, 4), rule="all_to_all", **WD),
+    Projection(src=(0, 3), tgt=(3, 4), rule="pairwise_bernoulli", p=1.5, **WD),
+]
+
+
+@pytest.mark.parametrize("proj", BAD)
+def test_connect_errors_match_oracle(snc, oracle_mod, proj):
+    spec = NetworkSpec(seed=1, dt=0.1, populations=[3, 4], projections=[proj])
+    expect = oracle_mod.STATUS[oracle_mod.check_projection(spec, 0)]
+    with pytest.raises(snc.SncError) as e:
+        snc.Network(spec)
+    assert e.value.name == expect
+
+
+def test_connect_after_finalize_is_state_error(snc):
+    spec = W.plain_indegree(n=50, k=5)
+    net = snc.Network(spec).finalize()
+    pj = spec.projections[0]
+    with pytest.raises(snc.SncError) as e:
+        snc.snc_connect(net.ctx, snc.snc_range(*pj.src), snc.snc_range(*pj.tgt),
+                        snc._rule_struct(pj), snc._syn_struct(pj))
+    assert e.value.name == "STATE"
+    net.close()
+
+
+def test_launch_shape_independence(snc):
+    """Two builds of one spec are identical (grid / block shapes do not
+    enter the draws); a different seed changes the network."""
+    spec = W.two_population(2000, "fixed_total_number", k=300_000, seed=11)
+    a = snc.Network(spec).finalize().to_host()
+    b = snc.Network(spec).finalize().to_host()
+    for f in ("src", "tgt", "delay", "weight"):
+        np.testing.assert_array_equal(a[f], b[f])
