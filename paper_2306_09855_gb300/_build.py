@@ -45,6 +45,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
               "-I", os.path.join(HERE, "..", "include")] + ARCH
     if verbose:
         common += ["-Xptxas", "-v"]
+    if os.environ.get("SNC_BOUNDS_CHECK") == "1":
+        common += ["-DSNC_BOUNDS_CHECK"]
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "gen_kernels.h"
+#include "snc_check.cuh"
 #include "snc_device.cuh"
 
 namespace snc {
@@ -63,6 +64,7 @@ __device__ void load_delay_table(const DevProj& P, const uint32_t* thr_blob, con
 
 __device__ __forceinline__ void store(const GenArgs& a, uint64_t pos, uint32_t s, uint32_t d, uint32_t t,
                                       uint32_t wbits) {
+  if (!SNC_IN_BOUNDS(a.err, 1u, pos, a.cap)) return;
   a.keys[pos] = pack_key(s, d, t, a.layout.node_bits, a.layout.delay_bits);
   a.vals[pos] = wbits;
 }
@@ -443,7 +445,7 @@ __global__ void total_resolve_kernel(TotalArgs a, const uint64_t* pending, uint6
     }
     if (!ok) {
       const unsigned long long at = atomicAdd(a.n_next, 1ull);
-      a.next_pending[at] = i;
+      if (SNC_IN_BOUNDS(a.err, 2u, at, P.count)) a.next_pending[at] = i;
     }
   }
 }

@@ -25,6 +25,8 @@ struct GenArgs {
   KeyLayout layout;
   uint64_t* keys;
   uint32_t* vals;
+  uint64_t cap;    // entries of keys / vals
+  uint32_t* err;   // device error block (bounds checks)
 };
 
 struct SamplerArgs {

@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "index_kernels.h"
+#include "snc_check.cuh"
 #include "snc_internal.h"
 
 namespace snc {
@@ -115,6 +116,7 @@ __global__ void node_index_kernel(NodeIndexArgs a) {
     const uint64_t mid = (lo + hi) >> 1;
     if ((a.keys[mid] >> src_shift) < i) lo = mid + 1; else hi = mid;
   }
+  if (!SNC_IN_BOUNDS(nullptr, 21u, lo, a.n + 1)) return;
   a.row_ptr[i] = lo;
   const uint64_t ng = *a.n_groups;
   uint64_t glo = 0, ghi = ng < a.group_cap ? ng : a.group_cap;

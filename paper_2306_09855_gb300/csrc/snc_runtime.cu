@@ -394,7 +394,7 @@ snc_status snc_finalize(snc_ctx* c) {
   uint32_t* d_thr = static_cast<uint32_t*>(dev_alloc(c, thr_blob.size() * sizeof(uint32_t)));
   uint16_t* d_guide = static_cast<uint16_t*>(dev_alloc(c, guide_blob.size() * sizeof(uint16_t)));
   DevProj* d_proj = static_cast<DevProj*>(dev_alloc(c, std::max<size_t>(1, np) * sizeof(DevProj)));
-  c->d_err = static_cast<uint32_t*>(dev_alloc(c, 2 * sizeof(uint64_t)));
+  c->d_err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint64_t)));
   c->d_n_groups = static_cast<uint64_t*>(dev_alloc(c, sizeof(uint64_t)));
   if (!d_thr || !d_guide || !d_proj || !c->d_err || !c->d_n_groups)
     return fail(c, SNC_ERR_OOM, "device allocation failed (tables)");
@@ -402,7 +402,7 @@ snc_status snc_finalize(snc_ctx* c) {
   c->stats.h2d_bytes += thr_blob.size() * sizeof(uint32_t) + guide_blob.size() * sizeof(uint16_t);
   SNC_CUDA(c, cudaMemcpyAsync(d_guide, guide_blob.data(), guide_blob.size() * sizeof(uint16_t),
                               cudaMemcpyHostToDevice, st));
-  SNC_CUDA(c, cudaMemsetAsync(c->d_err, 0, 2 * sizeof(uint64_t), st));
+  SNC_CUDA(c, cudaMemsetAsync(c->d_err, 0, 8 * sizeof(uint64_t), st));
   SNC_CUDA(c, cudaMemsetAsync(c->d_n_groups, 0, sizeof(uint64_t), st));
 
   // Count phase: pairwise Bernoulli per-target counts and offsets.
@@ -472,8 +472,10 @@ snc_status snc_finalize(snc_ctx* c) {
     direct.push_back(d);
   }
   c->n_syn = off;
-  SNC_CUDA(c, cudaMemcpyAsync(d_proj, dp.data(), std::max<size_t>(1, np) * sizeof(DevProj), cudaMemcpyHostToDevice, st));
-  c->stats.h2d_bytes += std::max<size_t>(1, np) * sizeof(DevProj);
+  if (np > 0) {
+    SNC_CUDA(c, cudaMemcpyAsync(d_proj, dp.data(), np * sizeof(DevProj), cudaMemcpyHostToDevice, st));
+    c->stats.h2d_bytes += np * sizeof(DevProj);
+  }
   DevProj* d_direct = nullptr;
   if (!direct.empty()) {
     d_direct = static_cast<DevProj*>(dev_alloc(c, direct.size() * sizeof(DevProj)));
@@ -504,6 +506,8 @@ snc_status snc_finalize(snc_ctx* c) {
   g.layout = c->layout;
   g.keys = keys_a;
   g.vals = vals_a;
+  g.cap = n;
+  g.err = c->d_err;
   const size_t table_smem = static_cast<size_t>(max_delay_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
   if (chunk > 0) {
     static bool configured = false;
@@ -618,16 +622,23 @@ snc_status snc_finalize(snc_ctx* c) {
   }
   cudaEventRecord(c->ev[c->n_ev++], st);
 
-  // Sort by (source, delay, target): generated arrays -> (keys_b, vals_b).
-  SNC_CUDA(c, radix_sort_run(keys_a, vals_a, keys_b, vals_b, keys_a, vals_a, n, c->passes, sort_scratch, c->d_err, st,
-                             c->ev + c->n_ev));
+  // Sort by (source, delay, target).  The passes ping-pong between the two
+  // buffers; the result lands in (keys_b, vals_b) for an odd number of
+  // passes and back in (keys_a, vals_a) for an even number.
+  const bool odd = (c->passes.n_passes & 1) != 0;
+  uint64_t* keys_res = odd ? keys_b : keys_a;
+  uint32_t* vals_res = odd ? vals_b : vals_a;
+  uint64_t* keys_oth = odd ? keys_a : keys_b;
+  uint32_t* vals_oth = odd ? vals_a : vals_b;
+  SNC_CUDA(c, radix_sort_run(keys_a, vals_a, keys_res, vals_res, keys_oth, vals_oth, n, c->passes, sort_scratch,
+                             c->d_err, st, c->ev + c->n_ev));
   c->n_ev += c->passes.n_passes + 1;
   if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 2;
   c->stats.n_passes = c->passes.n_passes;
   c->stats.key_bits = c->layout.total_bits();
   dev_free(c, sort_scratch);
-  dev_free(c, keys_a);
-  dev_free(c, vals_a);
+  dev_free(c, keys_oth);
+  dev_free(c, vals_oth);
 
   // Index: unpack target / delay, group starts, row_ptr and p_i.
   const uint64_t n_delay_values = max_step;
@@ -645,7 +656,7 @@ snc_status snc_finalize(snc_ctx* c) {
   SNC_CUDA(c, cudaMemsetAsync(istatus, 0, (itiles + 1) * sizeof(uint64_t) + 64, st));
   if (n > 0) {
     IndexArgs ia{};
-    ia.keys = keys_b;
+    ia.keys = keys_res;
     ia.n = n;
     ia.node_bits = c->layout.node_bits;
     ia.delay_bits = c->layout.delay_bits;
@@ -662,7 +673,7 @@ snc_status snc_finalize(snc_ctx* c) {
     SNC_CUDA(c, cudaGetLastError());
   }
   NodeIndexArgs na{};
-  na.keys = keys_b;
+  na.keys = keys_res;
   na.n = n;
   na.n_nodes = c->n_nodes;
   na.node_bits = c->layout.node_bits;
@@ -676,9 +687,9 @@ snc_status snc_finalize(snc_ctx* c) {
   ++c->stats.kernel_launches;
   SNC_CUDA(c, cudaGetLastError());
   cudaEventRecord(c->ev[c->n_ev++], st);
-  c->weight = reinterpret_cast<float*>(vals_b);
+  c->weight = reinterpret_cast<float*>(vals_res);
   dev_free(c, istatus);
-  dev_free(c, keys_b);
+  dev_free(c, keys_res);
   dev_free(c, d_direct);
   dev_free(c, d_prim_off);
   c->finalized = true;
@@ -692,6 +703,7 @@ snc_status snc_synchronize(snc_ctx* c) {
   SNC_CUDA(c, cudaStreamSynchronize(c->stream));
   if (!c->finalized) return SNC_OK;
   if (!c->synced) {
+    SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned + 4, c->d_err, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
     SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned + 1, c->d_n_groups, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
     c->stats.d2h_bytes += sizeof(uint32_t) + sizeof(uint64_t);
@@ -701,7 +713,12 @@ snc_status snc_synchronize(snc_ctx* c) {
     c->synced = true;
     if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
     if (err & kErrSamplerBound) return fail(c, SNC_ERR_TIMEOUT, "a sampler exceeded its attempt bound");
-    if (err & kErrBounds) return fail(c, SNC_ERR_CUDA, "a device index check failed");
+    if (err & kErrBounds) {
+      const uint32_t* w = reinterpret_cast<const uint32_t*>(c->h_pinned + 4);
+      return fail(c, SNC_ERR_CUDA, "a device index check failed (site %u, index %llu, limit %llu)", w[2],
+                  static_cast<unsigned long long>(w[4] | (static_cast<uint64_t>(w[5]) << 32)),
+                  static_cast<unsigned long long>(w[6] | (static_cast<uint64_t>(w[7]) << 32)));
+    }
   }
   return SNC_OK;
 }

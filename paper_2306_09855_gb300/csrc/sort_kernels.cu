@@ -17,6 +17,7 @@
 
 #include <cstdint>
 
+#include "snc_check.cuh"
 #include "snc_internal.h"
 #include "sort_kernels.h"
 
@@ -252,6 +253,10 @@ __global__ void __launch_bounds__(TPB) onesweep_kernel(OnesweepArgs a) {
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
       if (!(pending & (1u << q))) continue;
+      if (!SNC_IN_BOUNDS(a.err, 12u, static_cast<uint64_t>(look[q]), static_cast<uint64_t>(tile))) {
+        pending &= ~(1u << q);
+        continue;
+      }
       const uint64_t v = ld_status(a.status + static_cast<size_t>(look[q]) * RADIX + tid * DPT + q);
       const bool fresh = ((v >> 48) & 0x3FFFull) == a.epoch;
       const uint64_t flag = fresh ? (v & (3ull << 62)) : 0ull;
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(TPB) onesweep_kernel(OnesweepArgs a) {
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
-    if (lpos[j] != 0xFFFFFFFFu) {
+    if (lpos[j] != 0xFFFFFFFFu && SNC_IN_BOUNDS(a.err, 10u, lpos[j], TILE)) {
       const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
       skeys[lpos[j]] = key[j];
       svals[lpos[j]] = a.vals_in[idx];
@@ -297,6 +302,7 @@ __global__ void __launch_bounds__(TPB) onesweep_kernel(OnesweepArgs a) {
     const uint64_t k = skeys[i];
     const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
     const uint64_t pos = glob[d] + i;
+    if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
     a.keys_out[pos] = k;
     a.vals_out[pos] = svals[i];
   }
@@ -382,9 +388,11 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 // Sorts n (key, value) pairs stably on the planned digits.  Pass 0 reads
 // (keys_in, vals_in); the passes alternate between (keys_tmp, vals_tmp) and
-// (keys_out, vals_out) so that the last one writes (keys_out, vals_out).
-// keys_tmp may alias keys_in (and vals_tmp vals_in): pass 0 has read the
-// input completely before pass 1 writes.  keys_tmp is unused for one pass.
+// (keys_out, vals_out) so that the last one writes (keys_out, vals_out):
+// with an even number of passes pass 0 writes keys_tmp.  keys_tmp may
+// therefore alias keys_in (and vals_tmp vals_in) only for an odd number of
+// passes (pass 0 has read the input completely before pass 1 writes it);
+// an aliased even-pass plan is rejected.  keys_tmp is unused for one pass.
 // scratch: sort_scratch_bytes(n, sp) bytes of device memory.
 // pass_events (optional, n_passes + 1 events): recorded after the histogram
 // and after each pass.
@@ -399,6 +407,9 @@ cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uin
   const int tile = onesweep_tile(sp.kernel_bits);
   const uint64_t tiles = (n + tile - 1) / tile;
   if (tiles > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  if ((sp.n_passes % 2 == 0) && (static_cast<const void*>(keys_tmp) == static_cast<const void*>(keys_in) ||
+                                 static_cast<const void*>(vals_tmp) == static_cast<const void*>(vals_in)))
+    return cudaErrorInvalidValue;
   unsigned char* p = static_cast<unsigned char*>(scratch);
   const size_t status_bytes = static_cast<size_t>(tiles) * (1u << sp.kernel_bits) * sizeof(uint64_t);
   uint64_t* status = reinterpret_cast<uint64_t*>(p);

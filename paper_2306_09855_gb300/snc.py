@@ -312,7 +312,7 @@ def _view_tensors(v, torch):
         typestr = {torch.uint64: "<u8", torch.int64: "<i8", torch.int32: "<i4",
                    torch.uint32: "<u4", torch.uint16: "<u2", torch.int16: "<i2",
                    torch.float32: "<f4"}[dtype]
-        a.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True),
+        a.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
                                       "version": 2}
         return torch.as_tensor(a, device="cuda")
     nn = int(v.n_nodes) + 1

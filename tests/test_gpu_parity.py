@@ -152,3 +152,20 @@ def test_launch_shape_independence(snc):
     b = snc.Network(spec).finalize().to_host()
     for f in ("src", "tgt", "delay", "weight"):
         np.testing.assert_array_equal(a[f], b[f])
+
+
+@pytest.mark.parametrize("n_nodes,delay,passes", [(4, Dist("const", 0.1), 1), (60, Dist("normal", 1.5, 0.75), 2),
+                                                  (3000, Dist("normal", 1.5, 0.75), 3),
+                                                  (18000, Dist("normal", 1.5, 0.75), 4)])
+def test_every_pass_parity(snc, oracle_mod, n_nodes, delay, passes):
+    """The sort's buffers alternate per pass, so the result buffer depends on
+    the parity of the pass count: cover 1, 2, 3 and 4 passes."""
+    half = n_nodes // 2
+    spec = NetworkSpec(seed=21, dt=0.1, populations=[half, n_nodes - half], projections=[
+        Projection(src=(0, n_nodes), tgt=(0, n_nodes), rule="fixed_total_number", k=150_001,
+                   weight=Dist("normal", 5.0, 1.0), delay=delay)])
+    net = snc.Network(spec).finalize()
+    got = net.to_host()
+    assert net.stats().n_passes == passes
+    net.close()
+    assert_network_equal(got, oracle_mod.build(spec), f"passes={passes}")
