@@ -207,6 +207,29 @@ snc_status snc_get_stats(const snc_ctx* ctx, snc_stats* out);
 snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                                 uint32_t* vals_out, uint64_t n, int key_bits, void* stream);
 
+/* Largest n accepted by snc_radix_sort_pairs_noalloc. */
+#define SNC_NOALLOC_MAX_PAIRS (1u << 19)
+
+/* The sort of snc_radix_sort_pairs for callers that must not allocate device
+ * memory (no counterpart in the paper).  Examples: a simulation loop that has
+ * handed all of the GPU's memory to its own pool, or latency-bound code that
+ * cannot afford the device synchronisation cudaMalloc / cudaFree may cause.
+ * It calls no allocator: its working memory (look-back words, histograms,
+ * the ping-pong buffers and an error word) is one 8 MiB file-scope device
+ * array that every GPU loading the library holds until the process exits.
+ * Arguments, layout and result are those of snc_radix_sort_pairs; the caller
+ * passes the input and output buffers.
+ * Limits and rules:
+ *   - n <= SNC_NOALLOC_MAX_PAIRS, else INVALID_ARG (nothing is queued);
+ *   - the first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture;
+ *   - every call shares the one array: calls whose work can overlap on the
+ *     GPU (other streams, other host threads) race and must be serialised
+ *     by the caller.  Each call clears what it needs before use.
+ * The call is asynchronous on `stream`; CUDA failures return CUDA. */
+snc_status snc_radix_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                                        uint32_t* vals_out, uint64_t n, int key_bits, void* stream);
+
 /* Readable description of the last failure on ctx (or of the last
  * context-free failure when ctx is NULL).  Never NULL. */
 const char* snc_last_error(const snc_ctx* ctx);

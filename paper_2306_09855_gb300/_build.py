@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsnc.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["snc_runtime.cu", "gen_kernels.cu", "sort_kernels.cu", "index_kernels.cu", "tables.cpp"]
+SOURCES = ["snc_runtime.cu", "gen_kernels.cu", "sort_kernels.cu", "index_kernels.cu", "tables.cpp",
+           "sort_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -242,6 +242,12 @@ snc_status plan_projection(snc_ctx* c, Projection& p) {
 
 }  // namespace
 
+namespace snc {
+// Lets other translation units report context-free failures through
+// snc_last_error(NULL).
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace snc
+
 extern "C" {
 
 snc_status snc_create(const snc_config* cfg, snc_ctx** out) {

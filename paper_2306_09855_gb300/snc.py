@@ -82,7 +82,8 @@ class snc_conn_view(ctypes.Structure):
 # Every symbol include/snc.h declares.
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_stage_times",
-           "snc_radix_sort_pairs", "snc_get_stats", "snc_last_error")
+           "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
+           "snc_last_error")
 
 _LIB = None
 
@@ -110,6 +111,7 @@ def load(build: bool = True):
         "snc_stage_times": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(I32),
                              ctypes.POINTER(I32)], I32),
         "snc_radix_sort_pairs": ([P, P, P, P, U64, I32, P], I32),
+        "snc_radix_sort_pairs_noalloc": ([P, P, P, P, U64, I32, P], I32),
         "snc_get_stats": ([P, ctypes.POINTER(snc_stats)], I32),
         "snc_last_error": ([P], ctypes.c_char_p),
     }
@@ -187,6 +189,16 @@ def snc_radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits, stre
     """Device pointers (ints) in, device pointers out."""
     _check(load().snc_radix_sort_pairs(keys_in, vals_in, keys_out, vals_out, n, key_bits,
                                        stream or None))
+
+
+def snc_radix_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, n, key_bits, stream=0):
+    """The same sort without any device allocation (scratch in a static
+    device array; n <= SNC_NOALLOC_MAX_PAIRS; calls must not overlap)."""
+    _check(load().snc_radix_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, n, key_bits,
+                                               stream or None))
+
+
+SNC_NOALLOC_MAX_PAIRS = 1 << 19
 
 
 def snc_get_stats(ctx):
