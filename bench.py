@@ -37,7 +37,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="snc", choices=["snc", "reference"])
-    ap.add_argument("--workload", default="rule_sweep", choices=["rule_sweep", "microcircuit", "plain", "small"])
+    ap.add_argument("--workload", default="rule_sweep",
+                    choices=["rule_sweep", "microcircuit", "plain", "small", "profile"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -58,8 +59,12 @@ def workload_specs(name):
     if name == "plain":
         return [W.plain_indegree()], {"workload": "2 x 1,000 nodes, fixed_indegree K=100, 400k connections",
                                       "seed": 1234, "dt_ms": 0.1}
+    if name == "profile":
+        return [W.two_population(100_000, "fixed_indegree", k=100)], {
+            "workload": "profiling case: 2 x 100,000 nodes, fixed_indegree K=100 (4e7 connections, "
+                        "same 43-bit key as the rule sweep)", "seed": 1234}
     return [W.rule_sweep("fixed_indegree", True, scale=0.1)], {
-        "workload": "small: 2 x 10,000 nodes fixed_indegree K=1000 (profiling case)", "seed": 1234}
+        "workload": "small: 2 x 10,000 nodes fixed_indegree K=1000", "seed": 1234}
 
 
 def measured_peaks():
