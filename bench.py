@@ -40,6 +40,8 @@ def parse_args():
     ap.add_argument("--workload", default="rule_sweep",
                     choices=["rule_sweep", "microcircuit", "plain", "small", "profile"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sort-digit-bits", type=int, default=None, help="tuning: widest radix digit")
+    ap.add_argument("--sort-group-tiles", type=int, default=None, help="tuning: tiles per look-back unit")
     return ap.parse_args()
 
 
@@ -196,6 +198,7 @@ def main():
         dist.init_process_group("nccl")
     from paper_2306_09855_gb300 import snc
     snc.load()
+    tuning = snc.snc_set_tuning(sort_digit_bits=args.sort_digit_bits, sort_group_tiles=args.sort_group_tiles)
     specs, config = workload_specs(args.workload)
     stream = torch.cuda.current_stream()
 
@@ -293,6 +296,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32+f32", "data": "synthetic",
         "config": dict(config, connections_per_step=n_total // max(1, args.steps),
+                       tuning={"sort_digit_bits": tuning.sort_digit_bits,
+                               "sort_group_tiles": tuning.sort_group_tiles,
+                               "gen_blocks_per_sm": tuning.gen_blocks_per_sm},
                        l2="inputs larger than L2 (>= 4.8 GB of keys+values per network)",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": {"bound": "hbm", "kernel": "onesweep radix pass", "achieved": achieved, "peak": peak,

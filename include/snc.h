@@ -92,9 +92,10 @@ typedef struct {
   snc_dist delay_ms;
 } snc_syn_spec;
 
-/* Optional device-memory provider.  alloc returns a device pointer of at
- * least `bytes` usable in stream order on `stream` (NULL on failure); free
- * releases it in stream order.  Used for every device buffer of a context. */
+/* Optional device-memory provider.  alloc returns a 256-byte aligned device
+ * pointer of at least `bytes` usable in stream order on `stream` (NULL on
+ * failure); free releases it in stream order.  Used for every device buffer
+ * of a context. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* user);
   void (*free)(void* ptr, size_t bytes, void* stream, void* user);
@@ -181,6 +182,24 @@ snc_status snc_copy_connections(snc_ctx* ctx, uint32_t* src, uint32_t* tgt, uint
  * *n_stages receives the number written (at most max_stages); *n_passes the
  * number of radix passes P.  STATE before a finalize has completed. */
 snc_status snc_stage_times(snc_ctx* ctx, float* ms, int max_stages, int* n_stages, int* n_passes);
+
+/* Process-wide kernel parameters (the autotuner's knobs).  They change
+ * speed only, never results: every draw is keyed by (projection, node, slot)
+ * and the sort is stable whatever its digit width. */
+typedef struct {
+  int32_t sort_digit_bits;   /* widest radix digit: 8..11 bits              */
+  int32_t sort_group_tiles;  /* 4096-key tiles per look-back unit: 1, 4, 8;
+                              * 0 = one tile, loaded by bulk copy (8-9 bit digits) */
+  int32_t gen_blocks_per_sm; /* generation grid = SMs x this (1..32)        */
+  int32_t reserved;
+} snc_tuning;
+
+/* Sets the parameters for later snc_finalize / sort calls of this process.
+ * INVALID_ARG for values outside the ranges above. */
+snc_status snc_set_tuning(const snc_tuning* t);
+
+/* Reads the current parameters. */
+snc_status snc_get_tuning(snc_tuning* t);
 
 /* Counters of the last snc_finalize (and later copies) on a context. */
 typedef struct {

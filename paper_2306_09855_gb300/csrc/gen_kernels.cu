@@ -62,11 +62,35 @@ __device__ void load_delay_table(const DevProj& P, const uint32_t* thr_blob, con
   for (uint32_t i = threadIdx.x; i < kDelayGuide; i += blockDim.x) t.guide[i] = guide_blob[P.d_goff + i];
 }
 
-__device__ __forceinline__ void store(const GenArgs& a, uint64_t pos, uint32_t s, uint32_t d, uint32_t t,
-                                      uint32_t wbits) {
+// Per-block digit counters in shared memory (at the start of the dynamic
+// shared memory of every generation kernel).
+struct BlockHist {
+  uint32_t* sh;
+  HistRegs r;
+};
+
+__device__ __forceinline__ BlockHist block_hist_begin(const GenArgs& a, uint32_t* smem) {
+  BlockHist h{smem, hist_regs(a.hist)};
+  hist_clear(h.sh, h.r);
+  return h;  // the caller synchronises before the first store
+}
+
+__device__ __forceinline__ void block_hist_end(const GenArgs& a, const BlockHist& h) {
+  __syncthreads();
+  if (h.r.n) hist_flush(h.sh, h.r, a.hist.global);
+}
+
+__device__ __forceinline__ uint32_t hist_words(const GenArgs& a) {
+  return a.hist.global ? static_cast<uint32_t>(a.hist.n_passes * a.hist.stride) : 0u;
+}
+
+__device__ __forceinline__ void store(const GenArgs& a, const BlockHist& h, uint64_t pos, uint32_t s, uint32_t d,
+                                      uint32_t t, uint32_t wbits) {
   if (!SNC_IN_BOUNDS(a.err, 1u, pos, a.cap)) return;
-  a.keys[pos] = pack_key(s, d, t, a.layout.node_bits, a.layout.delay_bits);
+  const uint64_t key = pack_key(s, d, t, a.layout.node_bits, a.layout.delay_bits);
+  a.keys[pos] = key;
   a.vals[pos] = wbits;
+  hist_add(h.sh, h.r, key);
 }
 
 }  // namespace
@@ -80,7 +104,10 @@ __device__ __forceinline__ void store(const GenArgs& a, uint64_t pos, uint32_t s
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
   extern __shared__ uint32_t smem_raw[];
-  SmemTables tabs{smem_raw, reinterpret_cast<uint16_t*>(smem_raw + a.max_delay_len)};
+  const uint32_t hw = hist_words(a);
+  SmemTables tabs{smem_raw + hw, reinterpret_cast<uint16_t*>(smem_raw + hw + a.max_delay_len)};
+  const BlockHist bh = block_hist_begin(a, smem_raw);
+  __syncthreads();
   int cur = -1;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   for (uint64_t c = blockIdx.x; c < a.total_chunks; c += gridDim.x) {
@@ -113,7 +140,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
         if (bp >= row_len) break;
         const uint32_t b = bp + (diag && bp >= diag_b ? 1u : 0u);
         const Words W = draw(P.k0, P.k1, kTagWD, 0, b, row);
-        store(a, row_out + bp, s, delay_step(P, tabs, W.x), P.t0 + b, weight_bits(P, W.z, W.w));
+        store(a, bh, row_out + bp, s, delay_step(P, tabs, W.x), P.t0 + b, weight_bits(P, W.z, W.w));
       }
       continue;
     }
@@ -184,10 +211,11 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
           s = P.s0 + rand_below(W.y, P.ns);
           t = P.t0 + rand_below(tw, P.nt);
         }
-        store(a, P.out_off + i, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+        store(a, bh, P.out_off + i, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
       }
     }
   }
+  block_hist_end(a, bh);
 }
 
 // ---------------------------------------------------------------------------
@@ -218,11 +246,13 @@ __global__ void bernoulli_count_kernel(const DevProj* proj, const uint32_t* thr_
 // ones are listed in ascending order.
 // ---------------------------------------------------------------------------
 __global__ void sampler_kernel(SamplerArgs a) {
-  extern __shared__ uint32_t bitmap_all[];
+  extern __shared__ uint32_t smem_all[];
   const DevProj& P = *a.proj;
   const uint32_t lane = lane_id();
   const uint32_t warp_in_block = threadIdx.x >> 5;
   const uint32_t warps_per_block = blockDim.x >> 5;
+  const BlockHist bh = block_hist_begin(a.gen, smem_all);
+  uint32_t* bitmap_all = smem_all + hist_words(a.gen);
   uint32_t* bitmap = bitmap_all + static_cast<size_t>(warp_in_block) * a.bitmap_words;
   // Delay table (shared by the block).
   uint32_t* dthr = bitmap_all + static_cast<size_t>(warps_per_block) * a.bitmap_words;
@@ -296,7 +326,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
             const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
             const uint32_t other = first_other + r;
             const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            store(a.gen, out + j, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+            store(a.gen, bh, out + j, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
           }
         }
         got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
@@ -331,7 +361,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
             const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
             const uint32_t other = first_other + r;
             const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            store(a.gen, out + j, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+            store(a.gen, bh, out + j, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
           } else {
             atomicOr(a.err, kErrBounds);
           }
@@ -342,6 +372,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
     }
     __syncwarp();
   }
+  block_hist_end(a.gen, bh);
 }
 
 // ---------------------------------------------------------------------------
@@ -385,7 +416,54 @@ __device__ uint64_t table_slot(const TotalArgs& a, uint64_t pair, bool insert) {
   return kEmpty;
 }
 
-__device__ __forceinline__ void claim(const TotalArgs& a, uint64_t pair, uint64_t slot) {
+// Packed form: key bits = pair_local, so one 64-bit atomic both matches the
+// pair and keeps the lowest claiming slot; an accepted entry (claim bit clear)
+// is smaller than every claim and therefore never replaced.
+__device__ __forceinline__ uint64_t packed_pair(const TotalArgs& a, const DevProj& P, uint32_t s, uint32_t t) {
+  return (static_cast<uint64_t>(s - P.s0) << a.t_bits) | (t - P.t0);
+}
+
+__device__ void claim_packed(const TotalArgs& a, uint64_t pair, uint64_t slot) {
+  const int sh = a.slot_bits + 1;
+  const uint64_t e = (pair << sh) | (1ull << a.slot_bits) | slot;
+  uint64_t h = pair_hash(pair) & a.table_mask;
+  for (uint64_t probe = 0; probe <= a.table_mask; ++probe) {
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(&a.table_keys[h]);
+    const uint64_t old = atomicCAS(w, kEmpty, e);
+    if (old == kEmpty) return;
+    if ((old >> sh) == pair) {
+      atomicMin(w, e);
+      return;
+    }
+    h = (h + 1) & a.table_mask;
+  }
+  atomicOr(a.err, kErrBounds);
+}
+
+// True if `slot` holds the lowest claim on `pair`; the winner marks the
+// entry accepted.
+__device__ bool resolve_packed(const TotalArgs& a, uint64_t pair, uint64_t slot) {
+  const int sh = a.slot_bits + 1;
+  const uint64_t e = (pair << sh) | (1ull << a.slot_bits) | slot;
+  uint64_t h = pair_hash(pair) & a.table_mask;
+  for (uint64_t probe = 0; probe <= a.table_mask; ++probe) {
+    const uint64_t v = a.table_keys[h];
+    if (v == kEmpty) return false;
+    if ((v >> sh) == pair) {
+      if (v != e) return false;
+      a.table_keys[h] = e & ~(1ull << a.slot_bits);
+      return true;
+    }
+    h = (h + 1) & a.table_mask;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void claim(const TotalArgs& a, const DevProj& P, uint64_t pair, uint64_t slot) {
+  if (a.packed) {
+    claim_packed(a, packed_pair(a, P, static_cast<uint32_t>(pair >> 32), static_cast<uint32_t>(pair)), slot);
+    return;
+  }
   const uint64_t h = table_slot(a, pair, true);
   if (h != kEmpty)
     atomicMin(reinterpret_cast<unsigned long long*>(&a.table_vals[h]), kClaim | slot);
@@ -408,7 +486,7 @@ __global__ void total_round0_kernel(TotalArgs a) {
     const uint32_t t = P.t0 + rand_below(tw, P.nt);
     const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
     a.pairs[i] = pair;
-    if (!P.multapses && allowed_pair(P, s, t)) claim(a, pair, i);
+    if (!P.multapses && allowed_pair(P, s, t)) claim(a, P, pair, i);
   }
 }
 
@@ -422,7 +500,7 @@ __global__ void total_claim_kernel(TotalArgs a, const uint64_t* pending, uint64_
     const uint32_t t = P.t0 + rand_below(D.y, P.nt);
     const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
     a.pairs[i] = pair;
-    if (!P.multapses && allowed_pair(P, s, t)) claim(a, pair, i);
+    if (!P.multapses && allowed_pair(P, s, t)) claim(a, P, pair, i);
   }
 }
 
@@ -439,9 +517,13 @@ __global__ void total_resolve_kernel(TotalArgs a, const uint64_t* pending, uint6
     const uint32_t s = static_cast<uint32_t>(pair >> 32), t = static_cast<uint32_t>(pair);
     bool ok = allowed_pair(P, s, t);
     if (ok && !P.multapses) {
-      const uint64_t h = table_slot(a, pair, false);
-      ok = h != kEmpty && a.table_vals[h] == (kClaim | i);
-      if (ok) a.table_vals[h] = i;
+      if (a.packed) {
+        ok = resolve_packed(a, packed_pair(a, P, s, t), i);
+      } else {
+        const uint64_t h = table_slot(a, pair, false);
+        ok = h != kEmpty && a.table_vals[h] == (kClaim | i);
+        if (ok) a.table_vals[h] = i;
+      }
     }
     if (!ok) {
       const unsigned long long at = atomicAdd(a.n_next, 1ull);
@@ -452,7 +534,9 @@ __global__ void total_resolve_kernel(TotalArgs a, const uint64_t* pending, uint6
 
 __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, const DevProj* proj, const uint64_t* pairs) {
   extern __shared__ uint32_t smem_raw[];
-  SmemTables tabs{smem_raw, reinterpret_cast<uint16_t*>(smem_raw + g.max_delay_len)};
+  const uint32_t hw = hist_words(g);
+  SmemTables tabs{smem_raw + hw, reinterpret_cast<uint16_t*>(smem_raw + hw + g.max_delay_len)};
+  const BlockHist bh = block_hist_begin(g, smem_raw);
   const DevProj& P = *proj;
   load_delay_table(P, g.thr_blob, g.guide_blob, tabs);
   __syncthreads();
@@ -460,9 +544,10 @@ __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, cons
   for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.count; i += stride) {
     const uint64_t pair = pairs[i];
     const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-    store(g, P.out_off + i, static_cast<uint32_t>(pair >> 32), delay_step(P, tabs, W.x),
+    store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32), delay_step(P, tabs, W.x),
           static_cast<uint32_t>(pair), weight_bits(P, W.z, W.w));
   }
+  block_hist_end(g, bh);
 }
 
 // ---------------------------------------------------------------------------

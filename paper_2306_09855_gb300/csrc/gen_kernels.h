@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include "digit_hist.cuh"
 #include "snc_internal.h"
 
 namespace snc {
@@ -27,6 +28,7 @@ struct GenArgs {
   uint32_t* vals;
   uint64_t cap;    // entries of keys / vals
   uint32_t* err;   // device error block (bounds checks)
+  HistPlan hist;   // digit counts of the sort's passes, accumulated as keys are written
 };
 
 struct SamplerArgs {
@@ -52,6 +54,11 @@ struct TotalArgs {
   uint64_t* table_keys;   // open-addressing hash table of pairs (~0 = empty)
   uint64_t* table_vals;   // accepted: slot; claimed this round: 2^63 | slot
   uint64_t table_mask;
+  // Packed table (one word per entry, used when it fits):
+  // (pair_local << (slot_bits + 1)) | (claimed_this_round << slot_bits) | slot
+  int packed;
+  int slot_bits;
+  int t_bits;           // bits of the target's local index in pair_local
   uint64_t* pending;      // slots still to redraw
   uint64_t* next_pending;
   unsigned long long* n_next;  // device counter of next_pending

@@ -17,92 +17,124 @@
 
 namespace snc {
 
-namespace {
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagInc = 2ull << 62;
-constexpr uint64_t kValMask = (1ull << 62) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
-}  // namespace
-
-__global__ void __launch_bounds__(kIndexThreads) index_kernel(IndexArgs a) {
-  constexpr int NW = kIndexThreads / 32;
-  __shared__ uint32_t tile_sh;
-  __shared__ uint32_t cnt[kIndexItems][NW];
-  __shared__ uint64_t group_base_sh;
+// Unpack of the sorted keys and group starts.  Block b covers keys
+// [b * kIndexTile, (b + 1) * kIndexTile); thread t of a block owns the
+// kIndexItems consecutive keys starting at t * kIndexItems.  Writes target
+// and delay (vector stores), one bit per key in `starts` (bit i of the
+// bitmap <-> key i) and the number of group starts of the block.
+__global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a) {
+  __shared__ uint32_t warp_cnt[kIndexThreads / 32];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  if (tid == 0) tile_sh = atomicAdd(a.tile_counter, 1u);
-  __syncthreads();
-  const uint32_t tile = tile_sh;
-  const uint64_t base = static_cast<uint64_t>(tile) * kIndexTile;
   const int sd_shift = a.node_bits;
   const uint64_t node_mask = (1ull << a.node_bits) - 1;
   const uint32_t delay_mask = (1u << a.delay_bits) - 1u;
-  uint32_t flags = 0;  // bit k: element k starts a group
+  const uint64_t n_blocks = (a.n + kIndexTile - 1) / kIndexTile;
+  for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+    const uint64_t base = blk * kIndexTile + static_cast<uint64_t>(tid) * kIndexItems;
+    uint64_t key[kIndexItems];
+    const bool full = base + kIndexItems <= a.n;
+    if (full) {
+      const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(a.keys + base);
 #pragma unroll
-  for (int k = 0; k < kIndexItems; ++k) {
-    const uint64_t q = base + static_cast<uint64_t>(k) * kIndexThreads + tid;
-    bool start = false;
-    if (q < a.n) {
-      const uint64_t key = a.keys[q];
-      a.target[q] = static_cast<uint32_t>(key & node_mask);
-      a.delay[q] = static_cast<uint16_t>((key >> sd_shift) & delay_mask);
-      start = q == 0 || (key >> sd_shift) != (a.keys[q - 1] >> sd_shift);
-    }
-    const uint32_t b = __ballot_sync(0xffffffffu, start);
-    if (lane == 0) cnt[k][warp] = __popc(b);
-    if (start) flags |= 1u << k;
-  }
-  __syncthreads();
-  // Exclusive offsets in tile order (k-major, then warp, then lane).
-  if (tid == 0) {
-    uint32_t run = 0;
-    for (int k = 0; k < kIndexItems; ++k)
-      for (int w = 0; w < NW; ++w) {
-        const uint32_t c = cnt[k][w];
-        cnt[k][w] = run;
-        run += c;
+      for (int k = 0; k < kIndexItems / 2; ++k) {
+        const ulonglong2 v = __ldg(k2 + k);
+        key[2 * k] = v.x;
+        key[2 * k + 1] = v.y;
       }
-    // Look-back over tiles for the number of groups before this tile.
-    uint64_t* st = a.status + tile;
-    const uint64_t total = run;
-    *reinterpret_cast<volatile unsigned long long*>(st) = (tile == 0 ? kFlagInc : kFlagAgg) | total;
-    uint64_t prefix = 0;
-    if (tile > 0) {
-      int64_t look = static_cast<int64_t>(tile) - 1;
-      uint32_t spins = 0;
-      while (look >= 0) {
-        const uint64_t v = *reinterpret_cast<const volatile unsigned long long*>(a.status + look);
-        const uint64_t f = v & (3ull << 62);
-        if (f == 0) {
-          if (++spins > kSpinLimit) {
-            atomicOr(a.err, kErrLookbackTimeout);
-            break;
-          }
-          continue;
+    } else {
+#pragma unroll
+      for (int k = 0; k < kIndexItems; ++k) key[k] = base + k < a.n ? __ldg(a.keys + base + k) : ~0ull;
+    }
+    // Predecessor of this thread's first key: the previous lane's last key,
+    // or one extra load for lane 0.
+    uint64_t prev = __shfl_up_sync(0xffffffffu, key[kIndexItems - 1], 1);
+    if (lane == 0) prev = (base > 0 && base < a.n) ? __ldg(a.keys + base - 1) : 0ull;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int k = 0; k < kIndexItems; ++k) {
+      const uint64_t q = base + k;
+      const uint64_t before = k == 0 ? prev : key[k - 1];
+      const bool start = q < a.n && (q == 0 || (key[k] >> sd_shift) != (before >> sd_shift));
+      bits |= (start ? 1u : 0u) << k;
+    }
+    if (full) {
+      uint32_t tv[kIndexItems];
+      uint16_t dv[kIndexItems];
+#pragma unroll
+      for (int k = 0; k < kIndexItems; ++k) {
+        tv[k] = static_cast<uint32_t>(key[k] & node_mask);
+        dv[k] = static_cast<uint16_t>((key[k] >> sd_shift) & delay_mask);
+      }
+      uint4* t4 = reinterpret_cast<uint4*>(a.target + base);
+#pragma unroll
+      for (int k = 0; k < kIndexItems / 4; ++k) t4[k] = make_uint4(tv[4 * k], tv[4 * k + 1], tv[4 * k + 2], tv[4 * k + 3]);
+      uint4* d4 = reinterpret_cast<uint4*>(a.delay + base);
+#pragma unroll
+      for (int k = 0; k < kIndexItems / 8; ++k)
+        d4[k] = make_uint4(dv[8 * k] | (static_cast<uint32_t>(dv[8 * k + 1]) << 16),
+                           dv[8 * k + 2] | (static_cast<uint32_t>(dv[8 * k + 3]) << 16),
+                           dv[8 * k + 4] | (static_cast<uint32_t>(dv[8 * k + 5]) << 16),
+                           dv[8 * k + 6] | (static_cast<uint32_t>(dv[8 * k + 7]) << 16));
+    } else {
+#pragma unroll
+      for (int k = 0; k < kIndexItems; ++k)
+        if (base + k < a.n) {
+          a.target[base + k] = static_cast<uint32_t>(key[k] & node_mask);
+          a.delay[base + k] = static_cast<uint16_t>((key[k] >> sd_shift) & delay_mask);
         }
-        prefix += v & kValMask;
-        if (f == kFlagInc) break;
-        --look;
-      }
-      *reinterpret_cast<volatile unsigned long long*>(st) = kFlagInc | (prefix + total);
     }
-    group_base_sh = prefix;
-    if (base + kIndexTile >= a.n) *a.n_groups = prefix + total;  // last tile
-  }
-  __syncthreads();
-  const uint64_t g0 = group_base_sh;
-  const uint32_t lt = (1u << lane) - 1u;
+    // Bitmap: kIndexItems (= 8) bits per thread, four threads per word.
+    static_assert(kIndexItems == 8, "bitmap assembly assumes one byte per thread");
+    const uint32_t b1 = __shfl_down_sync(0xffffffffu, bits, 1);
+    const uint32_t b2 = __shfl_down_sync(0xffffffffu, bits, 2);
+    const uint32_t b3 = __shfl_down_sync(0xffffffffu, bits, 3);
+    if ((lane & 3u) == 0) a.starts[blk * (kIndexTile / 32) + tid / 4] = bits | (b1 << 8) | (b2 << 16) | (b3 << 24);
+    uint32_t c = __popc(bits);
 #pragma unroll
-  for (int k = 0; k < kIndexItems; ++k) {
-    const bool start = (flags >> k) & 1u;
-    const uint32_t b = __ballot_sync(0xffffffffu, start);
-    if (start) {
-      const uint64_t g = g0 + cnt[k][warp] + __popc(b & lt);
-      const uint64_t q = base + static_cast<uint64_t>(k) * kIndexThreads + tid;
-      if (g < a.group_cap) a.group_first[g] = q;
-      else atomicOr(a.err, kErrBounds);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) warp_cnt[warp] = c;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t total = 0;
+      for (int w = 0; w < kIndexThreads / 32; ++w) total += warp_cnt[w];
+      a.block_counts[blk] = total;
     }
+    __syncthreads();
   }
+}
+
+// group_first[g] = position of the g-th group start, from the bitmap and the
+// exclusive scan of the per-block counts.
+__global__ void __launch_bounds__(kIndexThreads) index_groups_kernel(IndexArgs a) {
+  __shared__ uint32_t warp_tmp[kIndexThreads / 32];
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint64_t n_blocks = (a.n + kIndexTile - 1) / kIndexTile;
+  for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+    const uint32_t word = a.starts[blk * (kIndexTile / 32) + tid / 4];
+    uint32_t bits = (word >> (8u * (tid & 3u))) & 0xFFu;
+    const uint32_t c = __popc(bits);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (static_cast<int>(lane) >= o) incl += y;
+    }
+    if (lane == 31) warp_tmp[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0;
+    for (uint32_t w = 0; w < warp; ++w) before += warp_tmp[w];
+    uint64_t g = a.block_offsets[blk] + before + incl - c;
+    const uint64_t q0 = blk * kIndexTile + static_cast<uint64_t>(tid) * kIndexItems;
+    while (bits) {
+      const uint32_t b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      if (g < a.group_cap) a.group_first[g] = q0 + b;
+      else atomicOr(a.err, kErrBounds);
+      ++g;
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && tid == 0) *a.n_groups = a.block_offsets[n_blocks];
 }
 
 // row_ptr[i] = first position whose source is >= i; group_ptr[i] = number of

@@ -8,7 +8,7 @@
 namespace snc {
 
 constexpr int kIndexThreads = 256;
-constexpr int kIndexItems = 16;
+constexpr int kIndexItems = 8;
 constexpr int kIndexTile = kIndexThreads * kIndexItems;
 
 struct IndexArgs {
@@ -17,11 +17,12 @@ struct IndexArgs {
   int node_bits, delay_bits;
   uint32_t* target;
   uint16_t* delay;
+  uint32_t* starts;          // group-start bitmap, kIndexTile / 32 words per block
+  uint32_t* block_counts;    // group starts per block
+  const uint64_t* block_offsets;  // exclusive scan of block_counts (n_blocks + 1)
   uint64_t* group_first;
   uint64_t group_cap;
-  uint64_t* n_groups;     // written by the last tile
-  uint64_t* status;       // one look-back word per tile, zero before the launch
-  uint32_t* tile_counter; // zero before the launch
+  uint64_t* n_groups;
   uint32_t* err;
 };
 
@@ -37,7 +38,8 @@ struct NodeIndexArgs {
   uint64_t* group_ptr;
 };
 
-__global__ void index_kernel(IndexArgs a);
+__global__ void index_unpack_kernel(IndexArgs a);
+__global__ void index_groups_kernel(IndexArgs a);
 __global__ void node_index_kernel(NodeIndexArgs a);
 __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes, uint32_t* src);
 

@@ -23,6 +23,7 @@ using namespace snc;
 namespace {
 
 constexpr int kMaxEvents = 4 + kMaxPasses + 2;
+int g_gen_blocks_per_sm = 8;
 thread_local std::string g_last_error = "no error";
 
 struct DevBuf {
@@ -93,6 +94,11 @@ void* dev_alloc(snc_ctx* c, size_t bytes) {
   } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
+  }
+  if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {
+    // The kernels use vector and bulk copies that need aligned arrays.
+    if (c->custom_alloc) c->alloc.free(p, bytes, c->stream, c->alloc.user);
+    return nullptr;
   }
   if (p) {
     c->bufs.push_back({p, bytes});
@@ -501,6 +507,13 @@ snc_status snc_finalize(snc_ctx* c) {
   if (!keys_a || !vals_a || !keys_b || !vals_b || !sort_scratch)
     return fail(c, SNC_ERR_OOM, "device allocation failed (%llu connections)", static_cast<unsigned long long>(n));
 
+  // The generation kernels count the sort's digits as they write the keys.
+  const SortScratch sort_lay = sort_scratch_layout(sort_scratch, n, c->passes);
+  SNC_CUDA(c, cudaMemsetAsync(sort_lay.hist, 0, static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long),
+                              st));
+  const HistPlan hplan = hist_plan(c->passes, sort_lay.hist);
+  const size_t hist_bytes = hist_smem_bytes(hplan);
+
   // Generation.
   GenArgs g{};
   g.projs = d_direct;
@@ -514,14 +527,16 @@ snc_status snc_finalize(snc_ctx* c) {
   g.vals = vals_a;
   g.cap = n;
   g.err = c->d_err;
-  const size_t table_smem = static_cast<size_t>(max_delay_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
+  g.hist = hplan;
+  const size_t table_smem =
+      hist_bytes + static_cast<size_t>(max_delay_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
   if (chunk > 0) {
     static bool configured = false;
     if (!configured) {
-      SNC_CUDA(c, cudaFuncSetAttribute(gen_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+      SNC_CUDA(c, cudaFuncSetAttribute(gen_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
       configured = true;
     }
-    const uint64_t grid = std::min<uint64_t>(chunk, static_cast<uint64_t>(c->sms) * 8);
+    const uint64_t grid = std::min<uint64_t>(chunk, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm);
     gen_direct_kernel<<<static_cast<unsigned>(grid), kGenThreads, table_smem, st>>>(g);
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
@@ -542,7 +557,8 @@ snc_status snc_finalize(snc_ctx* c) {
       s.prim_offsets = d_prim_off ? d_prim_off + dp[i].prim_off : nullptr;
       s.err = c->d_err;
       const size_t bitmap_bytes = static_cast<size_t>(s.bitmap_words) * sizeof(uint32_t);
-      const size_t tab = static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
+      const size_t tab =
+          hist_bytes + static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
       int warps = static_cast<int>(std::min<size_t>(8, (kSamplerSmem - tab) / std::max<size_t>(bitmap_bytes, 4)));
       if (warps < 1) return fail(c, SNC_ERR_UNSUPPORTED, "sampler bitmap does not fit shared memory");
       const size_t smem = static_cast<size_t>(warps) * bitmap_bytes + tab;
@@ -570,11 +586,21 @@ snc_status snc_finalize(snc_ctx* c) {
         uint64_t cap = 1;
         if (!p.rule.allow_multapses) {
           while (cap < 2 * N + 64) cap <<= 1;
+          // One word per entry when (source, target, slot) fit in 63 bits.
+          const int s_bits = bit_width(p.src.n > 0 ? p.src.n - 1u : 0u);
+          const int t_bits = bit_width(p.tgt.n > 0 ? p.tgt.n - 1u : 0u);
+          const int slot_bits = std::max(1, bit_width(N - 1));
+          t.packed = (s_bits + t_bits + slot_bits + 1 <= 63) ? 1 : 0;
+          t.slot_bits = slot_bits;
+          t.t_bits = t_bits;
           t.table_keys = static_cast<uint64_t*>(dev_alloc(c, cap * sizeof(uint64_t)));
-          t.table_vals = static_cast<uint64_t*>(dev_alloc(c, cap * sizeof(uint64_t)));
-          if (!t.table_keys || !t.table_vals) return fail(c, SNC_ERR_OOM, "device allocation failed (pair table)");
+          if (!t.table_keys) return fail(c, SNC_ERR_OOM, "device allocation failed (pair table)");
           SNC_CUDA(c, cudaMemsetAsync(t.table_keys, 0xFF, cap * sizeof(uint64_t), st));
-          SNC_CUDA(c, cudaMemsetAsync(t.table_vals, 0xFF, cap * sizeof(uint64_t), st));
+          if (!t.packed) {
+            t.table_vals = static_cast<uint64_t*>(dev_alloc(c, cap * sizeof(uint64_t)));
+            if (!t.table_vals) return fail(c, SNC_ERR_OOM, "device allocation failed (pair table)");
+            SNC_CUDA(c, cudaMemsetAsync(t.table_vals, 0xFF, cap * sizeof(uint64_t), st));
+          }
         }
         t.table_mask = cap - 1;
         if (!t.pairs || !t.pending || !t.next_pending || !t.n_next)
@@ -606,10 +632,11 @@ snc_status snc_finalize(snc_ctx* c) {
         }
         GenArgs ge = g;
         ge.max_delay_len = dp[i].d_len;
-        const size_t tsm = static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
+        const size_t tsm =
+            hist_bytes + static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
         static bool econf = false;
         if (!econf) {
-          SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+          SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
           econf = true;
         }
         total_emit_kernel<<<grid, kGenThreads, tsm, st>>>(ge, d_proj + i, t.pairs);
@@ -637,9 +664,9 @@ snc_status snc_finalize(snc_ctx* c) {
   uint64_t* keys_oth = odd ? keys_a : keys_b;
   uint32_t* vals_oth = odd ? vals_a : vals_b;
   SNC_CUDA(c, radix_sort_run(keys_a, vals_a, keys_res, vals_res, keys_oth, vals_oth, n, c->passes, sort_scratch,
-                             c->d_err, st, c->ev + c->n_ev));
+                             c->d_err, st, c->ev + c->n_ev, /*hist_ready=*/true));
   c->n_ev += c->passes.n_passes + 1;
-  if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 2;
+  if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
   c->stats.n_passes = c->passes.n_passes;
   c->stats.key_bits = c->layout.total_bits();
   dev_free(c, sort_scratch);
@@ -654,12 +681,14 @@ snc_status snc_finalize(snc_ctx* c) {
   c->group_first = static_cast<uint64_t*>(dev_alloc(c, c->group_cap * sizeof(uint64_t)));
   c->row_ptr = static_cast<uint64_t*>(dev_alloc(c, (c->n_nodes + 1) * sizeof(uint64_t)));
   c->group_ptr = static_cast<uint64_t*>(dev_alloc(c, (c->n_nodes + 1) * sizeof(uint64_t)));
-  const uint64_t itiles = (n + kIndexTile - 1) / kIndexTile;
-  uint64_t* istatus = static_cast<uint64_t*>(dev_alloc(c, (itiles + 1) * sizeof(uint64_t) + 64));
-  if (!c->target || !c->delay || !c->group_first || !c->row_ptr || !c->group_ptr || !istatus)
+  const uint64_t iblocks = (n + kIndexTile - 1) / kIndexTile;
+  uint32_t* starts = static_cast<uint32_t*>(dev_alloc(c, (iblocks * (kIndexTile / 32) + 1) * sizeof(uint32_t)));
+  uint32_t* bcounts = static_cast<uint32_t*>(dev_alloc(c, (iblocks + 1) * sizeof(uint32_t)));
+  uint64_t* boffsets = static_cast<uint64_t*>(dev_alloc(c, (iblocks + 1) * sizeof(uint64_t)));
+  uint64_t* iscan = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(iblocks) + 1) * sizeof(uint64_t)));
+  if (!c->target || !c->delay || !c->group_first || !c->row_ptr || !c->group_ptr || !starts || !bcounts || !boffsets ||
+      !iscan)
     return fail(c, SNC_ERR_OOM, "device allocation failed (index)");
-  uint32_t* icounter = reinterpret_cast<uint32_t*>(istatus + itiles + 1);
-  SNC_CUDA(c, cudaMemsetAsync(istatus, 0, (itiles + 1) * sizeof(uint64_t) + 64, st));
   if (n > 0) {
     IndexArgs ia{};
     ia.keys = keys_res;
@@ -668,13 +697,20 @@ snc_status snc_finalize(snc_ctx* c) {
     ia.delay_bits = c->layout.delay_bits;
     ia.target = c->target;
     ia.delay = c->delay;
+    ia.starts = starts;
+    ia.block_counts = bcounts;
+    ia.block_offsets = boffsets;
     ia.group_first = c->group_first;
     ia.group_cap = c->group_cap;
     ia.n_groups = c->d_n_groups;
-    ia.status = istatus;
-    ia.tile_counter = icounter;
     ia.err = c->d_err;
-    index_kernel<<<static_cast<unsigned>(itiles), kIndexThreads, 0, st>>>(ia);
+    const unsigned igrid = static_cast<unsigned>(std::min<uint64_t>(iblocks, static_cast<uint64_t>(c->sms) * 8));
+    index_unpack_kernel<<<igrid, kIndexThreads, 0, st>>>(ia);
+    ++c->stats.kernel_launches;
+    SNC_CUDA(c, cudaGetLastError());
+    SNC_CUDA(c, exclusive_scan_u32(bcounts, iblocks, boffsets, iscan, st));
+    c->stats.kernel_launches += 3;
+    index_groups_kernel<<<igrid, kIndexThreads, 0, st>>>(ia);
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
   }
@@ -694,7 +730,10 @@ snc_status snc_finalize(snc_ctx* c) {
   SNC_CUDA(c, cudaGetLastError());
   cudaEventRecord(c->ev[c->n_ev++], st);
   c->weight = reinterpret_cast<float*>(vals_res);
-  dev_free(c, istatus);
+  dev_free(c, starts);
+  dev_free(c, bcounts);
+  dev_free(c, boffsets);
+  dev_free(c, iscan);
   dev_free(c, keys_res);
   dev_free(c, d_direct);
   dev_free(c, d_prim_off);
@@ -820,6 +859,29 @@ snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in
   if (e == cudaSuccess) e = radix_sort_run(keys_in, vals_in, keys_out, vals_out, ktmp, vtmp, n, sp, scratch, err, st, nullptr);
   release();
   if (e != cudaSuccess) return fail(nullptr, SNC_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e));
+  return SNC_OK;
+}
+
+snc_status snc_set_tuning(const snc_tuning* t) {
+  if (!t) return fail(nullptr, SNC_ERR_INVALID_ARG, "null tuning");
+  if (t->sort_digit_bits < 8 || t->sort_digit_bits > 11)
+    return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_digit_bits outside [8, 11]");
+  if (t->sort_group_tiles != 0 && t->sort_group_tiles != 1 && t->sort_group_tiles != 4 && t->sort_group_tiles != 8)
+    return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_group_tiles must be 0, 1, 4 or 8");
+  if (t->gen_blocks_per_sm < 1 || t->gen_blocks_per_sm > 32)
+    return fail(nullptr, SNC_ERR_INVALID_ARG, "gen_blocks_per_sm outside [1, 32]");
+  g_sort_tuning.max_digit_bits = t->sort_digit_bits;
+  g_sort_tuning.group_tiles = t->sort_group_tiles;
+  g_gen_blocks_per_sm = t->gen_blocks_per_sm;
+  return SNC_OK;
+}
+
+snc_status snc_get_tuning(snc_tuning* t) {
+  if (!t) return fail(nullptr, SNC_ERR_INVALID_ARG, "null tuning");
+  t->sort_digit_bits = g_sort_tuning.max_digit_bits;
+  t->sort_group_tiles = g_sort_tuning.group_tiles;
+  t->gen_blocks_per_sm = g_gen_blocks_per_sm;
+  t->reserved = 0;
   return SNC_OK;
 }
 

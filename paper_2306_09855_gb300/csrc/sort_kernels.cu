@@ -17,6 +17,7 @@
 
 #include <cstdint>
 
+#include "digit_hist.cuh"
 #include "snc_check.cuh"
 #include "snc_internal.h"
 #include "sort_kernels.h"
@@ -75,36 +76,42 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_t
 
 // ---------------------------------------------------------------------------
 // Histogram of every pass's digit over all keys (shared-memory counters per
-// block, merged into global 64-bit counters).  A warp whose 32 keys share a
-// digit adds 32 once instead of 32 conflicting atomics.
+// block, merged into global 64-bit counters).
 // ---------------------------------------------------------------------------
-__global__ void radix_hist_kernel(const uint64_t* __restrict__ keys, uint64_t n, SortPasses sp,
-                                  unsigned long long* __restrict__ hist) {
+__global__ void __launch_bounds__(512) radix_hist_kernel(const uint64_t* __restrict__ keys, uint64_t n, HistPlan plan) {
   extern __shared__ uint32_t sh[];
-  const int bins = sp.n_passes * kMaxRadix;
-  for (int i = threadIdx.x; i < bins; i += blockDim.x) sh[i] = 0;
+  const HistRegs r = hist_regs(plan);
+  hist_clear(sh, r);
   __syncthreads();
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t warps_total = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
-  const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (uint64_t base = gw * 32; base < n; base += warps_total * 32) {
-    const uint64_t i = base + lane;
-    const bool valid = i < n;
-    const uint64_t key = valid ? keys[i] : 0ull;
-    for (int p = 0; p < sp.n_passes; ++p) {
-      const uint32_t d = static_cast<uint32_t>(key >> sp.shift[p]) & sp.mask[p];
-      const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
-      const bool all_valid = base + 32 <= n;
-      if (__all_sync(0xffffffffu, d == d0) && all_valid) {
-        if (lane == 0) atomicAdd(&sh[p * kMaxRadix + d], 32u);
-      } else if (valid) {
-        atomicAdd(&sh[p * kMaxRadix + d], 1u);
-      }
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  const uint64_t pairs = n / 2;
+  const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys);
+  const bool aligned = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+  if (aligned) {
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < pairs; i += stride) {
+      const ulonglong2 v = k2[i];
+      hist_add(sh, r, v.x);
+      hist_add(sh, r, v.y);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) hist_add(sh, r, keys[n - 1]);
+  } else {
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+      hist_add(sh, r, keys[i]);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < bins; i += blockDim.x)
-    if (sh[i]) atomicAdd(&hist[i], static_cast<unsigned long long>(sh[i]));
+  hist_flush(sh, r, plan.global);
+}
+
+HistPlan hist_plan(const SortPasses& sp, unsigned long long* global) {
+  HistPlan h{};
+  h.global = global;
+  h.n_passes = sp.n_passes;
+  h.stride = 1 << sp.kernel_bits;
+  for (int p = 0; p < kMaxPasses; ++p) {
+    h.shift[p] = p < sp.n_passes ? sp.shift[p] : 0;
+    h.mask[p] = p < sp.n_passes ? sp.mask[p] : 0u;
+  }
+  return h;
 }
 
 // Exclusive scan of each pass's digit counts (one block of kDigitScanThreads
@@ -143,221 +150,570 @@ __global__ void radix_digit_scan_kernel(const unsigned long long* __restrict__ h
 }
 
 // ---------------------------------------------------------------------------
-// One onesweep pass.  Tile = TPB threads x IPT keys; warp w owns keys
-// [w*32*IPT, (w+1)*32*IPT) of the tile, lane-interleaved, so that ranking
-// warp by warp and item by item preserves input order (stability).
+// One onesweep pass.  Tile = 256 threads x 16 keys; warp w ranks keys
+// [w*512, (w+1)*512) of the tile lane-interleaved, so that ranking warp by
+// warp and item by item preserves input order (stability).
+//
+// G = 1: a block ranks its tile, publishes the tile's digit counts, looks
+// back over earlier tiles for its global offsets and scatters the tile.
+// G > 1: a block takes a group of G consecutive tiles, first counts the
+// group's digits (so that the look-back runs once per group), then ranks and
+// scatters the group's tiles one after another with per-digit running
+// offsets; the second read of the group's keys is meant to hit L2.
+// Groups / tiles are taken from a dynamic ticket, so every predecessor has
+// already started when a block waits for it.
 // ---------------------------------------------------------------------------
-template <int BITS, int TPB, int IPT>
-__global__ void __launch_bounds__(TPB) onesweep_kernel(OnesweepArgs a) {
-  constexpr int RADIX = 1 << BITS;
-  constexpr int NW = TPB / 32;
-  constexpr int TILE = TPB * IPT;
-  constexpr int DPT = RADIX / TPB;  // digits per thread
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+template <int BITS, int G>
+struct Onesweep {
+  static constexpr int TPB = kSortThreads, IPT = kSortItems, TILE = kSortTile;
+  static constexpr int RADIX = 1 << BITS;
+  static constexpr int NW = TPB / 32;
+  static constexpr int GROUP = TILE * G;
+  static constexpr int DPT = RADIX / TPB;  // digits per thread
+  static constexpr int W = DPT >= 8 ? 2 : (DPT >= 4 ? 4 : 8);  // look-back window per round
+  static constexpr int MINB = BITS <= 9 ? 3 : 2;                // resident blocks per SM
+  static constexpr size_t kCntBytes = static_cast<size_t>(NW) * RADIX * sizeof(uint16_t);
+  static constexpr size_t kTileBytes = static_cast<size_t>(TILE) * (sizeof(uint64_t) + sizeof(uint32_t));
+  static constexpr size_t kUnion = kCntBytes > kTileBytes ? kCntBytes : kTileBytes;
+  static constexpr size_t kSmem = kUnion + RADIX * sizeof(uint32_t) * 2 + RADIX * sizeof(uint64_t);
+};
+
+// Sum, for each of this thread's DPT digits, the counts that groups before
+// `unit` published (decoupled look-back, W predecessors per round trip).
+template <int RADIX, int DPT, int W>
+__device__ __forceinline__ void look_back(const OnesweepArgs& a, uint32_t unit, uint64_t (&prefix)[DPT]) {
+  const uint32_t tid = threadIdx.x;
+  int32_t look[DPT];
+  uint32_t pending = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    prefix[q] = 0;
+    look[q] = static_cast<int32_t>(unit) - 1;
+    if (unit > 0) pending |= 1u << q;
+  }
+  uint32_t spins = 0;
+  uint32_t backoff = 32u;
+  while (pending) {
+    bool progress = false;
+    uint64_t v[DPT][W];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q)
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const int32_t t = look[q] - w;
+        v[q][w] = ((pending >> q) & 1u) && t >= 0
+                      ? ld_status(a.status + static_cast<size_t>(t) * RADIX + tid * DPT + q)
+                      : 0ull;
+      }
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      if (!((pending >> q) & 1u)) continue;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const uint64_t x = v[q][w];
+        const bool fresh = ((x >> 48) & 0x3FFFull) == a.epoch;
+        const uint64_t flag = fresh ? (x & (3ull << 62)) : 0ull;
+        if (flag == 0 || look[q] < 0) break;  // not yet published: read again next round
+        progress = true;
+        prefix[q] += x & kCountMask;
+        if (flag == kFlagInc) {
+          pending &= ~(1u << q);
+          break;
+        }
+        --look[q];
+      }
+    }
+    if (pending && !progress) {
+      if (++spins > kSpinLimit) {
+        atomicOr(a.err, kErrLookbackTimeout);
+        break;
+      }
+      __nanosleep(backoff);  // let the other warps of the SM issue
+      backoff = backoff < 1024u ? backoff * 2u : 1024u;
+    } else {
+      backoff = 32u;
+    }
+  }
+}
+
+template <int BITS, int G>
+__global__ void __launch_bounds__(kSortThreads, Onesweep<BITS, G>::MINB) onesweep_kernel(OnesweepArgs a) {
+  using C = Onesweep<BITS, G>;
+  constexpr int RADIX = C::RADIX, NW = C::NW, TILE = C::TILE, GROUP = C::GROUP, DPT = C::DPT, W = C::W;
+  constexpr int TPB = C::TPB, IPT = C::IPT;
   static_assert(RADIX % TPB == 0, "radix must be a multiple of the block size");
-  constexpr size_t kCntBytes = static_cast<size_t>(NW) * RADIX * sizeof(uint16_t);
-  constexpr size_t kTileBytes = static_cast<size_t>(TILE) * (sizeof(uint64_t) + sizeof(uint32_t));
-  constexpr size_t kUnion = kCntBytes > kTileBytes ? kCntBytes : kTileBytes;
 
   extern __shared__ __align__(16) unsigned char smem[];
   uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem);
   uint64_t* skeys = reinterpret_cast<uint64_t*>(smem);
   uint32_t* svals = reinterpret_cast<uint32_t*>(smem + static_cast<size_t>(TILE) * sizeof(uint64_t));
-  uint32_t* local_start = reinterpret_cast<uint32_t*>(smem + kUnion);
-  uint64_t* glob = reinterpret_cast<uint64_t*>(smem + kUnion + RADIX * sizeof(uint32_t));
-  __shared__ uint32_t tile_sh;
+  uint32_t* ghist = reinterpret_cast<uint32_t*>(smem + C::kUnion);
+  uint32_t* local_start = ghist + RADIX;
+  uint64_t* run = reinterpret_cast<uint64_t*>(smem + C::kUnion + 2 * RADIX * sizeof(uint32_t));
+  __shared__ uint32_t unit_sh;
   __shared__ uint32_t warp_tmp[32];
   __shared__ uint32_t scan_total;
 
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  if (tid == 0) tile_sh = atomicAdd(a.tile_counter, 1u);
-  for (int i = tid; i < NW * RADIX / 2; i += TPB) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
-  __syncthreads();
-  const uint32_t tile = tile_sh;
-  const uint64_t tile_base = static_cast<uint64_t>(tile) * TILE;
-  const uint64_t warp_base = tile_base + static_cast<uint64_t>(warp) * 32 * IPT;
   const uint32_t mask = a.mask;
   const int shift = a.shift;
-
-  uint64_t key[IPT];
-  uint32_t rank[IPT];
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
-    key[j] = idx < a.n ? a.keys_in[idx] : 0ull;
-  }
-
-  // Rank within the warp: peers with an equal digit share one counter update.
-  uint16_t* my = wcnt + static_cast<size_t>(warp) * RADIX;
   const uint32_t lt = lanemask_lt();
+  const uint64_t ep = static_cast<uint64_t>(a.epoch) << 48;
+
+  for (;;) {
+    if (tid == 0) unit_sh = atomicAdd(a.tile_counter, 1u);
+    if (G > 1)
+      for (int i = tid; i < RADIX; i += TPB) ghist[i] = 0u;
+    __syncthreads();
+    const uint32_t unit = unit_sh;
+    if (static_cast<uint64_t>(unit) * GROUP >= a.n) break;
+    const uint64_t gbase = static_cast<uint64_t>(unit) * GROUP;
+    uint64_t* st_row = a.status + static_cast<size_t>(unit) * RADIX + static_cast<size_t>(tid) * DPT;
+
+    if (G > 1) {
+      // Digit counts of the whole group (coalesced, order irrelevant).
+      for (int s = 0; s < G; ++s) {
+        const uint64_t tbase = gbase + static_cast<uint64_t>(s) * TILE;
+        if (tbase >= a.n) break;
+        uint32_t d[IPT];
 #pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
-    const bool valid = idx < a.n;
-    const uint32_t d = valid ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const int leader = __ffs(peers) - 1;
-    uint32_t old = 0;
-    if (static_cast<int>(lane) == leader && valid) {
-      old = my[d];
-      my[d] = static_cast<uint16_t>(old + __popc(peers));
+        for (int j = 0; j < IPT; ++j) {
+          const uint64_t idx = tbase + static_cast<uint64_t>(j) * TPB + tid;
+          d[j] = idx < a.n ? (static_cast<uint32_t>(a.keys_in[idx] >> shift) & mask) : static_cast<uint32_t>(RADIX);
+        }
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+          const uint32_t d0 = __shfl_sync(0xffffffffu, d[j], 0);
+          if (__all_sync(0xffffffffu, d[j] == d0)) {
+            if (lane == 0 && d0 < RADIX) atomicAdd(&ghist[d0], 32u);
+          } else if (d[j] < RADIX) {
+            atomicAdd(&ghist[d[j]], 1u);
+          }
+        }
+      }
+      __syncthreads();
+      uint32_t cnt[DPT];
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) {
+        cnt[q] = ghist[tid * DPT + q];
+        st_status(st_row + q, (unit == 0 ? kFlagInc : kFlagAgg) | ep | cnt[q]);
+      }
+      uint64_t prefix[DPT];
+      look_back<RADIX, DPT, W>(a, unit, prefix);
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) {
+        if (unit > 0) st_status(st_row + q, kFlagInc | ep | ((prefix[q] + cnt[q]) & kCountMask));
+        run[tid * DPT + q] = a.digit_start[tid * DPT + q] + prefix[q];
+      }
     }
-    old = __shfl_sync(0xffffffffu, old, leader);
-    rank[j] = old + __popc(peers & lt);
-    __syncwarp();
+
+    for (int s = 0; s < G; ++s) {
+      const uint64_t tbase = gbase + static_cast<uint64_t>(s) * TILE;
+      if (tbase >= a.n) break;
+      __syncthreads();  // previous tile's staging and run[] update are complete
+      for (int i = tid; i < NW * RADIX / 2; i += TPB) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
+      __syncthreads();
+      const uint64_t warp_base = tbase + static_cast<uint64_t>(warp) * 32 * IPT;
+      uint64_t key[IPT];
+      uint32_t rank[IPT];
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
+        key[j] = idx < a.n ? a.keys_in[idx] : 0ull;
+      }
+      uint16_t* my = wcnt + static_cast<size_t>(warp) * RADIX;
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
+        const bool valid = idx < a.n;
+        const uint32_t d = valid ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (static_cast<int>(lane) == leader && valid) {
+          old = my[d];
+          my[d] = static_cast<uint16_t>(old + __popc(peers));
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[j] = old + __popc(peers & lt);
+        __syncwarp();
+      }
+      __syncthreads();
+      // Per digit: exclusive offsets across warps and the tile total.
+      uint32_t tot[DPT];
+      uint32_t tsum = 0;
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          const uint32_t c = wcnt[w * RADIX + d];
+          wcnt[w * RADIX + d] = static_cast<uint16_t>(r);
+          r += c;
+        }
+        tot[q] = r;
+        tsum += r;
+      }
+      if (G == 1) {
+        // Publish the tile's counts before the local scan, then look back.
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) st_status(st_row + q, (unit == 0 ? kFlagInc : kFlagAgg) | ep | tot[q]);
+      }
+      uint32_t excl = block_excl_scan<TPB>(tsum, warp_tmp, &scan_total);
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) {
+        local_start[tid * DPT + q] = excl;
+        excl += tot[q];
+      }
+      if (G == 1) {
+        uint64_t prefix[DPT];
+        look_back<RADIX, DPT, W>(a, unit, prefix);
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+          if (unit > 0) st_status(st_row + q, kFlagInc | ep | ((prefix[q] + tot[q]) & kCountMask));
+          run[tid * DPT + q] = a.digit_start[tid * DPT + q] + prefix[q];
+        }
+      }
+      __syncthreads();
+      uint32_t lpos[IPT];
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
+        const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & mask;
+        lpos[j] = idx < a.n ? local_start[d] + wcnt[warp * RADIX + d] + rank[j] : 0xFFFFFFFFu;
+      }
+      __syncthreads();  // counters are dead; the union becomes the staging area
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        if (lpos[j] != 0xFFFFFFFFu && SNC_IN_BOUNDS(a.err, 10u, lpos[j], TILE)) {
+          const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
+          skeys[lpos[j]] = key[j];
+          svals[lpos[j]] = a.vals_in[idx];
+        }
+      }
+      __syncthreads();
+      const uint64_t left = a.n - tbase;
+      const uint32_t valid = left < static_cast<uint64_t>(TILE) ? static_cast<uint32_t>(left) : static_cast<uint32_t>(TILE);
+      for (uint32_t i = tid; i < valid; i += TPB) {
+        const uint64_t k = skeys[i];
+        const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
+        const uint64_t pos = run[d] + (i - local_start[d]);
+        if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
+        a.keys_out[pos] = k;
+        a.vals_out[pos] = svals[i];
+      }
+      __syncthreads();  // all reads of run[] for this tile are done
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) run[tid * DPT + q] += tot[q];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-fed onesweep pass for 8- and 9-bit digits (one look-back per 4096-key
+// tile).  A persistent block takes tiles from the ticket; one thread issues
+// two bulk copies (cp.async.bulk, completion on an mbarrier) that bring the
+// tile's keys and values into shared memory, so the ranking reads keys from
+// shared memory and all tile-local indices are 32-bit.  After the keys are in
+// registers the key buffer is reused to stage the tile in digit order.  The
+// last, partial tile is loaded with ordinary loads.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbarrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+template <int BITS>
+struct OnesweepTma {
+  static constexpr int TPB = kSortThreads, IPT = kSortItems, TILE = kSortTile;
+  static constexpr int RADIX = 1 << BITS;
+  static constexpr int NW = TPB / 32;
+  static constexpr int DPT = RADIX / TPB;
+  static constexpr int W = DPT >= 2 ? 4 : 8;
+  static constexpr int MINB = BITS <= 8 ? 3 : 2;  // resident blocks per SM (shared memory bound)
+  static constexpr size_t kKeysBytes = static_cast<size_t>(TILE) * sizeof(uint64_t);  // input / staged keys
+  static constexpr size_t kValsBytes = static_cast<size_t>(TILE) * sizeof(uint32_t);
+  static constexpr size_t kCntBytes = static_cast<size_t>(NW) * RADIX * sizeof(uint16_t);
+  static constexpr size_t kOffVals = kKeysBytes;
+  static constexpr size_t kOffStageVals = kOffVals + kValsBytes;
+  static constexpr size_t kOffCnt = kOffStageVals + kValsBytes;
+  static constexpr size_t kOffLocal = kOffCnt + kCntBytes;
+  static constexpr size_t kOffGlob = kOffLocal + RADIX * sizeof(uint32_t);
+  static constexpr size_t kOffBar = kOffGlob + RADIX * sizeof(uint64_t);
+  static constexpr size_t kSmem = kOffBar + 16;
+};
+
+template <int BITS>
+__global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) onesweep_tma_kernel(OnesweepArgs a) {
+  using C = OnesweepTma<BITS>;
+  constexpr int RADIX = C::RADIX, NW = C::NW, TILE = C::TILE, DPT = C::DPT, W = C::W;
+  constexpr int TPB = C::TPB, IPT = C::IPT;
+  static_assert(RADIX % TPB == 0, "radix must be a multiple of the block size");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* skeys = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* vin = reinterpret_cast<uint32_t*>(smem + C::kOffVals);
+  uint32_t* svals = reinterpret_cast<uint32_t*>(smem + C::kOffStageVals);
+  uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem + C::kOffCnt);
+  uint32_t* local_start = reinterpret_cast<uint32_t*>(smem + C::kOffLocal);
+  uint64_t* globm = reinterpret_cast<uint64_t*>(smem + C::kOffGlob);  // global position of local index 0
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::kOffBar);
+  __shared__ uint32_t unit_sh;
+  __shared__ uint32_t warp_tmp[32];
+  __shared__ uint32_t scan_total;
+
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t mask = a.mask;
+  const int shift = a.shift;
+  const uint32_t lt = lanemask_lt();
+  const uint64_t ep = static_cast<uint64_t>(a.epoch) << 48;
+  const uint64_t n_tiles = (a.n + TILE - 1) / TILE;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbarrier_init();
   }
   __syncthreads();
+  uint32_t parity = 0;
 
-  // Per digit: exclusive offsets across warps and the tile total.
-  uint32_t tot[DPT];
-#pragma unroll
-  for (int q = 0; q < DPT; ++q) {
-    const int d = tid * DPT + q;
-    uint32_t run = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      const uint32_t c = wcnt[w * RADIX + d];
-      wcnt[w * RADIX + d] = static_cast<uint16_t>(run);
-      run += c;
+  for (;;) {
+    if (tid == 0) {
+      const uint32_t t = atomicAdd(a.tile_counter, 1u);
+      unit_sh = t;
+      const uint64_t tb = static_cast<uint64_t>(t) * TILE;
+      if (t < n_tiles && tb + TILE <= a.n) {
+        fence_proxy_async_smem();  // earlier generic accesses to the buffers come first
+        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(C::kKeysBytes + C::kValsBytes));
+        bulk_load(skeys, a.keys_in + tb, static_cast<uint32_t>(C::kKeysBytes), bar);
+        bulk_load(vin, a.vals_in + tb, static_cast<uint32_t>(C::kValsBytes), bar);
+      }
     }
-    tot[q] = run;
-  }
-  // Publish this tile's counts before looking back.
-  uint64_t* st_row = a.status + static_cast<size_t>(tile) * RADIX + static_cast<size_t>(tid) * DPT;
-  const uint64_t ep = static_cast<uint64_t>(a.epoch) << 48;
-#pragma unroll
-  for (int q = 0; q < DPT; ++q) st_status(st_row + q, (tile == 0 ? kFlagInc : kFlagAgg) | ep | tot[q]);
+    for (int i = tid; i < NW * RADIX / 2; i += TPB) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
+    __syncthreads();
+    const uint32_t unit = unit_sh;
+    if (unit >= n_tiles) break;
+    const uint64_t tbase = static_cast<uint64_t>(unit) * TILE;
+    const uint32_t valid = a.n - tbase < static_cast<uint64_t>(TILE) ? static_cast<uint32_t>(a.n - tbase) : TILE;
+    if (valid == TILE) {
+      uint32_t spins = 0;
+      bool ok = true;
+      while (!mbar_try_wait(bar, parity)) {
+        if (++spins > kSpinLimit) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) {
+        // Give the copies a second bounded chance to land before leaving.
+        if (tid == 0) atomicOr(a.err, kErrLookbackTimeout);
+        spins = 0;
+        while (!mbar_try_wait(bar, parity) && ++spins < kSpinLimit) {
+        }
+        break;
+      }
+      parity ^= 1u;
+    } else {
+      for (uint32_t i = tid; i < valid; i += TPB) {
+        skeys[i] = a.keys_in[tbase + i];
+        vin[i] = a.vals_in[tbase + i];
+      }
+      __syncthreads();
+    }
 
-  // Tile-local exclusive scan over digits.
-  uint32_t tsum = 0;
+    // Rank within the warp (keys from shared memory).
+    const uint32_t wbase = warp * 32u * IPT;
+    uint64_t key[IPT];
+    uint32_t rank[IPT];
+    uint16_t* my = wcnt + static_cast<size_t>(warp) * RADIX;
 #pragma unroll
-  for (int q = 0; q < DPT; ++q) tsum += tot[q];
-  uint32_t run = block_excl_scan<TPB>(tsum, warp_tmp, &scan_total);
-#pragma unroll
-  for (int q = 0; q < DPT; ++q) {
-    local_start[tid * DPT + q] = run;
-    run += tot[q];
-  }
-
-  // Decoupled look-back, all of this thread's digits in flight together.
-  uint64_t prefix[DPT];
-  int64_t look[DPT];
-  uint32_t pending = 0;
-#pragma unroll
-  for (int q = 0; q < DPT; ++q) {
-    prefix[q] = 0;
-    look[q] = static_cast<int64_t>(tile) - 1;
-    if (tile > 0) pending |= 1u << q;
-  }
-  uint32_t spins = 0;
-  while (pending) {
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
+      const bool ok = li < valid;
+      key[j] = ok ? skeys[li] : 0ull;
+      const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (static_cast<int>(lane) == leader && ok) {
+        old = my[d];
+        my[d] = static_cast<uint16_t>(old + __popc(peers));
+      }
+      old = __shfl_sync(0xffffffffu, old, leader);
+      rank[j] = old + __popc(peers & lt);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t tot[DPT];
+    uint32_t tsum = 0;
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
-      if (!(pending & (1u << q))) continue;
-      if (!SNC_IN_BOUNDS(a.err, 12u, static_cast<uint64_t>(look[q]), static_cast<uint64_t>(tile))) {
-        pending &= ~(1u << q);
-        continue;
+      const int d = tid * DPT + q;
+      uint32_t r = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = wcnt[w * RADIX + d];
+        wcnt[w * RADIX + d] = static_cast<uint16_t>(r);
+        r += c;
       }
-      const uint64_t v = ld_status(a.status + static_cast<size_t>(look[q]) * RADIX + tid * DPT + q);
-      const bool fresh = ((v >> 48) & 0x3FFFull) == a.epoch;
-      const uint64_t flag = fresh ? (v & (3ull << 62)) : 0ull;
-      if (flag == 0) continue;
-      prefix[q] += v & kCountMask;
-      if (flag == kFlagInc) pending &= ~(1u << q);
-      else --look[q];
+      tot[q] = r;
+      tsum += r;
     }
-    if (pending && ++spins > kSpinLimit) {
-      atomicOr(a.err, kErrLookbackTimeout);
-      break;
+    uint64_t* st_row = a.status + static_cast<size_t>(unit) * RADIX + static_cast<size_t>(tid) * DPT;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) st_status(st_row + q, (unit == 0 ? kFlagInc : kFlagAgg) | ep | tot[q]);
+    uint32_t excl = block_excl_scan<TPB>(tsum, warp_tmp, &scan_total);
+    uint32_t my_start[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      my_start[q] = excl;
+      local_start[tid * DPT + q] = excl;
+      excl += tot[q];
     }
-  }
+    __syncthreads();
+    // Stage the tile in digit order while the predecessors publish (the key
+    // buffer is free: the keys are in registers).
 #pragma unroll
-  for (int q = 0; q < DPT; ++q) {
-    const int d = tid * DPT + q;
-    if (tile > 0) st_status(st_row + q, kFlagInc | ep | ((prefix[q] + tot[q]) & kCountMask));
-    glob[d] = a.digit_start[d] + prefix[q] - local_start[d];
-  }
-  __syncthreads();
-
-  // Local positions; then the tile is staged in digit order.
-  uint32_t lpos[IPT];
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
-    const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & mask;
-    lpos[j] = idx < a.n ? local_start[d] + wcnt[warp * RADIX + d] + rank[j] : 0xFFFFFFFFu;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    if (lpos[j] != 0xFFFFFFFFu && SNC_IN_BOUNDS(a.err, 10u, lpos[j], TILE)) {
-      const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
-      skeys[lpos[j]] = key[j];
-      svals[lpos[j]] = a.vals_in[idx];
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
+      if (li < valid) {
+        const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & mask;
+        const uint32_t lp = local_start[d] + wcnt[warp * RADIX + d] + rank[j];
+        if (SNC_IN_BOUNDS(a.err, 10u, lp, TILE)) {
+          skeys[lp] = key[j];
+          svals[lp] = vin[li];
+        }
+      }
     }
-  }
-  __syncthreads();
-  const uint64_t left = a.n - tile_base;
-  const uint32_t valid = left < static_cast<uint64_t>(TILE) ? static_cast<uint32_t>(left) : static_cast<uint32_t>(TILE);
-  for (uint32_t i = tid; i < valid; i += TPB) {
-    const uint64_t k = skeys[i];
-    const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
-    const uint64_t pos = glob[d] + i;
-    if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
-    a.keys_out[pos] = k;
-    a.vals_out[pos] = svals[i];
+    uint64_t prefix[DPT];
+    look_back<RADIX, DPT, W>(a, unit, prefix);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = tid * DPT + q;
+      if (unit > 0) st_status(st_row + q, kFlagInc | ep | ((prefix[q] + tot[q]) & kCountMask));
+      globm[d] = a.digit_start[d] + prefix[q] - my_start[q];
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < valid; i += TPB) {
+      const uint64_t k = skeys[i];
+      const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
+      const uint64_t pos = globm[d] + i;
+      if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
+      a.keys_out[pos] = k;
+      a.vals_out[pos] = svals[i];
+    }
+    __syncthreads();
   }
 }
 
-template <int BITS, int TPB, int IPT>
-size_t onesweep_smem() {
-  constexpr int RADIX = 1 << BITS;
-  constexpr int NW = TPB / 32;
-  constexpr int TILE = TPB * IPT;
-  constexpr size_t cnt = static_cast<size_t>(NW) * RADIX * sizeof(uint16_t);
-  constexpr size_t tilebytes = static_cast<size_t>(TILE) * (sizeof(uint64_t) + sizeof(uint32_t));
-  constexpr size_t u = cnt > tilebytes ? cnt : tilebytes;
-  return u + RADIX * sizeof(uint32_t) + RADIX * sizeof(uint64_t);
-}
-
-template <int BITS, int TPB, int IPT>
-cudaError_t launch_onesweep(const OnesweepArgs& a, uint32_t n_tiles, cudaStream_t st) {
-  const size_t sm = onesweep_smem<BITS, TPB, IPT>();
-  static bool configured = false;  // per process; attribute is per function
+template <int BITS>
+cudaError_t launch_onesweep_tma(const OnesweepArgs& a, int sms, cudaStream_t st) {
+  using C = OnesweepTma<BITS>;
+  static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS, TPB, IPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(C::kSmem));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  onesweep_kernel<BITS, TPB, IPT><<<n_tiles, TPB, sm, st>>>(a);
+  const uint64_t tiles = (a.n + C::TILE - 1) / C::TILE;
+  const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
+  const uint64_t grid = tiles < resident ? tiles : resident;
+  onesweep_tma_kernel<BITS><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
   return cudaGetLastError();
 }
 
-// Tile shape per digit width.
-int onesweep_tile(int bits) {
-  switch (bits) {
-    case 8: return 256 * 16;
-    case 9: return 256 * 16;
-    case 10: return 256 * 16;
-    default: return 512 * 12;
+template <int BITS, int G>
+cudaError_t launch_onesweep(const OnesweepArgs& a, int sms, cudaStream_t st) {
+  using C = Onesweep<BITS, G>;
+  static bool configured = false;  // the attribute is per function; set once per process
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(C::kSmem));
+    if (e != cudaSuccess) return e;
+    configured = true;
   }
+  const uint64_t units = (a.n + C::GROUP - 1) / C::GROUP;
+  const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
+  const uint64_t grid = units < resident ? units : resident;
+  onesweep_kernel<BITS, G><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_onesweep_bits(int bits, const OnesweepArgs& a, uint32_t n_tiles, cudaStream_t st) {
-  switch (bits) {
-    case 8: return launch_onesweep<8, 256, 16>(a, n_tiles, st);
-    case 9: return launch_onesweep<9, 256, 16>(a, n_tiles, st);
-    case 10: return launch_onesweep<10, 256, 16>(a, n_tiles, st);
-    case 11: return launch_onesweep<11, 512, 12>(a, n_tiles, st);
+// Keys per look-back unit for a digit width and group size.
+int onesweep_group(int bits, int group_tiles) {
+  (void)bits;
+  return kSortTile * (group_tiles > 0 ? group_tiles : 1);
+}
+
+template <int BITS>
+cudaError_t launch_onesweep_g(int group_tiles, const OnesweepArgs& a, int sms, cudaStream_t st) {
+  switch (group_tiles) {
+    case 0:
+      if (BITS <= 9) return launch_onesweep_tma<(BITS <= 9 ? BITS : 9)>(a, sms, st);
+      return launch_onesweep<BITS, 1>(a, sms, st);
+    case 1: return launch_onesweep<BITS, 1>(a, sms, st);
+    case 4: return launch_onesweep<BITS, 4>(a, sms, st);
+    case 8: return launch_onesweep<BITS, 8>(a, sms, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-// Digit plan: the fewest passes of at most 11 bits, widths as even as
+cudaError_t launch_onesweep_bits(int bits, int group_tiles, const OnesweepArgs& a, int sms, cudaStream_t st) {
+  switch (bits) {
+    case 8: return launch_onesweep_g<8>(group_tiles, a, sms, st);
+    case 9: return launch_onesweep_g<9>(group_tiles, a, sms, st);
+    case 10: return launch_onesweep_g<10>(group_tiles, a, sms, st);
+    case 11: return launch_onesweep_g<11>(group_tiles, a, sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Process-wide sort tuning (set by snc_set_tuning / the autotuner).
+SortTuning g_sort_tuning{8, 0};
+
+// Digit plan: the fewest passes of at most max_bits bits, widths as even as
 // possible, the kernel's digit width the widest of them (at least 8).
-SortPasses plan_passes(int key_bits) {
+SortPasses plan_passes(int key_bits) { return plan_passes(key_bits, g_sort_tuning); }
+
+SortPasses plan_passes(int key_bits, const SortTuning& tune) {
   SortPasses sp{};
-  sp.n_passes = (key_bits + 10) / 11;
+  const int max_bits = tune.max_digit_bits < 8 ? 8 : (tune.max_digit_bits > 11 ? 11 : tune.max_digit_bits);
+  sp.n_passes = (key_bits + max_bits - 1) / max_bits;
   if (sp.n_passes < 1) sp.n_passes = 1;
   int shift = 0;
   int widest = 0;
@@ -370,12 +726,14 @@ SortPasses plan_passes(int key_bits) {
     if (w > widest) widest = w;
   }
   sp.kernel_bits = widest < 8 ? 8 : widest;
+  sp.group_tiles = (tune.group_tiles == 0 || tune.group_tiles == 1 || tune.group_tiles == 4) ? tune.group_tiles : 8;
   return sp;
 }
 
 size_t sort_scratch_bytes(uint64_t n, const SortPasses& sp) {
-  const uint64_t tiles = (n + onesweep_tile(sp.kernel_bits) - 1) / onesweep_tile(sp.kernel_bits);
-  const size_t status = static_cast<size_t>(tiles ? tiles : 1) * (1u << sp.kernel_bits) * sizeof(uint64_t);
+  const uint64_t groups = (n + onesweep_group(sp.kernel_bits, sp.group_tiles) - 1) /
+                          onesweep_group(sp.kernel_bits, sp.group_tiles);
+  const size_t status = static_cast<size_t>(groups ? groups : 1) * (1u << sp.kernel_bits) * sizeof(uint64_t);
   const size_t hist = static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long);
   const size_t start = static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(uint64_t);
   const size_t counters = 64 * sizeof(uint32_t);
@@ -396,52 +754,74 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 // scratch: sort_scratch_bytes(n, sp) bytes of device memory.
 // pass_events (optional, n_passes + 1 events): recorded after the histogram
 // and after each pass.
+SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp) {
+  SortScratch l{};
+  const int group = onesweep_group(sp.kernel_bits, sp.group_tiles);
+  const uint64_t groups = (n + group - 1) / group;
+  unsigned char* p = static_cast<unsigned char*>(scratch);
+  l.status_bytes = static_cast<size_t>(groups ? groups : 1) * (1u << sp.kernel_bits) * sizeof(uint64_t);
+  l.status = reinterpret_cast<uint64_t*>(p);
+  p += align256(l.status_bytes);
+  l.hist = reinterpret_cast<unsigned long long*>(p);
+  p += align256(static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long));
+  l.start = reinterpret_cast<uint64_t*>(p);
+  p += align256(static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(uint64_t));
+  l.counters = reinterpret_cast<uint32_t*>(p);
+  return l;
+}
+
 cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
                            uint64_t* keys_tmp, uint32_t* vals_tmp, uint64_t n, const SortPasses& sp, void* scratch,
-                           uint32_t* err, cudaStream_t st, cudaEvent_t* pass_events) {
+                           uint32_t* err, cudaStream_t st, cudaEvent_t* pass_events, bool hist_ready) {
   if (n == 0) {
     if (pass_events)
       for (int i = 0; i <= sp.n_passes; ++i) cudaEventRecord(pass_events[i], st);
     return cudaSuccess;
   }
-  const int tile = onesweep_tile(sp.kernel_bits);
-  const uint64_t tiles = (n + tile - 1) / tile;
-  if (tiles > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+  const int group = onesweep_group(sp.kernel_bits, sp.group_tiles);
+  const uint64_t groups = (n + group - 1) / group;
+  if (groups > 0x7FFFFFFFull) return cudaErrorInvalidValue;
   if ((sp.n_passes % 2 == 0) && (static_cast<const void*>(keys_tmp) == static_cast<const void*>(keys_in) ||
                                  static_cast<const void*>(vals_tmp) == static_cast<const void*>(vals_in)))
     return cudaErrorInvalidValue;
-  unsigned char* p = static_cast<unsigned char*>(scratch);
-  const size_t status_bytes = static_cast<size_t>(tiles) * (1u << sp.kernel_bits) * sizeof(uint64_t);
-  uint64_t* status = reinterpret_cast<uint64_t*>(p);
-  p += align256(status_bytes);
-  unsigned long long* hist = reinterpret_cast<unsigned long long*>(p);
-  p += align256(static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long));
-  uint64_t* start = reinterpret_cast<uint64_t*>(p);
-  p += align256(static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(uint64_t));
-  uint32_t* counters = reinterpret_cast<uint32_t*>(p);
+  const SortScratch lay = sort_scratch_layout(scratch, n, sp);
+  uint64_t* status = lay.status;
+  const size_t status_bytes = lay.status_bytes;
+  unsigned long long* hist = lay.hist;
+  uint64_t* start = lay.start;
+  uint32_t* counters = lay.counters;
 
   cudaError_t e;
   if ((e = cudaMemsetAsync(status, 0, status_bytes, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(hist, 0, static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long), st)) !=
-      cudaSuccess)
-    return e;
   if ((e = cudaMemsetAsync(counters, 0, 64 * sizeof(uint32_t), st)) != cudaSuccess) return e;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t hist_smem = static_cast<size_t>(sp.n_passes) * kMaxRadix * sizeof(uint32_t);
-  static bool hist_configured = false;
-  if (!hist_configured) {
-    e = cudaFuncSetAttribute(radix_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kMaxPasses * kMaxRadix * sizeof(uint32_t)));
-    if (e != cudaSuccess) return e;
-    hist_configured = true;
+  if (!hist_ready) {
+    if ((e = cudaMemsetAsync(hist, 0, static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long),
+                             st)) != cudaSuccess)
+      return e;
+    const HistPlan plan = hist_plan(sp, hist);
+    const size_t hist_smem = hist_smem_bytes(plan);
+    static bool hist_configured = false;
+    if (!hist_configured) {
+      e = cudaFuncSetAttribute(radix_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(kMaxPasses * kMaxRadix * sizeof(uint32_t)));
+      if (e != cudaSuccess) return e;
+      hist_configured = true;
+    }
+    radix_hist_kernel<<<sms * 2, 512, hist_smem, st>>>(keys_in, n, plan);
   }
-  radix_hist_kernel<<<sms * 2, 512, hist_smem, st>>>(keys_in, n, sp, hist);
   radix_digit_scan_kernel<<<sp.n_passes, kDigitScanThreads, 0, st>>>(hist, start);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (pass_events) cudaEventRecord(pass_events[0], st);
 
+  // The bulk-copy kernel needs 16-byte aligned arrays; fall back otherwise.
+  const auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  int group_tiles = sp.group_tiles;
+  if (group_tiles == 0 && !(aligned16(keys_in) && aligned16(vals_in) && aligned16(keys_out) && aligned16(vals_out) &&
+                            (sp.n_passes < 2 || (aligned16(keys_tmp) && aligned16(vals_tmp)))))
+    group_tiles = 1;
   const uint64_t* kin = keys_in;
   const uint32_t* vin = vals_in;
   for (int pass = 0; pass < sp.n_passes; ++pass) {
@@ -461,7 +841,7 @@ cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uin
     a.tile_counter = counters + pass;
     a.epoch = static_cast<uint32_t>(pass + 1);
     a.err = err;
-    if ((e = launch_onesweep_bits(sp.kernel_bits, a, static_cast<uint32_t>(tiles), st)) != cudaSuccess) return e;
+    if ((e = launch_onesweep_bits(sp.kernel_bits, group_tiles, a, sms, st)) != cudaSuccess) return e;
     if (pass_events) cudaEventRecord(pass_events[pass + 1], st);
     kin = kout;
     vin = vout;

@@ -16,6 +16,7 @@ constexpr int kDigitScanThreads = 256;
 struct SortPasses {
   int n_passes;
   int kernel_bits;  // digit width the pass kernel is instantiated for
+  int group_tiles;  // tiles per look-back unit (1, 4 or 8)
   int shift[kMaxPasses];
   uint32_t mask[kMaxPasses];
 };
@@ -29,17 +30,38 @@ struct OnesweepArgs {
   int shift;
   uint32_t mask;
   const uint64_t* digit_start;  // global exclusive digit offsets of this pass
-  uint64_t* status;             // look-back words [tile][digit]
-  uint32_t* tile_counter;       // dynamic tile ids, zero before the pass
+  uint64_t* status;             // look-back words [group][digit]
+  uint32_t* tile_counter;       // dynamic group tickets, zero before the pass
   uint32_t epoch;               // 1..16383, distinct for every pass sharing `status`
   uint32_t* err;
 };
 
-SortPasses plan_passes(int key_bits);
-int onesweep_tile(int bits);
+// Sort parameters chosen by the tuner: widest digit (8..11 bits) and tiles
+// per look-back unit (1, 4, 8).
+struct SortTuning {
+  int max_digit_bits;
+  int group_tiles;
+};
+extern SortTuning g_sort_tuning;
+
+SortPasses plan_passes(int key_bits);  // with g_sort_tuning
+SortPasses plan_passes(int key_bits, const SortTuning& tune);
+int onesweep_group(int bits, int group_tiles);
 size_t sort_scratch_bytes(uint64_t n, const SortPasses& sp);
+// Where the parts of the sort's scratch live (sort_scratch_bytes in total).
+struct SortScratch {
+  uint64_t* status;
+  size_t status_bytes;
+  unsigned long long* hist;  // [kMaxPasses][kMaxRadix] digit counts
+  uint64_t* start;           // [kMaxPasses][kMaxRadix] exclusive digit offsets
+  uint32_t* counters;        // tile tickets, one per pass
+};
+SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp);
+
+// hist_ready: the digit counts are already in the scratch's hist area (for
+// example accumulated by the kernels that produced the keys).
 cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
                            uint64_t* keys_tmp, uint32_t* vals_tmp, uint64_t n, const SortPasses& sp, void* scratch,
-                           uint32_t* err, cudaStream_t st, cudaEvent_t* pass_events);
+                           uint32_t* err, cudaStream_t st, cudaEvent_t* pass_events, bool hist_ready = false);
 
 }  // namespace snc

@@ -65,6 +65,11 @@ class snc_config(ctypes.Structure):
                 ("allocator", ctypes.POINTER(snc_allocator))]
 
 
+class snc_tuning(ctypes.Structure):
+    _fields_ = [("sort_digit_bits", ctypes.c_int32), ("sort_group_tiles", ctypes.c_int32),
+                ("gen_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class snc_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
                 ("d2h_bytes", ctypes.c_uint64), ("n_passes", ctypes.c_int32),
@@ -83,7 +88,7 @@ class snc_conn_view(ctypes.Structure):
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
-           "snc_last_error")
+           "snc_set_tuning", "snc_get_tuning", "snc_last_error")
 
 _LIB = None
 
@@ -113,6 +118,8 @@ def load(build: bool = True):
         "snc_radix_sort_pairs": ([P, P, P, P, U64, I32, P], I32),
         "snc_radix_sort_pairs_noalloc": ([P, P, P, P, U64, I32, P], I32),
         "snc_get_stats": ([P, ctypes.POINTER(snc_stats)], I32),
+        "snc_set_tuning": ([ctypes.POINTER(snc_tuning)], I32),
+        "snc_get_tuning": ([ctypes.POINTER(snc_tuning)], I32),
         "snc_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():
@@ -205,6 +212,24 @@ def snc_get_stats(ctx):
     st = snc_stats()
     _check(load().snc_get_stats(ctx, ctypes.byref(st)), ctx)
     return st
+
+
+def snc_set_tuning(sort_digit_bits=None, sort_group_tiles=None, gen_blocks_per_sm=None):
+    t = snc_get_tuning()
+    if sort_digit_bits is not None:
+        t.sort_digit_bits = int(sort_digit_bits)
+    if sort_group_tiles is not None:
+        t.sort_group_tiles = int(sort_group_tiles)
+    if gen_blocks_per_sm is not None:
+        t.gen_blocks_per_sm = int(gen_blocks_per_sm)
+    _check(load().snc_set_tuning(ctypes.byref(t)))
+    return t
+
+
+def snc_get_tuning():
+    t = snc_tuning()
+    _check(load().snc_get_tuning(ctypes.byref(t)))
+    return t
 
 
 def snc_last_error(ctx=None):

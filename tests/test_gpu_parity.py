@@ -154,18 +154,26 @@ def test_launch_shape_independence(snc):
         np.testing.assert_array_equal(a[f], b[f])
 
 
-@pytest.mark.parametrize("n_nodes,delay,passes", [(4, Dist("const", 0.1), 1), (60, Dist("normal", 1.5, 0.75), 2),
-                                                  (3000, Dist("normal", 1.5, 0.75), 3),
-                                                  (18000, Dist("normal", 1.5, 0.75), 4)])
-def test_every_pass_parity(snc, oracle_mod, n_nodes, delay, passes):
+@pytest.mark.parametrize("digit_bits,group", [(11, 8), (8, 0), (9, 4)], ids=["d11g8", "d8tma", "d9g4"])
+@pytest.mark.parametrize("n_nodes,delay", [(4, Dist("const", 0.1)), (60, Dist("normal", 1.5, 0.75)),
+                                           (3000, Dist("normal", 1.5, 0.75)),
+                                           (18000, Dist("normal", 1.5, 0.75))])
+def test_every_pass_parity(snc, oracle_mod, n_nodes, delay, digit_bits, group):
     """The sort's buffers alternate per pass, so the result buffer depends on
-    the parity of the pass count: cover 1, 2, 3 and 4 passes."""
+    the parity of the pass count: cover odd and even counts for every kernel
+    variant (1-4 passes of up to 11 bits, 1-6 passes of 8 bits)."""
     half = n_nodes // 2
     spec = NetworkSpec(seed=21, dt=0.1, populations=[half, n_nodes - half], projections=[
         Projection(src=(0, n_nodes), tgt=(0, n_nodes), rule="fixed_total_number", k=150_001,
                    weight=Dist("normal", 5.0, 1.0), delay=delay)])
-    net = snc.Network(spec).finalize()
-    got = net.to_host()
-    assert net.stats().n_passes == passes
-    net.close()
-    assert_network_equal(got, oracle_mod.build(spec), f"passes={passes}")
+    old = snc.snc_get_tuning()
+    try:
+        snc.snc_set_tuning(sort_digit_bits=digit_bits, sort_group_tiles=group)
+        net = snc.Network(spec).finalize()
+        got = net.to_host()
+        st = net.stats()
+        net.close()
+    finally:
+        snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles)
+    assert st.n_passes == -(-st.key_bits // digit_bits)
+    assert_network_equal(got, oracle_mod.build(spec), f"passes={st.n_passes}")

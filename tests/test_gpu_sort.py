@@ -40,3 +40,56 @@ def test_sort_matches_stable_argsort(torch_snc, n, bits):
     np.testing.assert_array_equal(kout.cpu().numpy().view(np.uint64), keys[order])
     np.testing.assert_array_equal(vout.cpu().numpy().view(np.uint32), vals[order])
     np.testing.assert_array_equal(kin.cpu().numpy().view(np.uint64), keys)  # input untouched
+
+
+TUNINGS = [(8, 0), (9, 0), (8, 1), (9, 4), (9, 8), (10, 8), (11, 4), (11, 8), (11, 1)]
+
+
+@pytest.mark.parametrize("bits,group", TUNINGS, ids=[f"d{b}g{g}" for b, g in TUNINGS])
+def test_every_sort_variant_matches_stable_argsort(torch_snc, bits, group):
+    """Every kernel variant the tuner can pick gives the stable order."""
+    torch, snc = torch_snc
+    old = snc.snc_get_tuning()
+    try:
+        snc.snc_set_tuning(sort_digit_bits=bits, sort_group_tiles=group)
+        for n, kb in ((70_001, 43), (4096 * 9, 20), (1000, 64)):
+            rng = np.random.default_rng(n + kb + bits)
+            keys = rng.integers(0, 1 << min(kb, 63), n, dtype=np.uint64) & ~np.uint64(0x3F)
+            vals = np.arange(n, dtype=np.uint32)
+            kin = torch.from_numpy(keys.view(np.int64)).cuda()
+            vin = torch.from_numpy(vals.view(np.int32)).cuda()
+            kout = torch.empty_like(kin)
+            vout = torch.empty_like(vin)
+            snc.snc_radix_sort_pairs(kin.data_ptr(), vin.data_ptr(), kout.data_ptr(), vout.data_ptr(), n, kb,
+                                     torch.cuda.current_stream().cuda_stream)
+            torch.cuda.synchronize()
+            order = np.argsort(keys, kind="stable")
+            np.testing.assert_array_equal(kout.cpu().numpy().view(np.uint64), keys[order])
+            np.testing.assert_array_equal(vout.cpu().numpy().view(np.uint32), vals[order])
+    finally:
+        snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles)
+
+
+def test_misaligned_buffers_fall_back(torch_snc):
+    """Arrays that are not 16-byte aligned are sorted by the non-bulk-copy path."""
+    torch, snc = torch_snc
+    old = snc.snc_get_tuning()
+    try:
+        snc.snc_set_tuning(sort_digit_bits=8, sort_group_tiles=0)
+        n = 50_000
+        rng = np.random.default_rng(5)
+        keys = rng.integers(0, 1 << 30, n + 1, dtype=np.uint64)
+        vals = np.arange(n + 1, dtype=np.uint32)
+        kin = torch.from_numpy(keys.view(np.int64)).cuda()
+        vin = torch.from_numpy(vals.view(np.int32)).cuda()
+        kout = torch.empty_like(kin)
+        vout = torch.empty_like(vin)
+        # offset every pointer by one element: 8 and 4 bytes
+        snc.snc_radix_sort_pairs(kin.data_ptr() + 8, vin.data_ptr() + 4, kout.data_ptr() + 8, vout.data_ptr() + 4,
+                                 n, 30, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        order = np.argsort(keys[1:], kind="stable")
+        np.testing.assert_array_equal(kout.cpu().numpy().view(np.uint64)[1:], keys[1:][order])
+        np.testing.assert_array_equal(vout.cpu().numpy().view(np.uint32)[1:], vals[1:][order])
+    finally:
+        snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles)
