@@ -38,7 +38,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="snc", choices=["snc", "reference"])
     ap.add_argument("--workload", default="rule_sweep",
-                    choices=["rule_sweep", "microcircuit", "plain", "small", "profile"])
+                    choices=["rule_sweep", "microcircuit", "plain", "small", "profile", "profile_total"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sort-digit-bits", type=int, default=None, help="tuning: widest radix digit")
     ap.add_argument("--sort-group-tiles", type=int, default=None, help="tuning: tiles per look-back unit")
@@ -65,6 +65,10 @@ def workload_specs(name):
         return [W.two_population(100_000, "fixed_indegree", k=100)], {
             "workload": "profiling case: 2 x 100,000 nodes, fixed_indegree K=100 (4e7 connections, "
                         "same 43-bit key as the rule sweep)", "seed": 1234}
+    if name == "profile_total":
+        return [W.two_population(30_000, "fixed_total_number", k=20_000_000, autapses=False, multapses=False)], {
+            "workload": "profiling case: 2 x 30,000 nodes, fixed_total_number 2e7 per call without autapses "
+                        "or multapses (8e7 connections)", "seed": 1234}
     return [W.rule_sweep("fixed_indegree", True, scale=0.1)], {
         "workload": "small: 2 x 10,000 nodes fixed_indegree K=1000", "seed": 1234}
 

@@ -474,6 +474,31 @@ __device__ __forceinline__ bool allowed_pair(const DevProj& P, uint32_t s, uint3
 }
 }  // namespace
 
+// Round 0 with the packed table and the `lost` marks: a slot that finds its
+// pair already held by a lower slot marks itself lost; a slot that displaces
+// a higher one marks that one lost.  Every claimant but the lowest of a pair
+// is marked by someone, so no second pass over the table is needed, and
+// round-0 entries are written in the accepted form (claim bit clear).
+__device__ void claim_round0(const TotalArgs& a, uint64_t pair, uint64_t slot) {
+  const int sh = a.slot_bits + 1;
+  const uint64_t slot_mask = (1ull << a.slot_bits) - 1;
+  const uint64_t e = (pair << sh) | slot;
+  uint64_t h = pair_hash(pair) & a.table_mask;
+  for (uint64_t probe = 0; probe <= a.table_mask; ++probe) {
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(&a.table_keys[h]);
+    const uint64_t old = atomicCAS(w, kEmpty, e);
+    if (old == kEmpty) return;
+    if ((old >> sh) == pair) {
+      const uint64_t prev = atomicMin(w, e);
+      if (prev < e) a.lost[slot] = 1;
+      else a.lost[prev & slot_mask] = 1;
+      return;
+    }
+    h = (h + 1) & a.table_mask;
+  }
+  atomicOr(a.err, kErrBounds);
+}
+
 __global__ void total_round0_kernel(TotalArgs a) {
   const DevProj& P = *a.proj;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
@@ -486,7 +511,24 @@ __global__ void total_round0_kernel(TotalArgs a) {
     const uint32_t t = P.t0 + rand_below(tw, P.nt);
     const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
     a.pairs[i] = pair;
-    if (!P.multapses && allowed_pair(P, s, t)) claim(a, P, pair, i);
+    if (a.lost) {
+      if (!allowed_pair(P, s, t)) a.lost[i] = 1;
+      else if (!P.multapses) claim_round0(a, packed_pair(a, P, s, t), i);
+    } else if (!P.multapses && allowed_pair(P, s, t)) {
+      claim(a, P, pair, i);
+    }
+  }
+}
+
+// Round-0 slots marked lost become the first pending list.
+__global__ void total_collect_kernel(TotalArgs a) {
+  const DevProj& P = *a.proj;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.count; i += stride) {
+    if (a.lost[i]) {
+      const unsigned long long at = atomicAdd(a.n_next, 1ull);
+      if (SNC_IN_BOUNDS(a.err, 2u, at, P.count)) a.next_pending[at] = i;
+    }
   }
 }
 

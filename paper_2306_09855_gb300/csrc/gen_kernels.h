@@ -59,12 +59,14 @@ struct TotalArgs {
   int packed;
   int slot_bits;
   int t_bits;           // bits of the target's local index in pair_local
+  uint8_t* lost;        // round-0 marks (packed table or no table); null: resolve pass
   uint64_t* pending;      // slots still to redraw
   uint64_t* next_pending;
   unsigned long long* n_next;  // device counter of next_pending
   uint32_t* err;
 };
 __global__ void total_round0_kernel(TotalArgs a);
+__global__ void total_collect_kernel(TotalArgs a);
 __global__ void total_claim_kernel(TotalArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round);
 __global__ void total_resolve_kernel(TotalArgs a, const uint64_t* pending, uint64_t n_pending, int all_slots);
 __global__ void total_emit_kernel(GenArgs g, const DevProj* proj, const uint64_t* pairs);

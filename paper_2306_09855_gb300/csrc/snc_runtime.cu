@@ -608,9 +608,17 @@ snc_status snc_finalize(snc_ctx* c) {
         const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
             1, std::min<uint64_t>((N + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
         SNC_CUDA(c, cudaMemsetAsync(t.n_next, 0, sizeof(unsigned long long), st));
+        if (t.packed || p.rule.allow_multapses) {
+          t.lost = static_cast<uint8_t*>(dev_alloc(c, N));
+          if (!t.lost) return fail(c, SNC_ERR_OOM, "device allocation failed (redraw marks)");
+          SNC_CUDA(c, cudaMemsetAsync(t.lost, 0, N, st));
+        }
         total_round0_kernel<<<grid, 256, 0, st>>>(t);
         ++c->stats.kernel_launches;
-        total_resolve_kernel<<<grid, 256, 0, st>>>(t, nullptr, 0, 1);
+        if (t.lost)
+          total_collect_kernel<<<grid, 256, 0, st>>>(t);
+        else
+          total_resolve_kernel<<<grid, 256, 0, st>>>(t, nullptr, 0, 1);
         ++c->stats.kernel_launches;
         SNC_CUDA(c, cudaGetLastError());
         for (uint32_t round = 1;; ++round) {
@@ -648,6 +656,7 @@ snc_status snc_finalize(snc_ctx* c) {
         dev_free(c, t.n_next);
         dev_free(c, t.table_keys);
         dev_free(c, t.table_vals);
+        dev_free(c, t.lost);
         return SNC_OK;
       }();
       if (r != SNC_OK) return r;

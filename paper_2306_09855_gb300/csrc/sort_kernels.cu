@@ -459,6 +459,80 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbarrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// 32-bit look-back words [tile][digit] = [flag:2][count:30] for the
+// bulk-copy kernel (the area is cleared before every pass, counts < 2^30).
+constexpr uint32_t kAgg32 = 1u << 30;
+constexpr uint32_t kInc32 = 2u << 30;
+constexpr uint32_t kCount32 = (1u << 30) - 1u;
+
+__device__ __forceinline__ void st_status32(uint32_t* p, uint32_t v) {
+  *reinterpret_cast<volatile uint32_t*>(p) = v;
+}
+__device__ __forceinline__ uint32_t ld_status32(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+template <int RADIX, int DPT, int W>
+__device__ __forceinline__ void look_back32(const OnesweepArgs& a, uint32_t unit, uint64_t (&prefix)[DPT]) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t* base = a.status32 + tid * DPT;
+  int32_t look[DPT];
+  uint32_t pending = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    prefix[q] = 0;
+    look[q] = static_cast<int32_t>(unit) - 1;
+    if (unit > 0) pending |= 1u << q;
+  }
+  uint32_t spins = 0, backoff = 32u;
+  while (pending) {
+    bool progress = false;
+    uint32_t v[DPT][W];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q)
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const int32_t t = look[q] - w;
+        v[q][w] = ((pending >> q) & 1u) && t >= 0 ? ld_status32(base + static_cast<size_t>(t) * RADIX + q) : 0u;
+      }
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      if (!((pending >> q) & 1u)) continue;
+      uint32_t sum = 0;
+      int used = 0;
+      bool done = false;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        if (done) continue;
+        const uint32_t x = v[q][w];
+        if (x < kAgg32) {  // not yet published
+          done = true;
+          continue;
+        }
+        sum += x & kCount32;
+        ++used;
+        if (x >= kInc32) {
+          pending &= ~(1u << q);
+          done = true;
+        }
+      }
+      prefix[q] += sum;
+      look[q] -= used;
+      progress = progress || used > 0;
+    }
+    if (pending && !progress) {
+      if (++spins > kSpinLimit) {
+        atomicOr(a.err, kErrLookbackTimeout);
+        break;
+      }
+      __nanosleep(backoff);
+      backoff = backoff < 1024u ? backoff * 2u : 1024u;
+    } else {
+      backoff = 32u;
+    }
+  }
+}
+
 template <int BITS>
 struct OnesweepTma {
   static constexpr int TPB = kSortThreads, IPT = kSortItems, TILE = kSortTile;
@@ -501,7 +575,6 @@ __global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) oneswee
   const uint32_t mask = a.mask;
   const int shift = a.shift;
   const uint32_t lt = lanemask_lt();
-  const uint64_t ep = static_cast<uint64_t>(a.epoch) << 48;
   const uint64_t n_tiles = (a.n + TILE - 1) / TILE;
 
   if (tid == 0) {
@@ -593,9 +666,9 @@ __global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) oneswee
       tot[q] = r;
       tsum += r;
     }
-    uint64_t* st_row = a.status + static_cast<size_t>(unit) * RADIX + static_cast<size_t>(tid) * DPT;
+    uint32_t* st_row = a.status32 + static_cast<size_t>(unit) * RADIX + static_cast<size_t>(tid) * DPT;
 #pragma unroll
-    for (int q = 0; q < DPT; ++q) st_status(st_row + q, (unit == 0 ? kFlagInc : kFlagAgg) | ep | tot[q]);
+    for (int q = 0; q < DPT; ++q) st_status32(st_row + q, (unit == 0 ? kInc32 : kAgg32) | tot[q]);
     uint32_t excl = block_excl_scan<TPB>(tsum, warp_tmp, &scan_total);
     uint32_t my_start[DPT];
 #pragma unroll
@@ -620,11 +693,11 @@ __global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) oneswee
       }
     }
     uint64_t prefix[DPT];
-    look_back<RADIX, DPT, W>(a, unit, prefix);
+    look_back32<RADIX, DPT, W>(a, unit, prefix);
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
       const int d = tid * DPT + q;
-      if (unit > 0) st_status(st_row + q, kFlagInc | ep | ((prefix[q] + tot[q]) & kCountMask));
+      if (unit > 0) st_status32(st_row + q, kInc32 | static_cast<uint32_t>((prefix[q] + tot[q]) & kCount32));
       globm[d] = a.digit_start[d] + prefix[q] - my_start[q];
     }
     __syncthreads();
@@ -816,12 +889,15 @@ cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uin
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (pass_events) cudaEventRecord(pass_events[0], st);
 
-  // The bulk-copy kernel needs 16-byte aligned arrays; fall back otherwise.
+  // The bulk-copy kernel needs 16-byte aligned arrays and counts below 2^30
+  // (30-bit look-back words); fall back otherwise.
   const auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   int group_tiles = sp.group_tiles;
-  if (group_tiles == 0 && !(aligned16(keys_in) && aligned16(vals_in) && aligned16(keys_out) && aligned16(vals_out) &&
-                            (sp.n_passes < 2 || (aligned16(keys_tmp) && aligned16(vals_tmp)))))
+  if (group_tiles == 0 &&
+      (n >= (1ull << 30) || !(aligned16(keys_in) && aligned16(vals_in) && aligned16(keys_out) &&
+                              aligned16(vals_out) && (sp.n_passes < 2 || (aligned16(keys_tmp) && aligned16(vals_tmp))))))
     group_tiles = 1;
+  const size_t status32_bytes = static_cast<size_t>((n + kSortTile - 1) / kSortTile) * (1u << sp.kernel_bits) * 4u;
   const uint64_t* kin = keys_in;
   const uint32_t* vin = vals_in;
   for (int pass = 0; pass < sp.n_passes; ++pass) {
@@ -841,6 +917,8 @@ cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uin
     a.tile_counter = counters + pass;
     a.epoch = static_cast<uint32_t>(pass + 1);
     a.err = err;
+    a.status32 = reinterpret_cast<uint32_t*>(status);
+    if (group_tiles == 0 && (e = cudaMemsetAsync(status, 0, status32_bytes, st)) != cudaSuccess) return e;
     if ((e = launch_onesweep_bits(sp.kernel_bits, group_tiles, a, sms, st)) != cudaSuccess) return e;
     if (pass_events) cudaEventRecord(pass_events[pass + 1], st);
     kin = kout;

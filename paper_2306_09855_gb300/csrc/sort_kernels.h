@@ -34,6 +34,7 @@ struct OnesweepArgs {
   uint32_t* tile_counter;       // dynamic group tickets, zero before the pass
   uint32_t epoch;               // 1..16383, distinct for every pass sharing `status`
   uint32_t* err;
+  uint32_t* status32;           // bulk-copy kernel: 32-bit words [tile][digit], cleared per pass
 };
 
 // Sort parameters chosen by the tuner: widest digit (8..11 bits) and tiles
