@@ -163,6 +163,19 @@ snc_status snc_connect(snc_ctx* ctx, snc_range src, snc_range tgt, const snc_con
  * a sampler range beyond the shared-memory bitmap. */
 snc_status snc_finalize(snc_ctx* ctx);
 
+/* Batched calibration (no counterpart in the paper, which builds one network
+ * at a time; useful for parameter scans): finalizes n unfinalized contexts
+ * of one device together, with one launch per stage for all of them.  The
+ * members' nodes are concatenated internally; every random draw stays keyed
+ * by the member's own seed and projection index, so each member's result is
+ * identical to what snc_finalize would give it alone.  All device work runs
+ * on ctxs[0]'s stream with ctxs[0]'s allocator; the members share the result
+ * memory, which is released when the last of them is destroyed.  Views and
+ * copies of each member work as for a single build.
+ * INVALID_ARG: empty list, null or repeated context, different devices.
+ * STATE: a context already finalized.  Other errors as snc_finalize. */
+snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n);
+
 /* Waits for the context's queued work and reports device-side failures
  * (TIMEOUT for a bounded wait that expired, CUDA for a launch error). */
 snc_status snc_synchronize(snc_ctx* ctx);

@@ -87,7 +87,7 @@ __device__ __forceinline__ uint32_t hist_words(const GenArgs& a) {
 __device__ __forceinline__ void store(const GenArgs& a, const BlockHist& h, uint64_t pos, uint32_t s, uint32_t d,
                                       uint32_t t, uint32_t wbits) {
   if (!SNC_IN_BOUNDS(a.err, 1u, pos, a.cap)) return;
-  const uint64_t key = pack_key(s, d, t, a.layout.node_bits, a.layout.delay_bits);
+  const uint64_t key = pack_key(s, d, t, a.layout.tgt_bits, a.layout.delay_bits);
   a.keys[pos] = key;
   a.vals[pos] = wbits;
   hist_add(h.sh, h.r, key);
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
         if (bp >= row_len) break;
         const uint32_t b = bp + (diag && bp >= diag_b ? 1u : 0u);
         const Words W = draw(P.k0, P.k1, kTagWD, 0, b, row);
-        store(a, bh, row_out + bp, s, delay_step(P, tabs, W.x), P.t0 + b, weight_bits(P, W.z, W.w));
+        store(a, bh, row_out + bp, s, delay_step(P, tabs, W.x), P.t0 + b - P.t_base, weight_bits(P, W.z, W.w));
       }
       continue;
     }
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
           s = P.s0 + rand_below(W.y, P.ns);
           t = P.t0 + rand_below(tw, P.nt);
         }
-        store(a, bh, P.out_off + i, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+        store(a, bh, P.out_off + i, s, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
       }
     }
   }
@@ -326,7 +326,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
             const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
             const uint32_t other = first_other + r;
             const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            store(a.gen, bh, out + j, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+            store(a.gen, bh, out + j, s, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
           }
         }
         got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
@@ -361,7 +361,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
             const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
             const uint32_t other = first_other + r;
             const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            store(a.gen, bh, out + j, s, delay_step(P, tabs, W.x), t, weight_bits(P, W.z, W.w));
+            store(a.gen, bh, out + j, s, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
           } else {
             atomicOr(a.err, kErrBounds);
           }
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, cons
     const uint64_t pair = pairs[i];
     const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
     store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32), delay_step(P, tabs, W.x),
-          static_cast<uint32_t>(pair), weight_bits(P, W.z, W.w));
+          static_cast<uint32_t>(pair) - P.t_base, weight_bits(P, W.z, W.w));
   }
   block_hist_end(g, bh);
 }

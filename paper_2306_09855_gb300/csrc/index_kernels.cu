@@ -25,8 +25,8 @@ namespace snc {
 __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a) {
   __shared__ uint32_t warp_cnt[kIndexThreads / 32];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const int sd_shift = a.node_bits;
-  const uint64_t node_mask = (1ull << a.node_bits) - 1;
+  const int sd_shift = a.tgt_bits;
+  const uint64_t node_mask = (1ull << a.tgt_bits) - 1;
   const uint32_t delay_mask = (1u << a.delay_bits) - 1u;
   const uint64_t n_blocks = (a.n + kIndexTile - 1) / kIndexTile;
   for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kIndexThreads) index_groups_kernel(IndexArgs a
 __global__ void node_index_kernel(NodeIndexArgs a) {
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i > a.n_nodes) return;
-  const int src_shift = a.node_bits + a.delay_bits;
+  const int src_shift = a.tgt_bits + a.delay_bits;
   uint64_t lo = 0, hi = a.n;
   while (lo < hi) {
     const uint64_t mid = (lo + hi) >> 1;
@@ -164,6 +164,40 @@ __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes,
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   for (uint64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) src[q] = static_cast<uint32_t>(i);
+}
+
+// One thread per (network, local node or end entry): total_nodes + n_nets.
+__global__ void rebase_nodes_kernel(RebaseArgs a) {
+  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= a.total_nodes + static_cast<uint64_t>(a.n_nets)) return;
+  // Entry i of the concatenated local arrays: network b holds entries
+  // [node_base[b] + b, node_base[b + 1] + b + 1).
+  int lo = 0, hi = a.n_nets - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.node_base[mid] + static_cast<uint64_t>(mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  const uint64_t local = i - a.node_base[b] - static_cast<uint64_t>(b);
+  const uint64_t g = a.node_base[b] + local;
+  const uint64_t first = a.node_base[b];
+  a.row_local[a.local_base[b] + local] = a.row_ptr[g] - a.row_ptr[first];
+  a.group_local[a.local_base[b] + local] = a.group_ptr[g] - a.group_ptr[first];
+}
+
+// group_first[g] -= first connection of the group's network.
+__global__ void rebase_groups_kernel(RebaseArgs a) {
+  const uint64_t ng = *a.n_groups < a.n_groups_cap ? *a.n_groups : a.n_groups_cap;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < ng; g += stride) {
+    // The network whose group range [group_ptr[base], group_ptr[base_next]) holds g.
+    int lo = 0, hi = a.n_nets - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.group_ptr[a.node_base[mid]] <= g) lo = mid; else hi = mid - 1;
+    }
+    a.group_first[g] -= a.row_ptr[a.node_base[lo]];
+  }
 }
 
 }  // namespace snc

@@ -14,7 +14,7 @@ constexpr int kIndexTile = kIndexThreads * kIndexItems;
 struct IndexArgs {
   const uint64_t* keys;  // sorted packed keys
   uint64_t n;
-  int node_bits, delay_bits;
+  int tgt_bits, delay_bits;
   uint32_t* target;
   uint16_t* delay;
   uint32_t* starts;          // group-start bitmap, kIndexTile / 32 words per block
@@ -30,7 +30,7 @@ struct NodeIndexArgs {
   const uint64_t* keys;
   uint64_t n;
   uint64_t n_nodes;
-  int node_bits, delay_bits;
+  int tgt_bits, delay_bits;
   const uint64_t* group_first;
   uint64_t group_cap;
   const uint64_t* n_groups;
@@ -42,5 +42,23 @@ __global__ void index_unpack_kernel(IndexArgs a);
 __global__ void index_groups_kernel(IndexArgs a);
 __global__ void node_index_kernel(NodeIndexArgs a);
 __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes, uint32_t* src);
+
+// Batches: per-network CSR offsets relative to the network's first
+// connection / group, and group starts relative to its first connection.
+struct RebaseArgs {
+  const uint64_t* row_ptr;     // global node CSR of the build [total_nodes + 1]
+  const uint64_t* group_ptr;   // [total_nodes + 1]
+  const uint64_t* node_base;   // first global node of each network [n_nets + 1]
+  const uint64_t* local_base;  // first entry of each network's local arrays [n_nets]
+  int n_nets;
+  uint64_t total_nodes;
+  uint64_t* row_local;         // concatenated per-network arrays of (n + 1) entries
+  uint64_t* group_local;
+  uint64_t* group_first;       // rebased in place
+  uint64_t n_groups_cap;
+  const uint64_t* n_groups;
+};
+__global__ void rebase_nodes_kernel(RebaseArgs a);
+__global__ void rebase_groups_kernel(RebaseArgs a);
 
 }  // namespace snc

@@ -23,7 +23,8 @@ constexpr int kDelayGuide = 257;  // guide-table entries per threshold table
 
 // One Connect call as the kernels see it (plain data, copied to the device).
 struct DevProj {
-  uint32_t s0, ns, t0, nt;
+  uint32_t s0, ns, t0, nt;  // global node ranges of the build
+  uint32_t t_base;          // first node of the projection's network (targets are packed relative to it)
   uint32_t rule;
   uint32_t autapses, multapses;
   uint32_t w_normal;
@@ -46,15 +47,18 @@ struct DevProj {
   uint32_t row_len;         // all_to_all: connections per source row (full row)
 };
 
-// Bit layout of the packed sort key: source | delay step | target.
+// Bit layout of the packed sort key: source | delay step | target.  The
+// source is a global node id of the build; the target is local to its
+// network (equal to the global id when a single network is built).
 struct KeyLayout {
-  int node_bits;
+  int src_bits;
   int delay_bits;
-  int total_bits() const { return 2 * node_bits + delay_bits; }
+  int tgt_bits;
+  int total_bits() const { return src_bits + delay_bits + tgt_bits; }
 };
 
-__host__ __device__ inline uint64_t pack_key(uint32_t s, uint32_t d, uint32_t t, int nb, int db) {
-  return (static_cast<uint64_t>(s) << (nb + db)) | (static_cast<uint64_t>(d) << nb) | t;
+__host__ __device__ inline uint64_t pack_key(uint32_t s, uint32_t d, uint32_t t_local, int tb, int db) {
+  return (static_cast<uint64_t>(s) << (tb + db)) | (static_cast<uint64_t>(d) << tb) | t_local;
 }
 
 // Host-side projection record.

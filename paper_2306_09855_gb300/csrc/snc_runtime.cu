@@ -8,6 +8,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -31,40 +33,130 @@ struct DevBuf {
   size_t bytes;
 };
 
+// Device memory of one build (a context, or all members of a batch), shared
+// by the member contexts and released when the last of them is destroyed.
+struct Storage {
+  snc_allocator alloc{};
+  bool custom_alloc = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<DevBuf> bufs;
+  uint64_t live_bytes = 0, peak_bytes = 0;
+  cudaEvent_t ev[kMaxEvents] = {};
+  int n_ev = 0;
+  bool events_ok = false;
+  uint64_t* h_pinned = nullptr;  // small pinned staging area
+  size_t h_pinned_words = 0;
+  uint32_t* d_err = nullptr;
+  uint64_t* d_n_groups = nullptr;
+  // Batches: per-member first connection / first group, read back at sync.
+  uint64_t* d_bases = nullptr;  // [2 * (members + 1)] on the device
+  uint64_t* h_bases = nullptr;  // pinned copy
+  int n_members = 1;
+  uint64_t n_total = 0;  // connections of the whole build
+  bool synced = false;
+  uint32_t err_bits = 0;
+  uint64_t n_groups = 0;
+
+  void* get(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (custom_alloc) {
+      p = alloc.alloc(bytes, stream, alloc.user);
+    } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {
+      // The kernels use vector and bulk copies that need aligned arrays.
+      if (custom_alloc) alloc.free(p, bytes, stream, alloc.user);
+      return nullptr;
+    }
+    if (p) {
+      bufs.push_back({p, bytes});
+      live_bytes += bytes;
+      if (live_bytes > peak_bytes) peak_bytes = live_bytes;
+    }
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < bufs.size(); ++i) {
+      if (bufs[i].p == p) {
+        if (custom_alloc)
+          alloc.free(p, bufs[i].bytes, stream, alloc.user);
+        else
+          cudaFreeAsync(p, stream);
+        live_bytes -= bufs[i].bytes;
+        bufs.erase(bufs.begin() + static_cast<long>(i));
+        return;
+      }
+    }
+  }
+  bool init_host(size_t words) {
+    for (int i = 0; i < kMaxEvents; ++i) {
+      if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+        cudaGetLastError();
+        for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+        return false;
+      }
+    }
+    events_ok = true;
+    if (cudaMallocHost(&h_pinned, words * sizeof(uint64_t)) != cudaSuccess) {
+      cudaGetLastError();
+      h_pinned = nullptr;
+      return false;
+    }
+    h_pinned_words = words;
+    return true;
+  }
+  ~Storage() {
+    cudaSetDevice(device);
+    cudaStreamSynchronize(stream);
+    while (!bufs.empty()) put(bufs.back().p);
+    cudaStreamSynchronize(stream);
+    if (events_ok)
+      for (int i = 0; i < kMaxEvents; ++i) cudaEventDestroy(ev[i]);
+    if (h_pinned) cudaFreeHost(h_pinned);
+    if (h_bases) cudaFreeHost(h_bases);
+    cudaGetLastError();
+  }
+};
+
 }  // namespace
 
 struct snc_ctx {
   snc_config cfg{};
-  snc_allocator alloc{};
-  bool custom_alloc = false;
   cudaStream_t stream = nullptr;
   int device = 0;
   int sms = 148;
   uint64_t n_nodes = 0;
   std::vector<Projection> projs;
   bool finalized = false;
-  bool synced = false;
   std::string err = "no error";
-  std::vector<DevBuf> bufs;
-  // results
+  std::shared_ptr<Storage> store;
+  // Position of this context in its build (member 0 of one for a plain
+  // finalize; a batch concatenates its members' nodes).
+  int member = 0;
+  uint64_t node_base = 0;
+  // Results: device views; for batch members resolved at synchronize.
+  bool view_ready = false;
   uint64_t n_syn = 0;
   uint64_t n_groups = 0;
   uint64_t group_cap = 0;
   uint64_t* row_ptr = nullptr;
+  uint64_t* group_ptr = nullptr;
+  uint32_t* target_all = nullptr;
+  uint16_t* delay_all = nullptr;
+  float* weight_all = nullptr;
+  uint64_t* group_first_all = nullptr;
   uint32_t* target = nullptr;
   uint16_t* delay = nullptr;
   float* weight = nullptr;
-  uint64_t* group_ptr = nullptr;
   uint64_t* group_first = nullptr;
-  uint64_t* d_n_groups = nullptr;
-  uint32_t* d_err = nullptr;
-  KeyLayout layout{1, 1};
+  KeyLayout layout{1, 1, 1};
   SortPasses passes{};
-  cudaEvent_t ev[kMaxEvents] = {};
-  int n_ev = 0;
-  uint64_t* h_pinned = nullptr;  // small pinned staging area
   snc_stats stats{};
-  uint64_t live_bytes = 0;
 };
 
 namespace {
@@ -87,45 +179,12 @@ snc_status fail(snc_ctx* c, snc_status st, const char* fmt, ...) {
   } while (0)
 
 void* dev_alloc(snc_ctx* c, size_t bytes) {
-  if (bytes == 0) bytes = 256;
-  void* p = nullptr;
-  if (c->custom_alloc) {
-    p = c->alloc.alloc(bytes, c->stream, c->alloc.user);
-  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
-    cudaGetLastError();
-    p = nullptr;
-  }
-  if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {
-    // The kernels use vector and bulk copies that need aligned arrays.
-    if (c->custom_alloc) c->alloc.free(p, bytes, c->stream, c->alloc.user);
-    return nullptr;
-  }
-  if (p) {
-    c->bufs.push_back({p, bytes});
-    c->live_bytes += bytes;
-    if (c->live_bytes > c->stats.device_bytes_peak) c->stats.device_bytes_peak = c->live_bytes;
-  }
+  void* p = c->store->get(bytes);
+  c->stats.device_bytes_peak = c->store->peak_bytes;
   return p;
 }
 
-void dev_free(snc_ctx* c, void* p) {
-  if (!p) return;
-  for (size_t i = 0; i < c->bufs.size(); ++i) {
-    if (c->bufs[i].p == p) {
-      if (c->custom_alloc)
-        c->alloc.free(p, c->bufs[i].bytes, c->stream, c->alloc.user);
-      else
-        cudaFreeAsync(p, c->stream);
-      c->live_bytes -= c->bufs[i].bytes;
-      c->bufs.erase(c->bufs.begin() + static_cast<long>(i));
-      return;
-    }
-  }
-}
-
-void free_all(snc_ctx* c) {
-  while (!c->bufs.empty()) dev_free(c, c->bufs.back().p);
-}
+void dev_free(snc_ctx* c, void* p) { c->store->put(p); }
 
 int bit_width(uint64_t v) {
   int b = 0;
@@ -259,6 +318,8 @@ extern "C" {
 snc_status snc_create(const snc_config* cfg, snc_ctx** out) {
   if (!cfg || !out) return fail(nullptr, SNC_ERR_INVALID_ARG, "snc_create: null argument");
   if (!(cfg->dt_ms > 0.0) || !std::isfinite(cfg->dt_ms)) return fail(nullptr, SNC_ERR_INVALID_ARG, "dt must be > 0");
+  if (cfg->allocator && (!cfg->allocator->alloc || !cfg->allocator->free))
+    return fail(nullptr, SNC_ERR_INVALID_ARG, "allocator without alloc/free");
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
     cudaGetLastError();
     return fail(nullptr, SNC_ERR_CUDA, "cannot select device %d", cfg->device);
@@ -268,28 +329,17 @@ snc_status snc_create(const snc_config* cfg, snc_ctx** out) {
   c->cfg = *cfg;
   c->device = cfg->device;
   c->stream = static_cast<cudaStream_t>(cfg->stream);
+  c->store = std::make_shared<Storage>();
+  c->store->device = c->device;
+  c->store->stream = c->stream;
   if (cfg->allocator) {
-    if (!cfg->allocator->alloc || !cfg->allocator->free) {
-      delete c;
-      return fail(nullptr, SNC_ERR_INVALID_ARG, "allocator without alloc/free");
-    }
-    c->alloc = *cfg->allocator;
-    c->custom_alloc = true;
+    c->store->alloc = *cfg->allocator;
+    c->store->custom_alloc = true;
   }
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
-  for (int i = 0; i < kMaxEvents; ++i) {
-    if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
-      cudaGetLastError();
-      for (int j = 0; j < i; ++j) cudaEventDestroy(c->ev[j]);
-      delete c;
-      return fail(nullptr, SNC_ERR_CUDA, "cudaEventCreate failed");
-    }
-  }
-  if (cudaMallocHost(&c->h_pinned, 64 * sizeof(uint64_t)) != cudaSuccess) {
-    cudaGetLastError();
-    for (int j = 0; j < kMaxEvents; ++j) cudaEventDestroy(c->ev[j]);
+  if (!c->store->init_host(64)) {
     delete c;
-    return fail(nullptr, SNC_ERR_OOM, "pinned staging allocation failed");
+    return fail(nullptr, SNC_ERR_CUDA, "event / pinned staging allocation failed");
   }
   *out = c;
   return SNC_OK;
@@ -298,11 +348,7 @@ snc_status snc_create(const snc_config* cfg, snc_ctx** out) {
 snc_status snc_destroy(snc_ctx* c) {
   if (!c) return SNC_OK;
   cudaSetDevice(c->device);
-  cudaStreamSynchronize(c->stream);
-  free_all(c);
-  cudaStreamSynchronize(c->stream);
-  for (int i = 0; i < kMaxEvents; ++i) cudaEventDestroy(c->ev[i]);
-  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  c->store.reset();  // the build's memory goes with its last member
   cudaGetLastError();
   delete c;
   return SNC_OK;
@@ -334,24 +380,55 @@ snc_status snc_connect(snc_ctx* c, snc_range src, snc_range tgt, const snc_conn_
   return SNC_OK;
 }
 
-snc_status snc_finalize(snc_ctx* c) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  if (c->finalized) return fail(c, SNC_ERR_STATE, "finalize called twice");
-  SNC_CUDA(c, cudaSetDevice(c->device));
-  cudaStream_t st = c->stream;
-  c->n_ev = 0;
-  cudaEventRecord(c->ev[c->n_ev++], st);
+}  // extern "C"
 
-  // Key layout: source | delay step | target.
+namespace {
+
+// Calibration of one build: a single context, or the members of a batch
+// whose nodes are concatenated (member m's node i is global node
+// node_base[m] + i).  Every draw is keyed by the member's seed and the
+// projection's index within its member, so each member's result equals its
+// own single build.  All device work runs on the first member's stream and
+// memory; the members share the result storage.
+snc_status finalize_build(snc_ctx* const* members, int n_members) {
+  snc_ctx* c = members[0];
+  SNC_CUDA(c, cudaSetDevice(c->device));
+  Storage& S = *c->store;
+  cudaStream_t st = c->stream;
+  S.n_ev = 0;
+  cudaEventRecord(S.ev[S.n_ev++], st);
+
+  // The union of the members' projections.
+  struct UnionProj {
+    const Projection* p;
+    const snc_ctx* owner;
+    uint32_t base;
+    uint32_t local;
+  };
+  std::vector<uint64_t> node_base(static_cast<size_t>(n_members) + 1, 0);
+  uint64_t max_nodes = 0;
+  std::vector<UnionProj> ups;
+  for (int m = 0; m < n_members; ++m) {
+    node_base[m + 1] = node_base[m] + members[m]->n_nodes;
+    max_nodes = std::max<uint64_t>(max_nodes, members[m]->n_nodes);
+    for (size_t i = 0; i < members[m]->projs.size(); ++i)
+      ups.push_back({&members[m]->projs[i], members[m], static_cast<uint32_t>(node_base[m]), static_cast<uint32_t>(i)});
+  }
+  const uint64_t total_nodes = node_base[n_members];
+  if (total_nodes > 0xFFFFFFFFull) return fail(c, SNC_ERR_UNSUPPORTED, "more than 2^32 - 1 nodes in one build");
+
+  // Key layout: global source | delay step | member-local target.
   uint32_t max_step = 1;
-  for (const Projection& p : c->projs) max_step = std::max(max_step, p.max_step);
-  c->layout.node_bits = std::max(1, bit_width(c->n_nodes > 0 ? c->n_nodes - 1 : 0));
+  for (const UnionProj& u : ups) max_step = std::max(max_step, u.p->max_step);
+  c->layout.src_bits = std::max(1, bit_width(total_nodes > 0 ? total_nodes - 1 : 0));
+  c->layout.tgt_bits = std::max(1, bit_width(max_nodes > 0 ? max_nodes - 1 : 0));
   c->layout.delay_bits = std::max(1, bit_width(max_step));
   if (c->layout.total_bits() > 64)
     return fail(c, SNC_ERR_UNSUPPORTED, "packed key of %d bits exceeds 64", c->layout.total_bits());
 
   // Table blobs: thresholds (uint32) and their guides (uint16 x 257).
-  const size_t np = c->projs.size();
+  const size_t np = ups.size();
+  std::vector<uint64_t> cnt(np);
   std::vector<uint32_t> thr_blob;
   std::vector<uint16_t> guide_blob;
   std::vector<DevProj> dp(np);
@@ -365,18 +442,20 @@ snc_status snc_finalize(snc_ctx* c) {
   };
   uint64_t n_var_primaries = 0;
   for (size_t i = 0; i < np; ++i) {
-    const Projection& p = c->projs[i];
+    const Projection& p = *ups[i].p;
     DevProj& d = dp[i];
     std::memset(&d, 0, sizeof d);
-    d.s0 = p.src.first;
+    cnt[i] = p.count;
+    d.s0 = p.src.first + ups[i].base;
     d.ns = p.src.n;
-    d.t0 = p.tgt.first;
+    d.t0 = p.tgt.first + ups[i].base;
     d.nt = p.tgt.n;
+    d.t_base = ups[i].base;
     d.rule = static_cast<uint32_t>(p.rule.kind);
     d.autapses = p.rule.allow_autapses ? 1u : 0u;
     d.multapses = p.rule.allow_multapses ? 1u : 0u;
-    d.k0 = static_cast<uint32_t>(c->cfg.seed);
-    d.k1 = static_cast<uint32_t>(c->cfg.seed >> 32) ^ static_cast<uint32_t>(i);
+    d.k0 = static_cast<uint32_t>(ups[i].owner->cfg.seed);
+    d.k1 = static_cast<uint32_t>(ups[i].owner->cfg.seed >> 32) ^ ups[i].local;
     d.k = p.rule.k;
     d.w_normal = (p.syn.weight.kind == SNC_DIST_NORMAL) ? 1u : 0u;
     d.w_mean = static_cast<float>(p.syn.weight.mean);
@@ -406,16 +485,16 @@ snc_status snc_finalize(snc_ctx* c) {
   uint32_t* d_thr = static_cast<uint32_t*>(dev_alloc(c, thr_blob.size() * sizeof(uint32_t)));
   uint16_t* d_guide = static_cast<uint16_t*>(dev_alloc(c, guide_blob.size() * sizeof(uint16_t)));
   DevProj* d_proj = static_cast<DevProj*>(dev_alloc(c, std::max<size_t>(1, np) * sizeof(DevProj)));
-  c->d_err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint64_t)));
-  c->d_n_groups = static_cast<uint64_t*>(dev_alloc(c, sizeof(uint64_t)));
-  if (!d_thr || !d_guide || !d_proj || !c->d_err || !c->d_n_groups)
+  S.d_err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint64_t)));
+  S.d_n_groups = static_cast<uint64_t*>(dev_alloc(c, sizeof(uint64_t)));
+  if (!d_thr || !d_guide || !d_proj || !S.d_err || !S.d_n_groups)
     return fail(c, SNC_ERR_OOM, "device allocation failed (tables)");
   SNC_CUDA(c, cudaMemcpyAsync(d_thr, thr_blob.data(), thr_blob.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
   c->stats.h2d_bytes += thr_blob.size() * sizeof(uint32_t) + guide_blob.size() * sizeof(uint16_t);
   SNC_CUDA(c, cudaMemcpyAsync(d_guide, guide_blob.data(), guide_blob.size() * sizeof(uint16_t),
                               cudaMemcpyHostToDevice, st));
-  SNC_CUDA(c, cudaMemsetAsync(c->d_err, 0, 8 * sizeof(uint64_t), st));
-  SNC_CUDA(c, cudaMemsetAsync(c->d_n_groups, 0, sizeof(uint64_t), st));
+  SNC_CUDA(c, cudaMemsetAsync(S.d_err, 0, 8 * sizeof(uint64_t), st));
+  SNC_CUDA(c, cudaMemsetAsync(S.d_n_groups, 0, sizeof(uint64_t), st));
 
   // Count phase: pairwise Bernoulli per-target counts and offsets.
   uint64_t* d_prim_off = nullptr;
@@ -428,13 +507,13 @@ snc_status snc_finalize(snc_ctx* c) {
     if (!d_prim_off || !d_counts || !d_scan_tmp) return fail(c, SNC_ERR_OOM, "device allocation failed (counts)");
     std::vector<size_t> bern;
     for (size_t i = 0; i < np; ++i)
-      if (c->projs[i].rule.kind == SNC_PAIRWISE_BERNOULLI) bern.push_back(i);
+      if (ups[i].p->rule.kind == SNC_PAIRWISE_BERNOULLI) bern.push_back(i);
     if (bern.size() > 60) {
       // read the totals in groups that fit the pinned staging area
     }
     for (size_t bi = 0; bi < bern.size(); ++bi) {
       const size_t i = bern[bi];
-      const uint32_t nt = c->projs[i].tgt.n;
+      const uint32_t nt = ups[i].p->tgt.n;
       if (nt > 0) {
         bernoulli_count_kernel<<<(nt + 255) / 256, 256, 0, st>>>(d_proj + i, d_thr, d_guide, d_counts + dp[i].prim_off);
         ++c->stats.kernel_launches;
@@ -448,42 +527,42 @@ snc_status snc_finalize(snc_ctx* c) {
       const size_t cnt = std::min<size_t>(64, bern.size() - b0);
       for (size_t j = 0; j < cnt; ++j) {
         const size_t i = bern[b0 + j];
-        SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned + j, d_prim_off + dp[i].prim_off + c->projs[i].tgt.n, sizeof(uint64_t),
+        SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + j, d_prim_off + dp[i].prim_off + ups[i].p->tgt.n, sizeof(uint64_t),
                                     cudaMemcpyDeviceToHost, st));
         c->stats.d2h_bytes += sizeof(uint64_t);
       }
       SNC_CUDA(c, cudaStreamSynchronize(st));
-      for (size_t j = 0; j < cnt; ++j) totals[b0 + j] = c->h_pinned[j];
+      for (size_t j = 0; j < cnt; ++j) totals[b0 + j] = S.h_pinned[j];
     }
-    for (size_t bi = 0; bi < bern.size(); ++bi) c->projs[bern[bi]].count = totals[bi];
+    for (size_t bi = 0; bi < bern.size(); ++bi) cnt[bern[bi]] = totals[bi];
     dev_free(c, d_counts);
     dev_free(c, d_scan_tmp);
   }
-  cudaEventRecord(c->ev[c->n_ev++], st);
+  cudaEventRecord(S.ev[S.n_ev++], st);
 
   // Output offsets and generation chunks.
   uint64_t off = 0;
   std::vector<DevProj> direct;
   uint64_t chunk = 0;
   for (size_t i = 0; i < np; ++i) {
-    const Projection& p = c->projs[i];
+    const Projection& p = *ups[i].p;
     DevProj& d = dp[i];
-    d.count = p.count;
+    d.count = cnt[i];
     d.out_off = off;
-    off += p.count;
-    if (p.count == 0 || is_sampler(p) || is_total_redraw(p)) continue;
+    off += cnt[i];
+    if (cnt[i] == 0 || is_sampler(p) || is_total_redraw(p)) continue;
     if (p.rule.kind == SNC_ALL_TO_ALL) {
       d.chunks_per_row = (p.tgt.n + kChunk - 1) / kChunk;
       d.row_len = p.tgt.n;
       d.n_chunks = static_cast<uint64_t>(p.src.n) * d.chunks_per_row;
     } else {
-      d.n_chunks = (p.count + kChunk - 1) / kChunk;
+      d.n_chunks = (cnt[i] + kChunk - 1) / kChunk;
     }
     d.chunk_begin = chunk;
     chunk += d.n_chunks;
     direct.push_back(d);
   }
-  c->n_syn = off;
+  const uint64_t n_total = off;
   if (np > 0) {
     SNC_CUDA(c, cudaMemcpyAsync(d_proj, dp.data(), np * sizeof(DevProj), cudaMemcpyHostToDevice, st));
     c->stats.h2d_bytes += np * sizeof(DevProj);
@@ -497,7 +576,7 @@ snc_status snc_finalize(snc_ctx* c) {
   }
 
   // Buffers: generated keys/values, the sort's second buffer, outputs.
-  const uint64_t n = c->n_syn;
+  const uint64_t n = n_total;
   c->passes = plan_passes(c->layout.total_bits());
   uint64_t* keys_a = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
   uint32_t* vals_a = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
@@ -526,7 +605,7 @@ snc_status snc_finalize(snc_ctx* c) {
   g.keys = keys_a;
   g.vals = vals_a;
   g.cap = n;
-  g.err = c->d_err;
+  g.err = S.d_err;
   g.hist = hplan;
   const size_t table_smem =
       hist_bytes + static_cast<size_t>(max_delay_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
@@ -542,8 +621,8 @@ snc_status snc_finalize(snc_ctx* c) {
     SNC_CUDA(c, cudaGetLastError());
   }
   for (size_t i = 0; i < np; ++i) {
-    const Projection& p = c->projs[i];
-    if (p.count == 0) continue;
+    const Projection& p = *ups[i].p;
+    if (cnt[i] == 0) continue;
     if (is_sampler(p)) {
       const uint32_t n_other = (p.rule.kind == SNC_FIXED_OUTDEGREE) ? p.tgt.n : p.src.n;
       const uint32_t n_primary = (p.rule.kind == SNC_FIXED_OUTDEGREE) ? p.src.n : p.tgt.n;
@@ -555,7 +634,7 @@ snc_status snc_finalize(snc_ctx* c) {
       s.max_delay_len = dp[i].d_len;
       s.bitmap_words = (n_other + 31u) / 32u;
       s.prim_offsets = d_prim_off ? d_prim_off + dp[i].prim_off : nullptr;
-      s.err = c->d_err;
+      s.err = S.d_err;
       const size_t bitmap_bytes = static_cast<size_t>(s.bitmap_words) * sizeof(uint32_t);
       const size_t tab =
           hist_bytes + static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
@@ -575,10 +654,10 @@ snc_status snc_finalize(snc_ctx* c) {
       SNC_CUDA(c, cudaGetLastError());
     } else if (is_total_redraw(p)) {
       const snc_status r = [&]() -> snc_status {
-        const uint64_t N = p.count;
+        const uint64_t N = cnt[i];
         TotalArgs t{};
         t.proj = d_proj + i;
-        t.err = c->d_err;
+        t.err = S.d_err;
         t.pairs = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
         t.pending = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
         t.next_pending = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
@@ -622,10 +701,10 @@ snc_status snc_finalize(snc_ctx* c) {
         ++c->stats.kernel_launches;
         SNC_CUDA(c, cudaGetLastError());
         for (uint32_t round = 1;; ++round) {
-          SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned, t.n_next, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+          SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned, t.n_next, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
           c->stats.d2h_bytes += sizeof(uint64_t);
           SNC_CUDA(c, cudaStreamSynchronize(st));
-          const uint64_t n_pend = c->h_pinned[0];
+          const uint64_t n_pend = S.h_pinned[0];
           if (n_pend == 0) break;
           if (round > 0xFFFFFFu) return fail(c, SNC_ERR_TIMEOUT, "fixed_total_number: redraw rounds exhausted");
           std::swap(t.pending, t.next_pending);
@@ -662,7 +741,7 @@ snc_status snc_finalize(snc_ctx* c) {
       if (r != SNC_OK) return r;
     }
   }
-  cudaEventRecord(c->ev[c->n_ev++], st);
+  cudaEventRecord(S.ev[S.n_ev++], st);
 
   // Sort by (source, delay, target).  The passes ping-pong between the two
   // buffers; the result lands in (keys_b, vals_b) for an odd number of
@@ -673,8 +752,8 @@ snc_status snc_finalize(snc_ctx* c) {
   uint64_t* keys_oth = odd ? keys_a : keys_b;
   uint32_t* vals_oth = odd ? vals_a : vals_b;
   SNC_CUDA(c, radix_sort_run(keys_a, vals_a, keys_res, vals_res, keys_oth, vals_oth, n, c->passes, sort_scratch,
-                             c->d_err, st, c->ev + c->n_ev, /*hist_ready=*/true));
-  c->n_ev += c->passes.n_passes + 1;
+                             S.d_err, st, S.ev + S.n_ev, /*hist_ready=*/true));
+  S.n_ev += c->passes.n_passes + 1;
   if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
   c->stats.n_passes = c->passes.n_passes;
   c->stats.key_bits = c->layout.total_bits();
@@ -684,35 +763,35 @@ snc_status snc_finalize(snc_ctx* c) {
 
   // Index: unpack target / delay, group starts, row_ptr and p_i.
   const uint64_t n_delay_values = max_step;
-  c->group_cap = std::max<uint64_t>(1, std::min<uint64_t>(n, c->n_nodes * n_delay_values));
-  c->target = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
-  c->delay = static_cast<uint16_t*>(dev_alloc(c, n * sizeof(uint16_t)));
-  c->group_first = static_cast<uint64_t*>(dev_alloc(c, c->group_cap * sizeof(uint64_t)));
-  c->row_ptr = static_cast<uint64_t*>(dev_alloc(c, (c->n_nodes + 1) * sizeof(uint64_t)));
-  c->group_ptr = static_cast<uint64_t*>(dev_alloc(c, (c->n_nodes + 1) * sizeof(uint64_t)));
+  const uint64_t group_cap = std::max<uint64_t>(1, std::min<uint64_t>(n, total_nodes * n_delay_values));
+  uint32_t* u_target = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+  uint16_t* u_delay = static_cast<uint16_t*>(dev_alloc(c, n * sizeof(uint16_t)));
+  uint64_t* u_group_first = static_cast<uint64_t*>(dev_alloc(c, group_cap * sizeof(uint64_t)));
+  uint64_t* u_row_ptr = static_cast<uint64_t*>(dev_alloc(c, (total_nodes + 1) * sizeof(uint64_t)));
+  uint64_t* u_group_ptr = static_cast<uint64_t*>(dev_alloc(c, (total_nodes + 1) * sizeof(uint64_t)));
   const uint64_t iblocks = (n + kIndexTile - 1) / kIndexTile;
   uint32_t* starts = static_cast<uint32_t*>(dev_alloc(c, (iblocks * (kIndexTile / 32) + 1) * sizeof(uint32_t)));
   uint32_t* bcounts = static_cast<uint32_t*>(dev_alloc(c, (iblocks + 1) * sizeof(uint32_t)));
   uint64_t* boffsets = static_cast<uint64_t*>(dev_alloc(c, (iblocks + 1) * sizeof(uint64_t)));
   uint64_t* iscan = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(iblocks) + 1) * sizeof(uint64_t)));
-  if (!c->target || !c->delay || !c->group_first || !c->row_ptr || !c->group_ptr || !starts || !bcounts || !boffsets ||
+  if (!u_target || !u_delay || !u_group_first || !u_row_ptr || !u_group_ptr || !starts || !bcounts || !boffsets ||
       !iscan)
     return fail(c, SNC_ERR_OOM, "device allocation failed (index)");
   if (n > 0) {
     IndexArgs ia{};
     ia.keys = keys_res;
     ia.n = n;
-    ia.node_bits = c->layout.node_bits;
+    ia.tgt_bits = c->layout.tgt_bits;
     ia.delay_bits = c->layout.delay_bits;
-    ia.target = c->target;
-    ia.delay = c->delay;
+    ia.target = u_target;
+    ia.delay = u_delay;
     ia.starts = starts;
     ia.block_counts = bcounts;
     ia.block_offsets = boffsets;
-    ia.group_first = c->group_first;
-    ia.group_cap = c->group_cap;
-    ia.n_groups = c->d_n_groups;
-    ia.err = c->d_err;
+    ia.group_first = u_group_first;
+    ia.group_cap = group_cap;
+    ia.n_groups = S.d_n_groups;
+    ia.err = S.d_err;
     const unsigned igrid = static_cast<unsigned>(std::min<uint64_t>(iblocks, static_cast<uint64_t>(c->sms) * 8));
     index_unpack_kernel<<<igrid, kIndexThreads, 0, st>>>(ia);
     ++c->stats.kernel_launches;
@@ -726,19 +805,73 @@ snc_status snc_finalize(snc_ctx* c) {
   NodeIndexArgs na{};
   na.keys = keys_res;
   na.n = n;
-  na.n_nodes = c->n_nodes;
-  na.node_bits = c->layout.node_bits;
+  na.n_nodes = total_nodes;
+  na.tgt_bits = c->layout.tgt_bits;
   na.delay_bits = c->layout.delay_bits;
-  na.group_first = c->group_first;
-  na.group_cap = c->group_cap;
-  na.n_groups = c->d_n_groups;
-  na.row_ptr = c->row_ptr;
-  na.group_ptr = c->group_ptr;
-  node_index_kernel<<<static_cast<unsigned>((c->n_nodes + 1 + 255) / 256), 256, 0, st>>>(na);
+  na.group_first = u_group_first;
+  na.group_cap = group_cap;
+  na.n_groups = S.d_n_groups;
+  na.row_ptr = u_row_ptr;
+  na.group_ptr = u_group_ptr;
+  node_index_kernel<<<static_cast<unsigned>((total_nodes + 1 + 255) / 256), 256, 0, st>>>(na);
   ++c->stats.kernel_launches;
   SNC_CUDA(c, cudaGetLastError());
-  cudaEventRecord(c->ev[c->n_ev++], st);
-  c->weight = reinterpret_cast<float*>(vals_res);
+  // Batches: each member's CSR and group offsets relative to its own first
+  // connection and group; its first connection and group are read back at
+  // synchronize.
+  uint64_t* local_rows = nullptr;
+  uint64_t* local_groups = nullptr;
+  std::vector<uint64_t> local_base(n_members, 0);
+  if (n_members > 1) {
+    for (int m = 1; m < n_members; ++m) local_base[m] = local_base[m - 1] + members[m - 1]->n_nodes + 1;
+    const uint64_t n_local = total_nodes + static_cast<uint64_t>(n_members);
+    local_rows = static_cast<uint64_t*>(dev_alloc(c, n_local * sizeof(uint64_t)));
+    local_groups = static_cast<uint64_t*>(dev_alloc(c, n_local * sizeof(uint64_t)));
+    uint64_t* d_meta = static_cast<uint64_t*>(dev_alloc(c, (2 * static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)));
+    S.d_bases = static_cast<uint64_t*>(dev_alloc(c, 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)));
+    if (!local_rows || !local_groups || !d_meta || !S.d_bases)
+      return fail(c, SNC_ERR_OOM, "device allocation failed (batch views)");
+    std::vector<uint64_t> meta(node_base.begin(), node_base.end());
+    meta.insert(meta.end(), local_base.begin(), local_base.end());
+    SNC_CUDA(c, cudaMemcpyAsync(d_meta, meta.data(), meta.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    c->stats.h2d_bytes += meta.size() * sizeof(uint64_t);
+    RebaseArgs rb{};
+    rb.row_ptr = u_row_ptr;
+    rb.group_ptr = u_group_ptr;
+    rb.node_base = d_meta;
+    rb.local_base = d_meta + n_members + 1;
+    rb.n_nets = n_members;
+    rb.total_nodes = total_nodes;
+    rb.row_local = local_rows;
+    rb.group_local = local_groups;
+    rb.group_first = u_group_first;
+    rb.n_groups_cap = group_cap;
+    rb.n_groups = S.d_n_groups;
+    // First connection / group of every member (and the totals) for the views.
+    for (int m = 0; m <= n_members; ++m) {
+      SNC_CUDA(c, cudaMemcpyAsync(S.d_bases + m, u_row_ptr + node_base[m], sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                                  st));
+      SNC_CUDA(c, cudaMemcpyAsync(S.d_bases + n_members + 1 + m, u_group_ptr + node_base[m], sizeof(uint64_t),
+                                  cudaMemcpyDeviceToDevice, st));
+    }
+    rebase_nodes_kernel<<<static_cast<unsigned>((n_local + 255) / 256), 256, 0, st>>>(rb);
+    ++c->stats.kernel_launches;
+    rebase_groups_kernel<<<static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>((group_cap + 255) / 256,
+                                                                                           static_cast<uint64_t>(c->sms) * 8))),
+                           256, 0, st>>>(rb);
+    ++c->stats.kernel_launches;
+    SNC_CUDA(c, cudaGetLastError());
+    if (!S.h_bases && cudaMallocHost(&S.h_bases, 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)) != cudaSuccess) {
+      cudaGetLastError();
+      S.h_bases = nullptr;
+      return fail(c, SNC_ERR_OOM, "pinned allocation failed (batch views)");
+    }
+    SNC_CUDA(c, cudaMemcpyAsync(S.h_bases, S.d_bases, 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t),
+                                cudaMemcpyDeviceToHost, st));
+    c->stats.d2h_bytes += 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t);
+    dev_free(c, d_meta);
+  }
+  cudaEventRecord(S.ev[S.n_ev++], st);
   dev_free(c, starts);
   dev_free(c, bcounts);
   dev_free(c, boffsets);
@@ -746,33 +879,100 @@ snc_status snc_finalize(snc_ctx* c) {
   dev_free(c, keys_res);
   dev_free(c, d_direct);
   dev_free(c, d_prim_off);
-  c->finalized = true;
-  c->synced = false;
+
+  S.n_members = n_members;
+  S.n_total = n_total;
+  S.synced = false;
+  for (int m = 0; m < n_members; ++m) {
+    snc_ctx* x = members[m];
+    if (m > 0) x->store = c->store;
+    x->member = m;
+    x->node_base = node_base[m];
+    x->layout = c->layout;
+    x->passes = c->passes;
+    x->group_cap = group_cap;
+    x->target_all = u_target;
+    x->delay_all = u_delay;
+    x->weight_all = reinterpret_cast<float*>(vals_res);
+    x->group_first_all = u_group_first;
+    x->row_ptr = n_members > 1 ? local_rows + local_base[m] : u_row_ptr;
+    x->group_ptr = n_members > 1 ? local_groups + local_base[m] : u_group_ptr;
+    x->view_ready = false;
+    x->finalized = true;
+    if (m > 0) x->stats = c->stats;
+  }
   return SNC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+snc_status snc_finalize(snc_ctx* c) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (c->finalized) return fail(c, SNC_ERR_STATE, "finalize called twice");
+  return finalize_build(&c, 1);
+}
+
+snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n) {
+  if (!ctxs || n <= 0) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: no contexts");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: null context");
+    if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
+    if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
+  }
+  const snc_status st = finalize_build(ctxs, n);
+  if (st != SNC_OK)
+    for (int i = 1; i < n; ++i) ctxs[i]->err = ctxs[0]->err;
+  return st;
 }
 
 snc_status snc_synchronize(snc_ctx* c) {
   if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
   SNC_CUDA(c, cudaSetDevice(c->device));
-  SNC_CUDA(c, cudaStreamSynchronize(c->stream));
+  Storage& S = *c->store;
+  SNC_CUDA(c, cudaStreamSynchronize(S.stream));
   if (!c->finalized) return SNC_OK;
-  if (!c->synced) {
-    SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned + 4, c->d_err, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
-    SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
-    SNC_CUDA(c, cudaMemcpyAsync(c->h_pinned + 1, c->d_n_groups, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
-    c->stats.d2h_bytes += sizeof(uint32_t) + sizeof(uint64_t);
-    SNC_CUDA(c, cudaStreamSynchronize(c->stream));
-    const uint32_t err = static_cast<uint32_t>(c->h_pinned[0] & 0xFFFFFFFFu);
-    c->n_groups = c->h_pinned[1];
-    c->synced = true;
-    if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
-    if (err & kErrSamplerBound) return fail(c, SNC_ERR_TIMEOUT, "a sampler exceeded its attempt bound");
-    if (err & kErrBounds) {
-      const uint32_t* w = reinterpret_cast<const uint32_t*>(c->h_pinned + 4);
-      return fail(c, SNC_ERR_CUDA, "a device index check failed (site %u, index %llu, limit %llu)", w[2],
-                  static_cast<unsigned long long>(w[4] | (static_cast<uint64_t>(w[5]) << 32)),
-                  static_cast<unsigned long long>(w[6] | (static_cast<uint64_t>(w[7]) << 32)));
+  if (!S.synced) {
+    SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + 4, S.d_err, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, S.stream));
+    SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + 1, S.d_n_groups, sizeof(uint64_t), cudaMemcpyDeviceToHost, S.stream));
+    c->stats.d2h_bytes += 5 * sizeof(uint64_t);
+    SNC_CUDA(c, cudaStreamSynchronize(S.stream));
+    S.err_bits = static_cast<uint32_t>(S.h_pinned[4] & 0xFFFFFFFFu);
+    S.n_groups = S.h_pinned[1];
+    S.synced = true;
+  }
+  if (!c->view_ready) {
+    if (S.n_members == 1) {
+      c->n_syn = S.n_total;
+      c->n_groups = S.n_groups;
+      c->target = c->target_all;
+      c->delay = c->delay_all;
+      c->weight = c->weight_all;
+      c->group_first = c->group_first_all;
+    } else {
+      const int M = S.n_members, m = c->member;
+      const uint64_t syn0 = S.h_bases[m], syn1 = S.h_bases[m + 1];
+      const uint64_t g0 = S.h_bases[M + 1 + m], g1 = S.h_bases[M + 1 + m + 1];
+      c->n_syn = syn1 - syn0;
+      c->n_groups = g1 - g0;
+      c->target = c->target_all + syn0;
+      c->delay = c->delay_all + syn0;
+      c->weight = c->weight_all + syn0;
+      c->group_first = c->group_first_all + g0;
     }
+    c->view_ready = true;
+  }
+  const uint32_t err = S.err_bits;
+  if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
+  if (err & kErrSamplerBound) return fail(c, SNC_ERR_TIMEOUT, "a sampler exceeded its attempt bound");
+  if (err & kErrBounds) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(S.h_pinned + 4);
+    return fail(c, SNC_ERR_CUDA, "a device index check failed (site %u, index %llu, limit %llu)", w[2],
+                static_cast<unsigned long long>(w[4] | (static_cast<uint64_t>(w[5]) << 32)),
+                static_cast<unsigned long long>(w[6] | (static_cast<uint64_t>(w[7]) << 32)));
   }
   return SNC_OK;
 }
@@ -802,7 +1002,7 @@ snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16
   if (s != SNC_OK) return s;
   if (cap < c->n_syn) return fail(c, SNC_ERR_INVALID_ARG, "capacity below the number of connections");
   const uint64_t n = c->n_syn;
-  cudaStream_t st = c->stream;
+  cudaStream_t st = c->store->stream;
   if (src && n > 0) {
     uint32_t* d_src = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
     if (!d_src) return fail(c, SNC_ERR_OOM, "device allocation failed (source expansion)");
@@ -826,11 +1026,12 @@ snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16
 snc_status snc_stage_times(snc_ctx* c, float* ms, int max_stages, int* n_stages, int* n_passes) {
   if (!c || !ms || max_stages < 0) return fail(c, SNC_ERR_INVALID_ARG, "null argument");
   if (!c->finalized) return fail(c, SNC_ERR_STATE, "no finalize has run");
-  SNC_CUDA(c, cudaStreamSynchronize(c->stream));
+  Storage& S = *c->store;
+  SNC_CUDA(c, cudaStreamSynchronize(S.stream));
   int k = 0;
-  for (int i = 1; i < c->n_ev && k < max_stages; ++i, ++k) {
+  for (int i = 1; i < S.n_ev && k < max_stages; ++i, ++k) {
     float t = 0.f;
-    SNC_CUDA(c, cudaEventElapsedTime(&t, c->ev[i - 1], c->ev[i]));
+    SNC_CUDA(c, cudaEventElapsedTime(&t, S.ev[i - 1], S.ev[i]));
     ms[k] = t;
   }
   if (n_stages) *n_stages = k;

@@ -88,7 +88,7 @@ class snc_conn_view(ctypes.Structure):
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
-           "snc_set_tuning", "snc_get_tuning", "snc_last_error")
+           "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_last_error")
 
 _LIB = None
 
@@ -110,6 +110,7 @@ def load(build: bool = True):
         "snc_connect": ([P, snc_range, snc_range, ctypes.POINTER(snc_conn_rule),
                          ctypes.POINTER(snc_syn_spec), ctypes.POINTER(U32)], I32),
         "snc_finalize": ([P], I32),
+        "snc_batch_finalize": ([ctypes.POINTER(P), I32], I32),
         "snc_synchronize": ([P], I32),
         "snc_get_connections": ([P, ctypes.POINTER(snc_conn_view)], I32),
         "snc_copy_connections": ([P, P, P, P, P, U64], I32),
@@ -164,6 +165,11 @@ def snc_connect(ctx, src, tgt, rule, syn):
 
 def snc_finalize(ctx):
     _check(load().snc_finalize(ctx), ctx)
+
+
+def snc_batch_finalize(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    _check(load().snc_batch_finalize(arr, len(ctxs)), ctxs[0] if ctxs else None)
 
 
 def snc_synchronize(ctx):
@@ -298,6 +304,19 @@ class Network:
     def finalize(self):
         snc_finalize(self.ctx)
         return self
+
+    @staticmethod
+    def batch(specs, device=0, stream=None, allocator="torch"):
+        """Build several networks with one launch per stage (snc_batch_finalize).
+
+        Returns one Network per spec; each holds a reference to the first
+        (whose allocator serves the shared result memory)."""
+        nets = [Network(sp, device=device, stream=stream, allocator=allocator) for sp in specs]
+        if nets:
+            snc_batch_finalize([n.ctx for n in nets])
+            for n in nets[1:]:
+                n._leader = nets[0]
+        return nets
 
     def synchronize(self):
         snc_synchronize(self.ctx)

@@ -186,7 +186,8 @@ def batched_sweep(count: int = 64, seed: int = 1234, scale: float = 1.0) -> List
         if rule == "fixed_indegree":
             spec = two_population(n, rule, k=k, autapses=mult, multapses=mult, seed=1234 + i)
         elif rule == "fixed_total_number":
-            spec = two_population(n, rule, k=k * n, autapses=mult, multapses=mult, seed=1234 + i)
+            # at most a quarter of the pairs, so that the no-multapse redraws stay short
+            spec = two_population(n, rule, k=min(k, n // 4) * n, autapses=mult, multapses=mult, seed=1234 + i)
         else:
             spec = two_population(n, rule, p=p, autapses=mult, multapses=True, seed=1234 + i)
         spec.name = f"batch{i}_{rule}_2x{n}"

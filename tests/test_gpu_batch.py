@@ -1,0 +1,69 @@
+"""Batched calibration (snc_batch_finalize): every member of a batch gets
+exactly the network a single build gives it, and the oracle's network."""
+import numpy as np
+import pytest
+
+from gpu_helpers import assert_network_equal
+from paper_2306_09855_gb300 import workloads as W
+from paper_2306_09855_gb300.workloads import Dist, NetworkSpec, Projection
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_09855_gb300 import snc as mod
+    mod.load()
+    return mod
+
+
+def _mixed_specs():
+    specs = [
+        W.two_population(700, "fixed_indegree", k=31, autapses=False, seed=1),
+        W.two_population(333, "pairwise_bernoulli", p=0.05, autapses=False, seed=2),
+        W.two_population(500, "fixed_total_number", k=40_000, autapses=False, multapses=False, seed=3),
+        W.two_population(64, "fixed_indegree", k=40, autapses=False, multapses=False, seed=4),
+        W.two_population(90, "all_to_all", autapses=False, seed=5),
+        NetworkSpec(seed=6, dt=0.1, populations=[7], projections=[]),
+        W.two_population(1200, "fixed_outdegree", k=17, seed=7),
+        W.two_population(40, "one_to_one", autapses=False, seed=8),
+    ]
+    specs += W.batched_sweep(count=6, scale=0.05)
+    return specs
+
+
+def test_batch_members_equal_single_builds_and_oracle(snc, oracle_mod):
+    specs = _mixed_specs()
+    nets = snc.Network.batch(specs)
+    for i, (spec, net) in enumerate(zip(specs, nets)):
+        got = net.to_host()
+        single = snc.Network(spec).finalize()
+        alone = single.to_host()
+        single.close()
+        for f in ("src", "tgt", "delay", "weight", "row_ptr", "group_ptr", "group_first"):
+            np.testing.assert_array_equal(got[f], alone[f], err_msg=f"member {i} {f}")
+        assert got["n_groups"] == alone["n_groups"]
+        assert_network_equal(got, oracle_mod.build(spec), f"member {i}")
+
+
+def test_batch_views_outlive_the_first_member(snc, oracle_mod):
+    specs = [W.two_population(300, "fixed_indegree", k=20, seed=s) for s in (10, 11, 12)]
+    nets = snc.Network.batch(specs)
+    nets[0].close()
+    for spec, net in zip(specs[1:], nets[1:]):
+        assert_network_equal(net.to_host(), oracle_mod.build(spec), "after leader closed")
+
+
+def test_batch_argument_errors(snc):
+    a = snc.Network(W.two_population(50, "fixed_indegree", k=5))
+    with pytest.raises(snc.SncError) as e:
+        snc.snc_batch_finalize([a.ctx, a.ctx])
+    assert e.value.name == "INVALID_ARG"
+    a.finalize()
+    b = snc.Network(W.two_population(50, "fixed_indegree", k=5))
+    with pytest.raises(snc.SncError) as e:
+        snc.snc_batch_finalize([b.ctx, a.ctx])
+    assert e.value.name == "STATE"
