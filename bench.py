@@ -38,7 +38,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="snc", choices=["snc", "reference"])
     ap.add_argument("--workload", default="rule_sweep",
-                    choices=["rule_sweep", "microcircuit", "plain", "small", "profile", "profile_total"])
+                    choices=["rule_sweep", "microcircuit", "plain", "small", "profile", "profile_total",
+                             "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sort-digit-bits", type=int, default=None, help="tuning: widest radix digit")
     ap.add_argument("--sort-group-tiles", type=int, default=None, help="tuning: tiles per look-back unit")
@@ -65,6 +66,12 @@ def workload_specs(name):
         return [W.two_population(100_000, "fixed_indegree", k=100)], {
             "workload": "profiling case: 2 x 100,000 nodes, fixed_indegree K=100 (4e7 connections, "
                         "same 43-bit key as the rule sweep)", "seed": 1234}
+    if name == "batched":
+        return W.batched_sweep(64), {
+            "workload": "batched: 64 independent two-population networks, N per population log-uniform "
+                        "2,000-50,000, fixed_indegree K 50-2,000 / fixed_total_number / pairwise_bernoulli "
+                        "p 0.005-0.05, per-instance seeds, built by one snc_batch_finalize",
+            "seed": 1234, "dt_ms": 0.1}
     if name == "profile_total":
         return [W.two_population(30_000, "fixed_total_number", k=20_000_000, autapses=False, multapses=False)], {
             "workload": "profiling case: 2 x 30,000 nodes, fixed_total_number 2e7 per call without autapses "
@@ -210,8 +217,24 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    batched = args.workload == "batched"
+    tune_info = None
+    if batched:
+        from paper_2306_09855_gb300 import autotune
+        tune_info = autotune.tune(specs, batched=True)
+
     def one_step(record):
         n_syn = 0
+        if batched:
+            nets = snc.Network.batch(specs, device=local, stream=stream)
+            for net in nets:
+                n_syn += int(net.view().n_syn)
+            if record is not None:
+                times, npass = nets[0].stage_times()
+                record.append((n_syn, times, npass, nets[0].stats()))
+            for net in reversed(nets):
+                net.close()
+            return n_syn
         for spec in specs:
             net = snc.Network(spec, device=local, stream=stream)
             net.finalize()
@@ -270,6 +293,7 @@ def main():
         names = ["count", "generate", "histogram"] + ["pass%d" % k for k in range(npass)] + ["index"]
         for nm, t in zip(names, times):
             stage_sum[nm] = stage_sum.get(nm, 0.0) + t
+    final_tuning = snc.snc_get_tuning()
     peak, peak_src = measured_peaks()
     achieved = (pass_bytes / (pass_ms / 1e3)) / 1e9 if pass_ms > 0 else 0.0
     traffic = None
@@ -281,16 +305,31 @@ def main():
     t0 = time.perf_counter()
     h2d = d2h = 0
     n_e2e = 0
-    for spec in specs:
-        net = snc.Network(spec, device=local, stream=stream)
-        net.finalize()
-        v = net.view()
-        n_e2e += int(v.n_syn)
-        st = net.stats()
-        h2d += int(st.h2d_bytes)
-        d2h += int(st.d2h_bytes)
-        net.close()
+    if batched:
+        nets = snc.Network.batch(specs, device=local, stream=stream)
+        for net in nets:
+            n_e2e += int(net.view().n_syn)
+        st = nets[0].stats()
+        h2d, d2h = int(st.h2d_bytes), int(st.d2h_bytes)
+        for net in reversed(nets):
+            net.close()
+    else:
+        for spec in specs:
+            net = snc.Network(spec, device=local, stream=stream)
+            net.finalize()
+            v = net.view()
+            n_e2e += int(v.n_syn)
+            st = net.stats()
+            h2d += int(st.h2d_bytes)
+            d2h += int(st.d2h_bytes)
+            net.close()
     e2e_s = time.perf_counter() - t0
+    sequential = None
+    if batched:
+        from paper_2306_09855_gb300 import autotune
+        seq_ms = autotune.time_build(specs, batched=False, repeats=1)
+        sequential = {"value": n_e2e / (seq_ms / 1e3), "unit": "connections/s", "ms": seq_ms,
+                      "note": "the same 64 networks built one after another with snc_finalize"}
 
     if rank != 0:
         return
@@ -300,9 +339,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32+f32", "data": "synthetic",
         "config": dict(config, connections_per_step=n_total // max(1, args.steps),
-                       tuning={"sort_digit_bits": tuning.sort_digit_bits,
-                               "sort_group_tiles": tuning.sort_group_tiles,
-                               "gen_blocks_per_sm": tuning.gen_blocks_per_sm},
+                       tuning={"sort_digit_bits": final_tuning.sort_digit_bits,
+                               "sort_group_tiles": final_tuning.sort_group_tiles,
+                               "gen_blocks_per_sm": final_tuning.gen_blocks_per_sm},
                        l2="inputs larger than L2 (>= 4.8 GB of keys+values per network)",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": {"bound": "hbm", "kernel": "onesweep radix pass", "achieved": achieved, "peak": peak,
@@ -317,6 +356,9 @@ def main():
                 "d2h_bytes_per_step": d2h, "note": "public API, host wall clock, network left on the device"},
         "clocks": clk,
     }
+    if batched:
+        line["sequential_builds"] = sequential
+        line["autotune"] = {"tuning": tune_info["tuning"], "cached": tune_info["cached"], "key": tune_info["key"]}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -223,16 +223,35 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
 // from word 0 of its COUNT draw (Sec. 4 names the rule; reading in the
 // design notes).
 // ---------------------------------------------------------------------------
-__global__ void bernoulli_count_kernel(const DevProj* proj, const uint32_t* thr_blob,
-                                       const uint16_t* guide_blob, uint32_t* counts) {
-  const DevProj& P = *proj;
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= P.nt) return;
-  const uint32_t node = P.t0 + b;
-  const int skip = (!P.autapses && node >= P.s0 && node - P.s0 < P.ns) ? 1 : 0;
-  const Words W = draw(P.k0, P.k1, kTagCount, 0, b, 0);
-  const uint32_t i = table_lookup(thr_blob + P.b_off[skip], guide_blob + P.b_goff[skip], P.b_len[skip], W.x);
-  counts[b] = P.b_base[skip] + i;
+// Index j of the segment holding element g: prefix[j] <= g < prefix[j + 1].
+__device__ __forceinline__ int find_segment(const uint64_t* prefix, int n, uint64_t g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void bernoulli_count_kernel(const DevProj* projs, const uint32_t* list, const uint64_t* prefix, int n_list,
+                                       const uint32_t* thr_blob, const uint16_t* guide_blob, uint32_t* counts) {
+  const uint64_t total = prefix[n_list];
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int j = find_segment(prefix, n_list, g);
+    const DevProj& P = projs[list[j]];
+    const uint32_t b = static_cast<uint32_t>(g - prefix[j]);
+    const uint32_t node = P.t0 + b;
+    const int skip = (!P.autapses && node >= P.s0 && node - P.s0 < P.ns) ? 1 : 0;
+    const Words W = draw(P.k0, P.k1, kTagCount, 0, b, 0);
+    const uint32_t i = table_lookup(thr_blob + P.b_off[skip], guide_blob + P.b_goff[skip], P.b_len[skip], W.x);
+    counts[g] = P.b_base[skip] + i;
+  }
+}
+
+__global__ void segment_totals_kernel(const uint64_t* offsets, const uint64_t* prefix, int n_list, uint64_t* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n_list) out[j] = offsets[prefix[j + 1]] - offsets[prefix[j]];
 }
 
 // ---------------------------------------------------------------------------
@@ -247,38 +266,47 @@ __global__ void bernoulli_count_kernel(const DevProj* proj, const uint32_t* thr_
 // ---------------------------------------------------------------------------
 __global__ void sampler_kernel(SamplerArgs a) {
   extern __shared__ uint32_t smem_all[];
-  const DevProj& P = *a.proj;
   const uint32_t lane = lane_id();
   const uint32_t warp_in_block = threadIdx.x >> 5;
   const uint32_t warps_per_block = blockDim.x >> 5;
   const BlockHist bh = block_hist_begin(a.gen, smem_all);
-  uint32_t* bitmap_all = smem_all + hist_words(a.gen);
-  uint32_t* bitmap = bitmap_all + static_cast<size_t>(warp_in_block) * a.bitmap_words;
-  // Delay table (shared by the block).
-  uint32_t* dthr = bitmap_all + static_cast<size_t>(warps_per_block) * a.bitmap_words;
-  uint16_t* dguide = reinterpret_cast<uint16_t*>(dthr + a.max_delay_len);
-  SmemTables tabs{dthr, dguide};
-  load_delay_table(P, a.thr_blob, a.guide_blob, tabs);
   __syncthreads();
+  uint32_t* warp_area =
+      smem_all + hist_words(a.gen) + static_cast<size_t>(warp_in_block) * (a.bitmap_words + a.table_words);
+  uint32_t* bitmap = warp_area;
+  SmemTables tabs{warp_area + a.bitmap_words, reinterpret_cast<uint16_t*>(warp_area + a.bitmap_words + a.max_delay_len)};
+  const uint64_t total = a.prim_prefix[a.n_list];
+  const uint64_t gw = static_cast<uint64_t>(blockIdx.x) * warps_per_block + warp_in_block;
+  const uint64_t n_warps = static_cast<uint64_t>(gridDim.x) * warps_per_block;
+  int cur = -1;
 
-  const bool indeg = P.rule != SNC_FIXED_OUTDEGREE;  // indegree and Bernoulli pick sources
-  const uint32_t n_primary = indeg ? P.nt : P.ns;
-  const uint32_t n_other = indeg ? P.ns : P.nt;
-  const uint32_t first_primary = indeg ? P.t0 : P.s0;
-  const uint32_t first_other = indeg ? P.s0 : P.t0;
-  const uint32_t gw = blockIdx.x * warps_per_block + warp_in_block;
-  const uint32_t n_warps = gridDim.x * warps_per_block;
-  const uint32_t words = (n_other + 31u) >> 5;
-
-  for (uint32_t b = gw; b < n_primary; b += n_warps) {
+  for (uint64_t gp = gw; gp < total; gp += n_warps) {
+    const int j = find_segment(a.prim_prefix, a.n_list, gp);
+    const DevProj& P = a.projs[a.list[j]];
+    if (j != cur) {
+      // This warp's copy of the projection's delay table.
+      if (P.d_table) {
+        for (uint32_t i = lane; i < P.d_len; i += 32) tabs.thr[i] = a.thr_blob[P.d_off + i];
+        for (uint32_t i = lane; i < kDelayGuide; i += 32) tabs.guide[i] = a.guide_blob[P.d_goff + i];
+      }
+      __syncwarp();
+      cur = j;
+    }
+    const uint32_t b = static_cast<uint32_t>(gp - a.prim_prefix[j]);
+    const bool indeg = P.rule != SNC_FIXED_OUTDEGREE;  // indegree and Bernoulli pick sources
+    const uint32_t n_other = indeg ? P.ns : P.nt;
+    const uint32_t first_primary = indeg ? P.t0 : P.s0;
+    const uint32_t first_other = indeg ? P.s0 : P.t0;
+    const uint32_t words = (n_other + 31u) >> 5;
+  {
     const uint32_t node = first_primary + b;
     const bool skip = !P.autapses && node >= first_other && node - first_other < n_other;
     const uint32_t skip_local = skip ? node - first_other : 0u;
     const uint32_t cand = n_other - (skip ? 1u : 0u);
     uint64_t want, out;
     if (P.rule == SNC_PAIRWISE_BERNOULLI) {
-      out = P.out_off + a.prim_offsets[b];
-      want = a.prim_offsets[b + 1] - a.prim_offsets[b];
+      out = P.out_off + (a.prim_offsets[P.prim_off + b] - a.prim_offsets[P.prim_off]);
+      want = a.prim_offsets[P.prim_off + b + 1] - a.prim_offsets[P.prim_off + b];
     } else {
       want = P.k;
       out = P.out_off + static_cast<uint64_t>(b) * P.k;
@@ -372,6 +400,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
     }
     __syncwarp();
   }
+  }
   block_hist_end(a.gen, bh);
 }
 
@@ -381,9 +410,19 @@ __global__ void sampler_kernel(SamplerArgs a) {
 // pair is not allowed redraws in round r >= 1 from its DEDUP draw.  With
 // multapses forbidden a pair may be held by one slot only: pairs accepted in
 // earlier rounds block it, and among the slots drawing it in the same round
-// the lowest wins.  Claims go through a hash table: a claim is 2^63 | slot
-// (atomicMin keeps the lowest), an accepted pair stores its slot (< 2^63), so
-// an accepted entry is never overwritten by a later claim.
+// the lowest wins.  All redraw projections of a build are handled together
+// (slots concatenated, one hash table region per projection), so every round
+// costs one launch pair and one read-back however many projections redraw.
+//
+// Table entries.  Packed (when it fits in 63 bits): one word
+//   (pair_local << (slot_bits + 1)) | (claimed_this_round << slot_bits) | slot.
+// Otherwise keys (global pair) and values (claim bit 63 | slot) in two
+// arrays.  Either way an accepted entry is smaller than any claim on the same
+// pair, so atomicMin never replaces it, and among claims it keeps the lowest
+// slot.  In round 0 a claimant that meets its pair marks the higher of the
+// two slots lost; every claimant but the lowest is marked by someone, so no
+// second pass over the table is needed and round-0 entries are written in
+// the accepted form.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr uint64_t kEmpty = ~0ull;
@@ -398,196 +437,205 @@ __device__ __forceinline__ uint64_t pair_hash(uint64_t key) {
   return key;
 }
 
-// Slot of `pair` in the table (inserted if absent), or ~0 if the probe bound
-// was exceeded.
-__device__ uint64_t table_slot(const TotalArgs& a, uint64_t pair, bool insert) {
-  uint64_t h = pair_hash(pair) & a.table_mask;
-  for (uint64_t probe = 0; probe <= a.table_mask; ++probe) {
-    uint64_t k = a.table_keys[h];
-    if (k == pair) return h;
-    if (k == kEmpty) {
-      if (!insert) return kEmpty;
-      k = atomicCAS(reinterpret_cast<unsigned long long*>(&a.table_keys[h]), kEmpty, pair);
-      if (k == kEmpty || k == pair) return h;
+__device__ __forceinline__ bool allowed_pair(const DevProj& P, uint32_t s, uint32_t t) {
+  return P.autapses || s != t;
+}
+
+// The slot g of the concatenated list: its projection and local slot.
+struct SlotRef {
+  const RedrawProj* r;
+  const DevProj* P;
+  uint64_t i;
+};
+
+__device__ __forceinline__ SlotRef slot_ref(const RedrawArgs& a, uint64_t g) {
+  int lo = 0, hi = a.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.rp[mid].slot_base <= g) lo = mid; else hi = mid - 1;
+  }
+  const RedrawProj* r = &a.rp[lo];
+  return SlotRef{r, &a.projs[r->proj], g - r->slot_base};
+}
+
+// Claim of `slot` on the pair (s, t) (global ids) in projection r's table.
+// round0: accepted form plus lost marks; otherwise a claim for resolve().
+__device__ void claim(const RedrawArgs& a, const RedrawProj& r, const DevProj& P, uint32_t s, uint32_t t,
+                      uint64_t slot, uint64_t gslot, bool round0) {
+  const uint64_t slot_mask = (1ull << r.slot_bits) - 1;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.table_keys + r.table_off);
+  if (r.packed) {
+    const int sh = r.slot_bits + 1;
+    const uint64_t pair = (static_cast<uint64_t>(s - P.s0) << r.t_bits) | (t - P.t0);
+    const uint64_t e = (pair << sh) | (round0 ? 0ull : (1ull << r.slot_bits)) | slot;
+    uint64_t h = pair_hash(pair) & r.table_mask;
+    for (uint64_t probe = 0; probe <= r.table_mask; ++probe) {
+      const uint64_t old = atomicCAS(keys + h, kEmpty, e);
+      if (old == kEmpty) return;
+      if ((old >> sh) == pair) {
+        const uint64_t prev = atomicMin(keys + h, e);
+        if (round0) {
+          if (prev < e) a.lost[gslot] = 1;
+          else a.lost[gslot - slot + (prev & slot_mask)] = 1;
+        }
+        return;
+      }
+      h = (h + 1) & r.table_mask;
     }
-    h = (h + 1) & a.table_mask;
+  } else {
+    unsigned long long* vals = reinterpret_cast<unsigned long long*>(a.table_vals + r.table_off);
+    const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
+    const uint64_t v = (round0 ? 0ull : kClaim) | slot;
+    uint64_t h = pair_hash(pair) & r.table_mask;
+    for (uint64_t probe = 0; probe <= r.table_mask; ++probe) {
+      uint64_t k = keys[h];
+      if (k == kEmpty) k = atomicCAS(keys + h, kEmpty, pair);
+      if (k == kEmpty || k == pair) {
+        const uint64_t prev = atomicMin(vals + h, v);
+        if (round0 && prev != kEmpty) {
+          if (prev < v) a.lost[gslot] = 1;
+          else a.lost[gslot - slot + (prev & ~kClaim)] = 1;
+        }
+        return;
+      }
+      h = (h + 1) & r.table_mask;
+    }
   }
   atomicOr(a.err, kErrBounds);
-  return kEmpty;
 }
 
-// Packed form: key bits = pair_local, so one 64-bit atomic both matches the
-// pair and keeps the lowest claiming slot; an accepted entry (claim bit clear)
-// is smaller than every claim and therefore never replaced.
-__device__ __forceinline__ uint64_t packed_pair(const TotalArgs& a, const DevProj& P, uint32_t s, uint32_t t) {
-  return (static_cast<uint64_t>(s - P.s0) << a.t_bits) | (t - P.t0);
-}
-
-__device__ void claim_packed(const TotalArgs& a, uint64_t pair, uint64_t slot) {
-  const int sh = a.slot_bits + 1;
-  const uint64_t e = (pair << sh) | (1ull << a.slot_bits) | slot;
-  uint64_t h = pair_hash(pair) & a.table_mask;
-  for (uint64_t probe = 0; probe <= a.table_mask; ++probe) {
-    unsigned long long* w = reinterpret_cast<unsigned long long*>(&a.table_keys[h]);
-    const uint64_t old = atomicCAS(w, kEmpty, e);
-    if (old == kEmpty) return;
-    if ((old >> sh) == pair) {
-      atomicMin(w, e);
-      return;
+// Round r >= 1: true if `slot` holds the lowest claim on its pair (and marks
+// the entry accepted).
+__device__ bool resolve(const RedrawArgs& a, const RedrawProj& r, const DevProj& P, uint32_t s, uint32_t t,
+                        uint64_t slot) {
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(a.table_keys + r.table_off);
+  if (r.packed) {
+    const int sh = r.slot_bits + 1;
+    const uint64_t pair = (static_cast<uint64_t>(s - P.s0) << r.t_bits) | (t - P.t0);
+    const uint64_t e = (pair << sh) | (1ull << r.slot_bits) | slot;
+    uint64_t h = pair_hash(pair) & r.table_mask;
+    for (uint64_t probe = 0; probe <= r.table_mask; ++probe) {
+      const uint64_t v = keys[h];
+      if (v == kEmpty) return false;
+      if ((v >> sh) == pair) {
+        if (v != e) return false;
+        keys[h] = e & ~(1ull << r.slot_bits);
+        return true;
+      }
+      h = (h + 1) & r.table_mask;
     }
-    h = (h + 1) & a.table_mask;
+    return false;
   }
-  atomicOr(a.err, kErrBounds);
-}
-
-// True if `slot` holds the lowest claim on `pair`; the winner marks the
-// entry accepted.
-__device__ bool resolve_packed(const TotalArgs& a, uint64_t pair, uint64_t slot) {
-  const int sh = a.slot_bits + 1;
-  const uint64_t e = (pair << sh) | (1ull << a.slot_bits) | slot;
-  uint64_t h = pair_hash(pair) & a.table_mask;
-  for (uint64_t probe = 0; probe <= a.table_mask; ++probe) {
-    const uint64_t v = a.table_keys[h];
-    if (v == kEmpty) return false;
-    if ((v >> sh) == pair) {
-      if (v != e) return false;
-      a.table_keys[h] = e & ~(1ull << a.slot_bits);
+  unsigned long long* vals = reinterpret_cast<unsigned long long*>(a.table_vals + r.table_off);
+  const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
+  uint64_t h = pair_hash(pair) & r.table_mask;
+  for (uint64_t probe = 0; probe <= r.table_mask; ++probe) {
+    const uint64_t k = keys[h];
+    if (k == kEmpty) return false;
+    if (k == pair) {
+      if (vals[h] != (kClaim | slot)) return false;
+      vals[h] = slot;
       return true;
     }
-    h = (h + 1) & a.table_mask;
+    h = (h + 1) & r.table_mask;
   }
   return false;
 }
 
-__device__ __forceinline__ void claim(const TotalArgs& a, const DevProj& P, uint64_t pair, uint64_t slot) {
-  if (a.packed) {
-    claim_packed(a, packed_pair(a, P, static_cast<uint32_t>(pair >> 32), static_cast<uint32_t>(pair)), slot);
-    return;
-  }
-  const uint64_t h = table_slot(a, pair, true);
-  if (h != kEmpty)
-    atomicMin(reinterpret_cast<unsigned long long*>(&a.table_vals[h]), kClaim | slot);
-}
-
-__device__ __forceinline__ bool allowed_pair(const DevProj& P, uint32_t s, uint32_t t) {
-  return P.autapses || s != t;
+__device__ __forceinline__ void push_pending(const RedrawArgs& a, uint64_t g) {
+  const unsigned long long at = atomicAdd(a.n_next, 1ull);
+  if (at < a.n_slots) a.next_pending[at] = g;
+  else atomicOr(a.err, kErrBounds);
 }
 }  // namespace
 
-// Round 0 with the packed table and the `lost` marks: a slot that finds its
-// pair already held by a lower slot marks itself lost; a slot that displaces
-// a higher one marks that one lost.  Every claimant but the lowest of a pair
-// is marked by someone, so no second pass over the table is needed, and
-// round-0 entries are written in the accepted form (claim bit clear).
-__device__ void claim_round0(const TotalArgs& a, uint64_t pair, uint64_t slot) {
-  const int sh = a.slot_bits + 1;
-  const uint64_t slot_mask = (1ull << a.slot_bits) - 1;
-  const uint64_t e = (pair << sh) | slot;
-  uint64_t h = pair_hash(pair) & a.table_mask;
-  for (uint64_t probe = 0; probe <= a.table_mask; ++probe) {
-    unsigned long long* w = reinterpret_cast<unsigned long long*>(&a.table_keys[h]);
-    const uint64_t old = atomicCAS(w, kEmpty, e);
-    if (old == kEmpty) return;
-    if ((old >> sh) == pair) {
-      const uint64_t prev = atomicMin(w, e);
-      if (prev < e) a.lost[slot] = 1;
-      else a.lost[prev & slot_mask] = 1;
-      return;
-    }
-    h = (h + 1) & a.table_mask;
-  }
-  atomicOr(a.err, kErrBounds);
-}
-
-__global__ void total_round0_kernel(TotalArgs a) {
-  const DevProj& P = *a.proj;
+__global__ void redraw_round0_kernel(RedrawArgs a) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.count; i += stride) {
-    const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-    const Words X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, i >> 2);
-    const uint32_t sel = static_cast<uint32_t>(i & 3u);
+  for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < a.n_slots; g += stride) {
+    const SlotRef x = slot_ref(a, g);
+    const DevProj& P = *x.P;
+    const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, x.i);
+    const Words X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, x.i >> 2);
+    const uint32_t sel = static_cast<uint32_t>(x.i & 3u);
     const uint32_t tw = sel == 0 ? X.x : sel == 1 ? X.y : sel == 2 ? X.z : X.w;
     const uint32_t s = P.s0 + rand_below(W.y, P.ns);
     const uint32_t t = P.t0 + rand_below(tw, P.nt);
-    const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
-    a.pairs[i] = pair;
-    if (a.lost) {
-      if (!allowed_pair(P, s, t)) a.lost[i] = 1;
-      else if (!P.multapses) claim_round0(a, packed_pair(a, P, s, t), i);
-    } else if (!P.multapses && allowed_pair(P, s, t)) {
-      claim(a, P, pair, i);
-    }
+    a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
+    if (!allowed_pair(P, s, t)) a.lost[g] = 1;
+    else if (!P.multapses) claim(a, *x.r, P, s, t, x.i, g, true);
   }
 }
 
 // Round-0 slots marked lost become the first pending list.
-__global__ void total_collect_kernel(TotalArgs a) {
-  const DevProj& P = *a.proj;
+__global__ void redraw_collect_kernel(RedrawArgs a) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.count; i += stride) {
-    if (a.lost[i]) {
-      const unsigned long long at = atomicAdd(a.n_next, 1ull);
-      if (SNC_IN_BOUNDS(a.err, 2u, at, P.count)) a.next_pending[at] = i;
-    }
-  }
+  for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < a.n_slots; g += stride)
+    if (a.lost[g]) push_pending(a, g);
 }
 
-__global__ void total_claim_kernel(TotalArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round) {
-  const DevProj& P = *a.proj;
+__global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pending; q += stride) {
-    const uint64_t i = pending[q];
-    const Words D = draw(P.k0, P.k1, kTagDedup, round, kPrimaryNone, i);
+    const uint64_t g = pending[q];
+    const SlotRef x = slot_ref(a, g);
+    const DevProj& P = *x.P;
+    const Words D = draw(P.k0, P.k1, kTagDedup, round, kPrimaryNone, x.i);
     const uint32_t s = P.s0 + rand_below(D.x, P.ns);
     const uint32_t t = P.t0 + rand_below(D.y, P.nt);
-    const uint64_t pair = (static_cast<uint64_t>(s) << 32) | t;
-    a.pairs[i] = pair;
-    if (!P.multapses && allowed_pair(P, s, t)) claim(a, P, pair, i);
+    a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
+    if (!P.multapses && allowed_pair(P, s, t)) claim(a, *x.r, P, s, t, x.i, g, false);
   }
 }
 
-// Decides the slots of this round: winners become accepted, the others are
-// appended to next_pending (order within the list is irrelevant: each slot's
+// Decides the slots of round r >= 1: winners become accepted, the others are
+// appended to next_pending (the order of the list is irrelevant: each slot's
 // later draws depend only on the slot and the round).
-__global__ void total_resolve_kernel(TotalArgs a, const uint64_t* pending, uint64_t n_pending, int all_slots) {
-  const DevProj& P = *a.proj;
-  const uint64_t n = all_slots ? P.count : n_pending;
+__global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n; q += stride) {
-    const uint64_t i = all_slots ? q : pending[q];
-    const uint64_t pair = a.pairs[i];
+  for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pending; q += stride) {
+    const uint64_t g = pending[q];
+    const SlotRef x = slot_ref(a, g);
+    const DevProj& P = *x.P;
+    const uint64_t pair = a.pairs[g];
     const uint32_t s = static_cast<uint32_t>(pair >> 32), t = static_cast<uint32_t>(pair);
     bool ok = allowed_pair(P, s, t);
-    if (ok && !P.multapses) {
-      if (a.packed) {
-        ok = resolve_packed(a, packed_pair(a, P, s, t), i);
-      } else {
-        const uint64_t h = table_slot(a, pair, false);
-        ok = h != kEmpty && a.table_vals[h] == (kClaim | i);
-        if (ok) a.table_vals[h] = i;
-      }
-    }
-    if (!ok) {
-      const unsigned long long at = atomicAdd(a.n_next, 1ull);
-      if (SNC_IN_BOUNDS(a.err, 2u, at, P.count)) a.next_pending[at] = i;
-    }
+    if (ok && !P.multapses) ok = resolve(a, *x.r, P, s, t, x.i);
+    if (!ok) push_pending(a, g);
   }
 }
 
-__global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, const DevProj* proj, const uint64_t* pairs) {
+// Writes the redraw projections' connections: the final pairs with the
+// round-0 weight and delay of each slot.  Blocks take chunks of kChunk slots
+// of one projection (delay table reloaded when the projection changes).
+__global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks) {
   extern __shared__ uint32_t smem_raw[];
   const uint32_t hw = hist_words(g);
   SmemTables tabs{smem_raw + hw, reinterpret_cast<uint16_t*>(smem_raw + hw + g.max_delay_len)};
   const BlockHist bh = block_hist_begin(g, smem_raw);
-  const DevProj& P = *proj;
-  load_delay_table(P, g.thr_blob, g.guide_blob, tabs);
   __syncthreads();
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < P.count; i += stride) {
-    const uint64_t pair = pairs[i];
-    const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-    store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32), delay_step(P, tabs, W.x),
-          static_cast<uint32_t>(pair) - P.t_base, weight_bits(P, W.z, W.w));
+  int cur = -1;
+  for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
+    int lo = 0, hi = a.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.rp[mid].chunk_base <= c) lo = mid; else hi = mid - 1;
+    }
+    const RedrawProj& r = a.rp[lo];
+    const DevProj& P = a.projs[r.proj];
+    if (lo != cur) {
+      __syncthreads();
+      load_delay_table(P, g.thr_blob, g.guide_blob, tabs);
+      __syncthreads();
+      cur = lo;
+    }
+    const uint64_t i0 = (c - r.chunk_base) * kChunk;
+    const uint64_t i1 = i0 + kChunk < P.count ? i0 + kChunk : P.count;
+    for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const uint64_t pair = a.pairs[r.slot_base + i];
+      const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
+      store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32), delay_step(P, tabs, W.x),
+            static_cast<uint32_t>(pair) - P.t_base, weight_bits(P, W.z, W.w));
+    }
   }
   block_hist_end(g, bh);
 }

@@ -31,45 +31,64 @@ struct GenArgs {
   HistPlan hist;   // digit counts of the sort's passes, accumulated as keys are written
 };
 
+// One launch serves every listed sampler projection: warps take primary
+// nodes of the concatenated list (prim_prefix), each warp keeping a bitmap
+// and the delay table of its current projection in shared memory.
 struct SamplerArgs {
-  GenArgs gen;               // output arrays and layout
-  const DevProj* proj;       // the one projection handled by the launch
+  GenArgs gen;                   // output arrays and layout
+  const DevProj* projs;          // projection table of the build
+  const uint32_t* list;          // projections handled by the launch
+  const uint64_t* prim_prefix;   // [n_list + 1] primaries before each listed projection
+  int n_list;
   const uint32_t* thr_blob;
   const uint16_t* guide_blob;
-  uint32_t max_delay_len;
-  uint32_t bitmap_words;     // per warp
-  const uint64_t* prim_offsets;  // Bernoulli: per-target offsets (n_primary + 1)
+  uint32_t max_delay_len;        // largest delay table among the listed projections
+  uint32_t table_words;          // per-warp table area (thresholds + guide), uint32 units
+  uint32_t bitmap_words;         // per-warp bitmap (largest candidate range)
+  const uint64_t* prim_offsets;  // Bernoulli: exclusive scan of all per-target counts
   uint32_t* err;
 };
 
 __global__ void gen_direct_kernel(GenArgs a);
-__global__ void bernoulli_count_kernel(const DevProj* proj, const uint32_t* thr_blob,
-                                       const uint16_t* guide_blob, uint32_t* counts);
+// Per-target Binomial counts of every listed pairwise_bernoulli projection
+// (targets concatenated in list order, prefix[n_list] in total).
+__global__ void bernoulli_count_kernel(const DevProj* projs, const uint32_t* list, const uint64_t* prefix, int n_list,
+                                       const uint32_t* thr_blob, const uint16_t* guide_blob, uint32_t* counts);
+// out[j] = offsets[prefix[j + 1]] - offsets[prefix[j]]: connections per listed projection.
+__global__ void segment_totals_kernel(const uint64_t* offsets, const uint64_t* prefix, int n_list, uint64_t* out);
 __global__ void sampler_kernel(SamplerArgs a);
 
-// fixed_total_number with autapses or multapses forbidden.
-struct TotalArgs {
-  const DevProj* proj;
-  uint64_t* pairs;        // per slot: (source << 32) | target, global ids
-  uint64_t* table_keys;   // open-addressing hash table of pairs (~0 = empty)
-  uint64_t* table_vals;   // accepted: slot; claimed this round: 2^63 | slot
-  uint64_t table_mask;
-  // Packed table (one word per entry, used when it fits):
-  // (pair_local << (slot_bits + 1)) | (claimed_this_round << slot_bits) | slot
-  int packed;
-  int slot_bits;
-  int t_bits;           // bits of the target's local index in pair_local
-  uint8_t* lost;        // round-0 marks (packed table or no table); null: resolve pass
-  uint64_t* pending;      // slots still to redraw
+// fixed_total_number with autapses or multapses forbidden: the redraw
+// projections of a build, their slots concatenated.
+struct RedrawProj {
+  uint32_t proj;        // index in the projection table
+  int packed;           // one-word table entries
+  int slot_bits;        // bits of a local slot
+  int t_bits;           // bits of the target's local index (packed pair)
+  uint64_t slot_base;   // first slot of this projection in the concatenation
+  uint64_t chunk_base;  // first emit chunk (kChunk slots) of this projection
+  uint64_t table_off;   // first entry of its hash table region
+  uint64_t table_mask;  // entries - 1 (power of two)
+};
+
+struct RedrawArgs {
+  const DevProj* projs;
+  const RedrawProj* rp;
+  int n;                       // redraw projections
+  uint64_t n_slots;            // all slots
+  uint64_t* pairs;             // per slot: (source << 32) | target, global ids
+  uint8_t* lost;               // round-0 marks
+  uint64_t* table_keys;        // hash tables (~0 = empty)
+  uint64_t* table_vals;        // values of the two-array tables
   uint64_t* next_pending;
   unsigned long long* n_next;  // device counter of next_pending
   uint32_t* err;
 };
-__global__ void total_round0_kernel(TotalArgs a);
-__global__ void total_collect_kernel(TotalArgs a);
-__global__ void total_claim_kernel(TotalArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round);
-__global__ void total_resolve_kernel(TotalArgs a, const uint64_t* pending, uint64_t n_pending, int all_slots);
-__global__ void total_emit_kernel(GenArgs g, const DevProj* proj, const uint64_t* pairs);
+__global__ void redraw_round0_kernel(RedrawArgs a);
+__global__ void redraw_collect_kernel(RedrawArgs a);
+__global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round);
+__global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending);
+__global__ void total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks);
 
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* block_tmp,
                                cudaStream_t st);

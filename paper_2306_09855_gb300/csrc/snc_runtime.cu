@@ -440,7 +440,6 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     guide_blob.resize(guide_blob.size() + kDelayGuide);
     guide_table(t, guide_blob.data() + goff);
   };
-  uint64_t n_var_primaries = 0;
   for (size_t i = 0; i < np; ++i) {
     const Projection& p = *ups[i].p;
     DevProj& d = dp[i];
@@ -475,8 +474,6 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         add_table(p.b_thr[s], d.b_off[s], d.b_goff[s]);
         max_binom_len = std::max(max_binom_len, d.b_len[s]);
       }
-      d.prim_off = n_var_primaries;
-      n_var_primaries += static_cast<uint64_t>(p.tgt.n) + 1;
     }
   }
   if (thr_blob.empty()) thr_blob.push_back(0);
@@ -496,47 +493,54 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   SNC_CUDA(c, cudaMemsetAsync(S.d_err, 0, 8 * sizeof(uint64_t), st));
   SNC_CUDA(c, cudaMemsetAsync(S.d_n_groups, 0, sizeof(uint64_t), st));
 
-  // Count phase: pairwise Bernoulli per-target counts and offsets.
+  // Count phase: per-target counts of every pairwise Bernoulli projection in
+  // one launch, one scan, one read-back of the per-projection totals.
   uint64_t* d_prim_off = nullptr;
-  if (n_var_primaries > 0) {
+  std::vector<uint32_t> bern;
+  std::vector<uint64_t> bern_prefix(1, 0);
+  for (size_t i = 0; i < np; ++i)
+    if (ups[i].p->rule.kind == SNC_PAIRWISE_BERNOULLI) {
+      dp[i].prim_off = bern_prefix.back();
+      bern.push_back(static_cast<uint32_t>(i));
+      bern_prefix.push_back(bern_prefix.back() + ups[i].p->tgt.n);
+    }
+  if (!bern.empty()) {
+    const uint64_t n_targets = bern_prefix.back();
+    const int nb = static_cast<int>(bern.size());
     SNC_CUDA(c, cudaMemcpyAsync(d_proj, dp.data(), np * sizeof(DevProj), cudaMemcpyHostToDevice, st));
     c->stats.h2d_bytes += np * sizeof(DevProj);
-    d_prim_off = static_cast<uint64_t*>(dev_alloc(c, n_var_primaries * sizeof(uint64_t)));
-    uint32_t* d_counts = static_cast<uint32_t*>(dev_alloc(c, n_var_primaries * sizeof(uint32_t)));
-    uint64_t* d_scan_tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_var_primaries) + 1) * sizeof(uint64_t)));
-    if (!d_prim_off || !d_counts || !d_scan_tmp) return fail(c, SNC_ERR_OOM, "device allocation failed (counts)");
-    std::vector<size_t> bern;
-    for (size_t i = 0; i < np; ++i)
-      if (ups[i].p->rule.kind == SNC_PAIRWISE_BERNOULLI) bern.push_back(i);
-    if (bern.size() > 60) {
-      // read the totals in groups that fit the pinned staging area
-    }
-    for (size_t bi = 0; bi < bern.size(); ++bi) {
-      const size_t i = bern[bi];
-      const uint32_t nt = ups[i].p->tgt.n;
-      if (nt > 0) {
-        bernoulli_count_kernel<<<(nt + 255) / 256, 256, 0, st>>>(d_proj + i, d_thr, d_guide, d_counts + dp[i].prim_off);
-        ++c->stats.kernel_launches;
-        SNC_CUDA(c, cudaGetLastError());
-      }
-      SNC_CUDA(c, exclusive_scan_u32(d_counts + dp[i].prim_off, nt, d_prim_off + dp[i].prim_off, d_scan_tmp, st));
-      c->stats.kernel_launches += 3;
-    }
+    d_prim_off = static_cast<uint64_t*>(dev_alloc(c, (n_targets + 1) * sizeof(uint64_t)));
+    uint32_t* d_counts = static_cast<uint32_t*>(dev_alloc(c, (n_targets + 1) * sizeof(uint32_t)));
+    uint64_t* d_scan_tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_targets) + 1) * sizeof(uint64_t)));
+    uint32_t* d_blist = static_cast<uint32_t*>(dev_alloc(c, bern.size() * sizeof(uint32_t)));
+    uint64_t* d_bprefix = static_cast<uint64_t*>(dev_alloc(c, bern_prefix.size() * sizeof(uint64_t)));
+    uint64_t* d_totals = static_cast<uint64_t*>(dev_alloc(c, bern.size() * sizeof(uint64_t)));
+    if (!d_prim_off || !d_counts || !d_scan_tmp || !d_blist || !d_bprefix || !d_totals)
+      return fail(c, SNC_ERR_OOM, "device allocation failed (counts)");
+    SNC_CUDA(c, cudaMemcpyAsync(d_blist, bern.data(), bern.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    SNC_CUDA(c, cudaMemcpyAsync(d_bprefix, bern_prefix.data(), bern_prefix.size() * sizeof(uint64_t),
+                                cudaMemcpyHostToDevice, st));
+    c->stats.h2d_bytes += bern.size() * sizeof(uint32_t) + bern_prefix.size() * sizeof(uint64_t);
+    const unsigned cgrid =
+        static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>((n_targets + 255) / 256, c->sms * 16ull)));
+    bernoulli_count_kernel<<<cgrid, 256, 0, st>>>(d_proj, d_blist, d_bprefix, nb, d_thr, d_guide, d_counts);
+    ++c->stats.kernel_launches;
+    SNC_CUDA(c, cudaGetLastError());
+    SNC_CUDA(c, exclusive_scan_u32(d_counts, n_targets, d_prim_off, d_scan_tmp, st));
+    c->stats.kernel_launches += 3;
+    segment_totals_kernel<<<(nb + 255) / 256, 256, 0, st>>>(d_prim_off, d_bprefix, nb, d_totals);
+    ++c->stats.kernel_launches;
+    SNC_CUDA(c, cudaGetLastError());
     std::vector<uint64_t> totals(bern.size());
-    for (size_t b0 = 0; b0 < bern.size(); b0 += 64) {
-      const size_t cnt = std::min<size_t>(64, bern.size() - b0);
-      for (size_t j = 0; j < cnt; ++j) {
-        const size_t i = bern[b0 + j];
-        SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + j, d_prim_off + dp[i].prim_off + ups[i].p->tgt.n, sizeof(uint64_t),
-                                    cudaMemcpyDeviceToHost, st));
-        c->stats.d2h_bytes += sizeof(uint64_t);
-      }
-      SNC_CUDA(c, cudaStreamSynchronize(st));
-      for (size_t j = 0; j < cnt; ++j) totals[b0 + j] = S.h_pinned[j];
-    }
+    SNC_CUDA(c, cudaMemcpyAsync(totals.data(), d_totals, bern.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    c->stats.d2h_bytes += bern.size() * sizeof(uint64_t);
+    SNC_CUDA(c, cudaStreamSynchronize(st));
     for (size_t bi = 0; bi < bern.size(); ++bi) cnt[bern[bi]] = totals[bi];
     dev_free(c, d_counts);
     dev_free(c, d_scan_tmp);
+    dev_free(c, d_blist);
+    dev_free(c, d_bprefix);
+    dev_free(c, d_totals);
   }
   cudaEventRecord(S.ev[S.n_ev++], st);
 
@@ -620,125 +624,171 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
   }
-  for (size_t i = 0; i < np; ++i) {
-    const Projection& p = *ups[i].p;
-    if (cnt[i] == 0) continue;
-    if (is_sampler(p)) {
-      const uint32_t n_other = (p.rule.kind == SNC_FIXED_OUTDEGREE) ? p.tgt.n : p.src.n;
-      const uint32_t n_primary = (p.rule.kind == SNC_FIXED_OUTDEGREE) ? p.src.n : p.tgt.n;
+  // Samplers (in/out-degree without multapses, Bernoulli subsets): one launch.
+  {
+    std::vector<uint32_t> slist;
+    std::vector<uint64_t> sprefix(1, 0);
+    uint32_t max_other = 1, max_len = 0;
+    for (size_t i = 0; i < np; ++i) {
+      const Projection& p = *ups[i].p;
+      if (cnt[i] == 0 || !is_sampler(p)) continue;
+      const bool out_deg = p.rule.kind == SNC_FIXED_OUTDEGREE;
+      slist.push_back(static_cast<uint32_t>(i));
+      sprefix.push_back(sprefix.back() + (out_deg ? p.src.n : p.tgt.n));
+      max_other = std::max<uint32_t>(max_other, out_deg ? p.tgt.n : p.src.n);
+      max_len = std::max(max_len, dp[i].d_len);
+    }
+    if (!slist.empty()) {
+      uint32_t* d_slist = static_cast<uint32_t*>(dev_alloc(c, slist.size() * sizeof(uint32_t)));
+      uint64_t* d_sprefix = static_cast<uint64_t*>(dev_alloc(c, sprefix.size() * sizeof(uint64_t)));
+      if (!d_slist || !d_sprefix) return fail(c, SNC_ERR_OOM, "device allocation failed (sampler list)");
+      SNC_CUDA(c, cudaMemcpyAsync(d_slist, slist.data(), slist.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+      SNC_CUDA(c, cudaMemcpyAsync(d_sprefix, sprefix.data(), sprefix.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                  st));
+      c->stats.h2d_bytes += slist.size() * sizeof(uint32_t) + sprefix.size() * sizeof(uint64_t);
       SamplerArgs s{};
       s.gen = g;
-      s.proj = d_proj + i;
+      s.projs = d_proj;
+      s.list = d_slist;
+      s.prim_prefix = d_sprefix;
+      s.n_list = static_cast<int>(slist.size());
       s.thr_blob = d_thr;
       s.guide_blob = d_guide;
-      s.max_delay_len = dp[i].d_len;
-      s.bitmap_words = (n_other + 31u) / 32u;
-      s.prim_offsets = d_prim_off ? d_prim_off + dp[i].prim_off : nullptr;
+      s.max_delay_len = max_len;
+      s.table_words = max_len + (kDelayGuide + 1) / 2 + 1;
+      s.bitmap_words = (max_other + 31u) / 32u;
+      s.prim_offsets = d_prim_off;
       s.err = S.d_err;
-      const size_t bitmap_bytes = static_cast<size_t>(s.bitmap_words) * sizeof(uint32_t);
-      const size_t tab =
-          hist_bytes + static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
-      int warps = static_cast<int>(std::min<size_t>(8, (kSamplerSmem - tab) / std::max<size_t>(bitmap_bytes, 4)));
+      const size_t per_warp = static_cast<size_t>(s.bitmap_words + s.table_words) * sizeof(uint32_t);
+      const int warps = static_cast<int>(std::min<size_t>(8, (kSamplerSmem - hist_bytes - 16) / per_warp));
       if (warps < 1) return fail(c, SNC_ERR_UNSUPPORTED, "sampler bitmap does not fit shared memory");
-      const size_t smem = static_cast<size_t>(warps) * bitmap_bytes + tab;
+      const size_t smem = hist_bytes + static_cast<size_t>(warps) * per_warp + 16;
       static bool sconf = false;
       if (!sconf) {
         SNC_CUDA(c, cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kSamplerSmem)));
         sconf = true;
       }
-      const uint64_t want_blocks = (static_cast<uint64_t>(n_primary) + warps - 1) / warps;
+      const uint64_t want_blocks = (sprefix.back() + warps - 1) / warps;
       const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want_blocks, static_cast<uint64_t>(c->sms) * 16));
       sampler_kernel<<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(s);
       ++c->stats.kernel_launches;
       SNC_CUDA(c, cudaGetLastError());
-    } else if (is_total_redraw(p)) {
-      const snc_status r = [&]() -> snc_status {
-        const uint64_t N = cnt[i];
-        TotalArgs t{};
-        t.proj = d_proj + i;
-        t.err = S.d_err;
-        t.pairs = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
-        t.pending = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
-        t.next_pending = static_cast<uint64_t*>(dev_alloc(c, N * sizeof(uint64_t)));
-        t.n_next = static_cast<unsigned long long*>(dev_alloc(c, sizeof(unsigned long long)));
+      dev_free(c, d_slist);
+      dev_free(c, d_sprefix);
+    }
+  }
+  // fixed_total_number with redraws: all such projections together, one
+  // read-back of the pending count per round.
+  {
+    std::vector<RedrawProj> rps;
+    uint64_t n_slots = 0, n_table = 0, n_chunks_r = 0;
+    bool any_vals = false;
+    uint32_t max_len = 0;
+    for (size_t i = 0; i < np; ++i) {
+      const Projection& p = *ups[i].p;
+      if (cnt[i] == 0 || !is_total_redraw(p)) continue;
+      const uint64_t N = cnt[i];
+      RedrawProj r{};
+      r.proj = static_cast<uint32_t>(i);
+      r.slot_base = n_slots;
+      r.chunk_base = n_chunks_r;
+      r.table_off = n_table;
+      r.slot_bits = std::max(1, bit_width(N - 1));
+      r.t_bits = bit_width(p.tgt.n > 0 ? p.tgt.n - 1u : 0u);
+      if (!p.rule.allow_multapses) {
         uint64_t cap = 1;
-        if (!p.rule.allow_multapses) {
-          while (cap < 2 * N + 64) cap <<= 1;
-          // One word per entry when (source, target, slot) fit in 63 bits.
-          const int s_bits = bit_width(p.src.n > 0 ? p.src.n - 1u : 0u);
-          const int t_bits = bit_width(p.tgt.n > 0 ? p.tgt.n - 1u : 0u);
-          const int slot_bits = std::max(1, bit_width(N - 1));
-          t.packed = (s_bits + t_bits + slot_bits + 1 <= 63) ? 1 : 0;
-          t.slot_bits = slot_bits;
-          t.t_bits = t_bits;
-          t.table_keys = static_cast<uint64_t*>(dev_alloc(c, cap * sizeof(uint64_t)));
-          if (!t.table_keys) return fail(c, SNC_ERR_OOM, "device allocation failed (pair table)");
-          SNC_CUDA(c, cudaMemsetAsync(t.table_keys, 0xFF, cap * sizeof(uint64_t), st));
-          if (!t.packed) {
-            t.table_vals = static_cast<uint64_t*>(dev_alloc(c, cap * sizeof(uint64_t)));
-            if (!t.table_vals) return fail(c, SNC_ERR_OOM, "device allocation failed (pair table)");
-            SNC_CUDA(c, cudaMemsetAsync(t.table_vals, 0xFF, cap * sizeof(uint64_t), st));
-          }
+        while (cap < 2 * N + 64) cap <<= 1;
+        // One word per entry when (source, target, slot) fit in 63 bits.
+        const int s_bits = bit_width(p.src.n > 0 ? p.src.n - 1u : 0u);
+        r.packed = (s_bits + r.t_bits + r.slot_bits + 1 <= 63) ? 1 : 0;
+        any_vals = any_vals || !r.packed;
+        r.table_mask = cap - 1;
+        n_table += cap;
+      }
+      n_slots += N;
+      n_chunks_r += (N + kChunk - 1) / kChunk;
+      max_len = std::max(max_len, dp[i].d_len);
+      rps.push_back(r);
+    }
+    if (!rps.empty()) {
+      RedrawArgs a{};
+      a.projs = d_proj;
+      a.n = static_cast<int>(rps.size());
+      a.n_slots = n_slots;
+      a.err = S.d_err;
+      RedrawProj* d_rp = static_cast<RedrawProj*>(dev_alloc(c, rps.size() * sizeof(RedrawProj)));
+      a.pairs = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
+      a.lost = static_cast<uint8_t*>(dev_alloc(c, n_slots));
+      uint64_t* pend_a = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
+      uint64_t* pend_b = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
+      a.n_next = static_cast<unsigned long long*>(dev_alloc(c, sizeof(unsigned long long)));
+      if (!d_rp || !a.pairs || !a.lost || !pend_a || !pend_b || !a.n_next)
+        return fail(c, SNC_ERR_OOM, "device allocation failed (redraw lists)");
+      if (n_table > 0) {
+        a.table_keys = static_cast<uint64_t*>(dev_alloc(c, n_table * sizeof(uint64_t)));
+        if (!a.table_keys) return fail(c, SNC_ERR_OOM, "device allocation failed (pair table)");
+        SNC_CUDA(c, cudaMemsetAsync(a.table_keys, 0xFF, n_table * sizeof(uint64_t), st));
+        if (any_vals) {
+          a.table_vals = static_cast<uint64_t*>(dev_alloc(c, n_table * sizeof(uint64_t)));
+          if (!a.table_vals) return fail(c, SNC_ERR_OOM, "device allocation failed (pair table)");
+          SNC_CUDA(c, cudaMemsetAsync(a.table_vals, 0xFF, n_table * sizeof(uint64_t), st));
         }
-        t.table_mask = cap - 1;
-        if (!t.pairs || !t.pending || !t.next_pending || !t.n_next)
-          return fail(c, SNC_ERR_OOM, "device allocation failed (redraw lists)");
-        const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(
-            1, std::min<uint64_t>((N + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
-        SNC_CUDA(c, cudaMemsetAsync(t.n_next, 0, sizeof(unsigned long long), st));
-        if (t.packed || p.rule.allow_multapses) {
-          t.lost = static_cast<uint8_t*>(dev_alloc(c, N));
-          if (!t.lost) return fail(c, SNC_ERR_OOM, "device allocation failed (redraw marks)");
-          SNC_CUDA(c, cudaMemsetAsync(t.lost, 0, N, st));
-        }
-        total_round0_kernel<<<grid, 256, 0, st>>>(t);
-        ++c->stats.kernel_launches;
-        if (t.lost)
-          total_collect_kernel<<<grid, 256, 0, st>>>(t);
-        else
-          total_resolve_kernel<<<grid, 256, 0, st>>>(t, nullptr, 0, 1);
-        ++c->stats.kernel_launches;
+      }
+      a.rp = d_rp;
+      SNC_CUDA(c, cudaMemcpyAsync(d_rp, rps.data(), rps.size() * sizeof(RedrawProj), cudaMemcpyHostToDevice, st));
+      c->stats.h2d_bytes += rps.size() * sizeof(RedrawProj);
+      SNC_CUDA(c, cudaMemsetAsync(a.lost, 0, n_slots, st));
+      SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
+      a.next_pending = pend_a;
+      const auto grid_for = [&](uint64_t items) {
+        return static_cast<unsigned>(
+            std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
+      };
+      redraw_round0_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
+      redraw_collect_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
+      c->stats.kernel_launches += 2;
+      SNC_CUDA(c, cudaGetLastError());
+      uint64_t* pending = pend_a;
+      uint64_t* next = pend_b;
+      for (uint32_t round = 1;; ++round) {
+        SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned, a.n_next, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        c->stats.d2h_bytes += sizeof(uint64_t);
+        SNC_CUDA(c, cudaStreamSynchronize(st));
+        const uint64_t n_pend = S.h_pinned[0];
+        if (n_pend == 0) break;
+        if (round > 0xFFFFFFu) return fail(c, SNC_ERR_TIMEOUT, "fixed_total_number: redraw rounds exhausted");
+        if (n_pend > n_slots) return fail(c, SNC_ERR_CUDA, "fixed_total_number: pending list overflow (internal error)");
+        a.next_pending = next;
+        SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
+        redraw_claim_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend, round);
+        redraw_resolve_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend);
+        c->stats.kernel_launches += 2;
         SNC_CUDA(c, cudaGetLastError());
-        for (uint32_t round = 1;; ++round) {
-          SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned, t.n_next, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-          c->stats.d2h_bytes += sizeof(uint64_t);
-          SNC_CUDA(c, cudaStreamSynchronize(st));
-          const uint64_t n_pend = S.h_pinned[0];
-          if (n_pend == 0) break;
-          if (round > 0xFFFFFFu) return fail(c, SNC_ERR_TIMEOUT, "fixed_total_number: redraw rounds exhausted");
-          std::swap(t.pending, t.next_pending);
-          SNC_CUDA(c, cudaMemsetAsync(t.n_next, 0, sizeof(unsigned long long), st));
-          const unsigned g2 = static_cast<unsigned>(std::max<uint64_t>(
-              1, std::min<uint64_t>((n_pend + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
-          total_claim_kernel<<<g2, 256, 0, st>>>(t, t.pending, n_pend, round);
-          ++c->stats.kernel_launches;
-          total_resolve_kernel<<<g2, 256, 0, st>>>(t, t.pending, n_pend, 0);
-          ++c->stats.kernel_launches;
-          SNC_CUDA(c, cudaGetLastError());
-        }
-        GenArgs ge = g;
-        ge.max_delay_len = dp[i].d_len;
-        const size_t tsm =
-            hist_bytes + static_cast<size_t>(dp[i].d_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
-        static bool econf = false;
-        if (!econf) {
-          SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-          econf = true;
-        }
-        total_emit_kernel<<<grid, kGenThreads, tsm, st>>>(ge, d_proj + i, t.pairs);
-        ++c->stats.kernel_launches;
-        SNC_CUDA(c, cudaGetLastError());
-        dev_free(c, t.pairs);
-        dev_free(c, t.pending);
-        dev_free(c, t.next_pending);
-        dev_free(c, t.n_next);
-        dev_free(c, t.table_keys);
-        dev_free(c, t.table_vals);
-        dev_free(c, t.lost);
-        return SNC_OK;
-      }();
-      if (r != SNC_OK) return r;
+        std::swap(pending, next);
+      }
+      GenArgs ge = g;
+      ge.max_delay_len = max_len;
+      const size_t tsm =
+          hist_bytes + static_cast<size_t>(max_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
+      static bool econf = false;
+      if (!econf) {
+        SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        econf = true;
+      }
+      const unsigned eg = static_cast<unsigned>(
+          std::min<uint64_t>(n_chunks_r, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm));
+      total_emit_kernel<<<eg, kGenThreads, tsm, st>>>(ge, a, n_chunks_r);
+      ++c->stats.kernel_launches;
+      SNC_CUDA(c, cudaGetLastError());
+      dev_free(c, d_rp);
+      dev_free(c, a.pairs);
+      dev_free(c, a.lost);
+      dev_free(c, pend_a);
+      dev_free(c, pend_b);
+      dev_free(c, a.n_next);
+      dev_free(c, a.table_keys);
+      dev_free(c, a.table_vals);
     }
   }
   cudaEventRecord(S.ev[S.n_ev++], st);
