@@ -25,6 +25,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -39,7 +41,7 @@ def parse_args():
     ap.add_argument("--impl", default="snc", choices=["snc", "reference"])
     ap.add_argument("--workload", default="rule_sweep",
                     choices=["rule_sweep", "microcircuit", "plain", "small", "profile", "profile_total",
-                             "batched"])
+                             "profile_sampler", "profile_bernoulli", "batched", "served"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sort-digit-bits", type=int, default=None, help="tuning: widest radix digit")
     ap.add_argument("--sort-group-tiles", type=int, default=None, help="tuning: tiles per look-back unit")
@@ -76,6 +78,14 @@ def workload_specs(name):
         return [W.two_population(30_000, "fixed_total_number", k=20_000_000, autapses=False, multapses=False)], {
             "workload": "profiling case: 2 x 30,000 nodes, fixed_total_number 2e7 per call without autapses "
                         "or multapses (8e7 connections)", "seed": 1234}
+    if name == "profile_sampler":
+        return [W.two_population(100_000, "fixed_indegree", k=100, autapses=False, multapses=False)], {
+            "workload": "profiling case: 2 x 100,000 nodes, fixed_indegree K=100 without autapses or "
+                        "multapses (4e7 connections)", "seed": 1234}
+    if name == "profile_bernoulli":
+        return [W.two_population(100_000, "pairwise_bernoulli", p=0.001, autapses=False)], {
+            "workload": "profiling case: 2 x 100,000 nodes, pairwise_bernoulli p=0.001 (about 4e7 "
+                        "connections)", "seed": 1234}
     return [W.rule_sweep("fixed_indegree", True, scale=0.1)], {
         "workload": "small: 2 x 10,000 nodes fixed_indegree K=1000", "seed": 1234}
 
@@ -90,10 +100,16 @@ def measured_peaks():
 
 
 def committed_traffic():
-    """DRAM bytes per element of one radix pass from the committed ncu summary."""
+    """DRAM bytes per element of one radix pass from the committed ncu summary,
+    or None when the sort kernels changed since those counters were taken."""
+    import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "onesweep_traffic.json")) as f:
-            return json.load(f)
+            tr = json.load(f)
+        with open(os.path.join(ROOT, "paper_2306_09855_gb300", "csrc", "sort_kernels.cu"), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != tr.get("sort_kernels_cu_sha1"):
+                return None
+        return tr
     except Exception:
         return None
 
@@ -194,10 +210,153 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def _serve(snc, srv, specs, arrivals, hold_s):
+    """Submit specs at the given arrival offsets (seconds; None = all at
+    once), collect every completion on a second thread, keep each network
+    resident for hold_s seconds after it finished, then release it.
+    Returns (wall seconds, per-request records, stats, host bytes)."""
+    import collections
+    import threading
+    done = []
+    io = {"h2d": 0, "d2h": 0}
+    t0 = time.perf_counter()
+
+    def completer():
+        held = collections.deque()
+        while len(done) < len(specs):
+            t = srv.wait_any(timeout_ms=20)
+            now = time.perf_counter()
+            while held and (held[0][0] <= now or t == 0 and len(done) == len(specs)):
+                srv.release(held.popleft()[1])
+            if t == 0:
+                continue
+            v = srv.view(t)
+            tm = srv.times(t)
+            st = snc.snc_get_stats(snc.snc_server_context(srv.srv, t))
+            io["h2d"] += int(st.h2d_bytes)
+            io["d2h"] += int(st.d2h_bytes)
+            done.append((int(v.n_syn), tm.latency_ms, tm.queued_ms, tm.batch_size, now))
+            if hold_s > 0:
+                held.append((now + hold_s, t))
+            else:
+                srv.release(t)
+        while held:
+            srv.release(held.popleft()[1])
+
+    th = threading.Thread(target=completer)
+    th.start()
+    for i, sp in enumerate(specs):
+        if arrivals is not None:
+            wait = t0 + arrivals[i] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+        srv.submit(sp)
+    th.join()
+    last = max(r[4] for r in done)
+    return last - t0, done, srv.stats(), io
+
+
+def run_served(args):
+    """Served form: a Poisson stream of 2,000 construction requests (sizes
+    log-uniform 1e5-5e8, rule uniform over the six, multapses on or off),
+    admitted under a 150 GB budget, results resident until released."""
+    import torch
+    from paper_2306_09855_gb300 import snc
+    from paper_2306_09855_gb300 import workloads as W
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    snc.load()
+    stream_specs = W.served_stream(2000)
+    specs = [sp for _, sp in stream_specs]
+    offsets = [t for t, _ in stream_specs]
+    budget = 150 * 10**9
+    slots, batch_nets, batch_syn = 4, 64, 40_000_000
+
+    def plain(spec_list):
+        n = 0
+        t0 = time.perf_counter()
+        for sp in spec_list:
+            net = snc.Network(sp, device=local)
+            net.finalize()
+            n += int(net.view().n_syn)
+            net.close()
+        torch.cuda.synchronize()
+        return n, time.perf_counter() - t0
+
+    for sp in specs[:max(3, args.warmup)]:
+        plain([sp])
+    # Plain-path capacity on the first 200 requests of the stream.
+    n_cap, t_cap = plain(specs[:200])
+    capacity = 200 / t_cap
+    rate = 0.7 * capacity
+    arrivals = [o / rate for o in offsets]
+    torch.cuda.empty_cache()
+
+    srv = snc.Server(budget, device=local, max_slots=slots, batch_max_nets=batch_nets, batch_max_syn=batch_syn)
+    try:
+        _serve(snc, srv, specs[:32], None, 0.0)  # warm the pool and the workers
+        clocks = ClockSampler(local)
+        clocks.start()
+        torch.cuda.synchronize()
+        wall, recs, st, io = _serve(snc, srv, specs, arrivals, hold_s=0.5)
+        clk = clocks.stop()
+        sat_wall, sat_recs, sat_st, _ = _serve(snc, srv, specs, None, 0.0)
+    finally:
+        srv.close()
+    torch.cuda.empty_cache()
+    n_plain, t_plain = plain(specs)
+    n_total = sum(r[0] for r in recs)
+    lat = [r[1] for r in recs]
+    sat_lat = [r[1] for r in sat_recs]
+    line = {
+        "metric": METRIC, "value": n_total / wall, "unit": "connections/s", "n_gpus": 1,
+        "steps": 1, "warmup": max(3, args.warmup), "ms_per_step": wall * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32",
+        "data": "synthetic",
+        "config": {"workload": "served: 2,000 two-population construction requests, Poisson arrivals, "
+                               "sizes log-uniform 1e5-5e8 connections, rule uniform over the six, "
+                               "multapses on/off, 150 GB budget, networks held 0.5 s after completion",
+                   "seed": 1234, "arrival_rate_per_s": rate, "plain_capacity_req_per_s": capacity,
+                   "budget_bytes": budget, "max_slots": slots, "batch_max_nets": batch_nets,
+                   "batch_max_syn": batch_syn, "connections": n_total,
+                   "l2": "inputs larger than L2 for most of the work (requests above 1e7 connections)",
+                   "timing": "host wall clock, submit of the first request to completion of the last"},
+        "latency_ms": {"p50": _percentile(lat, 50), "p99": _percentile(lat, 99),
+                       "mean": sum(lat) / len(lat), "max": max(lat)},
+        "server": {"builds": int(st.builds), "batched_builds": int(st.batched_builds),
+                   "peak_reserved_bytes": int(st.peak_reserved_bytes)},
+        "saturated": {"value": sum(r[0] for r in sat_recs) / sat_wall, "unit": "connections/s",
+                      "note": "all 2,000 requests submitted at once, released on completion",
+                      "latency_ms": {"p50": _percentile(sat_lat, 50), "p99": _percentile(sat_lat, 99)},
+                      "builds": int(sat_st.builds) - int(st.builds),
+                      "batched_builds": int(sat_st.batched_builds) - int(st.batched_builds)},
+        "plain_sequential": {"value": n_plain / t_plain, "unit": "connections/s",
+                             "note": "the same 2,000 requests built one after another with snc_finalize"},
+        "roofline": None,
+        "gpu_launches": None,
+        "e2e": {"value": n_total / wall, "unit": "connections/s", "h2d_bytes_per_step": io["h2d"],
+                "d2h_bytes_per_step": io["d2h"],
+                "note": "the served stream through the public API; networks stay on the device"},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "served":
+        run_served(args)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -301,24 +460,37 @@ def main():
     if tr and pass_launches:
         traffic = tr["dram_bytes_per_element"] * (pass_bytes / 24.0) / pass_launches
 
-    # End to end through the public API, host buffers and wall clock.
+    # End to end through the public API with host buffers: every step
+    # plans on the host, copies the plans in, builds, and copies every
+    # connection (source, target, delay, weight: 14 B) back into page-locked
+    # host arrays, all inside the host wall-clock region.
+    max_syn = max(r[0] for r in records) if records else 0
+    host = {name: torch.empty(max(1, max_syn), dtype=dt, pin_memory=True).numpy()
+            for name, dt in (("src", torch.int32), ("tgt", torch.int32), ("delay", torch.int16),
+                             ("weight", torch.float32))}
+    host = {"src": host["src"].view(np.uint32), "tgt": host["tgt"].view(np.uint32),
+            "delay": host["delay"].view(np.uint16), "weight": host["weight"]}
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2d = d2h = 0
     n_e2e = 0
     if batched:
         nets = snc.Network.batch(specs, device=local, stream=stream)
         for net in nets:
-            n_e2e += int(net.view().n_syn)
-        st = nets[0].stats()
-        h2d, d2h = int(st.h2d_bytes), int(st.d2h_bytes)
+            n_syn = int(net.view().n_syn)
+            n_e2e += n_syn
+            net.to_host_arrays(host)
+            st = net.stats()
+            d2h += int(st.d2h_bytes)
+        h2d = int(nets[0].stats().h2d_bytes)
         for net in reversed(nets):
             net.close()
     else:
         for spec in specs:
             net = snc.Network(spec, device=local, stream=stream)
             net.finalize()
-            v = net.view()
-            n_e2e += int(v.n_syn)
+            n_e2e += int(net.view().n_syn)
+            net.to_host_arrays(host)
             st = net.stats()
             h2d += int(st.h2d_bytes)
             d2h += int(st.d2h_bytes)
@@ -353,7 +525,9 @@ def main():
         "generate_GBps": (gen_bytes / (gen_ms / 1e3)) / 1e9 if gen_ms else None,
         "gpu_launches": launches,
         "e2e": {"value": n_e2e / e2e_s, "unit": "connections/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "note": "public API, host wall clock, network left on the device"},
+                "d2h_bytes_per_step": d2h,
+                "note": "public API, host wall clock: plan, build, and copy of every connection "
+                        "(14 B each) into page-locked host arrays"},
         "clocks": clk,
     }
     if batched:

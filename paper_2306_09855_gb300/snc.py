@@ -84,11 +84,35 @@ class snc_conn_view(ctypes.Structure):
                 ("group_first", ctypes.c_void_p)]
 
 
-# Every symbol include/snc.h declares.
+class snc_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int32),
+                ("max_slots", ctypes.c_int32), ("batch_max_nets", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("batch_max_syn", ctypes.c_uint64)]
+
+
+class snc_job_times(ctypes.Structure):
+    _fields_ = [("queued_ms", ctypes.c_double), ("build_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("batch_size", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class snc_server_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "submitted", "completed", "failed", "released", "queued", "running", "builds",
+        "batched_builds", "reserved_bytes", "resident_bytes", "peak_reserved_bytes",
+        "connections_built")]
+
+
+SNC_JOB_QUEUED, SNC_JOB_RUNNING, SNC_JOB_DONE, SNC_JOB_FAILED = range(4)
+
+# Every symbol include/snc.h and include/snc_server.h declare.
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
-           "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_last_error")
+           "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_last_error",
+           "snc_server_create", "snc_server_destroy", "snc_server_submit", "snc_server_poll",
+           "snc_server_wait_any", "snc_server_context", "snc_server_times", "snc_server_release",
+           "snc_server_get_stats", "snc_estimate_build")
 
 _LIB = None
 
@@ -122,6 +146,16 @@ def load(build: bool = True):
         "snc_set_tuning": ([ctypes.POINTER(snc_tuning)], I32),
         "snc_get_tuning": ([ctypes.POINTER(snc_tuning)], I32),
         "snc_last_error": ([P], ctypes.c_char_p),
+        "snc_server_create": ([ctypes.POINTER(snc_server_config), ctypes.POINTER(P)], I32),
+        "snc_server_destroy": ([P], I32),
+        "snc_server_submit": ([P, P, ctypes.POINTER(U64)], I32),
+        "snc_server_poll": ([P, U64, ctypes.POINTER(I32), ctypes.POINTER(snc_conn_view)], I32),
+        "snc_server_wait_any": ([P, I32, ctypes.POINTER(U64)], I32),
+        "snc_server_context": ([P, U64, ctypes.POINTER(P)], I32),
+        "snc_server_times": ([P, U64, ctypes.POINTER(snc_job_times)], I32),
+        "snc_server_release": ([P, U64], I32),
+        "snc_server_get_stats": ([P, ctypes.POINTER(snc_server_stats)], I32),
+        "snc_estimate_build": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)], I32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -182,12 +216,22 @@ def snc_get_connections(ctx):
     return v
 
 
-def snc_copy_connections(ctx, n_syn):
-    out = {"src": np.empty(n_syn, np.uint32), "tgt": np.empty(n_syn, np.uint32),
-           "delay": np.empty(n_syn, np.uint16), "weight": np.empty(n_syn, np.float32)}
+def snc_copy_connections(ctx, n_syn, out=None):
+    """Copy the sorted connections into host arrays.  `out` may hold
+    preallocated (e.g. page-locked) arrays "src", "tgt" (uint32), "delay"
+    (uint16) and "weight" (float32) of at least n_syn entries each."""
+    if out is None:
+        out = {"src": np.empty(n_syn, np.uint32), "tgt": np.empty(n_syn, np.uint32),
+               "delay": np.empty(n_syn, np.uint16), "weight": np.empty(n_syn, np.float32)}
+    else:
+        want = {"src": np.uint32, "tgt": np.uint32, "delay": np.uint16, "weight": np.float32}
+        for name, dt in want.items():
+            a = out[name]
+            if a.dtype != dt or a.size < n_syn or not a.flags.c_contiguous:
+                raise ValueError("output array %r: need %d contiguous %s" % (name, n_syn, np.dtype(dt).name))
     _check(load().snc_copy_connections(ctx, out["src"].ctypes.data, out["tgt"].ctypes.data,
                                        out["delay"].ctypes.data, out["weight"].ctypes.data,
-                                       n_syn), ctx)
+                                       max(n_syn, min(a.size for a in out.values()))), ctx)
     return out
 
 
@@ -242,6 +286,68 @@ def snc_last_error(ctx=None):
     return load().snc_last_error(ctx).decode()
 
 
+def snc_estimate_build(ctx):
+    """(peak device bytes, resident device bytes, connections) of finalizing ctx."""
+    peak, res, n = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().snc_estimate_build(ctx, ctypes.byref(peak), ctypes.byref(res), ctypes.byref(n)), ctx)
+    return peak.value, res.value, n.value
+
+
+def snc_server_create(hbm_budget_bytes, device=0, max_slots=4, batch_max_nets=32, batch_max_syn=40_000_000):
+    cfg = snc_server_config(hbm_budget_bytes=int(hbm_budget_bytes), device=int(device),
+                            max_slots=int(max_slots), batch_max_nets=int(batch_max_nets), reserved=0,
+                            batch_max_syn=int(batch_max_syn))
+    h = ctypes.c_void_p()
+    _check(load().snc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def snc_server_destroy(srv):
+    _check(load().snc_server_destroy(srv))
+
+
+def snc_server_submit(srv, ctx):
+    t = ctypes.c_uint64()
+    _check(load().snc_server_submit(srv, ctx, ctypes.byref(t)))
+    return t.value
+
+
+def snc_server_poll(srv, ticket, want_view=False):
+    """(state, view or None)."""
+    state = ctypes.c_int32()
+    v = snc_conn_view()
+    _check(load().snc_server_poll(srv, ticket, ctypes.byref(state), ctypes.byref(v) if want_view else None))
+    return state.value, (v if want_view and state.value == SNC_JOB_DONE else None)
+
+
+def snc_server_wait_any(srv, timeout_ms=-1):
+    t = ctypes.c_uint64()
+    _check(load().snc_server_wait_any(srv, int(timeout_ms), ctypes.byref(t)))
+    return t.value
+
+
+def snc_server_context(srv, ticket):
+    h = ctypes.c_void_p()
+    _check(load().snc_server_context(srv, ticket, ctypes.byref(h)))
+    return h
+
+
+def snc_server_times(srv, ticket):
+    t = snc_job_times()
+    _check(load().snc_server_times(srv, ticket, ctypes.byref(t)))
+    return t
+
+
+def snc_server_release(srv, ticket):
+    _check(load().snc_server_release(srv, ticket))
+
+
+def snc_server_get_stats(srv):
+    st = snc_server_stats()
+    _check(load().snc_server_get_stats(srv, ctypes.byref(st)))
+    return st
+
+
 # ----------------------------------------------------------------------------
 # PyTorch as device-memory provider.
 # ----------------------------------------------------------------------------
@@ -279,6 +385,84 @@ def _syn_struct(pj):
                                         float(pj.weight.std)),
                         delay_ms=snc_dist(DIST_ID[pj.delay.kind], 0, float(pj.delay.mean),
                                           float(pj.delay.std)))
+
+
+def create_context(spec, device=0, stream_ptr=None, allocator=None):
+    """snc_create + CreatePopulation + Connect calls of a NetworkSpec (no finalize)."""
+    cfg = snc_config(seed=int(spec.seed) & 0xFFFFFFFFFFFFFFFF, dt_ms=float(spec.dt),
+                     device=device, reserved=0, stream=stream_ptr,
+                     allocator=ctypes.pointer(allocator) if allocator is not None else None)
+    ctx = snc_create(cfg)
+    try:
+        for n in spec.populations:
+            snc_create_population(ctx, int(n))
+        for pj in spec.projections:
+            snc_connect(ctx, snc_range(*pj.src), snc_range(*pj.tgt), _rule_struct(pj), _syn_struct(pj))
+    except Exception:
+        snc_destroy(ctx)
+        raise
+    return ctx
+
+
+class Server:
+    """The served form (include/snc_server.h): submit NetworkSpecs, collect
+    finished networks, release them.  Device memory comes from the server's
+    own pool; results stay on the device until released."""
+
+    def __init__(self, hbm_budget_bytes, device=0, max_slots=4, batch_max_nets=32,
+                 batch_max_syn=40_000_000):
+        self.device = device
+        self.srv = snc_server_create(hbm_budget_bytes, device, max_slots, batch_max_nets, batch_max_syn)
+
+    def submit(self, spec):
+        ctx = create_context(spec, self.device)
+        try:
+            return snc_server_submit(self.srv, ctx)
+        except Exception:
+            snc_destroy(ctx)
+            raise
+
+    def wait_any(self, timeout_ms=-1):
+        return snc_server_wait_any(self.srv, timeout_ms)
+
+    def state(self, ticket):
+        return snc_server_poll(self.srv, ticket)[0]
+
+    def view(self, ticket):
+        return snc_server_poll(self.srv, ticket, want_view=True)[1]
+
+    def times(self, ticket):
+        return snc_server_times(self.srv, ticket)
+
+    def to_host(self, ticket):
+        """The finished network copied to host numpy arrays (as Network.to_host)."""
+        import torch
+        ctx = snc_server_context(self.srv, ticket)
+        v = self.view(ticket)
+        out = snc_copy_connections(ctx, int(v.n_syn))
+        t = _view_tensors(v, torch)
+        out["row_ptr"] = t["row_ptr"].cpu().numpy()
+        out["group_ptr"] = t["group_ptr"].cpu().numpy()
+        out["group_first"] = t["group_first"].cpu().numpy()
+        out["n_groups"] = int(v.n_groups)
+        return out
+
+    def release(self, ticket):
+        snc_server_release(self.srv, ticket)
+
+    def stats(self):
+        return snc_server_get_stats(self.srv)
+
+    def close(self):
+        if self.srv:
+            snc_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Network:
@@ -338,6 +522,13 @@ class Network:
         out["group_first"] = t["group_first"].cpu().numpy()
         out["n_groups"] = int(v.n_groups)
         return out
+
+    def to_host_arrays(self, out):
+        """Copy the connections into caller-owned host arrays (see
+        snc_copy_connections); returns the number of connections."""
+        n = int(self.view().n_syn)
+        snc_copy_connections(self.ctx, n, out)
+        return n
 
     def stage_times(self):
         return snc_stage_times(self.ctx)
