@@ -77,6 +77,25 @@ struct Projection {
   uint32_t max_step = 1;
 };
 
+// Device-memory estimate of finalizing one context (snc_runtime.cu).
+struct BuildEstimate {
+  uint64_t n_syn;           // connections (an upper bound for Bernoulli projections)
+  uint64_t peak_bytes;      // device memory at the build's peak
+  uint64_t resident_bytes;  // device memory the finished network keeps
+  uint64_t n_nodes;
+  uint32_t max_step;        // largest delay step
+};
+snc_status estimate_build(const snc_ctx* c, BuildEstimate* e);
+
+// Runtime hooks of the server (snc_runtime.cu).  rebind_build replaces the
+// stream (and, when alloc != nullptr, the allocator) a context builds with;
+// allowed before finalize, and after a finished build to pick the stream its
+// memory is released on.
+void rebind_build(snc_ctx* c, cudaStream_t stream, const snc_allocator* alloc);
+uint64_t storage_live_bytes(const snc_ctx* c);  // device bytes the context's storage holds
+int ctx_device(const snc_ctx* c);
+bool ctx_finalized(const snc_ctx* c);
+
 // Host threshold tables (tables.cpp).
 int delay_thresholds(double mu, double sigma, double dt, std::vector<uint32_t>& thr, uint32_t& base);
 int binomial_thresholds(uint64_t n, double p, std::vector<uint32_t>& thr, uint64_t& base);

@@ -311,6 +311,70 @@ namespace snc {
 // Lets other translation units report context-free failures through
 // snc_last_error(NULL).
 void set_last_error(const char* msg) { g_last_error = msg; }
+
+snc_status estimate_build(const snc_ctx* c, BuildEstimate* e) {
+  if (!c || !e) return SNC_ERR_INVALID_ARG;
+  uint64_t n = 0, redraw_slots = 0, redraw_table = 0, primaries = 0;
+  uint32_t max_step = 1;
+  for (const Projection& p : c->projs) {
+    max_step = std::max(max_step, p.max_step);
+    if (p.rule.kind == SNC_PAIRWISE_BERNOULLI) {
+      // Hard bound: every target draws at most base + table length sources
+      // (Sec. 4 reading of the Bernoulli rule); the estimate takes the mean
+      // plus ten standard deviations of the total when that is lower.
+      const uint64_t hard = static_cast<uint64_t>(p.tgt.n) *
+                            std::max(p.b_base[0] + p.b_thr[0].size(), p.b_base[1] + p.b_thr[1].size());
+      const double mean = static_cast<double>(p.tgt.n) * p.src.n * p.rule.p;
+      const double soft = mean + 10.0 * std::sqrt(mean * (1.0 - p.rule.p)) + 1024.0;
+      n += std::min<uint64_t>(hard, static_cast<uint64_t>(soft));
+      primaries += p.tgt.n;
+    } else {
+      n += p.count;
+      if (is_sampler(p)) primaries += (p.rule.kind == SNC_FIXED_OUTDEGREE) ? p.src.n : p.tgt.n;
+      if (is_total_redraw(p)) {
+        redraw_slots += p.count;
+        if (!p.rule.allow_multapses) {
+          uint64_t cap = 1;
+          while (cap < 2 * p.count + 64) cap <<= 1;
+          redraw_table += 2 * cap;  // keys and (when not packed) values
+        }
+      }
+    }
+  }
+  const uint64_t N = c->n_nodes;
+  const uint64_t gc = std::max<uint64_t>(1, std::min<uint64_t>(n, N * (static_cast<uint64_t>(max_step) + 1)));
+  KeyLayout lay{std::max(1, bit_width(N > 0 ? N - 1 : 0)), std::max(1, bit_width(max_step)),
+                std::max(1, bit_width(N > 0 ? N - 1 : 0))};
+  const uint64_t scratch = lay.total_bits() <= 64 ? sort_scratch_bytes(n, plan_passes(lay.total_bits())) : 0;
+  // Generation and sort: two key/value buffers, sort scratch, the redraw
+  // lists and tables, per-primary offsets.
+  const uint64_t gen = 24 * n + scratch + 25 * redraw_slots + 8 * redraw_table + 16 * (primaries + 1);
+  // Index: sorted keys and weights, unpacked targets and delays, group
+  // starts, row and group pointers (twice for batch members), block scans.
+  const uint64_t index = 18 * n + n / 8 + 8 * gc + 32 * (N + 1) + 16 * (primaries + 1);
+  // Allocation granularity and the small per-build arrays.
+  const uint64_t slack = 96ull << 20;
+  e->n_syn = n;
+  e->peak_bytes = std::max(gen, index) + slack;
+  e->resident_bytes = 10 * n + 8 * gc + 32 * (N + 1) + slack;
+  e->n_nodes = N;
+  e->max_step = max_step;
+  return SNC_OK;
+}
+
+void rebind_build(snc_ctx* c, cudaStream_t stream, const snc_allocator* alloc) {
+  c->stream = stream;
+  c->cfg.stream = stream;
+  c->store->stream = stream;
+  if (alloc) {
+    c->store->alloc = *alloc;
+    c->store->custom_alloc = true;
+  }
+}
+
+uint64_t storage_live_bytes(const snc_ctx* c) { return c->store ? c->store->live_bytes : 0; }
+int ctx_device(const snc_ctx* c) { return c->device; }
+bool ctx_finalized(const snc_ctx* c) { return c->finalized; }
 }  // namespace snc
 
 extern "C" {
@@ -614,11 +678,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   const size_t table_smem =
       hist_bytes + static_cast<size_t>(max_delay_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
   if (chunk > 0) {
-    static bool configured = false;
-    if (!configured) {
-      SNC_CUDA(c, cudaFuncSetAttribute(gen_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-      configured = true;
-    }
+    // Set on every launch: the attribute is per function and device, and
+    // builds may run on several threads and devices.
+    SNC_CUDA(c, cudaFuncSetAttribute(gen_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     const uint64_t grid = std::min<uint64_t>(chunk, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm);
     gen_direct_kernel<<<static_cast<unsigned>(grid), kGenThreads, table_smem, st>>>(g);
     ++c->stats.kernel_launches;
@@ -663,12 +725,10 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       const int warps = static_cast<int>(std::min<size_t>(8, (kSamplerSmem - hist_bytes - 16) / per_warp));
       if (warps < 1) return fail(c, SNC_ERR_UNSUPPORTED, "sampler bitmap does not fit shared memory");
       const size_t smem = hist_bytes + static_cast<size_t>(warps) * per_warp + 16;
-      static bool sconf = false;
-      if (!sconf) {
-        SNC_CUDA(c, cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(kSamplerSmem)));
-        sconf = true;
-      }
+      // Set on every launch: the attribute is per function and device, and
+      // builds may run on several threads and devices.
+      SNC_CUDA(c, cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSamplerSmem)));
       const uint64_t want_blocks = (sprefix.back() + warps - 1) / warps;
       const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(want_blocks, static_cast<uint64_t>(c->sms) * 16));
       sampler_kernel<<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(s);
@@ -771,11 +831,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       ge.max_delay_len = max_len;
       const size_t tsm =
           hist_bytes + static_cast<size_t>(max_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
-      static bool econf = false;
-      if (!econf) {
-        SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-        econf = true;
-      }
+      // Set on every launch: the attribute is per function and device, and
+      // builds may run on several threads and devices.
+      SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
       const unsigned eg = static_cast<unsigned>(
           std::min<uint64_t>(n_chunks_r, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm));
       total_emit_kernel<<<eg, kGenThreads, tsm, st>>>(ge, a, n_chunks_r);

@@ -716,13 +716,11 @@ __global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) oneswee
 template <int BITS>
 cudaError_t launch_onesweep_tma(const OnesweepArgs& a, int sms, cudaStream_t st) {
   using C = OnesweepTma<BITS>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(C::kSmem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // Set on every launch: the attribute is per function and device, and
+  // builds may run on several threads and devices.
+  cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(C::kSmem));
+  if (e != cudaSuccess) return e;
   const uint64_t tiles = (a.n + C::TILE - 1) / C::TILE;
   const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
   const uint64_t grid = tiles < resident ? tiles : resident;
@@ -733,13 +731,11 @@ cudaError_t launch_onesweep_tma(const OnesweepArgs& a, int sms, cudaStream_t st)
 template <int BITS, int G>
 cudaError_t launch_onesweep(const OnesweepArgs& a, int sms, cudaStream_t st) {
   using C = Onesweep<BITS, G>;
-  static bool configured = false;  // the attribute is per function; set once per process
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(C::kSmem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // Set on every launch: the attribute is per function and device, and
+  // builds may run on several threads and devices.
+  cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(C::kSmem));
+  if (e != cudaSuccess) return e;
   const uint64_t units = (a.n + C::GROUP - 1) / C::GROUP;
   const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
   const uint64_t grid = units < resident ? units : resident;
@@ -876,13 +872,11 @@ cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uin
       return e;
     const HistPlan plan = hist_plan(sp, hist);
     const size_t hist_smem = hist_smem_bytes(plan);
-    static bool hist_configured = false;
-    if (!hist_configured) {
-      e = cudaFuncSetAttribute(radix_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(kMaxPasses * kMaxRadix * sizeof(uint32_t)));
-      if (e != cudaSuccess) return e;
-      hist_configured = true;
-    }
+    // Set on every launch: the attribute is per function and device, and
+    // builds may run on several threads and devices.
+    e = cudaFuncSetAttribute(radix_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kMaxPasses * kMaxRadix * sizeof(uint32_t)));
+    if (e != cudaSuccess) return e;
     radix_hist_kernel<<<sms * 2, 512, hist_smem, st>>>(keys_in, n, plan);
   }
   radix_digit_scan_kernel<<<sp.n_passes, kDigitScanThreads, 0, st>>>(hist, start);

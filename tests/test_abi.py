@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads, and exports every symbol that
-include/snc.h declares (no GPU needed: no compute call is made)."""
+include/*.h declare (no GPU needed: no compute call is made)."""
 import os
 import re
 
@@ -9,7 +9,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    text = open(os.path.join(ROOT, "include", "snc.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     return sorted(set(re.findall(r"^\s*(?:snc_status|const char\*)\s+(snc_\w+)\s*\(", text, re.M)))
 
 
@@ -40,3 +41,20 @@ def test_sort_argument_checks_need_no_gpu():
         snc.snc_radix_sort_pairs(0, 0, 0, 0, 10, 0)
     assert e.value.name == "INVALID_ARG"
     snc.snc_radix_sort_pairs(0, 0, 0, 0, 0, 12)  # empty input: nothing to do
+
+
+def test_server_config_checks_need_no_gpu():
+    from paper_2306_09855_gb300 import snc
+    for kw in ({"hbm_budget_bytes": 0}, {"hbm_budget_bytes": 1 << 30, "max_slots": 0},
+               {"hbm_budget_bytes": 1 << 30, "max_slots": 65},
+               {"hbm_budget_bytes": 1 << 30, "batch_max_nets": 0},
+               {"hbm_budget_bytes": 1 << 30, "batch_max_nets": 257}):
+        with pytest.raises(snc.SncError) as e:
+            snc.snc_server_create(**kw)
+        assert e.value.name == "INVALID_ARG"
+    for call in (lambda: snc.snc_server_submit(None, None), lambda: snc.snc_server_wait_any(None),
+                 lambda: snc.snc_server_get_stats(None), lambda: snc.snc_server_release(None, 1)):
+        with pytest.raises(snc.SncError) as e:
+            call()
+        assert e.value.name == "INVALID_ARG"
+    snc.snc_server_destroy(None)
