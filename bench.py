@@ -359,22 +359,17 @@ def main():
         run_served(args)
         return
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2306_09855_gb300 import replicas
+    rank, world, local = replicas.world()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    replicas.init("nccl")
     from paper_2306_09855_gb300 import snc
     snc.load()
     tuning = snc.snc_set_tuning(sort_digit_bits=args.sort_digit_bits, sort_group_tiles=args.sort_group_tiles)
     specs, config = workload_specs(args.workload)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+    barrier = replicas.barrier
 
     batched = args.workload == "batched"
     tune_info = None
@@ -426,14 +421,7 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([ms, float(n_total)], device="cuda", dtype=torch.float64)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        ms, n_all = float(tmax[0]), float(t[1])
-    else:
-        n_all = float(n_total)
+    ms, n_all = replicas.reduce_timing(ms, n_total, device="cuda")
     value = n_all / (ms / 1e3)
 
     # Dominant kernel: the onesweep radix pass.  Algorithmic bytes per launch:
@@ -496,6 +484,7 @@ def main():
             d2h += int(st.d2h_bytes)
             net.close()
     e2e_s = time.perf_counter() - t0
+    e2e_ms_all, n_e2e_all = replicas.reduce_timing(e2e_s * 1e3, n_e2e, device="cuda")
     sequential = None
     if batched:
         from paper_2306_09855_gb300 import autotune
@@ -524,7 +513,7 @@ def main():
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
         "generate_GBps": (gen_bytes / (gen_ms / 1e3)) / 1e9 if gen_ms else None,
         "gpu_launches": launches,
-        "e2e": {"value": n_e2e / e2e_s, "unit": "connections/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": n_e2e_all / (e2e_ms_all / 1e3), "unit": "connections/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "note": "public API, host wall clock: plan, build, and copy of every connection "
                         "(14 B each) into page-locked host arrays"},
