@@ -166,7 +166,7 @@ def generate(spec):
 
 
 def sort_index(n_nodes, src, tgt, delay, weight):
-    """Stable sort by (source, delay, target) and the CSR / group index."""
+    """Stable sort by (source, delay) and the CSR / group index."""
     src = np.array(src, dtype=np.uint32)
     tgt = np.array(tgt, dtype=np.uint32)
     delay = np.array(delay, dtype=np.uint16)

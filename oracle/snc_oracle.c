@@ -15,8 +15,8 @@
  *      i_newconns (Sec. 2.1, Eqs. 2-3 and the per-rule index formulas);
  *   3. weight and integer delay of every connection (Sec. 2.1, last
  *      paragraph: delay = round(d / dt), at least one step);
- *   4. a stable sort by (source, delay, target) (Sec. 2.2: source first,
- *      delay second; target and generation order fix the rest);
+ *   4. a stable sort by (source, delay) (Sec. 2.2: source first, delay
+ *      second; connections equal in both keep their generation order);
  *   5. the group index: a connection starts a group when its source or its
  *      delay differs from the previous one; G_i groups per source and
  *      p_i = sum_{j<i} G_j (Sec. 2.2, Eq. for p_i).
@@ -798,13 +798,13 @@ static int cmp_rec(const void* x, const void* y) {
   const or_rec* b = (const or_rec*)y;
   if (a->s != b->s) return a->s < b->s ? -1 : 1;
   if (a->d != b->d) return a->d < b->d ? -1 : 1;
-  if (a->t != b->t) return a->t < b->t ? -1 : 1;
   if (a->gen != b->gen) return a->gen < b->gen ? -1 : 1;
   return 0;
 }
 
-/* Sorts the n connections (in place) by (source, delay, target), ties in
- * generation order; then builds
+/* Sorts the n connections (in place) by source, then delay (the two keys
+ * of Sec. 2.2), connections with equal source and delay in generation order
+ * (a stable sort); then builds
  *   row_ptr[i]  = number of connections with source < i,   i = 0..n_nodes;
  *   group_first = positions q where q == 0 or (s, d)[q] != (s, d)[q-1];
  *   group_ptr[i] = p_i = sum_{j<i} G_j, G_j the groups of source j.
