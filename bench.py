@@ -425,17 +425,19 @@ def main():
     value = n_all / (ms / 1e3)
 
     # Dominant kernel: the onesweep radix pass.  Algorithmic bytes per launch:
-    # read key (8 B) + value (4 B), write key + value = 24 B per connection.
+    # read and write the key ((source, delay): 4 B, or 8 B above 32 bits)
+    # and the value ((target, weight): 8 B): 24 B (32 B) per connection.
     pass_bytes, pass_ms, pass_launches = 0.0, 0.0, 0
     gen_bytes, gen_ms, launches = 0.0, 0.0, 0
     stage_sum = {}
     for n_syn, times, npass, st in records:
         launches += int(st.kernel_launches)
+        pair = (4.0 if st.key_bits <= 32 else 8.0) + 8.0
         for k in range(npass):
-            pass_bytes += 24.0 * n_syn
+            pass_bytes += 2.0 * pair * n_syn
             pass_ms += times[3 + k]
             pass_launches += 1
-        gen_bytes += 12.0 * n_syn
+        gen_bytes += pair * n_syn
         gen_ms += times[1]
         names = ["count", "generate", "histogram"] + ["pass%d" % k for k in range(npass)] + ["index"]
         for nm, t in zip(names, times):
@@ -446,7 +448,7 @@ def main():
     traffic = None
     tr = committed_traffic()
     if tr and pass_launches:
-        traffic = tr["dram_bytes_per_element"] * (pass_bytes / 24.0) / pass_launches
+        traffic = tr["dram_bytes_per_element"] * (sum(r[0] * r[2] for r in records)) / pass_launches
 
     # End to end through the public API with host buffers: every step
     # plans on the host, copies the plans in, builds, and copies every

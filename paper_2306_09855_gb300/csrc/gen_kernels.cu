@@ -87,9 +87,12 @@ __device__ __forceinline__ uint32_t hist_words(const GenArgs& a) {
 __device__ __forceinline__ void store(const GenArgs& a, const BlockHist& h, uint64_t pos, uint32_t s, uint32_t d,
                                       uint32_t t, uint32_t wbits) {
   if (!SNC_IN_BOUNDS(a.err, 1u, pos, a.cap)) return;
-  const uint64_t key = pack_key(s, d, t, a.layout.tgt_bits, a.layout.delay_bits);
-  a.keys[pos] = key;
-  a.vals[pos] = wbits;
+  const uint64_t key = pack_key(s, d, a.layout.delay_bits);
+  if (a.key32)
+    static_cast<uint32_t*>(a.keys)[pos] = static_cast<uint32_t>(key);
+  else
+    static_cast<uint64_t*>(a.keys)[pos] = key;
+  a.vals[pos] = pack_value(t, wbits);
   hist_add(h.sh, h.r, key);
 }
 

@@ -24,8 +24,9 @@ struct GenArgs {
   const uint16_t* guide_blob;
   uint32_t max_delay_len;  // largest delay table among the launched projections
   KeyLayout layout;
-  uint64_t* keys;
-  uint32_t* vals;
+  void* keys;      // uint32_t[cap] when key32, else uint64_t[cap]: (source, delay)
+  uint64_t* vals;  // (target, weight bits)
+  int key32;
   uint64_t cap;    // entries of keys / vals
   uint32_t* err;   // device error block (bounds checks)
   HistPlan hist;   // digit counts of the sort's passes, accumulated as keys are written

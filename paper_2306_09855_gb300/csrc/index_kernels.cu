@@ -1,5 +1,5 @@
-// index_kernels.cu -- unpacking of the sorted keys and the group index of
-// Sec. 2.2.
+// index_kernels.cu -- unpacking of the sorted (key, value) pairs into
+// target / delay / weight arrays, and the group index of Sec. 2.2.
 //
 // A connection starts a group when its source or its delay differs from the
 // previous connection's.  group_first[g] is the position of the g-th group
@@ -17,57 +17,77 @@
 
 namespace snc {
 
-// Unpack of the sorted keys and group starts.  Block b covers keys
+// Unpack of the sorted pairs and group starts.  Block b covers positions
 // [b * kIndexTile, (b + 1) * kIndexTile); thread t of a block owns the
-// kIndexItems consecutive keys starting at t * kIndexItems.  Writes target
-// and delay (vector stores), one bit per key in `starts` (bit i of the
-// bitmap <-> key i) and the number of group starts of the block.
+// kIndexItems consecutive positions starting at t * kIndexItems.  Writes
+// target, delay and weight (vector stores), one bit per position in
+// `starts` (bit i of the bitmap <-> position i) and the number of group
+// starts of the block.  A group starts where the (source, delay) key
+// changes.
+template <typename K>
 __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a) {
   __shared__ uint32_t warp_cnt[kIndexThreads / 32];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const int sd_shift = a.tgt_bits;
-  const uint64_t node_mask = (1ull << a.tgt_bits) - 1;
+  const K* keys = static_cast<const K*>(a.keys);
   const uint32_t delay_mask = (1u << a.delay_bits) - 1u;
   const uint64_t n_blocks = (a.n + kIndexTile - 1) / kIndexTile;
+  constexpr int KPV = 16 / sizeof(K);  // keys per 16-byte vector
   for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
     const uint64_t base = blk * kIndexTile + static_cast<uint64_t>(tid) * kIndexItems;
-    uint64_t key[kIndexItems];
+    K key[kIndexItems];
+    uint64_t val[kIndexItems];
     const bool full = base + kIndexItems <= a.n;
     if (full) {
-      const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(a.keys + base);
+      const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
+#pragma unroll
+      for (int k = 0; k < kIndexItems / KPV; ++k) {
+        const uint4 v = __ldg(k4 + k);
+        const K* kv = reinterpret_cast<const K*>(&v);
+#pragma unroll
+        for (int j = 0; j < KPV; ++j) key[k * KPV + j] = kv[j];
+      }
+      const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(a.vals + base);
 #pragma unroll
       for (int k = 0; k < kIndexItems / 2; ++k) {
-        const ulonglong2 v = __ldg(k2 + k);
-        key[2 * k] = v.x;
-        key[2 * k + 1] = v.y;
+        const ulonglong2 v = __ldg(v2 + k);
+        val[2 * k] = v.x;
+        val[2 * k + 1] = v.y;
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < kIndexItems; ++k) key[k] = base + k < a.n ? __ldg(a.keys + base + k) : ~0ull;
+      for (int k = 0; k < kIndexItems; ++k) {
+        key[k] = base + k < a.n ? __ldg(keys + base + k) : K(0);
+        val[k] = base + k < a.n ? __ldg(a.vals + base + k) : 0ull;
+      }
     }
     // Predecessor of this thread's first key: the previous lane's last key,
     // or one extra load for lane 0.
-    uint64_t prev = __shfl_up_sync(0xffffffffu, key[kIndexItems - 1], 1);
-    if (lane == 0) prev = (base > 0 && base < a.n) ? __ldg(a.keys + base - 1) : 0ull;
+    K prev = __shfl_up_sync(0xffffffffu, key[kIndexItems - 1], 1);
+    if (lane == 0) prev = (base > 0 && base < a.n) ? __ldg(keys + base - 1) : K(0);
     uint32_t bits = 0;
 #pragma unroll
     for (int k = 0; k < kIndexItems; ++k) {
       const uint64_t q = base + k;
-      const uint64_t before = k == 0 ? prev : key[k - 1];
-      const bool start = q < a.n && (q == 0 || (key[k] >> sd_shift) != (before >> sd_shift));
+      const K before = k == 0 ? prev : key[k - 1];
+      const bool start = q < a.n && (q == 0 || key[k] != before);
       bits |= (start ? 1u : 0u) << k;
     }
     if (full) {
-      uint32_t tv[kIndexItems];
+      uint32_t tv[kIndexItems], wv[kIndexItems];
       uint16_t dv[kIndexItems];
 #pragma unroll
       for (int k = 0; k < kIndexItems; ++k) {
-        tv[k] = static_cast<uint32_t>(key[k] & node_mask);
-        dv[k] = static_cast<uint16_t>((key[k] >> sd_shift) & delay_mask);
+        tv[k] = static_cast<uint32_t>(val[k] >> 32);
+        wv[k] = static_cast<uint32_t>(val[k]);
+        dv[k] = static_cast<uint16_t>(static_cast<uint32_t>(key[k]) & delay_mask);
       }
       uint4* t4 = reinterpret_cast<uint4*>(a.target + base);
+      uint4* w4 = reinterpret_cast<uint4*>(a.weight + base);
 #pragma unroll
-      for (int k = 0; k < kIndexItems / 4; ++k) t4[k] = make_uint4(tv[4 * k], tv[4 * k + 1], tv[4 * k + 2], tv[4 * k + 3]);
+      for (int k = 0; k < kIndexItems / 4; ++k) {
+        t4[k] = make_uint4(tv[4 * k], tv[4 * k + 1], tv[4 * k + 2], tv[4 * k + 3]);
+        w4[k] = make_uint4(wv[4 * k], wv[4 * k + 1], wv[4 * k + 2], wv[4 * k + 3]);
+      }
       uint4* d4 = reinterpret_cast<uint4*>(a.delay + base);
 #pragma unroll
       for (int k = 0; k < kIndexItems / 8; ++k)
@@ -79,8 +99,9 @@ __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a
 #pragma unroll
       for (int k = 0; k < kIndexItems; ++k)
         if (base + k < a.n) {
-          a.target[base + k] = static_cast<uint32_t>(key[k] & node_mask);
-          a.delay[base + k] = static_cast<uint16_t>((key[k] >> sd_shift) & delay_mask);
+          a.target[base + k] = static_cast<uint32_t>(val[k] >> 32);
+          a.weight[base + k] = static_cast<uint32_t>(val[k]);
+          a.delay[base + k] = static_cast<uint16_t>(static_cast<uint32_t>(key[k]) & delay_mask);
         }
     }
     // Bitmap: kIndexItems (= 8) bits per thread, four threads per word.
@@ -139,14 +160,15 @@ __global__ void __launch_bounds__(kIndexThreads) index_groups_kernel(IndexArgs a
 
 // row_ptr[i] = first position whose source is >= i; group_ptr[i] = number of
 // group starts before row_ptr[i].  i = 0 .. n_nodes.
+template <typename K>
 __global__ void node_index_kernel(NodeIndexArgs a) {
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i > a.n_nodes) return;
-  const int src_shift = a.tgt_bits + a.delay_bits;
+  const K* keys = static_cast<const K*>(a.keys);
   uint64_t lo = 0, hi = a.n;
   while (lo < hi) {
     const uint64_t mid = (lo + hi) >> 1;
-    if ((a.keys[mid] >> src_shift) < i) lo = mid + 1; else hi = mid;
+    if ((static_cast<uint64_t>(keys[mid]) >> a.delay_bits) < i) lo = mid + 1; else hi = mid;
   }
   if (!SNC_IN_BOUNDS(nullptr, 21u, lo, a.n + 1)) return;
   a.row_ptr[i] = lo;
@@ -157,6 +179,23 @@ __global__ void node_index_kernel(NodeIndexArgs a) {
     if (a.group_first[mid] < lo) glo = mid + 1; else ghi = mid;
   }
   a.group_ptr[i] = glo;
+}
+
+cudaError_t launch_index_unpack(const IndexArgs& a, unsigned grid, cudaStream_t st) {
+  if (a.key32)
+    index_unpack_kernel<uint32_t><<<grid, kIndexThreads, 0, st>>>(a);
+  else
+    index_unpack_kernel<uint64_t><<<grid, kIndexThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_index(const NodeIndexArgs& a, cudaStream_t st) {
+  const unsigned grid = static_cast<unsigned>((a.n_nodes + 1 + 255) / 256);
+  if (a.key32)
+    node_index_kernel<uint32_t><<<grid, 256, 0, st>>>(a);
+  else
+    node_index_kernel<uint64_t><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 // Source of every connection from row_ptr (for host copies).

@@ -12,11 +12,14 @@ constexpr int kIndexItems = 8;
 constexpr int kIndexTile = kIndexThreads * kIndexItems;
 
 struct IndexArgs {
-  const uint64_t* keys;  // sorted packed keys
+  const void* keys;          // sorted (source, delay) keys: uint32_t when key32, else uint64_t
+  const uint64_t* vals;      // sorted (target, weight) values
+  int key32;
   uint64_t n;
-  int tgt_bits, delay_bits;
+  int delay_bits;
   uint32_t* target;
   uint16_t* delay;
+  uint32_t* weight;          // fp32 bits
   uint32_t* starts;          // group-start bitmap, kIndexTile / 32 words per block
   uint32_t* block_counts;    // group starts per block
   const uint64_t* block_offsets;  // exclusive scan of block_counts (n_blocks + 1)
@@ -27,10 +30,11 @@ struct IndexArgs {
 };
 
 struct NodeIndexArgs {
-  const uint64_t* keys;
+  const void* keys;
+  int key32;
   uint64_t n;
   uint64_t n_nodes;
-  int tgt_bits, delay_bits;
+  int delay_bits;
   const uint64_t* group_first;
   uint64_t group_cap;
   const uint64_t* n_groups;
@@ -38,9 +42,10 @@ struct NodeIndexArgs {
   uint64_t* group_ptr;
 };
 
-__global__ void index_unpack_kernel(IndexArgs a);
+// Launch the unpack / node-index kernel for the key width of the build.
+cudaError_t launch_index_unpack(const IndexArgs& a, unsigned grid, cudaStream_t st);
 __global__ void index_groups_kernel(IndexArgs a);
-__global__ void node_index_kernel(NodeIndexArgs a);
+cudaError_t launch_node_index(const NodeIndexArgs& a, cudaStream_t st);
 __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes, uint32_t* src);
 
 // Batches: per-network CSR offsets relative to the network's first

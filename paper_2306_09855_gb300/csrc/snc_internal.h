@@ -47,18 +47,25 @@ struct DevProj {
   uint32_t row_len;         // all_to_all: connections per source row (full row)
 };
 
-// Bit layout of the packed sort key: source | delay step | target.  The
-// source is a global node id of the build; the target is local to its
-// network (equal to the global id when a single network is built).
+// Sort key and value of a connection.  The key packs source | delay step
+// (Sec. 2.2 sorts by these two keys); it is 32 bits wide when the two fit,
+// else 64.  The source is a global node id of the build.  The value packs
+// the target (local to its network, equal to the global id when a single
+// network is built) above the fp32 weight's bits.
 struct KeyLayout {
   int src_bits;
   int delay_bits;
-  int tgt_bits;
-  int total_bits() const { return src_bits + delay_bits + tgt_bits; }
+  int tgt_bits;  // bits of the largest member-local target (value field: 32)
+  int total_bits() const { return src_bits + delay_bits; }
+  bool key32() const { return total_bits() <= 32; }
 };
 
-__host__ __device__ inline uint64_t pack_key(uint32_t s, uint32_t d, uint32_t t_local, int tb, int db) {
-  return (static_cast<uint64_t>(s) << (tb + db)) | (static_cast<uint64_t>(d) << tb) | t_local;
+__host__ __device__ inline uint64_t pack_key(uint32_t s, uint32_t d, int db) {
+  return (static_cast<uint64_t>(s) << db) | d;
+}
+
+__host__ __device__ inline uint64_t pack_value(uint32_t t_local, uint32_t wbits) {
+  return (static_cast<uint64_t>(t_local) << 32) | wbits;
 }
 
 // Host-side projection record.

@@ -345,13 +345,14 @@ snc_status estimate_build(const snc_ctx* c, BuildEstimate* e) {
   const uint64_t gc = std::max<uint64_t>(1, std::min<uint64_t>(n, N * (static_cast<uint64_t>(max_step) + 1)));
   KeyLayout lay{std::max(1, bit_width(N > 0 ? N - 1 : 0)), std::max(1, bit_width(max_step)),
                 std::max(1, bit_width(N > 0 ? N - 1 : 0))};
-  const uint64_t scratch = lay.total_bits() <= 64 ? sort_scratch_bytes(n, plan_passes(lay.total_bits())) : 0;
+  const uint64_t scratch = sort_scratch_bytes(n, plan_passes(lay.total_bits()));
+  const uint64_t pair = (lay.key32() ? 4 : 8) + 8;  // key + (target, weight) value
   // Generation and sort: two key/value buffers, sort scratch, the redraw
   // lists and tables, per-primary offsets.
-  const uint64_t gen = 24 * n + scratch + 25 * redraw_slots + 8 * redraw_table + 16 * (primaries + 1);
-  // Index: sorted keys and weights, unpacked targets and delays, group
+  const uint64_t gen = 2 * pair * n + scratch + 25 * redraw_slots + 8 * redraw_table + 16 * (primaries + 1);
+  // Index: sorted pairs, unpacked targets, delays and weights, group
   // starts, row and group pointers (twice for batch members), block scans.
-  const uint64_t index = 18 * n + n / 8 + 8 * gc + 32 * (N + 1) + 16 * (primaries + 1);
+  const uint64_t index = (pair + 10) * n + n / 8 + 8 * gc + 32 * (N + 1) + 16 * (primaries + 1);
   // Allocation granularity and the small per-build arrays.
   const uint64_t slack = 96ull << 20;
   e->n_syn = n;
@@ -646,10 +647,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // Buffers: generated keys/values, the sort's second buffer, outputs.
   const uint64_t n = n_total;
   c->passes = plan_passes(c->layout.total_bits());
-  uint64_t* keys_a = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
-  uint32_t* vals_a = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
-  uint64_t* keys_b = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
-  uint32_t* vals_b = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+  const bool key32 = c->layout.key32();
+  const size_t key_bytes = key32 ? sizeof(uint32_t) : sizeof(uint64_t);
+  void* keys_a = dev_alloc(c, n * key_bytes);
+  uint64_t* vals_a = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
+  void* keys_b = dev_alloc(c, n * key_bytes);
+  uint64_t* vals_b = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
   void* sort_scratch = dev_alloc(c, sort_scratch_bytes(n, c->passes));
   if (!keys_a || !vals_a || !keys_b || !vals_b || !sort_scratch)
     return fail(c, SNC_ERR_OOM, "device allocation failed (%llu connections)", static_cast<unsigned long long>(n));
@@ -672,6 +675,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   g.layout = c->layout;
   g.keys = keys_a;
   g.vals = vals_a;
+  g.key32 = key32 ? 1 : 0;
   g.cap = n;
   g.err = S.d_err;
   g.hist = hplan;
@@ -851,16 +855,23 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   }
   cudaEventRecord(S.ev[S.n_ev++], st);
 
-  // Sort by (source, delay, target).  The passes ping-pong between the two
-  // buffers; the result lands in (keys_b, vals_b) for an odd number of
-  // passes and back in (keys_a, vals_a) for an even number.
+  // Stable sort by (source, delay): equal keys keep generation order.  The
+  // passes ping-pong between the two buffers; the result lands in
+  // (keys_b, vals_b) for an odd number of passes and back in (keys_a,
+  // vals_a) for an even number.
   const bool odd = (c->passes.n_passes & 1) != 0;
-  uint64_t* keys_res = odd ? keys_b : keys_a;
-  uint32_t* vals_res = odd ? vals_b : vals_a;
-  uint64_t* keys_oth = odd ? keys_a : keys_b;
-  uint32_t* vals_oth = odd ? vals_a : vals_b;
-  SNC_CUDA(c, radix_sort_run(keys_a, vals_a, keys_res, vals_res, keys_oth, vals_oth, n, c->passes, sort_scratch,
-                             S.d_err, st, S.ev + S.n_ev, /*hist_ready=*/true));
+  void* keys_res = odd ? keys_b : keys_a;
+  uint64_t* vals_res = odd ? vals_b : vals_a;
+  void* keys_oth = odd ? keys_a : keys_b;
+  uint64_t* vals_oth = odd ? vals_a : vals_b;
+  if (key32)
+    SNC_CUDA(c, radix_sort_run(static_cast<const uint32_t*>(keys_a), vals_a, static_cast<uint32_t*>(keys_res), vals_res,
+                               static_cast<uint32_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
+                               S.ev + S.n_ev, /*hist_ready=*/true));
+  else
+    SNC_CUDA(c, radix_sort_run(static_cast<const uint64_t*>(keys_a), vals_a, static_cast<uint64_t*>(keys_res), vals_res,
+                               static_cast<uint64_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
+                               S.ev + S.n_ev, /*hist_ready=*/true));
   S.n_ev += c->passes.n_passes + 1;
   if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
   c->stats.n_passes = c->passes.n_passes;
@@ -869,11 +880,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   dev_free(c, keys_oth);
   dev_free(c, vals_oth);
 
-  // Index: unpack target / delay, group starts, row_ptr and p_i.
+  // Index: unpack target / delay / weight, group starts, row_ptr and p_i.
   const uint64_t n_delay_values = max_step;
   const uint64_t group_cap = std::max<uint64_t>(1, std::min<uint64_t>(n, total_nodes * n_delay_values));
   uint32_t* u_target = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
   uint16_t* u_delay = static_cast<uint16_t*>(dev_alloc(c, n * sizeof(uint16_t)));
+  float* u_weight = static_cast<float*>(dev_alloc(c, n * sizeof(float)));
   uint64_t* u_group_first = static_cast<uint64_t*>(dev_alloc(c, group_cap * sizeof(uint64_t)));
   uint64_t* u_row_ptr = static_cast<uint64_t*>(dev_alloc(c, (total_nodes + 1) * sizeof(uint64_t)));
   uint64_t* u_group_ptr = static_cast<uint64_t*>(dev_alloc(c, (total_nodes + 1) * sizeof(uint64_t)));
@@ -882,17 +894,19 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   uint32_t* bcounts = static_cast<uint32_t*>(dev_alloc(c, (iblocks + 1) * sizeof(uint32_t)));
   uint64_t* boffsets = static_cast<uint64_t*>(dev_alloc(c, (iblocks + 1) * sizeof(uint64_t)));
   uint64_t* iscan = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(iblocks) + 1) * sizeof(uint64_t)));
-  if (!u_target || !u_delay || !u_group_first || !u_row_ptr || !u_group_ptr || !starts || !bcounts || !boffsets ||
-      !iscan)
+  if (!u_target || !u_delay || !u_weight || !u_group_first || !u_row_ptr || !u_group_ptr || !starts || !bcounts ||
+      !boffsets || !iscan)
     return fail(c, SNC_ERR_OOM, "device allocation failed (index)");
   if (n > 0) {
     IndexArgs ia{};
     ia.keys = keys_res;
+    ia.vals = vals_res;
+    ia.key32 = key32 ? 1 : 0;
     ia.n = n;
-    ia.tgt_bits = c->layout.tgt_bits;
     ia.delay_bits = c->layout.delay_bits;
     ia.target = u_target;
     ia.delay = u_delay;
+    ia.weight = reinterpret_cast<uint32_t*>(u_weight);
     ia.starts = starts;
     ia.block_counts = bcounts;
     ia.block_offsets = boffsets;
@@ -901,9 +915,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     ia.n_groups = S.d_n_groups;
     ia.err = S.d_err;
     const unsigned igrid = static_cast<unsigned>(std::min<uint64_t>(iblocks, static_cast<uint64_t>(c->sms) * 8));
-    index_unpack_kernel<<<igrid, kIndexThreads, 0, st>>>(ia);
+    SNC_CUDA(c, launch_index_unpack(ia, igrid, st));
     ++c->stats.kernel_launches;
-    SNC_CUDA(c, cudaGetLastError());
     SNC_CUDA(c, exclusive_scan_u32(bcounts, iblocks, boffsets, iscan, st));
     c->stats.kernel_launches += 3;
     index_groups_kernel<<<igrid, kIndexThreads, 0, st>>>(ia);
@@ -912,18 +925,17 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   }
   NodeIndexArgs na{};
   na.keys = keys_res;
+  na.key32 = key32 ? 1 : 0;
   na.n = n;
   na.n_nodes = total_nodes;
-  na.tgt_bits = c->layout.tgt_bits;
   na.delay_bits = c->layout.delay_bits;
   na.group_first = u_group_first;
   na.group_cap = group_cap;
   na.n_groups = S.d_n_groups;
   na.row_ptr = u_row_ptr;
   na.group_ptr = u_group_ptr;
-  node_index_kernel<<<static_cast<unsigned>((total_nodes + 1 + 255) / 256), 256, 0, st>>>(na);
+  SNC_CUDA(c, launch_node_index(na, st));
   ++c->stats.kernel_launches;
-  SNC_CUDA(c, cudaGetLastError());
   // Batches: each member's CSR and group offsets relative to its own first
   // connection and group; its first connection and group are read back at
   // synchronize.
@@ -985,6 +997,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   dev_free(c, boffsets);
   dev_free(c, iscan);
   dev_free(c, keys_res);
+  dev_free(c, vals_res);
   dev_free(c, d_direct);
   dev_free(c, d_prim_off);
 
@@ -1001,7 +1014,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     x->group_cap = group_cap;
     x->target_all = u_target;
     x->delay_all = u_delay;
-    x->weight_all = reinterpret_cast<float*>(vals_res);
+    x->weight_all = u_weight;
     x->group_first_all = u_group_first;
     x->row_ptr = n_members > 1 ? local_rows + local_base[m] : u_row_ptr;
     x->group_ptr = n_members > 1 ? local_groups + local_base[m] : u_group_ptr;

@@ -1,11 +1,12 @@
-// sort_kernels.cu -- stable LSD radix sort of (64-bit key, 32-bit value)
-// pairs: one upfront histogram of every digit, then one "onesweep" pass per
-// digit (Adinets & Merrill 2022) whose tiles find their global offsets by
-// decoupled look-back (Merrill & Garland 2016).
+// sort_kernels.cu -- stable LSD radix sort of (key, value) pairs with 32- or
+// 64-bit keys and values: one upfront histogram of every digit, then one
+// "onesweep" pass per digit (Adinets & Merrill 2022) whose tiles find their
+// global offsets by decoupled look-back (Merrill & Garland 2016).
 //
 // The paper sorts connections by source and delay with an extension of radix
-// sort (Sec. 2.2); here the key also carries the target, and the sort is a
-// plain stable LSD sort over the packed key's bits.
+// sort (Sec. 2.2).  Here the key packs (source, delay) and the value carries
+// (target, weight); the sort is stable, so connections with equal keys keep
+// their generation order.
 //
 // Look-back status words are 64-bit: [flag:2][epoch:14][count:48].  The epoch
 // changes every pass, so a stale word from an earlier pass reads as "not yet
@@ -78,25 +79,29 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_t
 // Histogram of every pass's digit over all keys (shared-memory counters per
 // block, merged into global 64-bit counters).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) radix_hist_kernel(const uint64_t* __restrict__ keys, uint64_t n, HistPlan plan) {
+template <typename K>
+__global__ void __launch_bounds__(512) radix_hist_kernel(const K* __restrict__ keys, uint64_t n, HistPlan plan) {
   extern __shared__ uint32_t sh[];
   const HistRegs r = hist_regs(plan);
   hist_clear(sh, r);
   __syncthreads();
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  const uint64_t pairs = n / 2;
-  const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(keys);
+  constexpr int PER = 16 / sizeof(K);  // keys per 16-byte vector
+  const uint64_t vecs = n / PER;
+  const uint4* k4 = reinterpret_cast<const uint4*>(keys);
   const bool aligned = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
   if (aligned) {
-    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < pairs; i += stride) {
-      const ulonglong2 v = k2[i];
-      hist_add(sh, r, v.x);
-      hist_add(sh, r, v.y);
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < vecs; i += stride) {
+      const uint4 v = k4[i];
+      const K* kv = reinterpret_cast<const K*>(&v);
+#pragma unroll
+      for (int j = 0; j < PER; ++j) hist_add(sh, r, static_cast<uint64_t>(kv[j]));
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) hist_add(sh, r, keys[n - 1]);
+    for (uint64_t i = vecs * PER + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+      hist_add(sh, r, static_cast<uint64_t>(keys[i]));
   } else {
     for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
-      hist_add(sh, r, keys[i]);
+      hist_add(sh, r, static_cast<uint64_t>(keys[i]));
   }
   __syncthreads();
   hist_flush(sh, r, plan.global);
@@ -167,7 +172,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
 
-template <int BITS, int G>
+template <int BITS, int G, typename K, typename V>
 struct Onesweep {
   static constexpr int TPB = kSortThreads, IPT = kSortItems, TILE = kSortTile;
   static constexpr int RADIX = 1 << BITS;
@@ -177,15 +182,15 @@ struct Onesweep {
   static constexpr int W = DPT >= 8 ? 2 : (DPT >= 4 ? 4 : 8);  // look-back window per round
   static constexpr int MINB = BITS <= 9 ? 3 : 2;                // resident blocks per SM
   static constexpr size_t kCntBytes = static_cast<size_t>(NW) * RADIX * sizeof(uint16_t);
-  static constexpr size_t kTileBytes = static_cast<size_t>(TILE) * (sizeof(uint64_t) + sizeof(uint32_t));
+  static constexpr size_t kTileBytes = static_cast<size_t>(TILE) * (sizeof(K) + sizeof(V));
   static constexpr size_t kUnion = kCntBytes > kTileBytes ? kCntBytes : kTileBytes;
   static constexpr size_t kSmem = kUnion + RADIX * sizeof(uint32_t) * 2 + RADIX * sizeof(uint64_t);
 };
 
 // Sum, for each of this thread's DPT digits, the counts that groups before
 // `unit` published (decoupled look-back, W predecessors per round trip).
-template <int RADIX, int DPT, int W>
-__device__ __forceinline__ void look_back(const OnesweepArgs& a, uint32_t unit, uint64_t (&prefix)[DPT]) {
+template <int RADIX, int DPT, int W, typename A>
+__device__ __forceinline__ void look_back(const A& a, uint32_t unit, uint64_t (&prefix)[DPT]) {
   const uint32_t tid = threadIdx.x;
   int32_t look[DPT];
   uint32_t pending = 0;
@@ -240,17 +245,18 @@ __device__ __forceinline__ void look_back(const OnesweepArgs& a, uint32_t unit, 
   }
 }
 
-template <int BITS, int G>
-__global__ void __launch_bounds__(kSortThreads, Onesweep<BITS, G>::MINB) onesweep_kernel(OnesweepArgs a) {
-  using C = Onesweep<BITS, G>;
+template <int BITS, int G, typename K, typename V>
+__global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
+    onesweep_kernel(OnesweepArgs<K, V> a) {
+  using C = Onesweep<BITS, G, K, V>;
   constexpr int RADIX = C::RADIX, NW = C::NW, TILE = C::TILE, GROUP = C::GROUP, DPT = C::DPT, W = C::W;
   constexpr int TPB = C::TPB, IPT = C::IPT;
   static_assert(RADIX % TPB == 0, "radix must be a multiple of the block size");
 
   extern __shared__ __align__(16) unsigned char smem[];
   uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem);
-  uint64_t* skeys = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* svals = reinterpret_cast<uint32_t*>(smem + static_cast<size_t>(TILE) * sizeof(uint64_t));
+  K* skeys = reinterpret_cast<K*>(smem);
+  V* svals = reinterpret_cast<V*>(smem + static_cast<size_t>(TILE) * sizeof(K));
   uint32_t* ghist = reinterpret_cast<uint32_t*>(smem + C::kUnion);
   uint32_t* local_start = ghist + RADIX;
   uint64_t* run = reinterpret_cast<uint64_t*>(smem + C::kUnion + 2 * RADIX * sizeof(uint32_t));
@@ -318,12 +324,12 @@ __global__ void __launch_bounds__(kSortThreads, Onesweep<BITS, G>::MINB) oneswee
       for (int i = tid; i < NW * RADIX / 2; i += TPB) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
       __syncthreads();
       const uint64_t warp_base = tbase + static_cast<uint64_t>(warp) * 32 * IPT;
-      uint64_t key[IPT];
+      K key[IPT];
       uint32_t rank[IPT];
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
-        key[j] = idx < a.n ? a.keys_in[idx] : 0ull;
+        key[j] = idx < a.n ? a.keys_in[idx] : K(0);
       }
       uint16_t* my = wcnt + static_cast<size_t>(warp) * RADIX;
 #pragma unroll
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(kSortThreads, Onesweep<BITS, G>::MINB) oneswee
       const uint64_t left = a.n - tbase;
       const uint32_t valid = left < static_cast<uint64_t>(TILE) ? static_cast<uint32_t>(left) : static_cast<uint32_t>(TILE);
       for (uint32_t i = tid; i < valid; i += TPB) {
-        const uint64_t k = skeys[i];
+        const K k = skeys[i];
         const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
         const uint64_t pos = run[d] + (i - local_start[d]);
         if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
@@ -472,8 +478,8 @@ __device__ __forceinline__ uint32_t ld_status32(const uint32_t* p) {
   return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
-template <int RADIX, int DPT, int W>
-__device__ __forceinline__ void look_back32(const OnesweepArgs& a, uint32_t unit, uint64_t (&prefix)[DPT]) {
+template <int RADIX, int DPT, int W, typename A>
+__device__ __forceinline__ void look_back32(const A& a, uint32_t unit, uint64_t (&prefix)[DPT]) {
   const uint32_t tid = threadIdx.x;
   const uint32_t* base = a.status32 + tid * DPT;
   int32_t look[DPT];
@@ -533,36 +539,41 @@ __device__ __forceinline__ void look_back32(const OnesweepArgs& a, uint32_t unit
   }
 }
 
-template <int BITS>
+template <int BITS, typename K, typename V>
 struct OnesweepTma {
   static constexpr int TPB = kSortThreads, IPT = kSortItems, TILE = kSortTile;
   static constexpr int RADIX = 1 << BITS;
   static constexpr int NW = TPB / 32;
   static constexpr int DPT = RADIX / TPB;
   static constexpr int W = DPT >= 2 ? 4 : 8;
-  static constexpr int MINB = BITS <= 8 ? 3 : 2;  // resident blocks per SM (shared memory bound)
-  static constexpr size_t kKeysBytes = static_cast<size_t>(TILE) * sizeof(uint64_t);  // input / staged keys
-  static constexpr size_t kValsBytes = static_cast<size_t>(TILE) * sizeof(uint32_t);
+  static constexpr size_t kKeysBytes = static_cast<size_t>(TILE) * sizeof(K);  // input / staged keys
+  static constexpr size_t kValsBytes = static_cast<size_t>(TILE) * sizeof(V);  // input values
+  static constexpr size_t kPermBytes = static_cast<size_t>(TILE) * sizeof(uint16_t);
   static constexpr size_t kCntBytes = static_cast<size_t>(NW) * RADIX * sizeof(uint16_t);
   static constexpr size_t kOffVals = kKeysBytes;
-  static constexpr size_t kOffStageVals = kOffVals + kValsBytes;
-  static constexpr size_t kOffCnt = kOffStageVals + kValsBytes;
+  static constexpr size_t kOffPerm = kOffVals + kValsBytes;
+  static constexpr size_t kOffCnt = kOffPerm + kPermBytes;
   static constexpr size_t kOffLocal = kOffCnt + kCntBytes;
   static constexpr size_t kOffGlob = kOffLocal + RADIX * sizeof(uint32_t);
   static constexpr size_t kOffBar = kOffGlob + RADIX * sizeof(uint64_t);
   static constexpr size_t kSmem = kOffBar + 16;
+  // Resident blocks per SM: shared memory (228 KB per SM, 1 KB reserved per
+  // block) and registers allow at most 3.
+  static constexpr int kFit = static_cast<int>((228u * 1024u) / (kSmem + 1024u + 256u));
+  static constexpr int MINB = kFit < 1 ? 1 : (kFit > 3 ? 3 : kFit);
 };
 
-template <int BITS>
-__global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) onesweep_tma_kernel(OnesweepArgs a) {
-  using C = OnesweepTma<BITS>;
+template <int BITS, typename K, typename V>
+__global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, K, V>::MINB))
+    onesweep_tma_kernel(OnesweepArgs<K, V> a) {
+  using C = OnesweepTma<BITS, K, V>;
   constexpr int RADIX = C::RADIX, NW = C::NW, TILE = C::TILE, DPT = C::DPT, W = C::W;
   constexpr int TPB = C::TPB, IPT = C::IPT;
   static_assert(RADIX % TPB == 0, "radix must be a multiple of the block size");
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* skeys = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* vin = reinterpret_cast<uint32_t*>(smem + C::kOffVals);
-  uint32_t* svals = reinterpret_cast<uint32_t*>(smem + C::kOffStageVals);
+  K* skeys = reinterpret_cast<K*>(smem);
+  V* vin = reinterpret_cast<V*>(smem + C::kOffVals);
+  uint16_t* perm = reinterpret_cast<uint16_t*>(smem + C::kOffPerm);  // staged slot -> input index
   uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem + C::kOffCnt);
   uint32_t* local_start = reinterpret_cast<uint32_t*>(smem + C::kOffLocal);
   uint64_t* globm = reinterpret_cast<uint64_t*>(smem + C::kOffGlob);  // global position of local index 0
@@ -630,14 +641,14 @@ __global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) oneswee
 
     // Rank within the warp (keys from shared memory).
     const uint32_t wbase = warp * 32u * IPT;
-    uint64_t key[IPT];
+    K key[IPT];
     uint32_t rank[IPT];
     uint16_t* my = wcnt + static_cast<size_t>(warp) * RADIX;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
       const bool ok = li < valid;
-      key[j] = ok ? skeys[li] : 0ull;
+      key[j] = ok ? skeys[li] : K(0);
       const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const int leader = __ffs(peers) - 1;
@@ -688,7 +699,7 @@ __global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) oneswee
         const uint32_t lp = local_start[d] + wcnt[warp * RADIX + d] + rank[j];
         if (SNC_IN_BOUNDS(a.err, 10u, lp, TILE)) {
           skeys[lp] = key[j];
-          svals[lp] = vin[li];
+          perm[lp] = static_cast<uint16_t>(li);
         }
       }
     }
@@ -702,44 +713,44 @@ __global__ void __launch_bounds__(kSortThreads, OnesweepTma<BITS>::MINB) oneswee
     }
     __syncthreads();
     for (uint32_t i = tid; i < valid; i += TPB) {
-      const uint64_t k = skeys[i];
+      const K k = skeys[i];
       const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
       const uint64_t pos = globm[d] + i;
       if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
       a.keys_out[pos] = k;
-      a.vals_out[pos] = svals[i];
+      a.vals_out[pos] = vin[perm[i]];
     }
     __syncthreads();
   }
 }
 
-template <int BITS>
-cudaError_t launch_onesweep_tma(const OnesweepArgs& a, int sms, cudaStream_t st) {
-  using C = OnesweepTma<BITS>;
+template <int BITS, typename K, typename V>
+cudaError_t launch_onesweep_tma(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
+  using C = OnesweepTma<BITS, K, V>;
   // Set on every launch: the attribute is per function and device, and
   // builds may run on several threads and devices.
-  cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS, K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(C::kSmem));
   if (e != cudaSuccess) return e;
   const uint64_t tiles = (a.n + C::TILE - 1) / C::TILE;
   const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
   const uint64_t grid = tiles < resident ? tiles : resident;
-  onesweep_tma_kernel<BITS><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
+  onesweep_tma_kernel<BITS, K, V><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int BITS, int G>
-cudaError_t launch_onesweep(const OnesweepArgs& a, int sms, cudaStream_t st) {
-  using C = Onesweep<BITS, G>;
+template <int BITS, int G, typename K, typename V>
+cudaError_t launch_onesweep(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
+  using C = Onesweep<BITS, G, K, V>;
   // Set on every launch: the attribute is per function and device, and
   // builds may run on several threads and devices.
-  cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS, G, K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(C::kSmem));
   if (e != cudaSuccess) return e;
   const uint64_t units = (a.n + C::GROUP - 1) / C::GROUP;
   const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
   const uint64_t grid = units < resident ? units : resident;
-  onesweep_kernel<BITS, G><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
+  onesweep_kernel<BITS, G, K, V><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -749,25 +760,26 @@ int onesweep_group(int bits, int group_tiles) {
   return kSortTile * (group_tiles > 0 ? group_tiles : 1);
 }
 
-template <int BITS>
-cudaError_t launch_onesweep_g(int group_tiles, const OnesweepArgs& a, int sms, cudaStream_t st) {
+template <int BITS, typename K, typename V>
+cudaError_t launch_onesweep_g(int group_tiles, const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
   switch (group_tiles) {
     case 0:
-      if (BITS <= 9) return launch_onesweep_tma<(BITS <= 9 ? BITS : 9)>(a, sms, st);
-      return launch_onesweep<BITS, 1>(a, sms, st);
-    case 1: return launch_onesweep<BITS, 1>(a, sms, st);
-    case 4: return launch_onesweep<BITS, 4>(a, sms, st);
-    case 8: return launch_onesweep<BITS, 8>(a, sms, st);
+      if (BITS <= 9) return launch_onesweep_tma<(BITS <= 9 ? BITS : 9), K, V>(a, sms, st);
+      return launch_onesweep<BITS, 1, K, V>(a, sms, st);
+    case 1: return launch_onesweep<BITS, 1, K, V>(a, sms, st);
+    case 4: return launch_onesweep<BITS, 4, K, V>(a, sms, st);
+    case 8: return launch_onesweep<BITS, 8, K, V>(a, sms, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_onesweep_bits(int bits, int group_tiles, const OnesweepArgs& a, int sms, cudaStream_t st) {
+template <typename K, typename V>
+cudaError_t launch_onesweep_bits(int bits, int group_tiles, const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
   switch (bits) {
-    case 8: return launch_onesweep_g<8>(group_tiles, a, sms, st);
-    case 9: return launch_onesweep_g<9>(group_tiles, a, sms, st);
-    case 10: return launch_onesweep_g<10>(group_tiles, a, sms, st);
-    case 11: return launch_onesweep_g<11>(group_tiles, a, sms, st);
+    case 8: return launch_onesweep_g<8, K, V>(group_tiles, a, sms, st);
+    case 9: return launch_onesweep_g<9, K, V>(group_tiles, a, sms, st);
+    case 10: return launch_onesweep_g<10, K, V>(group_tiles, a, sms, st);
+    case 11: return launch_onesweep_g<11, K, V>(group_tiles, a, sms, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -839,9 +851,12 @@ SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp)
   return l;
 }
 
-cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                           uint64_t* keys_tmp, uint32_t* vals_tmp, uint64_t n, const SortPasses& sp, void* scratch,
-                           uint32_t* err, cudaStream_t st, cudaEvent_t* pass_events, bool hist_ready) {
+template <typename K, typename V>
+cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* vals_out, K* keys_tmp, V* vals_tmp,
+                           uint64_t n, const SortPasses& sp, void* scratch, uint32_t* err, cudaStream_t st,
+                           cudaEvent_t* pass_events, bool hist_ready) {
+  // The pass kernels shift keys by up to the key width minus one.
+  if (static_cast<size_t>(sp.shift[sp.n_passes - 1]) >= 8 * sizeof(K)) return cudaErrorInvalidValue;
   if (n == 0) {
     if (pass_events)
       for (int i = 0; i <= sp.n_passes; ++i) cudaEventRecord(pass_events[i], st);
@@ -874,10 +889,10 @@ cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uin
     const size_t hist_smem = hist_smem_bytes(plan);
     // Set on every launch: the attribute is per function and device, and
     // builds may run on several threads and devices.
-    e = cudaFuncSetAttribute(radix_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(radix_hist_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kMaxPasses * kMaxRadix * sizeof(uint32_t)));
     if (e != cudaSuccess) return e;
-    radix_hist_kernel<<<sms * 2, 512, hist_smem, st>>>(keys_in, n, plan);
+    radix_hist_kernel<K><<<sms * 2, 512, hist_smem, st>>>(keys_in, n, plan);
   }
   radix_digit_scan_kernel<<<sp.n_passes, kDigitScanThreads, 0, st>>>(hist, start);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -892,13 +907,13 @@ cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uin
                               aligned16(vals_out) && (sp.n_passes < 2 || (aligned16(keys_tmp) && aligned16(vals_tmp))))))
     group_tiles = 1;
   const size_t status32_bytes = static_cast<size_t>((n + kSortTile - 1) / kSortTile) * (1u << sp.kernel_bits) * 4u;
-  const uint64_t* kin = keys_in;
-  const uint32_t* vin = vals_in;
+  const K* kin = keys_in;
+  const V* vin = vals_in;
   for (int pass = 0; pass < sp.n_passes; ++pass) {
     const bool to_out = ((sp.n_passes - 1 - pass) & 1) == 0;
-    uint64_t* kout = to_out ? keys_out : keys_tmp;
-    uint32_t* vout = to_out ? vals_out : vals_tmp;
-    OnesweepArgs a{};
+    K* kout = to_out ? keys_out : keys_tmp;
+    V* vout = to_out ? vals_out : vals_tmp;
+    OnesweepArgs<K, V> a{};
     a.keys_in = kin;
     a.vals_in = vin;
     a.keys_out = kout;
@@ -913,12 +928,22 @@ cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uin
     a.err = err;
     a.status32 = reinterpret_cast<uint32_t*>(status);
     if (group_tiles == 0 && (e = cudaMemsetAsync(status, 0, status32_bytes, st)) != cudaSuccess) return e;
-    if ((e = launch_onesweep_bits(sp.kernel_bits, group_tiles, a, sms, st)) != cudaSuccess) return e;
+    if ((e = launch_onesweep_bits<K, V>(sp.kernel_bits, group_tiles, a, sms, st)) != cudaSuccess) return e;
     if (pass_events) cudaEventRecord(pass_events[pass + 1], st);
     kin = kout;
     vin = vout;
   }
   return cudaSuccess;
 }
+
+template cudaError_t radix_sort_run<uint64_t, uint32_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*,
+                                                        uint64_t*, uint32_t*, uint64_t, const SortPasses&, void*,
+                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool);
+template cudaError_t radix_sort_run<uint32_t, uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*,
+                                                        uint32_t*, uint64_t*, uint64_t, const SortPasses&, void*,
+                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool);
+template cudaError_t radix_sort_run<uint64_t, uint64_t>(const uint64_t*, const uint64_t*, uint64_t*, uint64_t*,
+                                                        uint64_t*, uint64_t*, uint64_t, const SortPasses&, void*,
+                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool);
 
 }  // namespace snc

@@ -21,11 +21,14 @@ struct SortPasses {
   uint32_t mask[kMaxPasses];
 };
 
+// Arguments of one pass over (key K, value V) pairs.  K is uint32_t or
+// uint64_t, V uint32_t or uint64_t.
+template <typename K, typename V>
 struct OnesweepArgs {
-  const uint64_t* keys_in;
-  const uint32_t* vals_in;
-  uint64_t* keys_out;
-  uint32_t* vals_out;
+  const K* keys_in;
+  const V* vals_in;
+  K* keys_out;
+  V* vals_out;
   uint64_t n;
   int shift;
   uint32_t mask;
@@ -59,10 +62,13 @@ struct SortScratch {
 };
 SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp);
 
+// Stable LSD sort of n (key, value) pairs on the planned digits.
 // hist_ready: the digit counts are already in the scratch's hist area (for
-// example accumulated by the kernels that produced the keys).
-cudaError_t radix_sort_run(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out, uint32_t* vals_out,
-                           uint64_t* keys_tmp, uint32_t* vals_tmp, uint64_t n, const SortPasses& sp, void* scratch,
-                           uint32_t* err, cudaStream_t st, cudaEvent_t* pass_events, bool hist_ready = false);
+// example accumulated by the kernels that produced the keys).  Instantiated
+// for (uint64_t, uint32_t), (uint32_t, uint64_t) and (uint64_t, uint64_t).
+template <typename K, typename V>
+cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* vals_out, K* keys_tmp, V* vals_tmp,
+                           uint64_t n, const SortPasses& sp, void* scratch, uint32_t* err, cudaStream_t st,
+                           cudaEvent_t* pass_events, bool hist_ready = false);
 
 }  // namespace snc

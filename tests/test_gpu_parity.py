@@ -157,11 +157,14 @@ def test_launch_shape_independence(snc):
 @pytest.mark.parametrize("digit_bits,group", [(11, 8), (8, 0), (9, 4)], ids=["d11g8", "d8tma", "d9g4"])
 @pytest.mark.parametrize("n_nodes,delay", [(4, Dist("const", 0.1)), (60, Dist("normal", 1.5, 0.75)),
                                            (3000, Dist("normal", 1.5, 0.75)),
-                                           (18000, Dist("normal", 1.5, 0.75))])
+                                           (600_000, Dist("normal", 1.5, 0.75)),
+                                           (140_000, Dist("const", 6000.0))],
+                         ids=["3bit", "12bit", "18bit", "26bit", "34bit_wide"])
 def test_every_pass_parity(snc, oracle_mod, n_nodes, delay, digit_bits, group):
     """The sort's buffers alternate per pass, so the result buffer depends on
     the parity of the pass count: cover odd and even counts for every kernel
-    variant (1-4 passes of up to 11 bits, 1-6 passes of 8 bits)."""
+    variant (1-4 passes of 8 bits on 32-bit keys, and a 34-bit key that
+    takes the 64-bit key path: 60,000 delay steps need 16 bits)."""
     half = n_nodes // 2
     spec = NetworkSpec(seed=21, dt=0.1, populations=[half, n_nodes - half], projections=[
         Projection(src=(0, n_nodes), tgt=(0, n_nodes), rule="fixed_total_number", k=150_001,
