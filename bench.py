@@ -45,6 +45,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sort-digit-bits", type=int, default=None, help="tuning: widest radix digit")
     ap.add_argument("--sort-group-tiles", type=int, default=None, help="tuning: tiles per look-back unit")
+    ap.add_argument("--sort-items", type=int, default=None, help="tuning: keys per thread of the bulk-copy pass")
     return ap.parse_args()
 
 
@@ -365,7 +366,8 @@ def main():
     replicas.init("nccl")
     from paper_2306_09855_gb300 import snc
     snc.load()
-    tuning = snc.snc_set_tuning(sort_digit_bits=args.sort_digit_bits, sort_group_tiles=args.sort_group_tiles)
+    tuning = snc.snc_set_tuning(sort_digit_bits=args.sort_digit_bits, sort_group_tiles=args.sort_group_tiles,
+                                sort_items=args.sort_items)
     specs, config = workload_specs(args.workload)
     stream = torch.cuda.current_stream()
 
@@ -504,7 +506,8 @@ def main():
         "config": dict(config, connections_per_step=n_total // max(1, args.steps),
                        tuning={"sort_digit_bits": final_tuning.sort_digit_bits,
                                "sort_group_tiles": final_tuning.sort_group_tiles,
-                               "gen_blocks_per_sm": final_tuning.gen_blocks_per_sm},
+                               "gen_blocks_per_sm": final_tuning.gen_blocks_per_sm,
+                               "sort_items": final_tuning.sort_items},
                        l2="inputs larger than L2 (>= 4.8 GB of keys+values per network)",
                        parallelism="replicas" if world > 1 else "single GPU"),
         "roofline": {"bound": "hbm", "kernel": "onesweep radix pass", "achieved": achieved, "peak": peak,

@@ -14,8 +14,15 @@ from typing import Dict, List, Sequence
 
 from . import snc
 
-# (sort digit bits, tiles per look-back unit, generation blocks per SM)
-CANDIDATES = [(8, 0, 8), (8, 0, 4), (8, 0, 16), (9, 0, 8), (9, 8, 8), (10, 8, 8), (11, 8, 8), (8, 1, 8)]
+# (sort digit bits, tiles per look-back unit, generation blocks per SM,
+#  keys per thread of the bulk-copy pass)
+CANDIDATES = [(8, 0, 8, 16), (9, 0, 8, 16), (8, 0, 8, 12), (8, 0, 4, 16), (8, 0, 16, 16), (10, 8, 8, 16),
+              (11, 8, 8, 16)]
+FIELDS = ("sort_digit_bits", "sort_group_tiles", "gen_blocks_per_sm", "sort_items")
+
+
+def _apply(tuning):
+    snc.snc_set_tuning(**dict(zip(FIELDS, tuning)))
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "snc_tuning.json")
 
@@ -71,7 +78,7 @@ def tune(specs: Sequence, batched: bool = True, candidates=CANDIDATES, cache_pat
     for sp in specs:
         for pj in sp.projections:
             n_est += int(pj.k) * int(pj.tgt[1]) if pj.rule == "fixed_indegree" else int(pj.k)
-    key = "%s/%s/%s/%s" % (_gpu_name(), _key_class(specs), _size_class(n_est), "batch" if batched else "single")
+    key = "v3/%s/%s/%s/%s" % (_gpu_name(), _key_class(specs), _size_class(n_est), "batch" if batched else "single")
     cache = {}
     if use_cache and os.path.exists(cache_path):
         try:
@@ -79,18 +86,18 @@ def tune(specs: Sequence, batched: bool = True, candidates=CANDIDATES, cache_pat
                 cache = json.load(f)
         except (OSError, ValueError):
             cache = {}
-    if use_cache and key in cache:
+    if use_cache and key in cache and len(cache[key].get("tuning", ())) == len(FIELDS):
         choice = cache[key]
-        snc.snc_set_tuning(*choice["tuning"])
+        _apply(choice["tuning"])
         return dict(choice, key=key, cached=True)
     results: List[Dict] = []
-    for bits, group, gen in candidates:
-        snc.snc_set_tuning(sort_digit_bits=bits, sort_group_tiles=group, gen_blocks_per_sm=gen)
+    for cand in candidates:
+        _apply(cand)
         t0 = time.perf_counter()
         ms = time_build(specs, batched)
-        results.append({"tuning": [bits, group, gen], "ms": ms, "tune_s": time.perf_counter() - t0})
+        results.append({"tuning": list(cand), "ms": ms, "tune_s": time.perf_counter() - t0})
     best = min(results, key=lambda r: r["ms"])
-    snc.snc_set_tuning(*best["tuning"])
+    _apply(best["tuning"])
     choice = {"tuning": best["tuning"], "ms": best["ms"], "all": results}
     if use_cache:
         cache[key] = choice

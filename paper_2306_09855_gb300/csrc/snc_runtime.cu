@@ -1201,8 +1201,13 @@ snc_status snc_set_tuning(const snc_tuning* t) {
     return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_group_tiles must be 0, 1, 4 or 8");
   if (t->gen_blocks_per_sm < 1 || t->gen_blocks_per_sm > 32)
     return fail(nullptr, SNC_ERR_INVALID_ARG, "gen_blocks_per_sm outside [1, 32]");
+  if (t->sort_items != 8 && t->sort_items != 12 && t->sort_items != 16)
+    return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_items must be 8, 12 or 16");
+  if (t->reserved[0] || t->reserved[1] || t->reserved[2] || t->reserved[3])
+    return fail(nullptr, SNC_ERR_INVALID_ARG, "reserved tuning fields must be 0");
   g_sort_tuning.max_digit_bits = t->sort_digit_bits;
   g_sort_tuning.group_tiles = t->sort_group_tiles;
+  g_sort_tuning.items = t->sort_items;
   g_gen_blocks_per_sm = t->gen_blocks_per_sm;
   return SNC_OK;
 }
@@ -1212,7 +1217,8 @@ snc_status snc_get_tuning(snc_tuning* t) {
   t->sort_digit_bits = g_sort_tuning.max_digit_bits;
   t->sort_group_tiles = g_sort_tuning.group_tiles;
   t->gen_blocks_per_sm = g_gen_blocks_per_sm;
-  t->reserved = 0;
+  t->sort_items = g_sort_tuning.items;
+  t->reserved[0] = t->reserved[1] = t->reserved[2] = t->reserved[3] = 0;
   return SNC_OK;
 }
 

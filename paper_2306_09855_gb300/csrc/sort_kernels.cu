@@ -539,46 +539,60 @@ __device__ __forceinline__ void look_back32(const A& a, uint32_t unit, uint64_t 
   }
 }
 
-template <int BITS, typename K, typename V>
+template <int BITS, int ITEMS, typename K, typename V>
 struct OnesweepTma {
-  static constexpr int TPB = kSortThreads, IPT = kSortItems, TILE = kSortTile;
+  static constexpr int TPB = kSortThreads, IPT = ITEMS, TILE = kSortThreads * ITEMS;
   static constexpr int RADIX = 1 << BITS;
   static constexpr int NW = TPB / 32;
   static constexpr int DPT = RADIX / TPB;
   static constexpr int W = DPT >= 2 ? 4 : 8;
   static constexpr size_t kKeysBytes = static_cast<size_t>(TILE) * sizeof(K);  // input / staged keys
-  static constexpr size_t kValsBytes = static_cast<size_t>(TILE) * sizeof(V);  // input values
-  static constexpr size_t kPermBytes = static_cast<size_t>(TILE) * sizeof(uint16_t);
+  static constexpr size_t kValsBytes = static_cast<size_t>(TILE) * sizeof(V);  // input / staged values
+  static constexpr size_t kBufBytes = (kKeysBytes + kValsBytes + 127) / 128 * 128;
   static constexpr size_t kCntBytes = static_cast<size_t>(NW) * RADIX * sizeof(uint16_t);
-  static constexpr size_t kOffVals = kKeysBytes;
-  static constexpr size_t kOffPerm = kOffVals + kValsBytes;
-  static constexpr size_t kOffCnt = kOffPerm + kPermBytes;
+  static constexpr size_t kOffCnt = kBufBytes;
   static constexpr size_t kOffLocal = kOffCnt + kCntBytes;
   static constexpr size_t kOffGlob = kOffLocal + RADIX * sizeof(uint32_t);
   static constexpr size_t kOffBar = kOffGlob + RADIX * sizeof(uint64_t);
   static constexpr size_t kSmem = kOffBar + 16;
   // Resident blocks per SM: shared memory (228 KB per SM, 1 KB reserved per
-  // block) and registers allow at most 3.
+  // block) and the register target of the item count (16 -> 3, 12 -> 4,
+  // 8 -> 5 blocks of 256 threads).
   static constexpr int kFit = static_cast<int>((228u * 1024u) / (kSmem + 1024u + 256u));
-  static constexpr int MINB = kFit < 1 ? 1 : (kFit > 3 ? 3 : kFit);
+  static constexpr int kRegCap = ITEMS >= 16 ? 3 : (ITEMS >= 12 ? 4 : 5);
+  static constexpr int MINB = kFit < 1 ? 1 : (kFit > kRegCap ? kRegCap : kFit);
 };
 
-template <int BITS, typename K, typename V>
-__global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, K, V>::MINB))
+// Bounded wait for a bulk copy, with the outcome voted over the block so
+// that every thread leaves together when it times out.
+__device__ __forceinline__ bool tile_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t spins = 0;
+  bool ok = true;
+  while (!mbar_try_wait(bar, parity)) {
+    if (++spins > kSpinLimit) {
+      ok = false;
+      break;
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// One pass.  A persistent block takes tiles from the ticket in increasing
+// order and sorts each before taking the next, so the lowest unfinished tile
+// is always being sorted and every look-back wait ends.
+template <int BITS, int ITEMS, typename K, typename V>
+__global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>::MINB))
     onesweep_tma_kernel(OnesweepArgs<K, V> a) {
-  using C = OnesweepTma<BITS, K, V>;
+  using C = OnesweepTma<BITS, ITEMS, K, V>;
   constexpr int RADIX = C::RADIX, NW = C::NW, TILE = C::TILE, DPT = C::DPT, W = C::W;
   constexpr int TPB = C::TPB, IPT = C::IPT;
   static_assert(RADIX % TPB == 0, "radix must be a multiple of the block size");
   extern __shared__ __align__(128) unsigned char smem[];
-  K* skeys = reinterpret_cast<K*>(smem);
-  V* vin = reinterpret_cast<V*>(smem + C::kOffVals);
-  uint16_t* perm = reinterpret_cast<uint16_t*>(smem + C::kOffPerm);  // staged slot -> input index
   uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem + C::kOffCnt);
   uint32_t* local_start = reinterpret_cast<uint32_t*>(smem + C::kOffLocal);
   uint64_t* globm = reinterpret_cast<uint64_t*>(smem + C::kOffGlob);  // global position of local index 0
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::kOffBar);
-  __shared__ uint32_t unit_sh;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kOffBar);
+  __shared__ uint32_t ticket_sh;
   __shared__ uint32_t warp_tmp[32];
   __shared__ uint32_t scan_total;
 
@@ -587,46 +601,48 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, K, V>::MINB))
   const int shift = a.shift;
   const uint32_t lt = lanemask_lt();
   const uint64_t n_tiles = (a.n + TILE - 1) / TILE;
+  const auto buf_keys = [&](int b) { return reinterpret_cast<K*>(smem + b * C::kBufBytes); };
+  const auto buf_vals = [&](int b) { return reinterpret_cast<V*>(smem + b * C::kBufBytes + C::kKeysBytes); };
+  const auto full_tile = [&](uint32_t t) {
+    return t < n_tiles && static_cast<uint64_t>(t) * TILE + TILE <= a.n;
+  };
+  // Thread 0: take a ticket and start its bulk copy into buffer b.
+  const auto take = [&](int b) {
+    const uint32_t t = atomicAdd(a.tile_counter, 1u);
+    ticket_sh = t;
+    if (full_tile(t)) {
+      const uint64_t tb = static_cast<uint64_t>(t) * TILE;
+      fence_proxy_async_smem();  // earlier generic accesses to the buffer come first
+      mbar_arrive_expect_tx(bars + b, static_cast<uint32_t>(C::kKeysBytes + C::kValsBytes));
+      bulk_load(buf_keys(b), a.keys_in + tb, static_cast<uint32_t>(C::kKeysBytes), bars + b);
+      bulk_load(buf_vals(b), a.vals_in + tb, static_cast<uint32_t>(C::kValsBytes), bars + b);
+    }
+  };
 
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(bars, 1);
     fence_mbarrier_init();
+    take(0);
   }
   __syncthreads();
+  uint32_t cur = ticket_sh;
   uint32_t parity = 0;
+  K* skeys = buf_keys(0);
+  V* vin = buf_vals(0);  // input values, then the staged values
 
   for (;;) {
-    if (tid == 0) {
-      const uint32_t t = atomicAdd(a.tile_counter, 1u);
-      unit_sh = t;
-      const uint64_t tb = static_cast<uint64_t>(t) * TILE;
-      if (t < n_tiles && tb + TILE <= a.n) {
-        fence_proxy_async_smem();  // earlier generic accesses to the buffers come first
-        mbar_arrive_expect_tx(bar, static_cast<uint32_t>(C::kKeysBytes + C::kValsBytes));
-        bulk_load(skeys, a.keys_in + tb, static_cast<uint32_t>(C::kKeysBytes), bar);
-        bulk_load(vin, a.vals_in + tb, static_cast<uint32_t>(C::kValsBytes), bar);
-      }
-    }
+    if (cur >= n_tiles) break;
     for (int i = tid; i < NW * RADIX / 2; i += TPB) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
     __syncthreads();
-    const uint32_t unit = unit_sh;
-    if (unit >= n_tiles) break;
+    const uint32_t unit = cur;
     const uint64_t tbase = static_cast<uint64_t>(unit) * TILE;
     const uint32_t valid = a.n - tbase < static_cast<uint64_t>(TILE) ? static_cast<uint32_t>(a.n - tbase) : TILE;
     if (valid == TILE) {
-      uint32_t spins = 0;
-      bool ok = true;
-      while (!mbar_try_wait(bar, parity)) {
-        if (++spins > kSpinLimit) {
-          ok = false;
-          break;
-        }
-      }
-      if (!ok) {
-        // Give the copies a second bounded chance to land before leaving.
+      if (!tile_wait(bars, parity)) {
+        // Give the copies in flight a second bounded chance to land, then leave.
         if (tid == 0) atomicOr(a.err, kErrLookbackTimeout);
-        spins = 0;
-        while (!mbar_try_wait(bar, parity) && ++spins < kSpinLimit) {
+        uint32_t spins = 0;
+        while (!mbar_try_wait(bars, parity) && ++spins < kSpinLimit) {
         }
         break;
       }
@@ -689,19 +705,32 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, K, V>::MINB))
       excl += tot[q];
     }
     __syncthreads();
-    // Stage the tile in digit order while the predecessors publish (the key
-    // buffer is free: the keys are in registers).
+    // Stage the tile in digit order while the predecessors publish.  The
+    // keys are in registers, so the key buffer takes the staged keys; the
+    // values are then read in input order into registers and, after a
+    // barrier, scattered into their own buffer in digit order, so that the
+    // output loop reads both buffers sequentially.
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
       if (li < valid) {
         const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & mask;
         const uint32_t lp = local_start[d] + wcnt[warp * RADIX + d] + rank[j];
-        if (SNC_IN_BOUNDS(a.err, 10u, lp, TILE)) {
-          skeys[lp] = key[j];
-          perm[lp] = static_cast<uint16_t>(li);
-        }
+        rank[j] = lp;
+        if (SNC_IN_BOUNDS(a.err, 10u, lp, TILE)) skeys[lp] = key[j];
       }
+    }
+    V val[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
+      val[j] = li < valid ? vin[li] : V(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
+      if (li < valid && SNC_IN_BOUNDS(a.err, 10u, rank[j], TILE)) vin[rank[j]] = val[j];
     }
     uint64_t prefix[DPT];
     look_back32<RADIX, DPT, W>(a, unit, prefix);
@@ -718,25 +747,35 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, K, V>::MINB))
       const uint64_t pos = globm[d] + i;
       if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
       a.keys_out[pos] = k;
-      a.vals_out[pos] = vin[perm[i]];
+      a.vals_out[pos] = vin[i];
     }
+    __syncthreads();  // the tile's buffers and counters are free again
+    if (tid == 0) take(0);
     __syncthreads();
+    cur = ticket_sh;
   }
 }
 
-template <int BITS, typename K, typename V>
+template <int BITS, int ITEMS, typename K, typename V>
 cudaError_t launch_onesweep_tma(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
-  using C = OnesweepTma<BITS, K, V>;
+  using C = OnesweepTma<BITS, ITEMS, K, V>;
   // Set on every launch: the attribute is per function and device, and
   // builds may run on several threads and devices.
-  cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS, K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(C::kSmem));
+  cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS, ITEMS, K, V>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C::kSmem));
   if (e != cudaSuccess) return e;
   const uint64_t tiles = (a.n + C::TILE - 1) / C::TILE;
   const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
   const uint64_t grid = tiles < resident ? tiles : resident;
-  onesweep_tma_kernel<BITS, K, V><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
+  onesweep_tma_kernel<BITS, ITEMS, K, V><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int BITS, typename K, typename V>
+cudaError_t launch_onesweep_tma_sel(const SortPasses& sp, const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
+  if (sp.items == 8) return launch_onesweep_tma<BITS, 8, K, V>(a, sms, st);
+  if (sp.items == 12) return launch_onesweep_tma<BITS, 12, K, V>(a, sms, st);
+  return launch_onesweep_tma<BITS, 16, K, V>(a, sms, st);
 }
 
 template <int BITS, int G, typename K, typename V>
@@ -754,17 +793,19 @@ cudaError_t launch_onesweep(const OnesweepArgs<K, V>& a, int sms, cudaStream_t s
   return cudaGetLastError();
 }
 
-// Keys per look-back unit for a digit width and group size.
-int onesweep_group(int bits, int group_tiles) {
-  (void)bits;
-  return kSortTile * (group_tiles > 0 ? group_tiles : 1);
+// Keys per look-back unit: one tile of the bulk-copy kernel, or a group of
+// 4096-key tiles.
+int onesweep_group(const SortPasses& sp) {
+  if (sp.group_tiles == 0 && sp.kernel_bits <= 9) return kSortThreads * (sp.items > 0 ? sp.items : kSortItems);
+  return kSortTile * (sp.group_tiles > 0 ? sp.group_tiles : 1);
 }
 
 template <int BITS, typename K, typename V>
-cudaError_t launch_onesweep_g(int group_tiles, const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
+cudaError_t launch_onesweep_g(const SortPasses& sp, int group_tiles, const OnesweepArgs<K, V>& a, int sms,
+                              cudaStream_t st) {
   switch (group_tiles) {
     case 0:
-      if (BITS <= 9) return launch_onesweep_tma<(BITS <= 9 ? BITS : 9), K, V>(a, sms, st);
+      if (BITS <= 9) return launch_onesweep_tma_sel<(BITS <= 9 ? BITS : 9), K, V>(sp, a, sms, st);
       return launch_onesweep<BITS, 1, K, V>(a, sms, st);
     case 1: return launch_onesweep<BITS, 1, K, V>(a, sms, st);
     case 4: return launch_onesweep<BITS, 4, K, V>(a, sms, st);
@@ -774,18 +815,19 @@ cudaError_t launch_onesweep_g(int group_tiles, const OnesweepArgs<K, V>& a, int 
 }
 
 template <typename K, typename V>
-cudaError_t launch_onesweep_bits(int bits, int group_tiles, const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
-  switch (bits) {
-    case 8: return launch_onesweep_g<8, K, V>(group_tiles, a, sms, st);
-    case 9: return launch_onesweep_g<9, K, V>(group_tiles, a, sms, st);
-    case 10: return launch_onesweep_g<10, K, V>(group_tiles, a, sms, st);
-    case 11: return launch_onesweep_g<11, K, V>(group_tiles, a, sms, st);
+cudaError_t launch_onesweep_bits(const SortPasses& sp, int group_tiles, const OnesweepArgs<K, V>& a, int sms,
+                                 cudaStream_t st) {
+  switch (sp.kernel_bits) {
+    case 8: return launch_onesweep_g<8, K, V>(sp, group_tiles, a, sms, st);
+    case 9: return launch_onesweep_g<9, K, V>(sp, group_tiles, a, sms, st);
+    case 10: return launch_onesweep_g<10, K, V>(sp, group_tiles, a, sms, st);
+    case 11: return launch_onesweep_g<11, K, V>(sp, group_tiles, a, sms, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 // Process-wide sort tuning (set by snc_set_tuning / the autotuner).
-SortTuning g_sort_tuning{8, 0};
+SortTuning g_sort_tuning{8, 0, 16};
 
 // Digit plan: the fewest passes of at most max_bits bits, widths as even as
 // possible, the kernel's digit width the widest of them (at least 8).
@@ -808,12 +850,12 @@ SortPasses plan_passes(int key_bits, const SortTuning& tune) {
   }
   sp.kernel_bits = widest < 8 ? 8 : widest;
   sp.group_tiles = (tune.group_tiles == 0 || tune.group_tiles == 1 || tune.group_tiles == 4) ? tune.group_tiles : 8;
+  sp.items = (tune.items == 8 || tune.items == 12) ? tune.items : 16;
   return sp;
 }
 
 size_t sort_scratch_bytes(uint64_t n, const SortPasses& sp) {
-  const uint64_t groups = (n + onesweep_group(sp.kernel_bits, sp.group_tiles) - 1) /
-                          onesweep_group(sp.kernel_bits, sp.group_tiles);
+  const uint64_t groups = (n + onesweep_group(sp) - 1) / onesweep_group(sp);
   const size_t status = static_cast<size_t>(groups ? groups : 1) * (1u << sp.kernel_bits) * sizeof(uint64_t);
   const size_t hist = static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long);
   const size_t start = static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(uint64_t);
@@ -837,7 +879,7 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 // and after each pass.
 SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp) {
   SortScratch l{};
-  const int group = onesweep_group(sp.kernel_bits, sp.group_tiles);
+  const int group = onesweep_group(sp);
   const uint64_t groups = (n + group - 1) / group;
   unsigned char* p = static_cast<unsigned char*>(scratch);
   l.status_bytes = static_cast<size_t>(groups ? groups : 1) * (1u << sp.kernel_bits) * sizeof(uint64_t);
@@ -862,7 +904,7 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
       for (int i = 0; i <= sp.n_passes; ++i) cudaEventRecord(pass_events[i], st);
     return cudaSuccess;
   }
-  const int group = onesweep_group(sp.kernel_bits, sp.group_tiles);
+  const int group = onesweep_group(sp);
   const uint64_t groups = (n + group - 1) / group;
   if (groups > 0x7FFFFFFFull) return cudaErrorInvalidValue;
   if ((sp.n_passes % 2 == 0) && (static_cast<const void*>(keys_tmp) == static_cast<const void*>(keys_in) ||
@@ -906,7 +948,8 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
       (n >= (1ull << 30) || !(aligned16(keys_in) && aligned16(vals_in) && aligned16(keys_out) &&
                               aligned16(vals_out) && (sp.n_passes < 2 || (aligned16(keys_tmp) && aligned16(vals_tmp))))))
     group_tiles = 1;
-  const size_t status32_bytes = static_cast<size_t>((n + kSortTile - 1) / kSortTile) * (1u << sp.kernel_bits) * 4u;
+  const uint64_t tile32 = onesweep_group(sp);  // the bulk-copy kernel's tile
+  const size_t status32_bytes = static_cast<size_t>((n + tile32 - 1) / tile32) * (1u << sp.kernel_bits) * 4u;
   const K* kin = keys_in;
   const V* vin = vals_in;
   for (int pass = 0; pass < sp.n_passes; ++pass) {
@@ -928,7 +971,7 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
     a.err = err;
     a.status32 = reinterpret_cast<uint32_t*>(status);
     if (group_tiles == 0 && (e = cudaMemsetAsync(status, 0, status32_bytes, st)) != cudaSuccess) return e;
-    if ((e = launch_onesweep_bits<K, V>(sp.kernel_bits, group_tiles, a, sms, st)) != cudaSuccess) return e;
+    if ((e = launch_onesweep_bits<K, V>(sp, group_tiles, a, sms, st)) != cudaSuccess) return e;
     if (pass_events) cudaEventRecord(pass_events[pass + 1], st);
     kin = kout;
     vin = vout;

@@ -16,7 +16,8 @@ constexpr int kDigitScanThreads = 256;
 struct SortPasses {
   int n_passes;
   int kernel_bits;  // digit width the pass kernel is instantiated for
-  int group_tiles;  // tiles per look-back unit (1, 4 or 8)
+  int group_tiles;  // tiles per look-back unit (1, 4 or 8); 0 = bulk-copy kernel
+  int items;        // bulk-copy kernel: keys per thread (8, 12 or 16)
   int shift[kMaxPasses];
   uint32_t mask[kMaxPasses];
 };
@@ -45,12 +46,13 @@ struct OnesweepArgs {
 struct SortTuning {
   int max_digit_bits;
   int group_tiles;
+  int items;      // keys per thread of the bulk-copy kernel
 };
 extern SortTuning g_sort_tuning;
 
 SortPasses plan_passes(int key_bits);  // with g_sort_tuning
 SortPasses plan_passes(int key_bits, const SortTuning& tune);
-int onesweep_group(int bits, int group_tiles);
+int onesweep_group(const SortPasses& sp);  // keys per look-back unit
 size_t sort_scratch_bytes(uint64_t n, const SortPasses& sp);
 // Where the parts of the sort's scratch live (sort_scratch_bytes in total).
 struct SortScratch {

@@ -67,7 +67,8 @@ class snc_config(ctypes.Structure):
 
 class snc_tuning(ctypes.Structure):
     _fields_ = [("sort_digit_bits", ctypes.c_int32), ("sort_group_tiles", ctypes.c_int32),
-                ("gen_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("gen_blocks_per_sm", ctypes.c_int32), ("sort_items", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class snc_stats(ctypes.Structure):
@@ -264,7 +265,7 @@ def snc_get_stats(ctx):
     return st
 
 
-def snc_set_tuning(sort_digit_bits=None, sort_group_tiles=None, gen_blocks_per_sm=None):
+def snc_set_tuning(sort_digit_bits=None, sort_group_tiles=None, gen_blocks_per_sm=None, sort_items=None):
     t = snc_get_tuning()
     if sort_digit_bits is not None:
         t.sort_digit_bits = int(sort_digit_bits)
@@ -272,6 +273,8 @@ def snc_set_tuning(sort_digit_bits=None, sort_group_tiles=None, gen_blocks_per_s
         t.sort_group_tiles = int(sort_group_tiles)
     if gen_blocks_per_sm is not None:
         t.gen_blocks_per_sm = int(gen_blocks_per_sm)
+    if sort_items is not None:
+        t.sort_items = int(sort_items)
     _check(load().snc_set_tuning(ctypes.byref(t)))
     return t
 

@@ -154,13 +154,14 @@ def test_launch_shape_independence(snc):
         np.testing.assert_array_equal(a[f], b[f])
 
 
-@pytest.mark.parametrize("digit_bits,group", [(11, 8), (8, 0), (9, 4)], ids=["d11g8", "d8tma", "d9g4"])
+@pytest.mark.parametrize("digit_bits,group,items", [(11, 8, 16), (8, 0, 16), (9, 4, 16), (8, 0, 12), (9, 0, 8)],
+                         ids=["d11g8", "d8tma", "d9g4", "d8tma_i12", "d9tma_i8"])
 @pytest.mark.parametrize("n_nodes,delay", [(4, Dist("const", 0.1)), (60, Dist("normal", 1.5, 0.75)),
                                            (3000, Dist("normal", 1.5, 0.75)),
                                            (600_000, Dist("normal", 1.5, 0.75)),
                                            (140_000, Dist("const", 6000.0))],
                          ids=["3bit", "12bit", "18bit", "26bit", "34bit_wide"])
-def test_every_pass_parity(snc, oracle_mod, n_nodes, delay, digit_bits, group):
+def test_every_pass_parity(snc, oracle_mod, n_nodes, delay, digit_bits, group, items):
     """The sort's buffers alternate per pass, so the result buffer depends on
     the parity of the pass count: cover odd and even counts for every kernel
     variant (1-4 passes of 8 bits on 32-bit keys, and a 34-bit key that
@@ -171,12 +172,13 @@ def test_every_pass_parity(snc, oracle_mod, n_nodes, delay, digit_bits, group):
                    weight=Dist("normal", 5.0, 1.0), delay=delay)])
     old = snc.snc_get_tuning()
     try:
-        snc.snc_set_tuning(sort_digit_bits=digit_bits, sort_group_tiles=group)
+        snc.snc_set_tuning(sort_digit_bits=digit_bits, sort_group_tiles=group, sort_items=items)
         net = snc.Network(spec).finalize()
         got = net.to_host()
         st = net.stats()
         net.close()
     finally:
-        snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles)
+        snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles,
+                           sort_items=old.sort_items)
     assert st.n_passes == -(-st.key_bits // digit_bits)
     assert_network_equal(got, oracle_mod.build(spec), f"passes={st.n_passes}")

@@ -42,16 +42,24 @@ def test_sort_matches_stable_argsort(torch_snc, n, bits):
     np.testing.assert_array_equal(kin.cpu().numpy().view(np.uint64), keys)  # input untouched
 
 
-TUNINGS = [(8, 0), (9, 0), (8, 1), (9, 4), (9, 8), (10, 8), (11, 4), (11, 8), (11, 1)]
+# (digit bits, tiles per look-back unit, keys per thread); the last only
+# matters for the bulk-copy kernel (group 0, 8-9 bit digits).
+TUNINGS = [(8, 0, 16), (9, 0, 16), (8, 0, 12), (9, 0, 12), (8, 0, 8), (9, 0, 8), (8, 1, 16), (9, 4, 16),
+           (9, 8, 16), (10, 8, 16), (11, 4, 16), (11, 8, 16), (11, 1, 16)]
 
 
-@pytest.mark.parametrize("bits,group", TUNINGS, ids=[f"d{b}g{g}" for b, g in TUNINGS])
-def test_every_sort_variant_matches_stable_argsort(torch_snc, bits, group):
+def _restore(snc, old):
+    snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles,
+                       sort_items=old.sort_items)
+
+
+@pytest.mark.parametrize("bits,group,items", TUNINGS, ids=[f"d{b}g{g}i{i}" for b, g, i in TUNINGS])
+def test_every_sort_variant_matches_stable_argsort(torch_snc, bits, group, items):
     """Every kernel variant the tuner can pick gives the stable order."""
     torch, snc = torch_snc
     old = snc.snc_get_tuning()
     try:
-        snc.snc_set_tuning(sort_digit_bits=bits, sort_group_tiles=group)
+        snc.snc_set_tuning(sort_digit_bits=bits, sort_group_tiles=group, sort_items=items)
         for n, kb in ((70_001, 43), (4096 * 9, 20), (1000, 64)):
             rng = np.random.default_rng(n + kb + bits)
             keys = rng.integers(0, 1 << min(kb, 63), n, dtype=np.uint64) & ~np.uint64(0x3F)
@@ -67,7 +75,7 @@ def test_every_sort_variant_matches_stable_argsort(torch_snc, bits, group):
             np.testing.assert_array_equal(kout.cpu().numpy().view(np.uint64), keys[order])
             np.testing.assert_array_equal(vout.cpu().numpy().view(np.uint32), vals[order])
     finally:
-        snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles)
+        _restore(snc, old)
 
 
 def test_misaligned_buffers_fall_back(torch_snc):
@@ -92,4 +100,4 @@ def test_misaligned_buffers_fall_back(torch_snc):
         np.testing.assert_array_equal(kout.cpu().numpy().view(np.uint64)[1:], keys[1:][order])
         np.testing.assert_array_equal(vout.cpu().numpy().view(np.uint32)[1:], vals[1:][order])
     finally:
-        snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles)
+        _restore(snc, old)
