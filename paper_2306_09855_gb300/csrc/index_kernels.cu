@@ -46,18 +46,20 @@ __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a
 #pragma unroll
         for (int j = 0; j < KPV; ++j) key[k * KPV + j] = kv[j];
       }
-      const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(a.vals + base);
+      if (!a.unpacked) {
+        const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(a.vals + base);
 #pragma unroll
-      for (int k = 0; k < kIndexItems / 2; ++k) {
-        const ulonglong2 v = __ldg(v2 + k);
-        val[2 * k] = v.x;
-        val[2 * k + 1] = v.y;
+        for (int k = 0; k < kIndexItems / 2; ++k) {
+          const ulonglong2 v = __ldg(v2 + k);
+          val[2 * k] = v.x;
+          val[2 * k + 1] = v.y;
+        }
       }
     } else {
 #pragma unroll
       for (int k = 0; k < kIndexItems; ++k) {
         key[k] = base + k < a.n ? __ldg(keys + base + k) : K(0);
-        val[k] = base + k < a.n ? __ldg(a.vals + base + k) : 0ull;
+        val[k] = base + k < a.n && !a.unpacked ? __ldg(a.vals + base + k) : 0ull;
       }
     }
     // Predecessor of this thread's first key: the previous lane's last key,
@@ -72,7 +74,9 @@ __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a
       const bool start = q < a.n && (q == 0 || key[k] != before);
       bits |= (start ? 1u : 0u) << k;
     }
-    if (full) {
+    if (a.unpacked) {
+      // target, weight and delay were written by the sort's last pass
+    } else if (full) {
       uint32_t tv[kIndexItems], wv[kIndexItems];
       uint16_t dv[kIndexItems];
 #pragma unroll

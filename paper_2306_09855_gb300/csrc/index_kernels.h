@@ -15,6 +15,7 @@ struct IndexArgs {
   const void* keys;          // sorted (source, delay) keys: uint32_t when key32, else uint64_t
   const uint64_t* vals;      // sorted (target, weight) values
   int key32;
+  int unpacked;              // the sort already wrote target / delay / weight: starts only
   uint64_t n;
   int delay_bits;
   uint32_t* target;

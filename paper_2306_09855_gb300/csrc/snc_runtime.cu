@@ -349,9 +349,11 @@ snc_status estimate_build(const snc_ctx* c, BuildEstimate* e) {
   const uint64_t pair = (lay.key32() ? 4 : 8) + 8;  // key + (target, weight) value
   // Generation and sort: two key/value buffers, sort scratch, the redraw
   // lists and tables, per-primary offsets.
-  const uint64_t gen = 2 * pair * n + scratch + 25 * redraw_slots + 8 * redraw_table + 16 * (primaries + 1);
-  // Index: sorted pairs, unpacked targets, delays and weights, group
-  // starts, row and group pointers (twice for batch members), block scans.
+  const uint64_t gen = 2 * pair * n + scratch +
+                       std::max<uint64_t>(25 * redraw_slots + 8 * redraw_table + 16 * (primaries + 1), 2 * n);
+  // Index: sorted keys, targets and weights (in the value buffer) and delays
+  // (or, when the sort could not unpack, separate target / weight arrays),
+  // group starts, row and group pointers (twice for batch members), scans.
   const uint64_t index = (pair + 10) * n + n / 8 + 8 * gc + 32 * (N + 1) + 16 * (primaries + 1);
   // Allocation granularity and the small per-build arrays.
   const uint64_t slack = 96ull << 20;
@@ -864,14 +866,24 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   uint64_t* vals_res = odd ? vals_b : vals_a;
   void* keys_oth = odd ? keys_a : keys_b;
   uint64_t* vals_oth = odd ? vals_a : vals_b;
+  // The last pass writes target and weight over the result value buffer
+  // (which it no longer needs) and the delays into their own array.
+  uint16_t* u_delay = static_cast<uint16_t*>(dev_alloc(c, n * sizeof(uint16_t)));
+  if (!u_delay) return fail(c, SNC_ERR_OOM, "device allocation failed (delays)");
+  SortUnpack unpack{};
+  unpack.target = reinterpret_cast<uint32_t*>(vals_res);
+  unpack.weight = reinterpret_cast<uint32_t*>(vals_res) + n;
+  unpack.delay = u_delay;
+  unpack.delay_mask = (1u << c->layout.delay_bits) - 1u;
+  bool fused = false;
   if (key32)
     SNC_CUDA(c, radix_sort_run(static_cast<const uint32_t*>(keys_a), vals_a, static_cast<uint32_t*>(keys_res), vals_res,
                                static_cast<uint32_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.ev + S.n_ev, /*hist_ready=*/true));
+                               S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused));
   else
     SNC_CUDA(c, radix_sort_run(static_cast<const uint64_t*>(keys_a), vals_a, static_cast<uint64_t*>(keys_res), vals_res,
                                static_cast<uint64_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.ev + S.n_ev, /*hist_ready=*/true));
+                               S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused));
   S.n_ev += c->passes.n_passes + 1;
   if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
   c->stats.n_passes = c->passes.n_passes;
@@ -883,9 +895,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // Index: unpack target / delay / weight, group starts, row_ptr and p_i.
   const uint64_t n_delay_values = max_step;
   const uint64_t group_cap = std::max<uint64_t>(1, std::min<uint64_t>(n, total_nodes * n_delay_values));
-  uint32_t* u_target = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
-  uint16_t* u_delay = static_cast<uint16_t*>(dev_alloc(c, n * sizeof(uint16_t)));
-  float* u_weight = static_cast<float*>(dev_alloc(c, n * sizeof(float)));
+  uint32_t* u_target = fused ? unpack.target : static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+  float* u_weight = fused ? reinterpret_cast<float*>(unpack.weight) : static_cast<float*>(dev_alloc(c, n * sizeof(float)));
   uint64_t* u_group_first = static_cast<uint64_t*>(dev_alloc(c, group_cap * sizeof(uint64_t)));
   uint64_t* u_row_ptr = static_cast<uint64_t*>(dev_alloc(c, (total_nodes + 1) * sizeof(uint64_t)));
   uint64_t* u_group_ptr = static_cast<uint64_t*>(dev_alloc(c, (total_nodes + 1) * sizeof(uint64_t)));
@@ -902,6 +913,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     ia.keys = keys_res;
     ia.vals = vals_res;
     ia.key32 = key32 ? 1 : 0;
+    ia.unpacked = fused ? 1 : 0;
     ia.n = n;
     ia.delay_bits = c->layout.delay_bits;
     ia.target = u_target;
@@ -997,7 +1009,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   dev_free(c, boffsets);
   dev_free(c, iscan);
   dev_free(c, keys_res);
-  dev_free(c, vals_res);
+  if (!fused) dev_free(c, vals_res);  // else it holds the targets and weights
   dev_free(c, d_direct);
   dev_free(c, d_prim_off);
 

@@ -154,6 +154,22 @@ __global__ void radix_digit_scan_kernel(const unsigned long long* __restrict__ h
   }
 }
 
+// Writes one sorted pair, or on an unpacking last pass its target, weight
+// and delay.
+template <bool UNPACK, typename K, typename V>
+__device__ __forceinline__ void emit_pair(const OnesweepArgs<K, V>& a, uint64_t pos, K k, V v) {
+  a.keys_out[pos] = k;
+  if constexpr (UNPACK && sizeof(V) == 8) {
+    {
+      a.unpack_target[pos] = static_cast<uint32_t>(v >> 32);
+      a.unpack_weight[pos] = static_cast<uint32_t>(v);
+      a.unpack_delay[pos] = static_cast<uint16_t>(static_cast<uint32_t>(k) & a.unpack_delay_mask);
+      return;
+    }
+  }
+  a.vals_out[pos] = v;
+}
+
 // ---------------------------------------------------------------------------
 // One onesweep pass.  Tile = 256 threads x 16 keys; warp w ranks keys
 // [w*512, (w+1)*512) of the tile lane-interleaved, so that ranking warp by
@@ -245,7 +261,7 @@ __device__ __forceinline__ void look_back(const A& a, uint32_t unit, uint64_t (&
   }
 }
 
-template <int BITS, int G, typename K, typename V>
+template <int BITS, int G, bool UNPACK, typename K, typename V>
 __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
     onesweep_kernel(OnesweepArgs<K, V> a) {
   using C = Onesweep<BITS, G, K, V>;
@@ -410,8 +426,7 @@ __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
         const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
         const uint64_t pos = run[d] + (i - local_start[d]);
         if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
-        a.keys_out[pos] = k;
-        a.vals_out[pos] = svals[i];
+        emit_pair<UNPACK>(a, pos, k, svals[i]);
       }
       __syncthreads();  // all reads of run[] for this tile are done
 #pragma unroll
@@ -580,7 +595,7 @@ __device__ __forceinline__ bool tile_wait(uint64_t* bar, uint32_t parity) {
 // One pass.  A persistent block takes tiles from the ticket in increasing
 // order and sorts each before taking the next, so the lowest unfinished tile
 // is always being sorted and every look-back wait ends.
-template <int BITS, int ITEMS, typename K, typename V>
+template <int BITS, int ITEMS, bool UNPACK, typename K, typename V>
 __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>::MINB))
     onesweep_tma_kernel(OnesweepArgs<K, V> a) {
   using C = OnesweepTma<BITS, ITEMS, K, V>;
@@ -746,8 +761,7 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
       const uint64_t pos = globm[d] + i;
       if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
-      a.keys_out[pos] = k;
-      a.vals_out[pos] = vin[i];
+      emit_pair<UNPACK>(a, pos, k, vin[i]);
     }
     __syncthreads();  // the tile's buffers and counters are free again
     if (tid == 0) take(0);
@@ -756,19 +770,28 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
   }
 }
 
-template <int BITS, int ITEMS, typename K, typename V>
-cudaError_t launch_onesweep_tma(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
+template <int BITS, int ITEMS, bool UNPACK, typename K, typename V>
+cudaError_t launch_onesweep_tma_u(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
   using C = OnesweepTma<BITS, ITEMS, K, V>;
   // Set on every launch: the attribute is per function and device, and
   // builds may run on several threads and devices.
-  cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS, ITEMS, K, V>,
+  cudaError_t e = cudaFuncSetAttribute(onesweep_tma_kernel<BITS, ITEMS, UNPACK, K, V>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C::kSmem));
   if (e != cudaSuccess) return e;
   const uint64_t tiles = (a.n + C::TILE - 1) / C::TILE;
   const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
   const uint64_t grid = tiles < resident ? tiles : resident;
-  onesweep_tma_kernel<BITS, ITEMS, K, V><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
+  onesweep_tma_kernel<BITS, ITEMS, UNPACK, K, V><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
   return cudaGetLastError();
+}
+
+// The unpacking variant exists for 64-bit values only (the build's sort).
+template <int BITS, int ITEMS, typename K, typename V>
+cudaError_t launch_onesweep_tma(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
+  if constexpr (sizeof(V) == 8) {
+    if (a.unpack_target) return launch_onesweep_tma_u<BITS, ITEMS, true, K, V>(a, sms, st);
+  }
+  return launch_onesweep_tma_u<BITS, ITEMS, false, K, V>(a, sms, st);
 }
 
 template <int BITS, typename K, typename V>
@@ -778,19 +801,27 @@ cudaError_t launch_onesweep_tma_sel(const SortPasses& sp, const OnesweepArgs<K, 
   return launch_onesweep_tma<BITS, 16, K, V>(a, sms, st);
 }
 
-template <int BITS, int G, typename K, typename V>
-cudaError_t launch_onesweep(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
+template <int BITS, int G, bool UNPACK, typename K, typename V>
+cudaError_t launch_onesweep_u(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
   using C = Onesweep<BITS, G, K, V>;
   // Set on every launch: the attribute is per function and device, and
   // builds may run on several threads and devices.
-  cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS, G, K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(C::kSmem));
+  cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS, G, UNPACK, K, V>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(C::kSmem));
   if (e != cudaSuccess) return e;
   const uint64_t units = (a.n + C::GROUP - 1) / C::GROUP;
   const uint64_t resident = static_cast<uint64_t>(C::MINB) * sms;
   const uint64_t grid = units < resident ? units : resident;
-  onesweep_kernel<BITS, G, K, V><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
+  onesweep_kernel<BITS, G, UNPACK, K, V><<<static_cast<unsigned>(grid), C::TPB, C::kSmem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int BITS, int G, typename K, typename V>
+cudaError_t launch_onesweep(const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
+  if constexpr (sizeof(V) == 8) {
+    if (a.unpack_target) return launch_onesweep_u<BITS, G, true, K, V>(a, sms, st);
+  }
+  return launch_onesweep_u<BITS, G, false, K, V>(a, sms, st);
 }
 
 // Keys per look-back unit: one tile of the bulk-copy kernel, or a group of
@@ -896,7 +927,8 @@ SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp)
 template <typename K, typename V>
 cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* vals_out, K* keys_tmp, V* vals_tmp,
                            uint64_t n, const SortPasses& sp, void* scratch, uint32_t* err, cudaStream_t st,
-                           cudaEvent_t* pass_events, bool hist_ready) {
+                           cudaEvent_t* pass_events, bool hist_ready, const SortUnpack* unpack, bool* fused) {
+  if (fused) *fused = false;
   // The pass kernels shift keys by up to the key width minus one.
   if (static_cast<size_t>(sp.shift[sp.n_passes - 1]) >= 8 * sizeof(K)) return cudaErrorInvalidValue;
   if (n == 0) {
@@ -970,6 +1002,13 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
     a.epoch = static_cast<uint32_t>(pass + 1);
     a.err = err;
     a.status32 = reinterpret_cast<uint32_t*>(status);
+    if (sizeof(V) == 8 && unpack && pass == sp.n_passes - 1) {
+      a.unpack_target = unpack->target;
+      a.unpack_weight = unpack->weight;
+      a.unpack_delay = unpack->delay;
+      a.unpack_delay_mask = unpack->delay_mask;
+      if (fused) *fused = true;
+    }
     if (group_tiles == 0 && (e = cudaMemsetAsync(status, 0, status32_bytes, st)) != cudaSuccess) return e;
     if ((e = launch_onesweep_bits<K, V>(sp, group_tiles, a, sms, st)) != cudaSuccess) return e;
     if (pass_events) cudaEventRecord(pass_events[pass + 1], st);
@@ -981,12 +1020,15 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
 
 template cudaError_t radix_sort_run<uint64_t, uint32_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*,
                                                         uint64_t*, uint32_t*, uint64_t, const SortPasses&, void*,
-                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool);
+                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool,
+                                                        const SortUnpack*, bool*);
 template cudaError_t radix_sort_run<uint32_t, uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*,
                                                         uint32_t*, uint64_t*, uint64_t, const SortPasses&, void*,
-                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool);
+                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool,
+                                                        const SortUnpack*, bool*);
 template cudaError_t radix_sort_run<uint64_t, uint64_t>(const uint64_t*, const uint64_t*, uint64_t*, uint64_t*,
                                                         uint64_t*, uint64_t*, uint64_t, const SortPasses&, void*,
-                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool);
+                                                        uint32_t*, cudaStream_t, cudaEvent_t*, bool,
+                                                        const SortUnpack*, bool*);
 
 }  // namespace snc

@@ -39,6 +39,21 @@ struct OnesweepArgs {
   uint32_t epoch;               // 1..16383, distinct for every pass sharing `status`
   uint32_t* err;
   uint32_t* status32;           // bulk-copy kernel: 32-bit words [tile][digit], cleared per pass
+  // Last pass of a build's sort: write the sorted values as separate target,
+  // weight and delay arrays instead of vals_out (null otherwise).
+  uint32_t* unpack_target;
+  uint32_t* unpack_weight;
+  uint16_t* unpack_delay;
+  uint32_t unpack_delay_mask;
+};
+
+// Separate output arrays of the last pass for (source, delay) keys with
+// (target << 32 | weight bits) values.
+struct SortUnpack {
+  uint32_t* target;
+  uint32_t* weight;
+  uint16_t* delay;
+  uint32_t delay_mask;
 };
 
 // Sort parameters chosen by the tuner: widest digit (8..11 bits) and tiles
@@ -68,9 +83,12 @@ SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp)
 // hist_ready: the digit counts are already in the scratch's hist area (for
 // example accumulated by the kernels that produced the keys).  Instantiated
 // for (uint64_t, uint32_t), (uint32_t, uint64_t) and (uint64_t, uint64_t).
+// unpack (64-bit values only): the last pass writes unpack's arrays instead
+// of vals_out (which it then leaves untouched); *fused reports whether it did.
 template <typename K, typename V>
 cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* vals_out, K* keys_tmp, V* vals_tmp,
                            uint64_t n, const SortPasses& sp, void* scratch, uint32_t* err, cudaStream_t st,
-                           cudaEvent_t* pass_events, bool hist_ready = false);
+                           cudaEvent_t* pass_events, bool hist_ready = false, const SortUnpack* unpack = nullptr,
+                           bool* fused = nullptr);
 
 }  // namespace snc
