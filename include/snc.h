@@ -176,6 +176,28 @@ snc_status snc_finalize(snc_ctx* ctx);
  * STATE: a context already finalized.  Other errors as snc_finalize. */
 snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n);
 
+/* The same batched build, recorded as a CUDA graph so that the networks can
+ * be rebuilt with new seeds by replaying the recorded device work
+ * (snc_batch_rebuild): repeated trials of one model, as in the paper's
+ * validation over many seeds (Sec. 2.7), or parameter scans over seeds.
+ * The first build runs immediately and gives the same result as
+ * snc_batch_finalize.  The build keeps all its temporary buffers (its peak
+ * device memory stays allocated).  Stage timers report the first build.
+ * UNSUPPORTED: a member uses pairwise_bernoulli or fixed_total_number without
+ * autapses or multapses (their counts need host round trips).  Other errors
+ * as snc_batch_finalize; CUDA if the capture fails. */
+snc_status snc_batch_finalize_graph(snc_ctx* const* ctxs, int n);
+
+/* Rebuilds every network of ctx's graph build (ctx: any member) with
+ * seeds[m] for member m (n = number of members, in the order given to
+ * snc_batch_finalize_graph), in place: the views keep their addresses, and
+ * the connection counts stay the same (the rules that allow graph builds
+ * have seed-independent counts); group counts and contents change.
+ * Asynchronous on the build's stream; waits for the previous build first.
+ * Result = snc_batch_finalize of the same contexts with those seeds.
+ * STATE: not a graph build.  INVALID_ARG: null pointers or n mismatch. */
+snc_status snc_batch_rebuild(snc_ctx* ctx, const uint64_t* seeds, int n);
+
 /* Waits for the context's queued work and reports device-side failures
  * (TIMEOUT for a bounded wait that expired, CUDA for a launch error). */
 snc_status snc_synchronize(snc_ctx* ctx);

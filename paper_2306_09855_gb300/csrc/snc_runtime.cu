@@ -57,9 +57,65 @@ struct Storage {
   bool synced = false;
   uint32_t err_bits = 0;
   uint64_t n_groups = 0;
+  // Host -> device copies go through pinned staging chunks that live as long
+  // as the build, so that a recorded graph can replay them.
+  std::vector<std::pair<unsigned char*, size_t>> stage_chunks;  // (memory, capacity)
+  size_t stage_used = 0;    // bytes used in the last chunk
+  size_t stage_total = 0;   // bytes staged by the current build
+  // Graph builds (snc_batch_finalize_graph): mode 1 keeps every buffer of
+  // the first build (no frees) and records the allocation order; mode 2 hands
+  // the recorded buffers out again while the same build is captured.
+  int mode = 0;
+  bool capturing = false;
+  std::vector<DevBuf> rec;
+  size_t rec_pos = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t own_stream = nullptr;  // graph builds run on a stream of their own
+  struct SeedSite {
+    DevProj* host;  // staged copy of a projection record
+    int member;
+    uint32_t local;
+  };
+  std::vector<SeedSite> seed_sites;
+  uint64_t generation = 0;  // bumped by every replay: member views are refreshed
+
+  void* stage(const void* src, size_t bytes) {
+    const size_t need = (bytes + 15) & ~static_cast<size_t>(15);
+    if (stage_chunks.empty() || stage_used + need > stage_chunks.back().second) {
+      if (capturing) return nullptr;  // reserved before the capture
+      const size_t cap = std::max<size_t>(need, 1u << 20);
+      void* p = nullptr;
+      if (cudaMallocHost(&p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      stage_chunks.push_back({static_cast<unsigned char*>(p), cap});
+      stage_used = 0;
+    }
+    unsigned char* dst = stage_chunks.back().first + stage_used;
+    std::memcpy(dst, src, bytes);
+    stage_used += need;
+    stage_total += need;
+    return dst;
+  }
+  bool reserve_stage(size_t bytes) {
+    void* p = nullptr;
+    const size_t cap = std::max<size_t>(bytes, 1u << 20);
+    if (cudaMallocHost(&p, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    stage_chunks.push_back({static_cast<unsigned char*>(p), cap});
+    stage_used = 0;
+    return true;
+  }
 
   void* get(size_t bytes) {
     if (bytes == 0) bytes = 256;
+    if (mode == 2) {  // replaying the recorded allocation order
+      if (rec_pos >= rec.size() || rec[rec_pos].bytes != bytes) return nullptr;
+      return rec[rec_pos++].p;
+    }
     void* p = nullptr;
     if (custom_alloc) {
       p = alloc.alloc(bytes, stream, alloc.user);
@@ -76,11 +132,12 @@ struct Storage {
       bufs.push_back({p, bytes});
       live_bytes += bytes;
       if (live_bytes > peak_bytes) peak_bytes = live_bytes;
+      if (mode == 1) rec.push_back({p, bytes});
     }
     return p;
   }
   void put(void* p) {
-    if (!p) return;
+    if (!p || mode != 0) return;  // graph builds keep every buffer
     for (size_t i = 0; i < bufs.size(); ++i) {
       if (bufs[i].p == p) {
         if (custom_alloc)
@@ -113,12 +170,16 @@ struct Storage {
   ~Storage() {
     cudaSetDevice(device);
     cudaStreamSynchronize(stream);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    mode = 0;
     while (!bufs.empty()) put(bufs.back().p);
     cudaStreamSynchronize(stream);
+    if (own_stream) cudaStreamDestroy(own_stream);
     if (events_ok)
       for (int i = 0; i < kMaxEvents; ++i) cudaEventDestroy(ev[i]);
     if (h_pinned) cudaFreeHost(h_pinned);
     if (h_bases) cudaFreeHost(h_bases);
+    for (auto& ch : stage_chunks) cudaFreeHost(ch.first);
     cudaGetLastError();
   }
 };
@@ -139,8 +200,10 @@ struct snc_ctx {
   // finalize; a batch concatenates its members' nodes).
   int member = 0;
   uint64_t node_base = 0;
-  // Results: device views; for batch members resolved at synchronize.
+  // Results: device views; for batch members resolved at synchronize (and
+  // again after every graph replay of the build).
   bool view_ready = false;
+  uint64_t view_gen = 0;
   uint64_t n_syn = 0;
   uint64_t n_groups = 0;
   uint64_t group_cap = 0;
@@ -185,6 +248,17 @@ void* dev_alloc(snc_ctx* c, size_t bytes) {
 }
 
 void dev_free(snc_ctx* c, void* p) { c->store->put(p); }
+
+// Host -> device copy through the build's pinned staging area; *staged
+// receives the staged host copy.
+cudaError_t upload(snc_ctx* c, void* dst, const void* src, size_t bytes, void** staged = nullptr) {
+  if (bytes == 0) return cudaSuccess;
+  void* h = c->store->stage(src, bytes);
+  if (!h) return cudaErrorMemoryAllocation;
+  if (staged) *staged = h;
+  c->stats.h2d_bytes += bytes;
+  return cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, c->store->stream);
+}
 
 int bit_width(uint64_t v) {
   int b = 0;
@@ -462,8 +536,14 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   SNC_CUDA(c, cudaSetDevice(c->device));
   Storage& S = *c->store;
   cudaStream_t st = c->stream;
-  S.n_ev = 0;
-  cudaEventRecord(S.ev[S.n_ev++], st);
+  // Stage timers (not while the build is being captured into a graph).
+  const auto mark = [&]() {
+    if (!S.capturing) cudaEventRecord(S.ev[S.n_ev++], st);
+  };
+  if (!S.capturing) S.n_ev = 0;
+  mark();
+  S.seed_sites.clear();
+  S.stage_total = 0;
 
   // The union of the members' projections.
   struct UnionProj {
@@ -471,6 +551,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     const snc_ctx* owner;
     uint32_t base;
     uint32_t local;
+    int member;
   };
   std::vector<uint64_t> node_base(static_cast<size_t>(n_members) + 1, 0);
   uint64_t max_nodes = 0;
@@ -479,7 +560,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     node_base[m + 1] = node_base[m] + members[m]->n_nodes;
     max_nodes = std::max<uint64_t>(max_nodes, members[m]->n_nodes);
     for (size_t i = 0; i < members[m]->projs.size(); ++i)
-      ups.push_back({&members[m]->projs[i], members[m], static_cast<uint32_t>(node_base[m]), static_cast<uint32_t>(i)});
+      ups.push_back({&members[m]->projs[i], members[m], static_cast<uint32_t>(node_base[m]), static_cast<uint32_t>(i), m});
   }
   const uint64_t total_nodes = node_base[n_members];
   if (total_nodes > 0xFFFFFFFFull) return fail(c, SNC_ERR_UNSUPPORTED, "more than 2^32 - 1 nodes in one build");
@@ -553,10 +634,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   S.d_n_groups = static_cast<uint64_t*>(dev_alloc(c, sizeof(uint64_t)));
   if (!d_thr || !d_guide || !d_proj || !S.d_err || !S.d_n_groups)
     return fail(c, SNC_ERR_OOM, "device allocation failed (tables)");
-  SNC_CUDA(c, cudaMemcpyAsync(d_thr, thr_blob.data(), thr_blob.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-  c->stats.h2d_bytes += thr_blob.size() * sizeof(uint32_t) + guide_blob.size() * sizeof(uint16_t);
-  SNC_CUDA(c, cudaMemcpyAsync(d_guide, guide_blob.data(), guide_blob.size() * sizeof(uint16_t),
-                              cudaMemcpyHostToDevice, st));
+  SNC_CUDA(c, upload(c, d_thr, thr_blob.data(), thr_blob.size() * sizeof(uint32_t)));
+  SNC_CUDA(c, upload(c, d_guide, guide_blob.data(), guide_blob.size() * sizeof(uint16_t)));
   SNC_CUDA(c, cudaMemsetAsync(S.d_err, 0, 8 * sizeof(uint64_t), st));
   SNC_CUDA(c, cudaMemsetAsync(S.d_n_groups, 0, sizeof(uint64_t), st));
 
@@ -574,8 +653,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   if (!bern.empty()) {
     const uint64_t n_targets = bern_prefix.back();
     const int nb = static_cast<int>(bern.size());
-    SNC_CUDA(c, cudaMemcpyAsync(d_proj, dp.data(), np * sizeof(DevProj), cudaMemcpyHostToDevice, st));
-    c->stats.h2d_bytes += np * sizeof(DevProj);
+    SNC_CUDA(c, upload(c, d_proj, dp.data(), np * sizeof(DevProj)));
     d_prim_off = static_cast<uint64_t*>(dev_alloc(c, (n_targets + 1) * sizeof(uint64_t)));
     uint32_t* d_counts = static_cast<uint32_t*>(dev_alloc(c, (n_targets + 1) * sizeof(uint32_t)));
     uint64_t* d_scan_tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_targets) + 1) * sizeof(uint64_t)));
@@ -584,10 +662,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     uint64_t* d_totals = static_cast<uint64_t*>(dev_alloc(c, bern.size() * sizeof(uint64_t)));
     if (!d_prim_off || !d_counts || !d_scan_tmp || !d_blist || !d_bprefix || !d_totals)
       return fail(c, SNC_ERR_OOM, "device allocation failed (counts)");
-    SNC_CUDA(c, cudaMemcpyAsync(d_blist, bern.data(), bern.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    SNC_CUDA(c, cudaMemcpyAsync(d_bprefix, bern_prefix.data(), bern_prefix.size() * sizeof(uint64_t),
-                                cudaMemcpyHostToDevice, st));
-    c->stats.h2d_bytes += bern.size() * sizeof(uint32_t) + bern_prefix.size() * sizeof(uint64_t);
+    SNC_CUDA(c, upload(c, d_blist, bern.data(), bern.size() * sizeof(uint32_t)));
+    SNC_CUDA(c, upload(c, d_bprefix, bern_prefix.data(), bern_prefix.size() * sizeof(uint64_t)));
     const unsigned cgrid =
         static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>((n_targets + 255) / 256, c->sms * 16ull)));
     bernoulli_count_kernel<<<cgrid, 256, 0, st>>>(d_proj, d_blist, d_bprefix, nb, d_thr, d_guide, d_counts);
@@ -609,11 +685,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     dev_free(c, d_bprefix);
     dev_free(c, d_totals);
   }
-  cudaEventRecord(S.ev[S.n_ev++], st);
+  mark();
 
   // Output offsets and generation chunks.
   uint64_t off = 0;
   std::vector<DevProj> direct;
+  std::vector<size_t> direct_src;  // union index of each direct projection
   uint64_t chunk = 0;
   for (size_t i = 0; i < np; ++i) {
     const Projection& p = *ups[i].p;
@@ -632,18 +709,25 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     d.chunk_begin = chunk;
     chunk += d.n_chunks;
     direct.push_back(d);
+    direct_src.push_back(i);
   }
   const uint64_t n_total = off;
+  // The projection records carry the Philox keys: their staged copies are
+  // where a graph replay puts new seeds.
   if (np > 0) {
-    SNC_CUDA(c, cudaMemcpyAsync(d_proj, dp.data(), np * sizeof(DevProj), cudaMemcpyHostToDevice, st));
-    c->stats.h2d_bytes += np * sizeof(DevProj);
+    void* h = nullptr;
+    SNC_CUDA(c, upload(c, d_proj, dp.data(), np * sizeof(DevProj), &h));
+    for (size_t i = 0; i < np; ++i)
+      S.seed_sites.push_back({static_cast<DevProj*>(h) + i, ups[i].member, ups[i].local});
   }
   DevProj* d_direct = nullptr;
   if (!direct.empty()) {
     d_direct = static_cast<DevProj*>(dev_alloc(c, direct.size() * sizeof(DevProj)));
     if (!d_direct) return fail(c, SNC_ERR_OOM, "device allocation failed (projections)");
-    SNC_CUDA(c, cudaMemcpyAsync(d_direct, direct.data(), direct.size() * sizeof(DevProj), cudaMemcpyHostToDevice, st));
-    c->stats.h2d_bytes += direct.size() * sizeof(DevProj);
+    void* h = nullptr;
+    SNC_CUDA(c, upload(c, d_direct, direct.data(), direct.size() * sizeof(DevProj), &h));
+    for (size_t k = 0; k < direct.size(); ++k)
+      S.seed_sites.push_back({static_cast<DevProj*>(h) + k, ups[direct_src[k]].member, ups[direct_src[k]].local});
   }
 
   // Buffers: generated keys/values, the sort's second buffer, outputs.
@@ -710,10 +794,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       uint32_t* d_slist = static_cast<uint32_t*>(dev_alloc(c, slist.size() * sizeof(uint32_t)));
       uint64_t* d_sprefix = static_cast<uint64_t*>(dev_alloc(c, sprefix.size() * sizeof(uint64_t)));
       if (!d_slist || !d_sprefix) return fail(c, SNC_ERR_OOM, "device allocation failed (sampler list)");
-      SNC_CUDA(c, cudaMemcpyAsync(d_slist, slist.data(), slist.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-      SNC_CUDA(c, cudaMemcpyAsync(d_sprefix, sprefix.data(), sprefix.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
-                                  st));
-      c->stats.h2d_bytes += slist.size() * sizeof(uint32_t) + sprefix.size() * sizeof(uint64_t);
+      SNC_CUDA(c, upload(c, d_slist, slist.data(), slist.size() * sizeof(uint32_t)));
+      SNC_CUDA(c, upload(c, d_sprefix, sprefix.data(), sprefix.size() * sizeof(uint64_t)));
       SamplerArgs s{};
       s.gen = g;
       s.projs = d_proj;
@@ -802,8 +884,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         }
       }
       a.rp = d_rp;
-      SNC_CUDA(c, cudaMemcpyAsync(d_rp, rps.data(), rps.size() * sizeof(RedrawProj), cudaMemcpyHostToDevice, st));
-      c->stats.h2d_bytes += rps.size() * sizeof(RedrawProj);
+      SNC_CUDA(c, upload(c, d_rp, rps.data(), rps.size() * sizeof(RedrawProj)));
       SNC_CUDA(c, cudaMemsetAsync(a.lost, 0, n_slots, st));
       SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
       a.next_pending = pend_a;
@@ -855,7 +936,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       dev_free(c, a.table_vals);
     }
   }
-  cudaEventRecord(S.ev[S.n_ev++], st);
+  mark();
 
   // Stable sort by (source, delay): equal keys keep generation order.  The
   // passes ping-pong between the two buffers; the result lands in
@@ -879,12 +960,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   if (key32)
     SNC_CUDA(c, radix_sort_run(static_cast<const uint32_t*>(keys_a), vals_a, static_cast<uint32_t*>(keys_res), vals_res,
                                static_cast<uint32_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused));
+                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused));
   else
     SNC_CUDA(c, radix_sort_run(static_cast<const uint64_t*>(keys_a), vals_a, static_cast<uint64_t*>(keys_res), vals_res,
                                static_cast<uint64_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused));
-  S.n_ev += c->passes.n_passes + 1;
+                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused));
+  if (!S.capturing) S.n_ev += c->passes.n_passes + 1;
   if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
   c->stats.n_passes = c->passes.n_passes;
   c->stats.key_bits = c->layout.total_bits();
@@ -965,8 +1046,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       return fail(c, SNC_ERR_OOM, "device allocation failed (batch views)");
     std::vector<uint64_t> meta(node_base.begin(), node_base.end());
     meta.insert(meta.end(), local_base.begin(), local_base.end());
-    SNC_CUDA(c, cudaMemcpyAsync(d_meta, meta.data(), meta.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    c->stats.h2d_bytes += meta.size() * sizeof(uint64_t);
+    SNC_CUDA(c, upload(c, d_meta, meta.data(), meta.size() * sizeof(uint64_t)));
     RebaseArgs rb{};
     rb.row_ptr = u_row_ptr;
     rb.group_ptr = u_group_ptr;
@@ -1003,7 +1083,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     c->stats.d2h_bytes += 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t);
     dev_free(c, d_meta);
   }
-  cudaEventRecord(S.ev[S.n_ev++], st);
+  mark();
   dev_free(c, starts);
   dev_free(c, bcounts);
   dev_free(c, boffsets);
@@ -1062,6 +1142,99 @@ snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n) {
   return st;
 }
 
+namespace {
+// A graph build replays the recorded device work: it needs every count known
+// on the host before generation (no pairwise_bernoulli count phase, no
+// total-number redraw rounds).
+bool graph_eligible(const snc_ctx* c) {
+  for (const Projection& p : c->projs)
+    if (p.rule.kind == SNC_PAIRWISE_BERNOULLI || is_total_redraw(p)) return false;
+  return true;
+}
+}  // namespace
+
+snc_status snc_batch_finalize_graph(snc_ctx* const* ctxs, int n) {
+  if (!ctxs || n <= 0) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: no contexts");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: null context");
+    if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
+    if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
+    if (!graph_eligible(ctxs[i]))
+      return fail(ctxs[i], SNC_ERR_UNSUPPORTED,
+                  "graph build: pairwise_bernoulli and total-number redraws need host round trips");
+  }
+  snc_ctx* c = ctxs[0];
+  Storage& S = *c->store;
+  SNC_CUDA(c, cudaSetDevice(c->device));
+  // A stream of the build's own (the legacy default stream cannot be
+  // captured), ordered after the work already queued on the caller's.
+  cudaStream_t own = nullptr;
+  SNC_CUDA(c, cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+  S.own_stream = own;
+  cudaEvent_t ready = nullptr;
+  SNC_CUDA(c, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  cudaEventRecord(ready, c->stream);
+  cudaStreamWaitEvent(own, ready, 0);
+  cudaEventDestroy(ready);
+  for (int i = 0; i < n; ++i) snc::rebind_build(ctxs[i], own, nullptr);
+  // First build: runs now and keeps every buffer, recording their order.
+  S.mode = 1;
+  S.rec.clear();
+  snc_status st = finalize_build(ctxs, n);
+  if (st != SNC_OK) {
+    for (int i = 1; i < n; ++i) ctxs[i]->err = ctxs[0]->err;
+    return st;
+  }
+  // Second pass over the same plan, captured: the same buffers in the same
+  // order, copies from a fresh staging chunk that the graph keeps reading.
+  if (!S.reserve_stage(S.stage_total + 4096)) return fail(c, SNC_ERR_OOM, "pinned staging allocation failed");
+  S.mode = 2;
+  S.rec_pos = 0;
+  S.capturing = true;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(S.stream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = finalize_build(ctxs, n);
+    const cudaError_t e2 = cudaStreamEndCapture(S.stream, &graph);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  S.capturing = false;
+  S.mode = 1;
+  if (e == cudaSuccess && st == SNC_OK) e = cudaGraphInstantiate(&S.gexec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    S.gexec = nullptr;
+    return fail(c, SNC_ERR_CUDA, "graph capture of the build failed: %s", cudaGetErrorString(e));
+  }
+  if (st != SNC_OK) return st;
+  return SNC_OK;
+}
+
+snc_status snc_batch_rebuild(snc_ctx* ctx, const uint64_t* seeds, int n) {
+  if (!ctx || !seeds) return fail(ctx, SNC_ERR_INVALID_ARG, "rebuild: null argument");
+  if (!ctx->finalized || !ctx->store || !ctx->store->gexec)
+    return fail(ctx, SNC_ERR_STATE, "rebuild: the context was not built by snc_batch_finalize_graph");
+  Storage& S = *ctx->store;
+  if (n != S.n_members) return fail(ctx, SNC_ERR_INVALID_ARG, "rebuild: %d seeds for %d networks", n, S.n_members);
+  SNC_CUDA(ctx, cudaSetDevice(ctx->device));
+  // The replayed copies read the staged records: the previous build must be done.
+  SNC_CUDA(ctx, cudaStreamSynchronize(S.stream));
+  for (const Storage::SeedSite& site : S.seed_sites) {
+    const uint64_t seed = seeds[site.member];
+    site.host->k0 = static_cast<uint32_t>(seed);
+    site.host->k1 = static_cast<uint32_t>(seed >> 32) ^ site.local;
+  }
+  ctx->cfg.seed = seeds[ctx->member];
+  S.synced = false;
+  ++S.generation;
+  SNC_CUDA(ctx, cudaGraphLaunch(S.gexec, S.stream));
+  ++ctx->stats.kernel_launches;
+  return SNC_OK;
+}
+
 snc_status snc_synchronize(snc_ctx* c) {
   if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
   SNC_CUDA(c, cudaSetDevice(c->device));
@@ -1077,7 +1250,7 @@ snc_status snc_synchronize(snc_ctx* c) {
     S.n_groups = S.h_pinned[1];
     S.synced = true;
   }
-  if (!c->view_ready) {
+  if (!c->view_ready || c->view_gen != S.generation) {
     if (S.n_members == 1) {
       c->n_syn = S.n_total;
       c->n_groups = S.n_groups;
@@ -1097,6 +1270,7 @@ snc_status snc_synchronize(snc_ctx* c) {
       c->group_first = c->group_first_all + g0;
     }
     c->view_ready = true;
+    c->view_gen = S.generation;
   }
   const uint32_t err = S.err_bits;
   if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");

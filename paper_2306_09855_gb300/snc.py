@@ -110,7 +110,8 @@ SNC_JOB_QUEUED, SNC_JOB_RUNNING, SNC_JOB_DONE, SNC_JOB_FAILED = range(4)
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
-           "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_last_error",
+           "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_batch_finalize_graph",
+           "snc_batch_rebuild", "snc_last_error",
            "snc_server_create", "snc_server_destroy", "snc_server_submit", "snc_server_poll",
            "snc_server_wait_any", "snc_server_context", "snc_server_times", "snc_server_release",
            "snc_server_get_stats", "snc_estimate_build")
@@ -136,6 +137,8 @@ def load(build: bool = True):
                          ctypes.POINTER(snc_syn_spec), ctypes.POINTER(U32)], I32),
         "snc_finalize": ([P], I32),
         "snc_batch_finalize": ([ctypes.POINTER(P), I32], I32),
+        "snc_batch_finalize_graph": ([ctypes.POINTER(P), I32], I32),
+        "snc_batch_rebuild": ([P, ctypes.POINTER(U64), I32], I32),
         "snc_synchronize": ([P], I32),
         "snc_get_connections": ([P, ctypes.POINTER(snc_conn_view)], I32),
         "snc_copy_connections": ([P, P, P, P, P, U64], I32),
@@ -205,6 +208,16 @@ def snc_finalize(ctx):
 def snc_batch_finalize(ctxs):
     arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
     _check(load().snc_batch_finalize(arr, len(ctxs)), ctxs[0] if ctxs else None)
+
+
+def snc_batch_finalize_graph(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    _check(load().snc_batch_finalize_graph(arr, len(ctxs)), ctxs[0] if ctxs else None)
+
+
+def snc_batch_rebuild(ctx, seeds):
+    arr = (ctypes.c_uint64 * len(seeds))(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in seeds])
+    _check(load().snc_batch_rebuild(ctx, arr, len(seeds)), ctx)
 
 
 def snc_synchronize(ctx):
@@ -504,6 +517,21 @@ class Network:
             for n in nets[1:]:
                 n._leader = nets[0]
         return nets
+
+    @staticmethod
+    def batch_graph(specs, device=0, stream=None, allocator="torch"):
+        """Batched build recorded as a CUDA graph (snc_batch_finalize_graph);
+        rebuild() then replays it with new seeds."""
+        nets = [Network(sp, device=device, stream=stream, allocator=allocator) for sp in specs]
+        if nets:
+            snc_batch_finalize_graph([n.ctx for n in nets])
+            for n in nets[1:]:
+                n._leader = nets[0]
+        return nets
+
+    def rebuild(self, seeds):
+        """Replay this context's graph build with one seed per member."""
+        snc_batch_rebuild(self.ctx, seeds)
 
     def synchronize(self):
         snc_synchronize(self.ctx)

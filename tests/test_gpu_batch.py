@@ -67,3 +67,64 @@ def test_batch_argument_errors(snc):
     with pytest.raises(snc.SncError) as e:
         snc.snc_batch_finalize([b.ctx, a.ctx])
     assert e.value.name == "STATE"
+
+
+def _fixed_count_specs():
+    from dataclasses import replace
+    specs = [
+        W.two_population(600, "fixed_indegree", k=40, autapses=False, multapses=False, seed=31),
+        W.two_population(500, "fixed_outdegree", k=25, seed=32),
+        W.two_population(400, "fixed_total_number", k=30_000, seed=33),
+        W.two_population(120, "all_to_all", autapses=False, seed=34),
+        W.two_population(300, "one_to_one", seed=35),
+        W.microcircuit(scale=0.03, seed=36),
+    ]
+    return specs, replace
+
+
+def test_graph_rebuild_equals_plain_builds_with_new_seeds(snc, oracle_mod):
+    specs, replace = _fixed_count_specs()
+    nets = snc.Network.batch_graph(specs)
+    fields = ("src", "tgt", "delay", "weight", "row_ptr", "group_ptr", "group_first")
+    first = [net.to_host() for net in nets]
+    for i, (spec, got) in enumerate(zip(specs, first)):
+        single = snc.Network(spec).finalize()
+        alone = single.to_host()
+        single.close()
+        for f in fields:
+            np.testing.assert_array_equal(got[f], alone[f], err_msg=f"first build {i} {f}")
+    for trial, offset in enumerate((1000, 2000)):
+        seeds = [sp.seed + offset + i for i, sp in enumerate(specs)]
+        nets[2].rebuild(seeds)  # any member replays the whole build
+        for i, (spec, net) in enumerate(zip(specs, nets)):
+            got = net.to_host()
+            ref_spec = replace(spec, seed=seeds[i])
+            single = snc.Network(ref_spec).finalize()
+            alone = single.to_host()
+            single.close()
+            for f in fields:
+                np.testing.assert_array_equal(got[f], alone[f], err_msg=f"trial {trial} member {i} {f}")
+            assert got["n_groups"] == alone["n_groups"]
+            if i == 0:
+                assert_network_equal(got, oracle_mod.build(ref_spec), f"trial {trial} vs oracle")
+    # back to the original seeds: the first result again
+    nets[0].rebuild([sp.seed for sp in specs])
+    for i, net in enumerate(nets):
+        got = net.to_host()
+        for f in fields:
+            np.testing.assert_array_equal(got[f], first[i][f], err_msg=f"replay {i} {f}")
+    for net in reversed(nets):
+        net.close()
+
+
+def test_graph_build_refuses_host_round_trips(snc):
+    for spec in (W.two_population(100, "pairwise_bernoulli", p=0.1, seed=1),
+                 W.two_population(100, "fixed_total_number", k=500, autapses=False, multapses=False, seed=2)):
+        with pytest.raises(snc.SncError) as e:
+            snc.Network.batch_graph([W.plain_indegree(n=50, k=5), spec])
+        assert e.value.name == "UNSUPPORTED"
+    net = snc.Network(W.plain_indegree(n=50, k=5)).finalize()
+    with pytest.raises(snc.SncError) as e:
+        net.rebuild([1])
+    assert e.value.name == "STATE"
+    net.close()
