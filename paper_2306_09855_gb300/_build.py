@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(log)
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + [o for o, _ in results] + \
-        ["-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+        ["-Xlinker", "-rpath=/usr/local/cuda/lib64", "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stderr)

@@ -84,6 +84,8 @@ __device__ __forceinline__ uint32_t hist_words(const GenArgs& a) {
   return a.hist.global ? static_cast<uint32_t>(a.hist.n_passes * a.hist.stride) : 0u;
 }
 
+// s and t are local to the connection's network (the build's node id minus
+// the network's first node).
 __device__ __forceinline__ void store(const GenArgs& a, const BlockHist& h, uint64_t pos, uint32_t s, uint32_t d,
                                       uint32_t t, uint32_t wbits) {
   if (!SNC_IN_BOUNDS(a.err, 1u, pos, a.cap)) return;
@@ -143,7 +145,8 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
         if (bp >= row_len) break;
         const uint32_t b = bp + (diag && bp >= diag_b ? 1u : 0u);
         const Words W = draw(P.k0, P.k1, kTagWD, 0, b, row);
-        store(a, bh, row_out + bp, s, delay_step(P, tabs, W.x), P.t0 + b - P.t_base, weight_bits(P, W.z, W.w));
+        store(a, bh, row_out + bp, s - P.t_base, delay_step(P, tabs, W.x), P.t0 + b - P.t_base,
+              weight_bits(P, W.z, W.w));
       }
       continue;
     }
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
           s = P.s0 + rand_below(W.y, P.ns);
           t = P.t0 + rand_below(tw, P.nt);
         }
-        store(a, bh, P.out_off + i, s, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+        store(a, bh, P.out_off + i, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
       }
     }
   }
@@ -357,7 +360,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
             const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
             const uint32_t other = first_other + r;
             const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            store(a.gen, bh, out + j, s, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+            store(a.gen, bh, out + j, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
           }
         }
         got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
@@ -392,7 +395,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
             const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
             const uint32_t other = first_other + r;
             const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            store(a.gen, bh, out + j, s, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+            store(a.gen, bh, out + j, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
           } else {
             atomicOr(a.err, kErrBounds);
           }
@@ -636,7 +639,7 @@ __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, Redr
     for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       const uint64_t pair = a.pairs[r.slot_base + i];
       const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-      store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32), delay_step(P, tabs, W.x),
+      store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32) - P.t_base, delay_step(P, tabs, W.x),
             static_cast<uint32_t>(pair) - P.t_base, weight_bits(P, W.z, W.w));
     }
   }

@@ -3,10 +3,11 @@
 //
 // A connection starts a group when its source or its delay differs from the
 // previous connection's.  group_first[g] is the position of the g-th group
-// start (a stream compaction whose tile offsets come from a decoupled
-// look-back scan), row_ptr[i] the first connection of source i and
-// group_ptr[i] = p_i = sum_{j<i} G_j the first group of source i (both found
-// by binary search, one thread per node).
+// start (a stream compaction over per-block counts), row_ptr[i] the first
+// connection of source i and group_ptr[i] = p_i = sum_{j<i} G_j the first
+// group of source i (both found by binary search, one thread per node).  A
+// batch's networks are separate segments of the arrays, each with its own
+// row_ptr and group_ptr.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -67,12 +68,33 @@ __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a
     K prev = __shfl_up_sync(0xffffffffu, key[kIndexItems - 1], 1);
     if (lane == 0) prev = (base > 0 && base < a.n) ? __ldg(keys + base - 1) : K(0);
     uint32_t bits = 0;
+    if (a.n_seg) {
+      // The network of each position: positions outside every network
+      // (alignment gaps) start nothing; a network's first position starts a
+      // group.
+      int lo = 0, hi = a.n_seg - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.seg_begin[mid] <= base) lo = mid; else hi = mid - 1;
+      }
+      int seg = lo;
 #pragma unroll
-    for (int k = 0; k < kIndexItems; ++k) {
-      const uint64_t q = base + k;
-      const K before = k == 0 ? prev : key[k - 1];
-      const bool start = q < a.n && (q == 0 || key[k] != before);
-      bits |= (start ? 1u : 0u) << k;
+      for (int k = 0; k < kIndexItems; ++k) {
+        const uint64_t q = base + k;
+        while (seg + 1 < a.n_seg && q >= a.seg_begin[seg + 1]) ++seg;
+        const K before = k == 0 ? prev : key[k - 1];
+        const bool real = q >= a.seg_begin[seg] && q < a.seg_end[seg];
+        const bool start = real && (q == a.seg_begin[seg] || key[k] != before);
+        bits |= (start ? 1u : 0u) << k;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kIndexItems; ++k) {
+        const uint64_t q = base + k;
+        const K before = k == 0 ? prev : key[k - 1];
+        const bool start = q < a.n && (q == 0 || key[k] != before);
+        bits |= (start ? 1u : 0u) << k;
+      }
     }
     if (a.unpacked) {
       // target, weight and delay were written by the sort's last pass
@@ -162,27 +184,41 @@ __global__ void __launch_bounds__(kIndexThreads) index_groups_kernel(IndexArgs a
   if (blockIdx.x == 0 && tid == 0) *a.n_groups = a.block_offsets[n_blocks];
 }
 
-// row_ptr[i] = first position whose source is >= i; group_ptr[i] = number of
-// group starts before row_ptr[i].  i = 0 .. n_nodes.
+// One thread per (network m, local node i = 0 .. n_nodes_m): the network's
+// CSR offset of i (first position of its segment whose source is >= i) and
+// the groups before it.
 template <typename K>
-__global__ void node_index_kernel(NodeIndexArgs a) {
-  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i > a.n_nodes) return;
-  const K* keys = static_cast<const K*>(a.keys);
-  uint64_t lo = 0, hi = a.n;
+__global__ void member_index_kernel(MemberIndexArgs a) {
+  const uint64_t e = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= a.n_entries) return;
+  int lo = 0, hi = a.n_members - 1;
   while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if ((static_cast<uint64_t>(keys[mid]) >> a.delay_bits) < i) lo = mid + 1; else hi = mid;
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.local_base[mid] <= e) lo = mid; else hi = mid - 1;
   }
-  if (!SNC_IN_BOUNDS(nullptr, 21u, lo, a.n + 1)) return;
-  a.row_ptr[i] = lo;
-  const uint64_t ng = *a.n_groups;
-  uint64_t glo = 0, ghi = ng < a.group_cap ? ng : a.group_cap;
-  while (glo < ghi) {
-    const uint64_t mid = (glo + ghi) >> 1;
-    if (a.group_first[mid] < lo) glo = mid + 1; else ghi = mid;
+  const int m = lo;
+  const uint64_t i = e - a.local_base[m];
+  const K* keys = static_cast<const K*>(a.keys);
+  const uint64_t sb = a.seg_begin[m];
+  uint64_t l = sb, h = a.seg_end[m];
+  while (l < h) {
+    const uint64_t mid = (l + h) >> 1;
+    if ((static_cast<uint64_t>(keys[mid]) >> a.delay_bits) < i) l = mid + 1; else h = mid;
   }
-  a.group_ptr[i] = glo;
+  a.row_local[e] = l - sb;
+  const uint64_t ng = *a.n_groups < a.group_cap ? *a.n_groups : a.group_cap;
+  const auto first_group_at = [&](uint64_t pos) {
+    uint64_t gl = 0, gh = ng;
+    while (gl < gh) {
+      const uint64_t mid = (gl + gh) >> 1;
+      if (a.group_first[mid] < pos) gl = mid + 1; else gh = mid;
+    }
+    return gl;
+  };
+  const uint64_t g0 = first_group_at(sb);
+  a.group_local[e] = first_group_at(l) - g0;
+  if (i == 0) a.gfirst[m] = g0;
+  if (e == 0) a.gfirst[a.n_members] = ng;
 }
 
 cudaError_t launch_index_unpack(const IndexArgs& a, unsigned grid, cudaStream_t st) {
@@ -193,13 +229,27 @@ cudaError_t launch_index_unpack(const IndexArgs& a, unsigned grid, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_node_index(const NodeIndexArgs& a, cudaStream_t st) {
-  const unsigned grid = static_cast<unsigned>((a.n_nodes + 1 + 255) / 256);
+cudaError_t launch_member_index(const MemberIndexArgs& a, cudaStream_t st) {
+  const unsigned grid = static_cast<unsigned>((a.n_entries + 255) / 256);
   if (a.key32)
-    node_index_kernel<uint32_t><<<grid, 256, 0, st>>>(a);
+    member_index_kernel<uint32_t><<<grid, 256, 0, st>>>(a);
   else
-    node_index_kernel<uint64_t><<<grid, 256, 0, st>>>(a);
+    member_index_kernel<uint64_t><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+__global__ void rebase_group_first_kernel(uint64_t* group_first, const uint64_t* n_groups, uint64_t group_cap,
+                                          const uint64_t* gfirst, const uint64_t* seg_begin, int n_members) {
+  const uint64_t ng = *n_groups < group_cap ? *n_groups : group_cap;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < ng; g += stride) {
+    int lo = 0, hi = n_members - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (gfirst[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    group_first[g] -= seg_begin[lo];
+  }
 }
 
 // Source of every connection from row_ptr (for host copies).
@@ -207,40 +257,6 @@ __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes,
   const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   for (uint64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) src[q] = static_cast<uint32_t>(i);
-}
-
-// One thread per (network, local node or end entry): total_nodes + n_nets.
-__global__ void rebase_nodes_kernel(RebaseArgs a) {
-  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= a.total_nodes + static_cast<uint64_t>(a.n_nets)) return;
-  // Entry i of the concatenated local arrays: network b holds entries
-  // [node_base[b] + b, node_base[b + 1] + b + 1).
-  int lo = 0, hi = a.n_nets - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.node_base[mid] + static_cast<uint64_t>(mid) <= i) lo = mid; else hi = mid - 1;
-  }
-  const int b = lo;
-  const uint64_t local = i - a.node_base[b] - static_cast<uint64_t>(b);
-  const uint64_t g = a.node_base[b] + local;
-  const uint64_t first = a.node_base[b];
-  a.row_local[a.local_base[b] + local] = a.row_ptr[g] - a.row_ptr[first];
-  a.group_local[a.local_base[b] + local] = a.group_ptr[g] - a.group_ptr[first];
-}
-
-// group_first[g] -= first connection of the group's network.
-__global__ void rebase_groups_kernel(RebaseArgs a) {
-  const uint64_t ng = *a.n_groups < a.n_groups_cap ? *a.n_groups : a.n_groups_cap;
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < ng; g += stride) {
-    // The network whose group range [group_ptr[base], group_ptr[base_next]) holds g.
-    int lo = 0, hi = a.n_nets - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (a.group_ptr[a.node_base[mid]] <= g) lo = mid; else hi = mid - 1;
-    }
-    a.group_first[g] -= a.row_ptr[a.node_base[lo]];
-  }
 }
 
 }  // namespace snc

@@ -28,43 +28,42 @@ struct IndexArgs {
   uint64_t group_cap;
   uint64_t* n_groups;
   uint32_t* err;
+  // Networks of the build: positions [seg_begin[m], seg_end[m]) hold network
+  // m's connections; positions between them belong to none.
+  int n_seg;
+  const uint64_t* seg_begin;
+  const uint64_t* seg_end;
 };
 
-struct NodeIndexArgs {
+// Per-network CSR and group offsets.  Network m owns entries
+// [local_base[m], local_base[m] + n_nodes_m + 1) of row_local / group_local:
+// row_local = first position (relative to seg_begin[m]) whose source is >= i,
+// group_local = groups of the network before it.  gfirst[m] = first group of
+// network m, gfirst[n_members] = all groups.
+struct MemberIndexArgs {
   const void* keys;
   int key32;
-  uint64_t n;
-  uint64_t n_nodes;
   int delay_bits;
+  int n_members;
+  const uint64_t* seg_begin;
+  const uint64_t* seg_end;
+  const uint64_t* local_base;
+  uint64_t n_entries;  // nodes of all networks + n_members
   const uint64_t* group_first;
   uint64_t group_cap;
   const uint64_t* n_groups;
-  uint64_t* row_ptr;
-  uint64_t* group_ptr;
+  uint64_t* row_local;
+  uint64_t* group_local;
+  uint64_t* gfirst;
 };
 
 // Launch the unpack / node-index kernel for the key width of the build.
 cudaError_t launch_index_unpack(const IndexArgs& a, unsigned grid, cudaStream_t st);
 __global__ void index_groups_kernel(IndexArgs a);
-cudaError_t launch_node_index(const NodeIndexArgs& a, cudaStream_t st);
+cudaError_t launch_member_index(const MemberIndexArgs& a, cudaStream_t st);
+// group_first[g] -= seg_begin of the network that owns group g.
+__global__ void rebase_group_first_kernel(uint64_t* group_first, const uint64_t* n_groups, uint64_t group_cap,
+                                          const uint64_t* gfirst, const uint64_t* seg_begin, int n_members);
 __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes, uint32_t* src);
-
-// Batches: per-network CSR offsets relative to the network's first
-// connection / group, and group starts relative to its first connection.
-struct RebaseArgs {
-  const uint64_t* row_ptr;     // global node CSR of the build [total_nodes + 1]
-  const uint64_t* group_ptr;   // [total_nodes + 1]
-  const uint64_t* node_base;   // first global node of each network [n_nets + 1]
-  const uint64_t* local_base;  // first entry of each network's local arrays [n_nets]
-  int n_nets;
-  uint64_t total_nodes;
-  uint64_t* row_local;         // concatenated per-network arrays of (n + 1) entries
-  uint64_t* group_local;
-  uint64_t* group_first;       // rebased in place
-  uint64_t n_groups_cap;
-  const uint64_t* n_groups;
-};
-__global__ void rebase_nodes_kernel(RebaseArgs a);
-__global__ void rebase_groups_kernel(RebaseArgs a);
 
 }  // namespace snc

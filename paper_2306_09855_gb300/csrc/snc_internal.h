@@ -49,13 +49,14 @@ struct DevProj {
 
 // Sort key and value of a connection.  The key packs source | delay step
 // (Sec. 2.2 sorts by these two keys); it is 32 bits wide when the two fit,
-// else 64.  The source is a global node id of the build.  The value packs
-// the target (local to its network, equal to the global id when a single
-// network is built) above the fp32 weight's bits.
+// else 64.  The value packs the target above the fp32 weight's bits.  Source
+// and target are local to the connection's network (equal to the node ids
+// when a single network is built); a batch sorts each network's connections
+// as a segment of its own.
 struct KeyLayout {
   int src_bits;
   int delay_bits;
-  int tgt_bits;  // bits of the largest member-local target (value field: 32)
+  int tgt_bits;  // bits of the largest network-local target (value field: 32)
   int total_bits() const { return src_bits + delay_bits; }
   bool key32() const { return total_bits() <= 32; }
 };

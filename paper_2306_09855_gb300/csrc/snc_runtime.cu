@@ -204,6 +204,8 @@ struct snc_ctx {
   // again after every graph replay of the build).
   bool view_ready = false;
   uint64_t view_gen = 0;
+  uint64_t seg_begin = 0;  // first position of this network's connections in the build's arrays
+  uint64_t seg_count = 0;
   uint64_t n_syn = 0;
   uint64_t n_groups = 0;
   uint64_t group_cap = 0;
@@ -568,7 +570,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // Key layout: global source | delay step | member-local target.
   uint32_t max_step = 1;
   for (const UnionProj& u : ups) max_step = std::max(max_step, u.p->max_step);
-  c->layout.src_bits = std::max(1, bit_width(total_nodes > 0 ? total_nodes - 1 : 0));
+  c->layout.src_bits = std::max(1, bit_width(max_nodes > 0 ? max_nodes - 1 : 0));  // network-local sources
   c->layout.tgt_bits = std::max(1, bit_width(max_nodes > 0 ? max_nodes - 1 : 0));
   c->layout.delay_bits = std::max(1, bit_width(max_step));
   if (c->layout.total_bits() > 64)
@@ -687,14 +689,31 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   }
   mark();
 
-  // Output offsets and generation chunks.
+  // Output offsets and generation chunks.  A batch's networks are segments
+  // of the arrays, each starting on a multiple of 4 positions (the sort's
+  // bulk copies need 16-byte aligned tiles); the few positions between
+  // segments belong to no network.
   uint64_t off = 0;
   std::vector<DevProj> direct;
   std::vector<size_t> direct_src;  // union index of each direct projection
   uint64_t chunk = 0;
+  std::vector<uint64_t> seg_begin(n_members, 0), seg_end(n_members, 0);
+  int cur_m = -1;
+  const auto open_member = [&](int m) {
+    if (cur_m >= 0) seg_end[cur_m] = off;
+    while (cur_m < m) {
+      ++cur_m;
+      if (n_members > 1) off = (off + 3) & ~3ull;
+      seg_begin[cur_m] = off;
+      seg_end[cur_m] = off;
+    }
+  };
+  uint64_t n_conn = 0;
   for (size_t i = 0; i < np; ++i) {
     const Projection& p = *ups[i].p;
     DevProj& d = dp[i];
+    if (ups[i].member != cur_m) open_member(ups[i].member);
+    n_conn += cnt[i];
     d.count = cnt[i];
     d.out_off = off;
     off += cnt[i];
@@ -711,7 +730,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     direct.push_back(d);
     direct_src.push_back(i);
   }
-  const uint64_t n_total = off;
+  open_member(n_members - 1);
+  seg_end[n_members - 1] = off;
+  const uint64_t n_total = off;  // positions, with the gaps between networks
   // The projection records carry the Philox keys: their staged copies are
   // where a graph replay puts new seeds.
   if (np > 0) {
@@ -732,22 +753,51 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
 
   // Buffers: generated keys/values, the sort's second buffer, outputs.
   const uint64_t n = n_total;
-  c->passes = plan_passes(c->layout.total_bits());
+  const bool segmented = n_members > 1;
+  if (segmented) {
+    for (int m = 0; m < n_members; ++m)
+      if (seg_end[m] - seg_begin[m] >= (1ull << 30))
+        return fail(c, SNC_ERR_UNSUPPORTED, "batch: network %d has 2^30 connections or more; build it alone", m);
+    // One launch per pass sorts every network as a segment: bulk-copy pass
+    // kernel (8-9 bit digits), digit counts per segment from the keys.
+    SortTuning tune = g_sort_tuning;
+    tune.max_digit_bits = std::min(tune.max_digit_bits, 9);
+    tune.group_tiles = 0;
+    c->passes = plan_passes(c->layout.total_bits(), tune);
+  } else {
+    c->passes = plan_passes(c->layout.total_bits());
+  }
+  // Segment tables (device): begin, end, first tile of each network.
+  const uint64_t seg_tile = static_cast<uint64_t>(onesweep_group(c->passes));
+  std::vector<uint32_t> tile_begin(n_members + 1, 0);
+  for (int m = 0; m < n_members; ++m)
+    tile_begin[m + 1] = tile_begin[m] + static_cast<uint32_t>((seg_end[m] - seg_begin[m] + seg_tile - 1) / seg_tile);
+  uint64_t* d_seg = static_cast<uint64_t*>(dev_alloc(c, 2 * static_cast<size_t>(n_members) * sizeof(uint64_t)));
+  uint32_t* d_tile_begin = static_cast<uint32_t*>(dev_alloc(c, (static_cast<size_t>(n_members) + 1) * sizeof(uint32_t)));
+  if (!d_seg || !d_tile_begin) return fail(c, SNC_ERR_OOM, "device allocation failed (segments)");
+  SNC_CUDA(c, upload(c, d_seg, seg_begin.data(), n_members * sizeof(uint64_t)));
+  SNC_CUDA(c, upload(c, d_seg + n_members, seg_end.data(), n_members * sizeof(uint64_t)));
+  SNC_CUDA(c, upload(c, d_tile_begin, tile_begin.data(), (n_members + 1) * sizeof(uint32_t)));
   const bool key32 = c->layout.key32();
   const size_t key_bytes = key32 ? sizeof(uint32_t) : sizeof(uint64_t);
   void* keys_a = dev_alloc(c, n * key_bytes);
   uint64_t* vals_a = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
   void* keys_b = dev_alloc(c, n * key_bytes);
   uint64_t* vals_b = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
-  void* sort_scratch = dev_alloc(c, sort_scratch_bytes(n, c->passes));
+  const uint64_t n_seg_tiles = tile_begin[n_members];
+  void* sort_scratch = dev_alloc(c, segmented ? sort_scratch_bytes(n, c->passes, n_seg_tiles, n_members)
+                                              : sort_scratch_bytes(n, c->passes));
   if (!keys_a || !vals_a || !keys_b || !vals_b || !sort_scratch)
     return fail(c, SNC_ERR_OOM, "device allocation failed (%llu connections)", static_cast<unsigned long long>(n));
 
-  // The generation kernels count the sort's digits as they write the keys.
-  const SortScratch sort_lay = sort_scratch_layout(sort_scratch, n, c->passes);
-  SNC_CUDA(c, cudaMemsetAsync(sort_lay.hist, 0, static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long),
-                              st));
-  const HistPlan hplan = hist_plan(c->passes, sort_lay.hist);
+  // The generation kernels count the sort's digits as they write the keys
+  // (a segmented sort counts per segment itself).
+  const SortScratch sort_lay = segmented ? sort_scratch_layout(sort_scratch, n, c->passes, n_seg_tiles, n_members)
+                                         : sort_scratch_layout(sort_scratch, n, c->passes);
+  if (!segmented)
+    SNC_CUDA(c, cudaMemsetAsync(sort_lay.hist, 0,
+                                static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long), st));
+  const HistPlan hplan = hist_plan(c->passes, segmented ? nullptr : sort_lay.hist);
   const size_t hist_bytes = hist_smem_bytes(hplan);
 
   // Generation.
@@ -957,14 +1007,22 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   unpack.delay = u_delay;
   unpack.delay_mask = (1u << c->layout.delay_bits) - 1u;
   bool fused = false;
+  SortSegments segs{};
+  segs.n_seg = n_members;
+  segs.begin = d_seg;
+  segs.end = d_seg + n_members;
+  segs.tile_begin = d_tile_begin;
+  segs.n_tiles = n_seg_tiles;
+  for (int m = 0; m < n_members; ++m) segs.max_len = std::max(segs.max_len, seg_end[m] - seg_begin[m]);
+  const SortSegments* seg_arg = segmented ? &segs : nullptr;
   if (key32)
     SNC_CUDA(c, radix_sort_run(static_cast<const uint32_t*>(keys_a), vals_a, static_cast<uint32_t*>(keys_res), vals_res,
                                static_cast<uint32_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused));
+                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused, seg_arg));
   else
     SNC_CUDA(c, radix_sort_run(static_cast<const uint64_t*>(keys_a), vals_a, static_cast<uint64_t*>(keys_res), vals_res,
                                static_cast<uint64_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused));
+                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused, seg_arg));
   if (!S.capturing) S.n_ev += c->passes.n_passes + 1;
   if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
   c->stats.n_passes = c->passes.n_passes;
@@ -979,15 +1037,22 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   uint32_t* u_target = fused ? unpack.target : static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
   float* u_weight = fused ? reinterpret_cast<float*>(unpack.weight) : static_cast<float*>(dev_alloc(c, n * sizeof(float)));
   uint64_t* u_group_first = static_cast<uint64_t*>(dev_alloc(c, group_cap * sizeof(uint64_t)));
-  uint64_t* u_row_ptr = static_cast<uint64_t*>(dev_alloc(c, (total_nodes + 1) * sizeof(uint64_t)));
-  uint64_t* u_group_ptr = static_cast<uint64_t*>(dev_alloc(c, (total_nodes + 1) * sizeof(uint64_t)));
+  // Per-network CSR and group offsets: network m's n_nodes_m + 1 entries
+  // start at local_base[m].
+  std::vector<uint64_t> local_base(n_members, 0);
+  for (int m = 1; m < n_members; ++m) local_base[m] = local_base[m - 1] + members[m - 1]->n_nodes + 1;
+  const uint64_t n_local = total_nodes + static_cast<uint64_t>(n_members);
+  uint64_t* u_row_ptr = static_cast<uint64_t*>(dev_alloc(c, n_local * sizeof(uint64_t)));
+  uint64_t* u_group_ptr = static_cast<uint64_t*>(dev_alloc(c, n_local * sizeof(uint64_t)));
+  uint64_t* d_local_base = static_cast<uint64_t*>(dev_alloc(c, n_members * sizeof(uint64_t)));
+  S.d_bases = static_cast<uint64_t*>(dev_alloc(c, (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)));
   const uint64_t iblocks = (n + kIndexTile - 1) / kIndexTile;
   uint32_t* starts = static_cast<uint32_t*>(dev_alloc(c, (iblocks * (kIndexTile / 32) + 1) * sizeof(uint32_t)));
   uint32_t* bcounts = static_cast<uint32_t*>(dev_alloc(c, (iblocks + 1) * sizeof(uint32_t)));
   uint64_t* boffsets = static_cast<uint64_t*>(dev_alloc(c, (iblocks + 1) * sizeof(uint64_t)));
   uint64_t* iscan = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(iblocks) + 1) * sizeof(uint64_t)));
-  if (!u_target || !u_delay || !u_weight || !u_group_first || !u_row_ptr || !u_group_ptr || !starts || !bcounts ||
-      !boffsets || !iscan)
+  if (!u_target || !u_delay || !u_weight || !u_group_first || !u_row_ptr || !u_group_ptr || !d_local_base ||
+      !S.d_bases || !starts || !bcounts || !boffsets || !iscan)
     return fail(c, SNC_ERR_OOM, "device allocation failed (index)");
   if (n > 0) {
     IndexArgs ia{};
@@ -1007,6 +1072,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     ia.group_cap = group_cap;
     ia.n_groups = S.d_n_groups;
     ia.err = S.d_err;
+    ia.n_seg = segmented ? n_members : 0;
+    ia.seg_begin = d_seg;
+    ia.seg_end = d_seg + n_members;
     const unsigned igrid = static_cast<unsigned>(std::min<uint64_t>(iblocks, static_cast<uint64_t>(c->sms) * 8));
     SNC_CUDA(c, launch_index_unpack(ia, igrid, st));
     ++c->stats.kernel_launches;
@@ -1016,73 +1084,42 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
   }
-  NodeIndexArgs na{};
-  na.keys = keys_res;
-  na.key32 = key32 ? 1 : 0;
-  na.n = n;
-  na.n_nodes = total_nodes;
-  na.delay_bits = c->layout.delay_bits;
-  na.group_first = u_group_first;
-  na.group_cap = group_cap;
-  na.n_groups = S.d_n_groups;
-  na.row_ptr = u_row_ptr;
-  na.group_ptr = u_group_ptr;
-  SNC_CUDA(c, launch_node_index(na, st));
+  SNC_CUDA(c, upload(c, d_local_base, local_base.data(), n_members * sizeof(uint64_t)));
+  if (n == 0) SNC_CUDA(c, cudaMemsetAsync(S.d_n_groups, 0, sizeof(uint64_t), st));
+  MemberIndexArgs mi{};
+  mi.keys = keys_res;
+  mi.key32 = key32 ? 1 : 0;
+  mi.delay_bits = c->layout.delay_bits;
+  mi.n_members = n_members;
+  mi.seg_begin = d_seg;
+  mi.seg_end = d_seg + n_members;
+  mi.local_base = d_local_base;
+  mi.n_entries = n_local;
+  mi.group_first = u_group_first;
+  mi.group_cap = group_cap;
+  mi.n_groups = S.d_n_groups;
+  mi.row_local = u_row_ptr;
+  mi.group_local = u_group_ptr;
+  mi.gfirst = S.d_bases;
+  SNC_CUDA(c, launch_member_index(mi, st));
   ++c->stats.kernel_launches;
-  // Batches: each member's CSR and group offsets relative to its own first
-  // connection and group; its first connection and group are read back at
-  // synchronize.
-  uint64_t* local_rows = nullptr;
-  uint64_t* local_groups = nullptr;
-  std::vector<uint64_t> local_base(n_members, 0);
-  if (n_members > 1) {
-    for (int m = 1; m < n_members; ++m) local_base[m] = local_base[m - 1] + members[m - 1]->n_nodes + 1;
-    const uint64_t n_local = total_nodes + static_cast<uint64_t>(n_members);
-    local_rows = static_cast<uint64_t*>(dev_alloc(c, n_local * sizeof(uint64_t)));
-    local_groups = static_cast<uint64_t*>(dev_alloc(c, n_local * sizeof(uint64_t)));
-    uint64_t* d_meta = static_cast<uint64_t*>(dev_alloc(c, (2 * static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)));
-    S.d_bases = static_cast<uint64_t*>(dev_alloc(c, 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)));
-    if (!local_rows || !local_groups || !d_meta || !S.d_bases)
-      return fail(c, SNC_ERR_OOM, "device allocation failed (batch views)");
-    std::vector<uint64_t> meta(node_base.begin(), node_base.end());
-    meta.insert(meta.end(), local_base.begin(), local_base.end());
-    SNC_CUDA(c, upload(c, d_meta, meta.data(), meta.size() * sizeof(uint64_t)));
-    RebaseArgs rb{};
-    rb.row_ptr = u_row_ptr;
-    rb.group_ptr = u_group_ptr;
-    rb.node_base = d_meta;
-    rb.local_base = d_meta + n_members + 1;
-    rb.n_nets = n_members;
-    rb.total_nodes = total_nodes;
-    rb.row_local = local_rows;
-    rb.group_local = local_groups;
-    rb.group_first = u_group_first;
-    rb.n_groups_cap = group_cap;
-    rb.n_groups = S.d_n_groups;
-    // First connection / group of every member (and the totals) for the views.
-    for (int m = 0; m <= n_members; ++m) {
-      SNC_CUDA(c, cudaMemcpyAsync(S.d_bases + m, u_row_ptr + node_base[m], sizeof(uint64_t), cudaMemcpyDeviceToDevice,
-                                  st));
-      SNC_CUDA(c, cudaMemcpyAsync(S.d_bases + n_members + 1 + m, u_group_ptr + node_base[m], sizeof(uint64_t),
-                                  cudaMemcpyDeviceToDevice, st));
-    }
-    rebase_nodes_kernel<<<static_cast<unsigned>((n_local + 255) / 256), 256, 0, st>>>(rb);
-    ++c->stats.kernel_launches;
-    rebase_groups_kernel<<<static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>((group_cap + 255) / 256,
-                                                                                           static_cast<uint64_t>(c->sms) * 8))),
-                           256, 0, st>>>(rb);
+  if (segmented) {
+    // group_first relative to each network's first connection.
+    rebase_group_first_kernel<<<static_cast<unsigned>(std::max<uint64_t>(
+                                    1, std::min<uint64_t>((group_cap + 255) / 256, static_cast<uint64_t>(c->sms) * 8))),
+                                256, 0, st>>>(u_group_first, S.d_n_groups, group_cap, S.d_bases, d_seg, n_members);
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
-    if (!S.h_bases && cudaMallocHost(&S.h_bases, 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)) != cudaSuccess) {
-      cudaGetLastError();
-      S.h_bases = nullptr;
-      return fail(c, SNC_ERR_OOM, "pinned allocation failed (batch views)");
-    }
-    SNC_CUDA(c, cudaMemcpyAsync(S.h_bases, S.d_bases, 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t),
-                                cudaMemcpyDeviceToHost, st));
-    c->stats.d2h_bytes += 2 * (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t);
-    dev_free(c, d_meta);
   }
+  // First group of every network (and the total) for the views.
+  if (!S.h_bases && cudaMallocHost(&S.h_bases, (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    S.h_bases = nullptr;
+    return fail(c, SNC_ERR_OOM, "pinned allocation failed (views)");
+  }
+  SNC_CUDA(c, cudaMemcpyAsync(S.h_bases, S.d_bases, (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t),
+                              cudaMemcpyDeviceToHost, st));
+  c->stats.d2h_bytes += (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t);
   mark();
   dev_free(c, starts);
   dev_free(c, bcounts);
@@ -1092,9 +1129,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   if (!fused) dev_free(c, vals_res);  // else it holds the targets and weights
   dev_free(c, d_direct);
   dev_free(c, d_prim_off);
+  dev_free(c, d_seg);
+  dev_free(c, d_tile_begin);
+  dev_free(c, d_local_base);
 
   S.n_members = n_members;
-  S.n_total = n_total;
+  S.n_total = n_conn;
   S.synced = false;
   for (int m = 0; m < n_members; ++m) {
     snc_ctx* x = members[m];
@@ -1108,8 +1148,10 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     x->delay_all = u_delay;
     x->weight_all = u_weight;
     x->group_first_all = u_group_first;
-    x->row_ptr = n_members > 1 ? local_rows + local_base[m] : u_row_ptr;
-    x->group_ptr = n_members > 1 ? local_groups + local_base[m] : u_group_ptr;
+    x->row_ptr = u_row_ptr + local_base[m];
+    x->group_ptr = u_group_ptr + local_base[m];
+    x->seg_begin = seg_begin[m];
+    x->seg_count = seg_end[m] - seg_begin[m];
     x->view_ready = false;
     x->finalized = true;
     if (m > 0) x->stats = c->stats;
@@ -1251,24 +1293,13 @@ snc_status snc_synchronize(snc_ctx* c) {
     S.synced = true;
   }
   if (!c->view_ready || c->view_gen != S.generation) {
-    if (S.n_members == 1) {
-      c->n_syn = S.n_total;
-      c->n_groups = S.n_groups;
-      c->target = c->target_all;
-      c->delay = c->delay_all;
-      c->weight = c->weight_all;
-      c->group_first = c->group_first_all;
-    } else {
-      const int M = S.n_members, m = c->member;
-      const uint64_t syn0 = S.h_bases[m], syn1 = S.h_bases[m + 1];
-      const uint64_t g0 = S.h_bases[M + 1 + m], g1 = S.h_bases[M + 1 + m + 1];
-      c->n_syn = syn1 - syn0;
-      c->n_groups = g1 - g0;
-      c->target = c->target_all + syn0;
-      c->delay = c->delay_all + syn0;
-      c->weight = c->weight_all + syn0;
-      c->group_first = c->group_first_all + g0;
-    }
+    const uint64_t g0 = S.h_bases[c->member], g1 = S.h_bases[c->member + 1];
+    c->n_syn = c->seg_count;
+    c->n_groups = g1 - g0;
+    c->target = c->target_all + c->seg_begin;
+    c->delay = c->delay_all + c->seg_begin;
+    c->weight = c->weight_all + c->seg_begin;
+    c->group_first = c->group_first_all + g0;
     c->view_ready = true;
     c->view_gen = S.generation;
   }

@@ -493,8 +493,11 @@ __device__ __forceinline__ uint32_t ld_status32(const uint32_t* p) {
   return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
+// The first tile of the sort (or of its segment) has no predecessor; the
+// others look back until an inclusive value, which the first tile of their
+// segment always publishes, so a look-back never leaves its segment.
 template <int RADIX, int DPT, int W, typename A>
-__device__ __forceinline__ void look_back32(const A& a, uint32_t unit, uint64_t (&prefix)[DPT]) {
+__device__ __forceinline__ void look_back32(const A& a, uint32_t unit, bool first, uint64_t (&prefix)[DPT]) {
   const uint32_t tid = threadIdx.x;
   const uint32_t* base = a.status32 + tid * DPT;
   int32_t look[DPT];
@@ -503,7 +506,7 @@ __device__ __forceinline__ void look_back32(const A& a, uint32_t unit, uint64_t 
   for (int q = 0; q < DPT; ++q) {
     prefix[q] = 0;
     look[q] = static_cast<int32_t>(unit) - 1;
-    if (unit > 0) pending |= 1u << q;
+    if (!first) pending |= 1u << q;
   }
   uint32_t spins = 0, backoff = 32u;
   while (pending) {
@@ -615,18 +618,43 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
   const uint32_t mask = a.mask;
   const int shift = a.shift;
   const uint32_t lt = lanemask_lt();
-  const uint64_t n_tiles = (a.n + TILE - 1) / TILE;
+  // Tiles: consecutive TILE-key ranges of [0, n), or with segments the
+  // tiles of each segment in turn (a segment's last tile may be partial).
+  const uint64_t n_tiles = a.n_seg ? a.seg_tile_begin[a.n_seg] : (a.n + TILE - 1) / TILE;
+  __shared__ uint64_t tile_base_sh;
+  __shared__ uint32_t tile_valid_sh, tile_seg_sh, tile_first_sh;
   const auto buf_keys = [&](int b) { return reinterpret_cast<K*>(smem + b * C::kBufBytes); };
   const auto buf_vals = [&](int b) { return reinterpret_cast<V*>(smem + b * C::kBufBytes + C::kKeysBytes); };
-  const auto full_tile = [&](uint32_t t) {
-    return t < n_tiles && static_cast<uint64_t>(t) * TILE + TILE <= a.n;
-  };
-  // Thread 0: take a ticket and start its bulk copy into buffer b.
+  // Thread 0: take a ticket, locate its tile and start its bulk copy into
+  // buffer b when the tile is full.
   const auto take = [&](int b) {
     const uint32_t t = atomicAdd(a.tile_counter, 1u);
     ticket_sh = t;
-    if (full_tile(t)) {
-      const uint64_t tb = static_cast<uint64_t>(t) * TILE;
+    if (t >= n_tiles) return;
+    uint64_t tb, end;
+    uint32_t seg = 0, first;
+    if (a.n_seg) {
+      int lo = 0, hi = a.n_seg - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.seg_tile_begin[mid] <= t) lo = mid; else hi = mid - 1;
+      }
+      seg = static_cast<uint32_t>(lo);
+      first = a.seg_tile_begin[seg];
+      tb = a.seg_begin[seg] + static_cast<uint64_t>(t - first) * TILE;
+      end = a.seg_end[seg];
+      first = t == first;
+    } else {
+      tb = static_cast<uint64_t>(t) * TILE;
+      end = a.n;
+      first = t == 0;
+    }
+    const uint32_t valid = end - tb < static_cast<uint64_t>(TILE) ? static_cast<uint32_t>(end - tb) : TILE;
+    tile_base_sh = tb;
+    tile_valid_sh = valid;
+    tile_seg_sh = seg;
+    tile_first_sh = first;
+    if (valid == TILE) {
       fence_proxy_async_smem();  // earlier generic accesses to the buffer come first
       mbar_arrive_expect_tx(bars + b, static_cast<uint32_t>(C::kKeysBytes + C::kValsBytes));
       bulk_load(buf_keys(b), a.keys_in + tb, static_cast<uint32_t>(C::kKeysBytes), bars + b);
@@ -650,8 +678,10 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
     for (int i = tid; i < NW * RADIX / 2; i += TPB) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
     __syncthreads();
     const uint32_t unit = cur;
-    const uint64_t tbase = static_cast<uint64_t>(unit) * TILE;
-    const uint32_t valid = a.n - tbase < static_cast<uint64_t>(TILE) ? static_cast<uint32_t>(a.n - tbase) : TILE;
+    const uint64_t tbase = tile_base_sh;
+    const uint32_t valid = tile_valid_sh;
+    const bool first_tile = tile_first_sh != 0;  // first tile of [0, n) or of its segment
+    const uint64_t* digit_start = a.digit_start + static_cast<size_t>(tile_seg_sh) * a.seg_digit_stride;
     if (valid == TILE) {
       if (!tile_wait(bars, parity)) {
         // Give the copies in flight a second bounded chance to land, then leave.
@@ -710,7 +740,7 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
     }
     uint32_t* st_row = a.status32 + static_cast<size_t>(unit) * RADIX + static_cast<size_t>(tid) * DPT;
 #pragma unroll
-    for (int q = 0; q < DPT; ++q) st_status32(st_row + q, (unit == 0 ? kInc32 : kAgg32) | tot[q]);
+    for (int q = 0; q < DPT; ++q) st_status32(st_row + q, (first_tile ? kInc32 : kAgg32) | tot[q]);
     uint32_t excl = block_excl_scan<TPB>(tsum, warp_tmp, &scan_total);
     uint32_t my_start[DPT];
 #pragma unroll
@@ -748,12 +778,12 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       if (li < valid && SNC_IN_BOUNDS(a.err, 10u, rank[j], TILE)) vin[rank[j]] = val[j];
     }
     uint64_t prefix[DPT];
-    look_back32<RADIX, DPT, W>(a, unit, prefix);
+    look_back32<RADIX, DPT, W>(a, unit, first_tile, prefix);
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
       const int d = tid * DPT + q;
-      if (unit > 0) st_status32(st_row + q, kInc32 | static_cast<uint32_t>((prefix[q] + tot[q]) & kCount32));
-      globm[d] = a.digit_start[d] + prefix[q] - my_start[q];
+      if (!first_tile) st_status32(st_row + q, kInc32 | static_cast<uint32_t>((prefix[q] + tot[q]) & kCount32));
+      globm[d] = digit_start[d] + prefix[q] - my_start[q];
     }
     __syncthreads();
     for (uint32_t i = tid; i < valid; i += TPB) {
@@ -885,13 +915,23 @@ SortPasses plan_passes(int key_bits, const SortTuning& tune) {
   return sp;
 }
 
-size_t sort_scratch_bytes(uint64_t n, const SortPasses& sp) {
-  const uint64_t groups = (n + onesweep_group(sp) - 1) / onesweep_group(sp);
+namespace {
+// Digit counters / offsets: [pass][kMaxRadix] for one range, or
+// [segment][pass][radix] for a segmented sort.
+size_t digit_entries(const SortPasses& sp, int n_seg) {
+  const size_t one = static_cast<size_t>(kMaxPasses) * kMaxRadix;
+  const size_t seg = static_cast<size_t>(n_seg) * sp.n_passes * (1u << sp.kernel_bits);
+  return seg > one ? seg : one;
+}
+}  // namespace
+
+size_t sort_scratch_bytes(uint64_t n, const SortPasses& sp, uint64_t n_tiles, int n_seg) {
+  uint64_t groups = (n + onesweep_group(sp) - 1) / onesweep_group(sp);
+  if (n_tiles > groups) groups = n_tiles;
   const size_t status = static_cast<size_t>(groups ? groups : 1) * (1u << sp.kernel_bits) * sizeof(uint64_t);
-  const size_t hist = static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long);
-  const size_t start = static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(uint64_t);
+  const size_t digits = digit_entries(sp, n_seg) * sizeof(uint64_t);
   const size_t counters = 64 * sizeof(uint32_t);
-  return status + hist + start + counters + 4 * 256;
+  return status + 2 * digits + counters + 4 * 256;
 }
 
 namespace {
@@ -908,27 +948,127 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 // scratch: sort_scratch_bytes(n, sp) bytes of device memory.
 // pass_events (optional, n_passes + 1 events): recorded after the histogram
 // and after each pass.
-SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp) {
+SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp, uint64_t n_tiles, int n_seg) {
   SortScratch l{};
   const int group = onesweep_group(sp);
-  const uint64_t groups = (n + group - 1) / group;
+  uint64_t groups = (n + group - 1) / group;
+  if (n_tiles > groups) groups = n_tiles;
   unsigned char* p = static_cast<unsigned char*>(scratch);
   l.status_bytes = static_cast<size_t>(groups ? groups : 1) * (1u << sp.kernel_bits) * sizeof(uint64_t);
   l.status = reinterpret_cast<uint64_t*>(p);
   p += align256(l.status_bytes);
+  l.hist_bytes = digit_entries(sp, n_seg) * sizeof(unsigned long long);
   l.hist = reinterpret_cast<unsigned long long*>(p);
-  p += align256(static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long));
+  p += align256(l.hist_bytes);
   l.start = reinterpret_cast<uint64_t*>(p);
-  p += align256(static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(uint64_t));
+  p += align256(digit_entries(sp, n_seg) * sizeof(uint64_t));
   l.counters = reinterpret_cast<uint32_t*>(p);
   return l;
+}
+
+// ---------------------------------------------------------------------------
+// Segmented sorts: digit counts per segment (keys read once, shared-memory
+// counters flushed whenever the block moves to another segment) and their
+// exclusive scans, offset by each segment's first position.
+// ---------------------------------------------------------------------------
+struct SegHistArgs {
+  int n_passes;
+  int shift[kMaxPasses];
+  uint32_t mask[kMaxPasses];
+  uint32_t radix;           // counters per (segment, pass)
+  int n_seg;
+  const uint64_t* begin;
+  const uint64_t* end;
+  const uint32_t* tile_begin;
+  uint64_t n_tiles;
+  uint32_t tile;            // keys per tile
+  uint32_t tiles_per_block;
+  unsigned long long* hist; // [segment][pass][radix]
+};
+
+template <typename K>
+__global__ void __launch_bounds__(256) seg_hist_kernel(const K* __restrict__ keys, SegHistArgs h) {
+  extern __shared__ uint32_t sh[];
+  const uint32_t nc = static_cast<uint32_t>(h.n_passes) * h.radix;
+  const auto flush = [&](int seg) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) {
+      const uint32_t v = sh[i];
+      if (v) atomicAdd(&h.hist[static_cast<size_t>(seg) * nc + i], static_cast<unsigned long long>(v));
+      sh[i] = 0u;
+    }
+    __syncthreads();
+  };
+  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) sh[i] = 0u;
+  for (uint64_t t0 = static_cast<uint64_t>(blockIdx.x) * h.tiles_per_block; t0 < h.n_tiles;
+       t0 += static_cast<uint64_t>(gridDim.x) * h.tiles_per_block) {
+    const uint64_t t1 = t0 + h.tiles_per_block < h.n_tiles ? t0 + h.tiles_per_block : h.n_tiles;
+    int lo = 0, hi = h.n_seg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (h.tile_begin[mid] <= t0) lo = mid; else hi = mid - 1;
+    }
+    int seg = lo;
+    __syncthreads();
+    for (uint64_t t = t0; t < t1; ++t) {
+      if (t >= h.tile_begin[seg + 1]) {
+        flush(seg);
+        while (t >= h.tile_begin[seg + 1]) ++seg;
+      }
+      const uint64_t tb = h.begin[seg] + (t - h.tile_begin[seg]) * h.tile;
+      const uint64_t te = tb + h.tile < h.end[seg] ? tb + h.tile : h.end[seg];
+      for (uint64_t i = tb + threadIdx.x; i < te; i += blockDim.x) {
+        const uint64_t k = static_cast<uint64_t>(keys[i]);
+#pragma unroll
+        for (int p = 0; p < kMaxPasses; ++p)
+          if (p < h.n_passes) atomicAdd(&sh[p * h.radix + (static_cast<uint32_t>(k >> h.shift[p]) & h.mask[p])], 1u);
+      }
+    }
+    flush(seg);
+  }
+}
+
+// start[s][p][d] = begin[s] + sum of the counts of digits below d.  One
+// block of 256 threads per (segment, pass).
+__global__ void __launch_bounds__(256) seg_digit_scan_kernel(const unsigned long long* __restrict__ hist,
+                                                             uint64_t* __restrict__ start, uint32_t radix,
+                                                             int n_passes, const uint64_t* __restrict__ begin) {
+  __shared__ uint64_t wsum[8];
+  const int seg = blockIdx.x / n_passes;
+  const size_t row = static_cast<size_t>(blockIdx.x) * radix;
+  const uint32_t per = radix / 256u;  // 1 or 2 digits per thread
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint64_t v0 = hist[row + threadIdx.x * per];
+  uint64_t v1 = per > 1 ? hist[row + threadIdx.x * per + 1] : 0ull;
+  const uint64_t sum = v0 + v1;
+  uint64_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (static_cast<int>(lane) >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  uint64_t before = begin[seg];
+  for (uint32_t w = 0; w < warp; ++w) before += wsum[w];
+  const uint64_t run = before + incl - sum;
+  start[row + threadIdx.x * per] = run;
+  if (per > 1) start[row + threadIdx.x * per + 1] = run + v0;
 }
 
 template <typename K, typename V>
 cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* vals_out, K* keys_tmp, V* vals_tmp,
                            uint64_t n, const SortPasses& sp, void* scratch, uint32_t* err, cudaStream_t st,
-                           cudaEvent_t* pass_events, bool hist_ready, const SortUnpack* unpack, bool* fused) {
+                           cudaEvent_t* pass_events, bool hist_ready, const SortUnpack* unpack, bool* fused,
+                           const SortSegments* segs) {
   if (fused) *fused = false;
+  const int n_seg = segs ? segs->n_seg : 0;
+  // Segments are sorted by the bulk-copy kernel only (8-9 bit digits, 30-bit
+  // look-back counts: every segment below 2^30 keys, 16-byte aligned arrays).
+  const auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (n_seg && (sp.group_tiles != 0 || sp.kernel_bits > 9 || segs->max_len >= (1ull << 30) || !al16(keys_in) ||
+                !al16(vals_in) || !al16(keys_out) || !al16(vals_out) || !al16(keys_tmp) || !al16(vals_tmp)))
+    return cudaErrorInvalidValue;
   // The pass kernels shift keys by up to the key width minus one.
   if (static_cast<size_t>(sp.shift[sp.n_passes - 1]) >= 8 * sizeof(K)) return cudaErrorInvalidValue;
   if (n == 0) {
@@ -942,7 +1082,8 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
   if ((sp.n_passes % 2 == 0) && (static_cast<const void*>(keys_tmp) == static_cast<const void*>(keys_in) ||
                                  static_cast<const void*>(vals_tmp) == static_cast<const void*>(vals_in)))
     return cudaErrorInvalidValue;
-  const SortScratch lay = sort_scratch_layout(scratch, n, sp);
+  const uint64_t n_tiles_seg = n_seg ? segs->n_tiles : 0;
+  const SortScratch lay = sort_scratch_layout(scratch, n, sp, n_tiles_seg, n_seg);
   uint64_t* status = lay.status;
   const size_t status_bytes = lay.status_bytes;
   unsigned long long* hist = lay.hist;
@@ -955,7 +1096,33 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (!hist_ready) {
+  const uint32_t radix = 1u << sp.kernel_bits;
+  if (n_seg) {
+    if ((e = cudaMemsetAsync(hist, 0, lay.hist_bytes, st)) != cudaSuccess) return e;
+    SegHistArgs h{};
+    h.n_passes = sp.n_passes;
+    for (int p = 0; p < kMaxPasses; ++p) {
+      h.shift[p] = p < sp.n_passes ? sp.shift[p] : 0;
+      h.mask[p] = p < sp.n_passes ? sp.mask[p] : 0u;
+    }
+    h.radix = radix;
+    h.n_seg = n_seg;
+    h.begin = segs->begin;
+    h.end = segs->end;
+    h.tile_begin = segs->tile_begin;
+    h.n_tiles = segs->n_tiles;
+    h.tile = static_cast<uint32_t>(onesweep_group(sp));
+    h.tiles_per_block = 16;
+    h.hist = hist;
+    const size_t hsm = static_cast<size_t>(sp.n_passes) * radix * sizeof(uint32_t);
+    if ((e = cudaFuncSetAttribute(seg_hist_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(hsm))) != cudaSuccess)
+      return e;
+    const uint64_t blocks = (segs->n_tiles + h.tiles_per_block - 1) / h.tiles_per_block;
+    seg_hist_kernel<K><<<static_cast<unsigned>(blocks ? blocks : 1), 256, hsm, st>>>(keys_in, h);
+    seg_digit_scan_kernel<<<static_cast<unsigned>(n_seg * sp.n_passes), 256, 0, st>>>(hist, start, radix, sp.n_passes,
+                                                                                     segs->begin);
+  } else if (!hist_ready) {
     if ((e = cudaMemsetAsync(hist, 0, static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long),
                              st)) != cudaSuccess)
       return e;
@@ -968,7 +1135,7 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
     if (e != cudaSuccess) return e;
     radix_hist_kernel<K><<<sms * 2, 512, hist_smem, st>>>(keys_in, n, plan);
   }
-  radix_digit_scan_kernel<<<sp.n_passes, kDigitScanThreads, 0, st>>>(hist, start);
+  if (!n_seg) radix_digit_scan_kernel<<<sp.n_passes, kDigitScanThreads, 0, st>>>(hist, start);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (pass_events) cudaEventRecord(pass_events[0], st);
 
@@ -976,12 +1143,13 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
   // (30-bit look-back words); fall back otherwise.
   const auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   int group_tiles = sp.group_tiles;
-  if (group_tiles == 0 &&
+  if (group_tiles == 0 && !n_seg &&
       (n >= (1ull << 30) || !(aligned16(keys_in) && aligned16(vals_in) && aligned16(keys_out) &&
                               aligned16(vals_out) && (sp.n_passes < 2 || (aligned16(keys_tmp) && aligned16(vals_tmp))))))
     group_tiles = 1;
   const uint64_t tile32 = onesweep_group(sp);  // the bulk-copy kernel's tile
-  const size_t status32_bytes = static_cast<size_t>((n + tile32 - 1) / tile32) * (1u << sp.kernel_bits) * 4u;
+  const uint64_t tiles32 = n_seg ? n_tiles_seg : (n + tile32 - 1) / tile32;
+  const size_t status32_bytes = static_cast<size_t>(tiles32) * (1u << sp.kernel_bits) * 4u;
   const K* kin = keys_in;
   const V* vin = vals_in;
   for (int pass = 0; pass < sp.n_passes; ++pass) {
@@ -996,7 +1164,14 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
     a.n = n;
     a.shift = sp.shift[pass];
     a.mask = sp.mask[pass];
-    a.digit_start = start + static_cast<size_t>(pass) * kMaxRadix;
+    a.digit_start = start + static_cast<size_t>(pass) * (n_seg ? radix : kMaxRadix);
+    a.n_seg = n_seg;
+    if (n_seg) {
+      a.seg_begin = segs->begin;
+      a.seg_end = segs->end;
+      a.seg_tile_begin = segs->tile_begin;
+      a.seg_digit_stride = static_cast<uint64_t>(sp.n_passes) * radix;
+    }
     a.status = status;
     a.tile_counter = counters + pass;
     a.epoch = static_cast<uint32_t>(pass + 1);
@@ -1021,14 +1196,14 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
 template cudaError_t radix_sort_run<uint64_t, uint32_t>(const uint64_t*, const uint32_t*, uint64_t*, uint32_t*,
                                                         uint64_t*, uint32_t*, uint64_t, const SortPasses&, void*,
                                                         uint32_t*, cudaStream_t, cudaEvent_t*, bool,
-                                                        const SortUnpack*, bool*);
+                                                        const SortUnpack*, bool*, const SortSegments*);
 template cudaError_t radix_sort_run<uint32_t, uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*,
                                                         uint32_t*, uint64_t*, uint64_t, const SortPasses&, void*,
                                                         uint32_t*, cudaStream_t, cudaEvent_t*, bool,
-                                                        const SortUnpack*, bool*);
+                                                        const SortUnpack*, bool*, const SortSegments*);
 template cudaError_t radix_sort_run<uint64_t, uint64_t>(const uint64_t*, const uint64_t*, uint64_t*, uint64_t*,
                                                         uint64_t*, uint64_t*, uint64_t, const SortPasses&, void*,
                                                         uint32_t*, cudaStream_t, cudaEvent_t*, bool,
-                                                        const SortUnpack*, bool*);
+                                                        const SortUnpack*, bool*, const SortSegments*);
 
 }  // namespace snc

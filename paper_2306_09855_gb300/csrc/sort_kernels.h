@@ -45,6 +45,15 @@ struct OnesweepArgs {
   uint32_t* unpack_weight;
   uint16_t* unpack_delay;
   uint32_t unpack_delay_mask;
+  // Segmented sort (bulk-copy kernel only): n_seg independent ranges
+  // [seg_begin[s], seg_end[s]) with their tiles numbered from
+  // seg_tile_begin[s]; digit_start then holds seg_digit_stride entries per
+  // segment.  n_seg = 0: one range [0, n).
+  int n_seg;
+  const uint64_t* seg_begin;
+  const uint64_t* seg_end;
+  const uint32_t* seg_tile_begin;
+  uint64_t seg_digit_stride;
 };
 
 // Separate output arrays of the last pass for (source, delay) keys with
@@ -68,16 +77,31 @@ extern SortTuning g_sort_tuning;
 SortPasses plan_passes(int key_bits);  // with g_sort_tuning
 SortPasses plan_passes(int key_bits, const SortTuning& tune);
 int onesweep_group(const SortPasses& sp);  // keys per look-back unit
-size_t sort_scratch_bytes(uint64_t n, const SortPasses& sp);
+// n_tiles / n_seg: the tiles and segments of a segmented sort (0 otherwise).
+size_t sort_scratch_bytes(uint64_t n, const SortPasses& sp, uint64_t n_tiles = 0, int n_seg = 0);
 // Where the parts of the sort's scratch live (sort_scratch_bytes in total).
 struct SortScratch {
   uint64_t* status;
   size_t status_bytes;
+  size_t hist_bytes;
   unsigned long long* hist;  // [kMaxPasses][kMaxRadix] digit counts
   uint64_t* start;           // [kMaxPasses][kMaxRadix] exclusive digit offsets
   uint32_t* counters;        // tile tickets, one per pass
 };
-SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp);
+SortScratch sort_scratch_layout(void* scratch, uint64_t n, const SortPasses& sp, uint64_t n_tiles = 0, int n_seg = 0);
+
+// Independent ranges sorted by one launch per pass (a batched build's
+// networks).  Device arrays: begin/end [n_seg], tile_begin [n_seg + 1] with
+// tiles of onesweep_group(sp) keys; n_tiles = tile_begin[n_seg] (host copy).
+// Every begin must be a multiple of 4.
+struct SortSegments {
+  int n_seg;
+  const uint64_t* begin;
+  const uint64_t* end;
+  const uint32_t* tile_begin;
+  uint64_t n_tiles;
+  uint64_t max_len;  // longest segment (host copy)
+};
 
 // Stable LSD sort of n (key, value) pairs on the planned digits.
 // hist_ready: the digit counts are already in the scratch's hist area (for
@@ -89,6 +113,6 @@ template <typename K, typename V>
 cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* vals_out, K* keys_tmp, V* vals_tmp,
                            uint64_t n, const SortPasses& sp, void* scratch, uint32_t* err, cudaStream_t st,
                            cudaEvent_t* pass_events, bool hist_ready = false, const SortUnpack* unpack = nullptr,
-                           bool* fused = nullptr);
+                           bool* fused = nullptr, const SortSegments* segs = nullptr);
 
 }  // namespace snc

@@ -128,3 +128,20 @@ def test_graph_build_refuses_host_round_trips(snc):
         net.rebuild([1])
     assert e.value.name == "STATE"
     net.close()
+
+
+def test_batch_above_2_pow_30_positions_matches_single_builds(snc):
+    """A batch whose arrays hold more than 2^30 connections (the per-segment
+    sort must not fall back to a whole-array sort)."""
+    specs = [W.two_population(100_000, "fixed_indegree", k=1400, seed=s) for s in (71, 72)]
+    nets = snc.Network.batch(specs)
+    assert sum(int(n.view().n_syn) for n in nets) > (1 << 30)
+    for i, (spec, net) in enumerate(zip(specs, nets)):
+        t = net.tensors()
+        single = snc.Network(spec).finalize()
+        r = single.tensors()
+        for f in ("row_ptr", "group_ptr", "target", "delay", "weight", "group_first"):
+            assert bool((t[f] == r[f]).all()), (i, f)
+        single.close()
+    for net in reversed(nets):
+        net.close()
