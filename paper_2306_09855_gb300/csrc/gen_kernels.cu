@@ -548,6 +548,36 @@ __device__ bool resolve(const RedrawArgs& a, const RedrawProj& r, const DevProj&
   return false;
 }
 
+// Bucketed claims.  Entries are (pair << (slot_bits + 1)) | claim << slot_bits
+// | slot with the pair and slot local to the projection, as in the packed
+// table above.
+__device__ __forceinline__ uint64_t local_pair(const RedrawProj& r, const DevProj& P, uint32_t s, uint32_t t) {
+  return (static_cast<uint64_t>(s - P.s0) << r.t_bits) | (t - P.t0);
+}
+
+__device__ __forceinline__ uint64_t bucket_of(const RedrawProj& r, uint64_t pair) {
+  return r.bucket_base + (r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull);
+}
+
+// Appends an entry to bucket b after its accepted pairs (round 0: the
+// accepted pairs are still being collected).
+__device__ __forceinline__ void bucket_put(const RedrawArgs& a, uint64_t b, uint64_t e, bool round0) {
+  const uint32_t pos = round0 ? atomicAdd(a.fill + b, 1u) : a.fill[b] + atomicAdd(a.pcount + b, 1u);
+  if (pos < a.cap) a.ent[b * a.cap + pos] = e;
+  else atomicOr(a.err, kErrBounds);
+}
+
+// The redraw projection that owns bucket b.
+__device__ __forceinline__ int bucket_owner(const RedrawArgs& a, uint64_t b) {
+  int lo = 0, hi = a.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.rp[mid].bucket_base <= b) lo = mid; else hi = mid - 1;
+  }
+  while (lo > 0 && (a.rp[lo].n_buckets == 0 || b >= a.rp[lo].bucket_base + a.rp[lo].n_buckets)) --lo;
+  return lo;
+}
+
 __device__ __forceinline__ void push_pending(const RedrawArgs& a, uint64_t g) {
   const unsigned long long at = atomicAdd(a.n_next, 1ull);
   if (at < a.n_slots) a.next_pending[at] = g;
@@ -567,8 +597,16 @@ __global__ void redraw_round0_kernel(RedrawArgs a) {
     const uint32_t s = P.s0 + rand_below(W.y, P.ns);
     const uint32_t t = P.t0 + rand_below(tw, P.nt);
     a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
-    if (!allowed_pair(P, s, t)) a.lost[g] = 1;
-    else if (!P.multapses) claim(a, *x.r, P, s, t, x.i, g, true);
+    if (!allowed_pair(P, s, t)) {
+      a.lost[g] = 1;
+    } else if (!P.multapses) {
+      if (a.bucketed) {
+        const uint64_t pair = local_pair(*x.r, P, s, t);
+        bucket_put(a, bucket_of(*x.r, pair), (pair << (x.r->slot_bits + 1)) | x.i, true);
+      } else {
+        claim(a, *x.r, P, s, t, x.i, g, true);
+      }
+    }
   }
 }
 
@@ -589,7 +627,135 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
     const uint32_t s = P.s0 + rand_below(D.x, P.ns);
     const uint32_t t = P.t0 + rand_below(D.y, P.nt);
     a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
-    if (!P.multapses && allowed_pair(P, s, t)) claim(a, *x.r, P, s, t, x.i, g, false);
+    if (a.bucketed) {
+      // Settled here unless the pair needs its bucket: not allowed -> next
+      // round; allowed with multapses -> accepted.
+      if (!allowed_pair(P, s, t)) {
+        push_pending(a, g);
+      } else if (!P.multapses) {
+        const uint64_t pair = local_pair(*x.r, P, s, t);
+        const int sb = x.r->slot_bits;
+        bucket_put(a, bucket_of(*x.r, pair), (pair << (sb + 1)) | (1ull << sb) | x.i, false);
+      }
+    } else if (!P.multapses && allowed_pair(P, s, t)) {
+      claim(a, *x.r, P, s, t, x.i, g, false);
+    }
+  }
+}
+
+// Round 0 of the bucketed claims, one block per bucket at a time: the
+// bucket's entries go into a shared-memory table where, for every pair, the
+// smallest entry (the lowest slot) stays; every other claimant is marked
+// lost.  The survivors are written back as the bucket's accepted pairs.
+__global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
+  __shared__ unsigned long long tab[kBucketTable];
+  __shared__ uint32_t kept;
+  for (uint64_t b = blockIdx.x; b < a.n_buckets; b += gridDim.x) {
+    const RedrawProj& r = a.rp[bucket_owner(a, b)];
+    const int sh = r.slot_bits + 1;
+    const uint64_t slot_mask = (1ull << r.slot_bits) - 1;
+    const uint32_t n = a.fill[b] < a.cap ? a.fill[b] : a.cap;
+    uint64_t* ent = a.ent + b * a.cap;
+    for (uint32_t i = threadIdx.x; i < kBucketTable; i += blockDim.x) tab[i] = kEmpty;
+    if (threadIdx.x == 0) kept = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t e = ent[i];
+      const uint64_t pair = e >> sh;
+      uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & (kBucketTable - 1);
+      for (uint32_t probe = 0; probe < kBucketTable; ++probe) {
+        const uint64_t old = atomicCAS(tab + h, kEmpty, e);
+        if (old == kEmpty) break;
+        if ((old >> sh) == pair) {
+          const uint64_t prev = atomicMin(tab + h, e);
+          const uint64_t loser = prev < e ? e : prev;
+          a.lost[r.slot_base + (loser & slot_mask)] = 1;
+          break;
+        }
+        h = (h + 1) & (kBucketTable - 1);
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kBucketTable; i += blockDim.x) {
+      const uint64_t e = tab[i];
+      if (e != kEmpty) ent[atomicAdd(&kept, 1u)] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.fill[b] = kept;
+    __syncthreads();
+  }
+}
+
+// Later rounds: a bucket's accepted pairs and its claims of the round go
+// into the table (accepted entries have the claim bit clear, so they beat
+// any claim on their pair); a claim wins if its entry is the one left for
+// its pair.  Winners join the accepted pairs, the others wait for the next
+// round.
+__global__ void __launch_bounds__(256) redraw_bucket_round_kernel(RedrawArgs a) {
+  __shared__ unsigned long long tab[kBucketTable];
+  __shared__ uint32_t won;
+  for (uint64_t b = blockIdx.x; b < a.n_buckets; b += gridDim.x) {
+    const uint32_t pc = a.pcount[b];
+    if (pc == 0) continue;  // uniform over the block
+    const RedrawProj& r = a.rp[bucket_owner(a, b)];
+    const int sh = r.slot_bits + 1;
+    const uint64_t claim_bit = 1ull << r.slot_bits;
+    const uint64_t slot_mask = claim_bit - 1;
+    const uint32_t acc = a.fill[b];
+    const uint32_t n = acc + pc <= a.cap ? acc + pc : a.cap;
+    uint64_t* ent = a.ent + b * a.cap;
+    for (uint32_t i = threadIdx.x; i < kBucketTable; i += blockDim.x) tab[i] = kEmpty;
+    if (threadIdx.x == 0) won = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t e = ent[i];
+      const uint64_t pair = e >> sh;
+      uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & (kBucketTable - 1);
+      for (uint32_t probe = 0; probe < kBucketTable; ++probe) {
+        const uint64_t old = atomicCAS(tab + h, kEmpty, e);
+        if (old == kEmpty) break;
+        if ((old >> sh) == pair) {
+          atomicMin(tab + h, e);
+          break;
+        }
+        h = (h + 1) & (kBucketTable - 1);
+      }
+    }
+    __syncthreads();
+    // Decide every claim (they stay in place until all are decided).
+    bool win[kBucketCap / 256];
+    uint64_t mine[kBucketCap / 256];
+#pragma unroll
+    for (int k = 0; k < static_cast<int>(kBucketCap / 256); ++k) {
+      const uint32_t i = acc + threadIdx.x + k * 256u;
+      win[k] = false;
+      mine[k] = 0;
+      if (i < n) {
+        const uint64_t e = ent[i];
+        mine[k] = e;
+        const uint64_t pair = e >> sh;
+        uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & (kBucketTable - 1);
+        for (uint32_t probe = 0; probe < kBucketTable; ++probe) {
+          const uint64_t v = tab[h];
+          if ((v >> sh) == pair) {
+            win[k] = v == e;
+            break;
+          }
+          h = (h + 1) & (kBucketTable - 1);
+        }
+        if (!win[k]) push_pending(a, r.slot_base + (e & slot_mask));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < static_cast<int>(kBucketCap / 256); ++k)
+      if (win[k]) ent[acc + atomicAdd(&won, 1u)] = mine[k] & ~claim_bit;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      a.fill[b] = acc + won;
+      a.pcount[b] = 0;
+    }
+    __syncthreads();
   }
 }
 

@@ -70,6 +70,12 @@ struct RedrawProj {
   uint64_t chunk_base;  // first emit chunk (kChunk slots) of this projection
   uint64_t table_off;   // first entry of its hash table region
   uint64_t table_mask;  // entries - 1 (power of two)
+  // Bucketed claims (RedrawArgs::bucketed): the projection's buckets are
+  // [bucket_base, bucket_base + n_buckets), n_buckets = 1 << bucket_bits (0
+  // when multapses are allowed: no pair table at all).
+  uint64_t bucket_base;
+  uint64_t n_buckets;
+  int bucket_bits;
 };
 
 struct RedrawArgs {
@@ -84,11 +90,27 @@ struct RedrawArgs {
   uint64_t* next_pending;
   unsigned long long* n_next;  // device counter of next_pending
   uint32_t* err;
+  // Bucketed claims: every pair is owned by one bucket (a hash of the pair);
+  // bucket b holds its accepted pairs in ent[b * cap, b * cap + fill[b]) and
+  // the round's claims right after them (pcount[b] of them).
+  int bucketed;
+  uint64_t* ent;
+  uint32_t* fill;
+  uint32_t* pcount;
+  uint32_t cap;
+  uint64_t n_buckets;
 };
+constexpr uint32_t kBucketCap = 2048;    // entries per bucket (accepted + one round's claims)
+constexpr uint32_t kBucketTable = 4096;  // shared-memory hash table of a bucket
+constexpr uint32_t kBucketMean = 1024;   // target mean of round-0 entries per bucket
 __global__ void redraw_round0_kernel(RedrawArgs a);
 __global__ void redraw_collect_kernel(RedrawArgs a);
 __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round);
 __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending);
+// Bucketed claims: round 0 keeps the lowest slot of every pair in each
+// bucket; later rounds settle each bucket's claims against its accepted pairs.
+__global__ void redraw_bucket0_kernel(RedrawArgs a);
+__global__ void redraw_bucket_round_kernel(RedrawArgs a);
 __global__ void total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks);
 
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* block_tmp,

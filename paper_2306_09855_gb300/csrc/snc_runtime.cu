@@ -909,6 +909,29 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       max_len = std::max(max_len, dp[i].d_len);
       rps.push_back(r);
     }
+    // Claims go to buckets of about kBucketMean pairs, each settled in a
+    // shared-memory table, when every pair table would be packed; else to
+    // one global hash table per projection.
+    bool bucketed = !rps.empty();
+    uint64_t n_buckets = 0;
+    for (RedrawProj& r : rps) {
+      const Projection& p = *ups[r.proj].p;
+      if (!p.rule.allow_multapses && !r.packed) bucketed = false;
+    }
+    if (bucketed) {
+      n_table = 0;
+      for (RedrawProj& r : rps) {
+        const Projection& p = *ups[r.proj].p;
+        r.bucket_base = n_buckets;
+        if (p.rule.allow_multapses) continue;
+        const uint64_t want = (cnt[r.proj] + kBucketMean - 1) / kBucketMean;
+        int bits = 0;
+        while ((1ull << bits) < want) ++bits;
+        r.bucket_bits = bits;
+        r.n_buckets = 1ull << bits;
+        n_buckets += r.n_buckets;
+      }
+    }
     if (!rps.empty()) {
       RedrawArgs a{};
       a.projs = d_proj;
@@ -933,6 +956,18 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
           SNC_CUDA(c, cudaMemsetAsync(a.table_vals, 0xFF, n_table * sizeof(uint64_t), st));
         }
       }
+      if (bucketed && n_buckets > 0) {
+        a.bucketed = 1;
+        a.cap = kBucketCap;
+        a.n_buckets = n_buckets;
+        a.ent = static_cast<uint64_t*>(dev_alloc(c, n_buckets * kBucketCap * sizeof(uint64_t)));
+        a.fill = static_cast<uint32_t*>(dev_alloc(c, 2 * n_buckets * sizeof(uint32_t)));
+        if (!a.ent || !a.fill) return fail(c, SNC_ERR_OOM, "device allocation failed (claim buckets)");
+        a.pcount = a.fill + n_buckets;
+        SNC_CUDA(c, cudaMemsetAsync(a.fill, 0, 2 * n_buckets * sizeof(uint32_t), st));
+      } else if (bucketed) {
+        a.bucketed = 1;  // autapse redraws only: no pair tables
+      }
       a.rp = d_rp;
       SNC_CUDA(c, upload(c, d_rp, rps.data(), rps.size() * sizeof(RedrawProj)));
       SNC_CUDA(c, cudaMemsetAsync(a.lost, 0, n_slots, st));
@@ -942,7 +977,13 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         return static_cast<unsigned>(
             std::max<uint64_t>(1, std::min<uint64_t>((items + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
       };
+      const unsigned bucket_grid = static_cast<unsigned>(
+          std::max<uint64_t>(1, std::min<uint64_t>(n_buckets, static_cast<uint64_t>(c->sms) * 6)));
       redraw_round0_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
+      if (a.bucketed && n_buckets > 0) {
+        redraw_bucket0_kernel<<<bucket_grid, 256, 0, st>>>(a);
+        ++c->stats.kernel_launches;
+      }
       redraw_collect_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
       c->stats.kernel_launches += 2;
       SNC_CUDA(c, cudaGetLastError());
@@ -959,7 +1000,11 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         a.next_pending = next;
         SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
         redraw_claim_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend, round);
-        redraw_resolve_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend);
+        if (a.bucketed) {
+          if (n_buckets > 0) redraw_bucket_round_kernel<<<bucket_grid, 256, 0, st>>>(a);
+        } else {
+          redraw_resolve_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend);
+        }
         c->stats.kernel_launches += 2;
         SNC_CUDA(c, cudaGetLastError());
         std::swap(pending, next);
@@ -984,6 +1029,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       dev_free(c, a.n_next);
       dev_free(c, a.table_keys);
       dev_free(c, a.table_vals);
+      dev_free(c, a.ent);
+      dev_free(c, a.fill);
     }
   }
   mark();
