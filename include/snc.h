@@ -212,6 +212,15 @@ snc_status snc_get_connections(snc_ctx* ctx, snc_conn_view* out);
 snc_status snc_copy_connections(snc_ctx* ctx, uint32_t* src, uint32_t* tgt, uint16_t* delay,
                                 float* weight, uint64_t cap);
 
+/* Copies the finalized network's index to host arrays (each may be NULL):
+ * row_ptr and group_ptr (p_i) of n_nodes + 1 entries, group_first of
+ * group_cap >= n_groups entries (Sec. 2.2).  With the target / delay /
+ * weight arrays of snc_copy_connections this is the whole network (the
+ * sources are implicit in row_ptr).  INVALID_ARG when group_cap < n_groups
+ * and group_first is given. */
+snc_status snc_copy_index(snc_ctx* ctx, uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
+                          uint64_t group_cap);
+
 /* Device time of each finalize stage (ms) after snc_synchronize:
  * [0] count, [1] generate, [2] histogram, [3..3+P) sort passes, then index.
  * *n_stages receives the number written (at most max_stages); *n_passes the

@@ -252,11 +252,16 @@ __global__ void rebase_group_first_kernel(uint64_t* group_first, const uint64_t*
   }
 }
 
-// Source of every connection from row_ptr (for host copies).
+// Source of every connection from row_ptr (for host copies): one warp per
+// node writes its row with coalesced stores.
 __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes, uint32_t* src) {
-  const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n_nodes) return;
-  for (uint64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) src[q] = static_cast<uint32_t>(i);
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t n_warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t i = warp; i < n_nodes; i += n_warps) {
+    const uint64_t b = row_ptr[i], e = row_ptr[i + 1];
+    for (uint64_t q = b + lane; q < e; q += 32) src[q] = static_cast<uint32_t>(i);
+  }
 }
 
 }  // namespace snc

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -33,6 +34,50 @@ struct DevBuf {
   size_t bytes;
 };
 
+// Page-locked host memory is recycled for the whole process: freeing it
+// (cudaFreeHost) would synchronize the device and stall builds running on
+// other streams when a context is destroyed.
+class PinnedPool {
+ public:
+  static size_t round_size(size_t bytes) {
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    return c;
+  }
+  void* get(size_t bytes) {
+    const size_t cls = round_size(bytes);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      auto& v = free_[cls];
+      if (!v.empty()) {
+        void* p = v.back();
+        v.pop_back();
+        return p;
+      }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, cls) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu_);
+    free_[round_size(bytes)].push_back(p);
+  }
+
+ private:
+  std::mutex mu_;
+  std::map<size_t, std::vector<void*>> free_;
+};
+
+PinnedPool& pinned_pool() {
+  static PinnedPool* pool = new PinnedPool();  // lives as long as the process
+  return *pool;
+}
+
 // Device memory of one build (a context, or all members of a batch), shared
 // by the member contexts and released when the last of them is destroyed.
 struct Storage {
@@ -52,6 +97,7 @@ struct Storage {
   // Batches: per-member first connection / first group, read back at sync.
   uint64_t* d_bases = nullptr;  // [2 * (members + 1)] on the device
   uint64_t* h_bases = nullptr;  // pinned copy
+  size_t h_bases_words = 0;
   int n_members = 1;
   uint64_t n_total = 0;  // connections of the whole build
   bool synced = false;
@@ -83,12 +129,9 @@ struct Storage {
     const size_t need = (bytes + 15) & ~static_cast<size_t>(15);
     if (stage_chunks.empty() || stage_used + need > stage_chunks.back().second) {
       if (capturing) return nullptr;  // reserved before the capture
-      const size_t cap = std::max<size_t>(need, 1u << 20);
-      void* p = nullptr;
-      if (cudaMallocHost(&p, cap) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-      }
+      const size_t cap = PinnedPool::round_size(std::max<size_t>(need, 1u << 20));
+      void* p = pinned_pool().get(cap);
+      if (!p) return nullptr;
       stage_chunks.push_back({static_cast<unsigned char*>(p), cap});
       stage_used = 0;
     }
@@ -99,12 +142,9 @@ struct Storage {
     return dst;
   }
   bool reserve_stage(size_t bytes) {
-    void* p = nullptr;
-    const size_t cap = std::max<size_t>(bytes, 1u << 20);
-    if (cudaMallocHost(&p, cap) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
-    }
+    const size_t cap = PinnedPool::round_size(std::max<size_t>(bytes, 1u << 20));
+    void* p = pinned_pool().get(cap);
+    if (!p) return false;
     stage_chunks.push_back({static_cast<unsigned char*>(p), cap});
     stage_used = 0;
     return true;
@@ -159,11 +199,8 @@ struct Storage {
       }
     }
     events_ok = true;
-    if (cudaMallocHost(&h_pinned, words * sizeof(uint64_t)) != cudaSuccess) {
-      cudaGetLastError();
-      h_pinned = nullptr;
-      return false;
-    }
+    h_pinned = static_cast<uint64_t*>(pinned_pool().get(words * sizeof(uint64_t)));
+    if (!h_pinned) return false;
     h_pinned_words = words;
     return true;
   }
@@ -177,9 +214,9 @@ struct Storage {
     if (own_stream) cudaStreamDestroy(own_stream);
     if (events_ok)
       for (int i = 0; i < kMaxEvents; ++i) cudaEventDestroy(ev[i]);
-    if (h_pinned) cudaFreeHost(h_pinned);
-    if (h_bases) cudaFreeHost(h_bases);
-    for (auto& ch : stage_chunks) cudaFreeHost(ch.first);
+    pinned_pool().put(h_pinned, h_pinned_words * sizeof(uint64_t));
+    pinned_pool().put(h_bases, h_bases_words * sizeof(uint64_t));
+    for (auto& ch : stage_chunks) pinned_pool().put(ch.first, ch.second);
     cudaGetLastError();
   }
 };
@@ -1159,10 +1196,10 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     SNC_CUDA(c, cudaGetLastError());
   }
   // First group of every network (and the total) for the views.
-  if (!S.h_bases && cudaMallocHost(&S.h_bases, (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t)) != cudaSuccess) {
-    cudaGetLastError();
-    S.h_bases = nullptr;
-    return fail(c, SNC_ERR_OOM, "pinned allocation failed (views)");
+  if (!S.h_bases) {
+    S.h_bases_words = static_cast<size_t>(n_members) + 1;
+    S.h_bases = static_cast<uint64_t*>(pinned_pool().get(S.h_bases_words * sizeof(uint64_t)));
+    if (!S.h_bases) return fail(c, SNC_ERR_OOM, "pinned allocation failed (views)");
   }
   SNC_CUDA(c, cudaMemcpyAsync(S.h_bases, S.d_bases, (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t),
                               cudaMemcpyDeviceToHost, st));
@@ -1392,18 +1429,36 @@ snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16
     uint32_t* d_src = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
     if (!d_src) return fail(c, SNC_ERR_OOM, "device allocation failed (source expansion)");
     if (c->n_nodes > 0) {
-      expand_sources_kernel<<<static_cast<unsigned>((c->n_nodes + 255) / 256), 256, 0, st>>>(c->row_ptr, c->n_nodes, d_src);
+      const uint64_t blocks = std::min<uint64_t>((c->n_nodes + 7) / 8, static_cast<uint64_t>(c->sms) * 16);
+      expand_sources_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(c->row_ptr, c->n_nodes, d_src);
       ++c->stats.kernel_launches;
     }
     SNC_CUDA(c, cudaGetLastError());
     SNC_CUDA(c, cudaMemcpyAsync(src, d_src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    SNC_CUDA(c, cudaStreamSynchronize(st));
-    dev_free(c, d_src);
+    dev_free(c, d_src);  // stream-ordered: after the copy
   }
   if (tgt && n > 0) SNC_CUDA(c, cudaMemcpyAsync(tgt, c->target, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   if (delay && n > 0) SNC_CUDA(c, cudaMemcpyAsync(delay, c->delay, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
   if (weight && n > 0) SNC_CUDA(c, cudaMemcpyAsync(weight, c->weight, n * sizeof(float), cudaMemcpyDeviceToHost, st));
   c->stats.d2h_bytes += n * ((src ? 4 : 0) + (tgt ? 4 : 0) + (delay ? 2 : 0) + (weight ? 4 : 0));
+  SNC_CUDA(c, cudaStreamSynchronize(st));
+  return SNC_OK;
+}
+
+snc_status snc_copy_index(snc_ctx* c, uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
+                          uint64_t group_cap) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (!c->finalized) return fail(c, SNC_ERR_STATE, "copy_index before finalize");
+  snc_status s = snc_synchronize(c);
+  if (s != SNC_OK) return s;
+  if (group_first && group_cap < c->n_groups) return fail(c, SNC_ERR_INVALID_ARG, "group capacity below n_groups");
+  cudaStream_t st = c->store->stream;
+  const size_t rows = (c->n_nodes + 1) * sizeof(uint64_t);
+  if (row_ptr) SNC_CUDA(c, cudaMemcpyAsync(row_ptr, c->row_ptr, rows, cudaMemcpyDeviceToHost, st));
+  if (group_ptr) SNC_CUDA(c, cudaMemcpyAsync(group_ptr, c->group_ptr, rows, cudaMemcpyDeviceToHost, st));
+  if (group_first && c->n_groups > 0)
+    SNC_CUDA(c, cudaMemcpyAsync(group_first, c->group_first, c->n_groups * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  c->stats.d2h_bytes += (row_ptr ? rows : 0) + (group_ptr ? rows : 0) + (group_first ? c->n_groups * sizeof(uint64_t) : 0);
   SNC_CUDA(c, cudaStreamSynchronize(st));
   return SNC_OK;
 }

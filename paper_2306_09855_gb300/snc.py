@@ -108,7 +108,8 @@ SNC_JOB_QUEUED, SNC_JOB_RUNNING, SNC_JOB_DONE, SNC_JOB_FAILED = range(4)
 
 # Every symbol include/snc.h and include/snc_server.h declare.
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
-           "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_stage_times",
+           "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_copy_index",
+           "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
            "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_batch_finalize_graph",
            "snc_batch_rebuild", "snc_last_error",
@@ -142,6 +143,7 @@ def load(build: bool = True):
         "snc_synchronize": ([P], I32),
         "snc_get_connections": ([P, ctypes.POINTER(snc_conn_view)], I32),
         "snc_copy_connections": ([P, P, P, P, P, U64], I32),
+        "snc_copy_index": ([P, P, P, P, U64], I32),
         "snc_stage_times": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(I32),
                              ctypes.POINTER(I32)], I32),
         "snc_radix_sort_pairs": ([P, P, P, P, U64, I32, P], I32),
@@ -246,6 +248,22 @@ def snc_copy_connections(ctx, n_syn, out=None):
     _check(load().snc_copy_connections(ctx, out["src"].ctypes.data, out["tgt"].ctypes.data,
                                        out["delay"].ctypes.data, out["weight"].ctypes.data,
                                        max(n_syn, min(a.size for a in out.values()))), ctx)
+    return out
+
+
+def snc_copy_index(ctx, n_nodes, n_groups, out=None):
+    """Copy row_ptr, group_ptr (n_nodes + 1 entries) and group_first
+    (n_groups entries) into host uint64 arrays (preallocated in `out` or new)."""
+    if out is None:
+        out = {"row_ptr": np.empty(n_nodes + 1, np.uint64), "group_ptr": np.empty(n_nodes + 1, np.uint64),
+               "group_first": np.empty(max(1, n_groups), np.uint64)}
+    for name in ("row_ptr", "group_ptr", "group_first"):
+        a = out[name]
+        need = n_groups if name == "group_first" else n_nodes + 1
+        if a.dtype != np.uint64 or a.size < need or not a.flags.c_contiguous:
+            raise ValueError("output array %r: need %d contiguous uint64" % (name, need))
+    _check(load().snc_copy_index(ctx, out["row_ptr"].ctypes.data, out["group_ptr"].ctypes.data,
+                                 out["group_first"].ctypes.data, out["group_first"].size), ctx)
     return out
 
 
@@ -559,6 +577,20 @@ class Network:
         snc_copy_connections); returns the number of connections."""
         n = int(self.view().n_syn)
         snc_copy_connections(self.ctx, n, out)
+        return n
+
+    def to_host_network(self, out):
+        """Copy the network as it is kept on the device -- target, delay and
+        weight arrays plus the CSR and group index (sources implicit in
+        row_ptr) -- into caller-owned host arrays (keys "tgt", "delay",
+        "weight", "row_ptr", "group_ptr", "group_first"); returns the
+        number of connections."""
+        v = self.view()
+        n = int(v.n_syn)
+        _check(load().snc_copy_connections(self.ctx, None, out["tgt"].ctypes.data, out["delay"].ctypes.data,
+                                           out["weight"].ctypes.data, min(out[k].size for k in ("tgt", "delay", "weight"))),
+               self.ctx)
+        snc_copy_index(self.ctx, int(v.n_nodes), int(v.n_groups), out)
         return n
 
     def stage_times(self):

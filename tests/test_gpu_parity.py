@@ -182,3 +182,25 @@ def test_every_pass_parity(snc, oracle_mod, n_nodes, delay, digit_bits, group, i
                            sort_items=old.sort_items)
     assert st.n_passes == -(-st.key_bits // digit_bits)
     assert_network_equal(got, oracle_mod.build(spec), f"passes={st.n_passes}")
+
+
+def test_copy_index_and_network_copy_match_views(snc):
+    spec = W.two_population(3000, "fixed_indegree", k=50, autapses=False, seed=41)
+    net = snc.Network(spec).finalize()
+    full = net.to_host()
+    v = net.view()
+    n, nn, ng = int(v.n_syn), int(v.n_nodes), int(v.n_groups)
+    out = {"tgt": np.empty(n, np.uint32), "delay": np.empty(n, np.uint16), "weight": np.empty(n, np.float32),
+           "row_ptr": np.empty(nn + 1, np.uint64), "group_ptr": np.empty(nn + 1, np.uint64),
+           "group_first": np.empty(ng + 5, np.uint64)}
+    assert net.to_host_network(out) == n
+    for f in ("tgt", "delay", "weight", "row_ptr", "group_ptr"):
+        np.testing.assert_array_equal(out[f].astype(full[f].dtype), full[f], err_msg=f)
+    np.testing.assert_array_equal(out["group_first"][:ng], full["group_first"][:ng])
+    src = np.repeat(np.arange(nn, dtype=np.uint32), np.diff(out["row_ptr"].astype(np.int64)))
+    np.testing.assert_array_equal(src, full["src"])
+    small = np.empty(max(1, ng - 1), np.uint64)
+    status = snc.load().snc_copy_index(net.ctx, out["row_ptr"].ctypes.data, out["group_ptr"].ctypes.data,
+                                       small.ctypes.data, small.size)
+    assert status == snc.SNC_ERR_INVALID_ARG
+    net.close()
