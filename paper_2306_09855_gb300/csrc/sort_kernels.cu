@@ -887,8 +887,12 @@ cudaError_t launch_onesweep_bits(const SortPasses& sp, int group_tiles, const On
   }
 }
 
-// Process-wide sort tuning (set by snc_set_tuning / the autotuner).
-SortTuning g_sort_tuning{8, 0, 16};
+// Process-wide sort tuning (set by snc_set_tuning / the autotuner).  Digits
+// of up to 9 bits: plan_passes takes the fewest passes and the narrowest
+// even widths, so 9-bit digits are used only where they save a pass (e.g. 3
+// passes instead of 4 for a 25-bit key; a 24-bit key keeps three 8-bit
+// passes).
+SortTuning g_sort_tuning{9, 0, 16};
 
 // Digit plan: the fewest passes of at most max_bits bits, widths as even as
 // possible, the kernel's digit width the widest of them (at least 8).
