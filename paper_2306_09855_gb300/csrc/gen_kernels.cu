@@ -598,7 +598,10 @@ __global__ void redraw_round0_kernel(RedrawArgs a) {
     const uint32_t t = P.t0 + rand_below(tw, P.nt);
     a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
     if (!allowed_pair(P, s, t)) {
-      a.lost[g] = 1;
+      // With buckets the pending list is built directly (its order does not
+      // matter: every later draw depends on the slot and the round only).
+      if (a.bucketed) push_pending(a, g);
+      else a.lost[g] = 1;
     } else if (!P.multapses) {
       if (a.bucketed) {
         const uint64_t pair = local_pair(*x.r, P, s, t);
@@ -645,8 +648,9 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
 
 // Round 0 of the bucketed claims, one block per bucket at a time: the
 // bucket's entries go into a shared-memory table where, for every pair, the
-// smallest entry (the lowest slot) stays; every other claimant is marked
-// lost.  The survivors are written back as the bucket's accepted pairs.
+// smallest entry (the lowest slot) stays; every other claimant joins the
+// pending list.  The survivors are written back as the bucket's accepted
+// pairs.
 __global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
   __shared__ unsigned long long tab[kBucketTable];
   __shared__ uint32_t kept;
@@ -669,7 +673,7 @@ __global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
         if ((old >> sh) == pair) {
           const uint64_t prev = atomicMin(tab + h, e);
           const uint64_t loser = prev < e ? e : prev;
-          a.lost[r.slot_base + (loser & slot_mask)] = 1;
+          push_pending(a, r.slot_base + (loser & slot_mask));
           break;
         }
         h = (h + 1) & (kBucketTable - 1);

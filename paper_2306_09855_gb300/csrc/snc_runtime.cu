@@ -977,11 +977,11 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       a.err = S.d_err;
       RedrawProj* d_rp = static_cast<RedrawProj*>(dev_alloc(c, rps.size() * sizeof(RedrawProj)));
       a.pairs = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
-      a.lost = static_cast<uint8_t*>(dev_alloc(c, n_slots));
+      a.lost = bucketed ? nullptr : static_cast<uint8_t*>(dev_alloc(c, n_slots));
       uint64_t* pend_a = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
       uint64_t* pend_b = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
       a.n_next = static_cast<unsigned long long*>(dev_alloc(c, sizeof(unsigned long long)));
-      if (!d_rp || !a.pairs || !a.lost || !pend_a || !pend_b || !a.n_next)
+      if (!d_rp || !a.pairs || (!bucketed && !a.lost) || !pend_a || !pend_b || !a.n_next)
         return fail(c, SNC_ERR_OOM, "device allocation failed (redraw lists)");
       if (n_table > 0) {
         a.table_keys = static_cast<uint64_t*>(dev_alloc(c, n_table * sizeof(uint64_t)));
@@ -1007,7 +1007,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       }
       a.rp = d_rp;
       SNC_CUDA(c, upload(c, d_rp, rps.data(), rps.size() * sizeof(RedrawProj)));
-      SNC_CUDA(c, cudaMemsetAsync(a.lost, 0, n_slots, st));
+      if (a.lost) SNC_CUDA(c, cudaMemsetAsync(a.lost, 0, n_slots, st));
       SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
       a.next_pending = pend_a;
       const auto grid_for = [&](uint64_t items) {
@@ -1017,12 +1017,17 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       const unsigned bucket_grid = static_cast<unsigned>(
           std::max<uint64_t>(1, std::min<uint64_t>(n_buckets, static_cast<uint64_t>(c->sms) * 6)));
       redraw_round0_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
-      if (a.bucketed && n_buckets > 0) {
-        redraw_bucket0_kernel<<<bucket_grid, 256, 0, st>>>(a);
+      ++c->stats.kernel_launches;
+      if (a.bucketed) {
+        // Round-0 losers go straight to the pending list.
+        if (n_buckets > 0) {
+          redraw_bucket0_kernel<<<bucket_grid, 256, 0, st>>>(a);
+          ++c->stats.kernel_launches;
+        }
+      } else {
+        redraw_collect_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
         ++c->stats.kernel_launches;
       }
-      redraw_collect_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
-      c->stats.kernel_launches += 2;
       SNC_CUDA(c, cudaGetLastError());
       uint64_t* pending = pend_a;
       uint64_t* next = pend_b;
