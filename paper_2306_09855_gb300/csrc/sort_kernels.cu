@@ -786,12 +786,32 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       globm[d] = digit_start[d] + prefix[q] - my_start[q];
     }
     __syncthreads();
-    for (uint32_t i = tid; i < valid; i += TPB) {
-      const K k = skeys[i];
-      const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
-      const uint64_t pos = globm[d] + i;
-      if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
-      emit_pair<UNPACK>(a, pos, k, vin[i]);
+    if (valid == TILE) {
+      // Full tile: all shared-memory reads first, then the stores, so that
+      // the stores of one thread are in flight together.
+      K kk[IPT];
+      V vv[IPT];
+      uint64_t pp[IPT];
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        kk[j] = skeys[tid + j * TPB];
+        vv[j] = vin[tid + j * TPB];
+      }
+#pragma unroll
+      for (int j = 0; j < IPT; ++j)
+        pp[j] = globm[static_cast<uint32_t>(kk[j] >> shift) & mask] + tid + static_cast<uint32_t>(j * TPB);
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        if (SNC_IN_BOUNDS(a.err, 11u, pp[j], a.n)) emit_pair<UNPACK>(a, pp[j], kk[j], vv[j]);
+      }
+    } else {
+      for (uint32_t i = tid; i < valid; i += TPB) {
+        const K k = skeys[i];
+        const uint32_t d = static_cast<uint32_t>(k >> shift) & mask;
+        const uint64_t pos = globm[d] + i;
+        if (!SNC_IN_BOUNDS(a.err, 11u + 0x100u * d, pos, a.n)) continue;
+        emit_pair<UNPACK>(a, pos, k, vin[i]);
+      }
     }
     __syncthreads();  // the tile's buffers and counters are free again
     if (tid == 0) take(0);
