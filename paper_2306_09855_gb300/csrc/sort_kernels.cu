@@ -712,13 +712,11 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       key[j] = ok ? skeys[li] : K(0);
       const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      const int leader = __ffs(peers) - 1;
-      uint32_t old = 0;
-      if (static_cast<int>(lane) == leader && ok) {
-        old = my[d];
-        my[d] = static_cast<uint16_t>(old + __popc(peers));
-      }
-      old = __shfl_sync(0xffffffffu, old, leader);
+      // Every lane reads its digit's counter (peers read the same word),
+      // then the lowest peer advances it past the whole peer set.
+      const uint32_t old = ok ? my[d] : 0u;
+      __syncwarp();
+      if (ok && static_cast<int>(lane) == __ffs(peers) - 1) my[d] = static_cast<uint16_t>(old + __popc(peers));
       rank[j] = old + __popc(peers & lt);
       __syncwarp();
     }
@@ -1209,7 +1207,15 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
       if (fused) *fused = true;
     }
     if (group_tiles == 0 && (e = cudaMemsetAsync(status, 0, status32_bytes, st)) != cudaSuccess) return e;
-    if ((e = launch_onesweep_bits<K, V>(sp, group_tiles, a, sms, st)) != cudaSuccess) return e;
+    // The bulk-copy kernel runs each pass at that pass's own digit width
+    // (at least 8 bits): a narrower radix ranks faster.  Digit starts and
+    // status words keep the plan's widest stride.
+    SortPasses sp_pass = sp;
+    if (group_tiles == 0) {
+      const int w = __builtin_popcount(sp.mask[pass]);
+      sp_pass.kernel_bits = w < 8 ? 8 : w;
+    }
+    if ((e = launch_onesweep_bits<K, V>(sp_pass, group_tiles, a, sms, st)) != cudaSuccess) return e;
     if (pass_events) cudaEventRecord(pass_events[pass + 1], st);
     kin = kout;
     vin = vout;
