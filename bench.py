@@ -516,6 +516,17 @@ def main():
         names = ["count", "generate", "histogram"] + ["pass%d" % k for k in range(npass)] + ["index"]
         for nm, t in zip(names, times):
             stage_sum[nm] = stage_sum.get(nm, 0.0) + t
+    per_network = None
+    if not batched and records:
+        per = {}
+        for k, (n_syn, times, npass, st, _, _) in enumerate(records):
+            name = specs[k % len(specs)].name
+            e = per.setdefault(name, {"network": name, "connections": n_syn, "key_bits": int(st.key_bits),
+                                      "passes": npass, "generate_ms": 0.0, "sort_ms": 0.0, "index_ms": 0.0})
+            e["generate_ms"] += (times[0] + times[1]) / args.steps
+            e["sort_ms"] += sum(times[2:3 + npass]) / args.steps
+            e["index_ms"] += times[3 + npass] / args.steps
+        per_network = list(per.values())
     final_tuning = snc.snc_get_tuning()
     peak, peak_src = measured_peaks()
     achieved = (pass_bytes / (pass_ms / 1e3)) / 1e9 if pass_ms > 0 else 0.0
@@ -632,6 +643,8 @@ def main():
                         "network's copy with the next one's build"},
         "clocks": clk,
     }
+    if per_network:
+        line["per_network"] = per_network
     if batched:
         line["sequential_builds"] = sequential
         line["autotune"] = {"tuning": tune_info["tuning"], "cached": tune_info["cached"], "key": tune_info["key"]}

@@ -585,6 +585,8 @@ __device__ __forceinline__ void push_pending(const RedrawArgs& a, uint64_t g) {
 }
 }  // namespace
 
+// Round 0 with global pair tables: every slot draws and stores its pair;
+// claims go to the projection's table.
 __global__ void redraw_round0_kernel(RedrawArgs a) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < a.n_slots; g += stride) {
@@ -597,19 +599,8 @@ __global__ void redraw_round0_kernel(RedrawArgs a) {
     const uint32_t s = P.s0 + rand_below(W.y, P.ns);
     const uint32_t t = P.t0 + rand_below(tw, P.nt);
     a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
-    if (!allowed_pair(P, s, t)) {
-      // With buckets the pending list is built directly (its order does not
-      // matter: every later draw depends on the slot and the round only).
-      if (a.bucketed) push_pending(a, g);
-      else a.lost[g] = 1;
-    } else if (!P.multapses) {
-      if (a.bucketed) {
-        const uint64_t pair = local_pair(*x.r, P, s, t);
-        bucket_put(a, bucket_of(*x.r, pair), (pair << (x.r->slot_bits + 1)) | x.i, true);
-      } else {
-        claim(a, *x.r, P, s, t, x.i, g, true);
-      }
-    }
+    if (!allowed_pair(P, s, t)) a.lost[g] = 1;
+    else if (!P.multapses) claim(a, *x.r, P, s, t, x.i, g, true);
   }
 }
 
@@ -630,6 +621,7 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
     const uint32_t s = P.s0 + rand_below(D.x, P.ns);
     const uint32_t t = P.t0 + rand_below(D.y, P.nt);
     a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
+    if (a.moved) atomicOr(a.moved + (g >> 5), 1u << (g & 31u));
     if (a.bucketed) {
       // Settled here unless the pair needs its bucket: not allowed -> next
       // round; allowed with multapses -> accepted.
@@ -642,6 +634,64 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
       }
     } else if (!P.multapses && allowed_pair(P, s, t)) {
       claim(a, *x.r, P, s, t, x.i, g, false);
+    }
+  }
+}
+
+// Target word of slot wbase + 32 q + lane from the IDX draws of a window of
+// 128 slots (lane l holds IDX(wbase / 4 + l), four target words).
+__device__ __forceinline__ uint32_t window_target_word(const Words& X, int q, uint32_t lane) {
+  const int src_lane = 8 * q + static_cast<int>(lane >> 2);
+  const uint32_t vx = __shfl_sync(0xffffffffu, X.x, src_lane);
+  const uint32_t vy = __shfl_sync(0xffffffffu, X.y, src_lane);
+  const uint32_t vz = __shfl_sync(0xffffffffu, X.z, src_lane);
+  const uint32_t vw = __shfl_sync(0xffffffffu, X.w, src_lane);
+  const uint32_t sel = lane & 3u;
+  return sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
+}
+
+// The redraw projection that owns emit chunk c.
+__device__ __forceinline__ int chunk_owner(const RedrawArgs& a, uint64_t c) {
+  int lo = 0, hi = a.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.rp[mid].chunk_base <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Round 0 of the bucketed claims: every slot draws its pair (WD word 1 for
+// the source; the IDX draws of a 128-slot window give the targets, one
+// draw per four slots); a pair that is not allowed joins the pending list,
+// an allowed one without multapses goes to its bucket.  Pairs are not
+// stored: the emit kernel draws them again.
+__global__ void __launch_bounds__(kGenThreads) redraw_bucket_draw_kernel(RedrawArgs a, uint64_t total_chunks) {
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
+    const RedrawProj& r = a.rp[chunk_owner(a, c)];
+    const DevProj& P = a.projs[r.proj];
+    const uint64_t start = (c - r.chunk_base) * kChunk;
+    const uint64_t end = min(start + kChunk, P.count);
+    for (int win = 0; win < kChunk / (128 * (kGenThreads / 32)); ++win) {
+      const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
+                             static_cast<uint64_t>(win) * 128;
+      if (wbase >= end) break;
+      const Words X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t tw = window_target_word(X, q, lane);
+        const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
+        if (i >= end) continue;
+        const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
+        const uint32_t s = P.s0 + rand_below(W.y, P.ns);
+        const uint32_t t = P.t0 + rand_below(tw, P.nt);
+        if (!allowed_pair(P, s, t)) {
+          push_pending(a, r.slot_base + i);
+        } else if (!P.multapses) {
+          const uint64_t pair = local_pair(r, P, s, t);
+          bucket_put(a, bucket_of(r, pair), (pair << (r.slot_bits + 1)) | i, true);
+        }
+      }
     }
   }
 }
@@ -782,20 +832,20 @@ __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uin
 
 // Writes the redraw projections' connections: the final pairs with the
 // round-0 weight and delay of each slot.  Blocks take chunks of kChunk slots
-// of one projection (delay table reloaded when the projection changes).
+// of one projection (delay table reloaded when the projection changes);
+// warps take windows of 128 slots, as in the draw kernel.  With bucketed
+// claims a slot that never redrew has its round-0 pair drawn again here;
+// otherwise every pair comes from `pairs`.
 __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks) {
   extern __shared__ uint32_t smem_raw[];
   const uint32_t hw = hist_words(g);
   SmemTables tabs{smem_raw + hw, reinterpret_cast<uint16_t*>(smem_raw + hw + g.max_delay_len)};
   const BlockHist bh = block_hist_begin(g, smem_raw);
   __syncthreads();
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   int cur = -1;
   for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
-    int lo = 0, hi = a.n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (a.rp[mid].chunk_base <= c) lo = mid; else hi = mid - 1;
-    }
+    const int lo = chunk_owner(a, c);
     const RedrawProj& r = a.rp[lo];
     const DevProj& P = a.projs[r.proj];
     if (lo != cur) {
@@ -804,13 +854,32 @@ __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, Redr
       __syncthreads();
       cur = lo;
     }
-    const uint64_t i0 = (c - r.chunk_base) * kChunk;
-    const uint64_t i1 = i0 + kChunk < P.count ? i0 + kChunk : P.count;
-    for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const uint64_t pair = a.pairs[r.slot_base + i];
-      const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-      store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32) - P.t_base, delay_step(P, tabs, W.x),
-            static_cast<uint32_t>(pair) - P.t_base, weight_bits(P, W.z, W.w));
+    const uint64_t start = (c - r.chunk_base) * kChunk;
+    const uint64_t end = min(start + kChunk, P.count);
+    for (int win = 0; win < kChunk / (128 * (kGenThreads / 32)); ++win) {
+      const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
+                             static_cast<uint64_t>(win) * 128;
+      if (wbase >= end) break;
+      Words X{0, 0, 0, 0};
+      if (a.moved) X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t tw = a.moved ? window_target_word(X, q, lane) : 0u;
+        const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
+        if (i >= end) continue;
+        const uint64_t gs = r.slot_base + i;
+        const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
+        uint32_t s, t;
+        if (!a.moved || ((a.moved[gs >> 5] >> (gs & 31u)) & 1u)) {
+          const uint64_t pair = a.pairs[gs];
+          s = static_cast<uint32_t>(pair >> 32);
+          t = static_cast<uint32_t>(pair);
+        } else {
+          s = P.s0 + rand_below(W.y, P.ns);
+          t = P.t0 + rand_below(tw, P.nt);
+        }
+        store(g, bh, P.out_off + i, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+      }
     }
   }
   block_hist_end(g, bh);

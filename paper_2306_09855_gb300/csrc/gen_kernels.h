@@ -99,6 +99,10 @@ struct RedrawArgs {
   uint32_t* pcount;
   uint32_t cap;
   uint64_t n_buckets;
+  // Bucketed claims: pairs[g] holds a slot's pair only if bit g is set here
+  // (the slot redrew); every other slot keeps its round-0 draw, which the
+  // emit kernel draws again.
+  uint32_t* moved;
 };
 constexpr uint32_t kBucketCap = 2048;    // entries per bucket (accepted + one round's claims)
 constexpr uint32_t kBucketTable = 4096;  // shared-memory hash table of a bucket
@@ -109,6 +113,7 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
 __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending);
 // Bucketed claims: round 0 keeps the lowest slot of every pair in each
 // bucket; later rounds settle each bucket's claims against its accepted pairs.
+__global__ void redraw_bucket_draw_kernel(RedrawArgs a, uint64_t total_chunks);
 __global__ void redraw_bucket0_kernel(RedrawArgs a);
 __global__ void redraw_bucket_round_kernel(RedrawArgs a);
 __global__ void total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks);

@@ -1005,6 +1005,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       } else if (bucketed) {
         a.bucketed = 1;  // autapse redraws only: no pair tables
       }
+      if (a.bucketed) {
+        const uint64_t words = (n_slots + 31) / 32;
+        a.moved = static_cast<uint32_t*>(dev_alloc(c, words * sizeof(uint32_t)));
+        if (!a.moved) return fail(c, SNC_ERR_OOM, "device allocation failed (redraw marks)");
+        SNC_CUDA(c, cudaMemsetAsync(a.moved, 0, words * sizeof(uint32_t), st));
+      }
       a.rp = d_rp;
       SNC_CUDA(c, upload(c, d_rp, rps.data(), rps.size() * sizeof(RedrawProj)));
       if (a.lost) SNC_CUDA(c, cudaMemsetAsync(a.lost, 0, n_slots, st));
@@ -1016,7 +1022,13 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       };
       const unsigned bucket_grid = static_cast<unsigned>(
           std::max<uint64_t>(1, std::min<uint64_t>(n_buckets, static_cast<uint64_t>(c->sms) * 6)));
-      redraw_round0_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
+      if (a.bucketed) {
+        const unsigned dg = static_cast<unsigned>(
+            std::min<uint64_t>(n_chunks_r, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm));
+        redraw_bucket_draw_kernel<<<dg, kGenThreads, 0, st>>>(a, n_chunks_r);
+      } else {
+        redraw_round0_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
+      }
       ++c->stats.kernel_launches;
       if (a.bucketed) {
         // Round-0 losers go straight to the pending list.
@@ -1073,6 +1085,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       dev_free(c, a.table_vals);
       dev_free(c, a.ent);
       dev_free(c, a.fill);
+      dev_free(c, a.moved);
     }
   }
   mark();

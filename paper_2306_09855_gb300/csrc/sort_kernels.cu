@@ -354,13 +354,9 @@ __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
         const bool valid = idx < a.n;
         const uint32_t d = valid ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const int leader = __ffs(peers) - 1;
-        uint32_t old = 0;
-        if (static_cast<int>(lane) == leader && valid) {
-          old = my[d];
-          my[d] = static_cast<uint16_t>(old + __popc(peers));
-        }
-        old = __shfl_sync(0xffffffffu, old, leader);
+        const uint32_t old = valid ? my[d] : 0u;
+        __syncwarp();
+        if (valid && static_cast<int>(lane) == __ffs(peers) - 1) my[d] = static_cast<uint16_t>(old + __popc(peers));
         rank[j] = old + __popc(peers & lt);
         __syncwarp();
       }
