@@ -559,10 +559,9 @@ __device__ __forceinline__ uint64_t bucket_of(const RedrawProj& r, uint64_t pair
   return r.bucket_base + (r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull);
 }
 
-// Appends an entry to bucket b after its accepted pairs (round 0: the
-// accepted pairs are still being collected).
-__device__ __forceinline__ void bucket_put(const RedrawArgs& a, uint64_t b, uint64_t e, bool round0) {
-  const uint32_t pos = round0 ? atomicAdd(a.fill + b, 1u) : a.fill[b] + atomicAdd(a.pcount + b, 1u);
+// Appends a claim of round r >= 1 to bucket b after its accepted pairs.
+__device__ __forceinline__ void bucket_put(const RedrawArgs& a, uint64_t b, uint64_t e) {
+  const uint32_t pos = a.fill[b] + atomicAdd(a.pcount + b, 1u);
   if (pos < a.cap) a.ent[b * a.cap + pos] = e;
   else atomicOr(a.err, kErrBounds);
 }
@@ -630,7 +629,7 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
       } else if (!P.multapses) {
         const uint64_t pair = local_pair(*x.r, P, s, t);
         const int sb = x.r->slot_bits;
-        bucket_put(a, bucket_of(*x.r, pair), (pair << (sb + 1)) | (1ull << sb) | x.i, false);
+        bucket_put(a, bucket_of(*x.r, pair), (pair << (sb + 1)) | (1ull << sb) | x.i);
       }
     } else if (!P.multapses && allowed_pair(P, s, t)) {
       claim(a, *x.r, P, s, t, x.i, g, false);
@@ -662,37 +661,114 @@ __device__ __forceinline__ int chunk_owner(const RedrawArgs& a, uint64_t c) {
 
 // Round 0 of the bucketed claims: every slot draws its pair (WD word 1 for
 // the source; the IDX draws of a 128-slot window give the targets, one
-// draw per four slots); a pair that is not allowed joins the pending list,
-// an allowed one without multapses goes to its bucket.  Pairs are not
-// stored: the emit kernel draws them again.
+// draw per four slots); a pair that is not allowed joins the pending list.
+// Without multapses the block's 4096 entries are counted per super-bucket
+// in shared memory, each super-bucket's run reserved with one global
+// atomic, and every entry written into its run.  Pairs are not stored: the
+// emit kernel draws them again.
 __global__ void __launch_bounds__(kGenThreads) redraw_bucket_draw_kernel(RedrawArgs a, uint64_t total_chunks) {
+  extern __shared__ uint32_t sh_super[];
+  uint32_t* cnt = sh_super;                // entries of the chunk per super-bucket
+  uint32_t* base = sh_super + a.max_super;  // reserved start of each run
+  constexpr int kWin = kChunk / (128 * (kGenThreads / 32));
+  constexpr int kPer = 4 * kWin;  // slots per thread and chunk
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
     const RedrawProj& r = a.rp[chunk_owner(a, c)];
     const DevProj& P = a.projs[r.proj];
+    const bool part = !P.multapses;  // uniform over the block
+    const uint32_t n_sup = part ? (1u << r.super_bits) : 0u;
+    const int fine_shift = r.bucket_bits - r.super_bits;
+    for (uint32_t s = threadIdx.x; s < n_sup; s += blockDim.x) cnt[s] = 0;
+    __syncthreads();
     const uint64_t start = (c - r.chunk_base) * kChunk;
     const uint64_t end = min(start + kChunk, P.count);
-    for (int win = 0; win < kChunk / (128 * (kGenThreads / 32)); ++win) {
+    uint64_t ent[kPer];
+    uint32_t rs[kPer];  // (super-bucket << 16) | rank in the chunk's run, ~0 = none
+#pragma unroll
+    for (int win = 0; win < kWin; ++win) {
       const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
                              static_cast<uint64_t>(win) * 128;
-      if (wbase >= end) break;
-      const Words X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
+      Words X{0, 0, 0, 0};
+      if (wbase < end) X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
+        const int k = win * 4 + q;
         const uint32_t tw = window_target_word(X, q, lane);
         const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
+        rs[k] = ~0u;
+        ent[k] = 0;
         if (i >= end) continue;
         const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
         const uint32_t s = P.s0 + rand_below(W.y, P.ns);
         const uint32_t t = P.t0 + rand_below(tw, P.nt);
         if (!allowed_pair(P, s, t)) {
           push_pending(a, r.slot_base + i);
-        } else if (!P.multapses) {
+        } else if (part) {
           const uint64_t pair = local_pair(r, P, s, t);
-          bucket_put(a, bucket_of(r, pair), (pair << (r.slot_bits + 1)) | i, true);
+          const uint64_t fine = r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull;
+          const uint32_t sb = static_cast<uint32_t>(fine >> fine_shift);
+          ent[k] = (pair << (r.slot_bits + 1)) | i;
+          rs[k] = (sb << 16) | atomicAdd(cnt + sb, 1u);
         }
       }
     }
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < n_sup; s += blockDim.x) {
+      const uint32_t n = cnt[s];
+      base[s] = n ? atomicAdd(a.sfill + r.super_base + s, n) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (rs[k] == ~0u) continue;
+      const uint32_t sb = rs[k] >> 16;
+      const uint64_t pos = static_cast<uint64_t>(base[sb]) + (rs[k] & 0xFFFFu);
+      if (pos < r.super_cap) a.sup[r.super_off + sb * r.super_cap + pos] = ent[k];
+      else atomicOr(a.err, kErrBounds);
+    }
+    __syncthreads();  // the counters are reused by the next chunk
+  }
+}
+
+// The redraw projection that owns super-bucket gs.
+__device__ __forceinline__ int super_owner(const RedrawArgs& a, uint64_t gs) {
+  int lo = 0, hi = a.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.rp[mid].super_base <= gs) lo = mid; else hi = mid - 1;
+  }
+  while (lo > 0 && (a.rp[lo].n_buckets == 0 || gs >= a.rp[lo].super_base + (1ull << a.rp[lo].super_bits))) --lo;
+  return lo;
+}
+
+// Spreads each super-bucket over its buckets: one block per super-bucket
+// at a time, the bucket fill counters in shared memory.
+__global__ void __launch_bounds__(256) redraw_bucket_split_kernel(RedrawArgs a) {
+  __shared__ uint32_t fcnt[1u << kSplitBits];
+  for (uint64_t gs = blockIdx.x; gs < a.n_super; gs += gridDim.x) {
+    const RedrawProj& r = a.rp[super_owner(a, gs)];
+    const uint64_t s = gs - r.super_base;
+    const int fine_shift = r.bucket_bits - r.super_bits;
+    const uint32_t n_fine = 1u << fine_shift;
+    const int sh = r.slot_bits + 1;
+    for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) fcnt[f] = 0;
+    __syncthreads();
+    const uint32_t n = a.sfill[gs] < r.super_cap ? a.sfill[gs] : static_cast<uint32_t>(r.super_cap);
+    const uint64_t* src = a.sup + r.super_off + s * r.super_cap;
+    const uint64_t first = r.bucket_base + (s << fine_shift);  // first bucket of this super-bucket
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t e = src[i];
+      const uint64_t pair = e >> sh;
+      const uint64_t fine = r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull;
+      const uint32_t f = static_cast<uint32_t>(fine) & (n_fine - 1u);
+      const uint32_t pos = atomicAdd(fcnt + f, 1u);
+      if (pos < a.cap) a.ent[(first + f) * a.cap + pos] = e;
+      else atomicOr(a.err, kErrBounds);
+    }
+    __syncthreads();
+    for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) a.fill[first + f] = fcnt[f];
+    __syncthreads();
   }
 }
 

@@ -76,6 +76,13 @@ struct RedrawProj {
   uint64_t bucket_base;
   uint64_t n_buckets;
   int bucket_bits;
+  // Round-0 entries first go to 2^super_bits super-buckets (the top bits of
+  // the bucket index; at most kSplitFanout buckets each), region s holding
+  // sup[super_off + s * super_cap, ... + sfill[super_base + s]).
+  int super_bits;
+  uint64_t super_base;
+  uint64_t super_cap;
+  uint64_t super_off;
 };
 
 struct RedrawArgs {
@@ -103,17 +110,25 @@ struct RedrawArgs {
   // (the slot redrew); every other slot keeps its round-0 draw, which the
   // emit kernel draws again.
   uint32_t* moved;
+  uint64_t* sup;
+  uint32_t* sfill;
+  uint64_t n_super;
+  uint32_t max_super;  // largest 2^super_bits of the build
 };
 constexpr uint32_t kBucketCap = 2048;    // entries per bucket (accepted + one round's claims)
 constexpr uint32_t kBucketTable = 4096;  // shared-memory hash table of a bucket
 constexpr uint32_t kBucketMean = 1024;   // target mean of round-0 entries per bucket
+constexpr int kSplitBits = 9;            // buckets per super-bucket: 2^kSplitBits at most
+constexpr int kMaxSuperBits = 12;        // super-buckets per projection: 2^12 at most
 __global__ void redraw_round0_kernel(RedrawArgs a);
 __global__ void redraw_collect_kernel(RedrawArgs a);
 __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round);
 __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending);
 // Bucketed claims: round 0 keeps the lowest slot of every pair in each
 // bucket; later rounds settle each bucket's claims against its accepted pairs.
+// dynamic shared memory: 2 * max_super * 4 bytes
 __global__ void redraw_bucket_draw_kernel(RedrawArgs a, uint64_t total_chunks);
+__global__ void redraw_bucket_split_kernel(RedrawArgs a);
 __global__ void redraw_bucket0_kernel(RedrawArgs a);
 __global__ void redraw_bucket_round_kernel(RedrawArgs a);
 __global__ void total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks);

@@ -463,7 +463,7 @@ snc_status estimate_build(const snc_ctx* c, BuildEstimate* e) {
   // Generation and sort: two key/value buffers, sort scratch, the redraw
   // lists and tables, per-primary offsets.
   const uint64_t gen = 2 * pair * n + scratch +
-                       std::max<uint64_t>(25 * redraw_slots + 8 * redraw_table + 16 * (primaries + 1), 2 * n);
+                       std::max<uint64_t>(34 * redraw_slots + 8 * redraw_table + 16 * (primaries + 1), 2 * n);
   // Index: sorted keys, targets and weights (in the value buffer) and delays
   // (or, when the sort could not unpack, separate target / weight arrays),
   // group starts, row and group pointers (twice for batch members), scans.
@@ -955,18 +955,42 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       const Projection& p = *ups[r.proj].p;
       if (!p.rule.allow_multapses && !r.packed) bucketed = false;
     }
+    uint64_t n_super = 0, sup_entries = 0;
+    uint32_t max_super = 1;
+    if (bucketed) {
+      for (RedrawProj& r : rps) {
+        const Projection& p = *ups[r.proj].p;
+        if (p.rule.allow_multapses) continue;
+        const uint64_t want = (cnt[r.proj] + kBucketMean - 1) / kBucketMean;
+        int bits = 0;
+        while ((1ull << bits) < want) ++bits;
+        if (bits - kSplitBits > kMaxSuperBits) bucketed = false;  // above 2^31 slots: global tables
+      }
+    }
     if (bucketed) {
       n_table = 0;
       for (RedrawProj& r : rps) {
         const Projection& p = *ups[r.proj].p;
         r.bucket_base = n_buckets;
+        r.super_base = n_super;
+        r.super_off = sup_entries;
         if (p.rule.allow_multapses) continue;
-        const uint64_t want = (cnt[r.proj] + kBucketMean - 1) / kBucketMean;
+        const uint64_t N = cnt[r.proj];
+        const uint64_t want = (N + kBucketMean - 1) / kBucketMean;
         int bits = 0;
         while ((1ull << bits) < want) ++bits;
         r.bucket_bits = bits;
         r.n_buckets = 1ull << bits;
         n_buckets += r.n_buckets;
+        // Super-buckets of up to 2^kSplitBits buckets; each region holds its
+        // mean share plus 16 standard deviations of the binomial count.
+        r.super_bits = bits > kSplitBits ? bits - kSplitBits : 0;
+        const uint64_t n_sup = 1ull << r.super_bits;
+        const double mean = static_cast<double>(N) / static_cast<double>(n_sup);
+        r.super_cap = std::min<uint64_t>(N, static_cast<uint64_t>(mean + 16.0 * std::sqrt(mean)) + 64);
+        n_super += n_sup;
+        sup_entries += n_sup * r.super_cap;
+        max_super = std::max<uint32_t>(max_super, static_cast<uint32_t>(n_sup));
       }
     }
     if (!rps.empty()) {
@@ -1002,6 +1026,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         if (!a.ent || !a.fill) return fail(c, SNC_ERR_OOM, "device allocation failed (claim buckets)");
         a.pcount = a.fill + n_buckets;
         SNC_CUDA(c, cudaMemsetAsync(a.fill, 0, 2 * n_buckets * sizeof(uint32_t), st));
+        a.n_super = n_super;
+        a.max_super = max_super;
+        a.sup = static_cast<uint64_t*>(dev_alloc(c, sup_entries * sizeof(uint64_t)));
+        a.sfill = static_cast<uint32_t*>(dev_alloc(c, n_super * sizeof(uint32_t)));
+        if (!a.sup || !a.sfill) return fail(c, SNC_ERR_OOM, "device allocation failed (claim super-buckets)");
+        SNC_CUDA(c, cudaMemsetAsync(a.sfill, 0, n_super * sizeof(uint32_t), st));
       } else if (bucketed) {
         a.bucketed = 1;  // autapse redraws only: no pair tables
       }
@@ -1025,7 +1055,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       if (a.bucketed) {
         const unsigned dg = static_cast<unsigned>(
             std::min<uint64_t>(n_chunks_r, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm));
-        redraw_bucket_draw_kernel<<<dg, kGenThreads, 0, st>>>(a, n_chunks_r);
+        redraw_bucket_draw_kernel<<<dg, kGenThreads, 2 * a.max_super * sizeof(uint32_t), st>>>(a, n_chunks_r);
       } else {
         redraw_round0_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
       }
@@ -1033,8 +1063,11 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       if (a.bucketed) {
         // Round-0 losers go straight to the pending list.
         if (n_buckets > 0) {
+          const unsigned split_grid = static_cast<unsigned>(
+              std::max<uint64_t>(1, std::min<uint64_t>(n_super, static_cast<uint64_t>(c->sms) * 8)));
+          redraw_bucket_split_kernel<<<split_grid, 256, 0, st>>>(a);
           redraw_bucket0_kernel<<<bucket_grid, 256, 0, st>>>(a);
-          ++c->stats.kernel_launches;
+          c->stats.kernel_launches += 2;
         }
       } else {
         redraw_collect_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
@@ -1086,6 +1119,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       dev_free(c, a.ent);
       dev_free(c, a.fill);
       dev_free(c, a.moved);
+      dev_free(c, a.sup);
+      dev_free(c, a.sfill);
     }
   }
   mark();

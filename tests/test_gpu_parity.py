@@ -204,3 +204,21 @@ def test_copy_index_and_network_copy_match_views(snc):
                                        small.ctypes.data, small.size)
     assert status == snc.SNC_ERR_INVALID_ARG
     net.close()
+
+
+def test_redraw_super_buckets(snc, oracle_mod):
+    """fixed_total_number without multapses above 2^19 slots: round-0 pairs
+    pass through several super-buckets before their buckets (1.5e6 slots on
+    1e7 pairs, so that many slots redraw over several rounds), next to a
+    projection that redraws autapses only."""
+    spec = NetworkSpec(seed=29, dt=0.1, populations=[2500, 1500], projections=[
+        Projection(src=(0, 2500), tgt=(0, 4000), rule="fixed_total_number", k=1_500_000, autapses=False,
+                   multapses=False, weight=Dist("normal", 5.0, 1.0), delay=Dist("normal", 1.5, 0.75)),
+        Projection(src=(2500, 1500), tgt=(0, 2500), rule="fixed_total_number", k=700_001, multapses=False,
+                   weight=Dist("normal", -3.0, 1.0), delay=Dist("normal", 1.5, 0.75)),
+        Projection(src=(0, 4000), tgt=(0, 4000), rule="fixed_total_number", k=600_000, autapses=False,
+                   weight=Dist("normal", 1.0, 0.5), delay=Dist("normal", 1.5, 0.75))])
+    net = snc.Network(spec).finalize()
+    got = net.to_host()
+    net.close()
+    assert_network_equal(got, oracle_mod.build(spec), "super-buckets")
