@@ -213,11 +213,11 @@ def test_redraw_super_buckets(snc, oracle_mod):
     projection that redraws autapses only."""
     spec = NetworkSpec(seed=29, dt=0.1, populations=[2500, 1500], projections=[
         Projection(src=(0, 2500), tgt=(0, 4000), rule="fixed_total_number", k=1_500_000, autapses=False,
-                   multapses=False, weight=Dist("normal", 5.0, 1.0), delay=Dist("normal", 1.5, 0.75)),
+                   multapses=False, weight=Dist("normal", 8.0, 1.0), delay=Dist("normal", 1.5, 0.75)),
         Projection(src=(2500, 1500), tgt=(0, 2500), rule="fixed_total_number", k=700_001, multapses=False,
-                   weight=Dist("normal", -3.0, 1.0), delay=Dist("normal", 1.5, 0.75)),
+                   weight=Dist("normal", -3.0, 0.4), delay=Dist("normal", 1.5, 0.75)),
         Projection(src=(0, 4000), tgt=(0, 4000), rule="fixed_total_number", k=600_000, autapses=False,
-                   weight=Dist("normal", 1.0, 0.5), delay=Dist("normal", 1.5, 0.75))])
+                   weight=Dist("normal", 2.0, 0.25), delay=Dist("normal", 1.5, 0.75))])
     net = snc.Network(spec).finalize()
     got = net.to_host()
     net.close()
