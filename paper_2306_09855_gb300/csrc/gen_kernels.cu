@@ -731,43 +731,93 @@ __global__ void __launch_bounds__(kGenThreads) redraw_bucket_draw_kernel(RedrawA
   }
 }
 
-// The redraw projection that owns super-bucket gs.
-__device__ __forceinline__ int super_owner(const RedrawArgs& a, uint64_t gs) {
-  int lo = 0, hi = a.n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a.rp[mid].super_base <= gs) lo = mid; else hi = mid - 1;
+// Finds pair's entry in a shared-memory table of `mask + 1` words (linear
+// probing from the pair's hash); the index of the entry, or of the empty
+// word that ends its probe sequence.
+__device__ __forceinline__ uint32_t table_find(const unsigned long long* tab, uint32_t mask, uint64_t pair, int sh) {
+  uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const uint64_t v = tab[h];
+    if (v == kEmpty || (v >> sh) == pair) return h;
+    h = (h + 1) & mask;
   }
-  while (lo > 0 && (a.rp[lo].n_buckets == 0 || gs >= a.rp[lo].super_base + (1ull << a.rp[lo].super_bits))) --lo;
-  return lo;
+  return h;
 }
 
-// Spreads each super-bucket over its buckets: one block per super-bucket
-// at a time, the bucket fill counters in shared memory.
-__global__ void __launch_bounds__(256) redraw_bucket_split_kernel(RedrawArgs a) {
+// Puts e into the table; the entry left for its pair is the smallest.
+// Returns the previous entry of the pair, or kEmpty when it was new.
+__device__ __forceinline__ uint64_t table_put(unsigned long long* tab, uint32_t mask, uint64_t e, int sh) {
+  const uint64_t pair = e >> sh;
+  uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const uint64_t old = atomicCAS(tab + h, kEmpty, e);
+    if (old == kEmpty) return kEmpty;
+    if ((old >> sh) == pair) return atomicMin(tab + h, e);
+    h = (h + 1) & mask;
+  }
+  return kEmpty;  // full table: cannot happen, entries <= words
+}
+
+// Spreads the super-buckets over their buckets.  A block takes a unit of
+// kSplitUnit entries of one super-bucket, counts them per bucket in shared
+// memory, reserves each bucket's run with one global atomic and writes the
+// entries into their runs.
+__global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(RedrawArgs a) {
   __shared__ uint32_t fcnt[1u << kSplitBits];
-  for (uint64_t gs = blockIdx.x; gs < a.n_super; gs += gridDim.x) {
-    const RedrawProj& r = a.rp[super_owner(a, gs)];
-    const uint64_t s = gs - r.super_base;
+  __shared__ uint32_t fbase[1u << kSplitBits];
+  constexpr int kPer = kSplitUnit / kSplitThreads;
+  for (uint64_t u = blockIdx.x; u < a.n_split_units; u += gridDim.x) {
+    int lo = 0, hi = a.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.rp[mid].split_base <= u) lo = mid; else hi = mid - 1;
+    }
+    const RedrawProj& r = a.rp[lo];
+    const uint64_t lu = u - r.split_base;
+    const uint64_t s = lu / r.split_per_super;
+    const uint64_t part = lu - s * r.split_per_super;
+    const uint64_t gs = r.super_base + s;
     const int fine_shift = r.bucket_bits - r.super_bits;
     const uint32_t n_fine = 1u << fine_shift;
     const int sh = r.slot_bits + 1;
-    for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) fcnt[f] = 0;
-    __syncthreads();
-    const uint32_t n = a.sfill[gs] < r.super_cap ? a.sfill[gs] : static_cast<uint32_t>(r.super_cap);
-    const uint64_t* src = a.sup + r.super_off + s * r.super_cap;
+    const uint64_t fill = a.sfill[gs] < r.super_cap ? a.sfill[gs] : r.super_cap;
+    const uint64_t i0 = part * kSplitUnit;
+    if (i0 >= fill) continue;  // uniform over the block
+    const uint32_t n = static_cast<uint32_t>(fill - i0 < kSplitUnit ? fill - i0 : kSplitUnit);
+    const uint64_t* src = a.sup + r.super_off + s * r.super_cap + i0;
     const uint64_t first = r.bucket_base + (s << fine_shift);  // first bucket of this super-bucket
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint64_t e = src[i];
-      const uint64_t pair = e >> sh;
-      const uint64_t fine = r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull;
-      const uint32_t f = static_cast<uint32_t>(fine) & (n_fine - 1u);
-      const uint32_t pos = atomicAdd(fcnt + f, 1u);
-      if (pos < a.cap) a.ent[(first + f) * a.cap + pos] = e;
-      else atomicOr(a.err, kErrBounds);
+    for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) fcnt[f] = 0;
+    uint64_t e[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = threadIdx.x + static_cast<uint32_t>(k) * kSplitThreads;
+      e[k] = i < n ? src[i] : kEmpty;
     }
     __syncthreads();
-    for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) a.fill[first + f] = fcnt[f];
+    uint32_t fr[kPer];  // (bucket << 16) | rank
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      fr[k] = ~0u;
+      if (e[k] == kEmpty) continue;
+      const uint64_t pair = e[k] >> sh;
+      const uint64_t fine = r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull;
+      const uint32_t f = static_cast<uint32_t>(fine) & (n_fine - 1u);
+      fr[k] = (f << 16) | atomicAdd(fcnt + f, 1u);
+    }
+    __syncthreads();
+    for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) {
+      const uint32_t c = fcnt[f];
+      fbase[f] = c ? atomicAdd(a.fill + first + f, c) : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (fr[k] == ~0u) continue;
+      const uint32_t f = fr[k] >> 16;
+      const uint32_t pos = fbase[f] + (fr[k] & 0xFFFFu);
+      if (pos < a.cap) a.ent[(first + f) * a.cap + pos] = e[k];
+      else atomicOr(a.err, kErrBounds);
+    }
     __syncthreads();
   }
 }
@@ -775,40 +825,39 @@ __global__ void __launch_bounds__(256) redraw_bucket_split_kernel(RedrawArgs a) 
 // Round 0 of the bucketed claims, one block per bucket at a time: the
 // bucket's entries go into a shared-memory table where, for every pair, the
 // smallest entry (the lowest slot) stays; every other claimant joins the
-// pending list.  The survivors are written back as the bucket's accepted
-// pairs.
+// pending list.  The entries left in the table are written back as the
+// bucket's accepted pairs.
 __global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
   __shared__ unsigned long long tab[kBucketTable];
   __shared__ uint32_t kept;
+  constexpr int kPer = kBucketCap / 256;
   for (uint64_t b = blockIdx.x; b < a.n_buckets; b += gridDim.x) {
     const RedrawProj& r = a.rp[bucket_owner(a, b)];
     const int sh = r.slot_bits + 1;
     const uint64_t slot_mask = (1ull << r.slot_bits) - 1;
     const uint32_t n = a.fill[b] < a.cap ? a.fill[b] : a.cap;
     uint64_t* ent = a.ent + b * a.cap;
+    // Entries are below 2^63, never kEmpty.
+    uint64_t mine[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = threadIdx.x + static_cast<uint32_t>(k) * 256u;
+      mine[k] = i < n ? ent[i] : kEmpty;
+    }
     for (uint32_t i = threadIdx.x; i < kBucketTable; i += blockDim.x) tab[i] = kEmpty;
     if (threadIdx.x == 0) kept = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint64_t e = ent[i];
-      const uint64_t pair = e >> sh;
-      uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & (kBucketTable - 1);
-      for (uint32_t probe = 0; probe < kBucketTable; ++probe) {
-        const uint64_t old = atomicCAS(tab + h, kEmpty, e);
-        if (old == kEmpty) break;
-        if ((old >> sh) == pair) {
-          const uint64_t prev = atomicMin(tab + h, e);
-          const uint64_t loser = prev < e ? e : prev;
-          push_pending(a, r.slot_base + (loser & slot_mask));
-          break;
-        }
-        h = (h + 1) & (kBucketTable - 1);
-      }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (mine[k] == kEmpty) continue;
+      const uint64_t prev = table_put(tab, kBucketTable - 1, mine[k], sh);
+      if (prev != kEmpty) push_pending(a, r.slot_base + ((prev < mine[k] ? mine[k] : prev) & slot_mask));
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kBucketTable; i += blockDim.x) {
-      const uint64_t e = tab[i];
-      if (e != kEmpty) ent[atomicAdd(&kept, 1u)] = e;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (mine[k] == kEmpty) continue;
+      if (tab[table_find(tab, kBucketTable - 1, mine[k] >> sh, sh)] == mine[k]) ent[atomicAdd(&kept, 1u)] = mine[k];
     }
     __syncthreads();
     if (threadIdx.x == 0) a.fill[b] = kept;
@@ -816,14 +865,16 @@ __global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
   }
 }
 
-// Later rounds: a bucket's accepted pairs and its claims of the round go
-// into the table (accepted entries have the claim bit clear, so they beat
-// any claim on their pair); a claim wins if its entry is the one left for
-// its pair.  Winners join the accepted pairs, the others wait for the next
-// round.
+// Later rounds: the round's claims of a bucket go into a table sized for
+// them (the lowest claim on a pair stays); then each accepted pair of the
+// bucket looks its pair up and, where a claim holds it, leaves its own
+// (smaller, claim bit clear) entry there.  A claim wins if its entry is the
+// one left for its pair: winners join the accepted pairs, the others wait
+// for the next round.
 __global__ void __launch_bounds__(256) redraw_bucket_round_kernel(RedrawArgs a) {
   __shared__ unsigned long long tab[kBucketTable];
   __shared__ uint32_t won;
+  constexpr int kPer = kBucketCap / 256;
   for (uint64_t b = blockIdx.x; b < a.n_buckets; b += gridDim.x) {
     const uint32_t pc = a.pcount[b];
     if (pc == 0) continue;  // uniform over the block
@@ -831,54 +882,52 @@ __global__ void __launch_bounds__(256) redraw_bucket_round_kernel(RedrawArgs a) 
     const int sh = r.slot_bits + 1;
     const uint64_t claim_bit = 1ull << r.slot_bits;
     const uint64_t slot_mask = claim_bit - 1;
-    const uint32_t acc = a.fill[b];
+    const uint32_t acc = a.fill[b] < a.cap ? a.fill[b] : a.cap;
     const uint32_t n = acc + pc <= a.cap ? acc + pc : a.cap;
     uint64_t* ent = a.ent + b * a.cap;
-    for (uint32_t i = threadIdx.x; i < kBucketTable; i += blockDim.x) tab[i] = kEmpty;
+    uint32_t words = 64;
+    while (words < 2 * (n - acc) && words < kBucketTable) words <<= 1;
+    const uint32_t mask = words - 1;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) tab[i] = kEmpty;
     if (threadIdx.x == 0) won = 0;
+    uint64_t mine[kPer];  // this thread's claims
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = acc + threadIdx.x + static_cast<uint32_t>(k) * 256u;
+      mine[k] = i < n ? ent[i] : kEmpty;
+    }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const uint64_t e = ent[i];
-      const uint64_t pair = e >> sh;
-      uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & (kBucketTable - 1);
-      for (uint32_t probe = 0; probe < kBucketTable; ++probe) {
-        const uint64_t old = atomicCAS(tab + h, kEmpty, e);
-        if (old == kEmpty) break;
-        if ((old >> sh) == pair) {
-          atomicMin(tab + h, e);
-          break;
-        }
-        h = (h + 1) & (kBucketTable - 1);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+      if (mine[k] != kEmpty) table_put(tab, mask, mine[k], sh);
+    __syncthreads();
+    for (uint32_t i0 = 0; i0 < acc; i0 += kPer * 256u) {
+      uint64_t v[kPer];
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const uint32_t i = i0 + threadIdx.x + static_cast<uint32_t>(k) * 256u;
+        v[k] = i < acc ? ent[i] : kEmpty;
+      }
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        if (v[k] == kEmpty) continue;
+        const uint32_t h = table_find(tab, mask, v[k] >> sh, sh);
+        if (tab[h] != kEmpty) atomicMin(tab + h, v[k]);
       }
     }
     __syncthreads();
     // Decide every claim (they stay in place until all are decided).
-    bool win[kBucketCap / 256];
-    uint64_t mine[kBucketCap / 256];
+    bool win[kPer];
 #pragma unroll
-    for (int k = 0; k < static_cast<int>(kBucketCap / 256); ++k) {
-      const uint32_t i = acc + threadIdx.x + k * 256u;
+    for (int k = 0; k < kPer; ++k) {
       win[k] = false;
-      mine[k] = 0;
-      if (i < n) {
-        const uint64_t e = ent[i];
-        mine[k] = e;
-        const uint64_t pair = e >> sh;
-        uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & (kBucketTable - 1);
-        for (uint32_t probe = 0; probe < kBucketTable; ++probe) {
-          const uint64_t v = tab[h];
-          if ((v >> sh) == pair) {
-            win[k] = v == e;
-            break;
-          }
-          h = (h + 1) & (kBucketTable - 1);
-        }
-        if (!win[k]) push_pending(a, r.slot_base + (e & slot_mask));
-      }
+      if (mine[k] == kEmpty) continue;
+      win[k] = tab[table_find(tab, mask, mine[k] >> sh, sh)] == mine[k];
+      if (!win[k]) push_pending(a, r.slot_base + (mine[k] & slot_mask));
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < static_cast<int>(kBucketCap / 256); ++k)
+    for (int k = 0; k < kPer; ++k)
       if (win[k]) ent[acc + atomicAdd(&won, 1u)] = mine[k] & ~claim_bit;
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -83,6 +83,10 @@ struct RedrawProj {
   uint64_t super_base;
   uint64_t super_cap;
   uint64_t super_off;
+  // Split units (kSplitUnit entries of one super-bucket): split_per_super
+  // per super-bucket, the projection's first unit split_base.
+  uint64_t split_base;
+  uint64_t split_per_super;
 };
 
 struct RedrawArgs {
@@ -114,12 +118,15 @@ struct RedrawArgs {
   uint32_t* sfill;
   uint64_t n_super;
   uint32_t max_super;  // largest 2^super_bits of the build
+  uint64_t n_split_units;
 };
 constexpr uint32_t kBucketCap = 2048;    // entries per bucket (accepted + one round's claims)
 constexpr uint32_t kBucketTable = 4096;  // shared-memory hash table of a bucket
 constexpr uint32_t kBucketMean = 1024;   // target mean of round-0 entries per bucket
 constexpr int kSplitBits = 9;            // buckets per super-bucket: 2^kSplitBits at most
 constexpr int kMaxSuperBits = 12;        // super-buckets per projection: 2^12 at most
+constexpr int kSplitThreads = 512;       // split kernel block
+constexpr uint32_t kSplitUnit = 8192;    // entries per split block and unit
 __global__ void redraw_round0_kernel(RedrawArgs a);
 __global__ void redraw_collect_kernel(RedrawArgs a);
 __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round);

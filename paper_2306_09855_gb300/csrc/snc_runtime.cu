@@ -955,7 +955,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       const Projection& p = *ups[r.proj].p;
       if (!p.rule.allow_multapses && !r.packed) bucketed = false;
     }
-    uint64_t n_super = 0, sup_entries = 0;
+    uint64_t n_super = 0, sup_entries = 0, n_split_units = 0;
     uint32_t max_super = 1;
     if (bucketed) {
       for (RedrawProj& r : rps) {
@@ -974,6 +974,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         r.bucket_base = n_buckets;
         r.super_base = n_super;
         r.super_off = sup_entries;
+        r.split_base = n_split_units;
         if (p.rule.allow_multapses) continue;
         const uint64_t N = cnt[r.proj];
         const uint64_t want = (N + kBucketMean - 1) / kBucketMean;
@@ -988,6 +989,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         const uint64_t n_sup = 1ull << r.super_bits;
         const double mean = static_cast<double>(N) / static_cast<double>(n_sup);
         r.super_cap = std::min<uint64_t>(N, static_cast<uint64_t>(mean + 16.0 * std::sqrt(mean)) + 64);
+        r.split_base = n_split_units;
+        r.split_per_super = std::max<uint64_t>(1, (r.super_cap + kSplitUnit - 1) / kSplitUnit);
+        n_split_units += n_sup * r.split_per_super;
         n_super += n_sup;
         sup_entries += n_sup * r.super_cap;
         max_super = std::max<uint32_t>(max_super, static_cast<uint32_t>(n_sup));
@@ -1028,6 +1032,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         SNC_CUDA(c, cudaMemsetAsync(a.fill, 0, 2 * n_buckets * sizeof(uint32_t), st));
         a.n_super = n_super;
         a.max_super = max_super;
+        a.n_split_units = n_split_units;
         a.sup = static_cast<uint64_t*>(dev_alloc(c, sup_entries * sizeof(uint64_t)));
         a.sfill = static_cast<uint32_t*>(dev_alloc(c, n_super * sizeof(uint32_t)));
         if (!a.sup || !a.sfill) return fail(c, SNC_ERR_OOM, "device allocation failed (claim super-buckets)");
@@ -1064,8 +1069,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         // Round-0 losers go straight to the pending list.
         if (n_buckets > 0) {
           const unsigned split_grid = static_cast<unsigned>(
-              std::max<uint64_t>(1, std::min<uint64_t>(n_super, static_cast<uint64_t>(c->sms) * 8)));
-          redraw_bucket_split_kernel<<<split_grid, 256, 0, st>>>(a);
+              std::max<uint64_t>(1, std::min<uint64_t>(n_split_units, static_cast<uint64_t>(c->sms) * 4)));
+          redraw_bucket_split_kernel<<<split_grid, kSplitThreads, 0, st>>>(a);
           redraw_bucket0_kernel<<<bucket_grid, 256, 0, st>>>(a);
           c->stats.kernel_launches += 2;
         }
