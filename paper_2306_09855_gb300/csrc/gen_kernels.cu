@@ -559,9 +559,16 @@ __device__ __forceinline__ uint64_t bucket_of(const RedrawProj& r, uint64_t pair
   return r.bucket_base + (r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull);
 }
 
-// Appends a claim of round r >= 1 to bucket b after its accepted pairs.
+// Appends a claim of round r >= 1 to bucket b after its accepted pairs; the
+// bucket's first claim of the round lists it as touched.
 __device__ __forceinline__ void bucket_put(const RedrawArgs& a, uint64_t b, uint64_t e) {
-  const uint32_t pos = a.fill[b] + atomicAdd(a.pcount + b, 1u);
+  const uint32_t k = atomicAdd(a.pcount + b, 1u);
+  if (k == 0) {
+    const unsigned long long at = atomicAdd(a.n_touched, 1ull);
+    if (at < a.n_buckets) a.touched[at] = b;
+    else atomicOr(a.err, kErrBounds);
+  }
+  const uint32_t pos = a.fill[b] + k;
   if (pos < a.cap) a.ent[b * a.cap + pos] = e;
   else atomicOr(a.err, kErrBounds);
 }
@@ -659,75 +666,143 @@ __device__ __forceinline__ int chunk_owner(const RedrawArgs& a, uint64_t c) {
   return lo;
 }
 
-// Round 0 of the bucketed claims: every slot draws its pair (WD word 1 for
-// the source; the IDX draws of a 128-slot window give the targets, one
-// draw per four slots); a pair that is not allowed joins the pending list.
-// Without multapses the block's 4096 entries are counted per super-bucket
-// in shared memory, each super-bucket's run reserved with one global
-// atomic, and every entry written into its run.  Pairs are not stored: the
-// emit kernel draws them again.
-__global__ void __launch_bounds__(kGenThreads) redraw_bucket_draw_kernel(RedrawArgs a, uint64_t total_chunks) {
-  extern __shared__ uint32_t sh_super[];
-  uint32_t* cnt = sh_super;                // entries of the chunk per super-bucket
-  uint32_t* base = sh_super + a.max_super;  // reserved start of each run
-  constexpr int kWin = kChunk / (128 * (kGenThreads / 32));
-  constexpr int kPer = 4 * kWin;  // slots per thread and chunk
+// Round 0 with buckets, fused with the emit: every slot draws its round-0
+// connection (WD for source, delay and weight; the IDX draws of a 128-slot
+// window give the targets, one draw per four slots) and writes it; slots
+// that redraw later are rewritten by the patch kernel.  A pair that is not
+// allowed joins the pending list.  Without multapses the pairs of half a
+// chunk (2048 slots) are counted per super-bucket in shared memory, each
+// super-bucket's run reserved with one global atomic (in the region of the
+// chunk's lane) and every entry written into its run.
+size_t redraw_draw_smem(const GenArgs& g, const RedrawArgs& a) {
+  const size_t words = (g.hist.global ? static_cast<size_t>(g.hist.n_passes) * g.hist.stride : 0u) +
+                       g.max_delay_len + (kDelayGuide + 1) / 2 + 2u * a.max_super;
+  return words * sizeof(uint32_t);
+}
+
+__global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks) {
+  extern __shared__ uint32_t smem_raw[];
+  const uint32_t hw = hist_words(g);
+  SmemTables tabs{smem_raw + hw, reinterpret_cast<uint16_t*>(smem_raw + hw + g.max_delay_len)};
+  uint32_t* cnt = smem_raw + hw + g.max_delay_len + (kDelayGuide + 1) / 2;  // entries per super-bucket
+  uint32_t* base = cnt + a.max_super;                                        // reserved start of each run
+  const BlockHist bh = block_hist_begin(g, smem_raw);
+  __syncthreads();
+  constexpr int kWin = kChunk / (128 * (kGenThreads / 32));  // windows per warp and chunk
+  constexpr int kHalf = kWin / 2;                             // windows per partition round
+  constexpr int kPer = 4 * kHalf;                             // slots per thread and round
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  int cur = -1;
   for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
-    const RedrawProj& r = a.rp[chunk_owner(a, c)];
+    const int lo = chunk_owner(a, c);
+    const RedrawProj& r = a.rp[lo];
     const DevProj& P = a.projs[r.proj];
+    if (lo != cur) {
+      __syncthreads();
+      load_delay_table(P, g.thr_blob, g.guide_blob, tabs);
+      __syncthreads();
+      cur = lo;
+    }
     const bool part = !P.multapses;  // uniform over the block
     const uint32_t n_sup = part ? (1u << r.super_bits) : 0u;
     const int fine_shift = r.bucket_bits - r.super_bits;
-    for (uint32_t s = threadIdx.x; s < n_sup; s += blockDim.x) cnt[s] = 0;
-    __syncthreads();
-    const uint64_t start = (c - r.chunk_base) * kChunk;
+    const uint64_t lc = c - r.chunk_base;
+    const uint32_t cl = static_cast<uint32_t>(lc % kSuperLanes);  // the chunk's lane
+    const uint64_t start = lc * kChunk;
     const uint64_t end = min(start + kChunk, P.count);
-    uint64_t ent[kPer];
-    uint32_t rs[kPer];  // (super-bucket << 16) | rank in the chunk's run, ~0 = none
+    for (int h = 0; h < kWin / kHalf; ++h) {
+      for (uint32_t s = threadIdx.x; s < n_sup; s += blockDim.x) cnt[s] = 0;
+      __syncthreads();
+      uint64_t ent[kPer];
+      uint32_t rs[kPer];  // (super-bucket << 16) | rank in the run, ~0 = none
 #pragma unroll
-    for (int win = 0; win < kWin; ++win) {
-      const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
-                             static_cast<uint64_t>(win) * 128;
-      Words X{0, 0, 0, 0};
-      if (wbase < end) X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
+      for (int w2 = 0; w2 < kHalf; ++w2) {
+        const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
+                               static_cast<uint64_t>(h * kHalf + w2) * 128;
+        Words X{0, 0, 0, 0};
+        if (wbase < end) X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = win * 4 + q;
-        const uint32_t tw = window_target_word(X, q, lane);
-        const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
-        rs[k] = ~0u;
-        ent[k] = 0;
-        if (i >= end) continue;
-        const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-        const uint32_t s = P.s0 + rand_below(W.y, P.ns);
-        const uint32_t t = P.t0 + rand_below(tw, P.nt);
-        if (!allowed_pair(P, s, t)) {
-          push_pending(a, r.slot_base + i);
-        } else if (part) {
-          const uint64_t pair = local_pair(r, P, s, t);
-          const uint64_t fine = r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull;
-          const uint32_t sb = static_cast<uint32_t>(fine >> fine_shift);
-          ent[k] = (pair << (r.slot_bits + 1)) | i;
-          rs[k] = (sb << 16) | atomicAdd(cnt + sb, 1u);
+        for (int q = 0; q < 4; ++q) {
+          const int k = w2 * 4 + q;
+          const uint32_t tw = window_target_word(X, q, lane);
+          const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
+          rs[k] = ~0u;
+          ent[k] = 0;
+          if (i >= end) continue;
+          const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
+          const uint32_t s = P.s0 + rand_below(W.y, P.ns);
+          const uint32_t t = P.t0 + rand_below(tw, P.nt);
+          store(g, bh, P.out_off + i, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base,
+                weight_bits(P, W.z, W.w));
+          if (!allowed_pair(P, s, t)) {
+            push_pending(a, r.slot_base + i);
+          } else if (part) {
+            const uint64_t pair = local_pair(r, P, s, t);
+            const uint64_t fine = r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull;
+            const uint32_t sb = static_cast<uint32_t>(fine >> fine_shift);
+            ent[k] = (pair << (r.slot_bits + 1)) | i;
+            rs[k] = (sb << 16) | atomicAdd(cnt + sb, 1u);
+          }
         }
       }
-    }
-    __syncthreads();
-    for (uint32_t s = threadIdx.x; s < n_sup; s += blockDim.x) {
-      const uint32_t n = cnt[s];
-      base[s] = n ? atomicAdd(a.sfill + r.super_base + s, n) : 0u;
-    }
-    __syncthreads();
+      __syncthreads();
+      for (uint32_t s = threadIdx.x; s < n_sup; s += blockDim.x) {
+        const uint32_t n = cnt[s];
+        const uint64_t fi = ((r.super_base + s) * kSuperLanes + cl) * kFillStride;
+        base[s] = n ? atomicAdd(a.sfill + fi, n) : 0u;
+      }
+      __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      if (rs[k] == ~0u) continue;
-      const uint32_t sb = rs[k] >> 16;
-      const uint64_t pos = static_cast<uint64_t>(base[sb]) + (rs[k] & 0xFFFFu);
-      if (pos < r.super_cap) a.sup[r.super_off + sb * r.super_cap + pos] = ent[k];
-      else atomicOr(a.err, kErrBounds);
+      for (int k = 0; k < kPer; ++k) {
+        if (rs[k] == ~0u) continue;
+        const uint32_t sb = rs[k] >> 16;
+        const uint64_t pos = static_cast<uint64_t>(base[sb]) + (rs[k] & 0xFFFFu);
+        if (pos < r.super_cap)
+          a.sup[r.super_off + (static_cast<uint64_t>(sb) * kSuperLanes + cl) * r.super_cap + pos] = ent[k];
+        else
+          atomicOr(a.err, kErrBounds);
+      }
+      __syncthreads();  // the counters are reused
     }
-    __syncthreads();  // the counters are reused by the next chunk
+  }
+  block_hist_end(g, bh);
+}
+
+// Rewrites the connection of every slot that redrew: its final pair (source
+// in the key, target in the value) with the delay and weight it already has;
+// the digit counts of the sort follow the key.
+__global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a) {
+  const HistRegs hr = hist_regs(g.hist);
+  const uint64_t words = (a.n_slots + 31) / 32;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  const uint64_t dmask = (1ull << g.layout.delay_bits) - 1;
+  for (uint64_t w = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; w < words; w += stride) {
+    uint32_t m = a.moved[w];
+    while (m) {
+      const uint64_t gs = w * 32 + static_cast<uint64_t>(__ffs(m) - 1);
+      m &= m - 1;
+      const SlotRef x = slot_ref(a, gs);
+      const DevProj& P = *x.P;
+      const uint64_t pos = P.out_off + x.i;
+      if (!SNC_IN_BOUNDS(a.err, 2u, pos, g.cap)) continue;
+      const uint64_t pair = a.pairs[gs];
+      const uint32_t s = static_cast<uint32_t>(pair >> 32), t = static_cast<uint32_t>(pair);
+      const uint64_t old = g.key32 ? static_cast<uint64_t>(static_cast<uint32_t*>(g.keys)[pos])
+                                   : static_cast<uint64_t*>(g.keys)[pos];
+      const uint64_t key = pack_key(s - P.t_base, static_cast<uint32_t>(old & dmask), g.layout.delay_bits);
+      if (g.key32) static_cast<uint32_t*>(g.keys)[pos] = static_cast<uint32_t>(key);
+      else static_cast<uint64_t*>(g.keys)[pos] = key;
+      g.vals[pos] = pack_value(t - P.t_base, static_cast<uint32_t>(g.vals[pos]));
+#pragma unroll
+      for (int p = 0; p < kMaxPasses; ++p) {
+        if (p >= hr.n) break;
+        const uint32_t d0 = static_cast<uint32_t>(old >> hr.shift[p]) & hr.mask[p];
+        const uint32_t d1 = static_cast<uint32_t>(key >> hr.shift[p]) & hr.mask[p];
+        if (d0 == d1) continue;
+        atomicAdd(g.hist.global + static_cast<size_t>(p) * kMaxRadix + d0, ~0ull);  // minus one
+        atomicAdd(g.hist.global + static_cast<size_t>(p) * kMaxRadix + d1, 1ull);
+      }
+    }
   }
 }
 
@@ -774,17 +849,18 @@ __global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(Redr
     }
     const RedrawProj& r = a.rp[lo];
     const uint64_t lu = u - r.split_base;
-    const uint64_t s = lu / r.split_per_super;
-    const uint64_t part = lu - s * r.split_per_super;
-    const uint64_t gs = r.super_base + s;
+    const uint64_t rr = lu / r.split_per_super;  // region (s, lane) = s * kSuperLanes + lane
+    const uint64_t part = lu - rr * r.split_per_super;
+    const uint64_t s = rr / kSuperLanes;
     const int fine_shift = r.bucket_bits - r.super_bits;
     const uint32_t n_fine = 1u << fine_shift;
     const int sh = r.slot_bits + 1;
-    const uint64_t fill = a.sfill[gs] < r.super_cap ? a.sfill[gs] : r.super_cap;
+    const uint64_t rf = a.sfill[(r.super_base * kSuperLanes + rr) * kFillStride];
+    const uint64_t fill = rf < r.super_cap ? rf : r.super_cap;
     const uint64_t i0 = part * kSplitUnit;
     if (i0 >= fill) continue;  // uniform over the block
     const uint32_t n = static_cast<uint32_t>(fill - i0 < kSplitUnit ? fill - i0 : kSplitUnit);
-    const uint64_t* src = a.sup + r.super_off + s * r.super_cap + i0;
+    const uint64_t* src = a.sup + r.super_off + rr * r.super_cap + i0;
     const uint64_t first = r.bucket_base + (s << fine_shift);  // first bucket of this super-bucket
     for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) fcnt[f] = 0;
     uint64_t e[kPer];
@@ -827,23 +903,28 @@ __global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(Redr
 // smallest entry (the lowest slot) stays; every other claimant joins the
 // pending list.  The entries left in the table are written back as the
 // bucket's accepted pairs.
-__global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
+__global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
   __shared__ unsigned long long tab[kBucketTable];
   __shared__ uint32_t kept;
   constexpr int kPer = kBucketCap / 256;
-  for (uint64_t b = blockIdx.x; b < a.n_buckets; b += gridDim.x) {
-    const RedrawProj& r = a.rp[bucket_owner(a, b)];
-    const int sh = r.slot_bits + 1;
-    const uint64_t slot_mask = (1ull << r.slot_bits) - 1;
-    const uint32_t n = a.fill[b] < a.cap ? a.fill[b] : a.cap;
-    uint64_t* ent = a.ent + b * a.cap;
-    // Entries are below 2^63, never kEmpty.
-    uint64_t mine[kPer];
+  // Entries are below 2^63, never kEmpty.  The next bucket's entries are
+  // loaded while this one's are looked up.
+  uint64_t b = blockIdx.x;
+  uint64_t mine[kPer];
+  {
+    const uint32_t n = b < a.n_buckets ? min(a.fill[b], a.cap) : 0u;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint32_t i = threadIdx.x + static_cast<uint32_t>(k) * 256u;
-      mine[k] = i < n ? ent[i] : kEmpty;
+      mine[k] = i < n ? a.ent[b * a.cap + i] : kEmpty;
     }
+  }
+  while (b < a.n_buckets) {
+    const uint64_t b2 = b + gridDim.x;
+    const uint32_t n2 = b2 < a.n_buckets ? min(a.fill[b2], a.cap) : 0u;
+    const RedrawProj& r = a.rp[bucket_owner(a, b)];
+    const int sh = r.slot_bits + 1;
+    const uint64_t slot_mask = (1ull << r.slot_bits) - 1;
     for (uint32_t i = threadIdx.x; i < kBucketTable; i += blockDim.x) tab[i] = kEmpty;
     if (threadIdx.x == 0) kept = 0;
     __syncthreads();
@@ -854,6 +935,13 @@ __global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
       if (prev != kEmpty) push_pending(a, r.slot_base + ((prev < mine[k] ? mine[k] : prev) & slot_mask));
     }
     __syncthreads();
+    uint64_t nxt[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint32_t i = threadIdx.x + static_cast<uint32_t>(k) * 256u;
+      nxt[k] = i < n2 ? a.ent[b2 * a.cap + i] : kEmpty;
+    }
+    uint64_t* ent = a.ent + b * a.cap;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       if (mine[k] == kEmpty) continue;
@@ -861,7 +949,9 @@ __global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) a.fill[b] = kept;
-    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) mine[k] = nxt[k];
+    b = b2;
   }
 }
 
@@ -871,13 +961,14 @@ __global__ void __launch_bounds__(256) redraw_bucket0_kernel(RedrawArgs a) {
 // (smaller, claim bit clear) entry there.  A claim wins if its entry is the
 // one left for its pair: winners join the accepted pairs, the others wait
 // for the next round.
-__global__ void __launch_bounds__(256) redraw_bucket_round_kernel(RedrawArgs a) {
+__global__ void __launch_bounds__(256, 4) redraw_bucket_round_kernel(RedrawArgs a) {
   __shared__ unsigned long long tab[kBucketTable];
   __shared__ uint32_t won;
   constexpr int kPer = kBucketCap / 256;
-  for (uint64_t b = blockIdx.x; b < a.n_buckets; b += gridDim.x) {
+  const uint64_t n_list = *a.n_touched < a.n_buckets ? *a.n_touched : a.n_buckets;
+  for (uint64_t q = blockIdx.x; q < n_list; q += gridDim.x) {
+    const uint64_t b = a.touched[q];
     const uint32_t pc = a.pcount[b];
-    if (pc == 0) continue;  // uniform over the block
     const RedrawProj& r = a.rp[bucket_owner(a, b)];
     const int sh = r.slot_bits + 1;
     const uint64_t claim_bit = 1ull << r.slot_bits;
@@ -955,12 +1046,10 @@ __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uin
   }
 }
 
-// Writes the redraw projections' connections: the final pairs with the
-// round-0 weight and delay of each slot.  Blocks take chunks of kChunk slots
-// of one projection (delay table reloaded when the projection changes);
-// warps take windows of 128 slots, as in the draw kernel.  With bucketed
-// claims a slot that never redrew has its round-0 pair drawn again here;
-// otherwise every pair comes from `pairs`.
+// Writes the redraw projections' connections (global pair tables): the final
+// pairs with the round-0 weight and delay of each slot.  Blocks take chunks
+// of kChunk slots of one projection (delay table reloaded when the
+// projection changes).
 __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks) {
   extern __shared__ uint32_t smem_raw[];
   const uint32_t hw = hist_words(g);
@@ -985,25 +1074,14 @@ __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, Redr
       const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
                              static_cast<uint64_t>(win) * 128;
       if (wbase >= end) break;
-      Words X{0, 0, 0, 0};
-      if (a.moved) X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const uint32_t tw = a.moved ? window_target_word(X, q, lane) : 0u;
         const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
         if (i >= end) continue;
-        const uint64_t gs = r.slot_base + i;
+        const uint64_t pair = a.pairs[r.slot_base + i];
         const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-        uint32_t s, t;
-        if (!a.moved || ((a.moved[gs >> 5] >> (gs & 31u)) & 1u)) {
-          const uint64_t pair = a.pairs[gs];
-          s = static_cast<uint32_t>(pair >> 32);
-          t = static_cast<uint32_t>(pair);
-        } else {
-          s = P.s0 + rand_below(W.y, P.ns);
-          t = P.t0 + rand_below(tw, P.nt);
-        }
-        store(g, bh, P.out_off + i, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+        store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32) - P.t_base, delay_step(P, tabs, W.x),
+              static_cast<uint32_t>(pair) - P.t_base, weight_bits(P, W.z, W.w));
       }
     }
   }

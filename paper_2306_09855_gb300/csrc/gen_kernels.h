@@ -77,14 +77,17 @@ struct RedrawProj {
   uint64_t n_buckets;
   int bucket_bits;
   // Round-0 entries first go to 2^super_bits super-buckets (the top bits of
-  // the bucket index; at most kSplitFanout buckets each), region s holding
-  // sup[super_off + s * super_cap, ... + sfill[super_base + s]).
+  // the bucket index; at most 2^kSplitBits buckets each).  Super-bucket s
+  // has kSuperLanes regions, one per residue of the emit chunk index:
+  // region (s, l) holds sup[super_off + (s * kSuperLanes + l) * super_cap,
+  // ...), its fill counter sfill[((super_base + s) * kSuperLanes + l) *
+  // kFillStride].
   int super_bits;
   uint64_t super_base;
   uint64_t super_cap;
   uint64_t super_off;
-  // Split units (kSplitUnit entries of one super-bucket): split_per_super
-  // per super-bucket, the projection's first unit split_base.
+  // Split units (kSplitUnit entries of one region): split_per_super per
+  // region, the projection's first unit split_base.
   uint64_t split_base;
   uint64_t split_per_super;
 };
@@ -119,12 +122,17 @@ struct RedrawArgs {
   uint64_t n_super;
   uint32_t max_super;  // largest 2^super_bits of the build
   uint64_t n_split_units;
+  // Buckets holding claims of the current round (each listed once).
+  uint64_t* touched;
+  unsigned long long* n_touched;
 };
 constexpr uint32_t kBucketCap = 2048;    // entries per bucket (accepted + one round's claims)
 constexpr uint32_t kBucketTable = 4096;  // shared-memory hash table of a bucket
 constexpr uint32_t kBucketMean = 1024;   // target mean of round-0 entries per bucket
 constexpr int kSplitBits = 9;            // buckets per super-bucket: 2^kSplitBits at most
 constexpr int kMaxSuperBits = 12;        // super-buckets per projection: 2^12 at most
+constexpr int kSuperLanes = 8;           // regions per super-bucket
+constexpr int kFillStride = 8;           // region fill counters 32 bytes apart
 constexpr int kSplitThreads = 512;       // split kernel block
 constexpr uint32_t kSplitUnit = 8192;    // entries per split block and unit
 __global__ void redraw_round0_kernel(RedrawArgs a);
@@ -133,8 +141,13 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
 __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending);
 // Bucketed claims: round 0 keeps the lowest slot of every pair in each
 // bucket; later rounds settle each bucket's claims against its accepted pairs.
-// dynamic shared memory: 2 * max_super * 4 bytes
-__global__ void redraw_bucket_draw_kernel(RedrawArgs a, uint64_t total_chunks);
+// Round 0 with buckets: writes every slot's round-0 connection and sends
+// its pair to its super-bucket.  Dynamic shared memory: histogram, delay
+// table, guide, then 2 * max_super counters.
+__global__ void redraw_draw_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks);
+size_t redraw_draw_smem(const GenArgs& g, const RedrawArgs& a);
+// Rewrites the connections of the slots that redrew (RedrawArgs::moved).
+__global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a);
 __global__ void redraw_bucket_split_kernel(RedrawArgs a);
 __global__ void redraw_bucket0_kernel(RedrawArgs a);
 __global__ void redraw_bucket_round_kernel(RedrawArgs a);

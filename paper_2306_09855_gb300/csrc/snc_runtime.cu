@@ -983,17 +983,21 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         r.bucket_bits = bits;
         r.n_buckets = 1ull << bits;
         n_buckets += r.n_buckets;
-        // Super-buckets of up to 2^kSplitBits buckets; each region holds its
-        // mean share plus 16 standard deviations of the binomial count.
+        // Super-buckets of up to 2^kSplitBits buckets, kSuperLanes regions
+        // each (one per residue of the chunk index).  A region holds the mean
+        // share of its lane's slots plus 16 standard deviations of the
+        // binomial count.
         r.super_bits = bits > kSplitBits ? bits - kSplitBits : 0;
         const uint64_t n_sup = 1ull << r.super_bits;
-        const double mean = static_cast<double>(N) / static_cast<double>(n_sup);
-        r.super_cap = std::min<uint64_t>(N, static_cast<uint64_t>(mean + 16.0 * std::sqrt(mean)) + 64);
+        const uint64_t chunks = (N + kChunk - 1) / kChunk;
+        const uint64_t lane_slots = std::min<uint64_t>(N, (chunks + kSuperLanes - 1) / kSuperLanes * kChunk);
+        const double mean = static_cast<double>(lane_slots) / static_cast<double>(n_sup);
+        r.super_cap = std::min<uint64_t>(lane_slots, static_cast<uint64_t>(mean + 16.0 * std::sqrt(mean)) + 64);
         r.split_base = n_split_units;
         r.split_per_super = std::max<uint64_t>(1, (r.super_cap + kSplitUnit - 1) / kSplitUnit);
-        n_split_units += n_sup * r.split_per_super;
+        n_split_units += n_sup * kSuperLanes * r.split_per_super;
         n_super += n_sup;
-        sup_entries += n_sup * r.super_cap;
+        sup_entries += n_sup * kSuperLanes * r.super_cap;
         max_super = std::max<uint32_t>(max_super, static_cast<uint32_t>(n_sup));
       }
     }
@@ -1008,7 +1012,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       a.lost = bucketed ? nullptr : static_cast<uint8_t*>(dev_alloc(c, n_slots));
       uint64_t* pend_a = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
       uint64_t* pend_b = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
-      a.n_next = static_cast<unsigned long long*>(dev_alloc(c, sizeof(unsigned long long)));
+      a.n_next = static_cast<unsigned long long*>(dev_alloc(c, 2 * sizeof(unsigned long long)));
+      a.n_touched = a.n_next + 1;
       if (!d_rp || !a.pairs || (!bucketed && !a.lost) || !pend_a || !pend_b || !a.n_next)
         return fail(c, SNC_ERR_OOM, "device allocation failed (redraw lists)");
       if (n_table > 0) {
@@ -1033,10 +1038,13 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         a.n_super = n_super;
         a.max_super = max_super;
         a.n_split_units = n_split_units;
+        const uint64_t sfill_words = n_super * kSuperLanes * kFillStride;
         a.sup = static_cast<uint64_t*>(dev_alloc(c, sup_entries * sizeof(uint64_t)));
-        a.sfill = static_cast<uint32_t*>(dev_alloc(c, n_super * sizeof(uint32_t)));
-        if (!a.sup || !a.sfill) return fail(c, SNC_ERR_OOM, "device allocation failed (claim super-buckets)");
-        SNC_CUDA(c, cudaMemsetAsync(a.sfill, 0, n_super * sizeof(uint32_t), st));
+        a.sfill = static_cast<uint32_t*>(dev_alloc(c, sfill_words * sizeof(uint32_t)));
+        a.touched = static_cast<uint64_t*>(dev_alloc(c, n_buckets * sizeof(uint64_t)));
+        if (!a.sup || !a.sfill || !a.touched)
+          return fail(c, SNC_ERR_OOM, "device allocation failed (claim super-buckets)");
+        SNC_CUDA(c, cudaMemsetAsync(a.sfill, 0, sfill_words * sizeof(uint32_t), st));
       } else if (bucketed) {
         a.bucketed = 1;  // autapse redraws only: no pair tables
       }
@@ -1049,7 +1057,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       a.rp = d_rp;
       SNC_CUDA(c, upload(c, d_rp, rps.data(), rps.size() * sizeof(RedrawProj)));
       if (a.lost) SNC_CUDA(c, cudaMemsetAsync(a.lost, 0, n_slots, st));
-      SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
+      SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, 2 * sizeof(unsigned long long), st));
       a.next_pending = pend_a;
       const auto grid_for = [&](uint64_t items) {
         return static_cast<unsigned>(
@@ -1057,10 +1065,17 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       };
       const unsigned bucket_grid = static_cast<unsigned>(
           std::max<uint64_t>(1, std::min<uint64_t>(n_buckets, static_cast<uint64_t>(c->sms) * 6)));
+      GenArgs ge = g;
+      ge.max_delay_len = max_len;
+      const unsigned eg = static_cast<unsigned>(
+          std::min<uint64_t>(n_chunks_r, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm));
       if (a.bucketed) {
-        const unsigned dg = static_cast<unsigned>(
-            std::min<uint64_t>(n_chunks_r, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm));
-        redraw_bucket_draw_kernel<<<dg, kGenThreads, 2 * a.max_super * sizeof(uint32_t), st>>>(a, n_chunks_r);
+        // Round 0 writes every slot's connection; the slots that redraw are
+        // rewritten after the last round.
+        const size_t dsm = redraw_draw_smem(ge, a);
+        SNC_CUDA(c, cudaFuncSetAttribute(redraw_draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(dsm)));
+        redraw_draw_kernel<<<eg, kGenThreads, dsm, st>>>(ge, a, n_chunks_r);
       } else {
         redraw_round0_kernel<<<grid_for(n_slots), 256, 0, st>>>(a);
       }
@@ -1090,10 +1105,13 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         if (round > 0xFFFFFFu) return fail(c, SNC_ERR_TIMEOUT, "fixed_total_number: redraw rounds exhausted");
         if (n_pend > n_slots) return fail(c, SNC_ERR_CUDA, "fixed_total_number: pending list overflow (internal error)");
         a.next_pending = next;
-        SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
+        SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, 2 * sizeof(unsigned long long), st));
         redraw_claim_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend, round);
         if (a.bucketed) {
-          if (n_buckets > 0) redraw_bucket_round_kernel<<<bucket_grid, 256, 0, st>>>(a);
+          // Touched buckets are at most the claims of the round.
+          const unsigned rg = static_cast<unsigned>(
+              std::max<uint64_t>(1, std::min<uint64_t>(n_pend, static_cast<uint64_t>(c->sms) * 6)));
+          if (n_buckets > 0) redraw_bucket_round_kernel<<<rg, 256, 0, st>>>(a);
         } else {
           redraw_resolve_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend);
         }
@@ -1101,16 +1119,17 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         SNC_CUDA(c, cudaGetLastError());
         std::swap(pending, next);
       }
-      GenArgs ge = g;
-      ge.max_delay_len = max_len;
-      const size_t tsm =
-          hist_bytes + static_cast<size_t>(max_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
-      // Set on every launch: the attribute is per function and device, and
-      // builds may run on several threads and devices.
-      SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-      const unsigned eg = static_cast<unsigned>(
-          std::min<uint64_t>(n_chunks_r, static_cast<uint64_t>(c->sms) * g_gen_blocks_per_sm));
-      total_emit_kernel<<<eg, kGenThreads, tsm, st>>>(ge, a, n_chunks_r);
+      if (a.bucketed) {
+        const uint64_t words = (n_slots + 31) / 32;
+        redraw_patch_kernel<<<grid_for(words), 256, 0, st>>>(ge, a);
+      } else {
+        const size_t tsm =
+            hist_bytes + static_cast<size_t>(max_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
+        // Set on every launch: the attribute is per function and device, and
+        // builds may run on several threads and devices.
+        SNC_CUDA(c, cudaFuncSetAttribute(total_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        total_emit_kernel<<<eg, kGenThreads, tsm, st>>>(ge, a, n_chunks_r);
+      }
       ++c->stats.kernel_launches;
       SNC_CUDA(c, cudaGetLastError());
       dev_free(c, d_rp);
@@ -1126,6 +1145,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       dev_free(c, a.moved);
       dev_free(c, a.sup);
       dev_free(c, a.sfill);
+      dev_free(c, a.touched);
     }
   }
   mark();
