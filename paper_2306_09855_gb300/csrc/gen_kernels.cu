@@ -834,13 +834,25 @@ __device__ __forceinline__ uint64_t table_put(unsigned long long* tab, uint32_t 
 }
 
 // Spreads the super-buckets over their buckets.  A block takes a unit of
-// kSplitUnit entries of one super-bucket, counts them per bucket in shared
-// memory, reserves each bucket's run with one global atomic and writes the
-// entries into their runs.
+// kSplitUnit entries of one region, counts them per bucket in shared
+// memory, stages them in bucket order, reserves each bucket's run with one
+// global atomic and writes every run with consecutive threads.
+size_t redraw_split_smem() {
+  return static_cast<size_t>(kSplitUnit) * (sizeof(uint64_t) + sizeof(uint16_t)) +
+         3u * (1u << kSplitBits) * sizeof(uint32_t) + 32 * sizeof(uint32_t);
+}
+
 __global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(RedrawArgs a) {
-  __shared__ uint32_t fcnt[1u << kSplitBits];
-  __shared__ uint32_t fbase[1u << kSplitBits];
+  extern __shared__ uint64_t split_smem[];
+  uint64_t* stage = split_smem;                                          // entries in bucket order
+  uint16_t* stage_f = reinterpret_cast<uint16_t*>(stage + kSplitUnit);  // their buckets
+  uint32_t* fcnt = reinterpret_cast<uint32_t*>(stage_f + kSplitUnit);
+  uint32_t* fbase = fcnt + (1u << kSplitBits);   // reserved start of each run
+  uint32_t* lstart = fbase + (1u << kSplitBits);  // start of each run in the stage
+  uint32_t* wsum = lstart + (1u << kSplitBits);   // warp totals of the scan
   constexpr int kPer = kSplitUnit / kSplitThreads;
+  static_assert((1u << kSplitBits) == kSplitThreads, "one bucket per thread in the scan");
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   for (uint64_t u = blockIdx.x; u < a.n_split_units; u += gridDim.x) {
     int lo = 0, hi = a.n - 1;
     while (lo < hi) {
@@ -862,7 +874,7 @@ __global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(Redr
     const uint32_t n = static_cast<uint32_t>(fill - i0 < kSplitUnit ? fill - i0 : kSplitUnit);
     const uint64_t* src = a.sup + r.super_off + rr * r.super_cap + i0;
     const uint64_t first = r.bucket_base + (s << fine_shift);  // first bucket of this super-bucket
-    for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) fcnt[f] = 0;
+    fcnt[threadIdx.x] = 0;
     uint64_t e[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
@@ -881,17 +893,44 @@ __global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(Redr
       fr[k] = (f << 16) | atomicAdd(fcnt + f, 1u);
     }
     __syncthreads();
-    for (uint32_t f = threadIdx.x; f < n_fine; f += blockDim.x) {
-      const uint32_t c = fcnt[f];
-      fbase[f] = c ? atomicAdd(a.fill + first + f, c) : 0u;
+    // Exclusive scan of the counts (bucket = thread) and the reservations.
+    const uint32_t c = fcnt[threadIdx.x];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= static_cast<uint32_t>(o)) x += y;
     }
+    if (lane == 31) wsum[warp] = x;
+    if (threadIdx.x < n_fine) fbase[threadIdx.x] = c ? atomicAdd(a.fill + first + threadIdx.x, c) : 0u;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = lane < kSplitThreads / 32 ? wsum[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= static_cast<uint32_t>(o)) w += y;
+      }
+      if (lane < kSplitThreads / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    lstart[threadIdx.x] = x - c + (warp ? wsum[warp - 1] : 0u);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       if (fr[k] == ~0u) continue;
       const uint32_t f = fr[k] >> 16;
-      const uint32_t pos = fbase[f] + (fr[k] & 0xFFFFu);
-      if (pos < a.cap) a.ent[(first + f) * a.cap + pos] = e[k];
+      const uint32_t at = lstart[f] + (fr[k] & 0xFFFFu);
+      if (at < kSplitUnit) {
+        stage[at] = e[k];
+        stage_f[at] = static_cast<uint16_t>(f);
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += kSplitThreads) {
+      const uint32_t f = stage_f[i];
+      const uint32_t pos = fbase[f] + (i - lstart[f]);
+      if (pos < a.cap) a.ent[(first + f) * a.cap + pos] = stage[i];
       else atomicOr(a.err, kErrBounds);
     }
     __syncthreads();
@@ -904,7 +943,7 @@ __global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(Redr
 // pending list.  The entries left in the table are written back as the
 // bucket's accepted pairs.
 __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
-  __shared__ unsigned long long tab[kBucketTable];
+  __shared__ __align__(16) unsigned long long tab[kBucketTable];
   __shared__ uint32_t kept;
   constexpr int kPer = kBucketCap / 256;
   // Entries are below 2^63, never kEmpty.  The next bucket's entries are
@@ -925,7 +964,8 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
     const RedrawProj& r = a.rp[bucket_owner(a, b)];
     const int sh = r.slot_bits + 1;
     const uint64_t slot_mask = (1ull << r.slot_bits) - 1;
-    for (uint32_t i = threadIdx.x; i < kBucketTable; i += blockDim.x) tab[i] = kEmpty;
+    for (uint32_t i = threadIdx.x; i < kBucketTable / 2; i += blockDim.x)
+      reinterpret_cast<ulonglong2*>(tab)[i] = make_ulonglong2(kEmpty, kEmpty);
     if (threadIdx.x == 0) kept = 0;
     __syncthreads();
 #pragma unroll
@@ -962,7 +1002,7 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
 // one left for its pair: winners join the accepted pairs, the others wait
 // for the next round.
 __global__ void __launch_bounds__(256, 4) redraw_bucket_round_kernel(RedrawArgs a) {
-  __shared__ unsigned long long tab[kBucketTable];
+  __shared__ __align__(16) unsigned long long tab[kBucketTable];
   __shared__ uint32_t won;
   constexpr int kPer = kBucketCap / 256;
   const uint64_t n_list = *a.n_touched < a.n_buckets ? *a.n_touched : a.n_buckets;
@@ -979,7 +1019,8 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket_round_kernel(RedrawArgs 
     uint32_t words = 64;
     while (words < 2 * (n - acc) && words < kBucketTable) words <<= 1;
     const uint32_t mask = words - 1;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) tab[i] = kEmpty;
+    for (uint32_t i = threadIdx.x; i < words / 2; i += blockDim.x)
+      reinterpret_cast<ulonglong2*>(tab)[i] = make_ulonglong2(kEmpty, kEmpty);
     if (threadIdx.x == 0) won = 0;
     uint64_t mine[kPer];  // this thread's claims
 #pragma unroll

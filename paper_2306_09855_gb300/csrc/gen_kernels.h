@@ -148,7 +148,8 @@ __global__ void redraw_draw_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunk
 size_t redraw_draw_smem(const GenArgs& g, const RedrawArgs& a);
 // Rewrites the connections of the slots that redrew (RedrawArgs::moved).
 __global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a);
-__global__ void redraw_bucket_split_kernel(RedrawArgs a);
+__global__ void redraw_bucket_split_kernel(RedrawArgs a);  // dynamic shared memory: redraw_split_smem()
+size_t redraw_split_smem();
 __global__ void redraw_bucket0_kernel(RedrawArgs a);
 __global__ void redraw_bucket_round_kernel(RedrawArgs a);
 __global__ void total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks);

@@ -1084,8 +1084,11 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         // Round-0 losers go straight to the pending list.
         if (n_buckets > 0) {
           const unsigned split_grid = static_cast<unsigned>(
-              std::max<uint64_t>(1, std::min<uint64_t>(n_split_units, static_cast<uint64_t>(c->sms) * 4)));
-          redraw_bucket_split_kernel<<<split_grid, kSplitThreads, 0, st>>>(a);
+              std::max<uint64_t>(1, std::min<uint64_t>(n_split_units, static_cast<uint64_t>(c->sms) * 2)));
+          const size_t ssm = redraw_split_smem();
+          SNC_CUDA(c, cudaFuncSetAttribute(redraw_bucket_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(ssm)));
+          redraw_bucket_split_kernel<<<split_grid, kSplitThreads, ssm, st>>>(a);
           redraw_bucket0_kernel<<<bucket_grid, 256, 0, st>>>(a);
           c->stats.kernel_launches += 2;
         }
