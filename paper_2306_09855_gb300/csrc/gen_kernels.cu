@@ -674,10 +674,14 @@ __device__ __forceinline__ int chunk_owner(const RedrawArgs& a, uint64_t c) {
 // chunk (2048 slots) are counted per super-bucket in shared memory, each
 // super-bucket's run reserved with one global atomic (in the region of the
 // chunk's lane) and every entry written into its run.
+namespace {
+constexpr int kDrawStage = kChunk / 2;  // entries of one partition round
+}
+
 size_t redraw_draw_smem(const GenArgs& g, const RedrawArgs& a) {
   const size_t words = (g.hist.global ? static_cast<size_t>(g.hist.n_passes) * g.hist.stride : 0u) +
-                       g.max_delay_len + (kDelayGuide + 1) / 2 + 2u * a.max_super;
-  return words * sizeof(uint32_t);
+                       g.max_delay_len + (kDelayGuide + 1) / 2 + 3u * a.max_super + 8u;
+  return (words + 1) / 2 * sizeof(uint64_t) + kDrawStage * (sizeof(uint64_t) + sizeof(uint16_t));
 }
 
 __global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks) {
@@ -686,6 +690,11 @@ __global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, Red
   SmemTables tabs{smem_raw + hw, reinterpret_cast<uint16_t*>(smem_raw + hw + g.max_delay_len)};
   uint32_t* cnt = smem_raw + hw + g.max_delay_len + (kDelayGuide + 1) / 2;  // entries per super-bucket
   uint32_t* base = cnt + a.max_super;                                        // reserved start of each run
+  uint32_t* lstart = base + a.max_super;                                     // start of each run in the stage
+  uint32_t* wsum = lstart + a.max_super;                                     // warp totals of the scan
+  const size_t words = hw + g.max_delay_len + (kDelayGuide + 1) / 2 + 3u * a.max_super + 8u;
+  uint64_t* stage = reinterpret_cast<uint64_t*>(smem_raw) + (words + 1) / 2;  // entries in super-bucket order
+  uint16_t* stage_s = reinterpret_cast<uint16_t*>(stage + kDrawStage);     // their super-buckets
   const BlockHist bh = block_hist_begin(g, smem_raw);
   __syncthreads();
   constexpr int kWin = kChunk / (128 * (kGenThreads / 32));  // windows per warp and chunk
@@ -746,23 +755,65 @@ __global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, Red
         }
       }
       __syncthreads();
+      if (!part) continue;  // uniform over the block; nothing counted
+      // Reserve each run; scan the counts (contiguous groups of super-buckets
+      // per thread) for the stage.
       for (uint32_t s = threadIdx.x; s < n_sup; s += blockDim.x) {
         const uint32_t n = cnt[s];
         const uint64_t fi = ((r.super_base + s) * kSuperLanes + cl) * kFillStride;
         base[s] = n ? atomicAdd(a.sfill + fi, n) : 0u;
       }
+      const uint32_t per = (n_sup + kGenThreads - 1) / kGenThreads;
+      const uint32_t s0 = threadIdx.x * per;
+      uint32_t sum = 0;
+      for (uint32_t j = 0; j < per; ++j)
+        if (s0 + j < n_sup) sum += cnt[s0 + j];
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t w = lane < kGenThreads / 32 ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+          if (lane >= static_cast<uint32_t>(o)) w += y;
+        }
+        if (lane < kGenThreads / 32) wsum[lane] = w;
+      }
+      __syncthreads();
+      uint32_t run = x - sum + (warp ? wsum[warp - 1] : 0u);
+      for (uint32_t j = 0; j < per; ++j)
+        if (s0 + j < n_sup) {
+          lstart[s0 + j] = run;
+          run += cnt[s0 + j];
+        }
+      const uint32_t total = wsum[kGenThreads / 32 - 1];
       __syncthreads();
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
         if (rs[k] == ~0u) continue;
         const uint32_t sb = rs[k] >> 16;
-        const uint64_t pos = static_cast<uint64_t>(base[sb]) + (rs[k] & 0xFFFFu);
+        const uint32_t at = lstart[sb] + (rs[k] & 0xFFFFu);
+        if (at < kDrawStage) {
+          stage[at] = ent[k];
+          stage_s[at] = static_cast<uint16_t>(sb);
+        }
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < total && i < kDrawStage; i += blockDim.x) {
+        const uint32_t sb = stage_s[i];
+        const uint64_t pos = static_cast<uint64_t>(base[sb]) + (i - lstart[sb]);
         if (pos < r.super_cap)
-          a.sup[r.super_off + (static_cast<uint64_t>(sb) * kSuperLanes + cl) * r.super_cap + pos] = ent[k];
+          a.sup[r.super_off + (static_cast<uint64_t>(sb) * kSuperLanes + cl) * r.super_cap + pos] = stage[i];
         else
           atomicOr(a.err, kErrBounds);
       }
-      __syncthreads();  // the counters are reused
+      __syncthreads();  // the counters and the stage are reused
     }
   }
   block_hist_end(g, bh);
@@ -772,7 +823,10 @@ __global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, Red
 // in the key, target in the value) with the delay and weight it already has;
 // the digit counts of the sort follow the key.
 __global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a) {
+  extern __shared__ uint32_t delta[];  // per pass and digit: changes of the block, mod 2^32
   const HistRegs hr = hist_regs(g.hist);
+  for (int i = threadIdx.x; i < hr.n * hr.stride; i += blockDim.x) delta[i] = 0u;
+  __syncthreads();
   const uint64_t words = (a.n_slots + 31) / 32;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   const uint64_t dmask = (1ull << g.layout.delay_bits) - 1;
@@ -799,10 +853,15 @@ __global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a) {
         const uint32_t d0 = static_cast<uint32_t>(old >> hr.shift[p]) & hr.mask[p];
         const uint32_t d1 = static_cast<uint32_t>(key >> hr.shift[p]) & hr.mask[p];
         if (d0 == d1) continue;
-        atomicAdd(g.hist.global + static_cast<size_t>(p) * kMaxRadix + d0, ~0ull);  // minus one
-        atomicAdd(g.hist.global + static_cast<size_t>(p) * kMaxRadix + d1, 1ull);
+        atomicAdd(delta + p * hr.stride + d0, ~0u);  // minus one
+        atomicAdd(delta + p * hr.stride + d1, 1u);
       }
     }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < hr.n * hr.stride; i += blockDim.x) {
+    const int32_t v = static_cast<int32_t>(delta[i]);
+    if (v) atomicAdd(g.hist.global + (i / hr.stride) * kMaxRadix + (i % hr.stride), static_cast<unsigned long long>(static_cast<int64_t>(v)));
   }
 }
 
@@ -937,6 +996,18 @@ __global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(Redr
   }
 }
 
+// Appends v (where keep) at base[0..) in shared counter *count: each warp
+// takes one contiguous range, so that its lanes write consecutive words.
+__device__ __forceinline__ void warp_append(uint64_t* base, uint32_t* count, bool keep, uint64_t v) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t m = __ballot_sync(0xffffffffu, keep);
+  if (!m) return;
+  uint32_t at = 0;
+  if (lane == static_cast<uint32_t>(__ffs(m) - 1)) at = atomicAdd(count, static_cast<uint32_t>(__popc(m)));
+  at = __shfl_sync(0xffffffffu, at, __ffs(m) - 1);
+  if (keep) base[at + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
 // Round 0 of the bucketed claims, one block per bucket at a time: the
 // bucket's entries go into a shared-memory table where, for every pair, the
 // smallest entry (the lowest slot) stays; every other claimant joins the
@@ -984,8 +1055,9 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
     uint64_t* ent = a.ent + b * a.cap;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-      if (mine[k] == kEmpty) continue;
-      if (tab[table_find(tab, kBucketTable - 1, mine[k] >> sh, sh)] == mine[k]) ent[atomicAdd(&kept, 1u)] = mine[k];
+      const bool keep =
+          mine[k] != kEmpty && tab[table_find(tab, kBucketTable - 1, mine[k] >> sh, sh)] == mine[k];
+      warp_append(ent, &kept, keep, mine[k]);
     }
     __syncthreads();
     if (threadIdx.x == 0) a.fill[b] = kept;
@@ -1059,8 +1131,7 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket_round_kernel(RedrawArgs 
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kPer; ++k)
-      if (win[k]) ent[acc + atomicAdd(&won, 1u)] = mine[k] & ~claim_bit;
+    for (int k = 0; k < kPer; ++k) warp_append(ent + acc, &won, win[k], mine[k] & ~claim_bit);
     __syncthreads();
     if (threadIdx.x == 0) {
       a.fill[b] = acc + won;

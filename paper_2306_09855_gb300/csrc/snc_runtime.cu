@@ -1124,7 +1124,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       }
       if (a.bucketed) {
         const uint64_t words = (n_slots + 31) / 32;
-        redraw_patch_kernel<<<grid_for(words), 256, 0, st>>>(ge, a);
+        const size_t psm = hist_bytes > 0 ? hist_bytes : 16;
+        redraw_patch_kernel<<<grid_for(words), 256, psm, st>>>(ge, a);
       } else {
         const size_t tsm =
             hist_bytes + static_cast<size_t>(max_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
