@@ -866,10 +866,11 @@ __global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a) {
 }
 
 // Finds pair's entry in a shared-memory table of `mask + 1` words (linear
-// probing from the pair's hash); the index of the entry, or of the empty
-// word that ends its probe sequence.
-__device__ __forceinline__ uint32_t table_find(const unsigned long long* tab, uint32_t mask, uint64_t pair, int sh) {
-  uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & mask;
+// probing from `hash`, the low word of the pair's hash); the index of the
+// entry, or of the empty word that ends its probe sequence.
+__device__ __forceinline__ uint32_t table_find(const unsigned long long* tab, uint32_t mask, uint64_t pair, int sh,
+                                               uint32_t hash) {
+  uint32_t h = hash & mask;
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     const uint64_t v = tab[h];
     if (v == kEmpty || (v >> sh) == pair) return h;
@@ -880,9 +881,10 @@ __device__ __forceinline__ uint32_t table_find(const unsigned long long* tab, ui
 
 // Puts e into the table; the entry left for its pair is the smallest.
 // Returns the previous entry of the pair, or kEmpty when it was new.
-__device__ __forceinline__ uint64_t table_put(unsigned long long* tab, uint32_t mask, uint64_t e, int sh) {
+__device__ __forceinline__ uint64_t table_put(unsigned long long* tab, uint32_t mask, uint64_t e, int sh,
+                                              uint32_t hash) {
   const uint64_t pair = e >> sh;
-  uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & mask;
+  uint32_t h = hash & mask;
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     const uint64_t old = atomicCAS(tab + h, kEmpty, e);
     if (old == kEmpty) return kEmpty;
@@ -1039,10 +1041,12 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
       reinterpret_cast<ulonglong2*>(tab)[i] = make_ulonglong2(kEmpty, kEmpty);
     if (threadIdx.x == 0) kept = 0;
     __syncthreads();
+    uint32_t hk[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
+      hk[k] = static_cast<uint32_t>(pair_hash(mine[k] >> sh));
       if (mine[k] == kEmpty) continue;
-      const uint64_t prev = table_put(tab, kBucketTable - 1, mine[k], sh);
+      const uint64_t prev = table_put(tab, kBucketTable - 1, mine[k], sh, hk[k]);
       if (prev != kEmpty) push_pending(a, r.slot_base + ((prev < mine[k] ? mine[k] : prev) & slot_mask));
     }
     __syncthreads();
@@ -1056,7 +1060,7 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const bool keep =
-          mine[k] != kEmpty && tab[table_find(tab, kBucketTable - 1, mine[k] >> sh, sh)] == mine[k];
+          mine[k] != kEmpty && tab[table_find(tab, kBucketTable - 1, mine[k] >> sh, sh, hk[k])] == mine[k];
       warp_append(ent, &kept, keep, mine[k]);
     }
     __syncthreads();
@@ -1101,9 +1105,12 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket_round_kernel(RedrawArgs 
       mine[k] = i < n ? ent[i] : kEmpty;
     }
     __syncthreads();
+    uint32_t hk[kPer];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k)
-      if (mine[k] != kEmpty) table_put(tab, mask, mine[k], sh);
+    for (int k = 0; k < kPer; ++k) {
+      hk[k] = static_cast<uint32_t>(pair_hash(mine[k] >> sh));
+      if (mine[k] != kEmpty) table_put(tab, mask, mine[k], sh, hk[k]);
+    }
     __syncthreads();
     for (uint32_t i0 = 0; i0 < acc; i0 += kPer * 256u) {
       uint64_t v[kPer];
@@ -1115,7 +1122,7 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket_round_kernel(RedrawArgs 
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
         if (v[k] == kEmpty) continue;
-        const uint32_t h = table_find(tab, mask, v[k] >> sh, sh);
+        const uint32_t h = table_find(tab, mask, v[k] >> sh, sh, static_cast<uint32_t>(pair_hash(v[k] >> sh)));
         if (tab[h] != kEmpty) atomicMin(tab + h, v[k]);
       }
     }
@@ -1126,7 +1133,7 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket_round_kernel(RedrawArgs 
     for (int k = 0; k < kPer; ++k) {
       win[k] = false;
       if (mine[k] == kEmpty) continue;
-      win[k] = tab[table_find(tab, mask, mine[k] >> sh, sh)] == mine[k];
+      win[k] = tab[table_find(tab, mask, mine[k] >> sh, sh, hk[k])] == mine[k];
       if (!win[k]) push_pending(a, r.slot_base + (mine[k] & slot_mask));
     }
     __syncthreads();

@@ -126,7 +126,7 @@ struct RedrawArgs {
   uint64_t* touched;
   unsigned long long* n_touched;
 };
-constexpr uint32_t kBucketCap = 2048;    // entries per bucket (accepted + one round's claims)
+constexpr uint32_t kBucketCap = 1536;    // entries per bucket (accepted + one round's claims): mean + 16 sd
 constexpr uint32_t kBucketTable = 4096;  // shared-memory hash table of a bucket
 constexpr uint32_t kBucketMean = 1024;   // target mean of round-0 entries per bucket
 constexpr int kSplitBits = 9;            // buckets per super-bucket: 2^kSplitBits at most
