@@ -555,22 +555,55 @@ __device__ __forceinline__ uint64_t local_pair(const RedrawProj& r, const DevPro
   return (static_cast<uint64_t>(s - P.s0) << r.t_bits) | (t - P.t0);
 }
 
-__device__ __forceinline__ uint64_t bucket_of(const RedrawProj& r, uint64_t pair) {
-  return r.bucket_base + (r.bucket_bits ? pair_hash(pair) >> (64 - r.bucket_bits) : 0ull);
+// Round r >= 1 with buckets: the claim of local slot i on (s, t) goes into
+// the table of the pair's bucket (accepted entries have the claim bit clear
+// and are smaller than any claim on their pair, so atomicMin keeps them;
+// among claims it keeps the lowest slot).
+__device__ void bucket_claim(const RedrawArgs& a, const RedrawProj& r, const DevProj& P, uint32_t s, uint32_t t,
+                             uint64_t i) {
+  const uint64_t pair = local_pair(r, P, s, t);
+  const uint64_t hash = pair_hash(pair);
+  const uint64_t b = r.bucket_base + (r.bucket_bits ? hash >> (64 - r.bucket_bits) : 0ull);
+  unsigned long long* tab = reinterpret_cast<unsigned long long*>(a.ent + b * a.cap);
+  const int sh = r.slot_bits + 1;
+  const uint64_t e = (pair << sh) | (1ull << r.slot_bits) | i;
+  const uint32_t mask = a.cap - 1;
+  uint32_t h = static_cast<uint32_t>(hash) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const uint64_t old = atomicCAS(tab + h, kEmpty, e);
+    if (old == kEmpty) return;
+    if ((old >> sh) == pair) {
+      atomicMin(tab + h, e);
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicOr(a.err, kErrBounds);  // full table: cannot happen below cap entries
 }
 
-// Appends a claim of round r >= 1 to bucket b after its accepted pairs; the
-// bucket's first claim of the round lists it as touched.
-__device__ __forceinline__ void bucket_put(const RedrawArgs& a, uint64_t b, uint64_t e) {
-  const uint32_t k = atomicAdd(a.pcount + b, 1u);
-  if (k == 0) {
-    const unsigned long long at = atomicAdd(a.n_touched, 1ull);
-    if (at < a.n_buckets) a.touched[at] = b;
-    else atomicOr(a.err, kErrBounds);
+// True if local slot i holds the lowest claim on (s, t) and no accepted pair
+// blocks it; the entry then becomes accepted.
+__device__ bool bucket_resolve(const RedrawArgs& a, const RedrawProj& r, const DevProj& P, uint32_t s, uint32_t t,
+                               uint64_t i) {
+  const uint64_t pair = local_pair(r, P, s, t);
+  const uint64_t hash = pair_hash(pair);
+  const uint64_t b = r.bucket_base + (r.bucket_bits ? hash >> (64 - r.bucket_bits) : 0ull);
+  uint64_t* tab = a.ent + b * a.cap;
+  const int sh = r.slot_bits + 1;
+  const uint64_t e = (pair << sh) | (1ull << r.slot_bits) | i;
+  const uint32_t mask = a.cap - 1;
+  uint32_t h = static_cast<uint32_t>(hash) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const uint64_t v = tab[h];
+    if (v == kEmpty) return false;
+    if ((v >> sh) == pair) {
+      if (v != e) return false;
+      tab[h] = e & ~(1ull << r.slot_bits);
+      return true;
+    }
+    h = (h + 1) & mask;
   }
-  const uint32_t pos = a.fill[b] + k;
-  if (pos < a.cap) a.ent[b * a.cap + pos] = e;
-  else atomicOr(a.err, kErrBounds);
+  return false;
 }
 
 // The redraw projection that owns bucket b.
@@ -628,18 +661,10 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
     const uint32_t t = P.t0 + rand_below(D.y, P.nt);
     a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
     if (a.moved) atomicOr(a.moved + (g >> 5), 1u << (g & 31u));
-    if (a.bucketed) {
-      // Settled here unless the pair needs its bucket: not allowed -> next
-      // round; allowed with multapses -> accepted.
-      if (!allowed_pair(P, s, t)) {
-        push_pending(a, g);
-      } else if (!P.multapses) {
-        const uint64_t pair = local_pair(*x.r, P, s, t);
-        const int sb = x.r->slot_bits;
-        bucket_put(a, bucket_of(*x.r, pair), (pair << (sb + 1)) | (1ull << sb) | x.i);
-      }
-    } else if (!P.multapses && allowed_pair(P, s, t)) {
-      claim(a, *x.r, P, s, t, x.i, g, false);
+    // The resolve kernel decides every slot (not allowed -> next round).
+    if (!P.multapses && allowed_pair(P, s, t)) {
+      if (a.bucketed) bucket_claim(a, *x.r, P, s, t, x.i);
+      else claim(a, *x.r, P, s, t, x.i, g, false);
     }
   }
 }
@@ -865,35 +890,6 @@ __global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a) {
   }
 }
 
-// Finds pair's entry in a shared-memory table of `mask + 1` words (linear
-// probing from `hash`, the low word of the pair's hash); the index of the
-// entry, or of the empty word that ends its probe sequence.
-__device__ __forceinline__ uint32_t table_find(const unsigned long long* tab, uint32_t mask, uint64_t pair, int sh,
-                                               uint32_t hash) {
-  uint32_t h = hash & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    const uint64_t v = tab[h];
-    if (v == kEmpty || (v >> sh) == pair) return h;
-    h = (h + 1) & mask;
-  }
-  return h;
-}
-
-// Puts e into the table; the entry left for its pair is the smallest.
-// Returns the previous entry of the pair, or kEmpty when it was new.
-__device__ __forceinline__ uint64_t table_put(unsigned long long* tab, uint32_t mask, uint64_t e, int sh,
-                                              uint32_t hash) {
-  const uint64_t pair = e >> sh;
-  uint32_t h = hash & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    const uint64_t old = atomicCAS(tab + h, kEmpty, e);
-    if (old == kEmpty) return kEmpty;
-    if ((old >> sh) == pair) return atomicMin(tab + h, e);
-    h = (h + 1) & mask;
-  }
-  return kEmpty;  // full table: cannot happen, entries <= words
-}
-
 // Spreads the super-buckets over their buckets.  A block takes a unit of
 // kSplitUnit entries of one region, counts them per bucket in shared
 // memory, stages them in bucket order, reserves each bucket's run with one
@@ -998,29 +994,17 @@ __global__ void __launch_bounds__(kSplitThreads) redraw_bucket_split_kernel(Redr
   }
 }
 
-// Appends v (where keep) at base[0..) in shared counter *count: each warp
-// takes one contiguous range, so that its lanes write consecutive words.
-__device__ __forceinline__ void warp_append(uint64_t* base, uint32_t* count, bool keep, uint64_t v) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t m = __ballot_sync(0xffffffffu, keep);
-  if (!m) return;
-  uint32_t at = 0;
-  if (lane == static_cast<uint32_t>(__ffs(m) - 1)) at = atomicAdd(count, static_cast<uint32_t>(__popc(m)));
-  at = __shfl_sync(0xffffffffu, at, __ffs(m) - 1);
-  if (keep) base[at + __popc(m & ((1u << lane) - 1u))] = v;
-}
-
 // Round 0 of the bucketed claims, one block per bucket at a time: the
 // bucket's entries go into a shared-memory table where, for every pair, the
 // smallest entry (the lowest slot) stays; every other claimant joins the
-// pending list.  The entries left in the table are written back as the
-// bucket's accepted pairs.
+// pending list.  The table is written back over the bucket's region as its
+// table of accepted pairs.
 __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
-  __shared__ __align__(16) unsigned long long tab[kBucketTable];
-  __shared__ uint32_t kept;
+  __shared__ __align__(16) unsigned long long tab[kBucketCap];
   constexpr int kPer = kBucketCap / 256;
+  constexpr uint32_t kMask = kBucketCap - 1;
   // Entries are below 2^63, never kEmpty.  The next bucket's entries are
-  // loaded while this one's are looked up.
+  // loaded while this one's table is built.
   uint64_t b = blockIdx.x;
   uint64_t mine[kPer];
   {
@@ -1037,114 +1021,38 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
     const RedrawProj& r = a.rp[bucket_owner(a, b)];
     const int sh = r.slot_bits + 1;
     const uint64_t slot_mask = (1ull << r.slot_bits) - 1;
-    for (uint32_t i = threadIdx.x; i < kBucketTable / 2; i += blockDim.x)
+    for (uint32_t i = threadIdx.x; i < kBucketCap / 2; i += blockDim.x)
       reinterpret_cast<ulonglong2*>(tab)[i] = make_ulonglong2(kEmpty, kEmpty);
-    if (threadIdx.x == 0) kept = 0;
     __syncthreads();
-    uint32_t hk[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-      hk[k] = static_cast<uint32_t>(pair_hash(mine[k] >> sh));
       if (mine[k] == kEmpty) continue;
-      const uint64_t prev = table_put(tab, kBucketTable - 1, mine[k], sh, hk[k]);
-      if (prev != kEmpty) push_pending(a, r.slot_base + ((prev < mine[k] ? mine[k] : prev) & slot_mask));
+      const uint64_t pair = mine[k] >> sh;
+      uint32_t h = static_cast<uint32_t>(pair_hash(pair)) & kMask;
+      for (uint32_t probe = 0; probe <= kMask; ++probe) {
+        const uint64_t old = atomicCAS(tab + h, kEmpty, mine[k]);
+        if (old == kEmpty) break;
+        if ((old >> sh) == pair) {
+          const uint64_t prev = atomicMin(tab + h, mine[k]);
+          push_pending(a, r.slot_base + ((prev < mine[k] ? mine[k] : prev) & slot_mask));
+          break;
+        }
+        h = (h + 1) & kMask;
+      }
     }
-    __syncthreads();
     uint64_t nxt[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint32_t i = threadIdx.x + static_cast<uint32_t>(k) * 256u;
       nxt[k] = i < n2 ? a.ent[b2 * a.cap + i] : kEmpty;
     }
-    uint64_t* ent = a.ent + b * a.cap;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const bool keep =
-          mine[k] != kEmpty && tab[table_find(tab, kBucketTable - 1, mine[k] >> sh, sh, hk[k])] == mine[k];
-      warp_append(ent, &kept, keep, mine[k]);
-    }
     __syncthreads();
-    if (threadIdx.x == 0) a.fill[b] = kept;
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(a.ent + b * a.cap);
+    for (uint32_t i = threadIdx.x; i < kBucketCap / 2; i += blockDim.x) dst[i] = reinterpret_cast<ulonglong2*>(tab)[i];
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < kPer; ++k) mine[k] = nxt[k];
     b = b2;
-  }
-}
-
-// Later rounds: the round's claims of a bucket go into a table sized for
-// them (the lowest claim on a pair stays); then each accepted pair of the
-// bucket looks its pair up and, where a claim holds it, leaves its own
-// (smaller, claim bit clear) entry there.  A claim wins if its entry is the
-// one left for its pair: winners join the accepted pairs, the others wait
-// for the next round.
-__global__ void __launch_bounds__(256, 4) redraw_bucket_round_kernel(RedrawArgs a) {
-  __shared__ __align__(16) unsigned long long tab[kBucketTable];
-  __shared__ uint32_t won;
-  constexpr int kPer = kBucketCap / 256;
-  const uint64_t n_list = *a.n_touched < a.n_buckets ? *a.n_touched : a.n_buckets;
-  for (uint64_t q = blockIdx.x; q < n_list; q += gridDim.x) {
-    const uint64_t b = a.touched[q];
-    const uint32_t pc = a.pcount[b];
-    const RedrawProj& r = a.rp[bucket_owner(a, b)];
-    const int sh = r.slot_bits + 1;
-    const uint64_t claim_bit = 1ull << r.slot_bits;
-    const uint64_t slot_mask = claim_bit - 1;
-    const uint32_t acc = a.fill[b] < a.cap ? a.fill[b] : a.cap;
-    const uint32_t n = acc + pc <= a.cap ? acc + pc : a.cap;
-    uint64_t* ent = a.ent + b * a.cap;
-    uint32_t words = 64;
-    while (words < 2 * (n - acc) && words < kBucketTable) words <<= 1;
-    const uint32_t mask = words - 1;
-    for (uint32_t i = threadIdx.x; i < words / 2; i += blockDim.x)
-      reinterpret_cast<ulonglong2*>(tab)[i] = make_ulonglong2(kEmpty, kEmpty);
-    if (threadIdx.x == 0) won = 0;
-    uint64_t mine[kPer];  // this thread's claims
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const uint32_t i = acc + threadIdx.x + static_cast<uint32_t>(k) * 256u;
-      mine[k] = i < n ? ent[i] : kEmpty;
-    }
-    __syncthreads();
-    uint32_t hk[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      hk[k] = static_cast<uint32_t>(pair_hash(mine[k] >> sh));
-      if (mine[k] != kEmpty) table_put(tab, mask, mine[k], sh, hk[k]);
-    }
-    __syncthreads();
-    for (uint32_t i0 = 0; i0 < acc; i0 += kPer * 256u) {
-      uint64_t v[kPer];
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        const uint32_t i = i0 + threadIdx.x + static_cast<uint32_t>(k) * 256u;
-        v[k] = i < acc ? ent[i] : kEmpty;
-      }
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        if (v[k] == kEmpty) continue;
-        const uint32_t h = table_find(tab, mask, v[k] >> sh, sh, static_cast<uint32_t>(pair_hash(v[k] >> sh)));
-        if (tab[h] != kEmpty) atomicMin(tab + h, v[k]);
-      }
-    }
-    __syncthreads();
-    // Decide every claim (they stay in place until all are decided).
-    bool win[kPer];
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      win[k] = false;
-      if (mine[k] == kEmpty) continue;
-      win[k] = tab[table_find(tab, mask, mine[k] >> sh, sh, hk[k])] == mine[k];
-      if (!win[k]) push_pending(a, r.slot_base + (mine[k] & slot_mask));
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) warp_append(ent + acc, &won, win[k], mine[k] & ~claim_bit);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      a.fill[b] = acc + won;
-      a.pcount[b] = 0;
-    }
-    __syncthreads();
   }
 }
 
@@ -1160,7 +1068,7 @@ __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uin
     const uint64_t pair = a.pairs[g];
     const uint32_t s = static_cast<uint32_t>(pair >> 32), t = static_cast<uint32_t>(pair);
     bool ok = allowed_pair(P, s, t);
-    if (ok && !P.multapses) ok = resolve(a, *x.r, P, s, t, x.i);
+    if (ok && !P.multapses) ok = a.bucketed ? bucket_resolve(a, *x.r, P, s, t, x.i) : resolve(a, *x.r, P, s, t, x.i);
     if (!ok) push_pending(a, g);
   }
 }

@@ -104,13 +104,14 @@ struct RedrawArgs {
   uint64_t* next_pending;
   unsigned long long* n_next;  // device counter of next_pending
   uint32_t* err;
-  // Bucketed claims: every pair is owned by one bucket (a hash of the pair);
-  // bucket b holds its accepted pairs in ent[b * cap, b * cap + fill[b]) and
-  // the round's claims right after them (pcount[b] of them).
+  // Bucketed claims: every pair is owned by one bucket (the top bits of its
+  // hash).  Round 0 fills ent[b * cap, b * cap + fill[b]) with the bucket's
+  // entries; the round-0 kernel turns the region into an open-addressing
+  // table of `cap` words (low bits of the hash, linear probing) holding the
+  // accepted pairs, and the claims of later rounds go into that table.
   int bucketed;
   uint64_t* ent;
   uint32_t* fill;
-  uint32_t* pcount;
   uint32_t cap;
   uint64_t n_buckets;
   // Bucketed claims: pairs[g] holds a slot's pair only if bit g is set here
@@ -122,12 +123,8 @@ struct RedrawArgs {
   uint64_t n_super;
   uint32_t max_super;  // largest 2^super_bits of the build
   uint64_t n_split_units;
-  // Buckets holding claims of the current round (each listed once).
-  uint64_t* touched;
-  unsigned long long* n_touched;
 };
-constexpr uint32_t kBucketCap = 1536;    // entries per bucket (accepted + one round's claims): mean + 16 sd
-constexpr uint32_t kBucketTable = 4096;  // shared-memory hash table of a bucket
+constexpr uint32_t kBucketCap = 2048;    // words of a bucket's table (mean 1024 entries, 32 sd)
 constexpr uint32_t kBucketMean = 1024;   // target mean of round-0 entries per bucket
 constexpr int kSplitBits = 9;            // buckets per super-bucket: 2^kSplitBits at most
 constexpr int kMaxSuperBits = 12;        // super-buckets per projection: 2^12 at most
@@ -140,7 +137,8 @@ __global__ void redraw_collect_kernel(RedrawArgs a);
 __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round);
 __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending);
 // Bucketed claims: round 0 keeps the lowest slot of every pair in each
-// bucket; later rounds settle each bucket's claims against its accepted pairs.
+// bucket and leaves the bucket's table of accepted pairs; later rounds claim
+// and resolve in those tables (redraw_claim_kernel, redraw_resolve_kernel).
 // Round 0 with buckets: writes every slot's round-0 connection and sends
 // its pair to its super-bucket.  Dynamic shared memory: histogram, delay
 // table, guide, then 2 * max_super counters.
@@ -151,7 +149,6 @@ __global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a);
 __global__ void redraw_bucket_split_kernel(RedrawArgs a);  // dynamic shared memory: redraw_split_smem()
 size_t redraw_split_smem();
 __global__ void redraw_bucket0_kernel(RedrawArgs a);
-__global__ void redraw_bucket_round_kernel(RedrawArgs a);
 __global__ void total_emit_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks);
 
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* block_tmp,

@@ -1012,8 +1012,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       a.lost = bucketed ? nullptr : static_cast<uint8_t*>(dev_alloc(c, n_slots));
       uint64_t* pend_a = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
       uint64_t* pend_b = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
-      a.n_next = static_cast<unsigned long long*>(dev_alloc(c, 2 * sizeof(unsigned long long)));
-      a.n_touched = a.n_next + 1;
+      a.n_next = static_cast<unsigned long long*>(dev_alloc(c, sizeof(unsigned long long)));
       if (!d_rp || !a.pairs || (!bucketed && !a.lost) || !pend_a || !pend_b || !a.n_next)
         return fail(c, SNC_ERR_OOM, "device allocation failed (redraw lists)");
       if (n_table > 0) {
@@ -1031,18 +1030,16 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         a.cap = kBucketCap;
         a.n_buckets = n_buckets;
         a.ent = static_cast<uint64_t*>(dev_alloc(c, n_buckets * kBucketCap * sizeof(uint64_t)));
-        a.fill = static_cast<uint32_t*>(dev_alloc(c, 2 * n_buckets * sizeof(uint32_t)));
+        a.fill = static_cast<uint32_t*>(dev_alloc(c, n_buckets * sizeof(uint32_t)));
         if (!a.ent || !a.fill) return fail(c, SNC_ERR_OOM, "device allocation failed (claim buckets)");
-        a.pcount = a.fill + n_buckets;
-        SNC_CUDA(c, cudaMemsetAsync(a.fill, 0, 2 * n_buckets * sizeof(uint32_t), st));
+        SNC_CUDA(c, cudaMemsetAsync(a.fill, 0, n_buckets * sizeof(uint32_t), st));
         a.n_super = n_super;
         a.max_super = max_super;
         a.n_split_units = n_split_units;
         const uint64_t sfill_words = n_super * kSuperLanes * kFillStride;
         a.sup = static_cast<uint64_t*>(dev_alloc(c, sup_entries * sizeof(uint64_t)));
         a.sfill = static_cast<uint32_t*>(dev_alloc(c, sfill_words * sizeof(uint32_t)));
-        a.touched = static_cast<uint64_t*>(dev_alloc(c, n_buckets * sizeof(uint64_t)));
-        if (!a.sup || !a.sfill || !a.touched)
+        if (!a.sup || !a.sfill)
           return fail(c, SNC_ERR_OOM, "device allocation failed (claim super-buckets)");
         SNC_CUDA(c, cudaMemsetAsync(a.sfill, 0, sfill_words * sizeof(uint32_t), st));
       } else if (bucketed) {
@@ -1057,7 +1054,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       a.rp = d_rp;
       SNC_CUDA(c, upload(c, d_rp, rps.data(), rps.size() * sizeof(RedrawProj)));
       if (a.lost) SNC_CUDA(c, cudaMemsetAsync(a.lost, 0, n_slots, st));
-      SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, 2 * sizeof(unsigned long long), st));
+      SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
       a.next_pending = pend_a;
       const auto grid_for = [&](uint64_t items) {
         return static_cast<unsigned>(
@@ -1108,16 +1105,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         if (round > 0xFFFFFFu) return fail(c, SNC_ERR_TIMEOUT, "fixed_total_number: redraw rounds exhausted");
         if (n_pend > n_slots) return fail(c, SNC_ERR_CUDA, "fixed_total_number: pending list overflow (internal error)");
         a.next_pending = next;
-        SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, 2 * sizeof(unsigned long long), st));
+        SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
         redraw_claim_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend, round);
-        if (a.bucketed) {
-          // Touched buckets are at most the claims of the round.
-          const unsigned rg = static_cast<unsigned>(
-              std::max<uint64_t>(1, std::min<uint64_t>(n_pend, static_cast<uint64_t>(c->sms) * 6)));
-          if (n_buckets > 0) redraw_bucket_round_kernel<<<rg, 256, 0, st>>>(a);
-        } else {
-          redraw_resolve_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend);
-        }
+        redraw_resolve_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend);
         c->stats.kernel_launches += 2;
         SNC_CUDA(c, cudaGetLastError());
         std::swap(pending, next);
@@ -1149,7 +1139,6 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       dev_free(c, a.moved);
       dev_free(c, a.sup);
       dev_free(c, a.sfill);
-      dev_free(c, a.touched);
     }
   }
   mark();
