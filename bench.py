@@ -507,13 +507,18 @@ def main():
     for n_syn, times, npass, st, _, _ in records:
         launches += int(st.kernel_launches)
         pair = (4.0 if st.key_bits <= 32 else 8.0) + 8.0
-        for k in range(npass):
-            pass_bytes += 2.0 * pair * n_syn
-            pass_ms += times[3 + k]
-            pass_launches += 1
+        if st.source_major:
+            # One per-source counting sort by delay instead of radix passes
+            # (every projection generated source by source): not a radix pass.
+            names = ["count", "generate", "source_offsets", "source_sort", "index"]
+        else:
+            for k in range(npass):
+                pass_bytes += 2.0 * pair * n_syn
+                pass_ms += times[3 + k]
+                pass_launches += 1
+            names = ["count", "generate", "histogram"] + ["pass%d" % k for k in range(npass)] + ["index"]
         gen_bytes += pair * n_syn
         gen_ms += times[1]
-        names = ["count", "generate", "histogram"] + ["pass%d" % k for k in range(npass)] + ["index"]
         for nm, t in zip(names, times):
             stage_sum[nm] = stage_sum.get(nm, 0.0) + t
     per_network = None
@@ -522,7 +527,9 @@ def main():
         for k, (n_syn, times, npass, st, _, _) in enumerate(records):
             name = specs[k % len(specs)].name
             e = per.setdefault(name, {"network": name, "connections": n_syn, "key_bits": int(st.key_bits),
-                                      "passes": npass, "generate_ms": 0.0, "sort_ms": 0.0, "index_ms": 0.0})
+                                      "passes": int(st.n_passes),
+                                      "sort": "source-major" if st.source_major else "radix",
+                                      "generate_ms": 0.0, "sort_ms": 0.0, "index_ms": 0.0})
             e["generate_ms"] += (times[0] + times[1]) / args.steps
             e["sort_ms"] += sum(times[2:3 + npass]) / args.steps
             e["index_ms"] += times[3 + npass] / args.steps

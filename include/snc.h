@@ -251,9 +251,14 @@ typedef struct {
   uint64_t kernel_launches; /* kernels this library launched                 */
   uint64_t h2d_bytes;       /* host -> device bytes copied                    */
   uint64_t d2h_bytes;       /* device -> host bytes copied                    */
-  int32_t n_passes;         /* radix passes of the sort                       */
+  int32_t n_passes;         /* radix passes of the sort (0: source-major sort) */
   int32_t key_bits;         /* width of the packed (source, delay, target) key */
   uint64_t device_bytes_peak; /* largest total of live device buffers          */
+  int32_t source_major;     /* 1: every projection generates source by source
+                             * (one_to_one, all_to_all, fixed_outdegree), so
+                             * the sort was a per-source counting sort by
+                             * delay step instead of radix passes            */
+  int32_t reserved;
 } snc_stats;
 
 /* Fills *out with the context's counters.  INVALID_ARG on null pointers. */

@@ -20,6 +20,7 @@
 #include "index_kernels.h"
 #include "snc_internal.h"
 #include "sort_kernels.h"
+#include "source_major.h"
 
 using namespace snc;
 
@@ -237,6 +238,7 @@ struct snc_ctx {
   // finalize; a batch concatenates its members' nodes).
   int member = 0;
   uint64_t node_base = 0;
+  int sort_stages = 0;  // timed sort stages of the last build (radix passes, or 1 for the source-major sort)
   // Results: device views; for batch members resolved at synchronize (and
   // again after every graph replay of the build).
   bool view_ready = false;
@@ -791,6 +793,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // Buffers: generated keys/values, the sort's second buffer, outputs.
   const uint64_t n = n_total;
   const bool segmented = n_members > 1;
+  // A single network whose projections all generate source by source
+  // (one_to_one, all_to_all, fixed_outdegree) is sorted per source by delay
+  // step instead of by radix passes.
+  bool src_major = !segmented && np > 0 && np <= static_cast<size_t>(kSrcMajorMaxProj) &&
+                   c->layout.delay_bits <= kSrcMajorMaxDelayBits;
+  for (size_t i = 0; i < np && src_major; ++i) src_major = source_major_rule(dp[i].rule);
   if (segmented) {
     for (int m = 0; m < n_members; ++m)
       if (seg_end[m] - seg_begin[m] >= (1ull << 30))
@@ -831,10 +839,10 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // (a segmented sort counts per segment itself).
   const SortScratch sort_lay = segmented ? sort_scratch_layout(sort_scratch, n, c->passes, n_seg_tiles, n_members)
                                          : sort_scratch_layout(sort_scratch, n, c->passes);
-  if (!segmented)
+  if (!segmented && !src_major)
     SNC_CUDA(c, cudaMemsetAsync(sort_lay.hist, 0,
                                 static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long), st));
-  const HistPlan hplan = hist_plan(c->passes, segmented ? nullptr : sort_lay.hist);
+  const HistPlan hplan = hist_plan(c->passes, (segmented || src_major) ? nullptr : sort_lay.hist);
   const size_t hist_bytes = hist_smem_bytes(hplan);
 
   // Generation.
@@ -1147,7 +1155,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // passes ping-pong between the two buffers; the result lands in
   // (keys_b, vals_b) for an odd number of passes and back in (keys_a,
   // vals_a) for an even number.
-  const bool odd = (c->passes.n_passes & 1) != 0;
+  const bool odd = src_major || (c->passes.n_passes & 1) != 0;
   void* keys_res = odd ? keys_b : keys_a;
   uint64_t* vals_res = odd ? vals_b : vals_a;
   void* keys_oth = odd ? keys_a : keys_b;
@@ -1170,7 +1178,45 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   segs.n_tiles = n_seg_tiles;
   for (int m = 0; m < n_members; ++m) segs.max_len = std::max(segs.max_len, seg_end[m] - seg_begin[m]);
   const SortSegments* seg_arg = segmented ? &segs : nullptr;
-  if (key32)
+  if (src_major) {
+    const uint64_t nn = total_nodes;
+    uint32_t* sm_counts = static_cast<uint32_t*>(dev_alloc(c, (nn + 1) * sizeof(uint32_t)));
+    uint64_t* sm_base = static_cast<uint64_t*>(dev_alloc(c, (nn + 1) * sizeof(uint64_t)));
+    uint64_t* sm_tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(nn) + 1) * sizeof(uint64_t)));
+    if (!sm_counts || !sm_base || !sm_tmp) return fail(c, SNC_ERR_OOM, "device allocation failed (source offsets)");
+    SrcMajorArgs sa{};
+    sa.projs = d_proj;
+    sa.n_proj = static_cast<int>(np);
+    sa.n_nodes = static_cast<uint32_t>(nn);
+    sa.counts = sm_counts;
+    sa.row_base = sm_base;
+    sa.keys_in = keys_a;
+    sa.vals_in = vals_a;
+    sa.key32 = key32 ? 1 : 0;
+    sa.delay_bits = c->layout.delay_bits;
+    sa.keys_out = keys_res;
+    sa.target = unpack.target;
+    sa.weight = unpack.weight;
+    sa.delay = unpack.delay;
+    sa.n = n;
+    sa.err = S.d_err;
+    const unsigned cg = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>((nn + 255) / 256, c->sms * 8ull)));
+    src_major_count_kernel<<<cg, 256, 0, st>>>(sa);
+    SNC_CUDA(c, exclusive_scan_u32(sm_counts, nn, sm_base, sm_tmp, st));
+    mark();
+    const unsigned sg = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(nn, c->sms * 8ull)));
+    src_major_sort_kernel<<<sg, kSrcMajorThreads, 0, st>>>(sa);
+    SNC_CUDA(c, cudaGetLastError());
+    mark();
+    fused = true;
+    c->stats.kernel_launches += 5;  // count, three scan kernels, sort
+    c->stats.n_passes = 0;
+    c->stats.source_major = 1;
+    c->sort_stages = 1;
+    dev_free(c, sm_counts);
+    dev_free(c, sm_base);
+    dev_free(c, sm_tmp);
+  } else if (key32)
     SNC_CUDA(c, radix_sort_run(static_cast<const uint32_t*>(keys_a), vals_a, static_cast<uint32_t*>(keys_res), vals_res,
                                static_cast<uint32_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
                                S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused, seg_arg));
@@ -1178,9 +1224,13 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     SNC_CUDA(c, radix_sort_run(static_cast<const uint64_t*>(keys_a), vals_a, static_cast<uint64_t*>(keys_res), vals_res,
                                static_cast<uint64_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
                                S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused, seg_arg));
-  if (!S.capturing) S.n_ev += c->passes.n_passes + 1;
-  if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
-  c->stats.n_passes = c->passes.n_passes;
+  if (!src_major) {
+    if (!S.capturing) S.n_ev += c->passes.n_passes + 1;
+    if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
+    c->stats.n_passes = c->passes.n_passes;
+    c->stats.source_major = 0;
+    c->sort_stages = c->passes.n_passes;
+  }
   c->stats.key_bits = c->layout.total_bits();
   dev_free(c, sort_scratch);
   dev_free(c, keys_oth);
@@ -1298,6 +1348,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     x->node_base = node_base[m];
     x->layout = c->layout;
     x->passes = c->passes;
+    x->sort_stages = c->sort_stages;
     x->group_cap = group_cap;
     x->target_all = u_target;
     x->delay_all = u_delay;
@@ -1546,7 +1597,7 @@ snc_status snc_stage_times(snc_ctx* c, float* ms, int max_stages, int* n_stages,
     ms[k] = t;
   }
   if (n_stages) *n_stages = k;
-  if (n_passes) *n_passes = c->passes.n_passes;
+  if (n_passes) *n_passes = c->sort_stages;
   return SNC_OK;
 }
 

@@ -74,7 +74,8 @@ class snc_tuning(ctypes.Structure):
 class snc_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
                 ("d2h_bytes", ctypes.c_uint64), ("n_passes", ctypes.c_int32),
-                ("key_bits", ctypes.c_int32), ("device_bytes_peak", ctypes.c_uint64)]
+                ("key_bits", ctypes.c_int32), ("device_bytes_peak", ctypes.c_uint64),
+                ("source_major", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class snc_conn_view(ctypes.Structure):

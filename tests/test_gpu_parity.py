@@ -222,3 +222,50 @@ def test_redraw_super_buckets(snc, oracle_mod):
     got = net.to_host()
     net.close()
     assert_network_equal(got, oracle_mod.build(spec), "super-buckets")
+
+
+def _build_with_stats(snc, spec):
+    net = snc.Network(spec).finalize()
+    got = net.to_host()
+    st = net.stats()
+    net.close()
+    return got, st
+
+
+@pytest.mark.parametrize("aut,mult", [(True, True), (False, False), (False, True)], ids=["both", "neither", "mult"])
+def test_source_major_sort(snc, oracle_mod, aut, mult):
+    """Builds made only of rules that generate source by source (one_to_one,
+    all_to_all, fixed_outdegree) take the per-source counting sort by delay
+    step: sources shared by several projections, rows longer than one chunk
+    (all_to_all on 3,000 targets), the one_to_one projection that drops all
+    its pairs, and the same result as the oracle's stable sort."""
+    WD = dict(weight=Dist("normal", 6.0, 1.0), delay=Dist("normal", 1.5, 0.75))
+    spec = NetworkSpec(seed=33, dt=0.1, populations=[1000, 3000, 500], projections=[
+        Projection(src=(0, 1000), tgt=(1000, 3000), rule="all_to_all", autapses=aut, multapses=mult, **WD),
+        Projection(src=(0, 4500), tgt=(0, 4500), rule="fixed_outdegree", k=37, autapses=aut, multapses=mult, **WD),
+        Projection(src=(1000, 500), tgt=(4000, 500), rule="one_to_one", autapses=aut, multapses=mult, **WD),
+        Projection(src=(4000, 500), tgt=(4000, 500), rule="one_to_one", autapses=aut, multapses=mult, **WD),
+        Projection(src=(500, 1000), tgt=(0, 1500), rule="all_to_all", autapses=aut, multapses=mult, **WD),
+        Projection(src=(4000, 500), tgt=(3000, 1500), rule="fixed_outdegree", k=1200, autapses=aut,
+                   multapses=mult, **WD)])
+    got, st = _build_with_stats(snc, spec)
+    assert st.source_major == 1 and st.n_passes == 0
+    assert_network_equal(got, oracle_mod.build(spec), "source-major")
+
+
+def test_source_major_falls_back(snc, oracle_mod):
+    """A fixed_indegree projection in the build, or delays beyond 9 bits, keep
+    the radix sort."""
+    WD = dict(weight=Dist("normal", 6.0, 1.0), delay=Dist("normal", 1.5, 0.75))
+    mixed = NetworkSpec(seed=34, dt=0.1, populations=[800, 800], projections=[
+        Projection(src=(0, 800), tgt=(800, 800), rule="all_to_all", **WD),
+        Projection(src=(800, 800), tgt=(0, 800), rule="fixed_indegree", k=40, **WD)])
+    got, st = _build_with_stats(snc, mixed)
+    assert st.source_major == 0 and st.n_passes >= 1
+    assert_network_equal(got, oracle_mod.build(mixed), "mixed rules")
+    wide = NetworkSpec(seed=35, dt=0.1, populations=[600, 600], projections=[
+        Projection(src=(0, 600), tgt=(600, 600), rule="fixed_outdegree", k=50, weight=Dist("normal", 6.0, 1.0),
+                   delay=Dist("const", 100.0))])
+    got, st = _build_with_stats(snc, wide)
+    assert st.source_major == 0
+    assert_network_equal(got, oracle_mod.build(wide), "wide delays")
