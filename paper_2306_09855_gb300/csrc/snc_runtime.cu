@@ -1204,7 +1204,10 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     src_major_count_kernel<<<cg, 256, 0, st>>>(sa);
     SNC_CUDA(c, exclusive_scan_u32(sm_counts, nn, sm_base, sm_tmp, st));
     mark();
-    const unsigned sg = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(nn, c->sms * 8ull)));
+    // One warp per source at a time.
+    const uint64_t warps = kSrcMajorThreads / 32;
+    const unsigned sg = static_cast<unsigned>(
+        std::max<uint64_t>(1, std::min<uint64_t>((nn + warps - 1) / warps, c->sms * 4ull)));
     src_major_sort_kernel<<<sg, kSrcMajorThreads, 0, st>>>(sa);
     SNC_CUDA(c, cudaGetLastError());
     mark();

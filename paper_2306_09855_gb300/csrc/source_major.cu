@@ -57,77 +57,88 @@ __global__ void src_major_count_kernel(SrcMajorArgs a) {
   }
 }
 
-// One block per source at a time.  Pass 1 counts the source's delay steps;
-// pass 2 takes its connections in generation order, chunk by chunk, ranks
-// each chunk stably per warp (warp w holds chunk items [w*32*I, (w+1)*32*I)
-// lane-interleaved, so warp, item and lane order is input order) and writes
-// every connection at the source's offset + its delay's running start + its
-// rank.
+// One warp per source at a time (no block barriers: sources are short).
+// Pass 1 counts the source's delay steps in the warp's shared-memory
+// histogram; pass 2 takes its connections in generation order, 32 at a time,
+// ranks equal delays by lane (match) after the delay's running offset, and
+// writes every connection at the source's offset + that rank.
 __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMajorArgs a) {
-  constexpr int TPB = kSrcMajorThreads, IPT = kSrcMajorItems, NW = TPB / 32;
+  constexpr int NW = kSrcMajorThreads / 32, U = kSrcMajorItems;
   constexpr int RMAX = 1 << kSrcMajorMaxDelayBits;
-  constexpr int DPT = RMAX / TPB;  // digits per thread in the per-digit loops
-  __shared__ uint64_t run_start[kSrcMajorMaxProj];
-  __shared__ uint64_t run_pre[kSrcMajorMaxProj + 1];  // elements before each run
-  __shared__ int n_runs;
-  __shared__ uint32_t running[RMAX];                   // delay counts, then next free offset per delay
-  __shared__ uint16_t wcnt[NW][RMAX];                  // per-warp counts, then per-warp offsets
-  __shared__ uint32_t scan_tmp[NW];
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  __shared__ uint32_t hist_all[NW][RMAX];  // delay counts, then running offsets
+  __shared__ uint64_t run_start_all[NW][kSrcMajorMaxProj];
+  __shared__ uint64_t run_pre_all[NW][kSrcMajorMaxProj + 1];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
+  uint32_t* hist = hist_all[warp];
+  uint64_t* run_start = run_start_all[warp];
+  uint64_t* run_pre = run_pre_all[warp];
   const uint32_t R = 1u << a.delay_bits;
   const uint32_t dmask = R - 1u;
+  const uint32_t per_lane = (R + 31u) / 32u;  // histogram bins per lane in the scan
+  const uint64_t total_warps = static_cast<uint64_t>(gridDim.x) * NW;
   const auto key_at = [&](uint64_t gi) -> uint64_t {
     return a.key32 ? static_cast<uint64_t>(static_cast<const uint32_t*>(a.keys_in)[gi])
                    : static_cast<const uint64_t*>(a.keys_in)[gi];
   };
-  // Position in the generated arrays of the source's e-th connection.
-  const auto gen_index = [&](uint64_t e) -> uint64_t {
-    int k = 0;
-    while (k + 1 < n_runs && run_pre[k + 1] <= e) ++k;
-    return run_start[k] + (e - run_pre[k]);
-  };
-  for (uint32_t s = blockIdx.x; s < a.n_nodes; s += gridDim.x) {
+  for (uint64_t s = static_cast<uint64_t>(blockIdx.x) * NW + warp; s < a.n_nodes; s += total_warps) {
     const uint64_t base = a.row_base[s];
     const uint64_t c = a.row_base[s + 1] - base;
-    if (c == 0) continue;  // uniform over the block
-    if (tid == 0) {
-      int k = 0;
-      uint64_t pre = 0;
-      for (int p = 0; p < a.n_proj; ++p) {
-        uint64_t start, len;
-        if (run_of(a.projs[p], s, start, len) && k < kSrcMajorMaxProj) {
-          run_start[k] = start;
-          run_pre[k] = pre;
-          pre += len;
-          ++k;
-        }
-      }
-      run_pre[k] = pre;
-      n_runs = k;
-      if (pre != c) atomicOr(a.err, kErrBounds);
+    if (c == 0) continue;  // uniform over the warp
+    // Runs: lane p looks at projection p; the runs are kept in projection
+    // (Connect) order.
+    uint64_t start = 0, len = 0;
+    const bool has = static_cast<int>(lane) < a.n_proj &&
+                     run_of(a.projs[lane], static_cast<uint32_t>(s), start, len);
+    const uint32_t hm = __ballot_sync(0xffffffffu, has);
+    const int n_runs = __popc(hm);
+    uint64_t pre = has ? len : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= static_cast<uint32_t>(o)) pre += y;
     }
-    for (uint32_t d = tid; d < RMAX; d += TPB) running[d] = 0;
-    __syncthreads();
-    if (n_runs == 0 || run_pre[n_runs] != c) {  // inconsistent plan: reported, nothing written
-      __syncthreads();
+    if (has) {
+      const int k = __popc(hm & lt);
+      run_start[k] = start;
+      run_pre[k] = pre - len;
+    }
+    const uint64_t total = __shfl_sync(0xffffffffu, pre, 31);
+    if (lane == 0) run_pre[n_runs] = total;
+    for (uint32_t d = lane; d < R; d += 32) hist[d] = 0;
+    __syncwarp();
+    if (total != c || n_runs == 0) {  // inconsistent plan: reported, nothing written
+      if (lane == 0) atomicOr(a.err, kErrBounds);
       continue;
     }
-    // Pass 1: delay counts of the source.
-    for (uint64_t e = tid; e < c; e += TPB) {
-      const uint64_t gi = gen_index(e);
-      if (!SNC_IN_BOUNDS(a.err, 30u, gi, a.n)) continue;
-      atomicAdd(&running[static_cast<uint32_t>(key_at(gi)) & dmask], 1u);
-    }
-    __syncthreads();
-    // Exclusive scan of the counts (DPT consecutive delays per thread).
-    {
-      uint32_t v[DPT];
-      uint32_t sum = 0;
+    const auto gen_index = [&](uint64_t e) -> uint64_t {
+      int k = 0;
+      while (k + 1 < n_runs && run_pre[k + 1] <= e) ++k;
+      return run_start[k] + (e - run_pre[k]);
+    };
+    // Pass 1: delay counts.
+    for (uint64_t e0 = 0; e0 < c; e0 += 32u * U) {
+      uint32_t d[U];
 #pragma unroll
-      for (int q = 0; q < DPT; ++q) {
-        v[q] = running[tid * DPT + q];
-        sum += v[q];
+      for (int u = 0; u < U; ++u) {
+        const uint64_t e = e0 + static_cast<uint32_t>(u) * 32u + lane;
+        d[u] = R;
+        if (e < c) {
+          const uint64_t gi = gen_index(e);
+          if (SNC_IN_BOUNDS(a.err, 30u, gi, a.n)) d[u] = static_cast<uint32_t>(key_at(gi)) & dmask;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (d[u] < R) atomicAdd(hist + d[u], 1u);
+    }
+    __syncwarp();
+    // Exclusive scan of the counts: lane l holds bins [l * per_lane, ...).
+    {
+      uint32_t sum = 0;
+      for (uint32_t q = 0; q < per_lane; ++q) {
+        const uint32_t b = lane * per_lane + q;
+        if (b < R) sum += hist[b];
       }
       uint32_t x = sum;
 #pragma unroll
@@ -135,73 +146,53 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= static_cast<uint32_t>(o)) x += y;
       }
-      if (lane == 31) scan_tmp[warp] = x;
-      __syncthreads();
-      uint32_t before = 0;
-      for (uint32_t w = 0; w < warp; ++w) before += scan_tmp[w];
-      uint32_t run = before + x - sum;
-#pragma unroll
-      for (int q = 0; q < DPT; ++q) {
-        running[tid * DPT + q] = run;
-        run += v[q];
+      uint32_t run = x - sum;
+      for (uint32_t q = 0; q < per_lane; ++q) {
+        const uint32_t b = lane * per_lane + q;
+        if (b < R) {
+          const uint32_t v = hist[b];
+          hist[b] = run;
+          run += v;
+        }
       }
     }
-    // Pass 2: chunks in generation order.
-    for (uint64_t cb = 0; cb < c; cb += static_cast<uint64_t>(TPB) * IPT) {
-      for (uint32_t i = tid; i < NW * RMAX / 2; i += TPB) reinterpret_cast<uint32_t*>(&wcnt[0][0])[i] = 0u;
-      __syncthreads();
-      uint64_t key[IPT], val[IPT];
-      uint32_t rank[IPT];
+    __syncwarp();
+    // Pass 2: 32 connections at a time in generation order.
+    for (uint64_t e0 = 0; e0 < c; e0 += 32u * U) {
+      uint64_t key[U], val[U];
 #pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint64_t e = cb + warp * 32u * IPT + static_cast<uint32_t>(j) * 32u + lane;
-        const bool ok = e < c;
-        uint64_t gi = 0;
-        if (ok) gi = gen_index(e);
-        const bool in = ok && SNC_IN_BOUNDS(a.err, 31u, gi, a.n);
-        key[j] = in ? key_at(gi) : 0ull;
-        val[j] = in ? a.vals_in[gi] : 0ull;
-        const uint32_t d = ok ? (static_cast<uint32_t>(key[j]) & dmask) : R;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t old = ok ? wcnt[warp][d] : 0u;
-        __syncwarp();
-        if (ok && static_cast<int>(lane) == __ffs(peers) - 1) wcnt[warp][d] = static_cast<uint16_t>(old + __popc(peers));
-        rank[j] = old + __popc(peers & lt);
-        __syncwarp();
-      }
-      __syncthreads();
-      uint32_t tot[DPT];
-#pragma unroll
-      for (int q = 0; q < DPT; ++q) {
-        const uint32_t d = tid * DPT + q;
-        uint32_t r = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const uint32_t cw = wcnt[w][d];
-          wcnt[w][d] = static_cast<uint16_t>(r);
-          r += cw;
+      for (int u = 0; u < U; ++u) {
+        const uint64_t e = e0 + static_cast<uint32_t>(u) * 32u + lane;
+        key[u] = ~0ull;
+        val[u] = 0;
+        if (e < c) {
+          const uint64_t gi = gen_index(e);
+          if (SNC_IN_BOUNDS(a.err, 31u, gi, a.n)) {
+            key[u] = key_at(gi);
+            val[u] = a.vals_in[gi];
+          }
         }
-        tot[q] = r;
       }
-      __syncthreads();
 #pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint64_t e = cb + warp * 32u * IPT + static_cast<uint32_t>(j) * 32u + lane;
-        if (e >= c) continue;
-        const uint32_t d = static_cast<uint32_t>(key[j]) & dmask;
-        const uint64_t pos = base + running[d] + wcnt[warp][d] + rank[j];
+      for (int u = 0; u < U; ++u) {
+        const bool ok = key[u] != ~0ull;
+        const uint32_t d = ok ? (static_cast<uint32_t>(key[u]) & dmask) : R;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t old = ok ? hist[d] : 0u;
+        __syncwarp();
+        if (ok && static_cast<int>(lane) == __ffs(peers) - 1) hist[d] = old + __popc(peers);
+        __syncwarp();
+        if (!ok) continue;
+        const uint64_t pos = base + old + __popc(peers & lt);
         if (!SNC_IN_BOUNDS(a.err, 32u, pos, a.n)) continue;
-        if (a.key32) static_cast<uint32_t*>(a.keys_out)[pos] = static_cast<uint32_t>(key[j]);
-        else static_cast<uint64_t*>(a.keys_out)[pos] = key[j];
-        a.target[pos] = static_cast<uint32_t>(val[j] >> 32);
-        a.weight[pos] = static_cast<uint32_t>(val[j]);
+        if (a.key32) static_cast<uint32_t*>(a.keys_out)[pos] = static_cast<uint32_t>(key[u]);
+        else static_cast<uint64_t*>(a.keys_out)[pos] = key[u];
+        a.target[pos] = static_cast<uint32_t>(val[u] >> 32);
+        a.weight[pos] = static_cast<uint32_t>(val[u]);
         a.delay[pos] = static_cast<uint16_t>(d);
       }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < DPT; ++q) running[tid * DPT + q] += tot[q];
-      __syncthreads();
     }
+    __syncwarp();
   }
 }
 

@@ -239,7 +239,7 @@ def test_source_major_sort(snc, oracle_mod, aut, mult):
     step: sources shared by several projections, rows longer than one chunk
     (all_to_all on 3,000 targets), the one_to_one projection that drops all
     its pairs, and the same result as the oracle's stable sort."""
-    WD = dict(weight=Dist("normal", 6.0, 1.0), delay=Dist("normal", 1.5, 0.75))
+    WD = dict(weight=Dist("normal", 20.0, 1.0), delay=Dist("normal", 1.5, 0.75))
     spec = NetworkSpec(seed=33, dt=0.1, populations=[1000, 3000, 500], projections=[
         Projection(src=(0, 1000), tgt=(1000, 3000), rule="all_to_all", autapses=aut, multapses=mult, **WD),
         Projection(src=(0, 4500), tgt=(0, 4500), rule="fixed_outdegree", k=37, autapses=aut, multapses=mult, **WD),
@@ -256,7 +256,7 @@ def test_source_major_sort(snc, oracle_mod, aut, mult):
 def test_source_major_falls_back(snc, oracle_mod):
     """A fixed_indegree projection in the build, or delays beyond 9 bits, keep
     the radix sort."""
-    WD = dict(weight=Dist("normal", 6.0, 1.0), delay=Dist("normal", 1.5, 0.75))
+    WD = dict(weight=Dist("normal", 20.0, 1.0), delay=Dist("normal", 1.5, 0.75))
     mixed = NetworkSpec(seed=34, dt=0.1, populations=[800, 800], projections=[
         Projection(src=(0, 800), tgt=(800, 800), rule="all_to_all", **WD),
         Projection(src=(800, 800), tgt=(0, 800), rule="fixed_indegree", k=40, **WD)])
