@@ -1204,15 +1204,17 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     src_major_count_kernel<<<cg, 256, 0, st>>>(sa);
     SNC_CUDA(c, exclusive_scan_u32(sm_counts, nn, sm_base, sm_tmp, st));
     mark();
-    // One warp per source at a time.
+    // Short sources one warp each, the others one block each.
     const uint64_t warps = kSrcMajorThreads / 32;
-    const unsigned sg = static_cast<unsigned>(
+    const unsigned wg = static_cast<unsigned>(
         std::max<uint64_t>(1, std::min<uint64_t>((nn + warps - 1) / warps, c->sms * 4ull)));
-    src_major_sort_kernel<<<sg, kSrcMajorThreads, 0, st>>>(sa);
+    src_major_small_kernel<<<wg, kSrcMajorThreads, 0, st>>>(sa);
+    const unsigned bg = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>(nn, c->sms * 4ull)));
+    src_major_sort_kernel<<<bg, kSrcMajorThreads, 0, st>>>(sa);
     SNC_CUDA(c, cudaGetLastError());
     mark();
     fused = true;
-    c->stats.kernel_launches += 5;  // count, three scan kernels, sort
+    c->stats.kernel_launches += 6;  // count, three scan kernels, two sorts
     c->stats.n_passes = 0;
     c->stats.source_major = 1;
     c->sort_stages = 1;

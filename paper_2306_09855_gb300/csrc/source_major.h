@@ -22,6 +22,8 @@ constexpr int kSrcMajorMaxProj = 16;   // projections of a build on this path
 constexpr int kSrcMajorMaxDelayBits = 9;
 constexpr int kSrcMajorThreads = 256;
 constexpr int kSrcMajorItems = 8;      // keys per thread and chunk
+constexpr int kSrcMajorChunk = kSrcMajorThreads * kSrcMajorItems;
+constexpr uint64_t kSrcMajorSmall = 256;  // sources up to this many connections: one warp each
 
 struct SrcMajorArgs {
   const DevProj* projs;
@@ -46,7 +48,9 @@ bool source_major_rule(uint32_t rule);
 
 // counts[s] = connections of source s over all projections.
 __global__ void src_major_count_kernel(SrcMajorArgs a);
-// Stable counting sort of each source's runs by delay step.
+// Stable counting sort of each source's runs by delay step: sources above
+// kSrcMajorSmall connections (a block each), and the others (a warp each).
 __global__ void src_major_sort_kernel(SrcMajorArgs a);
+__global__ void src_major_small_kernel(SrcMajorArgs a);
 
 }  // namespace snc
