@@ -796,8 +796,10 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // A single network whose projections all generate source by source
   // (one_to_one, all_to_all, fixed_outdegree) is sorted per source by delay
   // step instead of by radix passes.
+  // (Worth it when sources average many connections: one_to_one stays on the
+  // radix sort.)
   bool src_major = !segmented && np > 0 && np <= static_cast<size_t>(kSrcMajorMaxProj) &&
-                   c->layout.delay_bits <= kSrcMajorMaxDelayBits;
+                   c->layout.delay_bits <= kSrcMajorMaxDelayBits && n >= 64 * std::max<uint64_t>(1, total_nodes);
   for (size_t i = 0; i < np && src_major; ++i) src_major = source_major_rule(dp[i].rule);
   if (segmented) {
     for (int m = 0; m < n_members; ++m)
@@ -1183,7 +1185,10 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     uint32_t* sm_counts = static_cast<uint32_t*>(dev_alloc(c, (nn + 1) * sizeof(uint32_t)));
     uint64_t* sm_base = static_cast<uint64_t*>(dev_alloc(c, (nn + 1) * sizeof(uint64_t)));
     uint64_t* sm_tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(nn) + 1) * sizeof(uint64_t)));
-    if (!sm_counts || !sm_base || !sm_tmp) return fail(c, SNC_ERR_OOM, "device allocation failed (source offsets)");
+    uint32_t* sm_long = static_cast<uint32_t*>(dev_alloc(c, (nn + 1) * sizeof(uint32_t)));
+    if (!sm_counts || !sm_base || !sm_tmp || !sm_long)
+      return fail(c, SNC_ERR_OOM, "device allocation failed (source offsets)");
+    SNC_CUDA(c, cudaMemsetAsync(sm_long + nn, 0, sizeof(uint32_t), st));
     SrcMajorArgs sa{};
     sa.projs = d_proj;
     sa.n_proj = static_cast<int>(np);
@@ -1200,6 +1205,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     sa.delay = unpack.delay;
     sa.n = n;
     sa.err = S.d_err;
+    sa.long_list = sm_long;
+    sa.n_long = sm_long + nn;
     const unsigned cg = static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>((nn + 255) / 256, c->sms * 8ull)));
     src_major_count_kernel<<<cg, 256, 0, st>>>(sa);
     SNC_CUDA(c, exclusive_scan_u32(sm_counts, nn, sm_base, sm_tmp, st));
@@ -1221,6 +1228,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     dev_free(c, sm_counts);
     dev_free(c, sm_base);
     dev_free(c, sm_tmp);
+    dev_free(c, sm_long);
   } else if (key32)
     SNC_CUDA(c, radix_sort_run(static_cast<const uint32_t*>(keys_a), vals_a, static_cast<uint32_t*>(keys_res), vals_res,
                                static_cast<uint32_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,

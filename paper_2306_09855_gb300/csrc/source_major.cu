@@ -54,6 +54,7 @@ __global__ void src_major_count_kernel(SrcMajorArgs a) {
       c = 0;
     }
     a.counts[s] = static_cast<uint32_t>(c);
+    if (c > kSrcMajorSmall) a.long_list[atomicAdd(a.n_long, 1u)] = s;
   }
 }
 
@@ -255,7 +256,9 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
     __syncthreads();  // scan_tmp is reused
     return total;
   };
-  for (uint32_t s = blockIdx.x; s < a.n_nodes; s += gridDim.x) {
+  const uint32_t n_long = *a.n_long;
+  for (uint32_t q = blockIdx.x; q < n_long; q += gridDim.x) {
+    const uint32_t s = a.long_list[q];
     const uint64_t base = a.row_base[s];
     const uint64_t c = a.row_base[s + 1] - base;
     if (c <= kSrcMajorSmall) continue;  // uniform over the block
@@ -292,8 +295,11 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
       while (k + 1 < n_runs && run_pre[k + 1] <= e) ++k;
       return run_start[k] + (e - run_pre[k]);
     };
+    // A source of one chunk is ranked, staged and written in one go (its
+    // staged order is its final order); longer ones count their delays first.
+    const bool one_chunk = c <= CH;
     // Pass 1: delay counts.
-    for (uint64_t e0 = 0; e0 < c; e0 += CH) {
+    for (uint64_t e0 = 0; !one_chunk && e0 < c; e0 += CH) {
       uint32_t d[IPT];
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
@@ -309,7 +315,7 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
         if (d[j] < R) atomicAdd(&running[d[j]], 1u);
     }
     __syncthreads();
-    {
+    if (!one_chunk) {
       uint32_t v[DPT];
 #pragma unroll
       for (int q = 0; q < DPT; ++q) v[q] = running[tid * DPT + q];
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
         const uint64_t k = skey[i];
         const uint64_t v = sval[i];
         const uint32_t d = static_cast<uint32_t>(k) & dmask;
-        const uint64_t pos = base + running[d] + (i - cstart[d]);
+        const uint64_t pos = base + (one_chunk ? i : running[d] + (i - cstart[d]));
         if (!SNC_IN_BOUNDS(a.err, 32u, pos, a.n)) continue;
         if (a.key32) static_cast<uint32_t*>(a.keys_out)[pos] = static_cast<uint32_t>(k);
         else static_cast<uint64_t*>(a.keys_out)[pos] = k;

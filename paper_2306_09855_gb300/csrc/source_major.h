@@ -41,6 +41,8 @@ struct SrcMajorArgs {
   uint16_t* delay;           // sorted delay steps
   uint64_t n;                // connections
   uint32_t* err;
+  uint32_t* long_list;       // sources above kSrcMajorSmall connections (any order)
+  uint32_t* n_long;          // their number
 };
 
 // True if every projection's rule generates source by source.
