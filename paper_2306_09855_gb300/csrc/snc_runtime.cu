@@ -796,10 +796,13 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // A single network whose projections all generate source by source
   // (one_to_one, all_to_all, fixed_outdegree) is sorted per source by delay
   // step instead of by radix passes.
-  // (Worth it when sources average many connections: one_to_one stays on the
-  // radix sort.)
+  // It pays when sources average between 64 connections and two chunks
+  // (one_to_one and long all_to_all rows stay on the radix sort, which was
+  // measured faster there).
+  const uint64_t per_source = n / std::max<uint64_t>(1, total_nodes);
   bool src_major = !segmented && np > 0 && np <= static_cast<size_t>(kSrcMajorMaxProj) &&
-                   c->layout.delay_bits <= kSrcMajorMaxDelayBits && n >= 64 * std::max<uint64_t>(1, total_nodes);
+                   c->layout.delay_bits <= kSrcMajorMaxDelayBits && per_source >= 64 &&
+                   per_source <= 2 * static_cast<uint64_t>(kSrcMajorChunk);
   for (size_t i = 0; i < np && src_major; ++i) src_major = source_major_rule(dp[i].rule);
   if (segmented) {
     for (int m = 0; m < n_members; ++m)
