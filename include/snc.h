@@ -235,7 +235,7 @@ typedef struct {
   int32_t sort_group_tiles;  /* 4096-key tiles per look-back unit: 1, 4, 8;
                               * 0 = one tile, loaded by bulk copy (8-9 bit digits) */
   int32_t gen_blocks_per_sm; /* generation grid = SMs x this (1..32)        */
-  int32_t sort_items;        /* bulk-copy pass: keys per thread, 8, 12 or 16 */
+  int32_t sort_items;        /* bulk-copy pass: keys per thread, 8, 12, 16, 24 or 32 */
   int32_t reserved[4];       /* must be 0                                    */
 } snc_tuning;
 

@@ -16,8 +16,8 @@ from . import snc
 
 # (sort digit bits, tiles per look-back unit, generation blocks per SM,
 #  keys per thread of the bulk-copy pass)
-CANDIDATES = [(8, 0, 8, 16), (9, 0, 8, 16), (8, 0, 8, 12), (8, 0, 4, 16), (8, 0, 16, 16), (10, 8, 8, 16),
-              (11, 8, 8, 16)]
+CANDIDATES = [(9, 0, 8, 32), (9, 0, 8, 24), (9, 0, 8, 16), (8, 0, 8, 32), (8, 0, 8, 16), (8, 0, 8, 12),
+              (9, 0, 4, 32), (9, 0, 16, 32), (11, 8, 8, 16)]
 FIELDS = ("sort_digit_bits", "sort_group_tiles", "gen_blocks_per_sm", "sort_items")
 
 
@@ -78,7 +78,7 @@ def tune(specs: Sequence, batched: bool = True, candidates=CANDIDATES, cache_pat
     for sp in specs:
         for pj in sp.projections:
             n_est += int(pj.k) * int(pj.tgt[1]) if pj.rule == "fixed_indegree" else int(pj.k)
-    key = "v3/%s/%s/%s/%s" % (_gpu_name(), _key_class(specs), _size_class(n_est), "batch" if batched else "single")
+    key = "v4/%s/%s/%s/%s" % (_gpu_name(), _key_class(specs), _size_class(n_est), "batch" if batched else "single")
     cache = {}
     if use_cache and os.path.exists(cache_path):
         try:

@@ -1658,8 +1658,8 @@ snc_status snc_set_tuning(const snc_tuning* t) {
     return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_group_tiles must be 0, 1, 4 or 8");
   if (t->gen_blocks_per_sm < 1 || t->gen_blocks_per_sm > 32)
     return fail(nullptr, SNC_ERR_INVALID_ARG, "gen_blocks_per_sm outside [1, 32]");
-  if (t->sort_items != 8 && t->sort_items != 12 && t->sort_items != 16)
-    return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_items must be 8, 12 or 16");
+  if (t->sort_items != 8 && t->sort_items != 12 && t->sort_items != 16 && t->sort_items != 24 && t->sort_items != 32)
+    return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_items must be 8, 12, 16, 24 or 32");
   if (t->reserved[0] || t->reserved[1] || t->reserved[2] || t->reserved[3])
     return fail(nullptr, SNC_ERR_INVALID_ARG, "reserved tuning fields must be 0");
   g_sort_tuning.max_digit_bits = t->sort_digit_bits;

@@ -570,10 +570,11 @@ struct OnesweepTma {
   static constexpr size_t kOffBar = kOffGlob + RADIX * sizeof(uint64_t);
   static constexpr size_t kSmem = kOffBar + 16;
   // Resident blocks per SM: shared memory (228 KB per SM, 1 KB reserved per
-  // block) and the register target of the item count (16 -> 3, 12 -> 4,
-  // 8 -> 5 blocks of 256 threads).
+  // block) and the register target of the item count (24 and 32 -> 2,
+  // 16 -> 3, 12 -> 4, 8 -> 5 blocks of 256 threads).  Larger tiles take
+  // fewer look-backs per key.
   static constexpr int kFit = static_cast<int>((228u * 1024u) / (kSmem + 1024u + 256u));
-  static constexpr int kRegCap = ITEMS >= 16 ? 3 : (ITEMS >= 12 ? 4 : 5);
+  static constexpr int kRegCap = ITEMS >= 20 ? 2 : (ITEMS >= 16 ? 3 : (ITEMS >= 12 ? 4 : 5));
   static constexpr int MINB = kFit < 1 ? 1 : (kFit > kRegCap ? kRegCap : kFit);
 };
 
@@ -842,6 +843,8 @@ template <int BITS, typename K, typename V>
 cudaError_t launch_onesweep_tma_sel(const SortPasses& sp, const OnesweepArgs<K, V>& a, int sms, cudaStream_t st) {
   if (sp.items == 8) return launch_onesweep_tma<BITS, 8, K, V>(a, sms, st);
   if (sp.items == 12) return launch_onesweep_tma<BITS, 12, K, V>(a, sms, st);
+  if (sp.items == 24) return launch_onesweep_tma<BITS, 24, K, V>(a, sms, st);
+  if (sp.items == 32) return launch_onesweep_tma<BITS, 32, K, V>(a, sms, st);
   return launch_onesweep_tma<BITS, 16, K, V>(a, sms, st);
 }
 
@@ -905,8 +908,9 @@ cudaError_t launch_onesweep_bits(const SortPasses& sp, int group_tiles, const On
 // of up to 9 bits: plan_passes takes the fewest passes and the narrowest
 // even widths, so 9-bit digits are used only where they save a pass (e.g. 3
 // passes instead of 4 for a 25-bit key; a 24-bit key keeps three 8-bit
-// passes).
-SortTuning g_sort_tuning{9, 0, 16};
+// passes).  32 keys per thread: 8,192-key tiles, two blocks per SM, about
+// half the look-backs per key of 16.
+SortTuning g_sort_tuning{9, 0, 32};
 
 // Digit plan: the fewest passes of at most max_bits bits, widths as even as
 // possible, the kernel's digit width the widest of them (at least 8).
@@ -929,7 +933,7 @@ SortPasses plan_passes(int key_bits, const SortTuning& tune) {
   }
   sp.kernel_bits = widest < 8 ? 8 : widest;
   sp.group_tiles = (tune.group_tiles == 0 || tune.group_tiles == 1 || tune.group_tiles == 4) ? tune.group_tiles : 8;
-  sp.items = (tune.items == 8 || tune.items == 12) ? tune.items : 16;
+  sp.items = (tune.items == 8 || tune.items == 12 || tune.items == 24 || tune.items == 32) ? tune.items : 16;
   return sp;
 }
 

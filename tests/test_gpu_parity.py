@@ -154,8 +154,9 @@ def test_launch_shape_independence(snc):
         np.testing.assert_array_equal(a[f], b[f])
 
 
-@pytest.mark.parametrize("digit_bits,group,items", [(11, 8, 16), (8, 0, 16), (9, 4, 16), (8, 0, 12), (9, 0, 8)],
-                         ids=["d11g8", "d8tma", "d9g4", "d8tma_i12", "d9tma_i8"])
+@pytest.mark.parametrize("digit_bits,group,items", [(11, 8, 16), (8, 0, 16), (9, 4, 16), (8, 0, 12), (9, 0, 8),
+                                                   (9, 0, 32), (8, 0, 24)],
+                         ids=["d11g8", "d8tma", "d9g4", "d8tma_i12", "d9tma_i8", "d9tma_i32", "d8tma_i24"])
 @pytest.mark.parametrize("n_nodes,delay", [(4, Dist("const", 0.1)), (60, Dist("normal", 1.5, 0.75)),
                                            (3000, Dist("normal", 1.5, 0.75)),
                                            (600_000, Dist("normal", 1.5, 0.75)),

@@ -44,8 +44,9 @@ def test_sort_matches_stable_argsort(torch_snc, n, bits):
 
 # (digit bits, tiles per look-back unit, keys per thread); the last only
 # matters for the bulk-copy kernel (group 0, 8-9 bit digits).
-TUNINGS = [(8, 0, 16), (9, 0, 16), (8, 0, 12), (9, 0, 12), (8, 0, 8), (9, 0, 8), (8, 1, 16), (9, 4, 16),
-           (9, 8, 16), (10, 8, 16), (11, 4, 16), (11, 8, 16), (11, 1, 16)]
+TUNINGS = [(8, 0, 16), (9, 0, 16), (8, 0, 12), (9, 0, 12), (8, 0, 8), (9, 0, 8), (8, 0, 24), (9, 0, 24),
+           (8, 0, 32), (9, 0, 32), (8, 1, 16), (9, 4, 16), (9, 8, 16), (10, 8, 16), (11, 4, 16), (11, 8, 16),
+           (11, 1, 16)]
 
 
 def _restore(snc, old):
