@@ -41,7 +41,8 @@ def parse_args():
     ap.add_argument("--impl", default="snc", choices=["snc", "reference"])
     ap.add_argument("--workload", default="rule_sweep",
                     choices=["rule_sweep", "microcircuit", "plain", "small", "profile", "profile_total",
-                             "profile_sampler", "profile_bernoulli", "batched", "served", "trials"])
+                             "profile_sampler", "profile_bernoulli", "profile_outdegree", "batched", "served",
+                             "trials"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sort-digit-bits", type=int, default=None, help="tuning: widest radix digit")
     ap.add_argument("--sort-group-tiles", type=int, default=None, help="tuning: tiles per look-back unit")
@@ -83,6 +84,10 @@ def workload_specs(name):
         return [W.two_population(100_000, "fixed_indegree", k=100, autapses=False, multapses=False)], {
             "workload": "profiling case: 2 x 100,000 nodes, fixed_indegree K=100 without autapses or "
                         "multapses (4e7 connections)", "seed": 1234}
+    if name == "profile_outdegree":
+        return [W.two_population(20_000, "fixed_outdegree", k=1000)], {
+            "workload": "profiling case: 2 x 20,000 nodes, fixed_outdegree K=1000 (8e7 connections, sorted per "
+                        "source by delay step)", "seed": 1234}
     if name == "profile_bernoulli":
         return [W.two_population(100_000, "pairwise_bernoulli", p=0.001, autapses=False)], {
             "workload": "profiling case: 2 x 100,000 nodes, pairwise_bernoulli p=0.001 (about 4e7 "
