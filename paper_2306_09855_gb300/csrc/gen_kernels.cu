@@ -320,14 +320,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
     if (want == 0) continue;
     const bool complement = 2 * want > cand;
     const uint32_t need = static_cast<uint32_t>(complement ? cand - want : want);
-    const bool hashed = a.hash_bits > 0;  // uniform over the launch
-    if (hashed && (complement || 2u * need > (1u << a.hash_bits))) {
-      // The host sizes the set for every primary; report instead of overfilling.
-      if (lane == 0) atomicOr(a.err, kErrSamplerBound);
-      continue;
-    }
-    const uint32_t clear_words = hashed ? (1u << a.hash_bits) : words;
-    for (uint32_t w = lane; w < clear_words; w += 32) bitmap[w] = 0u;
+    for (uint32_t w = lane; w < words; w += 32) bitmap[w] = 0u;
     __syncwarp();
     uint32_t got = 0;
     uint64_t call = 0;
@@ -351,20 +344,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
         const uint32_t u = sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
         const uint32_t r = endpoint(u, n_other, skip, skip_local);
         const uint32_t bit = 1u << (r & 31u);
-        bool seen;
-        uint32_t slot = 0;  // hash set: the word holding r, or the empty word ending its probe
-        if (hashed) {
-          const uint32_t hmask = (1u << a.hash_bits) - 1u;
-          slot = (r * 0x9E3779B1u) >> (32 - a.hash_bits);
-          uint32_t v = bitmap[slot];
-          for (uint32_t probe = 0; v != 0u && v != r + 1u && probe < hmask; ++probe) {
-            slot = (slot + 1u) & hmask;
-            v = bitmap[slot];
-          }
-          seen = v == r + 1u;
-        } else {
-          seen = (bitmap[r >> 5] & bit) != 0u;
-        }
+        const bool seen = (bitmap[r >> 5] & bit) != 0u;
         const uint32_t peers = __match_any_sync(0xffffffffu, r);
         const bool first = (__ffs(peers) - 1) == static_cast<int>(lane);
         const bool fresh = !seen && first;
@@ -374,16 +354,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
         const bool take = fresh && rank < room;
         __syncwarp();
         if (take) {
-          if (hashed) {
-            // Taken values are distinct: claim the first empty word from here.
-            const uint32_t hmask = (1u << a.hash_bits) - 1u;
-            for (uint32_t probe = 0; probe <= hmask; ++probe) {
-              if (atomicCAS(&bitmap[slot], 0u, r + 1u) == 0u) break;
-              slot = (slot + 1u) & hmask;
-            }
-          } else {
-            atomicOr(&bitmap[r >> 5], bit);
-          }
+          atomicOr(&bitmap[r >> 5], bit);
           if (!complement) {
             const uint32_t j = got + rank;
             const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);

@@ -45,10 +45,7 @@ struct SamplerArgs {
   const uint16_t* guide_blob;
   uint32_t max_delay_len;        // largest delay table among the listed projections
   uint32_t table_words;          // per-warp table area (thresholds + guide), uint32 units
-  uint32_t bitmap_words;         // per-warp bitmap (largest candidate range), or the hash set
-  int hash_bits;                 // > 0: the taken values are kept in a hash set of 2^hash_bits
-                                 // words (value + 1, 0 = empty) instead of a bitmap; only when no
-                                 // listed primary can want more than half of its candidates
+  uint32_t bitmap_words;         // per-warp bitmap (largest candidate range)
   const uint64_t* prim_offsets;  // Bernoulli: exclusive scan of all per-target counts
   uint32_t* err;
 };

@@ -881,22 +881,14 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     std::vector<uint32_t> slist;
     std::vector<uint64_t> sprefix(1, 0);
     uint32_t max_other = 1, max_len = 0;
-    uint64_t max_need = 0;  // most values one primary can take
-    bool sparse = true;     // no primary can want more than half of its candidates
     for (size_t i = 0; i < np; ++i) {
       const Projection& p = *ups[i].p;
       if (cnt[i] == 0 || !is_sampler(p)) continue;
       const bool out_deg = p.rule.kind == SNC_FIXED_OUTDEGREE;
       slist.push_back(static_cast<uint32_t>(i));
       sprefix.push_back(sprefix.back() + (out_deg ? p.src.n : p.tgt.n));
-      const uint32_t n_other = out_deg ? p.tgt.n : p.src.n;
-      max_other = std::max<uint32_t>(max_other, n_other);
+      max_other = std::max<uint32_t>(max_other, out_deg ? p.tgt.n : p.src.n);
       max_len = std::max(max_len, dp[i].d_len);
-      const uint64_t need = p.rule.kind == SNC_PAIRWISE_BERNOULLI
-                                ? std::max(p.b_base[0] + p.b_thr[0].size(), p.b_base[1] + p.b_thr[1].size())
-                                : p.rule.k;
-      max_need = std::max(max_need, need);
-      if (2 * need + 2 > n_other) sparse = false;  // one candidate may be left out (autapse skip)
     }
     if (!slist.empty()) {
       uint32_t* d_slist = static_cast<uint32_t*>(dev_alloc(c, slist.size() * sizeof(uint32_t)));
@@ -915,14 +907,6 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       s.max_delay_len = max_len;
       s.table_words = max_len + (kDelayGuide + 1) / 2 + 1;
       s.bitmap_words = (max_other + 31u) / 32u;
-      // Sparse selections keep the taken values in a hash set (at most half
-      // full) when it is smaller than the bitmap: more warps per SM.
-      int hbits = 6;
-      while ((1ull << hbits) < 2 * max_need) ++hbits;
-      if (sparse && (1ull << hbits) < s.bitmap_words) {
-        s.hash_bits = hbits;
-        s.bitmap_words = 1u << hbits;
-      }
       s.prim_offsets = d_prim_off;
       s.err = S.d_err;
       const size_t per_warp = static_cast<size_t>(s.bitmap_words + s.table_words) * sizeof(uint32_t);
