@@ -270,3 +270,17 @@ def test_source_major_falls_back(snc, oracle_mod):
     got, st = _build_with_stats(snc, wide)
     assert st.source_major == 0
     assert_network_equal(got, oracle_mod.build(wide), "wide delays")
+
+
+def test_sparse_samplers_wide_ranges(snc, oracle_mod):
+    """Selections without replacement of at most 100 of 20,000-60,000
+    candidates (in-degree, out-degree with the autapse skip, Bernoulli
+    subsets) in one build: the oracle's sequential rule exactly."""
+    WD = dict(weight=Dist("normal", 20.0, 1.0), delay=Dist("normal", 1.5, 0.75))
+    spec = NetworkSpec(seed=44, dt=0.1, populations=[60_000, 20_000], projections=[
+        Projection(src=(0, 60_000), tgt=(60_000, 20_000), rule="fixed_indegree", k=90, multapses=False, **WD),
+        Projection(src=(0, 60_000), tgt=(0, 60_000), rule="fixed_outdegree", k=25, autapses=False,
+                   multapses=False, **WD),
+        Projection(src=(60_000, 20_000), tgt=(0, 30_000), rule="pairwise_bernoulli", p=0.002, **WD)])
+    got, _ = _build_with_stats(snc, spec)
+    assert_network_equal(got, oracle_mod.build(spec), "sparse samplers")
