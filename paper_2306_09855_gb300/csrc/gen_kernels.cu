@@ -355,27 +355,16 @@ __global__ void sampler_kernel(SamplerArgs a) {
         __syncwarp();
         if (take) {
           atomicOr(&bitmap[r >> 5], bit);
-          // Slot j's value, parked in its value word until the selection is
-          // complete (the connections are then written in slot order).
-          if (!complement && SNC_IN_BOUNDS(a.err, 3u, out + got + rank, a.gen.cap)) a.gen.vals[out + got + rank] = r;
+          if (!complement) {
+            const uint32_t j = got + rank;
+            const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
+            const uint32_t other = first_other + r;
+            const uint32_t s = indeg ? other : node, t = indeg ? node : other;
+            store(a.gen, bh, out + j, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+          }
         }
         got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
         __syncwarp();
-      }
-    }
-    if (!complement) {
-      // The slots' draws are independent: two per lane in flight.
-      for (uint32_t j0 = 0; j0 < need; j0 += 64) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t j = j0 + static_cast<uint32_t>(h) * 32u + lane;
-          if (j >= need || !SNC_IN_BOUNDS(a.err, 3u, out + j, a.gen.cap)) continue;
-          const uint32_t r = static_cast<uint32_t>(a.gen.vals[out + j]);
-          const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
-          const uint32_t other = first_other + r;
-          const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-          store(a.gen, bh, out + j, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
-        }
       }
     }
     if (complement) {
