@@ -284,3 +284,16 @@ def test_sparse_samplers_wide_ranges(snc, oracle_mod):
         Projection(src=(60_000, 20_000), tgt=(0, 30_000), rule="pairwise_bernoulli", p=0.002, **WD)])
     got, _ = _build_with_stats(snc, spec)
     assert_network_equal(got, oracle_mod.build(spec), "sparse samplers")
+
+
+def test_redraw_global_tables(snc, oracle_mod):
+    """fixed_total_number without multapses on node ranges too wide for a
+    packed (pair, slot) word (2 x 2.1e6 nodes, 1.1e6 slots: 68 bits) takes the
+    global pair tables instead of buckets; same network as the oracle."""
+    WD = dict(weight=Dist("normal", 20.0, 1.0), delay=Dist("normal", 1.5, 0.75))
+    spec = NetworkSpec(seed=45, dt=0.1, populations=[2_100_000, 2_100_000], projections=[
+        Projection(src=(0, 4_200_000), tgt=(0, 4_200_000), rule="fixed_total_number", k=1_100_000,
+                   autapses=False, multapses=False, **WD),
+        Projection(src=(0, 1000), tgt=(0, 1000), rule="fixed_total_number", k=200_000, autapses=False, **WD)])
+    got, _ = _build_with_stats(snc, spec)
+    assert_network_equal(got, oracle_mod.build(spec), "global tables")
