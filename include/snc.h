@@ -221,6 +221,20 @@ snc_status snc_copy_connections(snc_ctx* ctx, uint32_t* src, uint32_t* tgt, uint
 snc_status snc_copy_index(snc_ctx* ctx, uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
                           uint64_t group_cap);
 
+/* Spike delivery through the index (Sec. 2.3, the spike array).  Entry e of
+ * the spike array names a source node src[e] (network-local id), the index
+ * grp[e] of one of its connection groups (0 = the group of its smallest
+ * delay; the source's groups are group_first[group_ptr[src] ...
+ * group_ptr[src + 1] - 1]) and a multiplicity mult[e].  For every connection
+ * of that group, weight * mult[e] is added to input[target]; input holds
+ * n_nodes floats and is accumulated into, not cleared.  All four arrays are
+ * device memory; the additions run on the context's stream in no fixed
+ * order (fp32 atomics).  Synchronous: returns when the delivery is done.
+ * INVALID_ARG when an entry names no group (the other entries are still
+ * delivered), STATE before snc_finalize. */
+snc_status snc_deliver(snc_ctx* ctx, const uint32_t* src, const uint32_t* grp, const float* mult,
+                       uint64_t n_spikes, float* input);
+
 /* Device time of each finalize stage (ms) after snc_synchronize:
  * [0] count, [1] generate, [2] histogram, [3..3+P) sort passes, then index.
  * *n_stages receives the number written (at most max_stages); *n_passes the

@@ -16,6 +16,10 @@ Parity status (see the pins in tests/test_oracle_*.py):
                     exhaustive subset-frequency tests on tiny ranges
   build             pinned against numpy's stable lexsort, bincount and a
                     per-source distinct-delay count
+  deliver           pinned by the column sums of the weight matrix (every
+                    group of every source once), linearity in the
+                    multiplicity, a hand-computed example and the group
+                    boundaries (tests/test_oracle_deliver.py)
 """
 from __future__ import annotations
 
@@ -191,6 +195,31 @@ def build(spec):
     out = sort_index(spec.n_nodes, g["src"], g["tgt"], g["delay"], g["weight"])
     out["per_proj"] = g["per_proj"]
     return out
+
+
+def deliver(net, n_nodes, src, grp, mult):
+    """Spike delivery through the index of an oracle network (Sec. 2.3):
+    per target the exact input (float64), the sum of |weight * mult| and
+    the number of additions, and the number of entries naming no group."""
+    src = np.ascontiguousarray(src, dtype=np.uint32)
+    grp = np.ascontiguousarray(grp, dtype=np.uint32)
+    mult = np.ascontiguousarray(mult, dtype=np.float32)
+    row_ptr = np.ascontiguousarray(net["row_ptr"], dtype=np.uint64)
+    group_ptr = np.ascontiguousarray(net["group_ptr"], dtype=np.uint64)
+    group_first = np.ascontiguousarray(net["group_first"], dtype=np.uint64)
+    if group_first.size == 0:
+        group_first = np.zeros(1, np.uint64)
+    tgt = np.ascontiguousarray(net["tgt"], dtype=np.uint32)
+    weight = np.ascontiguousarray(net["weight"], dtype=np.float32)
+    inp = np.zeros(max(1, n_nodes), np.float64)
+    absv = np.zeros(max(1, n_nodes), np.float64)
+    terms = np.zeros(max(1, n_nodes), np.uint64)
+    bad = ctypes.c_uint64(0)
+    _check(_lib().or_deliver(ctypes.c_uint32(n_nodes), ctypes.c_uint64(tgt.size), _ptr(row_ptr), _ptr(group_ptr),
+                             _ptr(group_first), _ptr(tgt), _ptr(weight), ctypes.c_uint64(src.size), _ptr(src),
+                             _ptr(grp), _ptr(mult), _ptr(inp), _ptr(absv), _ptr(terms), ctypes.byref(bad)),
+           "deliver")
+    return {"input": inp[:n_nodes], "abs": absv[:n_nodes], "terms": terms[:n_nodes], "bad": int(bad.value)}
 
 
 def generate_primary(spec, proj, primary):

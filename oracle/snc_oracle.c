@@ -853,3 +853,42 @@ int or_sort_index(uint32_t n_nodes, uint64_t n, uint32_t* src, uint32_t* tgt, ui
   *n_groups = g;
   return OR_OK;
 }
+
+/* Spike delivery through the index (Sec. 2.3): entry e of the spike array
+ * names source src[e], the grp[e]-th of its connection groups (groups in
+ * position order, i.e. by increasing delay) and a multiplicity mult[e];
+ * every connection q of that group adds weight[q] * mult[e] to the input of
+ * its target.  The group's connections are positions group_first[g] up to
+ * the next group's first position, or up to row_ptr[src + 1] for the
+ * source's last group.  Accumulated in double precision, entries in order;
+ * abs_in[t] collects |weight * mult| and n_terms[t] the number of additions
+ * (the bound of any fp32 summation order).  *bad counts the entries that name
+ * no group (skipped). */
+int or_deliver(uint32_t n_nodes, uint64_t n_syn, const uint64_t* row_ptr, const uint64_t* group_ptr,
+               const uint64_t* group_first, const uint32_t* tgt, const float* weight, uint64_t n_spikes,
+               const uint32_t* src, const uint32_t* grp, const float* mult, double* input, double* abs_in,
+               uint64_t* n_terms, uint64_t* bad) {
+  *bad = 0;
+  for (uint32_t t = 0; t < n_nodes; ++t) {
+    input[t] = 0.0;
+    abs_in[t] = 0.0;
+    n_terms[t] = 0;
+  }
+  for (uint64_t e = 0; e < n_spikes; ++e) {
+    const uint32_t s = src[e];
+    if (s >= n_nodes || (uint64_t)grp[e] >= group_ptr[s + 1] - group_ptr[s]) {
+      *bad += 1;
+      continue;
+    }
+    const uint64_t g = group_ptr[s] + grp[e];
+    const uint64_t first = group_first[g];
+    const uint64_t last = g + 1 < group_ptr[s + 1] ? group_first[g + 1] : row_ptr[s + 1];
+    for (uint64_t q = first; q < last && q < n_syn; ++q) {
+      const double x = (double)weight[q] * (double)mult[e];
+      input[tgt[q]] += x;
+      abs_in[tgt[q]] += x < 0 ? -x : x;
+      n_terms[tgt[q]] += 1;
+    }
+  }
+  return OR_OK;
+}

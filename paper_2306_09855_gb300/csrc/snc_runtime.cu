@@ -21,6 +21,7 @@
 #include "snc_internal.h"
 #include "sort_kernels.h"
 #include "source_major.h"
+#include "deliver.h"
 
 using namespace snc;
 
@@ -1551,6 +1552,57 @@ snc_status snc_get_connections(snc_ctx* c, snc_conn_view* out) {
   out->weight = c->weight;
   out->group_ptr = c->group_ptr;
   out->group_first = c->group_first;
+  return SNC_OK;
+}
+
+snc_status snc_deliver(snc_ctx* c, const uint32_t* src, const uint32_t* grp, const float* mult,
+                       uint64_t n_spikes, float* input) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (!c->finalized) return fail(c, SNC_ERR_STATE, "deliver before finalize");
+  snc_conn_view v{};
+  snc_status s = snc_get_connections(c, &v);  // synchronizes and resolves the views
+  if (s != SNC_OK) return s;
+  if (n_spikes == 0) return SNC_OK;
+  if (!src || !grp || !mult || !input) return fail(c, SNC_ERR_INVALID_ARG, "null spike array or input");
+  cudaStream_t st = c->store->stream;
+  uint32_t* sizes = static_cast<uint32_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint32_t)));
+  uint64_t* offsets = static_cast<uint64_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint64_t)));
+  uint64_t* tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_spikes) + 1) * sizeof(uint64_t)));
+  uint32_t* err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint32_t)));
+  if (!sizes || !offsets || !tmp || !err) return fail(c, SNC_ERR_OOM, "device allocation failed (spike array)");
+  SNC_CUDA(c, cudaMemsetAsync(err, 0, 8 * sizeof(uint32_t), st));
+  DeliverArgs a{};
+  a.src = src;
+  a.grp = grp;
+  a.mult = mult;
+  a.n_spikes = n_spikes;
+  a.row_ptr = v.row_ptr;
+  a.group_ptr = v.group_ptr;
+  a.group_first = v.group_first;
+  a.target = v.target;
+  a.weight = v.weight;
+  a.n_nodes = v.n_nodes;
+  a.n_syn = v.n_syn;
+  a.sizes = sizes;
+  a.offsets = offsets;
+  a.input = input;
+  a.err = err;
+  const unsigned g1 = static_cast<unsigned>(
+      std::max<uint64_t>(1, std::min<uint64_t>((n_spikes + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
+  deliver_size_kernel<<<g1, 256, 0, st>>>(a);
+  SNC_CUDA(c, exclusive_scan_u32(sizes, n_spikes, offsets, tmp, st));
+  deliver_kernel<<<static_cast<unsigned>(c->sms) * 8, kDeliverThreads, 0, st>>>(a);
+  SNC_CUDA(c, cudaGetLastError());
+  c->stats.kernel_launches += 5;
+  uint32_t* h_err = reinterpret_cast<uint32_t*>(c->store->h_pinned + 12);
+  SNC_CUDA(c, cudaMemcpyAsync(h_err, err, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  SNC_CUDA(c, cudaStreamSynchronize(st));
+  const uint32_t bits = h_err[0];
+  dev_free(c, sizes);
+  dev_free(c, offsets);
+  dev_free(c, tmp);
+  dev_free(c, err);
+  if (bits & kErrBounds) return fail(c, SNC_ERR_INVALID_ARG, "a spike array entry names no connection group");
   return SNC_OK;
 }
 

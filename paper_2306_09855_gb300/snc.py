@@ -110,7 +110,7 @@ SNC_JOB_QUEUED, SNC_JOB_RUNNING, SNC_JOB_DONE, SNC_JOB_FAILED = range(4)
 # Every symbol include/snc.h and include/snc_server.h declare.
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_copy_index",
-           "snc_stage_times",
+           "snc_deliver", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
            "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_batch_finalize_graph",
            "snc_batch_rebuild", "snc_last_error",
@@ -145,6 +145,7 @@ def load(build: bool = True):
         "snc_get_connections": ([P, ctypes.POINTER(snc_conn_view)], I32),
         "snc_copy_connections": ([P, P, P, P, P, U64], I32),
         "snc_copy_index": ([P, P, P, P, U64], I32),
+        "snc_deliver": ([P, P, P, P, U64, P], I32),
         "snc_stage_times": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(I32),
                              ctypes.POINTER(I32)], I32),
         "snc_radix_sort_pairs": ([P, P, P, P, U64, I32, P], I32),
@@ -266,6 +267,12 @@ def snc_copy_index(ctx, n_nodes, n_groups, out=None):
     _check(load().snc_copy_index(ctx, out["row_ptr"].ctypes.data, out["group_ptr"].ctypes.data,
                                  out["group_first"].ctypes.data, out["group_first"].size), ctx)
     return out
+
+
+def snc_deliver(ctx, src_ptr, grp_ptr, mult_ptr, n_spikes, input_ptr):
+    """Deliver a spike array (device pointers: uint32 sources, uint32 group
+    indices, float multiplicities) into the float input array of n_nodes."""
+    _check(load().snc_deliver(ctx, src_ptr, grp_ptr, mult_ptr, int(n_spikes), input_ptr), ctx)
 
 
 def snc_stage_times(ctx):
@@ -557,6 +564,18 @@ class Network:
 
     def view(self):
         return snc_get_connections(self.ctx)
+
+    def deliver(self, src, grp, mult, input):
+        """Deliver a spike array given as device tensors (int32/uint32 sources
+        and group indices, float32 multiplicities) into the float32 `input`
+        tensor of n_nodes entries (accumulated)."""
+        n = int(src.numel())
+        if int(grp.numel()) != n or int(mult.numel()) != n:
+            raise ValueError("src, grp and mult need the same length")
+        for t, size in ((src, 4), (grp, 4), (mult, 4), (input, 4)):
+            if not t.is_cuda or t.element_size() != size or not t.is_contiguous():
+                raise ValueError("spike arrays and input must be contiguous 4-byte device tensors")
+        snc_deliver(self.ctx, src.data_ptr(), grp.data_ptr(), mult.data_ptr(), n, input.data_ptr())
 
     def tensors(self):
         """Zero-copy torch views of the device arrays."""
