@@ -42,7 +42,7 @@ def parse_args():
     ap.add_argument("--workload", default="rule_sweep",
                     choices=["rule_sweep", "microcircuit", "plain", "small", "profile", "profile_total",
                              "profile_sampler", "profile_bernoulli", "profile_outdegree", "batched", "served",
-                             "trials", "deliver"])
+                             "trials", "deliver", "profile_deliver"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sort-digit-bits", type=int, default=None, help="tuning: widest radix digit")
     ap.add_argument("--sort-group-tiles", type=int, default=None, help="tuning: tiles per look-back unit")
@@ -436,7 +436,8 @@ def run_deliver(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     snc.load()
-    spec = W.rule_sweep("fixed_indegree", True)
+    small = args.workload == "profile_deliver"
+    spec = W.two_population(100_000, "fixed_indegree", k=100) if small else W.rule_sweep("fixed_indegree", True)
     stream = torch.cuda.current_stream()
     net = snc.Network(spec, stream=stream).finalize()
     v = net.view()
@@ -444,7 +445,7 @@ def run_deliver(args):
     gp = torch.empty(n_nodes + 1, dtype=torch.int64, device="cuda")
     host = snc.snc_copy_index(net.ctx, n_nodes, int(v.n_groups))
     gp.copy_(torch.from_numpy(host["group_ptr"].view(np.int64)))
-    n_spikes = 1_000_000
+    n_spikes = 200_000 if small else 1_000_000
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1234)
     groups = (gp[1:] - gp[:-1])
@@ -496,8 +497,10 @@ def run_deliver(args):
         "metric": "spike deliveries/sec (connections delivered through the index) on 1 GB300", "value": n_conn / (ms / 1e3),
         "unit": "connections/s", "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "spike delivery: rule-sweep fixed_indegree network (2 x 100,000 nodes, K=1000, 4e8 "
-                               "connections), 10^6 spike-array entries per step (random source and group)",
+        "config": {"workload": ("profiling case: fixed_indegree 2 x 100,000 nodes, K=100 (4e7 connections), "
+                                "2e5 spike-array entries per step") if small else
+                               ("spike delivery: rule-sweep fixed_indegree network (2 x 100,000 nodes, K=1000, 4e8 "
+                                "connections), 10^6 spike-array entries per step (random source and group)"),
                    "connections_per_step": n_conn // max(1, steps), "l2": "target and weight arrays larger than L2"},
         "roofline": {"bound": "hbm", "kernel": "deliver_kernel", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
@@ -521,7 +524,7 @@ def main():
     if args.workload == "trials":
         run_trials(args)
         return
-    if args.workload == "deliver":
+    if args.workload in ("deliver", "profile_deliver"):
         run_deliver(args)
         return
     import torch
