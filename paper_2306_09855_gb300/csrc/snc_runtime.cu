@@ -293,28 +293,6 @@ void dev_free(snc_ctx* c, void* p) { c->store->put(p); }
 
 // Host -> device copy through the build's pinned staging area; *staged
 // receives the staged host copy.
-__global__ void copy_words_kernel(uint64_t* dst, const uint64_t* src, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
-}
-
-// Small device -> host read into page-locked memory: a one-block kernel
-// stores the words through the buffer's device mapping, so the read does not
-// wait behind large copies that other streams have queued on the copy
-// engines (a build's count and pending-list reads would otherwise stall
-// behind another network's copy to the host).  A plain copy where the
-// buffer has no device mapping.
-cudaError_t read_small(snc_ctx* c, uint64_t* h_dst, const uint64_t* d_src, size_t n_words, cudaStream_t st) {
-  c->stats.d2h_bytes += n_words * sizeof(uint64_t);
-  void* mapped = nullptr;
-  if (n_words <= 4096 && cudaHostGetDevicePointer(&mapped, h_dst, 0) == cudaSuccess && mapped) {
-    copy_words_kernel<<<1, 256, 0, st>>>(static_cast<uint64_t*>(mapped), d_src, static_cast<int>(n_words));
-    ++c->stats.kernel_launches;
-    return cudaGetLastError();
-  }
-  cudaGetLastError();  // no mapping: clear the query's error
-  return cudaMemcpyAsync(h_dst, d_src, n_words * sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
-}
-
 cudaError_t upload(snc_ctx* c, void* dst, const void* src, size_t bytes, void** staged = nullptr) {
   if (bytes == 0) return cudaSuccess;
   void* h = c->store->stage(src, bytes);
@@ -738,13 +716,11 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     segment_totals_kernel<<<(nb + 255) / 256, 256, 0, st>>>(d_prim_off, d_bprefix, nb, d_totals);
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
-    uint64_t* totals = static_cast<uint64_t*>(pinned_pool().get(bern.size() * sizeof(uint64_t)));
-    if (!totals) return fail(c, SNC_ERR_OOM, "pinned allocation failed (Bernoulli totals)");
-    const cudaError_t re = read_small(c, totals, d_totals, bern.size(), st);
-    const cudaError_t se = re == cudaSuccess ? cudaStreamSynchronize(st) : re;
-    for (size_t bi = 0; bi < bern.size() && se == cudaSuccess; ++bi) cnt[bern[bi]] = totals[bi];
-    pinned_pool().put(totals, bern.size() * sizeof(uint64_t));
-    SNC_CUDA(c, se);
+    std::vector<uint64_t> totals(bern.size());
+    SNC_CUDA(c, cudaMemcpyAsync(totals.data(), d_totals, bern.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    c->stats.d2h_bytes += bern.size() * sizeof(uint64_t);
+    SNC_CUDA(c, cudaStreamSynchronize(st));
+    for (size_t bi = 0; bi < bern.size(); ++bi) cnt[bern[bi]] = totals[bi];
     dev_free(c, d_counts);
     dev_free(c, d_scan_tmp);
     dev_free(c, d_blist);
@@ -1135,7 +1111,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       uint64_t* pending = pend_a;
       uint64_t* next = pend_b;
       for (uint32_t round = 1;; ++round) {
-        SNC_CUDA(c, read_small(c, S.h_pinned, reinterpret_cast<const uint64_t*>(a.n_next), 1, st));
+        SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned, a.n_next, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        c->stats.d2h_bytes += sizeof(uint64_t);
         SNC_CUDA(c, cudaStreamSynchronize(st));
         const uint64_t n_pend = S.h_pinned[0];
         if (n_pend == 0) break;
@@ -1362,7 +1339,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     S.h_bases = static_cast<uint64_t*>(pinned_pool().get(S.h_bases_words * sizeof(uint64_t)));
     if (!S.h_bases) return fail(c, SNC_ERR_OOM, "pinned allocation failed (views)");
   }
-  SNC_CUDA(c, read_small(c, S.h_bases, S.d_bases, static_cast<size_t>(n_members) + 1, st));
+  SNC_CUDA(c, cudaMemcpyAsync(S.h_bases, S.d_bases, (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t),
+                              cudaMemcpyDeviceToHost, st));
+  c->stats.d2h_bytes += (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t);
   mark();
   dev_free(c, starts);
   dev_free(c, bcounts);
@@ -1528,8 +1507,9 @@ snc_status snc_synchronize(snc_ctx* c) {
   SNC_CUDA(c, cudaStreamSynchronize(S.stream));
   if (!c->finalized) return SNC_OK;
   if (!S.synced) {
-    SNC_CUDA(c, read_small(c, S.h_pinned + 4, reinterpret_cast<const uint64_t*>(S.d_err), 4, S.stream));
-    SNC_CUDA(c, read_small(c, S.h_pinned + 1, S.d_n_groups, 1, S.stream));
+    SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + 4, S.d_err, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, S.stream));
+    SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + 1, S.d_n_groups, sizeof(uint64_t), cudaMemcpyDeviceToHost, S.stream));
+    c->stats.d2h_bytes += 5 * sizeof(uint64_t);
     SNC_CUDA(c, cudaStreamSynchronize(S.stream));
     S.err_bits = static_cast<uint32_t>(S.h_pinned[4] & 0xFFFFFFFFu);
     S.n_groups = S.h_pinned[1];
@@ -1614,9 +1594,10 @@ snc_status snc_deliver(snc_ctx* c, const uint32_t* src, const uint32_t* grp, con
   deliver_kernel<<<static_cast<unsigned>(c->sms) * 8, kDeliverThreads, 0, st>>>(a);
   SNC_CUDA(c, cudaGetLastError());
   c->stats.kernel_launches += 5;
-  SNC_CUDA(c, read_small(c, c->store->h_pinned + 12, reinterpret_cast<const uint64_t*>(err), 1, st));
+  uint32_t* h_err = reinterpret_cast<uint32_t*>(c->store->h_pinned + 12);
+  SNC_CUDA(c, cudaMemcpyAsync(h_err, err, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   SNC_CUDA(c, cudaStreamSynchronize(st));
-  const uint32_t bits = static_cast<uint32_t>(c->store->h_pinned[12] & 0xFFFFFFFFu);
+  const uint32_t bits = h_err[0];
   dev_free(c, sizes);
   dev_free(c, offsets);
   dev_free(c, tmp);
