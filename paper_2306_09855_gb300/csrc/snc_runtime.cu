@@ -293,21 +293,6 @@ void dev_free(snc_ctx* c, void* p) { c->store->put(p); }
 
 // Host -> device copy through the build's pinned staging area; *staged
 // receives the staged host copy.
-// Large device -> host copy in pieces of 64 MB: the copy engines take the
-// pieces of several streams in turn, so a small read of another build (a
-// count, a pending-list length) waits for one piece instead of a whole
-// network's arrays.
-cudaError_t copy_to_host(void* dst, const void* src, size_t bytes, cudaStream_t st) {
-  constexpr size_t kPiece = 64ull << 20;
-  for (size_t off = 0; off < bytes; off += kPiece) {
-    const size_t len = bytes - off < kPiece ? bytes - off : kPiece;
-    const cudaError_t e = cudaMemcpyAsync(static_cast<char*>(dst) + off, static_cast<const char*>(src) + off, len,
-                                          cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
 cudaError_t upload(snc_ctx* c, void* dst, const void* src, size_t bytes, void** staged = nullptr) {
   if (bytes == 0) return cudaSuccess;
   void* h = c->store->stage(src, bytes);
@@ -1639,12 +1624,12 @@ snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16
       ++c->stats.kernel_launches;
     }
     SNC_CUDA(c, cudaGetLastError());
-    SNC_CUDA(c, copy_to_host(src, d_src, n * sizeof(uint32_t), st));
+    SNC_CUDA(c, cudaMemcpyAsync(src, d_src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     dev_free(c, d_src);  // stream-ordered: after the copy
   }
-  if (tgt && n > 0) SNC_CUDA(c, copy_to_host(tgt, c->target, n * sizeof(uint32_t), st));
-  if (delay && n > 0) SNC_CUDA(c, copy_to_host(delay, c->delay, n * sizeof(uint16_t), st));
-  if (weight && n > 0) SNC_CUDA(c, copy_to_host(weight, c->weight, n * sizeof(float), st));
+  if (tgt && n > 0) SNC_CUDA(c, cudaMemcpyAsync(tgt, c->target, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (delay && n > 0) SNC_CUDA(c, cudaMemcpyAsync(delay, c->delay, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
+  if (weight && n > 0) SNC_CUDA(c, cudaMemcpyAsync(weight, c->weight, n * sizeof(float), cudaMemcpyDeviceToHost, st));
   c->stats.d2h_bytes += n * ((src ? 4 : 0) + (tgt ? 4 : 0) + (delay ? 2 : 0) + (weight ? 4 : 0));
   SNC_CUDA(c, cudaStreamSynchronize(st));
   return SNC_OK;
@@ -1662,7 +1647,7 @@ snc_status snc_copy_index(snc_ctx* c, uint64_t* row_ptr, uint64_t* group_ptr, ui
   if (row_ptr) SNC_CUDA(c, cudaMemcpyAsync(row_ptr, c->row_ptr, rows, cudaMemcpyDeviceToHost, st));
   if (group_ptr) SNC_CUDA(c, cudaMemcpyAsync(group_ptr, c->group_ptr, rows, cudaMemcpyDeviceToHost, st));
   if (group_first && c->n_groups > 0)
-    SNC_CUDA(c, copy_to_host(group_first, c->group_first, c->n_groups * sizeof(uint64_t), st));
+    SNC_CUDA(c, cudaMemcpyAsync(group_first, c->group_first, c->n_groups * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
   c->stats.d2h_bytes += (row_ptr ? rows : 0) + (group_ptr ? rows : 0) + (group_first ? c->n_groups * sizeof(uint64_t) : 0);
   SNC_CUDA(c, cudaStreamSynchronize(st));
   return SNC_OK;
