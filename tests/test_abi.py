@@ -58,3 +58,27 @@ def test_server_config_checks_need_no_gpu():
             call()
         assert e.value.name == "INVALID_ARG"
     snc.snc_server_destroy(None)
+
+
+def test_tuning_ranges_need_no_gpu():
+    from paper_2306_09855_gb300 import snc
+    old = snc.snc_get_tuning()
+    try:
+        for items in (8, 12, 16, 24, 32):
+            snc.snc_set_tuning(sort_items=items)
+            assert snc.snc_get_tuning().sort_items == items
+        for bad in ({"sort_items": 20}, {"sort_items": 64}, {"sort_digit_bits": 12}, {"sort_group_tiles": 3},
+                    {"gen_blocks_per_sm": 0}):
+            with pytest.raises(snc.SncError) as e:
+                snc.snc_set_tuning(**bad)
+            assert e.value.name == "INVALID_ARG"
+    finally:
+        snc.snc_set_tuning(sort_digit_bits=old.sort_digit_bits, sort_group_tiles=old.sort_group_tiles,
+                           gen_blocks_per_sm=old.gen_blocks_per_sm, sort_items=old.sort_items)
+
+
+def test_deliver_argument_checks_need_no_gpu():
+    from paper_2306_09855_gb300 import snc
+    with pytest.raises(snc.SncError) as e:
+        snc.snc_deliver(None, 0, 0, 0, 10, 0)
+    assert e.value.name == "INVALID_ARG"
