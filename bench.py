@@ -642,9 +642,9 @@ def main():
     # plans on the host, copies the plans in, builds, and copies the whole
     # network as the device holds it (target, delay, weight: 10 B per
     # connection, plus row_ptr, p_i and group_first) back into page-locked
-    # host arrays, all inside the host wall-clock region.  Three host threads,
+    # host arrays, all inside the host wall-clock region.  Two host threads,
     # each with its own stream and host arrays, take the networks in turn,
-    # so that one network's copy to the host overlaps the next ones' builds.
+    # so that one network's copy to the host overlaps the next one's build.
     import threading
     max_syn = max(r[0] for r in records) if records else 0
     max_groups = max(max(r[4] for r in records), max_syn if batched else 0) if records else 0
@@ -661,7 +661,7 @@ def main():
                 "row_ptr": h["row_ptr"].view(np.uint64), "group_ptr": h["group_ptr"].view(np.uint64),
                 "group_first": h["group_first"].view(np.uint64)}
 
-    n_workers = 1 if batched else 3
+    n_workers = 1 if batched else 2
     hosts = [host_arrays() for _ in range(n_workers)]
     streams = [torch.cuda.Stream(device=local) for _ in range(n_workers)]
     totals = [[0, 0, 0] for _ in range(n_workers)]  # connections, h2d, d2h
@@ -742,7 +742,7 @@ def main():
                 "d2h_bytes_per_step": d2h,
                 "note": "public API, host wall clock: plan, build, and copy of each network as held on the "
                         "device (target, delay, weight: 10 B per connection; row_ptr, p_i, group_first) into "
-                        "page-locked host arrays; three host threads with their own streams overlap one "
+                        "page-locked host arrays; two host threads with their own streams overlap one "
                         "network's copy with the next one's build"},
         "clocks": clk,
     }
