@@ -433,8 +433,9 @@ __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
 }
 
 // ---------------------------------------------------------------------------
-// TMA-fed onesweep pass for 8- and 9-bit digits (one look-back per 4096-key
-// tile).  A persistent block takes tiles from the ticket; one thread issues
+// TMA-fed onesweep pass for 8- and 9-bit digits (one look-back per tile of
+// 256 threads x ITEMS keys, 2,048 to 8,192).  A persistent block takes tiles
+// from the ticket; one thread issues
 // two bulk copies (cp.async.bulk, completion on an mbarrier) that bring the
 // tile's keys and values into shared memory, so the ranking reads keys from
 // shared memory and all tile-local indices are 32-bit.  After the keys are in
