@@ -1,10 +1,10 @@
 // gen_kernels.cu -- connection generation directly in GPU memory (Sec. 2.1).
 //
 // Every kernel writes, for connection number `pos` of the concatenated
-// generation order, the packed sort key (source | delay step | target) and
-// the weight bits.  The paper's index formulas decide (source, target); the
-// counter-based stream decides every random quantity, so the output does not
-// depend on grid or block sizes.
+// generation order, the packed sort key (source | delay step) and the value
+// (target | weight bits).  The paper's index formulas decide (source,
+// target); the counter-based stream decides every random quantity, so the
+// output does not depend on grid or block sizes.
 //
 //   gen_direct_kernel   one_to_one, all_to_all, in/out-degree with multapses,
 //                       fixed_total_number with multapses and autapses
@@ -12,9 +12,10 @@
 //   sampler_kernel      in/out-degree without multapses and the Bernoulli
 //                       subsets: one warp per primary node, distinct draws
 //                       tracked in a shared-memory bitmap
-//   total_*             fixed_total_number with autapses or multapses
-//                       forbidden: round-based redraws, duplicates found with a
-//                       device hash table
+//   redraw_*            fixed_total_number with autapses or multapses
+//                       forbidden: round-based redraws; duplicates found per
+//                       hash bucket in shared memory (global pair tables when
+//                       a (pair, slot) entry does not fit 63 bits)
 #include <cuda_runtime.h>
 
 #include <cstdint>
