@@ -238,7 +238,9 @@ snc_status snc_deliver(snc_ctx* ctx, const uint32_t* src, const uint32_t* grp, c
 /* Device time of each finalize stage (ms) after snc_synchronize:
  * [0] count, [1] generate, [2] histogram, [3..3+P) sort passes, then index.
  * *n_stages receives the number written (at most max_stages); *n_passes the
- * number of radix passes P.  STATE before a finalize has completed. */
+ * number of sort stages P: the radix passes, or 1 when the build was sorted
+ * per source (snc_stats.source_major; [2] is then the per-source offsets and
+ * [3] the per-source sort).  STATE before a finalize has completed. */
 snc_status snc_stage_times(snc_ctx* ctx, float* ms, int max_stages, int* n_stages, int* n_passes);
 
 /* Process-wide kernel parameters (the autotuner's knobs).  They change
