@@ -34,6 +34,7 @@ __global__ void deliver_size_kernel(DeliverArgs a) {
       size = 0;
     }
     a.sizes[e] = static_cast<uint32_t>(size);
+    a.first[e] = start;
   }
 }
 
@@ -62,9 +63,7 @@ __global__ void __launch_bounds__(kDeliverThreads) deliver_kernel(DeliverArgs a)
       const uint64_t q = q0 + static_cast<uint64_t>(j) * kDeliverThreads + threadIdx.x;
       if (q >= total) break;
       const uint64_t e = entry_of(q, lo, hi);
-      uint64_t start = 0, size = 0;
-      if (!group_range(a, a.src[e], a.grp[e], start, size)) continue;  // reported by the size kernel
-      const uint64_t c = start + (q - a.offsets[e]);
+      const uint64_t c = a.first[e] + (q - a.offsets[e]);  // invalid entries own no q
       if (!SNC_IN_BOUNDS(a.err, 40u, c, a.n_syn)) continue;
       const uint32_t t = a.target[c];
       if (!SNC_IN_BOUNDS(a.err, 41u, t, a.n_nodes)) continue;

@@ -28,13 +28,15 @@ struct DeliverArgs {
   uint64_t n_nodes;
   uint64_t n_syn;
   uint32_t* sizes;              // [n_spikes]: connections of each entry's group (0 if invalid)
+  uint64_t* first;              // [n_spikes]: first connection of each entry's group
   const uint64_t* offsets;      // [n_spikes + 1]: exclusive scan of sizes
   float* input;                 // [n_nodes], accumulated into
   uint32_t* err;
 };
 
-// sizes[e] = connections in entry e's group; an entry outside the index
-// sets the bounds bit of the error word and delivers nothing.
+// sizes[e] = connections in entry e's group and first[e] its first
+// connection; an entry outside the index sets the bounds bit of the error
+// word and delivers nothing.
 __global__ void deliver_size_kernel(DeliverArgs a);
 // One thread per delivered connection (block ranges of
 // kDeliverThreads * kDeliverItems connections).

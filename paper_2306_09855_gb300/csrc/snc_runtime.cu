@@ -1568,8 +1568,10 @@ snc_status snc_deliver(snc_ctx* c, const uint32_t* src, const uint32_t* grp, con
   uint32_t* sizes = static_cast<uint32_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint32_t)));
   uint64_t* offsets = static_cast<uint64_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint64_t)));
   uint64_t* tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_spikes) + 1) * sizeof(uint64_t)));
+  uint64_t* first = static_cast<uint64_t*>(dev_alloc(c, n_spikes * sizeof(uint64_t)));
   uint32_t* err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint32_t)));
-  if (!sizes || !offsets || !tmp || !err) return fail(c, SNC_ERR_OOM, "device allocation failed (spike array)");
+  if (!sizes || !offsets || !tmp || !first || !err)
+    return fail(c, SNC_ERR_OOM, "device allocation failed (spike array)");
   SNC_CUDA(c, cudaMemsetAsync(err, 0, 8 * sizeof(uint32_t), st));
   DeliverArgs a{};
   a.src = src;
@@ -1584,6 +1586,7 @@ snc_status snc_deliver(snc_ctx* c, const uint32_t* src, const uint32_t* grp, con
   a.n_nodes = v.n_nodes;
   a.n_syn = v.n_syn;
   a.sizes = sizes;
+  a.first = first;
   a.offsets = offsets;
   a.input = input;
   a.err = err;
@@ -1601,6 +1604,7 @@ snc_status snc_deliver(snc_ctx* c, const uint32_t* src, const uint32_t* grp, con
   dev_free(c, sizes);
   dev_free(c, offsets);
   dev_free(c, tmp);
+  dev_free(c, first);
   dev_free(c, err);
   if (bits & kErrBounds) return fail(c, SNC_ERR_INVALID_ARG, "a spike array entry names no connection group");
   return SNC_OK;
