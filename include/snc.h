@@ -221,6 +221,17 @@ snc_status snc_copy_connections(snc_ctx* ctx, uint32_t* src, uint32_t* tgt, uint
 snc_status snc_copy_index(snc_ctx* ctx, uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
                           uint64_t group_cap);
 
+/* Target shard (Sec. 4 names target-distributed construction as future
+ * work): the build keeps only the connections whose target node is in
+ * [first, first + n).  Every draw is keyed by (projection, node, slot), so a
+ * rank that builds its shard regenerates exactly the connections the whole
+ * network would give it, with no exchange between ranks; the shard's
+ * connections come in the whole network's (source, delay, generation)
+ * order, indexed over all source nodes.  Before snc_finalize (STATE after);
+ * INVALID_ARG at snc_finalize when the range exceeds the nodes, and in a
+ * batch.  Graph builds refuse sharded contexts (UNSUPPORTED). */
+snc_status snc_set_target_shard(snc_ctx* ctx, uint32_t first, uint32_t n);
+
 /* Spike delivery through the index (Sec. 2.3, the spike array).  Entry e of
  * the spike array names a source node src[e] (network-local id), the index
  * grp[e] of one of its connection groups (0 = the group of its smallest

@@ -264,4 +264,31 @@ __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes,
   }
 }
 
+// Target shards: flags[i] = 1 when connection i's target (the value's high
+// word) lies in [first, first + count).
+__global__ void shard_flag_kernel(const uint64_t* vals, uint64_t n, uint32_t first, uint32_t count, uint32_t* flags) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t t = static_cast<uint32_t>(vals[i] >> 32);
+    flags[i] = (t >= first && t - first < count) ? 1u : 0u;
+  }
+}
+
+// Keeps the flagged connections, in generation order, at their scanned
+// positions (offsets = exclusive scan of the flags).
+__global__ void shard_compact_kernel(const void* keys_in, const uint64_t* vals_in, int key32, uint64_t n,
+                                     const uint64_t* offsets, uint32_t first, uint32_t count, void* keys_out,
+                                     uint64_t* vals_out) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t v = vals_in[i];
+    const uint32_t t = static_cast<uint32_t>(v >> 32);
+    if (!(t >= first && t - first < count)) continue;
+    const uint64_t o = offsets[i];
+    if (key32) static_cast<uint32_t*>(keys_out)[o] = static_cast<const uint32_t*>(keys_in)[i];
+    else static_cast<uint64_t*>(keys_out)[o] = static_cast<const uint64_t*>(keys_in)[i];
+    vals_out[o] = v;
+  }
+}
+
 }  // namespace snc

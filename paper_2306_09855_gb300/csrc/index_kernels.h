@@ -65,5 +65,11 @@ cudaError_t launch_member_index(const MemberIndexArgs& a, cudaStream_t st);
 __global__ void rebase_group_first_kernel(uint64_t* group_first, const uint64_t* n_groups, uint64_t group_cap,
                                           const uint64_t* gfirst, const uint64_t* seg_begin, int n_members);
 __global__ void expand_sources_kernel(const uint64_t* row_ptr, uint64_t n_nodes, uint32_t* src);
+// Target shards: flag the connections whose target is in [first, first +
+// count), then keep them in generation order.
+__global__ void shard_flag_kernel(const uint64_t* vals, uint64_t n, uint32_t first, uint32_t count, uint32_t* flags);
+__global__ void shard_compact_kernel(const void* keys_in, const uint64_t* vals_in, int key32, uint64_t n,
+                                     const uint64_t* offsets, uint32_t first, uint32_t count, void* keys_out,
+                                     uint64_t* vals_out);
 
 }  // namespace snc

@@ -240,6 +240,10 @@ struct snc_ctx {
   int member = 0;
   uint64_t node_base = 0;
   int sort_stages = 0;  // timed sort stages of the last build (radix passes, or 1 for the source-major sort)
+  // Target shard: keep only the connections whose target is in
+  // [shard_first, shard_first + shard_n) (snc_set_target_shard).
+  bool sharded = false;
+  uint32_t shard_first = 0, shard_n = 0;
   // Results: device views; for batch members resolved at synchronize (and
   // again after every graph replay of the build).
   bool view_ready = false;
@@ -792,8 +796,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   }
 
   // Buffers: generated keys/values, the sort's second buffer, outputs.
-  const uint64_t n = n_total;
+  uint64_t n = n_total;  // connections; a target shard keeps fewer after generation
   const bool segmented = n_members > 1;
+  const bool sharded = !segmented && c->sharded;
   // A single network whose projections all generate source by source
   // (one_to_one, all_to_all, fixed_outdegree) is sorted per source by delay
   // step instead of by radix passes.
@@ -801,7 +806,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // (one_to_one and long all_to_all rows stay on the radix sort, which was
   // measured faster there).
   const uint64_t per_source = n / std::max<uint64_t>(1, total_nodes);
-  bool src_major = !segmented && np > 0 && np <= static_cast<size_t>(kSrcMajorMaxProj) &&
+  bool src_major = !segmented && !sharded && np > 0 && np <= static_cast<size_t>(kSrcMajorMaxProj) &&
                    c->layout.delay_bits <= kSrcMajorMaxDelayBits && per_source >= 64 &&
                    per_source <= 2 * static_cast<uint64_t>(kSrcMajorChunk);
   for (size_t i = 0; i < np && src_major; ++i) src_major = source_major_rule(dp[i].rule);
@@ -845,10 +850,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // (a segmented sort counts per segment itself).
   const SortScratch sort_lay = segmented ? sort_scratch_layout(sort_scratch, n, c->passes, n_seg_tiles, n_members)
                                          : sort_scratch_layout(sort_scratch, n, c->passes);
-  if (!segmented && !src_major)
+  // (A target shard counts the digits of the kept connections in the sort.)
+  const bool gen_counts = !segmented && !src_major && !sharded;
+  if (gen_counts)
     SNC_CUDA(c, cudaMemsetAsync(sort_lay.hist, 0,
                                 static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long), st));
-  const HistPlan hplan = hist_plan(c->passes, (segmented || src_major) ? nullptr : sort_lay.hist);
+  const HistPlan hplan = hist_plan(c->passes, gen_counts ? sort_lay.hist : nullptr);
   const size_t hist_bytes = hist_smem_bytes(hplan);
 
   // Generation.
@@ -1157,6 +1164,34 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   }
   mark();
 
+  // Target shard: keep the connections whose target is in the shard, in
+  // generation order (so the stable sort below gives the full network's
+  // order restricted to them), compacted into the second buffer pair.
+  if (sharded && n > 0) {
+    uint32_t* flags = static_cast<uint32_t*>(dev_alloc(c, (n + 1) * sizeof(uint32_t)));
+    uint64_t* offs = static_cast<uint64_t*>(dev_alloc(c, (n + 1) * sizeof(uint64_t)));
+    uint64_t* tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n) + 1) * sizeof(uint64_t)));
+    if (!flags || !offs || !tmp) return fail(c, SNC_ERR_OOM, "device allocation failed (target shard)");
+    const unsigned fg = static_cast<unsigned>(
+        std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
+    shard_flag_kernel<<<fg, 256, 0, st>>>(vals_a, n, c->shard_first, c->shard_n, flags);
+    SNC_CUDA(c, exclusive_scan_u32(flags, n, offs, tmp, st));
+    shard_compact_kernel<<<fg, 256, 0, st>>>(keys_a, vals_a, key32 ? 1 : 0, n, offs, c->shard_first, c->shard_n,
+                                             keys_b, vals_b);
+    SNC_CUDA(c, cudaGetLastError());
+    c->stats.kernel_launches += 5;
+    SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned, offs + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    c->stats.d2h_bytes += sizeof(uint64_t);
+    SNC_CUDA(c, cudaStreamSynchronize(st));
+    n = S.h_pinned[0];
+    seg_end[0] = seg_begin[0] + n;
+    std::swap(keys_a, keys_b);
+    std::swap(vals_a, vals_b);
+    dev_free(c, flags);
+    dev_free(c, offs);
+    dev_free(c, tmp);
+  }
+
   // Stable sort by (source, delay): equal keys keep generation order.  The
   // passes ping-pong between the two buffers; the result lands in
   // (keys_b, vals_b) for an odd number of passes and back in (keys_a,
@@ -1236,11 +1271,11 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   } else if (key32)
     SNC_CUDA(c, radix_sort_run(static_cast<const uint32_t*>(keys_a), vals_a, static_cast<uint32_t*>(keys_res), vals_res,
                                static_cast<uint32_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused, seg_arg));
+                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/!sharded, &unpack, &fused, seg_arg));
   else
     SNC_CUDA(c, radix_sort_run(static_cast<const uint64_t*>(keys_a), vals_a, static_cast<uint64_t*>(keys_res), vals_res,
                                static_cast<uint64_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/true, &unpack, &fused, seg_arg));
+                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/!sharded, &unpack, &fused, seg_arg));
   if (!src_major) {
     if (!S.capturing) S.n_ev += c->passes.n_passes + 1;
     if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
@@ -1389,7 +1424,19 @@ extern "C" {
 snc_status snc_finalize(snc_ctx* c) {
   if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
   if (c->finalized) return fail(c, SNC_ERR_STATE, "finalize called twice");
+  if (c->sharded && static_cast<uint64_t>(c->shard_first) + c->shard_n > c->n_nodes)
+    return fail(c, SNC_ERR_INVALID_ARG, "target shard [%u, %u + %u) outside the %llu nodes", c->shard_first,
+                c->shard_first, c->shard_n, static_cast<unsigned long long>(c->n_nodes));
   return finalize_build(&c, 1);
+}
+
+snc_status snc_set_target_shard(snc_ctx* c, uint32_t first, uint32_t n) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (c->finalized) return fail(c, SNC_ERR_STATE, "set_target_shard after finalize");
+  c->sharded = true;
+  c->shard_first = first;
+  c->shard_n = n;
+  return SNC_OK;
 }
 
 snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n) {
@@ -1398,6 +1445,7 @@ snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n) {
     if (!ctxs[i]) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: null context");
     if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
     if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
+    if (ctxs[i]->sharded) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a target shard is built alone");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
   }
@@ -1412,6 +1460,7 @@ namespace {
 // on the host before generation (no pairwise_bernoulli count phase, no
 // total-number redraw rounds).
 bool graph_eligible(const snc_ctx* c) {
+  if (c->sharded) return false;  // the kept count is read back before the sort
   for (const Projection& p : c->projs)
     if (p.rule.kind == SNC_PAIRWISE_BERNOULLI || is_total_redraw(p)) return false;
   return true;
@@ -1424,6 +1473,7 @@ snc_status snc_batch_finalize_graph(snc_ctx* const* ctxs, int n) {
     if (!ctxs[i]) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: null context");
     if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
     if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
+    if (ctxs[i]->sharded) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a target shard is built alone");
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
     if (!graph_eligible(ctxs[i]))

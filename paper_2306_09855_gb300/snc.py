@@ -110,7 +110,7 @@ SNC_JOB_QUEUED, SNC_JOB_RUNNING, SNC_JOB_DONE, SNC_JOB_FAILED = range(4)
 # Every symbol include/snc.h and include/snc_server.h declare.
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_copy_index",
-           "snc_deliver", "snc_stage_times",
+           "snc_deliver", "snc_set_target_shard", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
            "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_batch_finalize_graph",
            "snc_batch_rebuild", "snc_last_error",
@@ -146,6 +146,7 @@ def load(build: bool = True):
         "snc_copy_connections": ([P, P, P, P, P, U64], I32),
         "snc_copy_index": ([P, P, P, P, U64], I32),
         "snc_deliver": ([P, P, P, P, U64, P], I32),
+        "snc_set_target_shard": ([P, U32, U32], I32),
         "snc_stage_times": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(I32),
                              ctypes.POINTER(I32)], I32),
         "snc_radix_sort_pairs": ([P, P, P, P, U64, I32, P], I32),
@@ -273,6 +274,10 @@ def snc_deliver(ctx, src_ptr, grp_ptr, mult_ptr, n_spikes, input_ptr):
     """Deliver a spike array (device pointers: uint32 sources, uint32 group
     indices, float multiplicities) into the float input array of n_nodes."""
     _check(load().snc_deliver(ctx, src_ptr, grp_ptr, mult_ptr, int(n_spikes), input_ptr), ctx)
+
+
+def snc_set_target_shard(ctx, first, n):
+    _check(load().snc_set_target_shard(ctx, int(first), int(n)), ctx)
 
 
 def snc_stage_times(ctx):
@@ -510,7 +515,7 @@ class Server:
 class Network:
     """Create -> Connect -> Finalize -> GetConnections for one NetworkSpec."""
 
-    def __init__(self, spec, device=0, stream=None, allocator="torch"):
+    def __init__(self, spec, device=0, stream=None, allocator="torch", target_shard=None):
         import torch
         self.spec = spec
         self._torch = torch
@@ -526,6 +531,8 @@ class Network:
         for pj in spec.projections:
             snc_connect(self.ctx, snc_range(*pj.src), snc_range(*pj.tgt), _rule_struct(pj),
                         _syn_struct(pj))
+        if target_shard is not None:  # (first, n): keep the connections onto these targets
+            snc_set_target_shard(self.ctx, *target_shard)
 
     def finalize(self):
         snc_finalize(self.ctx)
