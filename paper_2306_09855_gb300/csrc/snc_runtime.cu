@@ -1185,6 +1185,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     SNC_CUDA(c, cudaStreamSynchronize(st));
     n = S.h_pinned[0];
     seg_end[0] = seg_begin[0] + n;
+    SNC_CUDA(c, upload(c, d_seg + n_members, seg_end.data(), sizeof(uint64_t)));  // the index reads the end
     std::swap(keys_a, keys_b);
     std::swap(vals_a, vals_b);
     dev_free(c, flags);
