@@ -229,7 +229,7 @@ snc_status snc_copy_index(snc_ctx* ctx, uint64_t* row_ptr, uint64_t* group_ptr, 
  * connections come in the whole network's (source, delay, generation)
  * order, indexed over all source nodes.  Before snc_finalize (STATE after);
  * INVALID_ARG at snc_finalize when the range exceeds the nodes, and in a
- * batch.  Graph builds refuse sharded contexts (UNSUPPORTED). */
+ * batch (graph builds included): a shard is built alone. */
 snc_status snc_set_target_shard(snc_ctx* ctx, uint32_t first, uint32_t n);
 
 /* Spike delivery through the index (Sec. 2.3, the spike array).  Entry e of

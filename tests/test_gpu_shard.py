@@ -70,6 +70,6 @@ def test_shard_errors(snc):
     assert e.value.name == "INVALID_ARG"
     with pytest.raises(snc.SncError) as e:
         snc.snc_batch_finalize_graph([a.ctx])
-    assert e.value.name == "UNSUPPORTED"
+    assert e.value.name == "INVALID_ARG"
     a.close()
     b.close()
