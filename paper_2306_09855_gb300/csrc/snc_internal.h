@@ -103,6 +103,7 @@ void rebind_build(snc_ctx* c, cudaStream_t stream, const snc_allocator* alloc);
 uint64_t storage_live_bytes(const snc_ctx* c);  // device bytes the context's storage holds
 int ctx_device(const snc_ctx* c);
 bool ctx_finalized(const snc_ctx* c);
+bool ctx_sharded(const snc_ctx* c);  // a target shard (built alone, never in a batch)
 
 // Host threshold tables (tables.cpp).
 int delay_thresholds(double mu, double sigma, double dt, std::vector<uint32_t>& thr, uint32_t& base);

@@ -498,6 +498,7 @@ void rebind_build(snc_ctx* c, cudaStream_t stream, const snc_allocator* alloc) {
 uint64_t storage_live_bytes(const snc_ctx* c) { return c->store ? c->store->live_bytes : 0; }
 int ctx_device(const snc_ctx* c) { return c->device; }
 bool ctx_finalized(const snc_ctx* c) { return c->finalized; }
+bool ctx_sharded(const snc_ctx* c) { return c->sharded; }
 }  // namespace snc
 
 extern "C" {

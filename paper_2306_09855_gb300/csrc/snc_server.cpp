@@ -102,10 +102,11 @@ struct snc_server {
     uint64_t nodes = head->est.n_nodes, max_nodes = head->est.n_nodes;
     uint32_t max_step = head->est.max_step;
     const uint64_t small = cfg.batch_max_syn / 2;
-    if (cfg.batch_max_nets > 1 && head->est.n_syn <= small) {
+    // (Target shards are built alone.)
+    if (cfg.batch_max_nets > 1 && head->est.n_syn <= small && !snc::ctx_sharded(head->ctx)) {
       while (!queue.empty() && static_cast<int>(out.size()) < cfg.batch_max_nets) {
         Job* j = queue.front();
-        if (j->est.n_syn > small || syn + j->est.n_syn > cfg.batch_max_syn) break;
+        if (j->est.n_syn > small || syn + j->est.n_syn > cfg.batch_max_syn || snc::ctx_sharded(j->ctx)) break;
         if (st.reserved_bytes + reserve + j->est.peak_bytes > cfg.hbm_budget_bytes) break;
         // The batched key: global source | delay step | member-local target.
         const uint64_t n2 = nodes + j->est.n_nodes, m2 = std::max(max_nodes, j->est.n_nodes);

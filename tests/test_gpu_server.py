@@ -153,3 +153,37 @@ def test_estimate_bounds_the_build(snc, spec):
     assert v.n_syn <= n_est
     assert st.device_bytes_peak <= peak
     net.close()
+
+
+def test_target_shards_are_served_alone(snc):
+    """Target shards of one network, submitted together with small requests
+    that could be batched: every shard is built alone and equals the shard
+    built without the server."""
+    spec = W.two_population(1200, "fixed_indegree", k=30, seed=41)
+    bounds = [(0, 800), (800, 900), (1700, 700)]
+    srv = snc.Server(hbm_budget_bytes=16 << 30, max_slots=2, batch_max_nets=8, batch_max_syn=8_000_000)
+    try:
+        tickets = []
+        for first, n in bounds:
+            net = snc.Network(spec, allocator=None, target_shard=(first, n))
+            tickets.append(snc.snc_server_submit(srv.srv, net.ctx))
+            net.ctx = None  # the server owns the context now
+        small = [srv.submit(W.two_population(300, "fixed_indegree", k=20, seed=50 + i)) for i in range(3)]
+        seen = set()
+        while len(seen) < len(tickets) + len(small):
+            t = srv.wait_any(timeout_ms=120_000)
+            assert t != 0, "server stalled"
+            seen.add(t)
+        for (first, n), t in zip(bounds, tickets):
+            assert srv.state(t) == snc.SNC_JOB_DONE
+            assert srv.times(t).batch_size == 1
+            alone = snc.Network(spec, target_shard=(first, n)).finalize()
+            ref = alone.to_host()
+            alone.close()
+            got = srv.to_host(t)
+            for f in FIELDS:
+                np.testing.assert_array_equal(got[f], ref[f], err_msg=f"shard {first}: {f}")
+        for t in tickets + small:
+            srv.release(t)
+    finally:
+        srv.close()
