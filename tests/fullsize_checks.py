@@ -79,6 +79,15 @@ def check_source_primary(torch, t, oracle_mod, spec, proj, a):
     return ref["tgt"].size
 
 
+def check_projection_counts(torch, t, src, spec):
+    """Every projection holds its count (fixed_total_number: N)."""
+    tg = t["target"].to(torch.int64)
+    for pj in spec.projections:
+        inside = ((src >= pj.src[0]) & (src < pj.src[0] + pj.src[1]) &
+                  (tg >= pj.tgt[0]) & (tg < pj.tgt[0] + pj.tgt[1]))
+        assert int(inside.sum()) == pj.k
+
+
 def check_total_no_multapses(torch, t, src, spec):
     """fixed_total_number without autapses or multapses: per projection N
     connections, no autapse, no pair twice."""
