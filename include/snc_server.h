@@ -20,7 +20,8 @@
  *     overlap on the device.
  *   - Small requests waiting back to back in the queue are built together by
  *     one batched finalize (snc_batch_finalize), up to `batch_max_nets`
- *     networks and `batch_max_syn` estimated connections per batch.
+ *     networks and `batch_max_syn` estimated connections per batch; a
+ *     target shard (snc_set_target_shard) is always built alone.
  *   - Device memory comes from a memory pool owned by the server (its
  *     contexts' own allocator settings are replaced); a released network's
  *     memory returns to that pool.
