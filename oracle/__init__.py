@@ -20,6 +20,10 @@ Parity status (see the pins in tests/test_oracle_*.py):
                     group of every source once), linearity in the
                     multiplicity, a hand-computed example and the group
                     boundaries (tests/test_oracle_deliver.py)
+  explicit arrays   node-id arrays pinned to the range forms by renaming
+                    invariances, per-connection weights by the Sec. 2.1
+                    numbering, delays by hand-computed steps, the complete
+                    cases by their unique results (tests/test_oracle_arrays.py)
 """
 from __future__ import annotations
 
@@ -50,7 +54,10 @@ class _Proj(ctypes.Structure):
                 ("k", ctypes.c_uint64), ("p", ctypes.c_double),
                 ("w_kind", ctypes.c_int32), ("d_kind", ctypes.c_int32),
                 ("w_mean", ctypes.c_double), ("w_std", ctypes.c_double),
-                ("d_mean", ctypes.c_double), ("d_std", ctypes.c_double)]
+                ("d_mean", ctypes.c_double), ("d_std", ctypes.c_double),
+                ("src_ids", ctypes.c_void_p), ("tgt_ids", ctypes.c_void_p),
+                ("w_arr", ctypes.c_void_p), ("d_arr", ctypes.c_void_p),
+                ("n_arr", ctypes.c_uint64)]
 
 
 class _Net(ctypes.Structure):
@@ -73,20 +80,51 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
 
 
+def _array(a, dtype, keep):
+    """(address, length) of an optional per-projection array as a contiguous
+    copy kept alive in `keep`; a given array has a non-null address even
+    when it is empty."""
+    if a is None:
+        return None, 0
+    a = np.ascontiguousarray(a, dtype=dtype).ravel()
+    buf = a if a.size else np.zeros(1, dtype)
+    keep.append(buf)
+    return buf.ctypes.data, a.size
+
+
+class _Marshalled:
+    """The ctypes network and projection structs plus the arrays they point into."""
+
+    def __init__(self, spec):
+        self.keep = []
+        self.net = _Net(seed=int(spec.seed) & 0xFFFFFFFFFFFFFFFF, dt=float(spec.dt),
+                        n_nodes=int(spec.n_nodes), n_proj=len(spec.projections))
+        self.arr = (_Proj * max(1, len(spec.projections)))()
+        for i, pj in enumerate(spec.projections):
+            src_ids, ns = _array(getattr(pj, "src_ids", None), np.uint32, self.keep)
+            tgt_ids, nt = _array(getattr(pj, "tgt_ids", None), np.uint32, self.keep)
+            w_arr, nw = _array(getattr(pj, "weights", None), np.float32, self.keep)
+            d_arr, nd = _array(getattr(pj, "delays", None), np.float32, self.keep)
+            if src_ids is not None and ns != pj.src[1]:
+                raise ValueError("projection %d: src count %d != len(src_ids) %d" % (i, pj.src[1], ns))
+            if tgt_ids is not None and nt != pj.tgt[1]:
+                raise ValueError("projection %d: tgt count %d != len(tgt_ids) %d" % (i, pj.tgt[1], nt))
+            if w_arr is not None and d_arr is not None and nw != nd:
+                raise ValueError("projection %d: %d weights but %d delays" % (i, nw, nd))
+            self.arr[i] = _Proj(src_first=pj.src[0], src_n=pj.src[1], tgt_first=pj.tgt[0],
+                                tgt_n=pj.tgt[1], rule=RULE_ID[pj.rule],
+                                allow_autapses=int(bool(pj.autapses)),
+                                allow_multapses=int(bool(pj.multapses)), pad0=0, k=int(pj.k),
+                                p=float(pj.p), w_kind=DIST_ID[pj.weight.kind],
+                                d_kind=DIST_ID[pj.delay.kind], w_mean=float(pj.weight.mean),
+                                w_std=float(pj.weight.std), d_mean=float(pj.delay.mean),
+                                d_std=float(pj.delay.std), src_ids=src_ids, tgt_ids=tgt_ids,
+                                w_arr=w_arr, d_arr=d_arr, n_arr=nw if w_arr is not None else nd)
+
+
 def _marshal(spec):
-    net = _Net(seed=int(spec.seed) & 0xFFFFFFFFFFFFFFFF, dt=float(spec.dt),
-               n_nodes=int(spec.n_nodes), n_proj=len(spec.projections))
-    arr = (_Proj * max(1, len(spec.projections)))()
-    for i, pj in enumerate(spec.projections):
-        arr[i] = _Proj(src_first=pj.src[0], src_n=pj.src[1], tgt_first=pj.tgt[0],
-                       tgt_n=pj.tgt[1], rule=RULE_ID[pj.rule],
-                       allow_autapses=int(bool(pj.autapses)),
-                       allow_multapses=int(bool(pj.multapses)), pad0=0, k=int(pj.k),
-                       p=float(pj.p), w_kind=DIST_ID[pj.weight.kind],
-                       d_kind=DIST_ID[pj.delay.kind], w_mean=float(pj.weight.mean),
-                       w_std=float(pj.weight.std), d_mean=float(pj.delay.mean),
-                       d_std=float(pj.delay.std))
-    return net, arr
+    m = _Marshalled(spec)
+    return m.net, m.arr, m
 
 
 def _check(st, what):
@@ -141,13 +179,13 @@ def normal_weights(mu, sigma, w2, w3):
 
 def check_projection(spec, index):
     """Status code Connect gives projection `index` (0 = accepted)."""
-    net, arr = _marshal(spec)
+    net, arr, _keep = _marshal(spec)
     return int(_lib().or_check_projection(ctypes.byref(net), ctypes.byref(arr[index])))
 
 
 def count(spec):
     """(total connections, per-projection counts) without storing them."""
-    net, arr = _marshal(spec)
+    net, arr, _keep = _marshal(spec)
     per = np.zeros(max(1, len(spec.projections)), dtype=np.uint64)
     n = ctypes.c_uint64(0)
     _check(_lib().or_generate(ctypes.byref(net), arr, None, None, None, None,
@@ -158,7 +196,7 @@ def count(spec):
 def generate(spec):
     """All connections in generation order (before the sort)."""
     total, per = count(spec)
-    net, arr = _marshal(spec)
+    net, arr, _keep = _marshal(spec)
     out = {"src": np.empty(total, np.uint32), "tgt": np.empty(total, np.uint32),
            "delay": np.empty(total, np.uint16), "weight": np.empty(total, np.float32)}
     n = ctypes.c_uint64(0)
@@ -224,7 +262,7 @@ def deliver(net, n_nodes, src, grp, mult):
 
 def generate_primary(spec, proj, primary):
     """Connections of one primary node of projection `proj`, in slot order."""
-    net, arr = _marshal(spec)
+    net, arr, _keep = _marshal(spec)
     pj = spec.projections[proj]
     cap = max(1, int(pj.src[1]) + int(pj.tgt[1]) + int(pj.k) + 1)
     out = {"src": np.empty(cap, np.uint32), "tgt": np.empty(cap, np.uint32),

@@ -12,9 +12,12 @@
  * What it computes, in the paper's order:
  *   1. node ids: contiguous, 0-based, in population-creation order (Sec. 2.1);
  *   2. connections of each Connect call in the rule's own numbering
- *      i_newconns (Sec. 2.1, Eqs. 2-3 and the per-rule index formulas);
- *   3. weight and integer delay of every connection (Sec. 2.1, last
- *      paragraph: delay = round(d / dt), at least one step);
+ *      i_newconns (Sec. 2.1, Eqs. 2-3 and the per-rule index formulas), on
+ *      node ranges or on explicit node-id arrays (the formulas then give
+ *      positions in the arrays);
+ *   3. weight and integer delay of every connection, drawn or given per
+ *      connection by arrays (Sec. 2.1, last paragraph: delay = round(d / dt),
+ *      at least one step);
  *   4. a stable sort by (source, delay) (Sec. 2.2: source first, delay
  *      second; connections equal in both keep their generation order);
  *   5. the group index: a connection starts a group when its source or its
@@ -70,7 +73,12 @@ enum { OR_DIST_CONST = 0, OR_DIST_NORMAL = 1 };
 #define OR_MAX_ROUND 0xFFFFFFu
 
 /* One Connect call.  Mirrors the argument list of Connect(sources, targets,
- * conn_dict, syn_dict) in Sec. 2.1 with contiguous node ranges. */
+ * conn_dict, syn_dict) in Sec. 2.1.  Sources and targets are contiguous node
+ * ranges, or explicit arrays of node ids (Sec. 2.1: the index formulas then
+ * give positions in the arrays, src_n / tgt_n their lengths).  Weights and
+ * delays follow their distributions, or per-connection arrays (Sec. 2.1)
+ * whose element i belongs to connection number i_newconns = i of the rule's
+ * own numbering (w_arr, d_arr in ms; n_arr elements; NULL = none). */
 typedef struct {
   uint32_t src_first, src_n, tgt_first, tgt_n;
   int32_t rule;
@@ -81,7 +89,22 @@ typedef struct {
   int32_t w_kind, d_kind;
   double w_mean, w_std;
   double d_mean, d_std; /* milliseconds */
+  const uint32_t* src_ids; /* src_n ids, or NULL for the range */
+  const uint32_t* tgt_ids; /* tgt_n ids, or NULL for the range */
+  const float* w_arr;
+  const float* d_arr;
+  uint64_t n_arr;
 } or_proj;
+
+/* Node id at position a of the source list and at position b of the target
+ * list (a range: first + position). */
+static uint32_t src_node(const or_proj* pj, uint32_t a) {
+  return pj->src_ids ? pj->src_ids[a] : pj->src_first + a;
+}
+
+static uint32_t tgt_node(const or_proj* pj, uint32_t b) {
+  return pj->tgt_ids ? pj->tgt_ids[b] : pj->tgt_first + b;
+}
 
 typedef struct {
   uint64_t seed;
@@ -336,38 +359,100 @@ typedef struct {
   uint32_t d_base;
   int d_len;
   uint32_t* d_thr;
+  double dt;        /* for per-connection delays in ms          */
   /* Bernoulli tables for the two possible numbers of candidates. */
   uint64_t b_base[2];
   int b_len[2];
   uint32_t* b_thr[2];
+  /* Explicit id arrays: position of each node in the source (0) and target
+   * (1) array, OR_ABSENT where it is not listed. */
+  uint32_t* pos[2];
 } or_tables;
+
+#define OR_ABSENT 0xFFFFFFFFu
 
 static void free_tables(or_tables* t) {
   free(t->d_thr);
   free(t->b_thr[0]);
   free(t->b_thr[1]);
+  free(t->pos[0]);
+  free(t->pos[1]);
   memset(t, 0, sizeof *t);
 }
 
-static int ranges_overlap_node(uint32_t first, uint32_t n, uint32_t node) {
-  return node >= first && node - first < n;
+/* Sec. 2.1: a delay in ms becomes round(d / dt) steps, at least one.  Round
+ * half up, in double.  Non-finite delays are INVALID_ARG, steps above the
+ * 16-bit delay field UNSUPPORTED. */
+static int delay_step_ms(double d, double dt, uint32_t* step) {
+  if (!isfinite(d)) return OR_ERR_INVALID_ARG;
+  double q = floor(d / dt + 0.5);
+  if (!(q == q)) return OR_ERR_INVALID_ARG;
+  if (q < 1.0) q = 1.0;
+  if (q > (double)OR_MAX_DELAY_STEP) return OR_ERR_UNSUPPORTED;
+  *step = (uint32_t)q;
+  return OR_OK;
 }
 
-static uint64_t overlap_count(const or_proj* pj) {
-  uint64_t a0 = pj->src_first, a1 = (uint64_t)pj->src_first + pj->src_n;
-  uint64_t b0 = pj->tgt_first, b1 = (uint64_t)pj->tgt_first + pj->tgt_n;
-  uint64_t lo = a0 > b0 ? a0 : b0, hi = a1 < b1 ? a1 : b1;
-  return hi > lo ? hi - lo : 0;
+/* Number of position pairs (a, b) whose nodes coincide,
+ * #{(a, b) : src_node(a) == tgt_node(b)}: the autapses among all pairs.
+ * For two ranges it is the length of their overlap. */
+static int equal_pairs(const or_net* net, const or_proj* pj, uint64_t* out) {
+  if (!pj->src_ids && !pj->tgt_ids) {
+    uint64_t a0 = pj->src_first, a1 = (uint64_t)pj->src_first + pj->src_n;
+    uint64_t b0 = pj->tgt_first, b1 = (uint64_t)pj->tgt_first + pj->tgt_n;
+    uint64_t lo = a0 > b0 ? a0 : b0, hi = a1 < b1 ? a1 : b1;
+    *out = hi > lo ? hi - lo : 0;
+    return OR_OK;
+  }
+  uint64_t* in_src = (uint64_t*)calloc(net->n_nodes ? net->n_nodes : 1, sizeof(uint64_t));
+  if (!in_src) return OR_ERR_OOM;
+  for (uint32_t a = 0; a < pj->src_n; ++a) in_src[src_node(pj, a)] += 1;
+  uint64_t n = 0;
+  for (uint32_t b = 0; b < pj->tgt_n; ++b) n += in_src[tgt_node(pj, b)];
+  free(in_src);
+  *out = n;
+  return OR_OK;
+}
+
+/* 1 if some id appears twice in ids[0..n), ids all below n_nodes. */
+static int has_duplicates(const uint32_t* ids, uint32_t n, uint32_t n_nodes, int* dup) {
+  unsigned char* seen = (unsigned char*)calloc(n_nodes ? n_nodes : 1, 1);
+  if (!seen) return OR_ERR_OOM;
+  *dup = 0;
+  for (uint32_t i = 0; i < n && !*dup; ++i) {
+    if (seen[ids[i]]) *dup = 1;
+    seen[ids[i]] = 1;
+  }
+  free(seen);
+  return OR_OK;
+}
+
+/* Position of `node` in the source (which = 0) or target (1) list, or -1. */
+static int64_t position_of(const or_proj* pj, const or_tables* t, int which, uint32_t node) {
+  const uint32_t* ids = which ? pj->tgt_ids : pj->src_ids;
+  if (ids) return t->pos[which][node] == OR_ABSENT ? -1 : (int64_t)t->pos[which][node];
+  uint32_t first = which ? pj->tgt_first : pj->src_first;
+  uint32_t n = which ? pj->tgt_n : pj->src_n;
+  return node >= first && node - first < n ? (int64_t)(node - first) : -1;
 }
 
 static int make_tables(const or_net* net, const or_proj* pj, or_tables* t) {
   memset(t, 0, sizeof *t);
-  if (pj->d_kind == OR_DIST_CONST || (pj->d_kind == OR_DIST_NORMAL && pj->d_std == 0.0)) {
-    double q = floor(pj->d_mean / net->dt + 0.5);
-    if (!(q == q)) return OR_ERR_INVALID_ARG;
-    if (q < 1.0) q = 1.0;
-    if (q > (double)OR_MAX_DELAY_STEP) return OR_ERR_UNSUPPORTED;
-    t->d_const = (uint32_t)q;
+  t->dt = net->dt;
+  for (int which = 0; which < 2; ++which) {
+    const uint32_t* ids = which ? pj->tgt_ids : pj->src_ids;
+    uint32_t n = which ? pj->tgt_n : pj->src_n;
+    if (!ids) continue;
+    t->pos[which] = (uint32_t*)malloc(sizeof(uint32_t) * (net->n_nodes ? net->n_nodes : 1));
+    if (!t->pos[which]) return OR_ERR_OOM;
+    for (uint32_t v = 0; v < net->n_nodes; ++v) t->pos[which][v] = OR_ABSENT;
+    for (uint32_t i = 0; i < n; ++i) t->pos[which][ids[i]] = i;
+  }
+  if (pj->d_arr) {
+    /* per-connection delays: converted one by one (delay_at) */
+  } else if (pj->d_kind == OR_DIST_CONST || (pj->d_kind == OR_DIST_NORMAL && pj->d_std == 0.0)) {
+    int st = delay_step_ms(pj->d_mean, net->dt, &t->d_const);
+    if (st) return st;
   } else if (pj->d_kind == OR_DIST_NORMAL) {
     t->d_thr = (uint32_t*)malloc(sizeof(uint32_t) * OR_MAX_TABLE);
     if (!t->d_thr) return OR_ERR_OOM;
@@ -402,6 +487,22 @@ static float weight_of(const or_proj* pj, uint32_t w2, uint32_t w3) {
   return or_normal_weight(pj->w_mean, pj->w_std, w2, w3);
 }
 
+/* Delay and weight of connection number inew: the per-connection array's
+ * element inew when there is one (checked before generation), else the
+ * distribution's value from the slot's WD words. */
+static uint16_t delay_at(const or_proj* pj, const or_tables* t, uint64_t inew, uint32_t u) {
+  if (pj->d_arr) {
+    uint32_t step = 1;
+    delay_step_ms((double)pj->d_arr[inew], t->dt, &step);
+    return (uint16_t)step;
+  }
+  return delay_of(t, u);
+}
+
+static float weight_at(const or_proj* pj, uint64_t inew, uint32_t w2, uint32_t w3) {
+  return pj->w_arr ? pj->w_arr[inew] : weight_of(pj, w2, w3);
+}
+
 /* Output sink: arrays in generation order. */
 typedef struct {
   uint32_t* src;
@@ -424,12 +525,14 @@ static int emit(or_sink* out, uint32_t s, uint32_t t, uint16_t d, float w) {
   return OR_OK;
 }
 
-/* Weight and delay of slot `slot` of primary node `primary`. */
+/* Weight and delay of slot `slot` of primary node `primary`, connection
+ * number inew. */
 static int emit_wd(const or_net* net, uint32_t proj, const or_proj* pj, const or_tables* t,
-                   uint32_t primary, uint64_t slot, uint32_t s, uint32_t tg, or_sink* out) {
+                   uint32_t primary, uint64_t slot, uint64_t inew, uint32_t s, uint32_t tg,
+                   or_sink* out) {
   uint32_t w[4];
   draw(net, proj, OR_TAG_WD, 0, primary, slot, w);
-  return emit(out, s, tg, delay_of(t, w[0]), weight_of(pj, w[2], w[3]));
+  return emit(out, s, tg, delay_at(pj, t, inew, w[0]), weight_at(pj, inew, w[2], w[3]));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -515,74 +618,81 @@ static int pair_set_insert(pair_set* ps, uint64_t key) {
  *   all_to_all:  primary = target b, slot a = source index (i = a*Nt + b is
  *                the paper's numbering; emitted per target here only for
  *                sampled checks);
- *   indegree:    primary = target b, s = s0 + rand(Ns), K slots;
- *   outdegree:   primary = source b, t = t0 + rand(Nt), K slots;
+ *   indegree:    primary = target b, s = source at rand(Ns), K slots,
+ *                connection number i = b*K + j;
+ *   outdegree:   primary = source b, t = target at rand(Nt), K slots,
+ *                i = b*K + j;
  *   bernoulli:   primary = target b, count ~ Binomial(candidates, p), then
- *                that many distinct sources. */
+ *                that many distinct sources.
+ * With autapses off the primary's own node, if the other list holds it (at
+ * one position: such lists are checked to hold distinct ids), is left out
+ * of the draws. */
 static int gen_primary(const or_net* net, uint32_t proj, const or_proj* pj,
                        const or_tables* t, uint32_t b, uint32_t* sel, or_sink* out) {
-  const uint32_t s0 = pj->src_first, t0 = pj->tgt_first;
   const uint32_t Ns = pj->src_n, Nt = pj->tgt_n;
   int st = OR_OK;
   if (pj->rule == OR_ALL_TO_ALL) {
     for (uint32_t a = 0; a < Ns && !st; ++a) {
-      uint32_t s = s0 + a, tg = t0 + b;
+      uint32_t s = src_node(pj, a), tg = tgt_node(pj, b);
       if (!pj->allow_autapses && s == tg) continue;
-      st = emit_wd(net, proj, pj, t, b, a, s, tg, out);
+      st = emit_wd(net, proj, pj, t, b, a, (uint64_t)a * Nt + b, s, tg, out);
     }
     return st;
   }
   if (pj->rule == OR_PAIRWISE_BERNOULLI) {
-    uint32_t node = t0 + b;
-    int skip = !pj->allow_autapses && ranges_overlap_node(s0, Ns, node);
-    uint32_t skip_local = skip ? node - s0 : 0;
+    uint32_t node = tgt_node(pj, b);
+    int64_t q = pj->allow_autapses ? -1 : position_of(pj, t, 0, node);
+    int skip = q >= 0;
+    uint32_t skip_local = skip ? (uint32_t)q : 0;
     uint32_t w[4];
     draw(net, proj, OR_TAG_COUNT, 0, b, 0, w);
     uint64_t nb = table_value(t->b_base[skip], t->b_thr[skip], t->b_len[skip], w[0]);
     st = sample_distinct(net, proj, b, Ns, skip, skip_local, nb, sel);
+    /* no per-connection arrays for this rule (the count is drawn) */
     for (uint64_t j = 0; j < nb && !st; ++j)
-      st = emit_wd(net, proj, pj, t, b, j, s0 + sel[j], node, out);
+      st = emit_wd(net, proj, pj, t, b, j, 0, src_node(pj, sel[j]), node, out);
     return st;
   }
   /* fixed_indegree / fixed_outdegree */
   int indeg = pj->rule == OR_FIXED_INDEGREE;
   uint32_t n_other = indeg ? Ns : Nt;
-  uint32_t first_primary = indeg ? t0 : s0;
-  uint32_t first_other = indeg ? s0 : t0;
   uint64_t K = pj->k;
-  uint32_t node = first_primary + b;
-  int skip = !pj->allow_autapses && ranges_overlap_node(first_other, n_other, node);
-  uint32_t skip_local = skip ? node - first_other : 0;
+  uint32_t node = indeg ? tgt_node(pj, b) : src_node(pj, b);
+  int64_t q = pj->allow_autapses ? -1 : position_of(pj, t, indeg ? 0 : 1, node);
+  int skip = q >= 0;
+  uint32_t skip_local = skip ? (uint32_t)q : 0;
   if (pj->allow_multapses) {
     for (uint64_t j = 0; j < K && !st; ++j) {
       uint32_t w[4];
       draw(net, proj, OR_TAG_WD, 0, b, j, w);
-      uint32_t other = first_other + draw_endpoint(w[1], n_other, skip, skip_local);
+      uint32_t r = draw_endpoint(w[1], n_other, skip, skip_local);
+      uint32_t other = indeg ? src_node(pj, r) : tgt_node(pj, r);
       uint32_t s = indeg ? other : node, tg = indeg ? node : other;
-      st = emit(out, s, tg, delay_of(t, w[0]), weight_of(pj, w[2], w[3]));
+      uint64_t inew = (uint64_t)b * K + j;
+      st = emit(out, s, tg, delay_at(pj, t, inew, w[0]), weight_at(pj, inew, w[2], w[3]));
     }
   } else {
     st = sample_distinct(net, proj, b, n_other, skip, skip_local, K, sel);
     for (uint64_t j = 0; j < K && !st; ++j) {
-      uint32_t other = first_other + sel[j];
+      uint32_t other = indeg ? src_node(pj, sel[j]) : tgt_node(pj, sel[j]);
       uint32_t s = indeg ? other : node, tg = indeg ? node : other;
-      st = emit_wd(net, proj, pj, t, b, j, s, tg, out);
+      st = emit_wd(net, proj, pj, t, b, j, (uint64_t)b * K + j, s, tg, out);
     }
   }
   return st;
 }
 
-/* fixed_total_number: slot i draws s = s0 + rand(Ns), t = t0 + rand(Nt)
- * (source from word 1 of its WD draw, target from word i mod 4 of IDX draw
- * floor(i/4)).  A slot whose pair is not allowed (an autapse when autapses
- * are off; with multapses off, a pair already held by an accepted slot or
- * drawn this round by a lower pending slot) redraws in round r = 1, 2, ...
- * from words 0 and 1 of its DEDUP draw of that round, until every slot
- * holds an allowed pair.  Visiting the pending slots in ascending order with
- * a running set of accepted pairs applies exactly that rule. */
+/* fixed_total_number: slot i draws the source at position rand(Ns) and the
+ * target at position rand(Nt) (source from word 1 of its WD draw, target
+ * from word i mod 4 of IDX draw floor(i/4)).  A slot whose pair is not
+ * allowed (an autapse when autapses are off; with multapses off, a pair
+ * already held by an accepted slot or drawn this round by a lower pending
+ * slot) redraws in round r = 1, 2, ... from words 0 and 1 of its DEDUP draw
+ * of that round, until every slot holds an allowed pair.  Visiting the
+ * pending slots in ascending order with a running set of accepted pairs
+ * applies exactly that rule.  Slot i is connection number i. */
 static int gen_total_number(const or_net* net, uint32_t proj, const or_proj* pj,
                             const or_tables* t, or_sink* out) {
-  const uint32_t s0 = pj->src_first, t0 = pj->tgt_first;
   const uint32_t Ns = pj->src_n, Nt = pj->tgt_n;
   uint64_t N = pj->k;
   if (N == 0) return OR_OK;
@@ -598,8 +708,8 @@ static int gen_total_number(const or_net* net, uint32_t proj, const or_proj* pj,
     uint32_t w[4], x[4];
     draw(net, proj, OR_TAG_WD, 0, OR_PRIMARY_NONE, i, w);
     draw(net, proj, OR_TAG_IDX, 0, OR_PRIMARY_NONE, i / 4, x);
-    ps[i] = s0 + rand_below(w[1], Ns);
-    pt[i] = t0 + rand_below(x[i % 4], Nt);
+    ps[i] = src_node(pj, rand_below(w[1], Ns));
+    pt[i] = tgt_node(pj, rand_below(x[i % 4], Nt));
     int ok = pj->allow_autapses || ps[i] != pt[i];
     if (ok && !pj->allow_multapses) ok = pair_set_insert(&set, ((uint64_t)ps[i] << 32) | pt[i]);
     if (!ok) pending[n_pending++] = i;
@@ -614,8 +724,8 @@ static int gen_total_number(const or_net* net, uint32_t proj, const or_proj* pj,
       uint64_t i = pending[q];
       uint32_t w[4];
       draw(net, proj, OR_TAG_DEDUP, round, OR_PRIMARY_NONE, i, w);
-      ps[i] = s0 + rand_below(w[0], Ns);
-      pt[i] = t0 + rand_below(w[1], Nt);
+      ps[i] = src_node(pj, rand_below(w[0], Ns));
+      pt[i] = tgt_node(pj, rand_below(w[1], Nt));
       int ok = pj->allow_autapses || ps[i] != pt[i];
       if (ok && !pj->allow_multapses) ok = pair_set_insert(&set, ((uint64_t)ps[i] << 32) | pt[i]);
       if (!ok) pending[still++] = i;
@@ -623,7 +733,7 @@ static int gen_total_number(const or_net* net, uint32_t proj, const or_proj* pj,
     n_pending = still;
   }
   for (uint64_t i = 0; i < N && !st; ++i)
-    st = emit_wd(net, proj, pj, t, OR_PRIMARY_NONE, i, ps[i], pt[i], out);
+    st = emit_wd(net, proj, pj, t, OR_PRIMARY_NONE, i, i, ps[i], pt[i], out);
   free(ps);
   free(pt);
   free(pending);
@@ -633,27 +743,27 @@ static int gen_total_number(const or_net* net, uint32_t proj, const or_proj* pj,
 
 static int gen_projection(const or_net* net, uint32_t proj, const or_proj* pj,
                           const or_tables* t, or_sink* out) {
-  const uint32_t s0 = pj->src_first, t0 = pj->tgt_first;
   const uint32_t Ns = pj->src_n, Nt = pj->tgt_n;
   int st = OR_OK;
   switch (pj->rule) {
     case OR_ONE_TO_ONE:
-      /* i = 0 .. N-1: s = s0 + i, t = t0 + i; with autapses off a pair with
-       * s == t is dropped. */
+      /* i = 0 .. N-1: source and target at position i; with autapses off a
+       * pair with s == t is dropped (its number i stays unused). */
       for (uint32_t i = 0; i < Ns && !st; ++i) {
-        uint32_t s = s0 + i, tg = t0 + i;
+        uint32_t s = src_node(pj, i), tg = tgt_node(pj, i);
         if (!pj->allow_autapses && s == tg) continue;
-        st = emit_wd(net, proj, pj, t, i, 0, s, tg, out);
+        st = emit_wd(net, proj, pj, t, i, 0, i, s, tg, out);
       }
       return st;
     case OR_ALL_TO_ALL:
-      /* i = a * Nt + b: s = s0 + floor(i / Nt), t = t0 + (i mod Nt); the
-       * draw of connection (a, b) is keyed by primary = target b, slot = a. */
+      /* i = a * Nt + b: source at position floor(i / Nt), target at
+       * position i mod Nt; the draw of connection (a, b) is keyed by
+       * primary = target b, slot = a. */
       for (uint32_t a = 0; a < Ns && !st; ++a)
         for (uint32_t b = 0; b < Nt && !st; ++b) {
-          uint32_t s = s0 + a, tg = t0 + b;
+          uint32_t s = src_node(pj, a), tg = tgt_node(pj, b);
           if (!pj->allow_autapses && s == tg) continue;
-          st = emit_wd(net, proj, pj, t, b, a, s, tg, out);
+          st = emit_wd(net, proj, pj, t, b, a, (uint64_t)a * Nt + b, s, tg, out);
         }
       return st;
     case OR_FIXED_TOTAL_NUMBER:
@@ -674,12 +784,50 @@ static int gen_projection(const or_net* net, uint32_t proj, const or_proj* pj,
   }
 }
 
-/* Argument checks done by Connect before anything is generated. */
+/* Connections the rule numbers (i_newconns = 0 .. count-1), before autapse
+ * drops: the length a per-connection weight or delay array must have. */
+static uint64_t numbered_count(const or_proj* pj) {
+  switch (pj->rule) {
+    case OR_ONE_TO_ONE: return pj->src_n;
+    case OR_ALL_TO_ALL: return (uint64_t)pj->src_n * pj->tgt_n;
+    case OR_FIXED_INDEGREE: return (uint64_t)pj->tgt_n * pj->k;
+    case OR_FIXED_OUTDEGREE: return (uint64_t)pj->src_n * pj->k;
+    default: return pj->k;
+  }
+}
+
+/* Argument checks done by Connect before anything is generated.
+ * Explicit id arrays: every id below n_nodes; with multapses off both
+ * arrays hold distinct ids (so distinct positions are distinct nodes); with
+ * autapses off, the list a per-primary rule draws from (sources of
+ * in-degree and Bernoulli, targets of out-degree) holds distinct ids (so
+ * the primary's own node sits at one position).  Per-connection arrays:
+ * not for pairwise_bernoulli (its count is drawn), numbered_count()
+ * elements, delays finite and at most 65535 steps. */
 int or_check_projection(const or_net* net, const or_proj* pj) {
   if (!(net->dt > 0.0)) return OR_ERR_INVALID_ARG;
-  if ((uint64_t)pj->src_first + pj->src_n > net->n_nodes) return OR_ERR_INVALID_ARG;
-  if ((uint64_t)pj->tgt_first + pj->tgt_n > net->n_nodes) return OR_ERR_INVALID_ARG;
-  uint64_t ov = overlap_count(pj);
+  for (int which = 0; which < 2; ++which) {
+    const uint32_t* ids = which ? pj->tgt_ids : pj->src_ids;
+    uint32_t first = which ? pj->tgt_first : pj->src_first;
+    uint32_t n = which ? pj->tgt_n : pj->src_n;
+    if (!ids) {
+      if ((uint64_t)first + n > net->n_nodes) return OR_ERR_INVALID_ARG;
+      continue;
+    }
+    for (uint32_t i = 0; i < n; ++i)
+      if (ids[i] >= net->n_nodes) return OR_ERR_INVALID_ARG;
+    int draws_here = which ? pj->rule == OR_FIXED_OUTDEGREE
+                           : pj->rule == OR_FIXED_INDEGREE || pj->rule == OR_PAIRWISE_BERNOULLI;
+    if (!pj->allow_multapses || (!pj->allow_autapses && draws_here)) {
+      int dup = 0;
+      int st = has_duplicates(ids, n, net->n_nodes, &dup);
+      if (st) return st;
+      if (dup) return OR_ERR_INVALID_ARG;
+    }
+  }
+  uint64_t ov = 0;
+  int st = equal_pairs(net, pj, &ov);
+  if (st) return st;
   switch (pj->rule) {
     case OR_ONE_TO_ONE:
       if (pj->src_n != pj->tgt_n) return OR_ERR_INVALID_ARG;
@@ -710,9 +858,18 @@ int or_check_projection(const or_net* net, const or_proj* pj) {
     }
     case OR_PAIRWISE_BERNOULLI:
       if (!(pj->p >= 0.0 && pj->p <= 1.0)) return OR_ERR_INVALID_ARG;
+      if (pj->w_arr || pj->d_arr) return OR_ERR_INVALID_ARG;
       break;
     default:
       return OR_ERR_INVALID_ARG;
+  }
+  if (pj->w_arr || pj->d_arr) {
+    if (pj->n_arr != numbered_count(pj)) return OR_ERR_INVALID_ARG;
+    for (uint64_t i = 0; pj->d_arr && i < pj->n_arr; ++i) {
+      uint32_t step;
+      st = delay_step_ms((double)pj->d_arr[i], net->dt, &step);
+      if (st) return st;
+    }
   }
   if (pj->d_kind != OR_DIST_CONST && pj->d_kind != OR_DIST_NORMAL) return OR_ERR_INVALID_ARG;
   if (pj->w_kind != OR_DIST_CONST && pj->w_kind != OR_DIST_NORMAL) return OR_ERR_INVALID_ARG;
@@ -766,8 +923,9 @@ int or_generate_primary(const or_net* net, const or_proj* projs, uint32_t proj,
   st = make_tables(net, pj, &t);
   if (!st) {
     if (pj->rule == OR_ONE_TO_ONE) {
-      uint32_t s = pj->src_first + primary, tg = pj->tgt_first + primary;
-      if (pj->allow_autapses || s != tg) st = emit_wd(net, proj, pj, &t, primary, 0, s, tg, &out);
+      uint32_t s = src_node(pj, primary), tg = tgt_node(pj, primary);
+      if (pj->allow_autapses || s != tg)
+        st = emit_wd(net, proj, pj, &t, primary, 0, primary, s, tg, &out);
     } else {
       uint64_t sel_n = pj->rule == OR_PAIRWISE_BERNOULLI || pj->rule == OR_ALL_TO_ALL
                            ? (uint64_t)pj->src_n + 1

@@ -434,8 +434,19 @@ def _syn_struct(pj):
                                           float(pj.delay.std)))
 
 
+def _ranges_only(spec):
+    """The library's Connect takes node ranges and weight/delay
+    distributions; explicit id arrays and per-connection arrays are refused
+    here rather than dropped."""
+    for i, pj in enumerate(spec.projections):
+        if getattr(pj, "has_arrays", False):
+            raise ValueError("projection %d: explicit id or per-connection arrays are not "
+                             "supported by snc_connect" % i)
+
+
 def create_context(spec, device=0, stream_ptr=None, allocator=None):
     """snc_create + CreatePopulation + Connect calls of a NetworkSpec (no finalize)."""
+    _ranges_only(spec)
     cfg = snc_config(seed=int(spec.seed) & 0xFFFFFFFFFFFFFFFF, dt_ms=float(spec.dt),
                      device=device, reserved=0, stream=stream_ptr,
                      allocator=ctypes.pointer(allocator) if allocator is not None else None)
@@ -517,6 +528,7 @@ class Network:
 
     def __init__(self, spec, device=0, stream=None, allocator="torch", target_shard=None):
         import torch
+        _ranges_only(spec)
         self.spec = spec
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)

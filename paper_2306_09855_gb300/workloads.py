@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -35,11 +35,16 @@ class Dist:
 
 @dataclass(frozen=True)
 class Projection:
-    """One Connect(sources, targets, conn_dict, syn_dict) call on node ranges.
+    """One Connect(sources, targets, conn_dict, syn_dict) call.
 
-    src, tgt: (first global node id, count).
+    src, tgt: (first global node id, count) of a node range.
     k: in-degree / out-degree K, or the total number N of fixed_total_number.
     p: connection probability of pairwise_bernoulli.
+    src_ids, tgt_ids: explicit node ids (uint32) in place of the range; the
+        range's count must then equal the array's length (its first id is
+        unused).
+    weights, delays: per-connection values (float32; delays in ms) in place
+        of the distributions, one per connection number of the rule.
     """
     src: Tuple[int, int]
     tgt: Tuple[int, int]
@@ -50,6 +55,14 @@ class Projection:
     multapses: bool = True
     weight: Dist = Dist("const", 1.0)
     delay: Dist = Dist("const", 1.0)
+    src_ids: Optional[np.ndarray] = field(default=None, compare=False, repr=False)
+    tgt_ids: Optional[np.ndarray] = field(default=None, compare=False, repr=False)
+    weights: Optional[np.ndarray] = field(default=None, compare=False, repr=False)
+    delays: Optional[np.ndarray] = field(default=None, compare=False, repr=False)
+
+    @property
+    def has_arrays(self) -> bool:
+        return any(a is not None for a in (self.src_ids, self.tgt_ids, self.weights, self.delays))
 
 
 @dataclass
