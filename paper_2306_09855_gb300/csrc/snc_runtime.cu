@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -294,6 +295,21 @@ void* dev_alloc(snc_ctx* c, size_t bytes) {
 }
 
 void dev_free(snc_ctx* c, void* p) { c->store->put(p); }
+
+// Calls on a finished network (delivery, host copies) free their temporary
+// buffers when they end, also on a graph-built network, whose store
+// otherwise keeps every buffer it hands out.
+class CallScope {
+ public:
+  explicit CallScope(snc_ctx* c) : s_(*c->store), saved_(s_.mode) { s_.mode = 0; }
+  ~CallScope() { s_.mode = saved_; }
+  CallScope(const CallScope&) = delete;
+  CallScope& operator=(const CallScope&) = delete;
+
+ private:
+  Storage& s_;
+  int saved_;
+};
 
 // Host -> device copy through the build's pinned staging area; *staged
 // receives the staged host copy.
@@ -1616,14 +1632,19 @@ snc_status snc_deliver(snc_ctx* c, const uint32_t* src, const uint32_t* grp, con
   if (s != SNC_OK) return s;
   if (n_spikes == 0) return SNC_OK;
   if (!src || !grp || !mult || !input) return fail(c, SNC_ERR_INVALID_ARG, "null spike array or input");
+  CallScope scope(c);
   cudaStream_t st = c->store->stream;
   uint32_t* sizes = static_cast<uint32_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint32_t)));
   uint64_t* offsets = static_cast<uint64_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint64_t)));
   uint64_t* tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_spikes) + 1) * sizeof(uint64_t)));
   uint64_t* first = static_cast<uint64_t*>(dev_alloc(c, n_spikes * sizeof(uint64_t)));
   uint32_t* err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint32_t)));
-  if (!sizes || !offsets || !tmp || !first || !err)
+  if (!sizes || !offsets || !tmp || !first || !err) {
+    for (void* p : {static_cast<void*>(sizes), static_cast<void*>(offsets), static_cast<void*>(tmp),
+                    static_cast<void*>(first), static_cast<void*>(err)})
+      dev_free(c, p);
     return fail(c, SNC_ERR_OOM, "device allocation failed (spike array)");
+  }
   SNC_CUDA(c, cudaMemsetAsync(err, 0, 8 * sizeof(uint32_t), st));
   DeliverArgs a{};
   a.src = src;
@@ -1670,6 +1691,7 @@ snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16
   if (s != SNC_OK) return s;
   if (cap < c->n_syn) return fail(c, SNC_ERR_INVALID_ARG, "capacity below the number of connections");
   const uint64_t n = c->n_syn;
+  CallScope scope(c);
   cudaStream_t st = c->store->stream;
   if (src && n > 0) {
     uint32_t* d_src = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));

@@ -145,3 +145,33 @@ def test_batch_above_2_pow_30_positions_matches_single_builds(snc):
         single.close()
     for net in reversed(nets):
         net.close()
+
+
+def test_graph_built_networks_free_call_buffers(snc):
+    """A graph-built batch keeps its build buffers for the replays, but host
+    copies and spike delivery on its members free their own temporaries:
+    repeated calls leave the peak of live device memory where the first
+    call put it."""
+    import torch
+    specs, _ = _fixed_count_specs()
+    nets = snc.Network.batch_graph(specs)
+    try:
+        net = nets[0]
+        t = net.tensors()
+        gp = t["group_ptr"]
+        src = torch.nonzero(gp[1:] > gp[:-1]).flatten().to(torch.int32)  # sources with a group
+        grp = torch.zeros_like(src)
+        mult = torch.ones(src.numel(), dtype=torch.float32, device=src.device)
+        inp = torch.zeros(int(net.view().n_nodes), dtype=torch.float32, device=src.device)
+        peaks = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            net.to_host()
+            net.deliver(src, grp, mult, inp)
+            net.synchronize()
+            peaks.append(int(net.stats().device_bytes_peak))
+        assert peaks[0] == peaks[1] == peaks[2], peaks
+        assert float(inp.abs().sum()) > 0
+    finally:
+        for net in reversed(nets):
+            net.close()
