@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <exception>
 #include <string>
 #include <vector>
 
@@ -104,6 +105,22 @@ uint64_t storage_live_bytes(const snc_ctx* c);  // device bytes the context's st
 int ctx_device(const snc_ctx* c);
 bool ctx_finalized(const snc_ctx* c);
 bool ctx_sharded(const snc_ctx* c);  // a target shard (built alone, never in a batch)
+
+// Entry points run their body through abi_guard: a C++ exception (host
+// memory or threads exhausted inside the standard library) becomes
+// SNC_ERR_OOM with a last-error message instead of crossing the C ABI.
+snc_status abi_exception(const char* what) noexcept;  // snc_runtime.cu
+
+template <class Body>
+snc_status abi_guard(Body&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::exception& e) {
+    return abi_exception(e.what());
+  } catch (...) {
+    return abi_exception("unknown exception");
+  }
+}
 
 // Host threshold tables (tables.cpp).
 int delay_thresholds(double mu, double sigma, double dt, std::vector<uint32_t>& thr, uint32_t& base);

@@ -448,6 +448,14 @@ namespace snc {
 // snc_last_error(NULL).
 void set_last_error(const char* msg) { g_last_error = msg; }
 
+snc_status abi_exception(const char* what) noexcept {
+  try {
+    g_last_error = std::string("host resources exhausted: ") + what;
+  } catch (...) {
+  }
+  return SNC_ERR_OOM;
+}
+
 snc_status estimate_build(const snc_ctx* c, BuildEstimate* e) {
   if (!c || !e) return SNC_ERR_INVALID_ARG;
   uint64_t n = 0, redraw_slots = 0, redraw_table = 0, primaries = 0;
@@ -520,68 +528,74 @@ bool ctx_sharded(const snc_ctx* c) { return c->sharded; }
 extern "C" {
 
 snc_status snc_create(const snc_config* cfg, snc_ctx** out) {
-  if (!cfg || !out) return fail(nullptr, SNC_ERR_INVALID_ARG, "snc_create: null argument");
-  if (!(cfg->dt_ms > 0.0) || !std::isfinite(cfg->dt_ms)) return fail(nullptr, SNC_ERR_INVALID_ARG, "dt must be > 0");
-  if (cfg->allocator && (!cfg->allocator->alloc || !cfg->allocator->free))
-    return fail(nullptr, SNC_ERR_INVALID_ARG, "allocator without alloc/free");
-  if (cudaSetDevice(cfg->device) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(nullptr, SNC_ERR_CUDA, "cannot select device %d", cfg->device);
-  }
-  snc_ctx* c = new (std::nothrow) snc_ctx();
-  if (!c) return fail(nullptr, SNC_ERR_OOM, "out of host memory");
-  c->cfg = *cfg;
-  c->device = cfg->device;
-  c->stream = static_cast<cudaStream_t>(cfg->stream);
-  c->store = std::make_shared<Storage>();
-  c->store->device = c->device;
-  c->store->stream = c->stream;
-  if (cfg->allocator) {
-    c->store->alloc = *cfg->allocator;
-    c->store->custom_alloc = true;
-  }
-  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
-  if (!c->store->init_host(64)) {
-    delete c;
-    return fail(nullptr, SNC_ERR_CUDA, "event / pinned staging allocation failed");
-  }
-  *out = c;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!cfg || !out) return fail(nullptr, SNC_ERR_INVALID_ARG, "snc_create: null argument");
+    if (!(cfg->dt_ms > 0.0) || !std::isfinite(cfg->dt_ms)) return fail(nullptr, SNC_ERR_INVALID_ARG, "dt must be > 0");
+    if (cfg->allocator && (!cfg->allocator->alloc || !cfg->allocator->free))
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "allocator without alloc/free");
+    if (cudaSetDevice(cfg->device) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(nullptr, SNC_ERR_CUDA, "cannot select device %d", cfg->device);
+    }
+    std::unique_ptr<snc_ctx> owner(new (std::nothrow) snc_ctx());  // freed if anything below throws
+    snc_ctx* c = owner.get();
+    if (!c) return fail(nullptr, SNC_ERR_OOM, "out of host memory");
+    c->cfg = *cfg;
+    c->device = cfg->device;
+    c->stream = static_cast<cudaStream_t>(cfg->stream);
+    c->store = std::make_shared<Storage>();
+    c->store->device = c->device;
+    c->store->stream = c->stream;
+    if (cfg->allocator) {
+      c->store->alloc = *cfg->allocator;
+      c->store->custom_alloc = true;
+    }
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (!c->store->init_host(64)) return fail(nullptr, SNC_ERR_CUDA, "event / pinned staging allocation failed");
+    *out = owner.release();
+    return SNC_OK;
+  });
 }
 
 snc_status snc_destroy(snc_ctx* c) {
-  if (!c) return SNC_OK;
-  cudaSetDevice(c->device);
-  c->store.reset();  // the build's memory goes with its last member
-  cudaGetLastError();
-  delete c;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return SNC_OK;
+    cudaSetDevice(c->device);
+    c->store.reset();  // the build's memory goes with its last member
+    cudaGetLastError();
+    delete c;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_create_population(snc_ctx* c, uint32_t n, uint32_t* first_id) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  if (c->finalized) return fail(c, SNC_ERR_STATE, "create_population after finalize");
-  if (c->n_nodes + n > 0xFFFFFFFFull) return fail(c, SNC_ERR_INVALID_ARG, "more than 2^32 - 1 nodes");
-  if (first_id) *first_id = static_cast<uint32_t>(c->n_nodes);
-  c->n_nodes += n;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    if (c->finalized) return fail(c, SNC_ERR_STATE, "create_population after finalize");
+    if (c->n_nodes + n > 0xFFFFFFFFull) return fail(c, SNC_ERR_INVALID_ARG, "more than 2^32 - 1 nodes");
+    if (first_id) *first_id = static_cast<uint32_t>(c->n_nodes);
+    c->n_nodes += n;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_connect(snc_ctx* c, snc_range src, snc_range tgt, const snc_conn_rule* rule,
                        const snc_syn_spec* syn, uint32_t* proj_id) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  if (!rule || !syn) return fail(c, SNC_ERR_INVALID_ARG, "connect: null rule or synapse spec");
-  if (c->finalized) return fail(c, SNC_ERR_STATE, "connect after finalize");
-  Projection p;
-  p.src = src;
-  p.tgt = tgt;
-  p.rule = *rule;
-  p.syn = *syn;
-  const snc_status st = plan_projection(c, p);
-  if (st != SNC_OK) return st;
-  if (proj_id) *proj_id = static_cast<uint32_t>(c->projs.size());
-  c->projs.push_back(std::move(p));
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    if (!rule || !syn) return fail(c, SNC_ERR_INVALID_ARG, "connect: null rule or synapse spec");
+    if (c->finalized) return fail(c, SNC_ERR_STATE, "connect after finalize");
+    Projection p;
+    p.src = src;
+    p.tgt = tgt;
+    p.rule = *rule;
+    p.syn = *syn;
+    const snc_status st = plan_projection(c, p);
+    if (st != SNC_OK) return st;
+    if (proj_id) *proj_id = static_cast<uint32_t>(c->projs.size());
+    c->projs.push_back(std::move(p));
+    return SNC_OK;
+  });
 }
 
 }  // extern "C"
@@ -1440,37 +1454,43 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
 extern "C" {
 
 snc_status snc_finalize(snc_ctx* c) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  if (c->finalized) return fail(c, SNC_ERR_STATE, "finalize called twice");
-  if (c->sharded && static_cast<uint64_t>(c->shard_first) + c->shard_n > c->n_nodes)
-    return fail(c, SNC_ERR_INVALID_ARG, "target shard [%u, %u + %u) outside the %llu nodes", c->shard_first,
-                c->shard_first, c->shard_n, static_cast<unsigned long long>(c->n_nodes));
-  return finalize_build(&c, 1);
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    if (c->finalized) return fail(c, SNC_ERR_STATE, "finalize called twice");
+    if (c->sharded && static_cast<uint64_t>(c->shard_first) + c->shard_n > c->n_nodes)
+      return fail(c, SNC_ERR_INVALID_ARG, "target shard [%u, %u + %u) outside the %llu nodes", c->shard_first,
+                  c->shard_first, c->shard_n, static_cast<unsigned long long>(c->n_nodes));
+    return finalize_build(&c, 1);
+  });
 }
 
 snc_status snc_set_target_shard(snc_ctx* c, uint32_t first, uint32_t n) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  if (c->finalized) return fail(c, SNC_ERR_STATE, "set_target_shard after finalize");
-  c->sharded = true;
-  c->shard_first = first;
-  c->shard_n = n;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    if (c->finalized) return fail(c, SNC_ERR_STATE, "set_target_shard after finalize");
+    c->sharded = true;
+    c->shard_first = first;
+    c->shard_n = n;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n) {
-  if (!ctxs || n <= 0) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: no contexts");
-  for (int i = 0; i < n; ++i) {
-    if (!ctxs[i]) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: null context");
-    if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
-    if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
-    if (ctxs[i]->sharded) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a target shard is built alone");
-    for (int j = 0; j < i; ++j)
-      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
-  }
-  const snc_status st = finalize_build(ctxs, n);
-  if (st != SNC_OK)
-    for (int i = 1; i < n; ++i) ctxs[i]->err = ctxs[0]->err;
-  return st;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!ctxs || n <= 0) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: no contexts");
+    for (int i = 0; i < n; ++i) {
+      if (!ctxs[i]) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: null context");
+      if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
+      if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
+      if (ctxs[i]->sharded) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a target shard is built alone");
+      for (int j = 0; j < i; ++j)
+        if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
+    }
+    const snc_status st = finalize_build(ctxs, n);
+    if (st != SNC_OK)
+      for (int i = 1; i < n; ++i) ctxs[i]->err = ctxs[0]->err;
+    return st;
+  });
 }
 
 namespace {
@@ -1486,333 +1506,357 @@ bool graph_eligible(const snc_ctx* c) {
 }  // namespace
 
 snc_status snc_batch_finalize_graph(snc_ctx* const* ctxs, int n) {
-  if (!ctxs || n <= 0) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: no contexts");
-  for (int i = 0; i < n; ++i) {
-    if (!ctxs[i]) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: null context");
-    if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
-    if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
-    if (ctxs[i]->sharded) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a target shard is built alone");
-    for (int j = 0; j < i; ++j)
-      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
-    if (!graph_eligible(ctxs[i]))
-      return fail(ctxs[i], SNC_ERR_UNSUPPORTED,
-                  "graph build: pairwise_bernoulli and total-number redraws need host round trips");
-  }
-  snc_ctx* c = ctxs[0];
-  Storage& S = *c->store;
-  SNC_CUDA(c, cudaSetDevice(c->device));
-  // A stream of the build's own (the legacy default stream cannot be
-  // captured), ordered after the work already queued on the caller's.
-  cudaStream_t own = nullptr;
-  SNC_CUDA(c, cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
-  S.own_stream = own;
-  cudaEvent_t ready = nullptr;
-  SNC_CUDA(c, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-  cudaEventRecord(ready, c->stream);
-  cudaStreamWaitEvent(own, ready, 0);
-  cudaEventDestroy(ready);
-  for (int i = 0; i < n; ++i) snc::rebind_build(ctxs[i], own, nullptr);
-  // First build: runs now and keeps every buffer, recording their order.
-  S.mode = 1;
-  S.rec.clear();
-  snc_status st = finalize_build(ctxs, n);
-  if (st != SNC_OK) {
-    for (int i = 1; i < n; ++i) ctxs[i]->err = ctxs[0]->err;
-    return st;
-  }
-  // Second pass over the same plan, captured: the same buffers in the same
-  // order, copies from a fresh staging chunk that the graph keeps reading.
-  if (!S.reserve_stage(S.stage_total + 4096)) return fail(c, SNC_ERR_OOM, "pinned staging allocation failed");
-  S.mode = 2;
-  S.rec_pos = 0;
-  S.capturing = true;
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(S.stream, cudaStreamCaptureModeRelaxed);
-  if (e == cudaSuccess) {
-    st = finalize_build(ctxs, n);
-    const cudaError_t e2 = cudaStreamEndCapture(S.stream, &graph);
-    if (e2 != cudaSuccess) e = e2;
-  }
-  S.capturing = false;
-  S.mode = 1;
-  if (e == cudaSuccess && st == SNC_OK) e = cudaGraphInstantiate(&S.gexec, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    S.gexec = nullptr;
-    return fail(c, SNC_ERR_CUDA, "graph capture of the build failed: %s", cudaGetErrorString(e));
-  }
-  if (st != SNC_OK) return st;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!ctxs || n <= 0) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: no contexts");
+    for (int i = 0; i < n; ++i) {
+      if (!ctxs[i]) return fail(nullptr, SNC_ERR_INVALID_ARG, "batch: null context");
+      if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
+      if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
+      if (ctxs[i]->sharded) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a target shard is built alone");
+      for (int j = 0; j < i; ++j)
+        if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
+      if (!graph_eligible(ctxs[i]))
+        return fail(ctxs[i], SNC_ERR_UNSUPPORTED,
+                    "graph build: pairwise_bernoulli and total-number redraws need host round trips");
+    }
+    snc_ctx* c = ctxs[0];
+    Storage& S = *c->store;
+    SNC_CUDA(c, cudaSetDevice(c->device));
+    // A stream of the build's own (the legacy default stream cannot be
+    // captured), ordered after the work already queued on the caller's.
+    cudaStream_t own = nullptr;
+    SNC_CUDA(c, cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    S.own_stream = own;
+    cudaEvent_t ready = nullptr;
+    SNC_CUDA(c, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    cudaEventRecord(ready, c->stream);
+    cudaStreamWaitEvent(own, ready, 0);
+    cudaEventDestroy(ready);
+    for (int i = 0; i < n; ++i) snc::rebind_build(ctxs[i], own, nullptr);
+    // First build: runs now and keeps every buffer, recording their order.
+    S.mode = 1;
+    S.rec.clear();
+    snc_status st = finalize_build(ctxs, n);
+    if (st != SNC_OK) {
+      for (int i = 1; i < n; ++i) ctxs[i]->err = ctxs[0]->err;
+      return st;
+    }
+    // Second pass over the same plan, captured: the same buffers in the same
+    // order, copies from a fresh staging chunk that the graph keeps reading.
+    if (!S.reserve_stage(S.stage_total + 4096)) return fail(c, SNC_ERR_OOM, "pinned staging allocation failed");
+    S.mode = 2;
+    S.rec_pos = 0;
+    S.capturing = true;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(S.stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      st = finalize_build(ctxs, n);
+      const cudaError_t e2 = cudaStreamEndCapture(S.stream, &graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    S.capturing = false;
+    S.mode = 1;
+    if (e == cudaSuccess && st == SNC_OK) e = cudaGraphInstantiate(&S.gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      S.gexec = nullptr;
+      return fail(c, SNC_ERR_CUDA, "graph capture of the build failed: %s", cudaGetErrorString(e));
+    }
+    if (st != SNC_OK) return st;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_batch_rebuild(snc_ctx* ctx, const uint64_t* seeds, int n) {
-  if (!ctx || !seeds) return fail(ctx, SNC_ERR_INVALID_ARG, "rebuild: null argument");
-  if (!ctx->finalized || !ctx->store || !ctx->store->gexec)
-    return fail(ctx, SNC_ERR_STATE, "rebuild: the context was not built by snc_batch_finalize_graph");
-  Storage& S = *ctx->store;
-  if (n != S.n_members) return fail(ctx, SNC_ERR_INVALID_ARG, "rebuild: %d seeds for %d networks", n, S.n_members);
-  SNC_CUDA(ctx, cudaSetDevice(ctx->device));
-  // The replayed copies read the staged records: the previous build must be done.
-  SNC_CUDA(ctx, cudaStreamSynchronize(S.stream));
-  for (const Storage::SeedSite& site : S.seed_sites) {
-    const uint64_t seed = seeds[site.member];
-    site.host->k0 = static_cast<uint32_t>(seed);
-    site.host->k1 = static_cast<uint32_t>(seed >> 32) ^ site.local;
-  }
-  ctx->cfg.seed = seeds[ctx->member];
-  S.synced = false;
-  ++S.generation;
-  SNC_CUDA(ctx, cudaGraphLaunch(S.gexec, S.stream));
-  ++ctx->stats.kernel_launches;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!ctx || !seeds) return fail(ctx, SNC_ERR_INVALID_ARG, "rebuild: null argument");
+    if (!ctx->finalized || !ctx->store || !ctx->store->gexec)
+      return fail(ctx, SNC_ERR_STATE, "rebuild: the context was not built by snc_batch_finalize_graph");
+    Storage& S = *ctx->store;
+    if (n != S.n_members) return fail(ctx, SNC_ERR_INVALID_ARG, "rebuild: %d seeds for %d networks", n, S.n_members);
+    SNC_CUDA(ctx, cudaSetDevice(ctx->device));
+    // The replayed copies read the staged records: the previous build must be done.
+    SNC_CUDA(ctx, cudaStreamSynchronize(S.stream));
+    for (const Storage::SeedSite& site : S.seed_sites) {
+      const uint64_t seed = seeds[site.member];
+      site.host->k0 = static_cast<uint32_t>(seed);
+      site.host->k1 = static_cast<uint32_t>(seed >> 32) ^ site.local;
+    }
+    ctx->cfg.seed = seeds[ctx->member];
+    S.synced = false;
+    ++S.generation;
+    SNC_CUDA(ctx, cudaGraphLaunch(S.gexec, S.stream));
+    ++ctx->stats.kernel_launches;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_synchronize(snc_ctx* c) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  SNC_CUDA(c, cudaSetDevice(c->device));
-  Storage& S = *c->store;
-  SNC_CUDA(c, cudaStreamSynchronize(S.stream));
-  if (!c->finalized) return SNC_OK;
-  if (!S.synced) {
-    SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + 4, S.d_err, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, S.stream));
-    SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + 1, S.d_n_groups, sizeof(uint64_t), cudaMemcpyDeviceToHost, S.stream));
-    c->stats.d2h_bytes += 5 * sizeof(uint64_t);
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    SNC_CUDA(c, cudaSetDevice(c->device));
+    Storage& S = *c->store;
     SNC_CUDA(c, cudaStreamSynchronize(S.stream));
-    S.err_bits = static_cast<uint32_t>(S.h_pinned[4] & 0xFFFFFFFFu);
-    S.n_groups = S.h_pinned[1];
-    S.synced = true;
-  }
-  if (!c->view_ready || c->view_gen != S.generation) {
-    const uint64_t g0 = S.h_bases[c->member], g1 = S.h_bases[c->member + 1];
-    c->n_syn = c->seg_count;
-    c->n_groups = g1 - g0;
-    c->target = c->target_all + c->seg_begin;
-    c->delay = c->delay_all + c->seg_begin;
-    c->weight = c->weight_all + c->seg_begin;
-    c->group_first = c->group_first_all + g0;
-    c->view_ready = true;
-    c->view_gen = S.generation;
-  }
-  const uint32_t err = S.err_bits;
-  if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
-  if (err & kErrSamplerBound) return fail(c, SNC_ERR_TIMEOUT, "a sampler exceeded its attempt bound");
-  if (err & kErrBounds) {
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(S.h_pinned + 4);
-    return fail(c, SNC_ERR_CUDA, "a device index check failed (site %u, index %llu, limit %llu)", w[2],
-                static_cast<unsigned long long>(w[4] | (static_cast<uint64_t>(w[5]) << 32)),
-                static_cast<unsigned long long>(w[6] | (static_cast<uint64_t>(w[7]) << 32)));
-  }
-  return SNC_OK;
+    if (!c->finalized) return SNC_OK;
+    if (!S.synced) {
+      SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + 4, S.d_err, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, S.stream));
+      SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned + 1, S.d_n_groups, sizeof(uint64_t), cudaMemcpyDeviceToHost, S.stream));
+      c->stats.d2h_bytes += 5 * sizeof(uint64_t);
+      SNC_CUDA(c, cudaStreamSynchronize(S.stream));
+      S.err_bits = static_cast<uint32_t>(S.h_pinned[4] & 0xFFFFFFFFu);
+      S.n_groups = S.h_pinned[1];
+      S.synced = true;
+    }
+    if (!c->view_ready || c->view_gen != S.generation) {
+      const uint64_t g0 = S.h_bases[c->member], g1 = S.h_bases[c->member + 1];
+      c->n_syn = c->seg_count;
+      c->n_groups = g1 - g0;
+      c->target = c->target_all + c->seg_begin;
+      c->delay = c->delay_all + c->seg_begin;
+      c->weight = c->weight_all + c->seg_begin;
+      c->group_first = c->group_first_all + g0;
+      c->view_ready = true;
+      c->view_gen = S.generation;
+    }
+    const uint32_t err = S.err_bits;
+    if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
+    if (err & kErrSamplerBound) return fail(c, SNC_ERR_TIMEOUT, "a sampler exceeded its attempt bound");
+    if (err & kErrBounds) {
+      const uint32_t* w = reinterpret_cast<const uint32_t*>(S.h_pinned + 4);
+      return fail(c, SNC_ERR_CUDA, "a device index check failed (site %u, index %llu, limit %llu)", w[2],
+                  static_cast<unsigned long long>(w[4] | (static_cast<uint64_t>(w[5]) << 32)),
+                  static_cast<unsigned long long>(w[6] | (static_cast<uint64_t>(w[7]) << 32)));
+    }
+    return SNC_OK;
+  });
 }
 
 snc_status snc_get_connections(snc_ctx* c, snc_conn_view* out) {
-  if (!c || !out) return fail(c, SNC_ERR_INVALID_ARG, "null argument");
-  if (!c->finalized) return fail(c, SNC_ERR_STATE, "get_connections before finalize");
-  const snc_status st = snc_synchronize(c);
-  if (st != SNC_OK) return st;
-  out->n_syn = c->n_syn;
-  out->n_nodes = c->n_nodes;
-  out->n_groups = c->n_groups;
-  out->row_ptr = c->row_ptr;
-  out->target = c->target;
-  out->delay = c->delay;
-  out->weight = c->weight;
-  out->group_ptr = c->group_ptr;
-  out->group_first = c->group_first;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c || !out) return fail(c, SNC_ERR_INVALID_ARG, "null argument");
+    if (!c->finalized) return fail(c, SNC_ERR_STATE, "get_connections before finalize");
+    const snc_status st = snc_synchronize(c);
+    if (st != SNC_OK) return st;
+    out->n_syn = c->n_syn;
+    out->n_nodes = c->n_nodes;
+    out->n_groups = c->n_groups;
+    out->row_ptr = c->row_ptr;
+    out->target = c->target;
+    out->delay = c->delay;
+    out->weight = c->weight;
+    out->group_ptr = c->group_ptr;
+    out->group_first = c->group_first;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_deliver(snc_ctx* c, const uint32_t* src, const uint32_t* grp, const float* mult,
                        uint64_t n_spikes, float* input) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  if (!c->finalized) return fail(c, SNC_ERR_STATE, "deliver before finalize");
-  snc_conn_view v{};
-  snc_status s = snc_get_connections(c, &v);  // synchronizes and resolves the views
-  if (s != SNC_OK) return s;
-  if (n_spikes == 0) return SNC_OK;
-  if (!src || !grp || !mult || !input) return fail(c, SNC_ERR_INVALID_ARG, "null spike array or input");
-  CallScope scope(c);
-  cudaStream_t st = c->store->stream;
-  uint32_t* sizes = static_cast<uint32_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint32_t)));
-  uint64_t* offsets = static_cast<uint64_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint64_t)));
-  uint64_t* tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_spikes) + 1) * sizeof(uint64_t)));
-  uint64_t* first = static_cast<uint64_t*>(dev_alloc(c, n_spikes * sizeof(uint64_t)));
-  uint32_t* err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint32_t)));
-  if (!sizes || !offsets || !tmp || !first || !err) {
-    for (void* p : {static_cast<void*>(sizes), static_cast<void*>(offsets), static_cast<void*>(tmp),
-                    static_cast<void*>(first), static_cast<void*>(err)})
-      dev_free(c, p);
-    return fail(c, SNC_ERR_OOM, "device allocation failed (spike array)");
-  }
-  SNC_CUDA(c, cudaMemsetAsync(err, 0, 8 * sizeof(uint32_t), st));
-  DeliverArgs a{};
-  a.src = src;
-  a.grp = grp;
-  a.mult = mult;
-  a.n_spikes = n_spikes;
-  a.row_ptr = v.row_ptr;
-  a.group_ptr = v.group_ptr;
-  a.group_first = v.group_first;
-  a.target = v.target;
-  a.weight = v.weight;
-  a.n_nodes = v.n_nodes;
-  a.n_syn = v.n_syn;
-  a.sizes = sizes;
-  a.first = first;
-  a.offsets = offsets;
-  a.input = input;
-  a.err = err;
-  const unsigned g1 = static_cast<unsigned>(
-      std::max<uint64_t>(1, std::min<uint64_t>((n_spikes + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
-  deliver_size_kernel<<<g1, 256, 0, st>>>(a);
-  SNC_CUDA(c, exclusive_scan_u32(sizes, n_spikes, offsets, tmp, st));
-  deliver_kernel<<<static_cast<unsigned>(c->sms) * 8, kDeliverThreads, 0, st>>>(a);
-  SNC_CUDA(c, cudaGetLastError());
-  c->stats.kernel_launches += 5;
-  uint32_t* h_err = reinterpret_cast<uint32_t*>(c->store->h_pinned + 12);
-  SNC_CUDA(c, cudaMemcpyAsync(h_err, err, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  SNC_CUDA(c, cudaStreamSynchronize(st));
-  const uint32_t bits = h_err[0];
-  dev_free(c, sizes);
-  dev_free(c, offsets);
-  dev_free(c, tmp);
-  dev_free(c, first);
-  dev_free(c, err);
-  if (bits & kErrBounds) return fail(c, SNC_ERR_INVALID_ARG, "a spike array entry names no connection group");
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    if (!c->finalized) return fail(c, SNC_ERR_STATE, "deliver before finalize");
+    snc_conn_view v{};
+    snc_status s = snc_get_connections(c, &v);  // synchronizes and resolves the views
+    if (s != SNC_OK) return s;
+    if (n_spikes == 0) return SNC_OK;
+    if (!src || !grp || !mult || !input) return fail(c, SNC_ERR_INVALID_ARG, "null spike array or input");
+    CallScope scope(c);
+    cudaStream_t st = c->store->stream;
+    uint32_t* sizes = static_cast<uint32_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint32_t)));
+    uint64_t* offsets = static_cast<uint64_t*>(dev_alloc(c, (n_spikes + 1) * sizeof(uint64_t)));
+    uint64_t* tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_spikes) + 1) * sizeof(uint64_t)));
+    uint64_t* first = static_cast<uint64_t*>(dev_alloc(c, n_spikes * sizeof(uint64_t)));
+    uint32_t* err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint32_t)));
+    if (!sizes || !offsets || !tmp || !first || !err) {
+      for (void* p : {static_cast<void*>(sizes), static_cast<void*>(offsets), static_cast<void*>(tmp),
+                      static_cast<void*>(first), static_cast<void*>(err)})
+        dev_free(c, p);
+      return fail(c, SNC_ERR_OOM, "device allocation failed (spike array)");
+    }
+    SNC_CUDA(c, cudaMemsetAsync(err, 0, 8 * sizeof(uint32_t), st));
+    DeliverArgs a{};
+    a.src = src;
+    a.grp = grp;
+    a.mult = mult;
+    a.n_spikes = n_spikes;
+    a.row_ptr = v.row_ptr;
+    a.group_ptr = v.group_ptr;
+    a.group_first = v.group_first;
+    a.target = v.target;
+    a.weight = v.weight;
+    a.n_nodes = v.n_nodes;
+    a.n_syn = v.n_syn;
+    a.sizes = sizes;
+    a.first = first;
+    a.offsets = offsets;
+    a.input = input;
+    a.err = err;
+    const unsigned g1 = static_cast<unsigned>(
+        std::max<uint64_t>(1, std::min<uint64_t>((n_spikes + 255) / 256, static_cast<uint64_t>(c->sms) * 16)));
+    deliver_size_kernel<<<g1, 256, 0, st>>>(a);
+    SNC_CUDA(c, exclusive_scan_u32(sizes, n_spikes, offsets, tmp, st));
+    deliver_kernel<<<static_cast<unsigned>(c->sms) * 8, kDeliverThreads, 0, st>>>(a);
+    SNC_CUDA(c, cudaGetLastError());
+    c->stats.kernel_launches += 5;
+    uint32_t* h_err = reinterpret_cast<uint32_t*>(c->store->h_pinned + 12);
+    SNC_CUDA(c, cudaMemcpyAsync(h_err, err, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    SNC_CUDA(c, cudaStreamSynchronize(st));
+    const uint32_t bits = h_err[0];
+    dev_free(c, sizes);
+    dev_free(c, offsets);
+    dev_free(c, tmp);
+    dev_free(c, first);
+    dev_free(c, err);
+    if (bits & kErrBounds) return fail(c, SNC_ERR_INVALID_ARG, "a spike array entry names no connection group");
+    return SNC_OK;
+  });
 }
 
 snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16_t* delay, float* weight,
                                 uint64_t cap) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  if (!c->finalized) return fail(c, SNC_ERR_STATE, "copy_connections before finalize");
-  snc_status s = snc_synchronize(c);
-  if (s != SNC_OK) return s;
-  if (cap < c->n_syn) return fail(c, SNC_ERR_INVALID_ARG, "capacity below the number of connections");
-  const uint64_t n = c->n_syn;
-  CallScope scope(c);
-  cudaStream_t st = c->store->stream;
-  if (src && n > 0) {
-    uint32_t* d_src = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
-    if (!d_src) return fail(c, SNC_ERR_OOM, "device allocation failed (source expansion)");
-    if (c->n_nodes > 0) {
-      const uint64_t blocks = std::min<uint64_t>((c->n_nodes + 7) / 8, static_cast<uint64_t>(c->sms) * 16);
-      expand_sources_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(c->row_ptr, c->n_nodes, d_src);
-      ++c->stats.kernel_launches;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    if (!c->finalized) return fail(c, SNC_ERR_STATE, "copy_connections before finalize");
+    snc_status s = snc_synchronize(c);
+    if (s != SNC_OK) return s;
+    if (cap < c->n_syn) return fail(c, SNC_ERR_INVALID_ARG, "capacity below the number of connections");
+    const uint64_t n = c->n_syn;
+    CallScope scope(c);
+    cudaStream_t st = c->store->stream;
+    if (src && n > 0) {
+      uint32_t* d_src = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+      if (!d_src) return fail(c, SNC_ERR_OOM, "device allocation failed (source expansion)");
+      if (c->n_nodes > 0) {
+        const uint64_t blocks = std::min<uint64_t>((c->n_nodes + 7) / 8, static_cast<uint64_t>(c->sms) * 16);
+        expand_sources_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(c->row_ptr, c->n_nodes, d_src);
+        ++c->stats.kernel_launches;
+      }
+      SNC_CUDA(c, cudaGetLastError());
+      SNC_CUDA(c, cudaMemcpyAsync(src, d_src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      dev_free(c, d_src);  // stream-ordered: after the copy
     }
-    SNC_CUDA(c, cudaGetLastError());
-    SNC_CUDA(c, cudaMemcpyAsync(src, d_src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    dev_free(c, d_src);  // stream-ordered: after the copy
-  }
-  if (tgt && n > 0) SNC_CUDA(c, cudaMemcpyAsync(tgt, c->target, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  if (delay && n > 0) SNC_CUDA(c, cudaMemcpyAsync(delay, c->delay, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
-  if (weight && n > 0) SNC_CUDA(c, cudaMemcpyAsync(weight, c->weight, n * sizeof(float), cudaMemcpyDeviceToHost, st));
-  c->stats.d2h_bytes += n * ((src ? 4 : 0) + (tgt ? 4 : 0) + (delay ? 2 : 0) + (weight ? 4 : 0));
-  SNC_CUDA(c, cudaStreamSynchronize(st));
-  return SNC_OK;
+    if (tgt && n > 0) SNC_CUDA(c, cudaMemcpyAsync(tgt, c->target, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (delay && n > 0) SNC_CUDA(c, cudaMemcpyAsync(delay, c->delay, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
+    if (weight && n > 0) SNC_CUDA(c, cudaMemcpyAsync(weight, c->weight, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    c->stats.d2h_bytes += n * ((src ? 4 : 0) + (tgt ? 4 : 0) + (delay ? 2 : 0) + (weight ? 4 : 0));
+    SNC_CUDA(c, cudaStreamSynchronize(st));
+    return SNC_OK;
+  });
 }
 
 snc_status snc_copy_index(snc_ctx* c, uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
                           uint64_t group_cap) {
-  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-  if (!c->finalized) return fail(c, SNC_ERR_STATE, "copy_index before finalize");
-  snc_status s = snc_synchronize(c);
-  if (s != SNC_OK) return s;
-  if (group_first && group_cap < c->n_groups) return fail(c, SNC_ERR_INVALID_ARG, "group capacity below n_groups");
-  cudaStream_t st = c->store->stream;
-  const size_t rows = (c->n_nodes + 1) * sizeof(uint64_t);
-  if (row_ptr) SNC_CUDA(c, cudaMemcpyAsync(row_ptr, c->row_ptr, rows, cudaMemcpyDeviceToHost, st));
-  if (group_ptr) SNC_CUDA(c, cudaMemcpyAsync(group_ptr, c->group_ptr, rows, cudaMemcpyDeviceToHost, st));
-  if (group_first && c->n_groups > 0)
-    SNC_CUDA(c, cudaMemcpyAsync(group_first, c->group_first, c->n_groups * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-  c->stats.d2h_bytes += (row_ptr ? rows : 0) + (group_ptr ? rows : 0) + (group_first ? c->n_groups * sizeof(uint64_t) : 0);
-  SNC_CUDA(c, cudaStreamSynchronize(st));
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    if (!c->finalized) return fail(c, SNC_ERR_STATE, "copy_index before finalize");
+    snc_status s = snc_synchronize(c);
+    if (s != SNC_OK) return s;
+    if (group_first && group_cap < c->n_groups) return fail(c, SNC_ERR_INVALID_ARG, "group capacity below n_groups");
+    cudaStream_t st = c->store->stream;
+    const size_t rows = (c->n_nodes + 1) * sizeof(uint64_t);
+    if (row_ptr) SNC_CUDA(c, cudaMemcpyAsync(row_ptr, c->row_ptr, rows, cudaMemcpyDeviceToHost, st));
+    if (group_ptr) SNC_CUDA(c, cudaMemcpyAsync(group_ptr, c->group_ptr, rows, cudaMemcpyDeviceToHost, st));
+    if (group_first && c->n_groups > 0)
+      SNC_CUDA(c, cudaMemcpyAsync(group_first, c->group_first, c->n_groups * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    c->stats.d2h_bytes += (row_ptr ? rows : 0) + (group_ptr ? rows : 0) + (group_first ? c->n_groups * sizeof(uint64_t) : 0);
+    SNC_CUDA(c, cudaStreamSynchronize(st));
+    return SNC_OK;
+  });
 }
 
 snc_status snc_stage_times(snc_ctx* c, float* ms, int max_stages, int* n_stages, int* n_passes) {
-  if (!c || !ms || max_stages < 0) return fail(c, SNC_ERR_INVALID_ARG, "null argument");
-  if (!c->finalized) return fail(c, SNC_ERR_STATE, "no finalize has run");
-  Storage& S = *c->store;
-  SNC_CUDA(c, cudaStreamSynchronize(S.stream));
-  int k = 0;
-  for (int i = 1; i < S.n_ev && k < max_stages; ++i, ++k) {
-    float t = 0.f;
-    SNC_CUDA(c, cudaEventElapsedTime(&t, S.ev[i - 1], S.ev[i]));
-    ms[k] = t;
-  }
-  if (n_stages) *n_stages = k;
-  if (n_passes) *n_passes = c->sort_stages;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c || !ms || max_stages < 0) return fail(c, SNC_ERR_INVALID_ARG, "null argument");
+    if (!c->finalized) return fail(c, SNC_ERR_STATE, "no finalize has run");
+    Storage& S = *c->store;
+    SNC_CUDA(c, cudaStreamSynchronize(S.stream));
+    int k = 0;
+    for (int i = 1; i < S.n_ev && k < max_stages; ++i, ++k) {
+      float t = 0.f;
+      SNC_CUDA(c, cudaEventElapsedTime(&t, S.ev[i - 1], S.ev[i]));
+      ms[k] = t;
+    }
+    if (n_stages) *n_stages = k;
+    if (n_passes) *n_passes = c->sort_stages;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                                 uint32_t* vals_out, uint64_t n, int key_bits, void* stream) {
-  if (key_bits < 1 || key_bits > 64) return fail(nullptr, SNC_ERR_INVALID_ARG, "key_bits outside [1, 64]");
-  if (n == 0) return SNC_OK;
-  if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(nullptr, SNC_ERR_INVALID_ARG, "null buffer");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const SortPasses sp = plan_passes(key_bits);
-  const size_t scratch_bytes = sort_scratch_bytes(n, sp);
-  void* scratch = nullptr;
-  uint64_t* ktmp = nullptr;
-  uint32_t* vtmp = nullptr;
-  uint32_t* err = nullptr;
-  auto release = [&]() {
-    if (scratch) cudaFreeAsync(scratch, st);
-    if (ktmp) cudaFreeAsync(ktmp, st);
-    if (vtmp) cudaFreeAsync(vtmp, st);
-    if (err) cudaFreeAsync(err, st);
-  };
-  if (cudaMallocAsync(&scratch, scratch_bytes, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&err), 256, st) != cudaSuccess ||
-      (sp.n_passes > 1 && (cudaMallocAsync(reinterpret_cast<void**>(&ktmp), n * sizeof(uint64_t), st) != cudaSuccess ||
-                           cudaMallocAsync(reinterpret_cast<void**>(&vtmp), n * sizeof(uint32_t), st) != cudaSuccess))) {
-    cudaGetLastError();
+  return snc::abi_guard([&]() -> snc_status {
+    if (key_bits < 1 || key_bits > 64) return fail(nullptr, SNC_ERR_INVALID_ARG, "key_bits outside [1, 64]");
+    if (n == 0) return SNC_OK;
+    if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(nullptr, SNC_ERR_INVALID_ARG, "null buffer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const SortPasses sp = plan_passes(key_bits);
+    const size_t scratch_bytes = sort_scratch_bytes(n, sp);
+    void* scratch = nullptr;
+    uint64_t* ktmp = nullptr;
+    uint32_t* vtmp = nullptr;
+    uint32_t* err = nullptr;
+    auto release = [&]() {
+      if (scratch) cudaFreeAsync(scratch, st);
+      if (ktmp) cudaFreeAsync(ktmp, st);
+      if (vtmp) cudaFreeAsync(vtmp, st);
+      if (err) cudaFreeAsync(err, st);
+    };
+    if (cudaMallocAsync(&scratch, scratch_bytes, st) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&err), 256, st) != cudaSuccess ||
+        (sp.n_passes > 1 && (cudaMallocAsync(reinterpret_cast<void**>(&ktmp), n * sizeof(uint64_t), st) != cudaSuccess ||
+                             cudaMallocAsync(reinterpret_cast<void**>(&vtmp), n * sizeof(uint32_t), st) != cudaSuccess))) {
+      cudaGetLastError();
+      release();
+      return fail(nullptr, SNC_ERR_OOM, "sort scratch allocation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(err, 0, 256, st);
+    if (e == cudaSuccess) e = radix_sort_run(keys_in, vals_in, keys_out, vals_out, ktmp, vtmp, n, sp, scratch, err, st, nullptr);
     release();
-    return fail(nullptr, SNC_ERR_OOM, "sort scratch allocation failed");
-  }
-  cudaError_t e = cudaMemsetAsync(err, 0, 256, st);
-  if (e == cudaSuccess) e = radix_sort_run(keys_in, vals_in, keys_out, vals_out, ktmp, vtmp, n, sp, scratch, err, st, nullptr);
-  release();
-  if (e != cudaSuccess) return fail(nullptr, SNC_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e));
-  return SNC_OK;
+    if (e != cudaSuccess) return fail(nullptr, SNC_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e));
+    return SNC_OK;
+  });
 }
 
 snc_status snc_set_tuning(const snc_tuning* t) {
-  if (!t) return fail(nullptr, SNC_ERR_INVALID_ARG, "null tuning");
-  if (t->sort_digit_bits < 8 || t->sort_digit_bits > 11)
-    return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_digit_bits outside [8, 11]");
-  if (t->sort_group_tiles != 0 && t->sort_group_tiles != 1 && t->sort_group_tiles != 4 && t->sort_group_tiles != 8)
-    return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_group_tiles must be 0, 1, 4 or 8");
-  if (t->gen_blocks_per_sm < 1 || t->gen_blocks_per_sm > 32)
-    return fail(nullptr, SNC_ERR_INVALID_ARG, "gen_blocks_per_sm outside [1, 32]");
-  if (t->sort_items != 8 && t->sort_items != 12 && t->sort_items != 16 && t->sort_items != 24 && t->sort_items != 32)
-    return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_items must be 8, 12, 16, 24 or 32");
-  if (t->reserved[0] || t->reserved[1] || t->reserved[2] || t->reserved[3])
-    return fail(nullptr, SNC_ERR_INVALID_ARG, "reserved tuning fields must be 0");
-  g_sort_tuning.max_digit_bits = t->sort_digit_bits;
-  g_sort_tuning.group_tiles = t->sort_group_tiles;
-  g_sort_tuning.items = t->sort_items;
-  g_gen_blocks_per_sm = t->gen_blocks_per_sm;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!t) return fail(nullptr, SNC_ERR_INVALID_ARG, "null tuning");
+    if (t->sort_digit_bits < 8 || t->sort_digit_bits > 11)
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_digit_bits outside [8, 11]");
+    if (t->sort_group_tiles != 0 && t->sort_group_tiles != 1 && t->sort_group_tiles != 4 && t->sort_group_tiles != 8)
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_group_tiles must be 0, 1, 4 or 8");
+    if (t->gen_blocks_per_sm < 1 || t->gen_blocks_per_sm > 32)
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "gen_blocks_per_sm outside [1, 32]");
+    if (t->sort_items != 8 && t->sort_items != 12 && t->sort_items != 16 && t->sort_items != 24 && t->sort_items != 32)
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "sort_items must be 8, 12, 16, 24 or 32");
+    if (t->reserved[0] || t->reserved[1] || t->reserved[2] || t->reserved[3])
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "reserved tuning fields must be 0");
+    g_sort_tuning.max_digit_bits = t->sort_digit_bits;
+    g_sort_tuning.group_tiles = t->sort_group_tiles;
+    g_sort_tuning.items = t->sort_items;
+    g_gen_blocks_per_sm = t->gen_blocks_per_sm;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_get_tuning(snc_tuning* t) {
-  if (!t) return fail(nullptr, SNC_ERR_INVALID_ARG, "null tuning");
-  t->sort_digit_bits = g_sort_tuning.max_digit_bits;
-  t->sort_group_tiles = g_sort_tuning.group_tiles;
-  t->gen_blocks_per_sm = g_gen_blocks_per_sm;
-  t->sort_items = g_sort_tuning.items;
-  t->reserved[0] = t->reserved[1] = t->reserved[2] = t->reserved[3] = 0;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!t) return fail(nullptr, SNC_ERR_INVALID_ARG, "null tuning");
+    t->sort_digit_bits = g_sort_tuning.max_digit_bits;
+    t->sort_group_tiles = g_sort_tuning.group_tiles;
+    t->gen_blocks_per_sm = g_gen_blocks_per_sm;
+    t->sort_items = g_sort_tuning.items;
+    t->reserved[0] = t->reserved[1] = t->reserved[2] = t->reserved[3] = 0;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_get_stats(const snc_ctx* c, snc_stats* out) {
-  if (!c || !out) return fail(nullptr, SNC_ERR_INVALID_ARG, "null argument");
-  *out = c->stats;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c || !out) return fail(nullptr, SNC_ERR_INVALID_ARG, "null argument");
+    *out = c->stats;
+    return SNC_OK;
+  });
 }
 
 const char* snc_last_error(const snc_ctx* c) {

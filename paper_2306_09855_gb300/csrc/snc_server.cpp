@@ -216,218 +216,243 @@ snc_status server_fail(snc_status s, const char* msg) {
 extern "C" {
 
 snc_status snc_estimate_build(const snc_ctx* ctx, uint64_t* peak_bytes, uint64_t* resident_bytes, uint64_t* n_syn) {
-  if (!ctx || !peak_bytes || !resident_bytes || !n_syn)
-    return server_fail(SNC_ERR_INVALID_ARG, "snc_estimate_build: null argument");
-  snc::BuildEstimate e{};
-  const snc_status s = snc::estimate_build(ctx, &e);
-  if (s != SNC_OK) return server_fail(s, "snc_estimate_build failed");
-  *peak_bytes = e.peak_bytes;
-  *resident_bytes = e.resident_bytes;
-  *n_syn = e.n_syn;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!ctx || !peak_bytes || !resident_bytes || !n_syn)
+      return server_fail(SNC_ERR_INVALID_ARG, "snc_estimate_build: null argument");
+    snc::BuildEstimate e{};
+    const snc_status s = snc::estimate_build(ctx, &e);
+    if (s != SNC_OK) return server_fail(s, "snc_estimate_build failed");
+    *peak_bytes = e.peak_bytes;
+    *resident_bytes = e.resident_bytes;
+    *n_syn = e.n_syn;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_server_create(const snc_server_config* cfg, snc_server** out) {
-  if (!cfg || !out) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_create: null argument");
-  if (cfg->hbm_budget_bytes == 0 || cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->batch_max_nets < 1 ||
-      cfg->batch_max_nets > 256 || cfg->reserved != 0)
-    return server_fail(SNC_ERR_INVALID_ARG, "snc_server_create: configuration out of range");
-  if (cudaSetDevice(cfg->device) != cudaSuccess) {
-    cudaGetLastError();
-    return server_fail(SNC_ERR_CUDA, "snc_server_create: cannot select the device");
-  }
-  std::unique_ptr<snc_server> srv(new (std::nothrow) snc_server());
-  if (!srv) return server_fail(SNC_ERR_OOM, "out of host memory");
-  srv->cfg = *cfg;
-  cudaMemPoolProps props{};
-  props.allocType = cudaMemAllocationTypePinned;
-  props.location.type = cudaMemLocationTypeDevice;
-  props.location.id = cfg->device;
-  if (cudaMemPoolCreate(&srv->pool, &props) != cudaSuccess) {
-    cudaGetLastError();
-    return server_fail(SNC_ERR_CUDA, "snc_server_create: memory pool creation failed");
-  }
-  // Keep freed memory in the pool up to the budget instead of returning it
-  // to the driver at every synchronization.
-  uint64_t keep = cfg->hbm_budget_bytes;
-  cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-  srv->alloc.alloc = pool_alloc;
-  srv->alloc.free = pool_free;
-  srv->alloc.user = srv->pool;
-  if (cudaStreamCreateWithFlags(&srv->release_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaGetLastError();
-    cudaMemPoolDestroy(srv->pool);
-    return server_fail(SNC_ERR_CUDA, "snc_server_create: stream creation failed");
-  }
-  for (int i = 0; i < cfg->max_slots; ++i) {
-    cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+  return snc::abi_guard([&]() -> snc_status {
+    if (!cfg || !out) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_create: null argument");
+    if (cfg->hbm_budget_bytes == 0 || cfg->max_slots < 1 || cfg->max_slots > 64 || cfg->batch_max_nets < 1 ||
+        cfg->batch_max_nets > 256 || cfg->reserved != 0)
+      return server_fail(SNC_ERR_INVALID_ARG, "snc_server_create: configuration out of range");
+    if (cudaSetDevice(cfg->device) != cudaSuccess) {
       cudaGetLastError();
-      for (cudaStream_t x : srv->streams) cudaStreamDestroy(x);
-      cudaStreamDestroy(srv->release_stream);
+      return server_fail(SNC_ERR_CUDA, "snc_server_create: cannot select the device");
+    }
+    std::unique_ptr<snc_server> srv(new (std::nothrow) snc_server());
+    if (!srv) return server_fail(SNC_ERR_OOM, "out of host memory");
+    srv->cfg = *cfg;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = cfg->device;
+    if (cudaMemPoolCreate(&srv->pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return server_fail(SNC_ERR_CUDA, "snc_server_create: memory pool creation failed");
+    }
+    // Keep freed memory in the pool up to the budget instead of returning it
+    // to the driver at every synchronization.
+    uint64_t keep = cfg->hbm_budget_bytes;
+    cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    srv->alloc.alloc = pool_alloc;
+    srv->alloc.free = pool_free;
+    srv->alloc.user = srv->pool;
+    if (cudaStreamCreateWithFlags(&srv->release_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
       cudaMemPoolDestroy(srv->pool);
       return server_fail(SNC_ERR_CUDA, "snc_server_create: stream creation failed");
     }
-    srv->streams.push_back(s);
-  }
-  snc_server* p = srv.release();
-  for (int i = 0; i < cfg->max_slots; ++i) p->workers.emplace_back([p, i] { p->worker(i); });
-  *out = p;
-  return SNC_OK;
+    for (int i = 0; i < cfg->max_slots; ++i) {
+      cudaStream_t s = nullptr;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        for (cudaStream_t x : srv->streams) cudaStreamDestroy(x);
+        cudaStreamDestroy(srv->release_stream);
+        cudaMemPoolDestroy(srv->pool);
+        return server_fail(SNC_ERR_CUDA, "snc_server_create: stream creation failed");
+      }
+      srv->streams.push_back(s);
+    }
+    snc_server* p = srv.release();
+    try {
+      for (int i = 0; i < cfg->max_slots; ++i) p->workers.emplace_back([p, i] { p->worker(i); });
+    } catch (...) {
+      snc_server_destroy(p);  // joins the workers already started and frees the rest
+      throw;
+    }
+    *out = p;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_server_destroy(snc_server* srv) {
-  if (!srv) return SNC_OK;
-  {
-    std::lock_guard<std::mutex> lk(srv->mu);
-    srv->stop = true;
-  }
-  srv->cv_work.notify_all();
-  for (std::thread& t : srv->workers) t.join();
-  cudaSetDevice(srv->cfg.device);
-  for (auto& kv : srv->jobs) {
-    Job& j = *kv.second;
-    if (j.ctx) {
-      snc::rebind_build(j.ctx, srv->release_stream, nullptr);
-      snc_destroy(j.ctx);
+  return snc::abi_guard([&]() -> snc_status {
+    if (!srv) return SNC_OK;
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      srv->stop = true;
     }
-  }
-  srv->jobs.clear();
-  cudaStreamSynchronize(srv->release_stream);
-  for (cudaStream_t s : srv->streams) cudaStreamDestroy(s);
-  cudaStreamDestroy(srv->release_stream);
-  cudaMemPoolDestroy(srv->pool);
-  cudaGetLastError();
-  delete srv;
-  return SNC_OK;
+    srv->cv_work.notify_all();
+    for (std::thread& t : srv->workers) t.join();
+    cudaSetDevice(srv->cfg.device);
+    for (auto& kv : srv->jobs) {
+      Job& j = *kv.second;
+      if (j.ctx) {
+        snc::rebind_build(j.ctx, srv->release_stream, nullptr);
+        snc_destroy(j.ctx);
+      }
+    }
+    srv->jobs.clear();
+    cudaStreamSynchronize(srv->release_stream);
+    for (cudaStream_t s : srv->streams) cudaStreamDestroy(s);
+    cudaStreamDestroy(srv->release_stream);
+    cudaMemPoolDestroy(srv->pool);
+    cudaGetLastError();
+    delete srv;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_server_submit(snc_server* srv, snc_ctx* ctx, uint64_t* ticket) {
-  if (!srv || !ctx || !ticket) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_submit: null argument");
-  if (snc::ctx_finalized(ctx)) return server_fail(SNC_ERR_STATE, "snc_server_submit: context already finalized");
-  if (snc::ctx_device(ctx) != srv->cfg.device)
-    return server_fail(SNC_ERR_INVALID_ARG, "snc_server_submit: context on another device");
-  auto job = std::make_unique<Job>();
-  if (snc::estimate_build(ctx, &job->est) != SNC_OK)
-    return server_fail(SNC_ERR_INVALID_ARG, "snc_server_submit: estimate failed");
-  if (job->est.peak_bytes > srv->cfg.hbm_budget_bytes)
-    return server_fail(SNC_ERR_INVALID_ARG, "snc_server_submit: the request alone exceeds the memory budget");
-  job->ctx = ctx;
-  job->t_submit = Clock::now();
-  {
-    std::lock_guard<std::mutex> lk(srv->mu);
-    if (srv->stop) return server_fail(SNC_ERR_STATE, "snc_server_submit: server is shutting down");
-    job->ticket = srv->next_ticket++;
-    *ticket = job->ticket;
-    srv->queue.push_back(job.get());
-    srv->jobs.emplace(job->ticket, std::move(job));
-    ++srv->st.submitted;
-    ++srv->st.queued;
-  }
-  srv->cv_work.notify_one();
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!srv || !ctx || !ticket) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_submit: null argument");
+    if (snc::ctx_finalized(ctx)) return server_fail(SNC_ERR_STATE, "snc_server_submit: context already finalized");
+    if (snc::ctx_device(ctx) != srv->cfg.device)
+      return server_fail(SNC_ERR_INVALID_ARG, "snc_server_submit: context on another device");
+    auto job = std::make_unique<Job>();
+    if (snc::estimate_build(ctx, &job->est) != SNC_OK)
+      return server_fail(SNC_ERR_INVALID_ARG, "snc_server_submit: estimate failed");
+    if (job->est.peak_bytes > srv->cfg.hbm_budget_bytes)
+      return server_fail(SNC_ERR_INVALID_ARG, "snc_server_submit: the request alone exceeds the memory budget");
+    job->ctx = ctx;
+    job->t_submit = Clock::now();
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      if (srv->stop) return server_fail(SNC_ERR_STATE, "snc_server_submit: server is shutting down");
+      job->ticket = srv->next_ticket++;
+      *ticket = job->ticket;
+      srv->queue.push_back(job.get());
+      srv->jobs.emplace(job->ticket, std::move(job));
+      ++srv->st.submitted;
+      ++srv->st.queued;
+    }
+    srv->cv_work.notify_one();
+    return SNC_OK;
+  });
 }
 
 snc_status snc_server_poll(snc_server* srv, uint64_t ticket, snc_job_state* state, snc_conn_view* view) {
-  if (!srv || !state) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_poll: null argument");
-  snc_ctx* ctx = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(srv->mu);
-    auto it = srv->jobs.find(ticket);
-    if (it == srv->jobs.end()) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_poll: unknown ticket");
-    Job& j = *it->second;
-    *state = j.state;
-    if (j.state == SNC_JOB_FAILED) return server_fail(j.status, j.error.c_str());
-    if (j.state != SNC_JOB_DONE || !view) return SNC_OK;
-    ctx = j.ctx;
-  }
-  return snc_get_connections(ctx, view);
+  return snc::abi_guard([&]() -> snc_status {
+    if (!srv || !state) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_poll: null argument");
+    snc_ctx* ctx = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      auto it = srv->jobs.find(ticket);
+      if (it == srv->jobs.end()) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_poll: unknown ticket");
+      Job& j = *it->second;
+      *state = j.state;
+      if (j.state == SNC_JOB_FAILED) return server_fail(j.status, j.error.c_str());
+      if (j.state != SNC_JOB_DONE || !view) return SNC_OK;
+      ctx = j.ctx;
+    }
+    return snc_get_connections(ctx, view);
+  });
 }
 
 snc_status snc_server_wait_any(snc_server* srv, int timeout_ms, uint64_t* ticket) {
-  if (!srv || !ticket) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_wait_any: null argument");
-  std::unique_lock<std::mutex> lk(srv->mu);
-  auto ready = [&] { return !srv->finished.empty(); };
-  if (timeout_ms < 0)
-    srv->cv_done.wait(lk, ready);
-  else
-    srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
-  if (srv->finished.empty()) {
-    *ticket = 0;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!srv || !ticket) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_wait_any: null argument");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto ready = [&] { return !srv->finished.empty(); };
+    if (timeout_ms < 0)
+      srv->cv_done.wait(lk, ready);
+    else
+      srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    if (srv->finished.empty()) {
+      *ticket = 0;
+      return SNC_OK;
+    }
+    *ticket = srv->finished.front();
+    srv->finished.pop_front();
     return SNC_OK;
-  }
-  *ticket = srv->finished.front();
-  srv->finished.pop_front();
-  return SNC_OK;
+  });
 }
 
 snc_status snc_server_context(snc_server* srv, uint64_t ticket, snc_ctx** ctx) {
-  if (!srv || !ctx) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_context: null argument");
-  std::lock_guard<std::mutex> lk(srv->mu);
-  auto it = srv->jobs.find(ticket);
-  if (it == srv->jobs.end()) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_context: unknown ticket");
-  *ctx = it->second->ctx;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!srv || !ctx) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_context: null argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(ticket);
+    if (it == srv->jobs.end()) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_context: unknown ticket");
+    *ctx = it->second->ctx;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_server_times(snc_server* srv, uint64_t ticket, snc_job_times* out) {
-  if (!srv || !out) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_times: null argument");
-  std::lock_guard<std::mutex> lk(srv->mu);
-  auto it = srv->jobs.find(ticket);
-  if (it == srv->jobs.end()) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_times: unknown ticket");
-  const Job& j = *it->second;
-  if (j.state != SNC_JOB_DONE && j.state != SNC_JOB_FAILED)
-    return server_fail(SNC_ERR_STATE, "snc_server_times: request not finished");
-  std::memset(out, 0, sizeof *out);
-  out->queued_ms = ms_between(j.t_submit, j.t_start);
-  out->build_ms = ms_between(j.t_start, j.t_done);
-  out->latency_ms = ms_between(j.t_submit, j.t_done);
-  out->batch_size = j.batch_size;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!srv || !out) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_times: null argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(ticket);
+    if (it == srv->jobs.end()) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_times: unknown ticket");
+    const Job& j = *it->second;
+    if (j.state != SNC_JOB_DONE && j.state != SNC_JOB_FAILED)
+      return server_fail(SNC_ERR_STATE, "snc_server_times: request not finished");
+    std::memset(out, 0, sizeof *out);
+    out->queued_ms = ms_between(j.t_submit, j.t_start);
+    out->build_ms = ms_between(j.t_start, j.t_done);
+    out->latency_ms = ms_between(j.t_submit, j.t_done);
+    out->batch_size = j.batch_size;
+    return SNC_OK;
+  });
 }
 
 snc_status snc_server_release(snc_server* srv, uint64_t ticket) {
-  if (!srv) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_release: null server");
-  std::unique_ptr<Job> job;
-  {
-    std::lock_guard<std::mutex> lk(srv->mu);
-    auto it = srv->jobs.find(ticket);
-    if (it == srv->jobs.end()) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_release: unknown ticket");
-    if (it->second->state != SNC_JOB_DONE && it->second->state != SNC_JOB_FAILED)
-      return server_fail(SNC_ERR_STATE, "snc_server_release: request still queued or running");
-    job = std::move(it->second);
-    srv->jobs.erase(it);
-  }
-  // The build's stream may be running another build by now: free on the
-  // server's release stream (the build itself has finished).
-  bool last = false;
-  {
-    std::lock_guard<std::mutex> rl(srv->release_mu);
-    cudaSetDevice(srv->cfg.device);
-    last = --job->group->live == 0;
-    // Only the last network of a build frees memory; the others leave the
-    // shared storage (and its stream) untouched for their siblings.
-    if (last) snc::rebind_build(job->ctx, srv->release_stream, nullptr);
-    snc_destroy(job->ctx);
-    job->ctx = nullptr;
-  }
-  {
-    std::lock_guard<std::mutex> lk(srv->mu);
-    ++srv->st.released;
-    if (last) {
-      srv->st.reserved_bytes -= job->group->resident_bytes;
-      srv->st.resident_bytes -= job->group->resident_bytes;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!srv) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_release: null server");
+    std::unique_ptr<Job> job;
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      auto it = srv->jobs.find(ticket);
+      if (it == srv->jobs.end()) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_release: unknown ticket");
+      if (it->second->state != SNC_JOB_DONE && it->second->state != SNC_JOB_FAILED)
+        return server_fail(SNC_ERR_STATE, "snc_server_release: request still queued or running");
+      job = std::move(it->second);
+      srv->jobs.erase(it);
     }
-  }
-  if (last) srv->cv_work.notify_all();
-  return SNC_OK;
+    // The build's stream may be running another build by now: free on the
+    // server's release stream (the build itself has finished).
+    bool last = false;
+    {
+      std::lock_guard<std::mutex> rl(srv->release_mu);
+      cudaSetDevice(srv->cfg.device);
+      last = --job->group->live == 0;
+      // Only the last network of a build frees memory; the others leave the
+      // shared storage (and its stream) untouched for their siblings.
+      if (last) snc::rebind_build(job->ctx, srv->release_stream, nullptr);
+      snc_destroy(job->ctx);
+      job->ctx = nullptr;
+    }
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      ++srv->st.released;
+      if (last) {
+        srv->st.reserved_bytes -= job->group->resident_bytes;
+        srv->st.resident_bytes -= job->group->resident_bytes;
+      }
+    }
+    if (last) srv->cv_work.notify_all();
+    return SNC_OK;
+  });
 }
 
 snc_status snc_server_get_stats(snc_server* srv, snc_server_stats* out) {
-  if (!srv || !out) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_get_stats: null argument");
-  std::lock_guard<std::mutex> lk(srv->mu);
-  *out = srv->st;
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    if (!srv || !out) return server_fail(SNC_ERR_INVALID_ARG, "snc_server_get_stats: null argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = srv->st;
+    return SNC_OK;
+  });
 }
 
 }  // extern "C"

@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "../../include/snc.h"
+#include "snc_internal.h"
 #include "sort_kernels.h"
 
 namespace snc {
@@ -80,35 +81,37 @@ cudaError_t scratch_address(int dev, unsigned char** out) {
 extern "C" snc_status snc_radix_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in,
                                                    uint64_t* keys_out, uint32_t* vals_out, uint64_t n,
                                                    int key_bits, void* stream) {
-  using namespace snc;
-  if (key_bits < 1 || key_bits > 64) return fail(SNC_ERR_INVALID_ARG, "key_bits outside [1, 64]");
-  if (n > kNoAllocMaxPairs) {
-    char msg[160];
-    snprintf(msg, sizeof msg, "n = %llu exceeds the %llu pairs the no-allocation sort holds",
-             static_cast<unsigned long long>(n), static_cast<unsigned long long>(kNoAllocMaxPairs));
-    return fail(SNC_ERR_INVALID_ARG, msg);
-  }
-  if (n == 0) return SNC_OK;
-  if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(SNC_ERR_INVALID_ARG, "null buffer");
-  const SortPasses sp = plan_passes(key_bits);
-  if (kSortOffset + sort_scratch_bytes(n, sp) > kNoAllocScratchBytes)
-    return fail(SNC_ERR_UNSUPPORTED, "sort scratch does not fit the static array");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(SNC_ERR_CUDA, "no usable current device");
-  unsigned char* base = nullptr;
-  e = scratch_address(dev, &base);
-  if (e != cudaSuccess) return fail(SNC_ERR_CUDA, cudaGetErrorString(e));
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  uint64_t* keys_tmp = reinterpret_cast<uint64_t*>(base);
-  uint32_t* vals_tmp = reinterpret_cast<uint32_t*>(base + kTmpKeysBytes);
-  uint32_t* err = reinterpret_cast<uint32_t*>(base + kErrOffset);
-  // The error word keeps the previous call's contents: clear it first (the
-  // sort clears its own look-back words, histograms and counters).
-  e = cudaMemsetAsync(err, 0, 256, st);
-  if (e == cudaSuccess)
-    e = radix_sort_run(keys_in, vals_in, keys_out, vals_out, keys_tmp, vals_tmp, n, sp, base + kSortOffset, err, st,
-                       nullptr);
-  if (e != cudaSuccess) return fail(SNC_ERR_CUDA, cudaGetErrorString(e));
-  return SNC_OK;
+  return snc::abi_guard([&]() -> snc_status {
+    using namespace snc;
+    if (key_bits < 1 || key_bits > 64) return fail(SNC_ERR_INVALID_ARG, "key_bits outside [1, 64]");
+    if (n > kNoAllocMaxPairs) {
+      char msg[160];
+      snprintf(msg, sizeof msg, "n = %llu exceeds the %llu pairs the no-allocation sort holds",
+               static_cast<unsigned long long>(n), static_cast<unsigned long long>(kNoAllocMaxPairs));
+      return fail(SNC_ERR_INVALID_ARG, msg);
+    }
+    if (n == 0) return SNC_OK;
+    if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(SNC_ERR_INVALID_ARG, "null buffer");
+    const SortPasses sp = plan_passes(key_bits);
+    if (kSortOffset + sort_scratch_bytes(n, sp) > kNoAllocScratchBytes)
+      return fail(SNC_ERR_UNSUPPORTED, "sort scratch does not fit the static array");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(SNC_ERR_CUDA, "no usable current device");
+    unsigned char* base = nullptr;
+    e = scratch_address(dev, &base);
+    if (e != cudaSuccess) return fail(SNC_ERR_CUDA, cudaGetErrorString(e));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint64_t* keys_tmp = reinterpret_cast<uint64_t*>(base);
+    uint32_t* vals_tmp = reinterpret_cast<uint32_t*>(base + kTmpKeysBytes);
+    uint32_t* err = reinterpret_cast<uint32_t*>(base + kErrOffset);
+    // The error word keeps the previous call's contents: clear it first (the
+    // sort clears its own look-back words, histograms and counters).
+    e = cudaMemsetAsync(err, 0, 256, st);
+    if (e == cudaSuccess)
+      e = radix_sort_run(keys_in, vals_in, keys_out, vals_out, keys_tmp, vals_tmp, n, sp, base + kSortOffset, err, st,
+                         nullptr);
+    if (e != cudaSuccess) return fail(SNC_ERR_CUDA, cudaGetErrorString(e));
+    return SNC_OK;
+  });
 }
