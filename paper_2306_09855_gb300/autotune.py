@@ -34,6 +34,19 @@ def _size_class(n_connections: int) -> str:
     return "large"
 
 
+def _connections(specs) -> int:
+    """Expected number of connections of the specifications (Sec. 2.1 counts;
+    pairwise_bernoulli its mean), for the size class of the cache key."""
+    n = 0.0
+    for sp in specs:
+        for pj in sp.projections:
+            ns, nt = int(pj.src[1]), int(pj.tgt[1])
+            n += {"one_to_one": ns, "all_to_all": ns * nt, "fixed_indegree": int(pj.k) * nt,
+                  "fixed_outdegree": int(pj.k) * ns, "fixed_total_number": int(pj.k),
+                  "pairwise_bernoulli": float(pj.p) * ns * nt}[pj.rule]
+    return int(n)
+
+
 def _key_class(specs) -> str:
     nodes = sum(sp.n_nodes for sp in specs)
     return "src%d" % max(1, int(nodes - 1).bit_length())
@@ -74,11 +87,8 @@ def time_build(specs: Sequence, batched: bool, repeats: int = 2) -> float:
 def tune(specs: Sequence, batched: bool = True, candidates=CANDIDATES, cache_path: str = DEFAULT_CACHE,
          use_cache: bool = True) -> Dict:
     """Pick and apply the fastest candidate for this workload class."""
-    n_est = 0
-    for sp in specs:
-        for pj in sp.projections:
-            n_est += int(pj.k) * int(pj.tgt[1]) if pj.rule == "fixed_indegree" else int(pj.k)
-    key = "v4/%s/%s/%s/%s" % (_gpu_name(), _key_class(specs), _size_class(n_est), "batch" if batched else "single")
+    key = "v4/%s/%s/%s/%s" % (_gpu_name(), _key_class(specs), _size_class(_connections(specs)),
+                              "batch" if batched else "single")
     cache = {}
     if use_cache and os.path.exists(cache_path):
         try:
