@@ -23,6 +23,7 @@
 #include "sort_kernels.h"
 #include "source_major.h"
 #include "deliver.h"
+#include "arrays.h"
 
 using namespace snc;
 
@@ -331,12 +332,6 @@ int bit_width(uint64_t v) {
   return b;
 }
 
-uint64_t overlap(const snc_range& a, const snc_range& b) {
-  const uint64_t lo = std::max<uint64_t>(a.first, b.first);
-  const uint64_t hi = std::min<uint64_t>(static_cast<uint64_t>(a.first) + a.n, static_cast<uint64_t>(b.first) + b.n);
-  return hi > lo ? hi - lo : 0;
-}
-
 bool is_sampler(const Projection& p) {
   return p.rule.kind == SNC_PAIRWISE_BERNOULLI ||
          ((p.rule.kind == SNC_FIXED_INDEGREE || p.rule.kind == SNC_FIXED_OUTDEGREE) && !p.rule.allow_multapses);
@@ -347,60 +342,17 @@ bool is_total_redraw(const Projection& p) {
 }
 
 // Validation and sizing of one Connect call (readings of Sec. 2.1 / Sec. 4).
+// The node lists, the rule's limits and the count are checked as for a call
+// with explicit arrays (arrays.cpp), here with both lists given as ranges.
 snc_status plan_projection(snc_ctx* c, Projection& p) {
   const snc_conn_rule& r = p.rule;
-  if (static_cast<uint64_t>(p.src.first) + p.src.n > c->n_nodes ||
-      static_cast<uint64_t>(p.tgt.first) + p.tgt.n > c->n_nodes)
-    return fail(c, SNC_ERR_INVALID_ARG, "connect: node range outside the created populations");
-  const uint64_t ov = overlap(p.src, p.tgt);
-  const bool aut = r.allow_autapses != 0;
-  switch (r.kind) {
-    case SNC_ONE_TO_ONE:
-      if (p.src.n != p.tgt.n) return fail(c, SNC_ERR_INVALID_ARG, "one_to_one: source and target sizes differ");
-      p.exact_count = true;
-      p.count = (!aut && p.src.first == p.tgt.first) ? 0 : p.src.n;
-      break;
-    case SNC_ALL_TO_ALL:
-      p.exact_count = true;
-      p.count = static_cast<uint64_t>(p.src.n) * p.tgt.n - (aut ? 0 : ov);
-      break;
-    case SNC_FIXED_INDEGREE:
-    case SNC_FIXED_OUTDEGREE: {
-      const bool indeg = r.kind == SNC_FIXED_INDEGREE;
-      const uint64_t n_other = indeg ? p.src.n : p.tgt.n;
-      const uint64_t n_primary = indeg ? p.tgt.n : p.src.n;
-      if (r.k > 0xFFFFFFFFull) return fail(c, SNC_ERR_INVALID_ARG, "degree K above 2^32 - 1");
-      if (r.k > 0 && n_primary > 0) {
-        const uint64_t least = (!aut && ov > 0) ? n_other - 1 : n_other;
-        if (least == 0) return fail(c, SNC_ERR_INVALID_ARG, "degree rule: no candidate nodes");
-        if (!r.allow_multapses && r.k > least)
-          return fail(c, SNC_ERR_INVALID_ARG, "degree K=%llu above the %llu candidates without multapses",
-                      static_cast<unsigned long long>(r.k), static_cast<unsigned long long>(least));
-      }
-      p.exact_count = true;
-      p.count = n_primary * r.k;
-      break;
-    }
-    case SNC_FIXED_TOTAL_NUMBER: {
-      if (r.k > 0) {
-        const uint64_t pairs = static_cast<uint64_t>(p.src.n) * p.tgt.n;
-        const uint64_t allowed = pairs - (aut ? 0 : ov);
-        if (allowed == 0) return fail(c, SNC_ERR_INVALID_ARG, "fixed_total_number: no allowed pair");
-        if (!r.allow_multapses && r.k > allowed)
-          return fail(c, SNC_ERR_INVALID_ARG, "fixed_total_number: N above the allowed pairs without multapses");
-      }
-      p.exact_count = true;
-      p.count = r.k;
-      break;
-    }
-    case SNC_PAIRWISE_BERNOULLI:
-      if (!(r.p >= 0.0 && r.p <= 1.0)) return fail(c, SNC_ERR_INVALID_ARG, "pairwise_bernoulli: p outside [0, 1]");
-      p.exact_count = false;
-      p.count = 0;
-      break;
-    default:
-      return fail(c, SNC_ERR_INVALID_ARG, "unknown rule %d", r.kind);
-  }
+  ArrayPlan lists;
+  std::string why;
+  const snc_status cs = check_connect_arrays(static_cast<uint32_t>(c->n_nodes), c->cfg.dt_ms, p.src, p.tgt, r,
+                                             ConnectArrays{}, &lists, &why);
+  if (cs != SNC_OK) return fail(c, cs, "connect: %s", why.c_str());
+  p.exact_count = r.kind != SNC_PAIRWISE_BERNOULLI;  // Bernoulli counts are drawn at finalize
+  p.count = lists.count;
   const snc_dist& wd = p.syn.weight;
   const snc_dist& dd = p.syn.delay_ms;
   if ((wd.kind != SNC_DIST_CONST && wd.kind != SNC_DIST_NORMAL) ||
@@ -411,11 +363,11 @@ snc_status plan_projection(snc_ctx* c, Projection& p) {
   if (!std::isfinite(wd.mean) || !std::isfinite(dd.mean)) return fail(c, SNC_ERR_INVALID_ARG, "non-finite mean");
   // Delay: constant step or threshold table (Sec. 2.1: round(d / dt), >= 1).
   if (dd.kind == SNC_DIST_CONST || dd.std == 0.0) {
-    double q = std::floor(dd.mean / c->cfg.dt_ms + 0.5);
-    if (q < 1.0) q = 1.0;
-    if (q > 65535.0) return fail(c, SNC_ERR_UNSUPPORTED, "delay above 65535 steps");
+    uint32_t step = 1;
+    if (delay_step_of(dd.mean, c->cfg.dt_ms, &step) != SNC_OK)
+      return fail(c, SNC_ERR_UNSUPPORTED, "delay above 65535 steps");
     p.d_table = false;
-    p.d_const = static_cast<uint32_t>(q);
+    p.d_const = step;
     p.max_step = p.d_const;
   } else {
     const int st = delay_thresholds(dd.mean, dd.std, c->cfg.dt_ms, p.d_thr, p.d_base);
