@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <exception>
 #include <string>
@@ -105,6 +106,31 @@ uint64_t storage_live_bytes(const snc_ctx* c);  // device bytes the context's st
 int ctx_device(const snc_ctx* c);
 bool ctx_finalized(const snc_ctx* c);
 bool ctx_sharded(const snc_ctx* c);  // a target shard (built alone, never in a batch)
+
+// Admission of the served form (snc_server.cpp): one queued request as the
+// admission sees it, and the limits it admits under.
+struct AdmitRequest {
+  uint64_t peak_bytes;  // estimated device memory at the build's peak
+  uint64_t n_syn;       // connections
+  uint64_t n_nodes;     // nodes of its network
+  uint32_t max_step;    // largest delay step
+  bool alone;           // built alone (a target shard)
+};
+struct AdmitLimits {
+  uint64_t budget_bytes;    // the server's device-memory budget
+  uint64_t reserved_bytes;  // reserved by running builds and resident results
+  uint64_t batch_max_syn;   // connections of one batched build at most
+  int batch_max_nets;       // networks of one batched build at most
+};
+// How many requests from the front of q[0..n) start as the next build, and
+// the memory they reserve (*reserve): none while the front one does not fit
+// the budget; else the front one, followed, when it is small (at most half
+// of batch_max_syn connections) and not built alone, by the longest run of
+// following small requests, none built alone, that keeps the batch within
+// batch_max_nets networks, batch_max_syn connections, the budget and a
+// batched key (global source | delay step | member-local target) of at most
+// 64 bits over fewer than 2^32 nodes.
+size_t admit_from_front(const AdmitRequest* q, size_t n, const AdmitLimits& lim, uint64_t* reserve);
 
 // Entry points run their body through abi_guard: a C++ exception (host
 // memory or threads exhausted inside the standard library) becomes

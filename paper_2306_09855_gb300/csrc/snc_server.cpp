@@ -71,6 +71,38 @@ void pool_free(void* p, size_t, void* stream, void*) { cudaFreeAsync(p, static_c
 
 }  // namespace
 
+namespace snc {
+
+size_t admit_from_front(const AdmitRequest* q, size_t n, const AdmitLimits& lim, uint64_t* reserve) {
+  *reserve = 0;
+  if (n == 0 || lim.reserved_bytes + q[0].peak_bytes > lim.budget_bytes) return 0;
+  uint64_t res = q[0].peak_bytes, syn = q[0].n_syn;
+  uint64_t nodes = q[0].n_nodes, max_nodes = q[0].n_nodes;
+  uint32_t max_step = q[0].max_step;
+  size_t take = 1;
+  const uint64_t small = lim.batch_max_syn / 2;
+  if (lim.batch_max_nets > 1 && q[0].n_syn <= small && !q[0].alone) {
+    while (take < n && static_cast<int>(take) < lim.batch_max_nets) {
+      const AdmitRequest& j = q[take];
+      if (j.n_syn > small || syn + j.n_syn > lim.batch_max_syn || j.alone) break;
+      if (lim.reserved_bytes + res + j.peak_bytes > lim.budget_bytes) break;
+      const uint64_t n2 = nodes + j.n_nodes, m2 = std::max(max_nodes, j.n_nodes);
+      const uint32_t d2 = std::max(max_step, j.max_step);
+      if (n2 > 0xFFFFFFFFull || bits_of(n2 - 1) + bits_of(m2 - 1) + bits_of(d2) > 64) break;
+      ++take;
+      res += j.peak_bytes;
+      syn += j.n_syn;
+      nodes = n2;
+      max_nodes = m2;
+      max_step = d2;
+    }
+  }
+  *reserve = res;
+  return take;
+}
+
+}  // namespace snc
+
 struct snc_server {
   snc_server_config cfg{};
   cudaMemPool_t pool = nullptr;
@@ -94,33 +126,22 @@ struct snc_server {
   std::vector<Job*> take_build() {
     std::vector<Job*> out;
     if (queue.empty()) return out;
-    Job* head = queue.front();
-    if (st.reserved_bytes + head->est.peak_bytes > cfg.hbm_budget_bytes) return out;
-    out.push_back(head);
-    queue.pop_front();
-    uint64_t reserve = head->est.peak_bytes, syn = head->est.n_syn;
-    uint64_t nodes = head->est.n_nodes, max_nodes = head->est.n_nodes;
-    uint32_t max_step = head->est.max_step;
-    const uint64_t small = cfg.batch_max_syn / 2;
-    // (Target shards are built alone.)
-    if (cfg.batch_max_nets > 1 && head->est.n_syn <= small && !snc::ctx_sharded(head->ctx)) {
-      while (!queue.empty() && static_cast<int>(out.size()) < cfg.batch_max_nets) {
-        Job* j = queue.front();
-        if (j->est.n_syn > small || syn + j->est.n_syn > cfg.batch_max_syn || snc::ctx_sharded(j->ctx)) break;
-        if (st.reserved_bytes + reserve + j->est.peak_bytes > cfg.hbm_budget_bytes) break;
-        // The batched key: global source | delay step | member-local target.
-        const uint64_t n2 = nodes + j->est.n_nodes, m2 = std::max(max_nodes, j->est.n_nodes);
-        const uint32_t d2 = std::max(max_step, j->est.max_step);
-        if (n2 > 0xFFFFFFFFull || bits_of(n2 - 1) + bits_of(m2 - 1) + bits_of(d2) > 64) break;
-        out.push_back(j);
-        queue.pop_front();
-        reserve += j->est.peak_bytes;
-        syn += j->est.n_syn;
-        nodes = n2;
-        max_nodes = m2;
-        max_step = d2;
-      }
+    // The admission looks at the first batch_max_nets requests at most.
+    std::vector<snc::AdmitRequest> front;
+    const size_t look = std::min<size_t>(queue.size(), static_cast<size_t>(std::max(1, cfg.batch_max_nets)));
+    for (size_t i = 0; i < look; ++i) {
+      const Job* j = queue[i];
+      // (Target shards are built alone.)
+      front.push_back({j->est.peak_bytes, j->est.n_syn, j->est.n_nodes, j->est.max_step, snc::ctx_sharded(j->ctx)});
     }
+    uint64_t reserve = 0;
+    const snc::AdmitLimits lim{cfg.hbm_budget_bytes, st.reserved_bytes, cfg.batch_max_syn, cfg.batch_max_nets};
+    const size_t take = snc::admit_from_front(front.data(), front.size(), lim, &reserve);
+    for (size_t i = 0; i < take; ++i) {
+      out.push_back(queue.front());
+      queue.pop_front();
+    }
+    if (out.empty()) return out;
     const Clock::time_point now = Clock::now();
     for (Job* j : out) {
       j->state = SNC_JOB_RUNNING;
