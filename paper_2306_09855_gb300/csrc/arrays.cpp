@@ -87,8 +87,11 @@ snc_status check_connect_arrays(uint32_t n_nodes, double dt_ms, const snc_range&
     case SNC_ONE_TO_ONE: {
       if (src.n != tgt.n) return refuse(SNC_ERR_INVALID_ARG, why, "one_to_one: source and target sizes differ");
       plan->numbered = src.n;
-      uint64_t same = 0;
-      for (uint32_t i = 0; i < src.n; ++i) same += node_at(a.src_ids, src, i) == node_at(a.tgt_ids, tgt, i);
+      uint64_t same = 0;  // pairs i with equal nodes: for two ranges all or none
+      if (!a.src_ids && !a.tgt_ids)
+        same = src.first == tgt.first ? src.n : 0;
+      else
+        for (uint32_t i = 0; i < src.n; ++i) same += node_at(a.src_ids, src, i) == node_at(a.tgt_ids, tgt, i);
       plan->count = src.n - (aut ? 0 : same);
       break;
     }
