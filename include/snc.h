@@ -111,8 +111,12 @@ typedef struct {
   const snc_allocator* allocator; /* NULL: cudaMallocAsync / cudaFreeAsync    */
 } snc_config;
 
-/* Device views of a finalized network, sorted by (source, delay, target).
- * Arrays live on the context's device and stay valid until snc_destroy.
+/* Device views of a finalized network, sorted stably by (source, delay
+ * step) (Sec. 2.2 sorts by these two keys): connections with equal source and
+ * delay keep their generation order (the order of the Connect calls, then
+ * the rule's connection numbering of Sec. 2.1), so targets are NOT ascending
+ * within a group.  Arrays live on the context's device and stay valid until
+ * snc_destroy.
  *   row_ptr[n_nodes + 1]: connections of source i are [row_ptr[i], row_ptr[i+1])
  *   target, delay (time steps >= 1), weight: [n_syn]
  *   group_ptr[n_nodes + 1]: p_i of Sec. 2.2 (groups of source i are
@@ -156,7 +160,8 @@ snc_status snc_connect(snc_ctx* ctx, snc_range src, snc_range tgt, const snc_con
                        const snc_syn_spec* syn, uint32_t* proj_id);
 
 /* Calibration (Sec. 2.2, 2.6): generates every connection on the device,
- * sorts them by (source, delay, target) and builds the CSR and group index.
+ * sorts them stably by (source, delay step) and builds the CSR and group
+ * index.
  * Work is queued on the context's stream; the call blocks only for the
  * small device->host reads that size variable-count rules.  After it,
  * snc_connect returns STATE.  UNSUPPORTED: packed key wider than 64 bits or
@@ -279,7 +284,7 @@ typedef struct {
   uint64_t h2d_bytes;       /* host -> device bytes copied                    */
   uint64_t d2h_bytes;       /* device -> host bytes copied                    */
   int32_t n_passes;         /* radix passes of the sort (0: source-major sort) */
-  int32_t key_bits;         /* width of the packed (source, delay, target) key */
+  int32_t key_bits;         /* width of the packed (source, delay step) sort key */
   uint64_t device_bytes_peak; /* largest total of live device buffers          */
   int32_t source_major;     /* 1: every projection generates source by source
                              * (one_to_one, all_to_all, fixed_outdegree), so
@@ -297,9 +302,12 @@ snc_status snc_get_stats(const snc_ctx* ctx, snc_stats* out);
  * keys_in / vals_in: device input (unchanged); keys_out / vals_out: device
  * output; the four buffers must not overlap.  stream: cudaStream_t (NULL =
  * default stream).  Scratch is allocated with cudaMallocAsync on `stream`
- * and released before return of the queued work.  The call is asynchronous;
- * errors from the device are reported by a later synchronizing call.
- * INVALID_ARG: null pointers with n > 0, key_bits outside [1, 64]. */
+ * and released in stream order.  The call waits for the sort on `stream`
+ * and reads its device error word, so a failure on the device is reported
+ * here: TIMEOUT when a bounded look-back wait expired (the output is then not
+ * sorted), CUDA for a launch or copy failure or another device error bit.
+ * INVALID_ARG: null pointers with n > 0, key_bits outside [1, 64].
+ * OOM: the scratch allocation failed. */
 snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                                 uint32_t* vals_out, uint64_t n, int key_bits, void* stream);
 
@@ -317,14 +325,36 @@ snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in
  * passes the input and output buffers.
  * Limits and rules:
  *   - n <= SNC_NOALLOC_MAX_PAIRS, else INVALID_ARG (nothing is queued);
+ *   - it sorts with a fixed digit plan (digits of at most 9 bits), whatever
+ *     snc_set_tuning chose for the other sorts, so that its scratch fits the
+ *     array for every accepted n and key width; UNSUPPORTED (scratch does
+ *     not fit) is kept as a guard and cannot occur with that plan;
  *   - the first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture;
+ *     that device current; make that first call before any stream capture.
+ *     The address is cached per device ordinal for the process: calls after
+ *     cudaDeviceReset (which reloads the module) are not supported;
  *   - every call shares the one array: calls whose work can overlap on the
  *     GPU (other streams, other host threads) race and must be serialised
  *     by the caller.  Each call clears what it needs before use.
- * The call is asynchronous on `stream`; CUDA failures return CUDA. */
+ * The call waits for the sort on `stream` and reads the array's error word:
+ * TIMEOUT when a bounded look-back wait expired (the output is then not
+ * sorted), CUDA for a launch or copy failure or another device error bit. */
 snc_status snc_radix_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                                         uint32_t* vals_out, uint64_t n, int key_bits, void* stream);
+
+/* Test support for the bounded device waits (no counterpart in the paper).
+ * Every wait of the sort's decoupled look-back is bounded; this call lets a
+ * test make such a wait expire without faulting or holding the GPU, to check
+ * that the expiry is reported as TIMEOUT and that later calls work.
+ * lookback_spin_limit: polling rounds of each look-back wait before it gives
+ * up (0 = the built-in bound, about 4e6 rounds with back-off);
+ * withhold_tile: the tile (of each sort pass) that never publishes its
+ * look-back words, so that every later tile's wait runs to its bound
+ * (0xFFFFFFFF = none, the default).  Process-wide, for sorts queued after the
+ * call (snc_finalize, the batched forms and the stand-alone sorts).  A
+ * timed-out tile still writes only inside its output arrays.  Reset with
+ * snc_set_wait_test(0, 0xFFFFFFFF). */
+snc_status snc_set_wait_test(uint32_t lookback_spin_limit, uint32_t withhold_tile);
 
 /* Readable description of the last failure on ctx (or of the last
  * context-free failure when ctx is NULL).  Never NULL. */

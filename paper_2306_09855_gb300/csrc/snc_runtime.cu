@@ -1764,8 +1764,23 @@ snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in
     }
     cudaError_t e = cudaMemsetAsync(err, 0, 256, st);
     if (e == cudaSuccess) e = radix_sort_run(keys_in, vals_in, keys_out, vals_out, ktmp, vtmp, n, sp, scratch, err, st, nullptr);
+    // The device error word tells whether a bounded wait expired (the output
+    // is then not sorted): read it once the queued work is done.
+    uint32_t bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, err, sizeof bits, cudaMemcpyDeviceToHost, st);
     release();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(nullptr, SNC_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e));
+    if (bits & kErrLookbackTimeout) return fail(nullptr, SNC_ERR_TIMEOUT, "radix sort: a look-back wait expired on the device");
+    if (bits) return fail(nullptr, SNC_ERR_CUDA, "radix sort: device error bits 0x%x", bits);
+    return SNC_OK;
+  });
+}
+
+snc_status snc_set_wait_test(uint32_t lookback_spin_limit, uint32_t withhold_tile) {
+  return snc::abi_guard([&]() -> snc_status {
+    g_wait_test.lookback_spin_limit = lookback_spin_limit ? lookback_spin_limit : kDefaultSpinLimit;
+    g_wait_test.withhold_unit = withhold_tile;
     return SNC_OK;
   });
 }

@@ -30,7 +30,7 @@ namespace {
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagInc = 2ull << 62;
 constexpr uint64_t kCountMask = (1ull << 48) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kSpinLimit = kDefaultSpinLimit;  // bulk-copy waits
 
 __device__ __forceinline__ void st_status(uint64_t* p, uint64_t v) {
   *reinterpret_cast<volatile unsigned long long*>(p) = v;
@@ -249,7 +249,7 @@ __device__ __forceinline__ void look_back(const A& a, uint32_t unit, uint64_t (&
       }
     }
     if (pending && !progress) {
-      if (++spins > kSpinLimit) {
+      if (++spins > a.lookback_spin_limit) {
         atomicOr(a.err, kErrLookbackTimeout);
         break;
       }
@@ -322,13 +322,14 @@ __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
 #pragma unroll
       for (int q = 0; q < DPT; ++q) {
         cnt[q] = ghist[tid * DPT + q];
-        st_status(st_row + q, (unit == 0 ? kFlagInc : kFlagAgg) | ep | cnt[q]);
+        if (unit != a.withhold_unit) st_status(st_row + q, (unit == 0 ? kFlagInc : kFlagAgg) | ep | cnt[q]);
       }
       uint64_t prefix[DPT];
       look_back<RADIX, DPT, W>(a, unit, prefix);
 #pragma unroll
       for (int q = 0; q < DPT; ++q) {
-        if (unit > 0) st_status(st_row + q, kFlagInc | ep | ((prefix[q] + cnt[q]) & kCountMask));
+        if (unit > 0 && unit != a.withhold_unit)
+          st_status(st_row + q, kFlagInc | ep | ((prefix[q] + cnt[q]) & kCountMask));
         run[tid * DPT + q] = a.digit_start[tid * DPT + q] + prefix[q];
       }
     }
@@ -380,7 +381,8 @@ __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
       if (G == 1) {
         // Publish the tile's counts before the local scan, then look back.
 #pragma unroll
-        for (int q = 0; q < DPT; ++q) st_status(st_row + q, (unit == 0 ? kFlagInc : kFlagAgg) | ep | tot[q]);
+        for (int q = 0; q < DPT; ++q)
+          if (unit != a.withhold_unit) st_status(st_row + q, (unit == 0 ? kFlagInc : kFlagAgg) | ep | tot[q]);
       }
       uint32_t excl = block_excl_scan<TPB>(tsum, warp_tmp, &scan_total);
 #pragma unroll
@@ -393,7 +395,8 @@ __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
         look_back<RADIX, DPT, W>(a, unit, prefix);
 #pragma unroll
         for (int q = 0; q < DPT; ++q) {
-          if (unit > 0) st_status(st_row + q, kFlagInc | ep | ((prefix[q] + tot[q]) & kCountMask));
+          if (unit > 0 && unit != a.withhold_unit)
+            st_status(st_row + q, kFlagInc | ep | ((prefix[q] + tot[q]) & kCountMask));
           run[tid * DPT + q] = a.digit_start[tid * DPT + q] + prefix[q];
         }
       }
@@ -542,7 +545,7 @@ __device__ __forceinline__ void look_back32(const A& a, uint32_t unit, bool firs
       progress = progress || used > 0;
     }
     if (pending && !progress) {
-      if (++spins > kSpinLimit) {
+      if (++spins > a.lookback_spin_limit) {
         atomicOr(a.err, kErrLookbackTimeout);
         break;
       }
@@ -736,7 +739,8 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
     }
     uint32_t* st_row = a.status32 + static_cast<size_t>(unit) * RADIX + static_cast<size_t>(tid) * DPT;
 #pragma unroll
-    for (int q = 0; q < DPT; ++q) st_status32(st_row + q, (first_tile ? kInc32 : kAgg32) | tot[q]);
+    for (int q = 0; q < DPT; ++q)
+      if (unit != a.withhold_unit) st_status32(st_row + q, (first_tile ? kInc32 : kAgg32) | tot[q]);
     uint32_t excl = block_excl_scan<TPB>(tsum, warp_tmp, &scan_total);
     uint32_t my_start[DPT];
 #pragma unroll
@@ -778,7 +782,8 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
       const int d = tid * DPT + q;
-      if (!first_tile) st_status32(st_row + q, kInc32 | static_cast<uint32_t>((prefix[q] + tot[q]) & kCount32));
+      if (!first_tile && unit != a.withhold_unit)
+        st_status32(st_row + q, kInc32 | static_cast<uint32_t>((prefix[q] + tot[q]) & kCount32));
       globm[d] = digit_start[d] + prefix[q] - my_start[q];
     }
     __syncthreads();
@@ -912,6 +917,7 @@ cudaError_t launch_onesweep_bits(const SortPasses& sp, int group_tiles, const On
 // passes).  32 keys per thread: 8,192-key tiles, two blocks per SM, about
 // half the look-backs per key of 16.
 SortTuning g_sort_tuning{9, 0, 32};
+WaitTest g_wait_test{kDefaultSpinLimit, 0xFFFFFFFFu};
 
 // Digit plan: the fewest passes of at most max_bits bits, widths as even as
 // possible, the kernel's digit width the widest of them (at least 8).
@@ -1199,6 +1205,8 @@ cudaError_t radix_sort_run(const K* keys_in, const V* vals_in, K* keys_out, V* v
     a.tile_counter = counters + pass;
     a.epoch = static_cast<uint32_t>(pass + 1);
     a.err = err;
+    a.lookback_spin_limit = g_wait_test.lookback_spin_limit;
+    a.withhold_unit = g_wait_test.withhold_unit;
     a.status32 = reinterpret_cast<uint32_t*>(status);
     if (sizeof(V) == 8 && unpack && pass == sp.n_passes - 1) {
       a.unpack_target = unpack->target;

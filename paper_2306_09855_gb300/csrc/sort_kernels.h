@@ -38,6 +38,11 @@ struct OnesweepArgs {
   uint32_t* tile_counter;       // dynamic group tickets, zero before the pass
   uint32_t epoch;               // 1..16383, distinct for every pass sharing `status`
   uint32_t* err;
+  // Bound of every look-back wait (iterations) and a tile that publishes no
+  // look-back word (0xFFFFFFFF = none): the second makes the waits of the
+  // tiles after it expire, which tests use to reach the TIMEOUT path.
+  uint32_t lookback_spin_limit;
+  uint32_t withhold_unit;
   uint32_t* status32;           // bulk-copy kernel: 32-bit words [tile][digit], cleared per pass
   // Last pass of a build's sort: write the sorted values as separate target,
   // weight and delay arrays instead of vals_out (null otherwise).
@@ -73,6 +78,14 @@ struct SortTuning {
   int items;      // keys per thread of the bulk-copy kernel
 };
 extern SortTuning g_sort_tuning;
+
+// Look-back bound and withheld tile of later sorts (snc_set_wait_test).
+struct WaitTest {
+  uint32_t lookback_spin_limit;
+  uint32_t withhold_unit;
+};
+extern WaitTest g_wait_test;
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
 SortPasses plan_passes(int key_bits);  // with g_sort_tuning
 SortPasses plan_passes(int key_bits, const SortTuning& tune);

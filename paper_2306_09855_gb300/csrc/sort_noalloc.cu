@@ -43,6 +43,13 @@ constexpr size_t kTmpKeysBytes = kNoAllocMaxPairs * sizeof(uint64_t);
 constexpr size_t kTmpValsBytes = kNoAllocMaxPairs * sizeof(uint32_t);
 constexpr size_t kErrOffset = kTmpKeysBytes + kTmpValsBytes;
 constexpr size_t kSortOffset = kErrOffset + 256;
+constexpr SortTuning kNoAllocTuning{9, 0, 32};
+// Worst case of the fixed plan: 64-bit keys take eight passes of 8 bits, and
+// the status words of 2^19 / 8,192 tiles, two digit tables and the tickets
+// must fit after the ping-pong buffers.
+constexpr size_t kWorstTiles = (kNoAllocMaxPairs + 8191) / 8192;
+constexpr size_t kWorstSortScratch = kWorstTiles * 512 * sizeof(uint64_t) + 2 * 8 * 2048 * sizeof(uint64_t) + 4096;
+static_assert(kSortOffset + kWorstSortScratch <= kNoAllocScratchBytes, "no-allocation scratch too small");
 
 __device__ __align__(256) static unsigned char g_sort_scratch[kNoAllocScratchBytes];
 
@@ -92,7 +99,11 @@ extern "C" snc_status snc_radix_sort_pairs_noalloc(const uint64_t* keys_in, cons
     }
     if (n == 0) return SNC_OK;
     if (!keys_in || !vals_in || !keys_out || !vals_out) return fail(SNC_ERR_INVALID_ARG, "null buffer");
-    const SortPasses sp = plan_passes(key_bits);
+    // A fixed plan (digits of at most 9 bits, 8,192-key tiles), whatever the
+    // process-wide tuning: its scratch fits the array for every n and key
+    // width this entry point accepts (a wider tuned digit would need 2,048
+    // look-back words per tile).
+    const SortPasses sp = plan_passes(key_bits, kNoAllocTuning);
     if (kSortOffset + sort_scratch_bytes(n, sp) > kNoAllocScratchBytes)
       return fail(SNC_ERR_UNSUPPORTED, "sort scratch does not fit the static array");
     int dev = 0;
@@ -111,7 +122,14 @@ extern "C" snc_status snc_radix_sort_pairs_noalloc(const uint64_t* keys_in, cons
     if (e == cudaSuccess)
       e = radix_sort_run(keys_in, vals_in, keys_out, vals_out, keys_tmp, vals_tmp, n, sp, base + kSortOffset, err, st,
                          nullptr);
+    // Wait for the sort and read its error word (a bounded device wait that
+    // expired leaves the output unsorted).
+    uint32_t bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, err, sizeof bits, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(SNC_ERR_CUDA, cudaGetErrorString(e));
+    if (bits & kErrLookbackTimeout) return fail(SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
+    if (bits) return fail(SNC_ERR_CUDA, "device error bits set by the sort");
     return SNC_OK;
   });
 }

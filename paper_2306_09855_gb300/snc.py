@@ -113,7 +113,7 @@ EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", 
            "snc_deliver", "snc_set_target_shard", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
            "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_batch_finalize_graph",
-           "snc_batch_rebuild", "snc_last_error",
+           "snc_batch_rebuild", "snc_set_wait_test", "snc_last_error",
            "snc_server_create", "snc_server_destroy", "snc_server_submit", "snc_server_poll",
            "snc_server_wait_any", "snc_server_context", "snc_server_times", "snc_server_release",
            "snc_server_get_stats", "snc_estimate_build")
@@ -154,6 +154,7 @@ def load(build: bool = True):
         "snc_get_stats": ([P, ctypes.POINTER(snc_stats)], I32),
         "snc_set_tuning": ([ctypes.POINTER(snc_tuning)], I32),
         "snc_get_tuning": ([ctypes.POINTER(snc_tuning)], I32),
+        "snc_set_wait_test": ([U32, U32], I32),
         "snc_last_error": ([P], ctypes.c_char_p),
         "snc_server_create": ([ctypes.POINTER(snc_server_config), ctypes.POINTER(P)], I32),
         "snc_server_destroy": ([P], I32),
@@ -301,6 +302,12 @@ def snc_radix_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, n, key_bi
 
 
 SNC_NOALLOC_MAX_PAIRS = 1 << 19
+
+
+def snc_set_wait_test(lookback_spin_limit=0, withhold_tile=0xFFFFFFFF):
+    """Bound of the sort's look-back waits and a tile that never publishes
+    (tests of the TIMEOUT path); snc_set_wait_test() restores the defaults."""
+    _check(load().snc_set_wait_test(int(lookback_spin_limit), int(withhold_tile)))
 
 
 def snc_get_stats(ctx):
