@@ -24,13 +24,16 @@ Parity status (see the pins in tests/test_oracle_*.py):
                     invariances, per-connection weights by the Sec. 2.1
                     numbering, delays by hand-computed steps, the complete
                     cases by their unique results (tests/test_oracle_arrays.py)
+  build_parallel    the same functions on host threads (snc_oracle_par.c):
+                    pinned equal, bit for bit, to build() on every rule and
+                    flag pair (tests/test_oracle_parallel.py)
 """
 from __future__ import annotations
 
 import ctypes
 import numpy as np
 
-from .build import build_oracle
+from .build import build_oracle, build_oracle_par
 
 RULE_ID = {"one_to_one": 0, "all_to_all": 1, "fixed_indegree": 2, "fixed_outdegree": 3,
            "fixed_total_number": 4, "pairwise_bernoulli": 5}
@@ -66,6 +69,19 @@ class _Net(ctypes.Structure):
 
 
 _LIB = None
+_LIB_PAR = None
+
+
+def _lib_par():
+    global _LIB_PAR
+    if _LIB_PAR is None:
+        _LIB_PAR = ctypes.CDLL(build_oracle_par())
+    return _LIB_PAR
+
+
+def max_threads():
+    """Host threads the parallel oracle uses by default."""
+    return int(_lib_par().or_max_threads())
 
 
 def _lib():
@@ -274,3 +290,39 @@ def generate_primary(spec, proj, primary):
                                       _ptr(out["weight"]), ctypes.c_uint64(cap),
                                       ctypes.byref(n)), "generate_primary")
     return {k: v[:n.value].copy() for k, v in out.items()}
+
+
+def generate_parallel(spec, threads=0):
+    """generate() on host threads: the same arrays (threads = 0: all)."""
+    net, arr, _keep = _marshal(spec)
+    lib = _lib_par()
+    per = np.zeros(max(1, len(spec.projections)), dtype=np.uint64)
+    n = ctypes.c_uint64(0)
+    _check(lib.or_generate_par(ctypes.byref(net), arr, None, None, None, None, ctypes.c_uint64(0),
+                               ctypes.byref(n), _ptr(per), ctypes.c_int(threads)), "count")
+    total = int(n.value)
+    out = {"src": np.empty(total, np.uint32), "tgt": np.empty(total, np.uint32),
+           "delay": np.empty(total, np.uint16), "weight": np.empty(total, np.float32)}
+    _check(lib.or_generate_par(ctypes.byref(net), arr, _ptr(out["src"]), _ptr(out["tgt"]), _ptr(out["delay"]),
+                               _ptr(out["weight"]), ctypes.c_uint64(total), ctypes.byref(n), None,
+                               ctypes.c_int(threads)), "generate")
+    out["per_proj"] = per[:len(spec.projections)].astype(np.int64)
+    return out
+
+
+def build_parallel(spec, threads=0):
+    """build() on host threads: the same network, bit for bit."""
+    g = generate_parallel(spec, threads)
+    n_nodes = spec.n_nodes
+    n = g["src"].size
+    row_ptr = np.zeros(n_nodes + 1, np.uint64)
+    group_ptr = np.zeros(n_nodes + 1, np.uint64)
+    group_first = np.zeros(max(1, n), np.uint64)
+    ng = ctypes.c_uint64(0)
+    _check(_lib_par().or_sort_index_par(ctypes.c_uint32(n_nodes), ctypes.c_uint64(n), _ptr(g["src"]),
+                                        _ptr(g["tgt"]), _ptr(g["delay"]), _ptr(g["weight"]), _ptr(row_ptr),
+                                        _ptr(group_ptr), _ptr(group_first), ctypes.byref(ng),
+                                        ctypes.c_int(threads)), "sort_index")
+    return {"src": g["src"], "tgt": g["tgt"], "delay": g["delay"], "weight": g["weight"], "row_ptr": row_ptr,
+            "group_ptr": group_ptr, "group_first": group_first[:ng.value], "n_groups": int(ng.value),
+            "per_proj": g["per_proj"]}
