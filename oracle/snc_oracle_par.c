@@ -11,9 +11,9 @@
  *     source rows of all_to_all) are generated in parallel, each into the
  *     range an exclusive scan of the per-primary counts gives it, so the
  *     output is the single-thread output position for position;
- *   - fixed_total_number with multapses and autapses allowed (no redraws)
- *     draws its slots in parallel; the redraw rule is run as written, on one
- *     thread;
+ *   - fixed_total_number draws its slots in parallel; with autapses or
+ *     multapses forbidden each redraw round sorts its (pair, slot) claims
+ *     (gen_total_number_par below states why the winners are the same);
  *   - the stable (source, delay) sort is a merge sort: chunks sorted in
  *     parallel by the same comparison (source, delay, generation position,
  *     a total order, so the result is unique), then merged pairwise.
@@ -37,6 +37,175 @@ static uint64_t count_primary(const or_net* net, uint32_t proj, const or_proj* p
   uint32_t w[4];
   draw(net, proj, OR_TAG_COUNT, 0, b, 0, w);
   return table_value(t->b_base[skip], t->b_thr[skip], t->b_len[skip], w[0]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* fixed_total_number with autapses or multapses forbidden, on host threads. */
+/* The rule of gen_total_number, round by round: a slot whose pair is not     */
+/* allowed redraws; in round 0 the lowest slot drawing a pair takes it, in   */
+/* round r >= 1 the lowest pending slot drawing a pair that no earlier round */
+/* took.  Visiting slots in ascending order with a running set (the single- */
+/* thread form) and sorting each round's (pair, slot) claims give the same   */
+/* winners: both pick, per pair, the lowest claiming slot of the first round */
+/* in which the pair is claimed.                                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  uint64_t key;
+  uint64_t slot;
+} or_claim;
+
+static int cmp_claim(const void* x, const void* y) {
+  const or_claim* a = (const or_claim*)x;
+  const or_claim* b = (const or_claim*)y;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  if (a->slot != b->slot) return a->slot < b->slot ? -1 : 1;
+  return 0;
+}
+
+/* Sorts c[0..n) by (key, slot) on host threads (chunks, then pairwise merges). */
+static int sort_claims(or_claim* c, uint64_t n) {
+  if (n < 2) return OR_OK;
+  or_claim* tmp = (or_claim*)malloc(sizeof(or_claim) * (size_t)n);
+  if (!tmp) return OR_ERR_OOM;
+  int chunks = 1;
+  while (chunks < 4 * omp_get_max_threads() && (uint64_t)chunks * 65536 < n) chunks <<= 1;
+  const uint64_t per = (n + chunks - 1) / chunks;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int k = 0; k < chunks; ++k) {
+    const uint64_t lo = (uint64_t)k * per < n ? (uint64_t)k * per : n;
+    const uint64_t hi = lo + per < n ? lo + per : n;
+    qsort(c + lo, (size_t)(hi - lo), sizeof(or_claim), cmp_claim);
+  }
+  or_claim* from = c;
+  or_claim* to = tmp;
+  for (uint64_t width = per; width < n; width *= 2) {
+    const uint64_t pairs = (n + 2 * width - 1) / (2 * width);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (uint64_t k = 0; k < pairs; ++k) {
+      const uint64_t lo = k * 2 * width;
+      const uint64_t mid = lo + width < n ? lo + width : n;
+      const uint64_t hi = mid + width < n ? mid + width : n;
+      uint64_t i = lo, j = mid, o = lo;
+      while (i < mid && j < hi) to[o++] = cmp_claim(&from[j], &from[i]) < 0 ? from[j++] : from[i++];
+      while (i < mid) to[o++] = from[i++];
+      while (j < hi) to[o++] = from[j++];
+    }
+    or_claim* x = from;
+    from = to;
+    to = x;
+  }
+  if (from != c) memcpy(c, from, sizeof(or_claim) * (size_t)n);
+  free(tmp);
+  return OR_OK;
+}
+
+static int key_in(const uint64_t* keys, uint64_t n, uint64_t k) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) / 2;
+    if (keys[mid] < k) lo = mid + 1; else hi = mid;
+  }
+  return lo < n && keys[lo] == k;
+}
+
+static int cmp_u64(const void* x, const void* y) {
+  const uint64_t a = *(const uint64_t*)x, b = *(const uint64_t*)y;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+static int gen_total_number_par(const or_net* net, uint32_t proj, const or_proj* pj, const or_tables* t,
+                                or_sink* out) {
+  const uint32_t Ns = pj->src_n, Nt = pj->tgt_n;
+  const uint64_t N = pj->k;
+  if (N == 0) return OR_OK;
+  if (out->src && out->pos + N > out->cap) return OR_ERR_INVALID_ARG;
+  const int dedup = !pj->allow_multapses;
+  int st = OR_OK;
+  uint32_t* ps = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+  uint32_t* pt = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+  unsigned char* okv = (unsigned char*)malloc((size_t)N);
+  uint64_t* pending = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)N);
+  or_claim* claims = dedup ? (or_claim*)malloc(sizeof(or_claim) * (size_t)N) : 0;
+  uint64_t* taken = dedup ? (uint64_t*)malloc(sizeof(uint64_t) * (size_t)N) : 0; /* sorted keys taken */
+  uint64_t n_taken = 0;
+  if (!ps || !pt || !okv || !pending || (dedup && (!claims || !taken))) st = OR_ERR_OOM;
+  uint64_t n_pending = 0;
+  for (uint32_t round = 0; !st; ++round) {
+    if (round > OR_MAX_ROUND) {
+      st = OR_ERR_TIMEOUT;
+      break;
+    }
+    const uint64_t n_visit = round == 0 ? N : n_pending;
+    if (round > 0 && n_pending == 0) break;
+    /* Draw every visited slot's pair (round 0: WD word 1 and IDX word
+     * i mod 4; later rounds: words 0 and 1 of the round's DEDUP draw). */
+#pragma omp parallel for schedule(static)
+    for (uint64_t q = 0; q < n_visit; ++q) {
+      const uint64_t i = round == 0 ? q : pending[q];
+      uint32_t w[4];
+      if (round == 0) {
+        uint32_t x[4];
+        draw(net, proj, OR_TAG_WD, 0, OR_PRIMARY_NONE, i, w);
+        draw(net, proj, OR_TAG_IDX, 0, OR_PRIMARY_NONE, i / 4, x);
+        ps[i] = src_node(pj, rand_below(w[1], Ns));
+        pt[i] = tgt_node(pj, rand_below(x[i % 4], Nt));
+      } else {
+        draw(net, proj, OR_TAG_DEDUP, round, OR_PRIMARY_NONE, i, w);
+        ps[i] = src_node(pj, rand_below(w[0], Ns));
+        pt[i] = tgt_node(pj, rand_below(w[1], Nt));
+      }
+      okv[i] = pj->allow_autapses || ps[i] != pt[i];
+      if (okv[i] && dedup && key_in(taken, n_taken, ((uint64_t)ps[i] << 32) | pt[i])) okv[i] = 0;
+    }
+    if (dedup) {
+      /* Among this round's allowed claims the lowest slot of each pair wins. */
+      uint64_t nc = 0;
+      for (uint64_t q = 0; q < n_visit; ++q) {
+        const uint64_t i = round == 0 ? q : pending[q];
+        if (okv[i]) {
+          claims[nc].key = ((uint64_t)ps[i] << 32) | pt[i];
+          claims[nc].slot = i;
+          ++nc;
+        }
+      }
+      st = sort_claims(claims, nc);
+      if (st) break;
+      uint64_t n_new = 0;
+      for (uint64_t c = 0; c < nc; ++c) {
+        if (c > 0 && claims[c].key == claims[c - 1].key) {
+          okv[claims[c].slot] = 0;  /* a lower slot took the pair this round */
+        } else {
+          taken[n_taken + n_new++] = claims[c].key;
+        }
+      }
+      n_taken += n_new;
+      if (round > 0) qsort(taken, (size_t)n_taken, sizeof(uint64_t), cmp_u64);
+    }
+    /* The losers, ascending, are the next round's pending slots. */
+    uint64_t still = 0;
+    for (uint64_t q = 0; q < n_visit; ++q) {
+      const uint64_t i = round == 0 ? q : pending[q];
+      if (!okv[i]) pending[still++] = i;
+    }
+    n_pending = still;
+  }
+  if (!st) {
+#pragma omp parallel for schedule(static) reduction(| : st)
+    for (uint64_t i = 0; i < N; ++i) {
+      or_sink one = {out->src ? out->src + out->pos + i : 0, out->tgt ? out->tgt + out->pos + i : 0,
+                     out->delay ? out->delay + out->pos + i : 0, out->weight ? out->weight + out->pos + i : 0, 0,
+                     1};
+      st |= emit_wd(net, proj, pj, t, OR_PRIMARY_NONE, i, i, ps[i], pt[i], &one);
+    }
+    out->pos += N;
+  }
+  free(ps);
+  free(pt);
+  free(okv);
+  free(pending);
+  free(claims);
+  free(taken);
+  return st;
 }
 
 static uint64_t sel_size(const or_proj* pj) {
@@ -68,6 +237,7 @@ static int gen_projection_par(const or_net* net, uint32_t proj, const or_proj* p
     out->pos += N;
     return st;
   }
+  if (rule == OR_FIXED_TOTAL_NUMBER) return gen_total_number_par(net, proj, pj, t, out);
   if (rule != OR_FIXED_INDEGREE && rule != OR_FIXED_OUTDEGREE && rule != OR_PAIRWISE_BERNOULLI &&
       rule != OR_ALL_TO_ALL)
     return gen_projection(net, proj, pj, t, out);

@@ -83,3 +83,14 @@ def test_empty_and_degenerate(oracle_mod):
     ])
     _same(oracle_mod, spec)
     _same(oracle_mod, NetworkSpec(seed=1, dt=0.1, populations=[10], projections=[]))
+
+
+@pytest.mark.parametrize("aut,mult,n", [(False, False, 1500), (True, False, 1599), (False, True, 20_000),
+                                        (False, False, 1)])
+def test_total_number_redraw_rounds(oracle_mod, aut, mult, n):
+    """Dense fixed_total_number (almost every allowed pair taken): many
+    redraw rounds, claims on the same pair within a round and across rounds;
+    the threaded rounds pick the single-thread oracle's winners."""
+    spec = NetworkSpec(seed=17, dt=0.1, populations=[40], projections=[
+        Projection(src=(0, 40), tgt=(0, 40), rule="fixed_total_number", k=n, autapses=aut, multapses=mult, **WD)])
+    _same(oracle_mod, spec, 3)
