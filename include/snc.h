@@ -159,6 +159,45 @@ snc_status snc_create_population(snc_ctx* ctx, uint32_t n, uint32_t* first_id);
 snc_status snc_connect(snc_ctx* ctx, snc_range src, snc_range tgt, const snc_conn_rule* rule,
                        const snc_syn_spec* syn, uint32_t* proj_id);
 
+/* Explicit node lists and per-connection values of one Connect call
+ * (Sec. 2.1: sources and targets may be given as arrays of node ids, the
+ * rule's index formulas then giving positions in the arrays; weights and
+ * delays may be given per connection by arrays as long as the number of
+ * connections).  Every pointer is host memory, read during the call only
+ * (the library keeps its own copy); NULL leaves that part as in snc_connect.
+ *   src_ids: src.n node ids in place of the range src (src.first ignored);
+ *   tgt_ids: tgt.n node ids in place of the range tgt (tgt.first ignored);
+ *   weights: n_conn weights in place of the weight distribution;
+ *   delays_ms: n_conn delays (ms) in place of the delay distribution, each
+ *     rounded to floor(d / dt + 1/2) steps, at least one.
+ * Element i of weights / delays_ms belongs to connection number i of the
+ * rule's numbering (one_to_one i; all_to_all a * Nt + b; fixed_indegree
+ * b * K + j; fixed_outdegree a * K + j; fixed_total_number the slot); a
+ * number whose pair is dropped as an autapse leaves its element unused;
+ * pairwise_bernoulli takes no per-connection arrays (its count is drawn).
+ * Positions and random draws are those of ranges of the same lengths, so
+ * listing the ids of a range gives the range's network; an autapse is a pair
+ * of equal node ids.  With multapses forbidden both lists must hold distinct
+ * ids; with autapses forbidden so must the list a per-primary rule draws
+ * from (sources of fixed_indegree and pairwise_bernoulli, targets of
+ * fixed_outdegree). */
+typedef struct {
+  const uint32_t* src_ids;
+  const uint32_t* tgt_ids;
+  const float* weights;
+  const float* delays_ms;
+  uint64_t n_conn; /* elements of weights / delays_ms */
+} snc_conn_arrays;
+
+/* Connect with explicit arrays (Sec. 2.1), otherwise as snc_connect (arrays
+ * may be NULL: then it is snc_connect).  INVALID_ARG in addition: an id at or
+ * above the created nodes, a repeated id where distinct ids are required,
+ * n_conn different from the rule's numbered connections, a non-finite delay,
+ * per-connection arrays with pairwise_bernoulli.  UNSUPPORTED: a delay above
+ * 65535 steps.  STATE after snc_finalize. */
+snc_status snc_connect_arrays(snc_ctx* ctx, snc_range src, snc_range tgt, const snc_conn_rule* rule,
+                              const snc_syn_spec* syn, const snc_conn_arrays* arrays, uint32_t* proj_id);
+
 /* Calibration (Sec. 2.2, 2.6): generates every connection on the device,
  * sorts them stably by (source, delay step) and builds the CSR and group
  * index.

@@ -55,6 +55,44 @@ __device__ __forceinline__ uint32_t weight_bits(const DevProj& P, uint32_t w2, u
   return __float_as_uint(w);
 }
 
+// Node (build id) at position pos of the projection's source / target list:
+// the range, or the explicit ids of the Connect call (Sec. 2.1).
+__device__ __forceinline__ uint32_t src_node(const DevProj& P, const ArrayBlobs& A, uint32_t pos) {
+  return P.src_list == kNoList ? P.s0 + pos : P.t_base + A.ids[P.src_list + pos];
+}
+__device__ __forceinline__ uint32_t tgt_node(const DevProj& P, const ArrayBlobs& A, uint32_t pos) {
+  return P.tgt_list == kNoList ? P.t0 + pos : P.t_base + A.ids[P.tgt_list + pos];
+}
+
+// Delay step and weight bits of connection number inew of the rule's own
+// numbering: given per connection (Sec. 2.1), or drawn from the slot's WD
+// words (which are drawn either way).
+__device__ __forceinline__ uint32_t conn_delay(const DevProj& P, const ArrayBlobs& A, const SmemTables& t,
+                                               uint64_t inew, uint32_t u) {
+  return P.d_list == kNoList ? delay_step(P, t, u) : A.steps[P.d_list + inew];
+}
+__device__ __forceinline__ uint32_t conn_weight(const DevProj& P, const ArrayBlobs& A, uint64_t inew, uint32_t w2,
+                                                uint32_t w3) {
+  return P.w_list == kNoList ? weight_bits(P, w2, w3) : A.ids[P.w_list + inew];
+}
+
+// Per-primary rules without autapses: whether primary b (build id `node`)
+// appears in the list drawn from, and at which position *q.
+__device__ __forceinline__ bool self_in_other(const DevProj& P, const ArrayBlobs& A, uint32_t b, uint32_t node,
+                                              uint32_t first_other, uint32_t n_other, uint32_t* q) {
+  if (P.autapses) return false;
+  if (P.self_list != kNoList) {
+    const uint32_t v = A.ids[P.self_list + b];
+    *q = v;
+    return v != kNoPosition;
+  }
+  if (node >= first_other && node - first_other < n_other) {
+    *q = node - first_other;
+    return true;
+  }
+  return false;
+}
+
 // Stage the projection's delay table into shared memory.
 __device__ void load_delay_table(const DevProj& P, const uint32_t* thr_blob, const uint16_t* guide_blob,
                                  SmemTables t) {
@@ -129,25 +167,44 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
     if (P.rule == SNC_ALL_TO_ALL) {
       // Row a (source s0 + a); targets b' in [part * kChunk, ...).  With
       // autapses off the diagonal target is skipped and later rows shift.
+      // With explicit lists the dropped target positions of the row come
+      // from the host (ascending).
       const uint32_t row = static_cast<uint32_t>(lc / P.chunks_per_row);
       const uint32_t part = static_cast<uint32_t>(lc % P.chunks_per_row);
-      const uint32_t s = P.s0 + row;
-      const bool diag = !P.autapses && s >= P.t0 && s - P.t0 < P.nt;
-      const uint32_t row_len = P.nt - (diag ? 1u : 0u);
-      uint64_t before = 0;  // diagonal skips in rows < row
-      if (!P.autapses) {
+      const uint32_t s = src_node(P, a.arr, row);
+      uint32_t n_drop = 0, diag_b = 0;
+      uint64_t before = 0;  // dropped pairs in rows < row
+      const uint32_t* drops = nullptr;
+      if (P.row_list != kNoList) {
+        before = a.arr.offs[P.row_list + row];
+        n_drop = static_cast<uint32_t>(a.arr.offs[P.row_list + row + 1] - before);
+        drops = a.arr.ids + P.drop_list + before;
+      } else if (!P.autapses) {
+        if (s >= P.t0 && s - P.t0 < P.nt) {
+          n_drop = 1;
+          diag_b = s - P.t0;
+        }
         const uint32_t lo = max(P.s0, P.t0), hi = min(P.s0 + P.ns, P.t0 + P.nt);
         if (hi > lo && s > lo) before = min(s, hi) - lo;
       }
+      const uint32_t row_len = P.nt - n_drop;
       const uint64_t row_out = P.out_off + static_cast<uint64_t>(row) * P.nt - before;
-      const uint32_t diag_b = s - P.t0;
       for (uint32_t e = threadIdx.x; e < kChunk; e += blockDim.x) {
         const uint32_t bp = part * kChunk + e;
         if (bp >= row_len) break;
-        const uint32_t b = bp + (diag && bp >= diag_b ? 1u : 0u);
-        const Words W = draw(P.k0, P.k1, kTagWD, 0, b, row);
-        store(a, bh, row_out + bp, s - P.t_base, delay_step(P, tabs, W.x), P.t0 + b - P.t_base,
-              weight_bits(P, W.z, W.w));
+        uint32_t b = bp;
+        if (drops) {
+          for (uint32_t k = 0; k < n_drop; ++k) {
+            if (drops[k] > b) break;
+            ++b;
+          }
+        } else if (n_drop && bp >= diag_b) {
+          b = bp + 1;
+        }
+        const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, row);
+        const uint64_t inew = static_cast<uint64_t>(row) * P.nt + b;
+        store(a, bh, row_out + bp, s - P.t_base, conn_delay(P, a.arr, tabs, inew, W.x),
+              tgt_node(P, a.arr, b) - P.t_base, conn_weight(P, a.arr, inew, W.z, W.w));
       }
       continue;
     }
@@ -175,14 +232,18 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
         }
         if (i >= end) continue;
         uint32_t s, t, primary;
-        uint64_t slot;
+        uint64_t slot, inew = i;
         switch (P.rule) {
-          case SNC_ONE_TO_ONE:
-            s = P.s0 + static_cast<uint32_t>(i);
-            t = P.t0 + static_cast<uint32_t>(i);
-            primary = static_cast<uint32_t>(i);
+          case SNC_ONE_TO_ONE: {
+            // pair i of the kept pairs (explicit lists without autapses)
+            const uint32_t pos = P.row_list != kNoList ? a.arr.ids[P.row_list + i] : static_cast<uint32_t>(i);
+            s = src_node(P, a.arr, pos);
+            t = tgt_node(P, a.arr, pos);
+            primary = pos;
             slot = 0;
+            inew = pos;
             break;
+          }
           case SNC_FIXED_INDEGREE:
           case SNC_FIXED_OUTDEGREE: {
             uint64_t b, j;
@@ -205,20 +266,23 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
             s = t = 0;
             break;
         }
-        const Words W = draw(P.k0, P.k1, kTagWD, 0, primary, slot);
+        const Words W = draw(P.k0, P.k1, kTagWD, 0, primary == kPrimaryNone ? primary : primary + P.prim_shift, slot);
         if (P.rule == SNC_FIXED_INDEGREE) {
-          t = P.t0 + primary;
-          const bool skip = !P.autapses && t >= P.s0 && t - P.s0 < P.ns;
-          s = P.s0 + endpoint(W.y, P.ns, skip, t - P.s0);
+          t = tgt_node(P, a.arr, primary);
+          uint32_t q = 0;
+          const bool skip = self_in_other(P, a.arr, primary, t, P.s0, P.ns, &q);
+          s = src_node(P, a.arr, endpoint(W.y, P.ns, skip, q));
         } else if (P.rule == SNC_FIXED_OUTDEGREE) {
-          s = P.s0 + primary;
-          const bool skip = !P.autapses && s >= P.t0 && s - P.t0 < P.nt;
-          t = P.t0 + endpoint(W.y, P.nt, skip, s - P.t0);
+          s = src_node(P, a.arr, primary);
+          uint32_t q = 0;
+          const bool skip = self_in_other(P, a.arr, primary, s, P.t0, P.nt, &q);
+          t = tgt_node(P, a.arr, endpoint(W.y, P.nt, skip, q));
         } else if (P.rule == SNC_FIXED_TOTAL_NUMBER) {
-          s = P.s0 + rand_below(W.y, P.ns);
-          t = P.t0 + rand_below(tw, P.nt);
+          s = src_node(P, a.arr, rand_below(W.y, P.ns));
+          t = tgt_node(P, a.arr, rand_below(tw, P.nt));
         }
-        store(a, bh, P.out_off + i, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+        store(a, bh, P.out_off + i, s - P.t_base, conn_delay(P, a.arr, tabs, inew, W.x), t - P.t_base,
+              conn_weight(P, a.arr, inew, W.z, W.w));
       }
     }
   }
@@ -241,16 +305,18 @@ __device__ __forceinline__ int find_segment(const uint64_t* prefix, int n, uint6
 }
 
 __global__ void bernoulli_count_kernel(const DevProj* projs, const uint32_t* list, const uint64_t* prefix, int n_list,
-                                       const uint32_t* thr_blob, const uint16_t* guide_blob, uint32_t* counts) {
+                                       const uint32_t* thr_blob, const uint16_t* guide_blob, ArrayBlobs arr,
+                                       uint32_t* counts) {
   const uint64_t total = prefix[n_list];
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total; g += stride) {
     const int j = find_segment(prefix, n_list, g);
     const DevProj& P = projs[list[j]];
     const uint32_t b = static_cast<uint32_t>(g - prefix[j]);
-    const uint32_t node = P.t0 + b;
-    const int skip = (!P.autapses && node >= P.s0 && node - P.s0 < P.ns) ? 1 : 0;
-    const Words W = draw(P.k0, P.k1, kTagCount, 0, b, 0);
+    const uint32_t node = tgt_node(P, arr, b);
+    uint32_t q = 0;
+    const int skip = self_in_other(P, arr, b, node, P.s0, P.ns, &q) ? 1 : 0;
+    const Words W = draw(P.k0, P.k1, kTagCount, 0, b + P.prim_shift, 0);
     const uint32_t i = table_lookup(thr_blob + P.b_off[skip], guide_blob + P.b_goff[skip], P.b_len[skip], W.x);
     counts[g] = P.b_base[skip] + i;
   }
@@ -302,13 +368,13 @@ __global__ void sampler_kernel(SamplerArgs a) {
     const uint32_t b = static_cast<uint32_t>(gp - a.prim_prefix[j]);
     const bool indeg = P.rule != SNC_FIXED_OUTDEGREE;  // indegree and Bernoulli pick sources
     const uint32_t n_other = indeg ? P.ns : P.nt;
-    const uint32_t first_primary = indeg ? P.t0 : P.s0;
     const uint32_t first_other = indeg ? P.s0 : P.t0;
     const uint32_t words = (n_other + 31u) >> 5;
   {
-    const uint32_t node = first_primary + b;
-    const bool skip = !P.autapses && node >= first_other && node - first_other < n_other;
-    const uint32_t skip_local = skip ? node - first_other : 0u;
+    const ArrayBlobs& A = a.gen.arr;
+    const uint32_t node = indeg ? tgt_node(P, A, b) : src_node(P, A, b);
+    uint32_t skip_local = 0;
+    const bool skip = self_in_other(P, A, b, node, first_other, n_other, &skip_local);
     const uint32_t cand = n_other - (skip ? 1u : 0u);
     uint64_t want, out;
     if (P.rule == SNC_PAIRWISE_BERNOULLI) {
@@ -332,7 +398,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
         break;
       }
       // One IDX draw per lane: attempts 4*(call + lane) .. +3.
-      const Words X = draw(P.k0, P.k1, kTagIdx, 0, b, call + lane);
+      const Words X = draw(P.k0, P.k1, kTagIdx, 0, b + P.prim_shift, call + lane);
       call += 32;
 #pragma unroll 1
       for (int q = 0; q < 4 && got < need; ++q) {
@@ -358,10 +424,12 @@ __global__ void sampler_kernel(SamplerArgs a) {
           atomicOr(&bitmap[r >> 5], bit);
           if (!complement) {
             const uint32_t j = got + rank;
-            const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
-            const uint32_t other = first_other + r;
+            const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, j);
+            const uint32_t other = indeg ? src_node(P, A, r) : tgt_node(P, A, r);
             const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            store(a.gen, bh, out + j, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+            const uint64_t inew = static_cast<uint64_t>(b + P.prim_shift) * P.k + j;
+            store(a.gen, bh, out + j, s - P.t_base, conn_delay(P, A, tabs, inew, W.x), t - P.t_base,
+                  conn_weight(P, A, inew, W.z, W.w));
           }
         }
         got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
@@ -393,10 +461,12 @@ __global__ void sampler_kernel(SamplerArgs a) {
           free_bits &= free_bits - 1;
           const uint32_t r = w * 32 + bitpos;
           if (j < want) {
-            const Words W = draw(P.k0, P.k1, kTagWD, 0, b, j);
-            const uint32_t other = first_other + r;
+            const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, j);
+            const uint32_t other = indeg ? src_node(P, A, r) : tgt_node(P, A, r);
             const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            store(a.gen, bh, out + j, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base, weight_bits(P, W.z, W.w));
+            const uint64_t inew = static_cast<uint64_t>(b + P.prim_shift) * P.k + j;
+            store(a.gen, bh, out + j, s - P.t_base, conn_delay(P, A, tabs, inew, W.x), t - P.t_base,
+                  conn_weight(P, A, inew, W.z, W.w));
           } else {
             atomicOr(a.err, kErrBounds);
           }
@@ -444,8 +514,13 @@ __device__ __forceinline__ uint64_t pair_hash(uint64_t key) {
   return key;
 }
 
-__device__ __forceinline__ bool allowed_pair(const DevProj& P, uint32_t s, uint32_t t) {
-  return P.autapses || s != t;
+// (s, t): source and target positions offset by s0 / t0 (equal to the
+// nodes for ranges); with explicit lists the nodes at those positions are
+// compared.
+__device__ __forceinline__ bool allowed_pair(const DevProj& P, const ArrayBlobs& A, uint32_t s, uint32_t t) {
+  if (P.autapses) return true;
+  if (P.src_list == kNoList && P.tgt_list == kNoList) return s != t;
+  return src_node(P, A, s - P.s0) != tgt_node(P, A, t - P.t0);
 }
 
 // The slot g of the concatenated list: its projection and local slot.
@@ -639,7 +714,7 @@ __global__ void redraw_round0_kernel(RedrawArgs a) {
     const uint32_t s = P.s0 + rand_below(W.y, P.ns);
     const uint32_t t = P.t0 + rand_below(tw, P.nt);
     a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
-    if (!allowed_pair(P, s, t)) a.lost[g] = 1;
+    if (!allowed_pair(P, a.arr, s, t)) a.lost[g] = 1;
     else if (!P.multapses) claim(a, *x.r, P, s, t, x.i, g, true);
   }
 }
@@ -663,7 +738,7 @@ __global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint6
     a.pairs[g] = (static_cast<uint64_t>(s) << 32) | t;
     if (a.moved) atomicOr(a.moved + (g >> 5), 1u << (g & 31u));
     // The resolve kernel decides every slot (not allowed -> next round).
-    if (!P.multapses && allowed_pair(P, s, t)) {
+    if (!P.multapses && allowed_pair(P, a.arr, s, t)) {
       if (a.bucketed) bucket_claim(a, *x.r, P, s, t, x.i);
       else claim(a, *x.r, P, s, t, x.i, g, false);
     }
@@ -765,11 +840,11 @@ __global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, Red
           ent[k] = 0;
           if (i >= end) continue;
           const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-          const uint32_t s = P.s0 + rand_below(W.y, P.ns);
-          const uint32_t t = P.t0 + rand_below(tw, P.nt);
-          store(g, bh, P.out_off + i, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base,
-                weight_bits(P, W.z, W.w));
-          if (!allowed_pair(P, s, t)) {
+          const uint32_t ps = rand_below(W.y, P.ns), pt = rand_below(tw, P.nt);
+          const uint32_t s = P.s0 + ps, t = P.t0 + pt;
+          store(g, bh, P.out_off + i, src_node(P, g.arr, ps) - P.t_base, conn_delay(P, g.arr, tabs, i, W.x),
+                tgt_node(P, g.arr, pt) - P.t_base, conn_weight(P, g.arr, i, W.z, W.w));
+          if (!allowed_pair(P, a.arr, s, t)) {
             push_pending(a, r.slot_base + i);
           } else if (part) {
             const uint64_t pair = local_pair(r, P, s, t);
@@ -866,7 +941,8 @@ __global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a) {
       const uint64_t pos = P.out_off + x.i;
       if (!SNC_IN_BOUNDS(a.err, 2u, pos, g.cap)) continue;
       const uint64_t pair = a.pairs[gs];
-      const uint32_t s = static_cast<uint32_t>(pair >> 32), t = static_cast<uint32_t>(pair);
+      const uint32_t s = src_node(P, g.arr, static_cast<uint32_t>(pair >> 32) - P.s0);
+      const uint32_t t = tgt_node(P, g.arr, static_cast<uint32_t>(pair) - P.t0);
       const uint64_t old = g.key32 ? static_cast<uint64_t>(static_cast<uint32_t*>(g.keys)[pos])
                                    : static_cast<uint64_t*>(g.keys)[pos];
       const uint64_t key = pack_key(s - P.t_base, static_cast<uint32_t>(old & dmask), g.layout.delay_bits);
@@ -1068,7 +1144,7 @@ __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uin
     const DevProj& P = *x.P;
     const uint64_t pair = a.pairs[g];
     const uint32_t s = static_cast<uint32_t>(pair >> 32), t = static_cast<uint32_t>(pair);
-    bool ok = allowed_pair(P, s, t);
+    bool ok = allowed_pair(P, a.arr, s, t);
     if (ok && !P.multapses) ok = a.bucketed ? bucket_resolve(a, *x.r, P, s, t, x.i) : resolve(a, *x.r, P, s, t, x.i);
     if (!ok) push_pending(a, g);
   }
@@ -1108,8 +1184,10 @@ __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, Redr
         if (i >= end) continue;
         const uint64_t pair = a.pairs[r.slot_base + i];
         const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-        store(g, bh, P.out_off + i, static_cast<uint32_t>(pair >> 32) - P.t_base, delay_step(P, tabs, W.x),
-              static_cast<uint32_t>(pair) - P.t_base, weight_bits(P, W.z, W.w));
+        const uint32_t s = src_node(P, g.arr, static_cast<uint32_t>(pair >> 32) - P.s0);
+        const uint32_t t = tgt_node(P, g.arr, static_cast<uint32_t>(pair) - P.t0);
+        store(g, bh, P.out_off + i, s - P.t_base, conn_delay(P, g.arr, tabs, i, W.x), t - P.t_base,
+              conn_weight(P, g.arr, i, W.z, W.w));
       }
     }
   }

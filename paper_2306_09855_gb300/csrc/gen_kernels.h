@@ -30,6 +30,7 @@ struct GenArgs {
   uint64_t cap;    // entries of keys / vals
   uint32_t* err;   // device error block (bounds checks)
   HistPlan hist;   // digit counts of the sort's passes, accumulated as keys are written
+  ArrayBlobs arr;  // explicit arrays of the Connect calls (DevProj list offsets)
 };
 
 // One launch serves every listed sampler projection: warps take primary
@@ -54,7 +55,8 @@ __global__ void gen_direct_kernel(GenArgs a);
 // Per-target Binomial counts of every listed pairwise_bernoulli projection
 // (targets concatenated in list order, prefix[n_list] in total).
 __global__ void bernoulli_count_kernel(const DevProj* projs, const uint32_t* list, const uint64_t* prefix, int n_list,
-                                       const uint32_t* thr_blob, const uint16_t* guide_blob, uint32_t* counts);
+                                       const uint32_t* thr_blob, const uint16_t* guide_blob, ArrayBlobs arr,
+                                       uint32_t* counts);
 // out[j] = offsets[prefix[j + 1]] - offsets[prefix[j]]: connections per listed projection.
 __global__ void segment_totals_kernel(const uint64_t* offsets, const uint64_t* prefix, int n_list, uint64_t* out);
 __global__ void sampler_kernel(SamplerArgs a);
@@ -94,6 +96,7 @@ struct RedrawProj {
 
 struct RedrawArgs {
   const DevProj* projs;
+  ArrayBlobs arr;              // explicit arrays (node lists compared for autapses)
   const RedrawProj* rp;
   int n;                       // redraw projections
   uint64_t n_slots;            // all slots

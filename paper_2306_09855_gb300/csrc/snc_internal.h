@@ -47,6 +47,34 @@ struct DevProj {
   uint64_t n_chunks;
   uint32_t chunks_per_row;  // all_to_all: chunks per source row
   uint32_t row_len;         // all_to_all: connections per source row (full row)
+  // Primary node index of the projection's first primary in the Connect
+  // call's own numbering: 0, except for a target shard, whose target-primary
+  // projections (one_to_one, all_to_all, fixed_indegree,
+  // pairwise_bernoulli) keep only the targets in the shard and key every
+  // draw by primary + prim_shift, the index the whole network uses.
+  uint32_t prim_shift;
+  uint32_t reserved0;
+  // Explicit arrays of the Connect call (Sec. 2.1), as offsets into the
+  // build's array blobs (kNoList: not given).  src_list / tgt_list: node ids
+  // (network-local) in place of the ranges; w_list: per-connection weight
+  // bits; d_list: per-connection delay steps (step blob); self_list: per
+  // primary node, the position of its node in the list drawn from
+  // (kNoPosition: absent), for per-primary rules without autapses;
+  // row_list: one_to_one without autapses, the kept positions (id blob);
+  // all_to_all without autapses, the dropped pairs before each source row
+  // (offset blob, ns + 1 entries); drop_list: all_to_all, the dropped target
+  // positions of every row, ascending per row (id blob).
+  uint64_t src_list, tgt_list, w_list, d_list, self_list, row_list, drop_list;
+};
+constexpr uint64_t kNoList = ~0ull;
+constexpr uint32_t kNoPosition = 0xFFFFFFFFu;
+
+// The build's array blobs (device): node ids, weight bits and positions
+// (uint32), delay steps (uint16), row offsets (uint64).
+struct ArrayBlobs {
+  const uint32_t* ids;
+  const uint16_t* steps;
+  const uint64_t* offs;
 };
 
 // Sort key and value of a connection.  The key packs source | delay step
@@ -85,6 +113,15 @@ struct Projection {
   uint64_t b_base[2] = {0, 0};
   std::vector<uint32_t> b_thr[2];
   uint32_t max_step = 1;
+  // Explicit arrays (snc_connect_arrays): node ids in place of the ranges
+  // (src_list / tgt_list set), per-connection weight bits and delay steps
+  // (empty: drawn).
+  bool src_list = false, tgt_list = false;
+  std::vector<uint32_t> src_ids, tgt_ids;
+  std::vector<uint32_t> w_bits;
+  std::vector<uint16_t> d_steps;
+  bool has_lists() const { return src_list || tgt_list; }
+  bool has_arrays() const { return has_lists() || !w_bits.empty() || !d_steps.empty(); }
 };
 
 // Device-memory estimate of finalizing one context (snc_runtime.cu).

@@ -14,6 +14,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/snc.h"
@@ -344,15 +345,32 @@ bool is_total_redraw(const Projection& p) {
 // Validation and sizing of one Connect call (readings of Sec. 2.1 / Sec. 4).
 // The node lists, the rule's limits and the count are checked as for a call
 // with explicit arrays (arrays.cpp), here with both lists given as ranges.
-snc_status plan_projection(snc_ctx* c, Projection& p) {
+snc_status plan_projection(snc_ctx* c, Projection& p, const ConnectArrays& arrays = ConnectArrays{}) {
   const snc_conn_rule& r = p.rule;
   ArrayPlan lists;
   std::string why;
   const snc_status cs = check_connect_arrays(static_cast<uint32_t>(c->n_nodes), c->cfg.dt_ms, p.src, p.tgt, r,
-                                             ConnectArrays{}, &lists, &why);
+                                             arrays, &lists, &why);
   if (cs != SNC_OK) return fail(c, cs, "connect: %s", why.c_str());
   p.exact_count = r.kind != SNC_PAIRWISE_BERNOULLI;  // Bernoulli counts are drawn at finalize
   p.count = lists.count;
+  // The library's own copy of the arrays (the caller's are read during the
+  // call only).
+  if (arrays.src_ids) {
+    p.src_list = true;
+    p.src_ids.assign(arrays.src_ids, arrays.src_ids + p.src.n);
+    p.src.first = 0;
+  }
+  if (arrays.tgt_ids) {
+    p.tgt_list = true;
+    p.tgt_ids.assign(arrays.tgt_ids, arrays.tgt_ids + p.tgt.n);
+    p.tgt.first = 0;
+  }
+  if (arrays.weights) {
+    p.w_bits.resize(arrays.n_conn);
+    std::memcpy(p.w_bits.data(), arrays.weights, arrays.n_conn * sizeof(float));
+  }
+  if (arrays.delays_ms) p.d_steps = std::move(lists.steps);
   const snc_dist& wd = p.syn.weight;
   const snc_dist& dd = p.syn.delay_ms;
   if ((wd.kind != SNC_DIST_CONST && wd.kind != SNC_DIST_NORMAL) ||
@@ -361,8 +379,17 @@ snc_status plan_projection(snc_ctx* c, Projection& p) {
   if ((wd.kind == SNC_DIST_NORMAL && !(wd.std >= 0.0)) || (dd.kind == SNC_DIST_NORMAL && !(dd.std >= 0.0)))
     return fail(c, SNC_ERR_INVALID_ARG, "negative standard deviation");
   if (!std::isfinite(wd.mean) || !std::isfinite(dd.mean)) return fail(c, SNC_ERR_INVALID_ARG, "non-finite mean");
-  // Delay: constant step or threshold table (Sec. 2.1: round(d / dt), >= 1).
-  if (dd.kind == SNC_DIST_CONST || dd.std == 0.0) {
+  // Delay: given per connection, constant step or threshold table (Sec. 2.1:
+  // round(d / dt), >= 1).
+  if (!p.d_steps.empty()) {
+    p.d_table = false;
+    p.d_const = 1;
+    p.max_step = std::max<uint32_t>(1, lists.max_step);
+  } else if (arrays.delays_ms) {  // zero numbered connections
+    p.d_table = false;
+    p.d_const = 1;
+    p.max_step = 1;
+  } else if (dd.kind == SNC_DIST_CONST || dd.std == 0.0) {
     uint32_t step = 1;
     if (delay_step_of(dd.mean, c->cfg.dt_ms, &step) != SNC_OK)
       return fail(c, SNC_ERR_UNSUPPORTED, "delay above 65535 steps");
@@ -533,6 +560,11 @@ snc_status snc_create_population(snc_ctx* c, uint32_t n, uint32_t* first_id) {
 
 snc_status snc_connect(snc_ctx* c, snc_range src, snc_range tgt, const snc_conn_rule* rule,
                        const snc_syn_spec* syn, uint32_t* proj_id) {
+  return snc_connect_arrays(c, src, tgt, rule, syn, nullptr, proj_id);
+}
+
+snc_status snc_connect_arrays(snc_ctx* c, snc_range src, snc_range tgt, const snc_conn_rule* rule,
+                              const snc_syn_spec* syn, const snc_conn_arrays* arrays, uint32_t* proj_id) {
   return snc::abi_guard([&]() -> snc_status {
     if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
     if (!rule || !syn) return fail(c, SNC_ERR_INVALID_ARG, "connect: null rule or synapse spec");
@@ -542,7 +574,15 @@ snc_status snc_connect(snc_ctx* c, snc_range src, snc_range tgt, const snc_conn_
     p.tgt = tgt;
     p.rule = *rule;
     p.syn = *syn;
-    const snc_status st = plan_projection(c, p);
+    ConnectArrays ca;
+    if (arrays) {
+      ca.src_ids = arrays->src_ids;
+      ca.tgt_ids = arrays->tgt_ids;
+      ca.weights = arrays->weights;
+      ca.delays_ms = arrays->delays_ms;
+      ca.n_conn = arrays->n_conn;
+    }
+    const snc_status st = plan_projection(c, p, ca);
     if (st != SNC_OK) return st;
     if (proj_id) *proj_id = static_cast<uint32_t>(c->projs.size());
     c->projs.push_back(std::move(p));
@@ -594,6 +634,50 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   const uint64_t total_nodes = node_base[n_members];
   if (total_nodes > 0xFFFFFFFFull) return fail(c, SNC_ERR_UNSUPPORTED, "more than 2^32 - 1 nodes in one build");
 
+  // Target shard.  A projection whose primary node is the target
+  // (one_to_one, all_to_all, fixed_indegree, pairwise_bernoulli) keeps only
+  // the targets inside the shard: its node range shrinks to them and its
+  // draws stay keyed by the whole network's primary index (prim_shift), so it
+  // generates exactly its share and nothing else.  fixed_outdegree and
+  // fixed_total_number draw their targets, and a call with explicit arrays
+  // has no contiguous target range, so these are generated whole and the
+  // connections onto other targets are filtered out after generation.
+  std::vector<Projection> shard_projs;
+  std::vector<uint32_t> prim_shift(ups.size(), 0);
+  bool shard_filter = false;
+  if (n_members == 1 && c->sharded) {
+    shard_projs.reserve(ups.size());
+    for (size_t i = 0; i < ups.size(); ++i) {
+      Projection q = *ups[i].p;
+      const int kind = q.rule.kind;
+      if (!q.has_arrays() && (kind == SNC_ONE_TO_ONE || kind == SNC_ALL_TO_ALL || kind == SNC_FIXED_INDEGREE ||
+                              kind == SNC_PAIRWISE_BERNOULLI)) {
+        const uint64_t f = c->shard_first, e = f + c->shard_n;
+        const uint64_t t0 = q.tgt.first, t1 = t0 + q.tgt.n;
+        const uint64_t lo = std::max(f, t0), hi = std::min(e, t1);
+        const uint32_t shift = hi > lo ? static_cast<uint32_t>(lo - t0) : 0u;
+        const uint32_t nt = hi > lo ? static_cast<uint32_t>(hi - lo) : 0u;
+        q.tgt.first = static_cast<uint32_t>(t0) + shift;
+        q.tgt.n = nt;
+        if (kind == SNC_ONE_TO_ONE) {  // pair i = (s0 + i, t0 + i)
+          q.src.first += shift;
+          q.src.n = nt;
+        }
+        ArrayPlan lists;
+        std::string why;
+        if (check_connect_arrays(static_cast<uint32_t>(c->n_nodes), c->cfg.dt_ms, q.src, q.tgt, q.rule,
+                                 ConnectArrays{}, &lists, &why) != SNC_OK)
+          return fail(c, SNC_ERR_INVALID_ARG, "target shard: %s", why.c_str());
+        q.count = lists.count;
+        prim_shift[i] = shift;
+      } else {
+        shard_filter = true;
+      }
+      shard_projs.push_back(std::move(q));
+    }
+    for (size_t i = 0; i < ups.size(); ++i) ups[i].p = &shard_projs[i];
+  }
+
   // Key layout: global source | delay step | member-local target.
   uint32_t max_step = 1;
   for (const UnionProj& u : ups) max_step = std::max(max_step, u.p->max_step);
@@ -627,6 +711,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     d.t0 = p.tgt.first + ups[i].base;
     d.nt = p.tgt.n;
     d.t_base = ups[i].base;
+    d.prim_shift = prim_shift[i];
     d.rule = static_cast<uint32_t>(p.rule.kind);
     d.autapses = p.rule.allow_autapses ? 1u : 0u;
     d.multapses = p.rule.allow_multapses ? 1u : 0u;
@@ -656,15 +741,93 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   if (thr_blob.empty()) thr_blob.push_back(0);
   if (guide_blob.empty()) guide_blob.resize(kDelayGuide, 0);
 
+  // Explicit arrays (Sec. 2.1): node ids, weights and delay steps of every
+  // call that gave them, plus what the kernels need to skip autapses on
+  // lists: the position of each primary's node in the list it draws from
+  // (per-primary rules), the kept pairs (one_to_one) and the dropped pairs
+  // of each source row (all_to_all).
+  std::vector<uint32_t> id_blob;
+  std::vector<uint16_t> step_blob;
+  std::vector<uint64_t> off_blob;
+  bool any_lists = false;
+  for (size_t i = 0; i < np; ++i) {
+    const Projection& p = *ups[i].p;
+    DevProj& d = dp[i];
+    d.src_list = d.tgt_list = d.w_list = d.d_list = d.self_list = d.row_list = d.drop_list = kNoList;
+    if (!p.has_arrays()) continue;
+    any_lists = any_lists || p.has_lists();
+    const auto append = [&](const std::vector<uint32_t>& v) {
+      const uint64_t off = id_blob.size();
+      id_blob.insert(id_blob.end(), v.begin(), v.end());
+      return off;
+    };
+    if (p.src_list) d.src_list = append(p.src_ids);
+    if (p.tgt_list) d.tgt_list = append(p.tgt_ids);
+    if (!p.w_bits.empty()) d.w_list = append(p.w_bits);
+    if (!p.d_steps.empty()) {
+      d.d_list = step_blob.size();
+      step_blob.insert(step_blob.end(), p.d_steps.begin(), p.d_steps.end());
+    }
+    if (!p.has_lists() || p.rule.allow_autapses) continue;
+    const auto src_at = [&](uint32_t a) { return p.src_list ? p.src_ids[a] : p.src.first + a; };
+    const auto tgt_at = [&](uint32_t b) { return p.tgt_list ? p.tgt_ids[b] : p.tgt.first + b; };
+    const int kind = p.rule.kind;
+    if (kind == SNC_FIXED_INDEGREE || kind == SNC_FIXED_OUTDEGREE || kind == SNC_PAIRWISE_BERNOULLI) {
+      // The list drawn from holds distinct ids here (checked at Connect).
+      const bool out = kind == SNC_FIXED_OUTDEGREE;
+      const uint32_t n_other = out ? p.tgt.n : p.src.n, n_prim = out ? p.src.n : p.tgt.n;
+      std::unordered_map<uint32_t, uint32_t> where;
+      where.reserve(n_other * 2u + 1u);
+      for (uint32_t k = 0; k < n_other; ++k) where.emplace(out ? tgt_at(k) : src_at(k), k);
+      std::vector<uint32_t> self(n_prim, kNoPosition);
+      for (uint32_t b = 0; b < n_prim; ++b) {
+        const auto it = where.find(out ? src_at(b) : tgt_at(b));
+        if (it != where.end()) self[b] = it->second;
+      }
+      d.self_list = append(self);
+    } else if (kind == SNC_ONE_TO_ONE) {
+      std::vector<uint32_t> kept;
+      kept.reserve(p.src.n);
+      for (uint32_t k = 0; k < p.src.n; ++k)
+        if (src_at(k) != tgt_at(k)) kept.push_back(k);
+      d.row_list = append(kept);
+    } else if (kind == SNC_ALL_TO_ALL) {
+      std::unordered_map<uint32_t, std::vector<uint32_t>> at;  // target id -> its positions, ascending
+      for (uint32_t b = 0; b < p.tgt.n; ++b) at[tgt_at(b)].push_back(b);
+      std::vector<uint32_t> drops;
+      d.row_list = off_blob.size();
+      uint64_t run = 0;
+      for (uint32_t a = 0; a < p.src.n; ++a) {
+        off_blob.push_back(run);
+        const auto it = at.find(src_at(a));
+        if (it == at.end()) continue;
+        drops.insert(drops.end(), it->second.begin(), it->second.end());
+        run += it->second.size();
+      }
+      off_blob.push_back(run);
+      d.drop_list = append(drops);
+    }
+  }
+  if (id_blob.empty()) id_blob.push_back(0);
+  if (step_blob.empty()) step_blob.push_back(0);
+  if (off_blob.empty()) off_blob.push_back(0);
+
   uint32_t* d_thr = static_cast<uint32_t*>(dev_alloc(c, thr_blob.size() * sizeof(uint32_t)));
   uint16_t* d_guide = static_cast<uint16_t*>(dev_alloc(c, guide_blob.size() * sizeof(uint16_t)));
   DevProj* d_proj = static_cast<DevProj*>(dev_alloc(c, std::max<size_t>(1, np) * sizeof(DevProj)));
   S.d_err = static_cast<uint32_t*>(dev_alloc(c, 8 * sizeof(uint64_t)));
   S.d_n_groups = static_cast<uint64_t*>(dev_alloc(c, sizeof(uint64_t)));
-  if (!d_thr || !d_guide || !d_proj || !S.d_err || !S.d_n_groups)
+  uint32_t* d_ids = static_cast<uint32_t*>(dev_alloc(c, id_blob.size() * sizeof(uint32_t)));
+  uint16_t* d_steps = static_cast<uint16_t*>(dev_alloc(c, step_blob.size() * sizeof(uint16_t)));
+  uint64_t* d_offs = static_cast<uint64_t*>(dev_alloc(c, off_blob.size() * sizeof(uint64_t)));
+  if (!d_thr || !d_guide || !d_proj || !S.d_err || !S.d_n_groups || !d_ids || !d_steps || !d_offs)
     return fail(c, SNC_ERR_OOM, "device allocation failed (tables)");
   SNC_CUDA(c, upload(c, d_thr, thr_blob.data(), thr_blob.size() * sizeof(uint32_t)));
   SNC_CUDA(c, upload(c, d_guide, guide_blob.data(), guide_blob.size() * sizeof(uint16_t)));
+  SNC_CUDA(c, upload(c, d_ids, id_blob.data(), id_blob.size() * sizeof(uint32_t)));
+  SNC_CUDA(c, upload(c, d_steps, step_blob.data(), step_blob.size() * sizeof(uint16_t)));
+  SNC_CUDA(c, upload(c, d_offs, off_blob.data(), off_blob.size() * sizeof(uint64_t)));
+  const ArrayBlobs arrays{d_ids, d_steps, d_offs};
   SNC_CUDA(c, cudaMemsetAsync(S.d_err, 0, 8 * sizeof(uint64_t), st));
   SNC_CUDA(c, cudaMemsetAsync(S.d_n_groups, 0, sizeof(uint64_t), st));
 
@@ -695,7 +858,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     SNC_CUDA(c, upload(c, d_bprefix, bern_prefix.data(), bern_prefix.size() * sizeof(uint64_t)));
     const unsigned cgrid =
         static_cast<unsigned>(std::max<uint64_t>(1, std::min<uint64_t>((n_targets + 255) / 256, c->sms * 16ull)));
-    bernoulli_count_kernel<<<cgrid, 256, 0, st>>>(d_proj, d_blist, d_bprefix, nb, d_thr, d_guide, d_counts);
+    bernoulli_count_kernel<<<cgrid, 256, 0, st>>>(d_proj, d_blist, d_bprefix, nb, d_thr, d_guide, arrays, d_counts);
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
     SNC_CUDA(c, exclusive_scan_u32(d_counts, n_targets, d_prim_off, d_scan_tmp, st));
@@ -793,6 +956,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
                    c->layout.delay_bits <= kSrcMajorMaxDelayBits && per_source >= 64 &&
                    per_source <= 2 * static_cast<uint64_t>(kSrcMajorChunk);
   for (size_t i = 0; i < np && src_major; ++i) src_major = source_major_rule(dp[i].rule);
+  if (any_lists) src_major = false;  // sources of a list are not generated in node order
   if (segmented) {
     for (int m = 0; m < n_members; ++m)
       if (seg_end[m] - seg_begin[m] >= (1ull << 30))
@@ -833,8 +997,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // (a segmented sort counts per segment itself).
   const SortScratch sort_lay = segmented ? sort_scratch_layout(sort_scratch, n, c->passes, n_seg_tiles, n_members)
                                          : sort_scratch_layout(sort_scratch, n, c->passes);
-  // (A target shard counts the digits of the kept connections in the sort.)
-  const bool gen_counts = !segmented && !src_major && !sharded;
+  // (A target shard that filters counts the digits of the kept connections
+  // in the sort.)
+  const bool gen_counts = !segmented && !src_major && !shard_filter;
   if (gen_counts)
     SNC_CUDA(c, cudaMemsetAsync(sort_lay.hist, 0,
                                 static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long), st));
@@ -856,6 +1021,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   g.cap = n;
   g.err = S.d_err;
   g.hist = hplan;
+  g.arr = arrays;
   const size_t table_smem =
       hist_bytes + static_cast<size_t>(max_delay_len) * sizeof(uint32_t) + kDelayGuide * sizeof(uint16_t) + 16;
   if (chunk > 0) {
@@ -1008,6 +1174,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     if (!rps.empty()) {
       RedrawArgs a{};
       a.projs = d_proj;
+      a.arr = arrays;
       a.n = static_cast<int>(rps.size());
       a.n_slots = n_slots;
       a.err = S.d_err;
@@ -1146,11 +1313,16 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     }
   }
   mark();
+  // The array blobs are read by generation only.
+  dev_free(c, d_ids);
+  dev_free(c, d_steps);
+  dev_free(c, d_offs);
 
-  // Target shard: keep the connections whose target is in the shard, in
-  // generation order (so the stable sort below gives the full network's
-  // order restricted to them), compacted into the second buffer pair.
-  if (sharded && n > 0) {
+  // Target shard with fixed_outdegree or fixed_total_number projections:
+  // keep the connections whose target is in the shard, in generation order
+  // (so the stable sort below gives the full network's order restricted to
+  // them), compacted into the second buffer pair.
+  if (shard_filter && n > 0) {
     uint32_t* flags = static_cast<uint32_t*>(dev_alloc(c, (n + 1) * sizeof(uint32_t)));
     uint64_t* offs = static_cast<uint64_t*>(dev_alloc(c, (n + 1) * sizeof(uint64_t)));
     uint64_t* tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n) + 1) * sizeof(uint64_t)));
@@ -1255,11 +1427,11 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   } else if (key32)
     SNC_CUDA(c, radix_sort_run(static_cast<const uint32_t*>(keys_a), vals_a, static_cast<uint32_t*>(keys_res), vals_res,
                                static_cast<uint32_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/!sharded, &unpack, &fused, seg_arg));
+                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/!shard_filter, &unpack, &fused, seg_arg));
   else
     SNC_CUDA(c, radix_sort_run(static_cast<const uint64_t*>(keys_a), vals_a, static_cast<uint64_t*>(keys_res), vals_res,
                                static_cast<uint64_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
-                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/!sharded, &unpack, &fused, seg_arg));
+                               S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/!shard_filter, &unpack, &fused, seg_arg));
   if (!src_major) {
     if (!S.capturing) S.n_ev += c->passes.n_passes + 1;
     if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;

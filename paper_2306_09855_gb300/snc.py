@@ -51,6 +51,11 @@ class snc_syn_spec(ctypes.Structure):
     _fields_ = [("weight", snc_dist), ("delay_ms", snc_dist)]
 
 
+class snc_conn_arrays(ctypes.Structure):
+    _fields_ = [("src_ids", ctypes.c_void_p), ("tgt_ids", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("delays_ms", ctypes.c_void_p), ("n_conn", ctypes.c_uint64)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -108,7 +113,8 @@ class snc_server_stats(ctypes.Structure):
 SNC_JOB_QUEUED, SNC_JOB_RUNNING, SNC_JOB_DONE, SNC_JOB_FAILED = range(4)
 
 # Every symbol include/snc.h and include/snc_server.h declare.
-EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_finalize",
+EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_connect_arrays",
+           "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_copy_index",
            "snc_deliver", "snc_set_target_shard", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
@@ -137,6 +143,9 @@ def load(build: bool = True):
         "snc_create_population": ([P, U32, ctypes.POINTER(U32)], I32),
         "snc_connect": ([P, snc_range, snc_range, ctypes.POINTER(snc_conn_rule),
                          ctypes.POINTER(snc_syn_spec), ctypes.POINTER(U32)], I32),
+        "snc_connect_arrays": ([P, snc_range, snc_range, ctypes.POINTER(snc_conn_rule),
+                                ctypes.POINTER(snc_syn_spec), ctypes.POINTER(snc_conn_arrays), ctypes.POINTER(U32)],
+                               I32),
         "snc_finalize": ([P], I32),
         "snc_batch_finalize": ([ctypes.POINTER(P), I32], I32),
         "snc_batch_finalize_graph": ([ctypes.POINTER(P), I32], I32),
@@ -204,6 +213,32 @@ def snc_connect(ctx, src, tgt, rule, syn):
     pid = ctypes.c_uint32()
     _check(load().snc_connect(ctx, src, tgt, ctypes.byref(rule), ctypes.byref(syn),
                               ctypes.byref(pid)), ctx)
+    return pid.value
+
+
+def snc_connect_arrays(ctx, src, tgt, rule, syn, src_ids=None, tgt_ids=None, weights=None, delays_ms=None):
+    """Connect with explicit node-id arrays and/or per-connection weight and
+    delay arrays (host numpy arrays, copied by the library)."""
+    keep = []
+
+    def ptr(a, dt):
+        if a is None:
+            return None, 0
+        a = np.ascontiguousarray(a, dtype=dt).ravel()
+        buf = a if a.size else np.zeros(1, dt)
+        keep.append(buf)
+        return buf.ctypes.data, a.size
+
+    sp, _ = ptr(src_ids, np.uint32)
+    tp, _ = ptr(tgt_ids, np.uint32)
+    wp, nw = ptr(weights, np.float32)
+    dp, nd = ptr(delays_ms, np.float32)
+    if wp is not None and dp is not None and nw != nd:
+        raise ValueError("weights and delays of different lengths")
+    arr = snc_conn_arrays(sp, tp, wp, dp, nw if wp is not None else nd)
+    pid = ctypes.c_uint32()
+    _check(load().snc_connect_arrays(ctx, src, tgt, ctypes.byref(rule), ctypes.byref(syn), ctypes.byref(arr),
+                                     ctypes.byref(pid)), ctx)
     return pid.value
 
 
@@ -441,19 +476,17 @@ def _syn_struct(pj):
                                           float(pj.delay.std)))
 
 
-def _ranges_only(spec):
-    """The library's Connect takes node ranges and weight/delay
-    distributions; explicit id arrays and per-connection arrays are refused
-    here rather than dropped."""
-    for i, pj in enumerate(spec.projections):
-        if getattr(pj, "has_arrays", False):
-            raise ValueError("projection %d: explicit id or per-connection arrays are not "
-                             "supported by snc_connect" % i)
+def _connect(ctx, pj):
+    """snc_connect, or snc_connect_arrays for a projection with explicit
+    node-id or per-connection arrays."""
+    if getattr(pj, "has_arrays", False):
+        return snc_connect_arrays(ctx, snc_range(*pj.src), snc_range(*pj.tgt), _rule_struct(pj), _syn_struct(pj),
+                                  src_ids=pj.src_ids, tgt_ids=pj.tgt_ids, weights=pj.weights, delays_ms=pj.delays)
+    return snc_connect(ctx, snc_range(*pj.src), snc_range(*pj.tgt), _rule_struct(pj), _syn_struct(pj))
 
 
 def create_context(spec, device=0, stream_ptr=None, allocator=None):
     """snc_create + CreatePopulation + Connect calls of a NetworkSpec (no finalize)."""
-    _ranges_only(spec)
     cfg = snc_config(seed=int(spec.seed) & 0xFFFFFFFFFFFFFFFF, dt_ms=float(spec.dt),
                      device=device, reserved=0, stream=stream_ptr,
                      allocator=ctypes.pointer(allocator) if allocator is not None else None)
@@ -462,7 +495,7 @@ def create_context(spec, device=0, stream_ptr=None, allocator=None):
         for n in spec.populations:
             snc_create_population(ctx, int(n))
         for pj in spec.projections:
-            snc_connect(ctx, snc_range(*pj.src), snc_range(*pj.tgt), _rule_struct(pj), _syn_struct(pj))
+            _connect(ctx, pj)
     except Exception:
         snc_destroy(ctx)
         raise
@@ -535,7 +568,6 @@ class Network:
 
     def __init__(self, spec, device=0, stream=None, allocator="torch", target_shard=None):
         import torch
-        _ranges_only(spec)
         self.spec = spec
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
@@ -548,8 +580,7 @@ class Network:
         for n in spec.populations:
             snc_create_population(self.ctx, int(n))
         for pj in spec.projections:
-            snc_connect(self.ctx, snc_range(*pj.src), snc_range(*pj.tgt), _rule_struct(pj),
-                        _syn_struct(pj))
+            _connect(self.ctx, pj)
         if target_shard is not None:  # (first, n): keep the connections onto these targets
             snc_set_target_shard(self.ctx, *target_shard)
 

@@ -317,13 +317,3 @@ def test_marshalling_checks_lengths(oracle_mod):
                     tgt_ids=np.arange(2, dtype=np.uint32))
     with pytest.raises(ValueError):
         oracle_mod.generate(net(10, [pj]))
-
-
-def test_library_binding_refuses_arrays():
-    """snc_connect takes ranges and distributions: the binding refuses a
-    specification with arrays instead of dropping them."""
-    from paper_2306_09855_gb300 import snc
-    pj = Projection(src=(0, 3), tgt=(0, 3), rule="one_to_one", src_ids=np.arange(3, dtype=np.uint32),
-                    tgt_ids=np.arange(3, dtype=np.uint32))
-    with pytest.raises(ValueError):
-        snc.create_context(net(10, [pj]))
