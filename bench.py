@@ -44,6 +44,8 @@ def parse_args():
                              "profile_sampler", "profile_bernoulli", "profile_outdegree", "batched", "served",
                              "trials", "deliver", "profile_deliver"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="rule sweep only: skip the microcircuit, batched and served lines")
     ap.add_argument("--sort-digit-bits", type=int, default=None, help="tuning: widest radix digit")
     ap.add_argument("--sort-group-tiles", type=int, default=None, help="tuning: tiles per look-back unit")
     ap.add_argument("--sort-items", type=int, default=None, help="tuning: keys per thread of the bulk-copy pass")
@@ -175,17 +177,55 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def host_info():
+    """nproc, CPU model and machine of the host the oracle runs on."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
 def cpu_baseline(sample_syn_target=1e7):
-    """The oracle (as it stands) on a bounded sample of the workload."""
+    """The oracle (as it stands) on a bounded sample of the workload, on one
+    core and on every core (its OpenMP form, pinned equal to the
+    single-thread oracle)."""
     import oracle
     from paper_2306_09855_gb300 import workloads as W
     spec = W.rule_sweep("fixed_indegree", True, scale=0.05)  # 2 x 5,000 nodes, K = 1,000: 2e7
     t0 = time.perf_counter()
     out = oracle.build(spec)
     dt = time.perf_counter() - t0
-    return {"value": out["src"].size / dt, "unit": "connections/s", "cores": 1, "kind": "oracle",
+    n = out["src"].size
+    del out
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    par = oracle.build_parallel(spec, threads)
+    dt_par = time.perf_counter() - t0
+    assert par["src"].size == n
+    del par
+    return {"value": n / dt, "unit": "connections/s", "cores": 1, "kind": "oracle",
             "sample": "fixed_indegree K=1000 on 2 x 5,000 nodes (%d connections), single-threaded C "
-                      "oracle: generate + stable sort + index, %.1f s" % (out["src"].size, dt)}
+                      "oracle: generate + stable sort + index, %.1f s" % (n, dt),
+            "omp": {"value": n / dt_par, "unit": "connections/s", "cores": threads, "seconds": dt_par,
+                    "note": "the same oracle on every host thread (OpenMP: primary nodes and the merge sort "
+                            "in parallel; pinned equal to the single-thread oracle)"},
+            "host": host_info()}
 
 
 def run_reference(args):
@@ -270,17 +310,18 @@ def _serve(snc, srv, specs, arrivals, hold_s):
     return last - t0, done, srv.stats(), io
 
 
-def run_served(args):
+def run_served(args, count=2000):
     """Served form: a Poisson stream of 2,000 construction requests (sizes
     log-uniform 1e5-5e8, rule uniform over the six, multapses on or off),
-    admitted under a 150 GB budget, results resident until released."""
+    admitted under a 150 GB budget, results resident until released.
+    Returns the JSON line."""
     import torch
     from paper_2306_09855_gb300 import snc
     from paper_2306_09855_gb300 import workloads as W
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     snc.load()
-    stream_specs = W.served_stream(2000)
+    stream_specs = W.served_stream(count)
     specs = [sp for _, sp in stream_specs]
     offsets = [t for t, _ in stream_specs]
     budget = 150 * 10**9
@@ -327,7 +368,7 @@ def run_served(args):
         "steps": 1, "warmup": max(3, args.warmup), "ms_per_step": wall * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32",
         "data": "synthetic",
-        "config": {"workload": "served: 2,000 two-population construction requests, Poisson arrivals, "
+        "config": {"workload": "served: %d two-population construction requests, Poisson arrivals, " % count +
                                "sizes log-uniform 1e5-5e8 connections, rule uniform over the six, "
                                "multapses on/off, 150 GB budget, networks held 0.5 s after completion",
                    "seed": 1234, "arrival_rate_per_s": rate, "plain_capacity_req_per_s": capacity,
@@ -340,12 +381,12 @@ def run_served(args):
         "server": {"builds": int(st.builds), "batched_builds": int(st.batched_builds),
                    "peak_reserved_bytes": int(st.peak_reserved_bytes)},
         "saturated": {"value": sum(r[0] for r in sat_recs) / sat_wall, "unit": "connections/s",
-                      "note": "all 2,000 requests submitted at once, released on completion",
+                      "note": "all %d requests submitted at once, released on completion" % count,
                       "latency_ms": {"p50": _percentile(sat_lat, 50), "p99": _percentile(sat_lat, 99)},
                       "builds": int(sat_st.builds) - int(st.builds),
                       "batched_builds": int(sat_st.batched_builds) - int(st.batched_builds)},
         "plain_sequential": {"value": n_plain / t_plain, "unit": "connections/s",
-                             "note": "the same 2,000 requests built one after another with snc_finalize"},
+                             "note": "the same %d requests built one after another with snc_finalize" % count},
         "roofline": None,
         "gpu_launches": None,
         "e2e": {"value": n_total / wall, "unit": "connections/s", "h2d_bytes_per_step": io["h2d"],
@@ -353,7 +394,7 @@ def run_served(args):
                 "note": "the served stream through the public API; networks stay on the device"},
         "clocks": clk,
     }
-    print(json.dumps(line))
+    return line
 
 
 def run_trials(args):
@@ -513,13 +554,117 @@ def run_deliver(args):
     print(json.dumps(line))
 
 
+def _digest(torch, net):
+    """Position-weighted sums of a built network's device arrays (equal
+    networks give equal digests; int64 sums wrap deterministically)."""
+    t = net.tensors()
+    out = [int(t["target"].numel()), int(t["group_first"].numel())]
+    for name in ("target", "delay", "weight", "row_ptr", "group_ptr", "group_first"):
+        x = t[name]
+        if x.numel() == 0:
+            out.append(0)
+            continue
+        x = x.view(torch.int32) if x.dtype == torch.float32 else x
+        x = x.to(torch.int64) & (0xFFFF if name == "delay" else -1)
+        w = torch.arange(x.numel(), device=x.device, dtype=torch.int64) % 65521 + 1
+        out.append(int((x * w).sum()))
+    return tuple(out)
+
+
+def _device_ms(torch, stream, fn):
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    r = fn()
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end), r
+
+
+def extra_microcircuit(torch, snc, local, stream, steps=5, warm=3):
+    """The microcircuit-shaped network (3.0e8 connections, 64
+    fixed_total_number calls): device-timed builds, as the main line."""
+    from paper_2306_09855_gb300 import workloads as W
+    spec = W.microcircuit()
+
+    def build():
+        net = snc.Network(spec, device=local, stream=stream).finalize()
+        n = int(net.view().n_syn)
+        net.close()
+        return n
+
+    for _ in range(warm):
+        build()
+    ms, n = _device_ms(torch, stream, lambda: sum(build() for _ in range(steps)))
+    return {"value": n / (ms / 1e3), "unit": "connections/s", "ms_per_build": ms / steps,
+            "connections": n // steps, "steps": steps, "warmup": warm,
+            "workload": "microcircuit-shaped: 8 populations, 77,169 nodes, 64 fixed_total_number calls"}
+
+
+def extra_batched(torch, snc, local, stream, steps=3, warm=2):
+    """64 networks of uneven size built by one snc_batch_finalize against the
+    same 64 built one after another with snc_finalize (device time), with
+    every member's arrays compared between the two (digests)."""
+    from paper_2306_09855_gb300 import autotune
+    from paper_2306_09855_gb300 import workloads as W
+    specs = W.batched_sweep(64)
+    saved = snc.snc_get_tuning()
+    try:
+        tune_info = autotune.tune(specs, batched=True)
+
+        def batched():
+            nets = snc.Network.batch(specs, device=local, stream=stream)
+            n = sum(int(x.view().n_syn) for x in nets)
+            return nets, n
+
+        def sequential():
+            nets = [snc.Network(sp, device=local, stream=stream).finalize() for sp in specs]
+            n = sum(int(x.view().n_syn) for x in nets)
+            return nets, n
+
+        def timed(fn):
+            for _ in range(warm):
+                nets, _ = fn()
+                for x in reversed(nets):
+                    x.close()
+            total_ms, total_n = 0.0, 0
+            for _ in range(steps):
+                ms, (nets, n) = _device_ms(torch, stream, fn)
+                total_ms += ms
+                total_n += n
+                for x in reversed(nets):
+                    x.close()
+            return total_n / (total_ms / 1e3), total_ms / steps, total_n // steps
+
+        v_b, ms_b, n_b = timed(batched)
+        v_s, ms_s, n_s = timed(sequential)
+        nets_b, _ = batched()
+        dig_b = [_digest(torch, x) for x in nets_b]
+        for x in reversed(nets_b):
+            x.close()
+        nets_s, _ = sequential()
+        dig_s = [_digest(torch, x) for x in nets_s]
+        for x in reversed(nets_s):
+            x.close()
+    finally:
+        snc.snc_set_tuning(sort_digit_bits=saved.sort_digit_bits, sort_group_tiles=saved.sort_group_tiles,
+                           gen_blocks_per_sm=saved.gen_blocks_per_sm, sort_items=saved.sort_items)
+    return {"value": v_b, "unit": "connections/s", "ms_per_build": ms_b, "connections": n_b,
+            "sequential_builds": {"value": v_s, "unit": "connections/s", "ms": ms_s, "connections": n_s},
+            "speedup": v_b / v_s, "identical": dig_b == dig_s and n_b == n_s,
+            "tuning": tune_info["tuning"], "tuning_cached": tune_info["cached"],
+            "workload": "64 two-population networks, N log-uniform 2,000-50,000, fixed_indegree / "
+                        "fixed_total_number / pairwise_bernoulli, per-instance seeds"}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.workload == "served":
-        run_served(args)
+        print(json.dumps(run_served(args)))
         return
     if args.workload == "trials":
         run_trials(args)
@@ -751,6 +896,22 @@ def main():
     if batched:
         line["sequential_builds"] = sequential
         line["autotune"] = {"tuning": tune_info["tuning"], "cached": tune_info["cached"], "key": tune_info["key"]}
+    if args.workload == "rule_sweep" and world == 1 and not args.no_extras:
+        # The paper's other model, the batched form and the served form on
+        # the same GPU, beside the rule sweep (each reported on its own).
+        for key, fn in (("microcircuit", lambda: extra_microcircuit(torch, snc, local, stream)),
+                        ("batched", lambda: extra_batched(torch, snc, local, stream)),
+                        ("served", lambda: run_served(args))):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # reported in the line, the rule sweep stands
+                line[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+            torch.cuda.empty_cache()
+        sv = line.get("served")
+        if isinstance(sv, dict) and "latency_ms" in sv:
+            line["served"] = {k: sv[k] for k in ("value", "unit", "latency_ms", "saturated", "plain_sequential",
+                                                 "server", "config", "clocks") if k in sv}
+            line["latency_ms"] = sv["latency_ms"]
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -55,33 +55,49 @@ __device__ __forceinline__ uint32_t weight_bits(const DevProj& P, uint32_t w2, u
   return __float_as_uint(w);
 }
 
+// Whether a projection record carries explicit arrays (Sec. 2.1); the
+// kernels run their array-free instance for the others (ARR = false), which
+// reads none of the list fields.
+__device__ __forceinline__ bool has_arrays(const DevProj& P) {
+  return P.src_list != kNoList || P.tgt_list != kNoList || P.w_list != kNoList || P.d_list != kNoList;
+}
+
 // Node (build id) at position pos of the projection's source / target list:
 // the range, or the explicit ids of the Connect call (Sec. 2.1).
+template <bool ARR>
 __device__ __forceinline__ uint32_t src_node(const DevProj& P, const ArrayBlobs& A, uint32_t pos) {
-  return P.src_list == kNoList ? P.s0 + pos : P.t_base + A.ids[P.src_list + pos];
+  if constexpr (ARR) return P.src_list == kNoList ? P.s0 + pos : P.t_base + A.ids[P.src_list + pos];
+  return P.s0 + pos;
 }
+template <bool ARR>
 __device__ __forceinline__ uint32_t tgt_node(const DevProj& P, const ArrayBlobs& A, uint32_t pos) {
-  return P.tgt_list == kNoList ? P.t0 + pos : P.t_base + A.ids[P.tgt_list + pos];
+  if constexpr (ARR) return P.tgt_list == kNoList ? P.t0 + pos : P.t_base + A.ids[P.tgt_list + pos];
+  return P.t0 + pos;
 }
 
 // Delay step and weight bits of connection number inew of the rule's own
 // numbering: given per connection (Sec. 2.1), or drawn from the slot's WD
 // words (which are drawn either way).
+template <bool ARR>
 __device__ __forceinline__ uint32_t conn_delay(const DevProj& P, const ArrayBlobs& A, const SmemTables& t,
                                                uint64_t inew, uint32_t u) {
-  return P.d_list == kNoList ? delay_step(P, t, u) : A.steps[P.d_list + inew];
+  if constexpr (ARR) return P.d_list == kNoList ? delay_step(P, t, u) : A.steps[P.d_list + inew];
+  return delay_step(P, t, u);
 }
+template <bool ARR>
 __device__ __forceinline__ uint32_t conn_weight(const DevProj& P, const ArrayBlobs& A, uint64_t inew, uint32_t w2,
                                                 uint32_t w3) {
-  return P.w_list == kNoList ? weight_bits(P, w2, w3) : A.ids[P.w_list + inew];
+  if constexpr (ARR) return P.w_list == kNoList ? weight_bits(P, w2, w3) : A.ids[P.w_list + inew];
+  return weight_bits(P, w2, w3);
 }
 
 // Per-primary rules without autapses: whether primary b (build id `node`)
 // appears in the list drawn from, and at which position *q.
+template <bool ARR>
 __device__ __forceinline__ bool self_in_other(const DevProj& P, const ArrayBlobs& A, uint32_t b, uint32_t node,
                                               uint32_t first_other, uint32_t n_other, uint32_t* q) {
   if (P.autapses) return false;
-  if (P.self_list != kNoList) {
+  if (ARR && P.self_list != kNoList) {
     const uint32_t v = A.ids[P.self_list + b];
     *q = v;
     return v != kNoPosition;
@@ -139,6 +155,136 @@ __device__ __forceinline__ void store(const GenArgs& a, const BlockHist& h, uint
 
 }  // namespace
 
+namespace {
+// One chunk of a direct rule (ARR: the projection carries explicit arrays).
+template <bool ARR>
+__device__ __forceinline__ void direct_chunk(const GenArgs& a, const BlockHist& bh, const SmemTables& tabs,
+                                             const DevProj& P, uint64_t lc, uint32_t warp, uint32_t lane) {
+  if (P.rule == SNC_ALL_TO_ALL) {
+    // Row a (source s0 + a); targets b' in [part * kChunk, ...).  With
+    // autapses off the diagonal target is skipped and later rows shift.
+    // With explicit lists the dropped target positions of the row come
+    // from the host (ascending).
+    const uint32_t row = static_cast<uint32_t>(lc / P.chunks_per_row);
+    const uint32_t part = static_cast<uint32_t>(lc % P.chunks_per_row);
+    const uint32_t s = src_node<ARR>(P, a.arr, row);
+    uint32_t n_drop = 0, diag_b = 0;
+    uint64_t before = 0;  // dropped pairs in rows < row
+    const uint32_t* drops = nullptr;
+    if (P.row_list != kNoList) {
+      before = a.arr.offs[P.row_list + row];
+      n_drop = static_cast<uint32_t>(a.arr.offs[P.row_list + row + 1] - before);
+      drops = a.arr.ids + P.drop_list + before;
+    } else if (!P.autapses) {
+      if (s >= P.t0 && s - P.t0 < P.nt) {
+        n_drop = 1;
+        diag_b = s - P.t0;
+      }
+      const uint32_t lo = max(P.s0, P.t0), hi = min(P.s0 + P.ns, P.t0 + P.nt);
+      if (hi > lo && s > lo) before = min(s, hi) - lo;
+    }
+    const uint32_t row_len = P.nt - n_drop;
+    const uint64_t row_out = P.out_off + static_cast<uint64_t>(row) * P.nt - before;
+    for (uint32_t e = threadIdx.x; e < kChunk; e += blockDim.x) {
+      const uint32_t bp = part * kChunk + e;
+      if (bp >= row_len) break;
+      uint32_t b = bp;
+      if (drops) {
+        for (uint32_t k = 0; k < n_drop; ++k) {
+          if (drops[k] > b) break;
+          ++b;
+        }
+      } else if (n_drop && bp >= diag_b) {
+        b = bp + 1;
+      }
+      const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, row);
+      const uint64_t inew = static_cast<uint64_t>(row) * P.nt + b;
+      store(a, bh, row_out + bp, s - P.t_base, conn_delay<ARR>(P, a.arr, tabs, inew, W.x),
+            tgt_node<ARR>(P, a.arr, b) - P.t_base, conn_weight<ARR>(P, a.arr, inew, W.z, W.w));
+    }
+    return;
+  }
+  const uint64_t start = lc * kChunk;
+  const uint64_t end = min(start + kChunk, P.count);
+  // Four windows of 128 per warp.
+  for (int win = 0; win < kChunk / (128 * (kGenThreads / 32)); ++win) {
+    const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
+                           static_cast<uint64_t>(win) * 128;
+    if (wbase >= end) break;
+    Words X{0, 0, 0, 0};
+    if (P.rule == SNC_FIXED_TOTAL_NUMBER) X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
+      uint32_t tw = 0;
+      if (P.rule == SNC_FIXED_TOTAL_NUMBER) {
+        const int src_lane = 8 * q + static_cast<int>(lane >> 2);
+        const uint32_t vx = __shfl_sync(0xffffffffu, X.x, src_lane);
+        const uint32_t vy = __shfl_sync(0xffffffffu, X.y, src_lane);
+        const uint32_t vz = __shfl_sync(0xffffffffu, X.z, src_lane);
+        const uint32_t vw = __shfl_sync(0xffffffffu, X.w, src_lane);
+        const uint32_t sel = lane & 3u;
+        tw = sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
+      }
+      if (i >= end) continue;
+      uint32_t s, t, primary;
+      uint64_t slot, inew = i;
+      switch (P.rule) {
+        case SNC_ONE_TO_ONE: {
+          // pair i of the kept pairs (explicit lists without autapses)
+          const uint32_t pos = P.row_list != kNoList ? a.arr.ids[P.row_list + i] : static_cast<uint32_t>(i);
+          s = src_node<ARR>(P, a.arr, pos);
+          t = tgt_node<ARR>(P, a.arr, pos);
+          primary = pos;
+          slot = 0;
+          inew = pos;
+          break;
+        }
+        case SNC_FIXED_INDEGREE:
+        case SNC_FIXED_OUTDEGREE: {
+          uint64_t b, j;
+          if (P.count <= 0xFFFFFFFFull) {
+            const uint32_t ii = static_cast<uint32_t>(i), kk = static_cast<uint32_t>(P.k);
+            b = ii / kk;
+            j = ii - static_cast<uint32_t>(b) * kk;
+          } else {
+            b = i / P.k;
+            j = i - b * P.k;
+          }
+          primary = static_cast<uint32_t>(b);
+          slot = j;
+          s = t = 0;
+          break;
+        }
+        default:  // fixed_total_number
+          primary = kPrimaryNone;
+          slot = i;
+          s = t = 0;
+          break;
+      }
+      const Words W = draw(P.k0, P.k1, kTagWD, 0, primary == kPrimaryNone ? primary : primary + P.prim_shift, slot);
+      if (P.rule == SNC_FIXED_INDEGREE) {
+        t = tgt_node<ARR>(P, a.arr, primary);
+        uint32_t q = 0;
+        const bool skip = self_in_other<ARR>(P, a.arr, primary, t, P.s0, P.ns, &q);
+        s = src_node<ARR>(P, a.arr, endpoint(W.y, P.ns, skip, q));
+      } else if (P.rule == SNC_FIXED_OUTDEGREE) {
+        s = src_node<ARR>(P, a.arr, primary);
+        uint32_t q = 0;
+        const bool skip = self_in_other<ARR>(P, a.arr, primary, s, P.t0, P.nt, &q);
+        t = tgt_node<ARR>(P, a.arr, endpoint(W.y, P.nt, skip, q));
+      } else if (P.rule == SNC_FIXED_TOTAL_NUMBER) {
+        s = src_node<ARR>(P, a.arr, rand_below(W.y, P.ns));
+        t = tgt_node<ARR>(P, a.arr, rand_below(tw, P.nt));
+      }
+      store(a, bh, P.out_off + i, s - P.t_base, conn_delay<ARR>(P, a.arr, tabs, inew, W.x), t - P.t_base,
+            conn_weight<ARR>(P, a.arr, inew, W.z, W.w));
+    }
+  }
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // Direct rules.  A chunk is kChunk consecutive connections of one projection
 // (for all_to_all: kChunk consecutive targets of one source row).  A warp
@@ -164,127 +310,10 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
     }
     const DevProj& P = a.projs[p];
     const uint64_t lc = c - P.chunk_begin;
-    if (P.rule == SNC_ALL_TO_ALL) {
-      // Row a (source s0 + a); targets b' in [part * kChunk, ...).  With
-      // autapses off the diagonal target is skipped and later rows shift.
-      // With explicit lists the dropped target positions of the row come
-      // from the host (ascending).
-      const uint32_t row = static_cast<uint32_t>(lc / P.chunks_per_row);
-      const uint32_t part = static_cast<uint32_t>(lc % P.chunks_per_row);
-      const uint32_t s = src_node(P, a.arr, row);
-      uint32_t n_drop = 0, diag_b = 0;
-      uint64_t before = 0;  // dropped pairs in rows < row
-      const uint32_t* drops = nullptr;
-      if (P.row_list != kNoList) {
-        before = a.arr.offs[P.row_list + row];
-        n_drop = static_cast<uint32_t>(a.arr.offs[P.row_list + row + 1] - before);
-        drops = a.arr.ids + P.drop_list + before;
-      } else if (!P.autapses) {
-        if (s >= P.t0 && s - P.t0 < P.nt) {
-          n_drop = 1;
-          diag_b = s - P.t0;
-        }
-        const uint32_t lo = max(P.s0, P.t0), hi = min(P.s0 + P.ns, P.t0 + P.nt);
-        if (hi > lo && s > lo) before = min(s, hi) - lo;
-      }
-      const uint32_t row_len = P.nt - n_drop;
-      const uint64_t row_out = P.out_off + static_cast<uint64_t>(row) * P.nt - before;
-      for (uint32_t e = threadIdx.x; e < kChunk; e += blockDim.x) {
-        const uint32_t bp = part * kChunk + e;
-        if (bp >= row_len) break;
-        uint32_t b = bp;
-        if (drops) {
-          for (uint32_t k = 0; k < n_drop; ++k) {
-            if (drops[k] > b) break;
-            ++b;
-          }
-        } else if (n_drop && bp >= diag_b) {
-          b = bp + 1;
-        }
-        const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, row);
-        const uint64_t inew = static_cast<uint64_t>(row) * P.nt + b;
-        store(a, bh, row_out + bp, s - P.t_base, conn_delay(P, a.arr, tabs, inew, W.x),
-              tgt_node(P, a.arr, b) - P.t_base, conn_weight(P, a.arr, inew, W.z, W.w));
-      }
-      continue;
-    }
-    const uint64_t start = lc * kChunk;
-    const uint64_t end = min(start + kChunk, P.count);
-    // Four windows of 128 per warp.
-    for (int win = 0; win < kChunk / (128 * (kGenThreads / 32)); ++win) {
-      const uint64_t wbase = start + (static_cast<uint64_t>(warp) * (kChunk / (kGenThreads / 32))) +
-                             static_cast<uint64_t>(win) * 128;
-      if (wbase >= end) break;
-      Words X{0, 0, 0, 0};
-      if (P.rule == SNC_FIXED_TOTAL_NUMBER) X = draw(P.k0, P.k1, kTagIdx, 0, kPrimaryNone, (wbase >> 2) + lane);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint64_t i = wbase + static_cast<uint64_t>(q) * 32 + lane;
-        uint32_t tw = 0;
-        if (P.rule == SNC_FIXED_TOTAL_NUMBER) {
-          const int src_lane = 8 * q + static_cast<int>(lane >> 2);
-          const uint32_t vx = __shfl_sync(0xffffffffu, X.x, src_lane);
-          const uint32_t vy = __shfl_sync(0xffffffffu, X.y, src_lane);
-          const uint32_t vz = __shfl_sync(0xffffffffu, X.z, src_lane);
-          const uint32_t vw = __shfl_sync(0xffffffffu, X.w, src_lane);
-          const uint32_t sel = lane & 3u;
-          tw = sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
-        }
-        if (i >= end) continue;
-        uint32_t s, t, primary;
-        uint64_t slot, inew = i;
-        switch (P.rule) {
-          case SNC_ONE_TO_ONE: {
-            // pair i of the kept pairs (explicit lists without autapses)
-            const uint32_t pos = P.row_list != kNoList ? a.arr.ids[P.row_list + i] : static_cast<uint32_t>(i);
-            s = src_node(P, a.arr, pos);
-            t = tgt_node(P, a.arr, pos);
-            primary = pos;
-            slot = 0;
-            inew = pos;
-            break;
-          }
-          case SNC_FIXED_INDEGREE:
-          case SNC_FIXED_OUTDEGREE: {
-            uint64_t b, j;
-            if (P.count <= 0xFFFFFFFFull) {
-              const uint32_t ii = static_cast<uint32_t>(i), kk = static_cast<uint32_t>(P.k);
-              b = ii / kk;
-              j = ii - static_cast<uint32_t>(b) * kk;
-            } else {
-              b = i / P.k;
-              j = i - b * P.k;
-            }
-            primary = static_cast<uint32_t>(b);
-            slot = j;
-            s = t = 0;
-            break;
-          }
-          default:  // fixed_total_number
-            primary = kPrimaryNone;
-            slot = i;
-            s = t = 0;
-            break;
-        }
-        const Words W = draw(P.k0, P.k1, kTagWD, 0, primary == kPrimaryNone ? primary : primary + P.prim_shift, slot);
-        if (P.rule == SNC_FIXED_INDEGREE) {
-          t = tgt_node(P, a.arr, primary);
-          uint32_t q = 0;
-          const bool skip = self_in_other(P, a.arr, primary, t, P.s0, P.ns, &q);
-          s = src_node(P, a.arr, endpoint(W.y, P.ns, skip, q));
-        } else if (P.rule == SNC_FIXED_OUTDEGREE) {
-          s = src_node(P, a.arr, primary);
-          uint32_t q = 0;
-          const bool skip = self_in_other(P, a.arr, primary, s, P.t0, P.nt, &q);
-          t = tgt_node(P, a.arr, endpoint(W.y, P.nt, skip, q));
-        } else if (P.rule == SNC_FIXED_TOTAL_NUMBER) {
-          s = src_node(P, a.arr, rand_below(W.y, P.ns));
-          t = tgt_node(P, a.arr, rand_below(tw, P.nt));
-        }
-        store(a, bh, P.out_off + i, s - P.t_base, conn_delay(P, a.arr, tabs, inew, W.x), t - P.t_base,
-              conn_weight(P, a.arr, inew, W.z, W.w));
-      }
-    }
+    if (has_arrays(P))
+      direct_chunk<true>(a, bh, tabs, P, lc, warp, lane);
+    else
+      direct_chunk<false>(a, bh, tabs, P, lc, warp, lane);
   }
   block_hist_end(a, bh);
 }
@@ -313,9 +342,9 @@ __global__ void bernoulli_count_kernel(const DevProj* projs, const uint32_t* lis
     const int j = find_segment(prefix, n_list, g);
     const DevProj& P = projs[list[j]];
     const uint32_t b = static_cast<uint32_t>(g - prefix[j]);
-    const uint32_t node = tgt_node(P, arr, b);
+    const uint32_t node = tgt_node<true>(P, arr, b);
     uint32_t q = 0;
-    const int skip = self_in_other(P, arr, b, node, P.s0, P.ns, &q) ? 1 : 0;
+    const int skip = self_in_other<true>(P, arr, b, node, P.s0, P.ns, &q) ? 1 : 0;
     const Words W = draw(P.k0, P.k1, kTagCount, 0, b + P.prim_shift, 0);
     const uint32_t i = table_lookup(thr_blob + P.b_off[skip], guide_blob + P.b_goff[skip], P.b_len[skip], W.x);
     counts[g] = P.b_base[skip] + i;
@@ -326,6 +355,125 @@ __global__ void segment_totals_kernel(const uint64_t* offsets, const uint64_t* p
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n_list) out[j] = offsets[prefix[j + 1]] - offsets[prefix[j]];
 }
+
+namespace {
+// The connections of primary node b of a sampler projection (one warp).
+template <bool ARR>
+__device__ __forceinline__ void sample_primary(const SamplerArgs& a, const BlockHist& bh, uint32_t* bitmap,
+                                               const SmemTables& tabs, const DevProj& P, uint32_t b,
+                                               uint32_t lane) {
+  const bool indeg = P.rule != SNC_FIXED_OUTDEGREE;  // indegree and Bernoulli pick sources
+  const uint32_t n_other = indeg ? P.ns : P.nt;
+  const uint32_t first_other = indeg ? P.s0 : P.t0;
+  const uint32_t words = (n_other + 31u) >> 5;
+  const ArrayBlobs& A = a.gen.arr;
+  const uint32_t node = indeg ? tgt_node<ARR>(P, A, b) : src_node<ARR>(P, A, b);
+  uint32_t skip_local = 0;
+  const bool skip = self_in_other<ARR>(P, A, b, node, first_other, n_other, &skip_local);
+  const uint32_t cand = n_other - (skip ? 1u : 0u);
+  uint64_t want, out;
+  if (P.rule == SNC_PAIRWISE_BERNOULLI) {
+    out = P.out_off + (a.prim_offsets[P.prim_off + b] - a.prim_offsets[P.prim_off]);
+    want = a.prim_offsets[P.prim_off + b + 1] - a.prim_offsets[P.prim_off + b];
+  } else {
+    want = P.k;
+    out = P.out_off + static_cast<uint64_t>(b) * P.k;
+  }
+  if (want == 0) return;
+  const bool complement = 2 * want > cand;
+  const uint32_t need = static_cast<uint32_t>(complement ? cand - want : want);
+  for (uint32_t w = lane; w < words; w += 32) bitmap[w] = 0u;
+  __syncwarp();
+  uint32_t got = 0;
+  uint64_t call = 0;
+  const uint64_t max_calls = 16ull * cand + 64;  // far above any plausible need
+  while (got < need) {
+    if (call > max_calls) {
+      if (lane == 0) atomicOr(a.err, kErrSamplerBound);
+      break;
+    }
+    // One IDX draw per lane: attempts 4*(call + lane) .. +3.
+    const Words X = draw(P.k0, P.k1, kTagIdx, 0, b + P.prim_shift, call + lane);
+    call += 32;
+#pragma unroll 1
+    for (int q = 0; q < 4 && got < need; ++q) {
+      const int src_lane = 8 * q + static_cast<int>(lane >> 2);
+      const uint32_t vx = __shfl_sync(0xffffffffu, X.x, src_lane);
+      const uint32_t vy = __shfl_sync(0xffffffffu, X.y, src_lane);
+      const uint32_t vz = __shfl_sync(0xffffffffu, X.z, src_lane);
+      const uint32_t vw = __shfl_sync(0xffffffffu, X.w, src_lane);
+      const uint32_t sel = lane & 3u;
+      const uint32_t u = sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
+      const uint32_t r = endpoint(u, n_other, skip, skip_local);
+      const uint32_t bit = 1u << (r & 31u);
+      const bool seen = (bitmap[r >> 5] & bit) != 0u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, r);
+      const bool first = (__ffs(peers) - 1) == static_cast<int>(lane);
+      const bool fresh = !seen && first;
+      const uint32_t fresh_mask = __ballot_sync(0xffffffffu, fresh);
+      const uint32_t rank = __popc(fresh_mask & ((1u << lane) - 1u));
+      const uint32_t room = need - got;
+      const bool take = fresh && rank < room;
+      __syncwarp();
+      if (take) {
+        atomicOr(&bitmap[r >> 5], bit);
+        if (!complement) {
+          const uint32_t j = got + rank;
+          const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, j);
+          const uint32_t other = indeg ? src_node<ARR>(P, A, r) : tgt_node<ARR>(P, A, r);
+          const uint32_t s = indeg ? other : node, t = indeg ? node : other;
+          const uint64_t inew = static_cast<uint64_t>(b + P.prim_shift) * P.k + j;
+          store(a.gen, bh, out + j, s - P.t_base, conn_delay<ARR>(P, A, tabs, inew, W.x), t - P.t_base,
+                conn_weight<ARR>(P, A, inew, W.z, W.w));
+        }
+      }
+      got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
+      __syncwarp();
+    }
+  }
+  if (complement) {
+    // Kept values in ascending order: free bits of the bitmap, minus the
+    // left-out node itself.
+    uint32_t base = 0;
+    for (uint32_t w0 = 0; w0 < words; w0 += 32) {
+      const uint32_t w = w0 + lane;
+      uint32_t free_bits = 0;
+      if (w < words) {
+        free_bits = ~bitmap[w];
+        if (w == words - 1 && (n_other & 31u)) free_bits &= (1u << (n_other & 31u)) - 1u;
+        if (skip && (skip_local >> 5) == w) free_bits &= ~(1u << (skip_local & 31u));
+      }
+      const uint32_t cnt = __popc(free_bits);
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (static_cast<int>(lane) >= o) incl += v;
+      }
+      uint32_t j = base + incl - cnt;
+      while (free_bits) {
+        const uint32_t bitpos = __ffs(free_bits) - 1;
+        free_bits &= free_bits - 1;
+        const uint32_t r = w * 32 + bitpos;
+        if (j < want) {
+          const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, j);
+          const uint32_t other = indeg ? src_node<ARR>(P, A, r) : tgt_node<ARR>(P, A, r);
+          const uint32_t s = indeg ? other : node, t = indeg ? node : other;
+          const uint64_t inew = static_cast<uint64_t>(b + P.prim_shift) * P.k + j;
+          store(a.gen, bh, out + j, s - P.t_base, conn_delay<ARR>(P, A, tabs, inew, W.x), t - P.t_base,
+                conn_weight<ARR>(P, A, inew, W.z, W.w));
+        } else {
+          atomicOr(a.err, kErrBounds);
+        }
+        ++j;
+      }
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+  __syncwarp();
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // Sampling without replacement, one warp per primary node.  Attempt a uses
@@ -366,117 +514,10 @@ __global__ void sampler_kernel(SamplerArgs a) {
       cur = j;
     }
     const uint32_t b = static_cast<uint32_t>(gp - a.prim_prefix[j]);
-    const bool indeg = P.rule != SNC_FIXED_OUTDEGREE;  // indegree and Bernoulli pick sources
-    const uint32_t n_other = indeg ? P.ns : P.nt;
-    const uint32_t first_other = indeg ? P.s0 : P.t0;
-    const uint32_t words = (n_other + 31u) >> 5;
-  {
-    const ArrayBlobs& A = a.gen.arr;
-    const uint32_t node = indeg ? tgt_node(P, A, b) : src_node(P, A, b);
-    uint32_t skip_local = 0;
-    const bool skip = self_in_other(P, A, b, node, first_other, n_other, &skip_local);
-    const uint32_t cand = n_other - (skip ? 1u : 0u);
-    uint64_t want, out;
-    if (P.rule == SNC_PAIRWISE_BERNOULLI) {
-      out = P.out_off + (a.prim_offsets[P.prim_off + b] - a.prim_offsets[P.prim_off]);
-      want = a.prim_offsets[P.prim_off + b + 1] - a.prim_offsets[P.prim_off + b];
-    } else {
-      want = P.k;
-      out = P.out_off + static_cast<uint64_t>(b) * P.k;
-    }
-    if (want == 0) continue;
-    const bool complement = 2 * want > cand;
-    const uint32_t need = static_cast<uint32_t>(complement ? cand - want : want);
-    for (uint32_t w = lane; w < words; w += 32) bitmap[w] = 0u;
-    __syncwarp();
-    uint32_t got = 0;
-    uint64_t call = 0;
-    const uint64_t max_calls = 16ull * cand + 64;  // far above any plausible need
-    while (got < need) {
-      if (call > max_calls) {
-        if (lane == 0) atomicOr(a.err, kErrSamplerBound);
-        break;
-      }
-      // One IDX draw per lane: attempts 4*(call + lane) .. +3.
-      const Words X = draw(P.k0, P.k1, kTagIdx, 0, b + P.prim_shift, call + lane);
-      call += 32;
-#pragma unroll 1
-      for (int q = 0; q < 4 && got < need; ++q) {
-        const int src_lane = 8 * q + static_cast<int>(lane >> 2);
-        const uint32_t vx = __shfl_sync(0xffffffffu, X.x, src_lane);
-        const uint32_t vy = __shfl_sync(0xffffffffu, X.y, src_lane);
-        const uint32_t vz = __shfl_sync(0xffffffffu, X.z, src_lane);
-        const uint32_t vw = __shfl_sync(0xffffffffu, X.w, src_lane);
-        const uint32_t sel = lane & 3u;
-        const uint32_t u = sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
-        const uint32_t r = endpoint(u, n_other, skip, skip_local);
-        const uint32_t bit = 1u << (r & 31u);
-        const bool seen = (bitmap[r >> 5] & bit) != 0u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, r);
-        const bool first = (__ffs(peers) - 1) == static_cast<int>(lane);
-        const bool fresh = !seen && first;
-        const uint32_t fresh_mask = __ballot_sync(0xffffffffu, fresh);
-        const uint32_t rank = __popc(fresh_mask & ((1u << lane) - 1u));
-        const uint32_t room = need - got;
-        const bool take = fresh && rank < room;
-        __syncwarp();
-        if (take) {
-          atomicOr(&bitmap[r >> 5], bit);
-          if (!complement) {
-            const uint32_t j = got + rank;
-            const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, j);
-            const uint32_t other = indeg ? src_node(P, A, r) : tgt_node(P, A, r);
-            const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            const uint64_t inew = static_cast<uint64_t>(b + P.prim_shift) * P.k + j;
-            store(a.gen, bh, out + j, s - P.t_base, conn_delay(P, A, tabs, inew, W.x), t - P.t_base,
-                  conn_weight(P, A, inew, W.z, W.w));
-          }
-        }
-        got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
-        __syncwarp();
-      }
-    }
-    if (complement) {
-      // Kept values in ascending order: free bits of the bitmap, minus the
-      // left-out node itself.
-      uint32_t base = 0;
-      for (uint32_t w0 = 0; w0 < words; w0 += 32) {
-        const uint32_t w = w0 + lane;
-        uint32_t free_bits = 0;
-        if (w < words) {
-          free_bits = ~bitmap[w];
-          if (w == words - 1 && (n_other & 31u)) free_bits &= (1u << (n_other & 31u)) - 1u;
-          if (skip && (skip_local >> 5) == w) free_bits &= ~(1u << (skip_local & 31u));
-        }
-        const uint32_t cnt = __popc(free_bits);
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (static_cast<int>(lane) >= o) incl += v;
-        }
-        uint32_t j = base + incl - cnt;
-        while (free_bits) {
-          const uint32_t bitpos = __ffs(free_bits) - 1;
-          free_bits &= free_bits - 1;
-          const uint32_t r = w * 32 + bitpos;
-          if (j < want) {
-            const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, j);
-            const uint32_t other = indeg ? src_node(P, A, r) : tgt_node(P, A, r);
-            const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-            const uint64_t inew = static_cast<uint64_t>(b + P.prim_shift) * P.k + j;
-            store(a.gen, bh, out + j, s - P.t_base, conn_delay(P, A, tabs, inew, W.x), t - P.t_base,
-                  conn_weight(P, A, inew, W.z, W.w));
-          } else {
-            atomicOr(a.err, kErrBounds);
-          }
-          ++j;
-        }
-        base += __shfl_sync(0xffffffffu, incl, 31);
-      }
-    }
-    __syncwarp();
-  }
+    if (has_arrays(P))
+      sample_primary<true>(a, bh, bitmap, tabs, P, b, lane);
+    else
+      sample_primary<false>(a, bh, bitmap, tabs, P, b, lane);
   }
   block_hist_end(a.gen, bh);
 }
@@ -520,7 +561,7 @@ __device__ __forceinline__ uint64_t pair_hash(uint64_t key) {
 __device__ __forceinline__ bool allowed_pair(const DevProj& P, const ArrayBlobs& A, uint32_t s, uint32_t t) {
   if (P.autapses) return true;
   if (P.src_list == kNoList && P.tgt_list == kNoList) return s != t;
-  return src_node(P, A, s - P.s0) != tgt_node(P, A, t - P.t0);
+  return src_node<true>(P, A, s - P.s0) != tgt_node<true>(P, A, t - P.t0);
 }
 
 // The slot g of the concatenated list: its projection and local slot.
@@ -814,6 +855,7 @@ __global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, Red
       cur = lo;
     }
     const bool part = !P.multapses;  // uniform over the block
+    const bool arr = has_arrays(P);   // uniform over the block
     const uint32_t n_sup = part ? (1u << r.super_bits) : 0u;
     const int fine_shift = r.bucket_bits - r.super_bits;
     const uint64_t lc = c - r.chunk_base;
@@ -842,8 +884,13 @@ __global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, Red
           const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
           const uint32_t ps = rand_below(W.y, P.ns), pt = rand_below(tw, P.nt);
           const uint32_t s = P.s0 + ps, t = P.t0 + pt;
-          store(g, bh, P.out_off + i, src_node(P, g.arr, ps) - P.t_base, conn_delay(P, g.arr, tabs, i, W.x),
-                tgt_node(P, g.arr, pt) - P.t_base, conn_weight(P, g.arr, i, W.z, W.w));
+          if (arr)
+            store(g, bh, P.out_off + i, src_node<true>(P, g.arr, ps) - P.t_base,
+                  conn_delay<true>(P, g.arr, tabs, i, W.x), tgt_node<true>(P, g.arr, pt) - P.t_base,
+                  conn_weight<true>(P, g.arr, i, W.z, W.w));
+          else
+            store(g, bh, P.out_off + i, s - P.t_base, delay_step(P, tabs, W.x), t - P.t_base,
+                  weight_bits(P, W.z, W.w));
           if (!allowed_pair(P, a.arr, s, t)) {
             push_pending(a, r.slot_base + i);
           } else if (part) {
@@ -941,8 +988,8 @@ __global__ void redraw_patch_kernel(GenArgs g, RedrawArgs a) {
       const uint64_t pos = P.out_off + x.i;
       if (!SNC_IN_BOUNDS(a.err, 2u, pos, g.cap)) continue;
       const uint64_t pair = a.pairs[gs];
-      const uint32_t s = src_node(P, g.arr, static_cast<uint32_t>(pair >> 32) - P.s0);
-      const uint32_t t = tgt_node(P, g.arr, static_cast<uint32_t>(pair) - P.t0);
+      const uint32_t s = src_node<true>(P, g.arr, static_cast<uint32_t>(pair >> 32) - P.s0);
+      const uint32_t t = tgt_node<true>(P, g.arr, static_cast<uint32_t>(pair) - P.t0);
       const uint64_t old = g.key32 ? static_cast<uint64_t>(static_cast<uint32_t*>(g.keys)[pos])
                                    : static_cast<uint64_t*>(g.keys)[pos];
       const uint64_t key = pack_key(s - P.t_base, static_cast<uint32_t>(old & dmask), g.layout.delay_bits);
@@ -1184,10 +1231,10 @@ __global__ void __launch_bounds__(kGenThreads) total_emit_kernel(GenArgs g, Redr
         if (i >= end) continue;
         const uint64_t pair = a.pairs[r.slot_base + i];
         const Words W = draw(P.k0, P.k1, kTagWD, 0, kPrimaryNone, i);
-        const uint32_t s = src_node(P, g.arr, static_cast<uint32_t>(pair >> 32) - P.s0);
-        const uint32_t t = tgt_node(P, g.arr, static_cast<uint32_t>(pair) - P.t0);
-        store(g, bh, P.out_off + i, s - P.t_base, conn_delay(P, g.arr, tabs, i, W.x), t - P.t_base,
-              conn_weight(P, g.arr, i, W.z, W.w));
+        const uint32_t s = src_node<true>(P, g.arr, static_cast<uint32_t>(pair >> 32) - P.s0);
+        const uint32_t t = tgt_node<true>(P, g.arr, static_cast<uint32_t>(pair) - P.t0);
+        store(g, bh, P.out_off + i, s - P.t_base, conn_delay<true>(P, g.arr, tabs, i, W.x), t - P.t_base,
+              conn_weight<true>(P, g.arr, i, W.z, W.w));
       }
     }
   }

@@ -45,21 +45,6 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// Lanes of the warp whose digit equals this lane's: one ballot per digit bit
-// (NB bits; a lane without a key passes d = 1 << (NB - 1), a bit no digit
-// has).  Ballots pipeline freely, unlike a chain of match instructions.
-template <int NB>
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
-  uint32_t peers = 0xffffffffu;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const uint32_t bit = (d >> b) & 1u;
-    const uint32_t m = __ballot_sync(0xffffffffu, bit);
-    peers &= bit ? m : ~m;
-  }
-  return peers;
-}
-
 // Exclusive scan over the block of one uint32 per thread; *total gets the sum.
 template <int TPB>
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_tmp, uint32_t* total) {
@@ -716,36 +701,29 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       __syncthreads();
     }
 
-    // Rank within the warp (keys from shared memory).  The peer sets of all
-    // items come first (ballots, independent of one another); then, item by
-    // item, every lane reads its digit's counter (peers read the same word)
-    // and the lowest peer advances it past the whole peer set.
+    // Rank within the warp (keys from shared memory).  The peer set of an
+    // item comes from the match instruction, whose cost falls with the
+    // number of distinct digits in the warp (structured networks, such as
+    // all_to_all's source-ordered rows, have few); per-bit ballots cost the
+    // same whatever the digits and measured slower on the rule sweep.
     const uint32_t wbase = warp * 32u * IPT;
     K key[IPT];
     uint32_t rank[IPT];
     uint16_t* my = wcnt + static_cast<size_t>(warp) * RADIX;
-    {
-      uint32_t peers[IPT];
-      const bool full = valid == TILE;  // uniform over the block
 #pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
-        const bool ok = li < valid;
-        key[j] = ok ? skeys[li] : K(0);
-        const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
-        peers[j] = full ? digit_peers<BITS>(d) : digit_peers<BITS + 1>(d);
-      }
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
-        const bool ok = li < valid;
-        const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
-        const uint32_t old = ok ? my[d] : 0u;
-        __syncwarp();
-        if (ok && static_cast<int>(lane) == __ffs(peers[j]) - 1) my[d] = static_cast<uint16_t>(old + __popc(peers[j]));
-        rank[j] = old + __popc(peers[j] & lt);
-        __syncwarp();
-      }
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
+      const bool ok = li < valid;
+      key[j] = ok ? skeys[li] : K(0);
+      const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      // Every lane reads its digit's counter (peers read the same word),
+      // then the lowest peer advances it past the whole peer set.
+      const uint32_t old = ok ? my[d] : 0u;
+      __syncwarp();
+      if (ok && static_cast<int>(lane) == __ffs(peers) - 1) my[d] = static_cast<uint16_t>(old + __popc(peers));
+      rank[j] = old + __popc(peers & lt);
+      __syncwarp();
     }
     __syncthreads();
     uint32_t tot[DPT];
