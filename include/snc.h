@@ -350,6 +350,36 @@ snc_status snc_get_stats(const snc_ctx* ctx, snc_stats* out);
 snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                                 uint32_t* vals_out, uint64_t n, int key_bits, void* stream);
 
+/* COPASS block sort (Appendix A of the paper: "COnstrained PArtition of
+ * Sorted Subarrays"): sorts n (key, value) pairs stably on the low key_bits
+ * bits of the keys, IN PLACE in keys / vals (device memory), keeping the
+ * array's division in blocks of `block` pairs: every block is sorted, then
+ * for each block in turn the remaining sorted blocks are partitioned by a
+ * common threshold so that their left partitions hold that block's share,
+ * which is gathered, the rest shifted to the end, and sorted into place.
+ * Working memory: two blocks of pairs plus the radix sort's scratch for one
+ * block (cudaMallocAsync on `stream`), instead of a second copy of all n
+ * pairs; the price is about twice the data movement of snc_radix_sort_pairs.
+ * block: a multiple of 1024, at most 256 blocks (n <= 256 * block).  The
+ * call waits for the sort and reads its device error word (TIMEOUT: a
+ * bounded look-back wait expired; CUDA: launch failure or another error
+ * bit).  INVALID_ARG: null pointers with n > 0, key_bits outside [1, 64],
+ * block not a multiple of 1024 or too small for n.  OOM: working memory. */
+snc_status snc_block_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t n, int key_bits, uint64_t block,
+                                void* stream);
+
+/* Builds ctx with the COPASS block sort (blocks of `block` connections, a
+ * multiple of 1024; 0 = the out-of-place radix sort, the default), for
+ * networks whose out-of-place sort would not fit the device: the sort then
+ * works in place with two blocks of working memory, and the sorted pairs are
+ * unpacked in place (targets over the value array, weights over the key
+ * array), so the build's peak device memory falls from about 26.5 to about
+ * 14 bytes per connection plus 24 bytes per block connection.  Results are
+ * identical to the default build.  Before snc_finalize (STATE after);
+ * INVALID_ARG at snc_finalize for a target shard, in a batch, or when the
+ * network needs more than 256 blocks. */
+snc_status snc_set_block_sort(snc_ctx* ctx, uint64_t block);
+
 /* Largest n accepted by snc_radix_sort_pairs_noalloc. */
 #define SNC_NOALLOC_MAX_PAIRS (1u << 19)
 

@@ -24,6 +24,11 @@ Parity status (see the pins in tests/test_oracle_*.py):
                     invariances, per-connection weights by the Sec. 2.1
                     numbering, delays by hand-computed steps, the complete
                     cases by their unique results (tests/test_oracle_arrays.py)
+  copass            the COPASS partition and block sort of Appendix A: pinned
+                    by brute force (the left partitions are the first m
+                    elements of the stable order), by the block sort equal to
+                    numpy's stable argsort, and by planted mistakes
+                    (tests/test_oracle_copass.py)
   build_parallel    the same functions on host threads (snc_oracle_par.c):
                     pinned equal, bit for bit, to build() on every rule and
                     flag pair (tests/test_oracle_parallel.py)
@@ -326,3 +331,27 @@ def build_parallel(spec, threads=0):
     return {"src": g["src"], "tgt": g["tgt"], "delay": g["delay"], "weight": g["weight"], "row_ptr": row_ptr,
             "group_ptr": group_ptr, "group_first": group_first[:ng.value], "n_groups": int(ng.value),
             "per_proj": g["per_proj"]}
+
+
+def copass_partition(runs, m):
+    """Left-partition sizes of the COPASS partition (Appendix A) of sorted
+    uint64 runs with sum = m."""
+    runs = [np.ascontiguousarray(r, dtype=np.uint64) for r in runs]
+    k = len(runs)
+    bufs = [r if r.size else np.zeros(1, np.uint64) for r in runs]
+    ptrs = (ctypes.c_void_p * max(1, k))(*[b.ctypes.data for b in bufs])
+    lens = np.array([r.size for r in runs] or [0], dtype=np.uint64)
+    part = np.zeros(max(1, k), dtype=np.uint64)
+    _check(_lib().or_copass_partition(ptrs, _ptr(lens), ctypes.c_uint32(k), ctypes.c_uint64(int(m)),
+                                      _ptr(part)), "copass_partition")
+    return part[:k].astype(np.int64)
+
+
+def copass_sort(keys, vals, block):
+    """The COPASS block sort (Appendix A) of uint64 keys with uint64 values,
+    blocks of `block` elements: (sorted keys, values)."""
+    keys = np.array(keys, dtype=np.uint64)
+    vals = np.array(vals, dtype=np.uint64)
+    _check(_lib().or_copass_sort(_ptr(keys), _ptr(vals), ctypes.c_uint64(keys.size), ctypes.c_uint64(int(block))),
+           "copass_sort")
+    return keys, vals

@@ -1012,6 +1012,215 @@ int or_sort_index(uint32_t n_nodes, uint64_t n, uint32_t* src, uint32_t* tgt, ui
   return OR_OK;
 }
 
+/* ======================================================================== */
+/* COPASS block sort (Appendix A): an array divided in k blocks is sorted    */
+/* keeping its block structure, with an auxiliary array of one block.        */
+/* ======================================================================== */
+
+/* Elements of sorted run a[0..n) that are <= t (upper = 1) or < t (upper = 0):
+ * a binary search. */
+static uint64_t count_below(const uint64_t* a, uint64_t n, uint64_t t, int upper) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (upper ? a[mid] <= t : a[mid] < t) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+/* The COPASS partition (Appendix A, "The COPASS partition algorithm"): k
+ * runs run[i][0..len[i]), each sorted ascending, and 0 <= m <= sum len[i].
+ * Finds left-partition sizes part[i] with sum part[i] = m such that every
+ * element of a left partition is <= every element of a right partition.
+ * The iteration keeps lo[i] = #{elements <= t_lo} and hi[i] = #{elements <
+ * t_hi} with sum lo < m < sum hi; each step takes the run l with the widest
+ * open interval, its middle element t~ as a trial threshold, and the counts
+ * mu_lo = #{< t~}, mu_hi = #{<= t~}: t~ is the threshold (case 1), or it
+ * becomes t_hi (case 2) or t_lo (case 3).  When every interval is at most
+ * one wide (last step, case 1) the undecided elements, one per run, at
+ * index lo[i] (the paper prints S_{i, m-bar}; the element between the two
+ * counts is S_{i, m-underbar} = S_{i, m-bar - 1}), are taken in ascending
+ * order of (value, run) until the left partitions hold m.  When t~ is the
+ * threshold (last step, case 2) the elements equal to it are shared out in
+ * run order.  Ties go to lower runs in both last steps, so that the runs'
+ * order (the original positions) decides among equal keys: the left
+ * partitions are the first m elements of the stable sort of the
+ * concatenated runs.  Keys are integers here, so the paper's initial
+ * thresholds min - 1 and max + 1 are replaced by "below every element" and
+ * "above every element" (no overflow); the counts they give, 0 and len[i],
+ * are what the paper derives from them. */
+int or_copass_partition(const uint64_t* const* run, const uint64_t* len, uint32_t k, uint64_t m,
+                        uint64_t* part) {
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < k; ++i) total += len[i];
+  if (m > total) return OR_ERR_INVALID_ARG;
+  uint64_t* lo = (uint64_t*)calloc(k ? k : 1, sizeof(uint64_t));
+  uint64_t* hi = (uint64_t*)calloc(k ? k : 1, sizeof(uint64_t));
+  uint64_t* mul = (uint64_t*)calloc(k ? k : 1, sizeof(uint64_t));
+  uint64_t* muh = (uint64_t*)calloc(k ? k : 1, sizeof(uint64_t));
+  if (!lo || !hi || !mul || !muh) {
+    free(lo); free(hi); free(mul); free(muh);
+    return OR_ERR_OOM;
+  }
+  for (uint32_t i = 0; i < k; ++i) hi[i] = len[i];
+  int st = OR_OK;
+  if (m == 0 || m == total) {  /* the trivial partitions */
+    for (uint32_t i = 0; i < k; ++i) part[i] = m == 0 ? 0 : len[i];
+    goto done;
+  }
+  for (;;) {
+    uint32_t l = 0;
+    uint64_t widest = 0;
+    for (uint32_t i = 0; i < k; ++i)
+      if (hi[i] - lo[i] > widest) {
+        widest = hi[i] - lo[i];
+        l = i;
+      }
+    uint64_t sum_lo = 0;
+    for (uint32_t i = 0; i < k; ++i) sum_lo += lo[i];
+    if (widest <= 1) {
+      /* Last step, case 1: undecided elements in ascending (value, run). */
+      uint64_t d = m - sum_lo;
+      for (uint32_t i = 0; i < k; ++i) part[i] = lo[i];
+      while (d > 0) {
+        int best = -1;
+        for (uint32_t i = 0; i < k; ++i) {
+          if (hi[i] != lo[i] + 1 || part[i] != lo[i]) continue;  /* no candidate, or taken */
+          if (best < 0 || run[i][lo[i]] < run[best][lo[best]]) best = (int)i;
+        }
+        if (best < 0) {
+          st = OR_ERR_INVALID_ARG;  /* cannot happen while sum lo < m < sum hi */
+          break;
+        }
+        part[best] = lo[best] + 1;
+        --d;
+      }
+      goto done;
+    }
+    const uint64_t mid = (lo[l] + hi[l]) / 2;
+    const uint64_t t = run[l][mid];
+    uint64_t sum_mul = 0, sum_muh = 0;
+    for (uint32_t i = 0; i < k; ++i) {
+      mul[i] = count_below(run[i], len[i], t, 0);
+      muh[i] = count_below(run[i], len[i], t, 1);
+      sum_mul += mul[i];
+      sum_muh += muh[i];
+    }
+    if (sum_mul <= m && m <= sum_muh) {
+      /* Last step, case 2: t is the threshold; its copies shared in run order. */
+      uint64_t d = m - sum_mul;
+      for (uint32_t i = 0; i < k; ++i) {
+        const uint64_t take = muh[i] - mul[i] < d ? muh[i] - mul[i] : d;
+        part[i] = mul[i] + take;
+        d -= take;
+      }
+      goto done;
+    }
+    if (m < sum_mul) {          /* case 2: the threshold is below t */
+      for (uint32_t i = 0; i < k; ++i) hi[i] = mul[i];
+    } else {                    /* case 3: the threshold is above t */
+      for (uint32_t i = 0; i < k; ++i) lo[i] = muh[i];
+    }
+  }
+done:
+  free(lo); free(hi); free(mul); free(muh);
+  return st;
+}
+
+typedef struct {
+  uint64_t key;
+  uint64_t val;
+  uint64_t pos;
+} or_kv;
+
+static int cmp_kv(const void* x, const void* y) {
+  const or_kv* a = (const or_kv*)x;
+  const or_kv* b = (const or_kv*)y;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  if (a->pos != b->pos) return a->pos < b->pos ? -1 : 1;
+  return 0;
+}
+
+/* Stable sort of n (key, value) pairs in place (the underlying sort of a
+ * block: qsort with the position as the last key). */
+static int stable_sort_kv(uint64_t* keys, uint64_t* vals, uint64_t n) {
+  or_kv* r = (or_kv*)malloc(sizeof(or_kv) * (n ? (size_t)n : 1));
+  if (!r) return OR_ERR_OOM;
+  for (uint64_t q = 0; q < n; ++q) {
+    r[q].key = keys[q];
+    r[q].val = vals[q];
+    r[q].pos = q;
+  }
+  qsort(r, (size_t)n, sizeof(or_kv), cmp_kv);
+  for (uint64_t q = 0; q < n; ++q) {
+    keys[q] = r[q].key;
+    vals[q] = r[q].val;
+  }
+  free(r);
+  return OR_OK;
+}
+
+/* The COPASS block sort (Appendix A, Fig. A): keys[0..n) with values, in
+ * blocks of `block` elements (the last block may be shorter), sorted stably
+ * by key keeping the block structure, with an auxiliary array of one block.
+ *   1. every block is sorted on its own;
+ *   2. for output block o = 0, 1, ...: the remaining runs (the sorted
+ *      blocks, shortened from the front as elements leave them) are
+ *      partitioned with m = the size of block o; the left partitions are
+ *      copied to the auxiliary array, the right partitions shifted to the
+ *      end of the array (run by run, last run first) so that block o is
+ *      free, the auxiliary array copied into block o and sorted.
+ * The runs stay in their original order, so equal keys keep it. */
+int or_copass_sort(uint64_t* keys, uint64_t* vals, uint64_t n, uint64_t block) {
+  if (block == 0) return OR_ERR_INVALID_ARG;
+  if (n == 0) return OR_OK;
+  const uint64_t nb = (n + block - 1) / block;
+  uint64_t* run_off = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nb);
+  uint64_t* run_len = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nb);
+  uint64_t* part = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)nb);
+  const uint64_t** run = (const uint64_t**)malloc(sizeof(uint64_t*) * (size_t)nb);
+  uint64_t* aux_k = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)block);
+  uint64_t* aux_v = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)block);
+  int st = (!run_off || !run_len || !part || !run || !aux_k || !aux_v) ? OR_ERR_OOM : OR_OK;
+  for (uint64_t b = 0; b < nb && !st; ++b) {
+    run_off[b] = b * block;
+    run_len[b] = b * block + block <= n ? block : n - b * block;
+    st = stable_sort_kv(keys + run_off[b], vals + run_off[b], run_len[b]);
+  }
+  for (uint64_t o = 0; o < nb && !st; ++o) {
+    const uint64_t first = o * block;
+    const uint64_t size = first + block <= n ? block : n - first;
+    /* Every run, in its original order (emptied runs have length 0). */
+    const uint32_t k = (uint32_t)nb;
+    for (uint32_t i = 0; i < k; ++i) run[i] = keys + run_off[i];
+    st = or_copass_partition(run, run_len, k, size, part);
+    if (st) break;
+    /* Left partitions to the auxiliary array, in run order. */
+    uint64_t a = 0;
+    for (uint32_t i = 0; i < k; ++i) {
+      memcpy(aux_k + a, keys + run_off[i], sizeof(uint64_t) * (size_t)part[i]);
+      memcpy(aux_v + a, vals + run_off[i], sizeof(uint64_t) * (size_t)part[i]);
+      a += part[i];
+    }
+    /* Right partitions shifted to the end, last run first. */
+    uint64_t end = n;
+    for (uint32_t i = k; i-- > 0;) {
+      const uint64_t src = run_off[i] + part[i], len = run_len[i] - part[i];
+      end -= len;
+      memmove(keys + end, keys + src, sizeof(uint64_t) * (size_t)len);
+      memmove(vals + end, vals + src, sizeof(uint64_t) * (size_t)len);
+      run_off[i] = end;
+      run_len[i] = len;
+    }
+    /* The auxiliary array becomes block o, sorted. */
+    memcpy(keys + first, aux_k, sizeof(uint64_t) * (size_t)size);
+    memcpy(vals + first, aux_v, sizeof(uint64_t) * (size_t)size);
+    st = stable_sort_kv(keys + first, vals + first, size);
+  }
+  free(run_off); free(run_len); free(part); free(run); free(aux_k); free(aux_v);
+  return st;
+}
+
 /* Spike delivery through the index (Sec. 2.3): entry e of the spike array
  * names source src[e], the grp[e]-th of its connection groups (groups in
  * position order, i.e. by increasing delay) and a multiplicity mult[e];

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libsnc.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["snc_runtime.cu", "gen_kernels.cu", "sort_kernels.cu", "index_kernels.cu", "tables.cpp",
            "sort_noalloc.cu", "snc_server.cpp", "source_major.cu", "deliver.cu",
-           "arrays.cpp"]
+           "arrays.cpp", "copass.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -10,6 +10,8 @@
 // row_ptr and group_ptr.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
 #include "index_kernels.h"
@@ -289,6 +291,57 @@ __global__ void shard_compact_kernel(const void* keys_in, const uint64_t* vals_i
     else static_cast<uint64_t*>(keys_out)[o] = static_cast<const uint64_t*>(keys_in)[i];
     vals_out[o] = v;
   }
+}
+
+// In-place unpack of a build sorted in place (COPASS block sort): windows
+// [x0, x1) in increasing order; take copies a window's keys and values into
+// a temporary block, put writes its targets as uint32 over the value array,
+// its weight bits over the key array and its delay steps into their own
+// array.  Position x writes bytes [4x, 4x + 4) of each array, which hold
+// pairs at positions <= x: already taken, so nothing is read after it was
+// overwritten.
+template <typename K>
+__global__ void unpack_take_kernel(const K* __restrict__ keys, const uint64_t* __restrict__ vals, uint64_t x0,
+                                   uint64_t x1, K* __restrict__ tk, uint64_t* __restrict__ tv) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t x = x0 + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < x1; x += stride) {
+    tk[x - x0] = keys[x];
+    tv[x - x0] = vals[x];
+  }
+}
+
+template <typename K>
+__global__ void unpack_put_kernel(uint32_t* __restrict__ weight, uint32_t* __restrict__ target,
+                                  uint16_t* __restrict__ delay, uint64_t x0, uint64_t x1, const K* __restrict__ tk,
+                                  const uint64_t* __restrict__ tv, uint32_t delay_mask) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t x = x0 + static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < x1; x += stride) {
+    const uint64_t v = tv[x - x0];
+    target[x] = static_cast<uint32_t>(v >> 32);
+    weight[x] = static_cast<uint32_t>(v);
+    delay[x] = static_cast<uint16_t>(static_cast<uint32_t>(tk[x - x0]) & delay_mask);
+  }
+}
+
+cudaError_t unpack_in_place(void* keys, int key32, uint64_t* vals, uint64_t n, uint64_t window, void* tk,
+                            uint64_t* tv, uint32_t delay_mask, uint16_t* delay, int sms, cudaStream_t st) {
+  for (uint64_t x0 = 0; x0 < n; x0 += window) {
+    const uint64_t x1 = x0 + window < n ? x0 + window : n;
+    const unsigned grid = static_cast<unsigned>(
+        std::max<uint64_t>(1, std::min<uint64_t>((x1 - x0 + 255) / 256, static_cast<uint64_t>(sms) * 8)));
+    if (key32) {
+      unpack_take_kernel<uint32_t><<<grid, 256, 0, st>>>(static_cast<const uint32_t*>(keys), vals, x0, x1,
+                                                         static_cast<uint32_t*>(tk), tv);
+      unpack_put_kernel<uint32_t><<<grid, 256, 0, st>>>(static_cast<uint32_t*>(keys), reinterpret_cast<uint32_t*>(vals),
+                                                        delay, x0, x1, static_cast<const uint32_t*>(tk), tv, delay_mask);
+    } else {
+      unpack_take_kernel<uint64_t><<<grid, 256, 0, st>>>(static_cast<const uint64_t*>(keys), vals, x0, x1,
+                                                         static_cast<uint64_t*>(tk), tv);
+      unpack_put_kernel<uint64_t><<<grid, 256, 0, st>>>(static_cast<uint32_t*>(keys), reinterpret_cast<uint32_t*>(vals),
+                                                        delay, x0, x1, static_cast<const uint64_t*>(tk), tv, delay_mask);
+    }
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace snc

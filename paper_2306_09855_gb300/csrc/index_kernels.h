@@ -72,4 +72,10 @@ __global__ void shard_compact_kernel(const void* keys_in, const uint64_t* vals_i
                                      const uint64_t* offsets, uint32_t first, uint32_t count, void* keys_out,
                                      uint64_t* vals_out);
 
+// In-place unpack after a block sort: targets over vals (as uint32), weight
+// bits over keys (as uint32), delays into `delay`; tk / tv: a temporary
+// block of `window` keys and values.
+cudaError_t unpack_in_place(void* keys, int key32, uint64_t* vals, uint64_t n, uint64_t window, void* tk,
+                            uint64_t* tv, uint32_t delay_mask, uint16_t* delay, int sms, cudaStream_t st);
+
 }  // namespace snc

@@ -25,6 +25,7 @@
 #include "source_major.h"
 #include "deliver.h"
 #include "arrays.h"
+#include "copass.h"
 
 using namespace snc;
 
@@ -247,6 +248,9 @@ struct snc_ctx {
   // [shard_first, shard_first + shard_n) (snc_set_target_shard).
   bool sharded = false;
   uint32_t shard_first = 0, shard_n = 0;
+  // COPASS block sort (snc_set_block_sort): blocks of this many connections,
+  // 0 = the out-of-place radix sort.
+  uint64_t block_sort = 0;
   // Results: device views; for batch members resolved at synchronize (and
   // again after every graph replay of the build).
   bool view_ready = false;
@@ -482,6 +486,17 @@ snc_status estimate_build(const snc_ctx* c, BuildEstimate* e) {
   const uint64_t slack = 96ull << 20;
   e->n_syn = n;
   e->peak_bytes = std::max(gen, index) + slack;
+  if (c->block_sort && !c->sharded) {
+    // COPASS block sort: one key/value buffer, the delays, two blocks of
+    // working memory and one block's sort scratch; the unpack works in place.
+    const uint64_t blk = c->block_sort;
+    const SortPasses sp = plan_passes(lay.total_bits());
+    const uint64_t base = pair * n + 2 * n;
+    const uint64_t sort = base + copass_scratch_bytes(blk, lay.key32() ? 4 : 8, 8, sp);
+    const uint64_t gen1 = pair * n + std::max<uint64_t>(34 * redraw_slots + 8 * redraw_table + 16 * (primaries + 1), 0);
+    const uint64_t idx1 = base + n / 8 + 8 * gc + 32 * (N + 1) + 16 * (primaries + 1) + pair * blk;
+    e->peak_bytes = std::max(std::max(gen1, sort), idx1) + slack;
+  }
   e->resident_bytes = 10 * n + 8 * gc + 32 * (N + 1) + slack;
   e->n_nodes = N;
   e->max_step = max_step;
@@ -983,14 +998,24 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   SNC_CUDA(c, upload(c, d_tile_begin, tile_begin.data(), (n_members + 1) * sizeof(uint32_t)));
   const bool key32 = c->layout.key32();
   const size_t key_bytes = key32 ? sizeof(uint32_t) : sizeof(uint64_t);
+  // COPASS block sort (Appendix A): the pairs are sorted in place in blocks,
+  // so there is no second key/value buffer, only two blocks of working
+  // memory; the sorted pairs are then unpacked in place.
+  const uint64_t block = c->block_sort;
+  const bool block_sorted = block > 0 && !segmented && !sharded;
+  if (block_sorted && (n + block - 1) / block > static_cast<uint64_t>(kCopassMaxRuns))
+    return fail(c, SNC_ERR_INVALID_ARG, "block sort: %llu connections need more than %d blocks of %llu",
+                static_cast<unsigned long long>(n), kCopassMaxRuns, static_cast<unsigned long long>(block));
+  if (block_sorted) src_major = false;
   void* keys_a = dev_alloc(c, n * key_bytes);
   uint64_t* vals_a = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
-  void* keys_b = dev_alloc(c, n * key_bytes);
-  uint64_t* vals_b = static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
+  void* keys_b = block_sorted ? nullptr : dev_alloc(c, n * key_bytes);
+  uint64_t* vals_b = block_sorted ? nullptr : static_cast<uint64_t*>(dev_alloc(c, n * sizeof(uint64_t)));
   const uint64_t n_seg_tiles = tile_begin[n_members];
-  void* sort_scratch = dev_alloc(c, segmented ? sort_scratch_bytes(n, c->passes, n_seg_tiles, n_members)
-                                              : sort_scratch_bytes(n, c->passes));
-  if (!keys_a || !vals_a || !keys_b || !vals_b || !sort_scratch)
+  void* sort_scratch = dev_alloc(c, block_sorted ? copass_scratch_bytes(block, static_cast<int>(key_bytes), 8, c->passes)
+                                    : segmented  ? sort_scratch_bytes(n, c->passes, n_seg_tiles, n_members)
+                                                 : sort_scratch_bytes(n, c->passes));
+  if (!keys_a || !vals_a || (!block_sorted && (!keys_b || !vals_b)) || !sort_scratch)
     return fail(c, SNC_ERR_OOM, "device allocation failed (%llu connections)", static_cast<unsigned long long>(n));
 
   // The generation kernels count the sort's digits as they write the keys
@@ -999,7 +1024,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
                                          : sort_scratch_layout(sort_scratch, n, c->passes);
   // (A target shard that filters counts the digits of the kept connections
   // in the sort.)
-  const bool gen_counts = !segmented && !src_major && !shard_filter;
+  const bool gen_counts = !segmented && !src_major && !shard_filter && !block_sorted;
   if (gen_counts)
     SNC_CUDA(c, cudaMemsetAsync(sort_lay.hist, 0,
                                 static_cast<size_t>(kMaxPasses) * kMaxRadix * sizeof(unsigned long long), st));
@@ -1352,7 +1377,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // passes ping-pong between the two buffers; the result lands in
   // (keys_b, vals_b) for an odd number of passes and back in (keys_a,
   // vals_a) for an even number.
-  const bool odd = src_major || (c->passes.n_passes & 1) != 0;
+  const bool odd = !block_sorted && (src_major || (c->passes.n_passes & 1) != 0);
   void* keys_res = odd ? keys_b : keys_a;
   uint64_t* vals_res = odd ? vals_b : vals_a;
   void* keys_oth = odd ? keys_a : keys_b;
@@ -1375,7 +1400,19 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   segs.n_tiles = n_seg_tiles;
   for (int m = 0; m < n_members; ++m) segs.max_len = std::max(segs.max_len, seg_end[m] - seg_begin[m]);
   const SortSegments* seg_arg = segmented ? &segs : nullptr;
-  if (src_major) {
+  if (block_sorted) {
+    // Sorted in place (keys_a, vals_a); one timed sort stage.
+    mark();
+    if (key32)
+      SNC_CUDA(c, copass_sort_run(static_cast<uint32_t*>(keys_a), vals_a, n, block, c->passes, sort_scratch, S.d_err, st));
+    else
+      SNC_CUDA(c, copass_sort_run(static_cast<uint64_t*>(keys_a), vals_a, n, block, c->passes, sort_scratch, S.d_err, st));
+    mark();
+    c->stats.kernel_launches += 2 * ((n + block - 1) / block) * (static_cast<uint64_t>(c->passes.n_passes) + 4);
+    c->stats.n_passes = c->passes.n_passes;
+    c->stats.source_major = 0;
+    c->sort_stages = 1;
+  } else if (src_major) {
     const uint64_t nn = total_nodes;
     uint32_t* sm_counts = static_cast<uint32_t*>(dev_alloc(c, (nn + 1) * sizeof(uint32_t)));
     uint64_t* sm_base = static_cast<uint64_t*>(dev_alloc(c, (nn + 1) * sizeof(uint64_t)));
@@ -1432,7 +1469,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     SNC_CUDA(c, radix_sort_run(static_cast<const uint64_t*>(keys_a), vals_a, static_cast<uint64_t*>(keys_res), vals_res,
                                static_cast<uint64_t*>(keys_oth), vals_oth, n, c->passes, sort_scratch, S.d_err, st,
                                S.capturing ? nullptr : S.ev + S.n_ev, /*hist_ready=*/!shard_filter, &unpack, &fused, seg_arg));
-  if (!src_major) {
+  if (!src_major && !block_sorted) {
     if (!S.capturing) S.n_ev += c->passes.n_passes + 1;
     if (n > 0) c->stats.kernel_launches += static_cast<uint64_t>(c->passes.n_passes) + 1;
     c->stats.n_passes = c->passes.n_passes;
@@ -1447,8 +1484,14 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // Index: unpack target / delay / weight, group starts, row_ptr and p_i.
   const uint64_t n_delay_values = max_step;
   const uint64_t group_cap = std::max<uint64_t>(1, std::min<uint64_t>(n, total_nodes * n_delay_values));
-  uint32_t* u_target = fused ? unpack.target : static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
-  float* u_weight = fused ? reinterpret_cast<float*>(unpack.weight) : static_cast<float*>(dev_alloc(c, n * sizeof(float)));
+  // (A block-sorted build unpacks in place after the index: targets over
+  // the value array, weights over the key array.)
+  uint32_t* u_target = fused          ? unpack.target
+                       : block_sorted ? reinterpret_cast<uint32_t*>(vals_res)
+                                      : static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+  float* u_weight = fused          ? reinterpret_cast<float*>(unpack.weight)
+                    : block_sorted ? static_cast<float*>(keys_res)
+                                   : static_cast<float*>(dev_alloc(c, n * sizeof(float)));
   uint64_t* u_group_first = static_cast<uint64_t*>(dev_alloc(c, group_cap * sizeof(uint64_t)));
   // Per-network CSR and group offsets: network m's n_nodes_m + 1 entries
   // start at local_base[m].
@@ -1472,7 +1515,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     ia.keys = keys_res;
     ia.vals = vals_res;
     ia.key32 = key32 ? 1 : 0;
-    ia.unpacked = fused ? 1 : 0;
+    ia.unpacked = (fused || block_sorted) ? 1 : 0;
     ia.n = n;
     ia.delay_bits = c->layout.delay_bits;
     ia.target = u_target;
@@ -1524,6 +1567,17 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
   }
+  if (block_sorted && n > 0) {
+    // The index has read the keys: unpack in place, one block at a time.
+    void* utk = dev_alloc(c, block * key_bytes);
+    uint64_t* utv = static_cast<uint64_t*>(dev_alloc(c, block * sizeof(uint64_t)));
+    if (!utk || !utv) return fail(c, SNC_ERR_OOM, "device allocation failed (unpack block)");
+    SNC_CUDA(c, unpack_in_place(keys_res, key32 ? 1 : 0, vals_res, n, block, utk, utv,
+                                (1u << c->layout.delay_bits) - 1u, u_delay, c->sms, st));
+    c->stats.kernel_launches += 2 * ((n + block - 1) / block);
+    dev_free(c, utk);
+    dev_free(c, utv);
+  }
   // First group of every network (and the total) for the views.
   if (!S.h_bases) {
     S.h_bases_words = static_cast<size_t>(n_members) + 1;
@@ -1538,8 +1592,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   dev_free(c, bcounts);
   dev_free(c, boffsets);
   dev_free(c, iscan);
-  dev_free(c, keys_res);
-  if (!fused) dev_free(c, vals_res);  // else it holds the targets and weights
+  if (!block_sorted) dev_free(c, keys_res);       // a block-sorted build keeps its weights there
+  if (!fused && !block_sorted) dev_free(c, vals_res);  // else it holds the targets (and weights)
   dev_free(c, d_direct);
   dev_free(c, d_prim_off);
   dev_free(c, d_seg);
@@ -1581,10 +1635,24 @@ snc_status snc_finalize(snc_ctx* c) {
   return snc::abi_guard([&]() -> snc_status {
     if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
     if (c->finalized) return fail(c, SNC_ERR_STATE, "finalize called twice");
+    if (c->sharded && c->block_sort)
+      return fail(c, SNC_ERR_INVALID_ARG, "a target shard is built with the out-of-place sort");
     if (c->sharded && static_cast<uint64_t>(c->shard_first) + c->shard_n > c->n_nodes)
       return fail(c, SNC_ERR_INVALID_ARG, "target shard [%u, %u + %u) outside the %llu nodes", c->shard_first,
                   c->shard_first, c->shard_n, static_cast<unsigned long long>(c->n_nodes));
     return finalize_build(&c, 1);
+  });
+}
+
+snc_status snc_set_block_sort(snc_ctx* c, uint64_t block) {
+  return snc::abi_guard([&]() -> snc_status {
+    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+    if (c->finalized) return fail(c, SNC_ERR_STATE, "set_block_sort after finalize");
+    if (block % kCopassAlign != 0)
+      return fail(c, SNC_ERR_INVALID_ARG, "block sort: block of %llu is not a multiple of %llu",
+                  static_cast<unsigned long long>(block), static_cast<unsigned long long>(kCopassAlign));
+    c->block_sort = block;
+    return SNC_OK;
   });
 }
 
@@ -1607,6 +1675,7 @@ snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n) {
       if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
       if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
       if (ctxs[i]->sharded) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a target shard is built alone");
+      if (ctxs[i]->block_sort) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a block-sorted build is built alone");
       for (int j = 0; j < i; ++j)
         if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
     }
@@ -1637,6 +1706,7 @@ snc_status snc_batch_finalize_graph(snc_ctx* const* ctxs, int n) {
       if (ctxs[i]->finalized) return fail(ctxs[i], SNC_ERR_STATE, "batch: context already finalized");
       if (ctxs[i]->device != ctxs[0]->device) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: contexts on different devices");
       if (ctxs[i]->sharded) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a target shard is built alone");
+      if (ctxs[i]->block_sort) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: a block-sorted build is built alone");
       for (int j = 0; j < i; ++j)
         if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
       if (!graph_eligible(ctxs[i]))
@@ -1945,6 +2015,43 @@ snc_status snc_radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in
     if (e != cudaSuccess) return fail(nullptr, SNC_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e));
     if (bits & kErrLookbackTimeout) return fail(nullptr, SNC_ERR_TIMEOUT, "radix sort: a look-back wait expired on the device");
     if (bits) return fail(nullptr, SNC_ERR_CUDA, "radix sort: device error bits 0x%x", bits);
+    return SNC_OK;
+  });
+}
+
+snc_status snc_block_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t n, int key_bits, uint64_t block,
+                                void* stream) {
+  return snc::abi_guard([&]() -> snc_status {
+    if (key_bits < 1 || key_bits > 64) return fail(nullptr, SNC_ERR_INVALID_ARG, "key_bits outside [1, 64]");
+    if (n == 0) return SNC_OK;
+    if (!keys || !vals) return fail(nullptr, SNC_ERR_INVALID_ARG, "null buffer");
+    if (block == 0 || block % kCopassAlign != 0)
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "block of %llu is not a positive multiple of %llu",
+                  static_cast<unsigned long long>(block), static_cast<unsigned long long>(kCopassAlign));
+    if ((n + block - 1) / block > static_cast<uint64_t>(kCopassMaxRuns))
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "%llu pairs need more than %d blocks of %llu",
+                  static_cast<unsigned long long>(n), kCopassMaxRuns, static_cast<unsigned long long>(block));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const SortPasses sp = plan_passes(key_bits);
+    void* scratch = nullptr;
+    uint32_t* err = nullptr;
+    if (cudaMallocAsync(&scratch, copass_scratch_bytes(block, 8, 4, sp), st) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void**>(&err), 256, st) != cudaSuccess) {
+      cudaGetLastError();
+      if (scratch) cudaFreeAsync(scratch, st);
+      if (err) cudaFreeAsync(err, st);
+      return fail(nullptr, SNC_ERR_OOM, "block sort working memory allocation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(err, 0, 256, st);
+    if (e == cudaSuccess) e = copass_sort_run(keys, vals, n, block, sp, scratch, err, st);
+    uint32_t bits = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, err, sizeof bits, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(scratch, st);
+    cudaFreeAsync(err, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(nullptr, SNC_ERR_CUDA, "block sort: %s", cudaGetErrorString(e));
+    if (bits & kErrLookbackTimeout) return fail(nullptr, SNC_ERR_TIMEOUT, "block sort: a look-back wait expired");
+    if (bits) return fail(nullptr, SNC_ERR_CUDA, "block sort: device error bits 0x%x", bits);
     return SNC_OK;
   });
 }

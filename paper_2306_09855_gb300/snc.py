@@ -117,7 +117,8 @@ EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", 
            "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_copy_index",
            "snc_deliver", "snc_set_target_shard", "snc_stage_times",
-           "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_get_stats",
+           "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_block_sort_pairs", "snc_set_block_sort",
+           "snc_get_stats",
            "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_batch_finalize_graph",
            "snc_batch_rebuild", "snc_set_wait_test", "snc_last_error",
            "snc_server_create", "snc_server_destroy", "snc_server_submit", "snc_server_poll",
@@ -160,6 +161,8 @@ def load(build: bool = True):
                              ctypes.POINTER(I32)], I32),
         "snc_radix_sort_pairs": ([P, P, P, P, U64, I32, P], I32),
         "snc_radix_sort_pairs_noalloc": ([P, P, P, P, U64, I32, P], I32),
+        "snc_block_sort_pairs": ([P, P, U64, I32, U64, P], I32),
+        "snc_set_block_sort": ([P, U64], I32),
         "snc_get_stats": ([P, ctypes.POINTER(snc_stats)], I32),
         "snc_set_tuning": ([ctypes.POINTER(snc_tuning)], I32),
         "snc_get_tuning": ([ctypes.POINTER(snc_tuning)], I32),
@@ -337,6 +340,16 @@ def snc_radix_sort_pairs_noalloc(keys_in, vals_in, keys_out, vals_out, n, key_bi
 
 
 SNC_NOALLOC_MAX_PAIRS = 1 << 19
+
+
+def snc_block_sort_pairs(keys, vals, n, key_bits, block, stream=0):
+    """COPASS block sort in place: device pointers (ints) of uint64 keys and
+    uint32 values, blocks of `block` pairs (a multiple of 1024)."""
+    _check(load().snc_block_sort_pairs(keys, vals, n, key_bits, block, stream or None))
+
+
+def snc_set_block_sort(ctx, block):
+    _check(load().snc_set_block_sort(ctx, int(block)), ctx)
 
 
 def snc_set_wait_test(lookback_spin_limit=0, withhold_tile=0xFFFFFFFF):
@@ -566,12 +579,12 @@ class Server:
 class Network:
     """Create -> Connect -> Finalize -> GetConnections for one NetworkSpec."""
 
-    def __init__(self, spec, device=0, stream=None, allocator="torch", target_shard=None):
+    def __init__(self, spec, device=0, stream=None, allocator="torch", target_shard=None, block_sort=0):
         import torch
         self.spec = spec
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
-        self._alloc = TorchAllocator(device) if allocator == "torch" else None
+        self._alloc = TorchAllocator(device) if allocator == "torch" else (allocator if allocator else None)
         cfg = snc_config(seed=int(spec.seed) & 0xFFFFFFFFFFFFFFFF, dt_ms=float(spec.dt),
                          device=device, reserved=0, stream=self.stream.cuda_stream,
                          allocator=ctypes.pointer(self._alloc.struct) if self._alloc else None)
@@ -583,6 +596,8 @@ class Network:
             _connect(self.ctx, pj)
         if target_shard is not None:  # (first, n): keep the connections onto these targets
             snc_set_target_shard(self.ctx, *target_shard)
+        if block_sort:  # COPASS block sort with blocks of this many connections
+            snc_set_block_sort(self.ctx, block_sort)
 
     def finalize(self):
         snc_finalize(self.ctx)
