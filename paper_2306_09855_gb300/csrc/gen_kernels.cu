@@ -405,18 +405,30 @@ __device__ __forceinline__ void sample_primary(const SamplerArgs& a, const Block
       const uint32_t sel = lane & 3u;
       const uint32_t u = sel == 0 ? vx : sel == 1 ? vy : sel == 2 ? vz : vw;
       const uint32_t r = endpoint(u, n_other, skip, skip_local);
-      const uint32_t bit = 1u << (r & 31u);
-      const bool seen = (bitmap[r >> 5] & bit) != 0u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, r);
-      const bool first = (__ffs(peers) - 1) == static_cast<int>(lane);
-      const bool fresh = !seen && first;
+      const uint32_t word = r >> 5, bit = 1u << (r & 31u);
+      const bool seen = (bitmap[word] & bit) != 0u;
+      __syncwarp();  // every lane has read its word before any lane sets a bit
+      // Unseen values are set at once; a lane that finds its bit already set
+      // by the group shares its value with another lane.  Only then (rarely:
+      // about 32^2 / (2 n_other) of the groups) does the match instruction,
+      // whose cost grows with the number of distinct values, pick the lowest
+      // lane of each value; otherwise every unseen lane holds a value no other
+      // lane holds and is the first of it.
+      const uint32_t prev = seen ? bit : atomicOr(&bitmap[word], bit);
+      bool fresh = !seen;
+      if (__any_sync(0xffffffffu, !seen && (prev & bit) != 0u)) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, r);
+        fresh = fresh && (__ffs(peers) - 1) == static_cast<int>(lane);
+      }
       const uint32_t fresh_mask = __ballot_sync(0xffffffffu, fresh);
       const uint32_t rank = __popc(fresh_mask & ((1u << lane) - 1u));
       const uint32_t room = need - got;
       const bool take = fresh && rank < room;
+      // New values beyond the room (last group only) leave the bitmap again:
+      // no other lane's kept value shares their bit.
+      if (fresh && !take) atomicAnd(&bitmap[word], ~bit);
       __syncwarp();
       if (take) {
-        atomicOr(&bitmap[r >> 5], bit);
         if (!complement) {
           const uint32_t j = got + rank;
           const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, j);

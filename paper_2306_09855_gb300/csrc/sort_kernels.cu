@@ -580,6 +580,9 @@ struct OnesweepTma {
   static constexpr int kFit = static_cast<int>((228u * 1024u) / (kSmem + 1024u + 256u));
   static constexpr int kRegCap = ITEMS >= 20 ? 2 : (ITEMS >= 16 ? 3 : (ITEMS >= 12 ? 4 : 5));
   static constexpr int MINB = kFit < 1 ? 1 : (kFit > kRegCap ? kRegCap : kFit);
+  // Peer masks in the warp's part of the key buffer (32 * IPT keys) during
+  // ranking: one 32-bit word per digit.
+  static constexpr bool kMaskRank = static_cast<size_t>(RADIX) * 4u <= 32u * IPT * sizeof(K);
 };
 
 // Bounded wait for a bulk copy, with the outcome voted over the block so
@@ -701,29 +704,67 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       __syncthreads();
     }
 
-    // Rank within the warp (keys from shared memory).  The peer set of an
-    // item comes from the match instruction, whose cost falls with the
-    // number of distinct digits in the warp (structured networks, such as
-    // all_to_all's source-ordered rows, have few); per-bit ballots cost the
-    // same whatever the digits and measured slower on the rule sweep.
+    // Rank within the warp.  An item's rank is its digit's count so far in
+    // the warp plus the lanes of its slot that hold the same digit and come
+    // before it (its peers).  The match instruction finds peers at a cost
+    // that grows with the number of distinct digits in the warp (about two
+    // SM cycles each, 60+ for random digits, and it saturates the SM's
+    // divergence unit); when the warp's part of the key buffer can hold one
+    // 32-bit lane mask per digit, the keys go to registers and the peers are
+    // collected there instead: each lane ORs its bit into its digit's mask,
+    // reads the mask back, and the lowest peer clears it.  A slot whose lanes
+    // all hold one digit (structured networks) skips the masks.
     const uint32_t wbase = warp * 32u * IPT;
     K key[IPT];
     uint32_t rank[IPT];
     uint16_t* my = wcnt + static_cast<size_t>(warp) * RADIX;
+    if constexpr (C::kMaskRank) {
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
-      const bool ok = li < valid;
-      key[j] = ok ? skeys[li] : K(0);
-      const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      // Every lane reads its digit's counter (peers read the same word),
-      // then the lowest peer advances it past the whole peer set.
-      const uint32_t old = ok ? my[d] : 0u;
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
+        key[j] = li < valid ? skeys[li] : K(0);
+      }
+      uint32_t* pmask = reinterpret_cast<uint32_t*>(skeys + wbase);  // this warp's keys are in registers now
       __syncwarp();
-      if (ok && static_cast<int>(lane) == __ffs(peers) - 1) my[d] = static_cast<uint16_t>(old + __popc(peers));
-      rank[j] = old + __popc(peers & lt);
+#pragma unroll
+      for (int i = static_cast<int>(lane); i < RADIX; i += 32) pmask[i] = 0u;
       __syncwarp();
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
+        const bool ok = li < valid;
+        const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
+        uint32_t peers = 0xffffffffu;
+        if (__reduce_min_sync(0xffffffffu, d) != __reduce_max_sync(0xffffffffu, d)) {
+          if (ok) atomicOr(pmask + d, 1u << lane);
+          __syncwarp();
+          peers = ok ? pmask[d] : 0u;
+        }
+        const uint32_t old = ok ? my[d] : 0u;
+        __syncwarp();
+        if (ok && static_cast<int>(lane) == __ffs(peers) - 1) {
+          my[d] = static_cast<uint16_t>(old + __popc(peers));
+          pmask[d] = 0u;
+        }
+        rank[j] = old + __popc(peers & lt);
+        __syncwarp();
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
+        const bool ok = li < valid;
+        key[j] = ok ? skeys[li] : K(0);
+        const uint32_t d = ok ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // Every lane reads its digit's counter (peers read the same word),
+        // then the lowest peer advances it past the whole peer set.
+        const uint32_t old = ok ? my[d] : 0u;
+        __syncwarp();
+        if (ok && static_cast<int>(lane) == __ffs(peers) - 1) my[d] = static_cast<uint16_t>(old + __popc(peers));
+        rank[j] = old + __popc(peers & lt);
+        __syncwarp();
+      }
     }
     __syncthreads();
     uint32_t tot[DPT];
