@@ -392,11 +392,19 @@ __device__ __forceinline__ void sample_primary(const SamplerArgs& a, const Block
       if (lane == 0) atomicOr(a.err, kErrSamplerBound);
       break;
     }
-    // One IDX draw per lane: attempts 4*(call + lane) .. +3.
+    // One IDX draw per lane: attempts 4*(call + lane) .. +3.  The four
+    // groups of 32 attempts are selected first; the WD draws of the kept
+    // values then run together (four independent chains per lane).
     const Words X = draw(P.k0, P.k1, kTagIdx, 0, b + P.prim_shift, call + lane);
     call += 32;
-#pragma unroll 1
-    for (int q = 0; q < 4 && got < need; ++q) {
+    uint32_t kept_j[4], kept_r[4];
+    bool kept[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      kept[q] = false;
+      kept_j[q] = 0;
+      kept_r[q] = 0;
+      if (got >= need) continue;  // uniform over the warp
       const int src_lane = 8 * q + static_cast<int>(lane >> 2);
       const uint32_t vx = __shfl_sync(0xffffffffu, X.x, src_lane);
       const uint32_t vy = __shfl_sync(0xffffffffu, X.y, src_lane);
@@ -427,20 +435,27 @@ __device__ __forceinline__ void sample_primary(const SamplerArgs& a, const Block
       // New values beyond the room (last group only) leave the bitmap again:
       // no other lane's kept value shares their bit.
       if (fresh && !take) atomicAnd(&bitmap[word], ~bit);
-      __syncwarp();
-      if (take) {
-        if (!complement) {
-          const uint32_t j = got + rank;
-          const Words W = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, j);
-          const uint32_t other = indeg ? src_node<ARR>(P, A, r) : tgt_node<ARR>(P, A, r);
-          const uint32_t s = indeg ? other : node, t = indeg ? node : other;
-          const uint64_t inew = static_cast<uint64_t>(b + P.prim_shift) * P.k + j;
-          store(a.gen, bh, out + j, s - P.t_base, conn_delay<ARR>(P, A, tabs, inew, W.x), t - P.t_base,
-                conn_weight<ARR>(P, A, inew, W.z, W.w));
-        }
-      }
+      kept[q] = take;
+      kept_j[q] = got + rank;
+      kept_r[q] = r;
       got += min(static_cast<uint32_t>(__popc(fresh_mask)), room);
       __syncwarp();
+    }
+    if (!complement) {
+      // Drawn for every lane (the chains interleave), stored for kept ones.
+      Words W[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) W[q] = draw(P.k0, P.k1, kTagWD, 0, b + P.prim_shift, kept_j[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!kept[q]) continue;
+        const uint32_t j = kept_j[q], r = kept_r[q];
+        const uint32_t other = indeg ? src_node<ARR>(P, A, r) : tgt_node<ARR>(P, A, r);
+        const uint32_t s = indeg ? other : node, t = indeg ? node : other;
+        const uint64_t inew = static_cast<uint64_t>(b + P.prim_shift) * P.k + j;
+        store(a.gen, bh, out + j, s - P.t_base, conn_delay<ARR>(P, A, tabs, inew, W[q].x), t - P.t_base,
+              conn_weight<ARR>(P, A, inew, W[q].z, W[q].w));
+      }
     }
   }
   if (complement) {

@@ -201,6 +201,9 @@ struct Onesweep {
   static constexpr size_t kTileBytes = static_cast<size_t>(TILE) * (sizeof(K) + sizeof(V));
   static constexpr size_t kUnion = kCntBytes > kTileBytes ? kCntBytes : kTileBytes;
   static constexpr size_t kSmem = kUnion + RADIX * sizeof(uint32_t) * 2 + RADIX * sizeof(uint64_t);
+  // Peer masks (one 32-bit word per warp and digit) after the counters,
+  // while ranking, when both fit the tile's staging area.
+  static constexpr bool kMaskRank = kCntBytes * 3 <= kTileBytes;
 };
 
 // Sum, for each of this thread's DPT digits, the counts that groups before
@@ -339,6 +342,8 @@ __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
       if (tbase >= a.n) break;
       __syncthreads();  // previous tile's staging and run[] update are complete
       for (int i = tid; i < NW * RADIX / 2; i += TPB) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
+      if constexpr (C::kMaskRank)
+        for (int i = tid; i < NW * RADIX; i += TPB) reinterpret_cast<uint32_t*>(smem + C::kCntBytes)[i] = 0u;
       __syncthreads();
       const uint64_t warp_base = tbase + static_cast<uint64_t>(warp) * 32 * IPT;
       K key[IPT];
@@ -349,15 +354,29 @@ __global__ void __launch_bounds__(kSortThreads, (Onesweep<BITS, G, K, V>::MINB))
         key[j] = idx < a.n ? a.keys_in[idx] : K(0);
       }
       uint16_t* my = wcnt + static_cast<size_t>(warp) * RADIX;
+      uint32_t* pmask = reinterpret_cast<uint32_t*>(smem + C::kCntBytes) + static_cast<size_t>(warp) * RADIX;
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const uint64_t idx = warp_base + static_cast<uint64_t>(j) * 32 + lane;
         const bool valid = idx < a.n;
         const uint32_t d = valid ? (static_cast<uint32_t>(key[j] >> shift) & mask) : static_cast<uint32_t>(RADIX);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t peers = 0xffffffffu;
+        if constexpr (C::kMaskRank) {
+          // Peers from the lane masks (as in the bulk-copy kernel below).
+          if (__reduce_min_sync(0xffffffffu, d) != __reduce_max_sync(0xffffffffu, d)) {
+            if (valid) atomicOr(pmask + d, 1u << lane);
+            __syncwarp();
+            peers = valid ? pmask[d] : 0u;
+          }
+        } else {
+          peers = __match_any_sync(0xffffffffu, d);
+        }
         const uint32_t old = valid ? my[d] : 0u;
         __syncwarp();
-        if (valid && static_cast<int>(lane) == __ffs(peers) - 1) my[d] = static_cast<uint16_t>(old + __popc(peers));
+        if (valid && static_cast<int>(lane) == __ffs(peers) - 1) {
+          my[d] = static_cast<uint16_t>(old + __popc(peers));
+          if constexpr (C::kMaskRank) pmask[d] = 0u;
+        }
         rank[j] = old + __popc(peers & lt);
         __syncwarp();
       }

@@ -323,8 +323,13 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
       block_scan(v, running);
     }
     // Pass 2: chunks in generation order.
+    // While a chunk is ranked the staging buffer is free: it holds one
+    // 32-bit lane mask per warp and delay step (the peers of an item).
+    static_assert(sizeof(skey) >= sizeof(uint32_t) * NW * RMAX, "peer masks fit the key staging buffer");
+    uint32_t* pmask = reinterpret_cast<uint32_t*>(skey) + warp * RMAX;
     for (uint64_t cb = 0; cb < c; cb += CH) {
       for (uint32_t i = tid; i < NW * RMAX / 2; i += TPB) reinterpret_cast<uint32_t*>(&wcnt[0][0])[i] = 0u;
+      for (uint32_t i = tid; i < NW * RMAX; i += TPB) reinterpret_cast<uint32_t*>(skey)[i] = 0u;
       __syncthreads();
       uint64_t key[IPT], val[IPT];
       uint32_t rank[IPT];
@@ -341,14 +346,26 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
           }
         }
       }
+      // Peers: each lane ORs its bit into its delay's mask and reads the mask
+      // back; the lowest peer advances the counter and clears the mask (the
+      // match instruction costs about two SM cycles per distinct delay in the
+      // warp).  A slot whose lanes hold one delay skips the masks.
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const bool ok = key[j] != ~0ull;
         const uint32_t d = ok ? (static_cast<uint32_t>(key[j]) & dmask) : R;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t peers = 0xffffffffu;
+        if (__reduce_min_sync(0xffffffffu, d) != __reduce_max_sync(0xffffffffu, d)) {
+          if (ok) atomicOr(pmask + d, 1u << lane);
+          __syncwarp();
+          peers = ok ? pmask[d] : 0u;
+        }
         const uint32_t old = ok ? wcnt[warp][d] : 0u;
         __syncwarp();
-        if (ok && static_cast<int>(lane) == __ffs(peers) - 1) wcnt[warp][d] = static_cast<uint16_t>(old + __popc(peers));
+        if (ok && static_cast<int>(lane) == __ffs(peers) - 1) {
+          wcnt[warp][d] = static_cast<uint16_t>(old + __popc(peers));
+          pmask[d] = 0u;
+        }
         rank[j] = old + __popc(peers & lt);
         __syncwarp();
       }
