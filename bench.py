@@ -788,10 +788,10 @@ def main():
     # plans on the host, copies the plans in, builds, and copies the whole
     # network as the device holds it (target, delay, weight: 10 B per
     # connection, plus row_ptr, p_i and group_first) back into page-locked
-    # host arrays, all inside the host wall-clock region.  Two host threads,
-    # each with its own stream and host arrays, take the networks in turn,
-    # so that one network's copy to the host overlaps the next one's build.
-    import threading
+    # host arrays, all inside the host wall-clock region.  One host thread
+    # queues network k's build on one of two streams and then copies network
+    # k - 1 (built on the other stream) to the host, so that each copy
+    # overlaps the next build and the copies follow one another on the link.
     max_syn = max(r[0] for r in records) if records else 0
     max_groups = max(max(r[4] for r in records), max_syn if batched else 0) if records else 0
     max_nodes = max(sp.n_nodes for sp in specs)
@@ -807,51 +807,43 @@ def main():
                 "row_ptr": h["row_ptr"].view(np.uint64), "group_ptr": h["group_ptr"].view(np.uint64),
                 "group_first": h["group_first"].view(np.uint64)}
 
-    n_workers = 1 if batched else 2
-    hosts = [host_arrays() for _ in range(n_workers)]
-    streams = [torch.cuda.Stream(device=local) for _ in range(n_workers)]
-    totals = [[0, 0, 0] for _ in range(n_workers)]  # connections, h2d, d2h
-    errors = []
-
-    def e2e_worker(w):
-        try:
-            torch.cuda.set_device(local)
-            for k in range(w, len(specs), n_workers):
-                net = snc.Network(specs[k], device=local, stream=streams[w])
-                net.finalize()
-                totals[w][0] += net.to_host_network(hosts[w])
-                st = net.stats()
-                totals[w][1] += int(st.h2d_bytes)
-                totals[w][2] += int(st.d2h_bytes)
-                net.close()
-        except Exception as exc:  # reported after the join
-            errors.append(exc)
+    host = host_arrays()
+    streams = [torch.cuda.Stream(device=local) for _ in range(2)]
 
     def e2e_pass():
         """One end-to-end pass over every network: (connections, h2d, d2h)."""
-        for t in totals:
-            t[0] = t[1] = t[2] = 0
         if batched:
             n_p = d2h_p = 0
             nets = snc.Network.batch(specs, device=local, stream=stream)
             for net in nets:
                 n_p += int(net.view().n_syn)
-                net.to_host_network(hosts[0])
+                net.to_host_network(host)
                 d2h_p += int(net.stats().d2h_bytes)
             h2d_p = int(nets[0].stats().h2d_bytes)
             for net in reversed(nets):
                 net.close()
             return n_p, h2d_p, d2h_p
-        threads = [threading.Thread(target=e2e_worker, args=(w,)) for w in range(n_workers)]
-        for th in threads:
-            th.start()
-        for th in threads:
-            th.join()
-        if errors:
-            raise errors[0]
-        return sum(t[0] for t in totals), sum(t[1] for t in totals), sum(t[2] for t in totals)
+        tot = [0, 0, 0]
 
-    # One untimed pass warms the worker streams' allocations and the pinned
+        def drain(net):
+            tot[0] += net.to_host_network(host)
+            st = net.stats()
+            tot[1] += int(st.h2d_bytes)
+            tot[2] += int(st.d2h_bytes)
+            net.close()
+
+        prev = None
+        for k, spec in enumerate(specs):
+            net = snc.Network(spec, device=local, stream=streams[k % 2])
+            net.finalize()  # queued (a Bernoulli count or a redraw round waits for its own stream)
+            if prev is not None:
+                drain(prev)
+            prev = net
+        if prev is not None:
+            drain(prev)
+        return tuple(tot)
+
+    # One untimed pass warms the streams' allocations and the pinned
     # host pages; then E2E_STEPS timed passes (the bytes reported per pass).
     e2e_pass()
     torch.cuda.synchronize()
@@ -897,9 +889,8 @@ def main():
                 "steps": E2E_STEPS, "warmup": 1,
                 "note": "public API, host wall clock: plan, build, and copy of each network as held on the "
                         "device (target, delay, weight: 10 B per connection; row_ptr, p_i, group_first) into "
-                        "page-locked host arrays; two host threads with their own streams overlap one "
-                        "network's copy with the next one's build; mean of the timed passes after one "
-                        "untimed pass"},
+                        "page-locked host arrays; one host thread, two streams: network k is built while "
+                        "network k - 1 is copied; mean of the timed passes after one untimed pass"},
         "clocks": clk,
     }
     if per_network:
