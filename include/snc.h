@@ -227,19 +227,31 @@ snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n);
  * The first build runs immediately and gives the same result as
  * snc_batch_finalize.  The build keeps all its temporary buffers (its peak
  * device memory stays allocated).  Stage timers report the first build.
- * UNSUPPORTED: a member uses pairwise_bernoulli or fixed_total_number without
- * autapses or multapses (their counts need host round trips).  Other errors
- * as snc_batch_finalize; CUDA if the capture fails. */
+ * Every rule is accepted.  Counts that a seed decides are kept on the
+ * device: a pairwise_bernoulli projection is given a capacity of mean + 10
+ * standard deviations + 32 of its Binomial total over ns * nt pairs (the
+ * positions its draw leaves free are sorted past the network's connections
+ * and are not part of any view), and fixed_total_number without autapses or
+ * multapses runs a fixed number of redraw rounds, chosen so that a slot is
+ * still pending after the last one with probability below 10^-12.
+ * UNSUPPORTED: a total-number projection without multapses so dense that
+ * the number of rounds would exceed 512.  Other errors as
+ * snc_batch_finalize; CUDA if the capture fails. */
 snc_status snc_batch_finalize_graph(snc_ctx* const* ctxs, int n);
 
 /* Rebuilds every network of ctx's graph build (ctx: any member) with
  * seeds[m] for member m (n = number of members, in the order given to
- * snc_batch_finalize_graph), in place: the views keep their addresses, and
- * the connection counts stay the same (the rules that allow graph builds
- * have seed-independent counts); group counts and contents change.
+ * snc_batch_finalize_graph), in place: the views keep their addresses;
+ * connection counts (of networks with pairwise_bernoulli projections), group
+ * counts and contents change, and the views follow at the next
+ * snc_synchronize or snc_get_connections.
  * Asynchronous on the build's stream; waits for the previous build first.
  * Result = snc_batch_finalize of the same contexts with those seeds.
- * STATE: not a graph build.  INVALID_ARG: null pointers or n mismatch. */
+ * STATE: not a graph build.  INVALID_ARG: null pointers or n mismatch.
+ * A replay that exceeds a bound fixed when the graph was recorded is
+ * reported by the next snc_synchronize: UNSUPPORTED for a pairwise_bernoulli
+ * total above its capacity, TIMEOUT for redraws still pending after the last
+ * recorded round (both far less likely than 10^-12 per replay). */
 snc_status snc_batch_rebuild(snc_ctx* ctx, const uint64_t* seeds, int n);
 
 /* Waits for the context's queued work and reports device-side failures

@@ -373,8 +373,13 @@ __device__ __forceinline__ void sample_primary(const SamplerArgs& a, const Block
   const uint32_t cand = n_other - (skip ? 1u : 0u);
   uint64_t want, out;
   if (P.rule == SNC_PAIRWISE_BERNOULLI) {
-    out = P.out_off + (a.prim_offsets[P.prim_off + b] - a.prim_offsets[P.prim_off]);
+    const uint64_t rel = a.prim_offsets[P.prim_off + b] - a.prim_offsets[P.prim_off];
     want = a.prim_offsets[P.prim_off + b + 1] - a.prim_offsets[P.prim_off + b];
+    out = P.out_off + rel;
+    if (rel + want > P.count) {  // only a graph replay can draw past the projection's capacity
+      if (lane == 0) atomicOr(a.err, kErrGraphCapacity);
+      return;
+    }
   } else {
     want = P.k;
     out = P.out_off + static_cast<uint64_t>(b) * P.k;
@@ -547,6 +552,50 @@ __global__ void sampler_kernel(SamplerArgs a) {
       sample_primary<false>(a, bh, bitmap, tabs, P, b, lane);
   }
   block_hist_end(a.gen, bh);
+}
+
+__global__ void bern_pad_kernel(GenArgs g, const DevProj* projs, const uint32_t* list, int n_list,
+                                const uint64_t* totals, uint64_t pad_key) {
+  const HistRegs hr = hist_regs(g.hist);
+  for (int k = blockIdx.y; k < n_list; k += gridDim.y) {
+    const DevProj& P = projs[list[k]];
+    const uint64_t tot = totals[k];
+    if (tot > P.count) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(g.err, kErrGraphCapacity);
+      continue;
+    }
+    const uint64_t n_pad = P.count - tot;
+    const uint64_t begin = P.out_off + tot;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
+      const uint64_t pos = begin + i;
+      if (!SNC_IN_BOUNDS(g.err, 3u, pos, g.cap)) break;
+      if (g.key32)
+        static_cast<uint32_t*>(g.keys)[pos] = static_cast<uint32_t>(pad_key);
+      else
+        static_cast<uint64_t*>(g.keys)[pos] = pad_key;
+      g.vals[pos] = 0ull;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n_pad > 0) {
+#pragma unroll
+      for (int p = 0; p < kMaxPasses; ++p)
+        if (p < hr.n)
+          atomicAdd(g.hist.global + p * kMaxRadix + (static_cast<uint32_t>(pad_key >> hr.shift[p]) & hr.mask[p]),
+                    static_cast<unsigned long long>(n_pad));
+    }
+  }
+}
+
+__global__ void member_real_kernel(const uint64_t* totals, const uint32_t* member, int n_list, const uint64_t* fixed,
+                                   const uint64_t* seg_begin, int n_members, uint64_t* real_end,
+                                   uint64_t* real_count) {
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_members; m += gridDim.x * blockDim.x) {
+    uint64_t cnt = fixed[m];
+    for (int k = 0; k < n_list; ++k)
+      if (member[k] == static_cast<uint32_t>(m)) cnt += totals[k];
+    real_count[m] = cnt;
+    real_end[m] = seg_begin[m] + cnt;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -794,7 +843,9 @@ __global__ void redraw_collect_kernel(RedrawArgs a) {
     if (a.lost[g]) push_pending(a, g);
 }
 
-__global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round) {
+__global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round,
+                                    const unsigned long long* d_count) {
+  if (d_count) n_pending = *d_count;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pending; q += stride) {
     const uint64_t g = pending[q];
@@ -1210,7 +1261,9 @@ __global__ void __launch_bounds__(256, 4) redraw_bucket0_kernel(RedrawArgs a) {
 // Decides the slots of round r >= 1: winners become accepted, the others are
 // appended to next_pending (the order of the list is irrelevant: each slot's
 // later draws depend only on the slot and the round).
-__global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending) {
+__global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending,
+                                      const unsigned long long* d_count) {
+  if (d_count) n_pending = *d_count;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n_pending; q += stride) {
     const uint64_t g = pending[q];
@@ -1222,6 +1275,10 @@ __global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uin
     if (ok && !P.multapses) ok = a.bucketed ? bucket_resolve(a, *x.r, P, s, t, x.i) : resolve(a, *x.r, P, s, t, x.i);
     if (!ok) push_pending(a, g);
   }
+}
+
+__global__ void redraw_rounds_check_kernel(const unsigned long long* d_count, uint32_t* err) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *d_count != 0) atomicOr(err, kErrGraphRounds);
 }
 
 // Writes the redraw projections' connections (global pair tables): the final

@@ -60,6 +60,21 @@ __global__ void bernoulli_count_kernel(const DevProj* projs, const uint32_t* lis
 // out[j] = offsets[prefix[j + 1]] - offsets[prefix[j]]: connections per listed projection.
 __global__ void segment_totals_kernel(const uint64_t* offsets, const uint64_t* prefix, int n_list, uint64_t* out);
 __global__ void sampler_kernel(SamplerArgs a);
+// Graph builds with pairwise_bernoulli projections.  Such a projection owns
+// `count` positions, a capacity fixed when the graph is recorded; positions
+// past the drawn total (totals[k] for list[k]) get the padding key, which
+// sorts after every connection, and a zero value, and are added to the
+// fused digit counts when the build counts digits in generation.
+// kErrGraphCapacity when a total exceeds its capacity.  grid.y strides over
+// the list.
+__global__ void bern_pad_kernel(GenArgs g, const DevProj* projs, const uint32_t* list, int n_list,
+                                const uint64_t* totals, uint64_t pad_key);
+// Connections each network of the build really holds: fixed[m] plus the
+// drawn totals of its pairwise_bernoulli projections (member[k] owns
+// totals[k]); real_end[m] = seg_begin[m] + that count.
+__global__ void member_real_kernel(const uint64_t* totals, const uint32_t* member, int n_list, const uint64_t* fixed,
+                                   const uint64_t* seg_begin, int n_members, uint64_t* real_end,
+                                   uint64_t* real_count);
 
 // fixed_total_number with autapses or multapses forbidden: the redraw
 // projections of a build, their slots concatenated.
@@ -137,8 +152,15 @@ constexpr int kSplitThreads = 512;       // split kernel block
 constexpr uint32_t kSplitUnit = 8192;    // entries per split block and unit
 __global__ void redraw_round0_kernel(RedrawArgs a);
 __global__ void redraw_collect_kernel(RedrawArgs a);
-__global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round);
-__global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending);
+// n_pending entries of `pending`, or *d_count of them when d_count is not
+// null (graph builds: the count stays on the device).
+__global__ void redraw_claim_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending, uint32_t round,
+                                    const unsigned long long* d_count);
+__global__ void redraw_resolve_kernel(RedrawArgs a, const uint64_t* pending, uint64_t n_pending,
+                                      const unsigned long long* d_count);
+// Graph builds: sets kErrGraphRounds when *d_count slots are still pending
+// after the last recorded round.
+__global__ void redraw_rounds_check_kernel(const unsigned long long* d_count, uint32_t* err);
 // Bucketed claims: round 0 keeps the lowest slot of every pair in each
 // bucket and leaves the bucket's table of accepted pairs; later rounds claim
 // and resolve in those tables (redraw_claim_kernel, redraw_resolve_kernel).

@@ -19,6 +19,10 @@ enum : uint32_t {
   kErrLookbackTimeout = 1u,  // a decoupled look-back wait hit its iteration bound
   kErrSamplerBound = 2u,     // a sampler exceeded its attempt bound
   kErrBounds = 4u,           // an internal index check failed
+  // Graph replays (snc_batch_rebuild) run with bounds fixed when the graph
+  // was recorded:
+  kErrGraphCapacity = 8u,    // a pairwise_bernoulli projection drew past its capacity
+  kErrGraphRounds = 16u,     // total-number redraws still pending after the recorded rounds
 };
 
 constexpr int kDelayGuide = 257;  // guide-table entries per threshold table
@@ -53,7 +57,11 @@ struct DevProj {
   // pairwise_bernoulli) keep only the targets in the shard and key every
   // draw by primary + prim_shift, the index the whole network uses.
   uint32_t prim_shift;
-  uint32_t reserved0;
+  // floor(i / k) for 32-bit i as ((t + ((i - t) >> k_sh1)) >> k_sh2) with
+  // t = umulhi(i, k_mul) (Granlund & Montgomery 1994, Fig. 4.1); set for
+  // 1 <= k < 2^32 (division_magic).
+  uint32_t k_mul;
+  uint32_t k_sh1, k_sh2;
   // Explicit arrays of the Connect call (Sec. 2.1), as offsets into the
   // build's array blobs (kNoList: not given).  src_list / tgt_list: node ids
   // (network-local) in place of the ranges; w_list: per-connection weight
@@ -66,6 +74,22 @@ struct DevProj {
   // positions of every row, ascending per row (id blob).
   uint64_t src_list, tgt_list, w_list, d_list, self_list, row_list, drop_list;
 };
+// Multiplier and shifts of DevProj::k_mul for a divisor 1 <= d < 2^32:
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, shifts min(l, 1) and
+// max(l - 1, 0) (Granlund & Montgomery 1994, Fig. 4.1).
+inline void division_magic(uint64_t d, uint32_t* mul, uint32_t* sh1, uint32_t* sh2) {
+  if (d == 0 || d > 0xFFFFFFFFull) {
+    *mul = 0;
+    *sh1 = *sh2 = 0;
+    return;
+  }
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  *mul = static_cast<uint32_t>(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  *sh1 = l < 1 ? static_cast<uint32_t>(l) : 1u;
+  *sh2 = l > 1 ? static_cast<uint32_t>(l - 1) : 0u;
+}
+
 constexpr uint64_t kNoList = ~0ull;
 constexpr uint32_t kNoPosition = 0xFFFFFFFFu;
 

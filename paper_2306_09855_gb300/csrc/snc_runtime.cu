@@ -104,6 +104,12 @@ struct Storage {
   uint64_t* d_bases = nullptr;  // [2 * (members + 1)] on the device
   uint64_t* h_bases = nullptr;  // pinned copy
   size_t h_bases_words = 0;
+  // Graph builds with pairwise_bernoulli projections: each network's
+  // connection count is drawn on the device at every replay; the build
+  // copies the counts here (pinned), read at sync.
+  uint64_t* h_real = nullptr;
+  size_t h_real_words = 0;
+  bool real_counts = false;
   int n_members = 1;
   uint64_t n_total = 0;  // connections of the whole build
   bool synced = false;
@@ -222,6 +228,7 @@ struct Storage {
       for (int i = 0; i < kMaxEvents; ++i) cudaEventDestroy(ev[i]);
     pinned_pool().put(h_pinned, h_pinned_words * sizeof(uint64_t));
     pinned_pool().put(h_bases, h_bases_words * sizeof(uint64_t));
+    pinned_pool().put(h_real, h_real_words * sizeof(uint64_t));
     for (auto& ch : stage_chunks) pinned_pool().put(ch.first, ch.second);
     cudaGetLastError();
   }
@@ -693,10 +700,18 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     for (size_t i = 0; i < ups.size(); ++i) ups[i].p = &shard_projs[i];
   }
 
-  // Key layout: global source | delay step | member-local target.
+  // A graph build cannot read the pairwise_bernoulli counts back (a replay
+  // draws new ones): each such projection gets a capacity, and the positions
+  // its draw leaves free hold a padding key above every real key (all ones,
+  // with one more source bit so that no node has that source).
+  const bool graph_build = S.mode != 0;
+  bool graph_pad = false;
+  for (const UnionProj& u : ups) graph_pad = graph_pad || (graph_build && u.p->rule.kind == SNC_PAIRWISE_BERNOULLI);
+
+  // Key layout: network-local source | delay step (the target is in the value).
   uint32_t max_step = 1;
   for (const UnionProj& u : ups) max_step = std::max(max_step, u.p->max_step);
-  c->layout.src_bits = std::max(1, bit_width(max_nodes > 0 ? max_nodes - 1 : 0));  // network-local sources
+  c->layout.src_bits = std::max(1, bit_width(graph_pad ? max_nodes : (max_nodes > 0 ? max_nodes - 1 : 0)));
   c->layout.tgt_bits = std::max(1, bit_width(max_nodes > 0 ? max_nodes - 1 : 0));
   c->layout.delay_bits = std::max(1, bit_width(max_step));
   if (c->layout.total_bits() > 64)
@@ -733,6 +748,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     d.k0 = static_cast<uint32_t>(ups[i].owner->cfg.seed);
     d.k1 = static_cast<uint32_t>(ups[i].owner->cfg.seed >> 32) ^ ups[i].local;
     d.k = p.rule.k;
+    division_magic(d.k, &d.k_mul, &d.k_sh1, &d.k_sh2);
     d.w_normal = (p.syn.weight.kind == SNC_DIST_NORMAL) ? 1u : 0u;
     d.w_mean = static_cast<float>(p.syn.weight.mean);
     d.w_std = static_cast<float>(p.syn.weight.std);
@@ -849,6 +865,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   // Count phase: per-target counts of every pairwise Bernoulli projection in
   // one launch, one scan, one read-back of the per-projection totals.
   uint64_t* d_prim_off = nullptr;
+  uint32_t* d_bern_list = nullptr;    // graph_pad: the Bernoulli projections and their drawn totals
+  uint64_t* d_bern_totals = nullptr;
   std::vector<uint32_t> bern;
   std::vector<uint64_t> bern_prefix(1, 0);
   for (size_t i = 0; i < np; ++i)
@@ -860,7 +878,12 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   if (!bern.empty()) {
     const uint64_t n_targets = bern_prefix.back();
     const int nb = static_cast<int>(bern.size());
-    SNC_CUDA(c, upload(c, d_proj, dp.data(), np * sizeof(DevProj)));
+    // The count kernel reads these records: their staged copy is a seed site
+    // too (a graph replay draws the counts with the new seeds).
+    void* h_counted = nullptr;
+    SNC_CUDA(c, upload(c, d_proj, dp.data(), np * sizeof(DevProj), &h_counted));
+    for (size_t i = 0; i < np; ++i)
+      S.seed_sites.push_back({static_cast<DevProj*>(h_counted) + i, ups[i].member, ups[i].local});
     d_prim_off = static_cast<uint64_t*>(dev_alloc(c, (n_targets + 1) * sizeof(uint64_t)));
     uint32_t* d_counts = static_cast<uint32_t*>(dev_alloc(c, (n_targets + 1) * sizeof(uint32_t)));
     uint64_t* d_scan_tmp = static_cast<uint64_t*>(dev_alloc(c, (scan_tmp_entries(n_targets) + 1) * sizeof(uint64_t)));
@@ -881,16 +904,31 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     segment_totals_kernel<<<(nb + 255) / 256, 256, 0, st>>>(d_prim_off, d_bprefix, nb, d_totals);
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
-    std::vector<uint64_t> totals(bern.size());
-    SNC_CUDA(c, cudaMemcpyAsync(totals.data(), d_totals, bern.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    c->stats.d2h_bytes += bern.size() * sizeof(uint64_t);
-    SNC_CUDA(c, cudaStreamSynchronize(st));
-    for (size_t bi = 0; bi < bern.size(); ++bi) cnt[bern[bi]] = totals[bi];
+    if (graph_pad) {
+      // Capacity: the total is a sum of Binomial counts over at most ns * nt
+      // pairs; mean + 10 sd + 32 is exceeded with probability below e^-48
+      // (Bernstein), and a replay that does exceed it reports an error.
+      for (size_t bi = 0; bi < bern.size(); ++bi) {
+        const Projection& p = *ups[bern[bi]].p;
+        const double pairs = static_cast<double>(p.src.n) * static_cast<double>(p.tgt.n);
+        const double q = std::min(1.0, std::max(0.0, p.rule.p));
+        const double bound = std::ceil(pairs * q + 10.0 * std::sqrt(pairs * q * (1.0 - q)) + 32.0);
+        cnt[bern[bi]] = static_cast<uint64_t>(std::min(bound, pairs));
+      }
+      d_bern_list = d_blist;
+      d_bern_totals = d_totals;
+    } else {
+      std::vector<uint64_t> totals(bern.size());
+      SNC_CUDA(c, cudaMemcpyAsync(totals.data(), d_totals, bern.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+      c->stats.d2h_bytes += bern.size() * sizeof(uint64_t);
+      SNC_CUDA(c, cudaStreamSynchronize(st));
+      for (size_t bi = 0; bi < bern.size(); ++bi) cnt[bern[bi]] = totals[bi];
+      dev_free(c, d_blist);
+      dev_free(c, d_totals);
+    }
     dev_free(c, d_counts);
     dev_free(c, d_scan_tmp);
-    dev_free(c, d_blist);
     dev_free(c, d_bprefix);
-    dev_free(c, d_totals);
   }
   mark();
 
@@ -996,6 +1034,31 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   SNC_CUDA(c, upload(c, d_seg, seg_begin.data(), n_members * sizeof(uint64_t)));
   SNC_CUDA(c, upload(c, d_seg + n_members, seg_end.data(), n_members * sizeof(uint64_t)));
   SNC_CUDA(c, upload(c, d_tile_begin, tile_begin.data(), (n_members + 1) * sizeof(uint32_t)));
+  // graph_pad: the index sees each network's real positions only ([begin,
+  // begin + drawn count)); the sort sorts whole segments, padding last.
+  uint64_t* d_seg_real = d_seg;
+  uint64_t* d_real_count = nullptr;
+  if (graph_pad) {
+    std::vector<uint64_t> fixed(n_members, 0);
+    std::vector<uint32_t> bern_member;
+    for (size_t i = 0; i < np; ++i)
+      if (ups[i].p->rule.kind != SNC_PAIRWISE_BERNOULLI) fixed[ups[i].member] += cnt[i];
+    for (uint32_t i : bern) bern_member.push_back(static_cast<uint32_t>(ups[i].member));
+    d_seg_real = static_cast<uint64_t*>(dev_alloc(c, 2 * static_cast<size_t>(n_members) * sizeof(uint64_t)));
+    d_real_count = static_cast<uint64_t*>(dev_alloc(c, static_cast<size_t>(n_members) * sizeof(uint64_t)));
+    uint64_t* d_fixed = static_cast<uint64_t*>(dev_alloc(c, static_cast<size_t>(n_members) * sizeof(uint64_t)));
+    uint32_t* d_bern_member = static_cast<uint32_t*>(dev_alloc(c, bern_member.size() * sizeof(uint32_t)));
+    if (!d_seg_real || !d_real_count || !d_fixed || !d_bern_member)
+      return fail(c, SNC_ERR_OOM, "device allocation failed (network counts)");
+    SNC_CUDA(c, upload(c, d_seg_real, seg_begin.data(), n_members * sizeof(uint64_t)));
+    SNC_CUDA(c, upload(c, d_fixed, fixed.data(), n_members * sizeof(uint64_t)));
+    SNC_CUDA(c, upload(c, d_bern_member, bern_member.data(), bern_member.size() * sizeof(uint32_t)));
+    member_real_kernel<<<(n_members + 255) / 256, 256, 0, st>>>(d_bern_totals, d_bern_member,
+                                                                static_cast<int>(bern.size()), d_fixed, d_seg_real,
+                                                                n_members, d_seg_real + n_members, d_real_count);
+    ++c->stats.kernel_launches;
+    SNC_CUDA(c, cudaGetLastError());
+  }
   const bool key32 = c->layout.key32();
   const size_t key_bytes = key32 ? sizeof(uint32_t) : sizeof(uint64_t);
   // COPASS block sort (Appendix A): the pairs are sorted in place in blocks,
@@ -1108,8 +1171,18 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       dev_free(c, d_sprefix);
     }
   }
+  if (graph_pad && !bern.empty()) {
+    const uint64_t pad_key = (c->layout.total_bits() >= 64) ? ~0ull : ((1ull << c->layout.total_bits()) - 1ull);
+    const dim3 pgrid(static_cast<unsigned>(std::max<uint64_t>(1, static_cast<uint64_t>(c->sms))),
+                     static_cast<unsigned>(std::min<size_t>(bern.size(), 65535)));
+    bern_pad_kernel<<<pgrid, 256, 0, st>>>(g, d_proj, d_bern_list, static_cast<int>(bern.size()), d_bern_totals,
+                                           pad_key);
+    ++c->stats.kernel_launches;
+    SNC_CUDA(c, cudaGetLastError());
+  }
   // fixed_total_number with redraws: all such projections together, one
-  // read-back of the pending count per round.
+  // read-back of the pending count per round (a graph build: a fixed number
+  // of rounds with the count on the device).
   {
     std::vector<RedrawProj> rps;
     uint64_t n_slots = 0, n_table = 0, n_chunks_r = 0;
@@ -1208,7 +1281,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       a.lost = bucketed ? nullptr : static_cast<uint8_t*>(dev_alloc(c, n_slots));
       uint64_t* pend_a = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
       uint64_t* pend_b = static_cast<uint64_t*>(dev_alloc(c, n_slots * sizeof(uint64_t)));
-      a.n_next = static_cast<unsigned long long*>(dev_alloc(c, sizeof(unsigned long long)));
+      // Two pending counters: a graph build keeps each round's count on the
+      // device (the round reads one, fills the other).
+      a.n_next = static_cast<unsigned long long*>(dev_alloc(c, 2 * sizeof(unsigned long long)));
       if (!d_rp || !a.pairs || (!bucketed && !a.lost) || !pend_a || !pend_b || !a.n_next)
         return fail(c, SNC_ERR_OOM, "device allocation failed (redraw lists)");
       if (n_table > 0) {
@@ -1292,7 +1367,46 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       SNC_CUDA(c, cudaGetLastError());
       uint64_t* pending = pend_a;
       uint64_t* next = pend_b;
-      for (uint32_t round = 1;; ++round) {
+      if (graph_build) {
+        // A pending slot redraws until its pair is free: it fails a round with
+        // probability at most q (the share of pairs already taken, or of
+        // pairs joining a node to itself), so after R rounds about
+        // n_slots * q^R remain; R is chosen for 10^-12.  Rounds with nothing
+        // pending cost a launch each; a replay with slots still pending after
+        // the last round reports TIMEOUT.
+        double q = 0.0;
+        for (const RedrawProj& r : rps) {
+          const Projection& p = *ups[r.proj].p;
+          const double pairs = std::max(1.0, static_cast<double>(p.src.n) * static_cast<double>(p.tgt.n));
+          double f = p.rule.allow_autapses ? 0.0 : 1.0 / std::max(1u, std::min(p.src.n, p.tgt.n));
+          if (!p.rule.allow_multapses) f += static_cast<double>(cnt[r.proj]) / pairs;
+          q = std::max(q, std::min(f, 1.0));
+        }
+        const double need = (std::log(static_cast<double>(n_slots) + 1.0) + 12.0 * std::log(10.0)) /
+                            std::max(1e-9, -std::log(std::max(q, 1e-300)));
+        if (q >= 1.0 || need > 512.0)
+          return fail(c, SNC_ERR_UNSUPPORTED,
+                      "graph build: fixed_total_number without multapses at this density needs host-driven rounds");
+        const uint32_t rounds = static_cast<uint32_t>(std::max(2.0, std::ceil(need)));
+        unsigned long long* cur_n = a.n_next;  // round 0 filled pend_a and this counter
+        unsigned long long* nxt_n = a.n_next + 1;
+        for (uint32_t round = 1; round <= rounds; ++round) {
+          RedrawArgs ar = a;
+          ar.next_pending = next;
+          ar.n_next = nxt_n;
+          SNC_CUDA(c, cudaMemsetAsync(nxt_n, 0, sizeof(unsigned long long), st));
+          redraw_claim_kernel<<<grid_for(n_slots), 256, 0, st>>>(ar, pending, 0, round, cur_n);
+          redraw_resolve_kernel<<<grid_for(n_slots), 256, 0, st>>>(ar, pending, 0, cur_n);
+          c->stats.kernel_launches += 2;
+          SNC_CUDA(c, cudaGetLastError());
+          std::swap(pending, next);
+          std::swap(cur_n, nxt_n);
+        }
+        redraw_rounds_check_kernel<<<1, 32, 0, st>>>(cur_n, S.d_err);
+        ++c->stats.kernel_launches;
+        SNC_CUDA(c, cudaGetLastError());
+      }
+      for (uint32_t round = 1; !graph_build; ++round) {
         SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned, a.n_next, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         c->stats.d2h_bytes += sizeof(uint64_t);
         SNC_CUDA(c, cudaStreamSynchronize(st));
@@ -1302,8 +1416,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         if (n_pend > n_slots) return fail(c, SNC_ERR_CUDA, "fixed_total_number: pending list overflow (internal error)");
         a.next_pending = next;
         SNC_CUDA(c, cudaMemsetAsync(a.n_next, 0, sizeof(unsigned long long), st));
-        redraw_claim_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend, round);
-        redraw_resolve_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend);
+        redraw_claim_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend, round, nullptr);
+        redraw_resolve_kernel<<<grid_for(n_pend), 256, 0, st>>>(a, pending, n_pend, nullptr);
         c->stats.kernel_launches += 2;
         SNC_CUDA(c, cudaGetLastError());
         std::swap(pending, next);
@@ -1528,9 +1642,9 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     ia.group_cap = group_cap;
     ia.n_groups = S.d_n_groups;
     ia.err = S.d_err;
-    ia.n_seg = segmented ? n_members : 0;
-    ia.seg_begin = d_seg;
-    ia.seg_end = d_seg + n_members;
+    ia.n_seg = (segmented || graph_pad) ? n_members : 0;
+    ia.seg_begin = d_seg_real;
+    ia.seg_end = d_seg_real + n_members;
     const unsigned igrid = static_cast<unsigned>(std::min<uint64_t>(iblocks, static_cast<uint64_t>(c->sms) * 8));
     SNC_CUDA(c, launch_index_unpack(ia, igrid, st));
     ++c->stats.kernel_launches;
@@ -1547,8 +1661,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   mi.key32 = key32 ? 1 : 0;
   mi.delay_bits = c->layout.delay_bits;
   mi.n_members = n_members;
-  mi.seg_begin = d_seg;
-  mi.seg_end = d_seg + n_members;
+  mi.seg_begin = d_seg_real;
+  mi.seg_end = d_seg_real + n_members;
   mi.local_base = d_local_base;
   mi.n_entries = n_local;
   mi.group_first = u_group_first;
@@ -1587,6 +1701,17 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   SNC_CUDA(c, cudaMemcpyAsync(S.h_bases, S.d_bases, (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t),
                               cudaMemcpyDeviceToHost, st));
   c->stats.d2h_bytes += (static_cast<size_t>(n_members) + 1) * sizeof(uint64_t);
+  S.real_counts = graph_pad;
+  if (graph_pad) {
+    if (!S.h_real) {
+      S.h_real_words = static_cast<size_t>(n_members);
+      S.h_real = static_cast<uint64_t*>(pinned_pool().get(S.h_real_words * sizeof(uint64_t)));
+      if (!S.h_real) return fail(c, SNC_ERR_OOM, "pinned allocation failed (views)");
+    }
+    SNC_CUDA(c, cudaMemcpyAsync(S.h_real, d_real_count, static_cast<size_t>(n_members) * sizeof(uint64_t),
+                                cudaMemcpyDeviceToHost, st));
+    c->stats.d2h_bytes += static_cast<size_t>(n_members) * sizeof(uint64_t);
+  }
   mark();
   dev_free(c, starts);
   dev_free(c, bcounts);
@@ -1599,6 +1724,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
   dev_free(c, d_seg);
   dev_free(c, d_tile_begin);
   dev_free(c, d_local_base);
+  dev_free(c, d_bern_list);
+  dev_free(c, d_bern_totals);
 
   S.n_members = n_members;
   S.n_total = n_conn;
@@ -1687,15 +1814,11 @@ snc_status snc_batch_finalize(snc_ctx* const* ctxs, int n) {
 }
 
 namespace {
-// A graph build replays the recorded device work: it needs every count known
-// on the host before generation (no pairwise_bernoulli count phase, no
-// total-number redraw rounds).
-bool graph_eligible(const snc_ctx* c) {
-  if (c->sharded) return false;  // the kept count is read back before the sort
-  for (const Projection& p : c->projs)
-    if (p.rule.kind == SNC_PAIRWISE_BERNOULLI || is_total_redraw(p)) return false;
-  return true;
-}
+// A graph build replays the recorded device work with every size fixed:
+// pairwise_bernoulli projections get capacities, total-number redraws a
+// fixed number of rounds (finalize_build); a target shard reads its kept
+// count back before the sort and is built alone.
+bool graph_eligible(const snc_ctx* c) { return !c->sharded; }
 }  // namespace
 
 snc_status snc_batch_finalize_graph(snc_ctx* const* ctxs, int n) {
@@ -1710,8 +1833,7 @@ snc_status snc_batch_finalize_graph(snc_ctx* const* ctxs, int n) {
       for (int j = 0; j < i; ++j)
         if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SNC_ERR_INVALID_ARG, "batch: context listed twice");
       if (!graph_eligible(ctxs[i]))
-        return fail(ctxs[i], SNC_ERR_UNSUPPORTED,
-                    "graph build: pairwise_bernoulli and total-number redraws need host round trips");
+        return fail(ctxs[i], SNC_ERR_UNSUPPORTED, "graph build: a target shard is built alone");
     }
     snc_ctx* c = ctxs[0];
     Storage& S = *c->store;
@@ -1804,7 +1926,7 @@ snc_status snc_synchronize(snc_ctx* c) {
     }
     if (!c->view_ready || c->view_gen != S.generation) {
       const uint64_t g0 = S.h_bases[c->member], g1 = S.h_bases[c->member + 1];
-      c->n_syn = c->seg_count;
+      c->n_syn = S.real_counts ? S.h_real[c->member] : c->seg_count;
       c->n_groups = g1 - g0;
       c->target = c->target_all + c->seg_begin;
       c->delay = c->delay_all + c->seg_begin;
@@ -1816,6 +1938,10 @@ snc_status snc_synchronize(snc_ctx* c) {
     const uint32_t err = S.err_bits;
     if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
     if (err & kErrSamplerBound) return fail(c, SNC_ERR_TIMEOUT, "a sampler exceeded its attempt bound");
+    if (err & kErrGraphRounds)
+      return fail(c, SNC_ERR_TIMEOUT, "graph replay: total-number redraws still pending after the recorded rounds");
+    if (err & kErrGraphCapacity)
+      return fail(c, SNC_ERR_UNSUPPORTED, "graph replay: a pairwise_bernoulli projection drew past its capacity");
     if (err & kErrBounds) {
       const uint32_t* w = reinterpret_cast<const uint32_t*>(S.h_pinned + 4);
       return fail(c, SNC_ERR_CUDA, "a device index check failed (site %u, index %llu, limit %llu)", w[2],

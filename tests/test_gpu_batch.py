@@ -117,12 +117,73 @@ def test_graph_rebuild_equals_plain_builds_with_new_seeds(snc, oracle_mod):
         net.close()
 
 
-def test_graph_build_refuses_host_round_trips(snc):
-    for spec in (W.two_population(100, "pairwise_bernoulli", p=0.1, seed=1),
-                 W.two_population(100, "fixed_total_number", k=500, autapses=False, multapses=False, seed=2)):
-        with pytest.raises(snc.SncError) as e:
-            snc.Network.batch_graph([W.plain_indegree(n=50, k=5), spec])
-        assert e.value.name == "UNSUPPORTED"
+def _graph_trials(snc, oracle_mod, specs, offsets, oracle_members):
+    """Graph build of `specs`, then rebuilds with shifted seeds: every member
+    equals its single build with those seeds (and the oracle for the members
+    listed), and the original seeds give the first result back."""
+    from dataclasses import replace
+    fields = ("src", "tgt", "delay", "weight", "row_ptr", "group_ptr", "group_first")
+    nets = snc.Network.batch_graph(specs)
+    try:
+        first = [net.to_host() for net in nets]
+        for trial, offset in enumerate((0,) + tuple(offsets)):
+            seeds = [sp.seed + offset + i * (offset > 0) for i, sp in enumerate(specs)]
+            if offset:
+                nets[-1].rebuild(seeds)
+            for i, (spec, net) in enumerate(zip(specs, nets)):
+                got = net.to_host()
+                ref_spec = replace(spec, seed=seeds[i])
+                single = snc.Network(ref_spec).finalize()
+                alone = single.to_host()
+                single.close()
+                assert int(net.view().n_syn) == alone["tgt"].size, (trial, i)
+                for f in fields:
+                    np.testing.assert_array_equal(got[f], alone[f], err_msg=f"trial {trial} member {i} {f}")
+                assert got["n_groups"] == alone["n_groups"]
+                if i in oracle_members:
+                    assert_network_equal(got, oracle_mod.build(ref_spec), f"trial {trial} member {i} vs oracle")
+        nets[0].rebuild([sp.seed for sp in specs])
+        for i, net in enumerate(nets):
+            got = net.to_host()
+            for f in fields:
+                np.testing.assert_array_equal(got[f], first[i][f], err_msg=f"replay {i} {f}")
+    finally:
+        for net in reversed(nets):
+            net.close()
+
+
+def test_graph_rebuild_of_seed_dependent_counts(snc, oracle_mod):
+    """Every rule in a graph build: pairwise_bernoulli totals (capacity and
+    padding) and fixed_total_number redraws (device-counted rounds) change
+    with the seed at every replay."""
+    specs = [
+        W.two_population(333, "pairwise_bernoulli", p=0.05, autapses=False, seed=2),
+        W.two_population(500, "fixed_total_number", k=40_000, autapses=False, multapses=False, seed=3),
+        W.two_population(700, "fixed_indegree", k=31, autapses=False, seed=1),
+        W.two_population(256, "pairwise_bernoulli", p=0.2, autapses=True, seed=4),  # 512 nodes: 2^9
+        W.two_population(300, "fixed_total_number", k=20_000, autapses=False, multapses=True, seed=5),
+        W.two_population(90, "all_to_all", autapses=False, seed=6),
+    ] + W.batched_sweep(count=6, scale=0.05)
+    _graph_trials(snc, oracle_mod, specs, (1000, 2000), oracle_members=(0, 1, 3))
+
+
+@pytest.mark.parametrize("spec", [
+    W.two_population(512, "pairwise_bernoulli", p=0.03, autapses=False, seed=41),
+    W.two_population(400, "fixed_total_number", k=30_000, autapses=False, multapses=False, seed=42),
+], ids=["bernoulli", "total_nomult"])
+def test_graph_rebuild_single_network(snc, oracle_mod, spec):
+    """A graph build of one network (digit counts fused in generation,
+    padding counted by its own kernel)."""
+    _graph_trials(snc, oracle_mod, [spec], (1000, 2000), oracle_members=(0,))
+
+
+def test_graph_build_refuses_what_it_cannot_replay(snc):
+    # A fixed_total_number without multapses taking almost every pair would
+    # need more than 512 device-counted rounds.
+    dense = W.two_population(40, "fixed_total_number", k=1500, autapses=False, multapses=False, seed=2)
+    with pytest.raises(snc.SncError) as e:
+        snc.Network.batch_graph([W.plain_indegree(n=50, k=5), dense])
+    assert e.value.name == "UNSUPPORTED"
     net = snc.Network(W.plain_indegree(n=50, k=5)).finalize()
     with pytest.raises(snc.SncError) as e:
         net.rebuild([1])
