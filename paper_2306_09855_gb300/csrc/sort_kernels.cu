@@ -630,7 +630,6 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
   static_assert(RADIX % TPB == 0, "radix must be a multiple of the block size");
   extern __shared__ __align__(128) unsigned char smem[];
   uint16_t* wcnt = reinterpret_cast<uint16_t*>(smem + C::kOffCnt);
-  uint32_t* local_start = reinterpret_cast<uint32_t*>(smem + C::kOffLocal);
   uint64_t* globm = reinterpret_cast<uint64_t*>(smem + C::kOffGlob);  // global position of local index 0
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kOffBar);
   __shared__ uint32_t ticket_sh;
@@ -786,6 +785,10 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       }
     }
     __syncthreads();
+    // Per digit (this thread's DPT digits): the tile's count, then, after the
+    // block scan, each warp's first staging position (digit start plus the
+    // counts of the warps before it) in place of its count, so that staging
+    // reads one offset per key.
     uint32_t tot[DPT];
     uint32_t tsum = 0;
 #pragma unroll
@@ -793,11 +796,7 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       const int d = tid * DPT + q;
       uint32_t r = 0;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const uint32_t c = wcnt[w * RADIX + d];
-        wcnt[w * RADIX + d] = static_cast<uint16_t>(r);
-        r += c;
-      }
+      for (int w = 0; w < NW; ++w) r += wcnt[w * RADIX + d];
       tot[q] = r;
       tsum += r;
     }
@@ -809,8 +808,15 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
     uint32_t my_start[DPT];
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
+      const int d = tid * DPT + q;
       my_start[q] = excl;
-      local_start[tid * DPT + q] = excl;
+      uint32_t run = excl;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = wcnt[w * RADIX + d];
+        wcnt[w * RADIX + d] = static_cast<uint16_t>(run);
+        run += c;
+      }
       excl += tot[q];
     }
     __syncthreads();
@@ -824,7 +830,7 @@ __global__ void __launch_bounds__(kSortThreads, (OnesweepTma<BITS, ITEMS, K, V>:
       const uint32_t li = wbase + static_cast<uint32_t>(j) * 32u + lane;
       if (li < valid) {
         const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & mask;
-        const uint32_t lp = local_start[d] + wcnt[warp * RADIX + d] + rank[j];
+        const uint32_t lp = wcnt[warp * RADIX + d] + rank[j];
         rank[j] = lp;
         if (SNC_IN_BOUNDS(a.err, 10u, lp, TILE)) skeys[lp] = key[j];
       }
