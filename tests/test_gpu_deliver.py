@@ -116,3 +116,28 @@ def test_batch_member_delivery(snc, oracle_mod):
     finally:
         for net in reversed(nets):
             net.close()
+
+
+@pytest.mark.parametrize("spec", [
+    W.rule_sweep("fixed_indegree", True, scale=0.05),
+    W.microcircuit(scale=0.05),
+], ids=["indegree", "microcircuit"])
+def test_delivery_on_the_gpus_own_network(snc, oracle_mod, spec):
+    """The oracle's delivery run on the arrays the GPU built (row_ptr,
+    group_ptr, group_first, target, weight), so both sums add the same fp32
+    weights: only the summation order differs, and the bound is that of fp32
+    summation alone, (terms + 1) * 2^-24 * sum |w * m|, with no weight term."""
+    net = snc.Network(spec).finalize()
+    try:
+        gpu_net = net.to_host()
+        rng = np.random.default_rng(23)
+        for n in (1000, 50_000):
+            src, grp, mult = _spikes(rng, gpu_net, spec.n_nodes, n)
+            got = _deliver_gpu(net, src, grp, mult, spec.n_nodes)
+            ref = oracle_mod.deliver(gpu_net, spec.n_nodes, src, grp, mult)
+            assert ref["bad"] == 0
+            tol = (ref["terms"].astype(np.float64) + 1.0) * 2.0 ** -24 * ref["abs"] * 1.01 + 1e-30
+            err = np.abs(got.astype(np.float64) - ref["input"])
+            assert np.all(err <= tol), (float(err.max()), int(np.argmax(err - tol)))
+    finally:
+        net.close()
