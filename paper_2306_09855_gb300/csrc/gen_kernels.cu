@@ -245,8 +245,10 @@ __device__ __forceinline__ void direct_chunk(const GenArgs& a, const BlockHist& 
           uint64_t b, j;
           if (P.count <= 0xFFFFFFFFull) {
             const uint32_t ii = static_cast<uint32_t>(i), kk = static_cast<uint32_t>(P.k);
-            b = ii / kk;
-            j = ii - static_cast<uint32_t>(b) * kk;
+            const uint32_t t = __umulhi(ii, P.k_mul);
+            const uint32_t bq = (t + ((ii - t) >> P.k_sh1)) >> P.k_sh2;  // ii / kk
+            b = bq;
+            j = ii - bq * kk;
           } else {
             b = i / P.k;
             j = i - b * P.k;
@@ -292,7 +294,7 @@ __device__ __forceinline__ void direct_chunk(const GenArgs& a, const BlockHist& 
 // each lane computes one IDX draw (four target words) for the window and the
 // words are passed around with shuffles.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
+__global__ void __launch_bounds__(kGenThreads, 4) gen_direct_kernel(GenArgs a) {
   extern __shared__ uint32_t smem_raw[];
   const uint32_t hw = hist_words(a);
   SmemTables tabs{smem_raw + hw, reinterpret_cast<uint16_t*>(smem_raw + hw + a.max_delay_len)};
@@ -308,7 +310,9 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(GenArgs a) {
       __syncthreads();
       cur = p;
     }
-    const DevProj& P = a.projs[p];
+    // A copy in registers: the output stores below cannot alias it, so its
+    // fields are not read again after every store.
+    const DevProj P = a.projs[p];
     const uint64_t lc = c - P.chunk_begin;
     if (has_arrays(P))
       direct_chunk<true>(a, bh, tabs, P, lc, warp, lane);
@@ -535,7 +539,7 @@ __global__ void sampler_kernel(SamplerArgs a) {
 
   for (uint64_t gp = gw; gp < total; gp += n_warps) {
     const int j = find_segment(a.prim_prefix, a.n_list, gp);
-    const DevProj& P = a.projs[a.list[j]];
+    const DevProj P = a.projs[a.list[j]];
     if (j != cur) {
       // This warp's copy of the projection's delay table.
       if (P.d_table) {
