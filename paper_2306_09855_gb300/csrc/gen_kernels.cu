@@ -292,7 +292,9 @@ __device__ __forceinline__ void direct_chunk(const GenArgs& a, const BlockHist& 
 // (for all_to_all: kChunk consecutive targets of one source row).  A warp
 // works on windows of 128 consecutive connections; for fixed_total_number
 // each lane computes one IDX draw (four target words) for the window and the
-// words are passed around with shuffles.
+// words are passed around with shuffles.  At least four blocks per SM (64
+// registers): with the projection record in registers the kernel would
+// otherwise take 88 and run two blocks per SM, measured slower.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kGenThreads, 4) gen_direct_kernel(GenArgs a) {
   extern __shared__ uint32_t smem_raw[];
