@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "connections built/sec (generate+sort+index) on 1 GB300, % HBM roofline; p50/p99 latency"
-E2E_STEPS = 2  # timed end-to-end passes, after one untimed pass
+E2E_STEPS = 3  # timed end-to-end passes, after one untimed pass
 
 
 def parse_args():
@@ -648,12 +648,39 @@ def extra_batched(torch, snc, local, stream, steps=3, warm=2):
         dig_s = [_digest(torch, x) for x in nets_s]
         for x in reversed(nets_s):
             x.close()
+        # The same 64 as one recorded CUDA graph, rebuilt with new seeds per
+        # step (Bernoulli totals and redraw rounds decided on the device),
+        # then with the original seeds again (must equal the batched build).
+        gnets = snc.Network.batch_graph(specs, device=local, stream=stream)
+        try:
+            def rebuild(step):
+                def fn():
+                    gnets[0].rebuild([sp.seed + 1000 * (step + 1) for sp in specs])
+                    return sum(int(x.view().n_syn) for x in gnets)
+                return fn
+            for w in range(warm):
+                rebuild(w)()
+            g_ms, g_n = 0.0, 0
+            for k in range(steps):
+                ms, n = _device_ms(torch, stream, rebuild(warm + k))
+                g_ms += ms
+                g_n += n
+            gnets[0].rebuild([sp.seed for sp in specs])
+            dig_g = [_digest(torch, x) for x in gnets]
+        finally:
+            for x in reversed(gnets):
+                x.close()
     finally:
         snc.snc_set_tuning(sort_digit_bits=saved.sort_digit_bits, sort_group_tiles=saved.sort_group_tiles,
                            gen_blocks_per_sm=saved.gen_blocks_per_sm, sort_items=saved.sort_items)
     return {"value": v_b, "unit": "connections/s", "ms_per_build": ms_b, "connections": n_b,
             "sequential_builds": {"value": v_s, "unit": "connections/s", "ms": ms_s, "connections": n_s},
             "speedup": v_b / v_s, "identical": dig_b == dig_s and n_b == n_s,
+            "graph_rebuild": {"value": g_n / (g_ms / 1e3), "unit": "connections/s", "ms_per_build": g_ms / steps,
+                              "identical_at_the_original_seeds": dig_g == dig_b,
+                              "note": "the 64 networks recorded once as a CUDA graph (snc_batch_finalize_graph) "
+                                      "and rebuilt with new seeds per step (snc_batch_rebuild); device time "
+                                      "through the views' refresh"},
             "tuning": tune_info["tuning"], "tuning_cached": tune_info["cached"],
             "workload": "64 two-population networks, N log-uniform 2,000-50,000, fixed_indegree / "
                         "fixed_total_number / pairwise_bernoulli, per-instance seeds"}
@@ -809,6 +836,12 @@ def main():
 
     host = host_arrays()
     streams = [torch.cuda.Stream(device=local) for _ in range(2)]
+    # The builds above left their device blocks in torch's cache, tied to
+    # their stream: hand them back so that the two streams below allocate
+    # their own (otherwise a full cache is emptied mid-leg, and every free
+    # waits for the whole device).
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
     def e2e_pass():
         """One end-to-end pass over every network: (connections, h2d, d2h)."""
@@ -849,8 +882,11 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     n_e2e = 0
+    e2e_pass_ms = []
     for _ in range(E2E_STEPS):
+        tp = time.perf_counter()
         n_p, h2d, d2h = e2e_pass()
+        e2e_pass_ms.append((time.perf_counter() - tp) * 1e3)
         n_e2e += n_p
     e2e_s = (time.perf_counter() - t0) / E2E_STEPS
     n_e2e //= E2E_STEPS
@@ -886,7 +922,7 @@ def main():
         "gpu_launches": launches,
         "e2e": {"value": n_e2e_all / (e2e_ms_all / 1e3), "unit": "connections/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "steps": E2E_STEPS, "warmup": 1,
+                "steps": E2E_STEPS, "warmup": 1, "pass_ms": [round(x, 1) for x in e2e_pass_ms],
                 "note": "public API, host wall clock: plan, build, and copy of each network as held on the "
                         "device (target, delay, weight: 10 B per connection; row_ptr, p_i, group_first) into "
                         "page-locked host arrays; one host thread, two streams: network k is built while "

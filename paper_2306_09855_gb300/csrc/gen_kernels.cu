@@ -393,7 +393,9 @@ __device__ __forceinline__ void sample_primary(const SamplerArgs& a, const Block
   if (want == 0) return;
   const bool complement = 2 * want > cand;
   const uint32_t need = static_cast<uint32_t>(complement ? cand - want : want);
-  for (uint32_t w = lane; w < words; w += 32) bitmap[w] = 0u;
+  // The bitmap area holds whole 16-byte units (bitmap_words is a multiple
+  // of four), so clear it with 16-byte stores.
+  for (uint32_t w = lane; w < (words + 3u) / 4u; w += 32) reinterpret_cast<uint4*>(bitmap)[w] = make_uint4(0u, 0u, 0u, 0u);
   __syncwarp();
   uint32_t got = 0;
   uint64_t call = 0;
@@ -910,7 +912,9 @@ size_t redraw_draw_smem(const GenArgs& g, const RedrawArgs& a) {
   return (words + 1) / 2 * sizeof(uint64_t) + kDrawStage * (sizeof(uint64_t) + sizeof(uint16_t));
 }
 
-__global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks) {
+// Four blocks per SM at least (64 registers), with the projection records in
+// registers (measured faster than reading them through global memory).
+__global__ void __launch_bounds__(kGenThreads, 4) redraw_draw_kernel(GenArgs g, RedrawArgs a, uint64_t total_chunks) {
   extern __shared__ uint32_t smem_raw[];
   const uint32_t hw = hist_words(g);
   SmemTables tabs{smem_raw + hw, reinterpret_cast<uint16_t*>(smem_raw + hw + g.max_delay_len)};
@@ -930,8 +934,8 @@ __global__ void __launch_bounds__(kGenThreads) redraw_draw_kernel(GenArgs g, Red
   int cur = -1;
   for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
     const int lo = chunk_owner(a, c);
-    const RedrawProj& r = a.rp[lo];
-    const DevProj& P = a.projs[r.proj];
+    const RedrawProj r = a.rp[lo];
+    const DevProj P = a.projs[r.proj];
     if (lo != cur) {
       __syncthreads();
       load_delay_table(P, g.thr_blob, g.guide_blob, tabs);

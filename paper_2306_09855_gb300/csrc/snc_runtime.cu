@@ -1150,8 +1150,10 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       s.thr_blob = d_thr;
       s.guide_blob = d_guide;
       s.max_delay_len = max_len;
-      s.table_words = max_len + (kDelayGuide + 1) / 2 + 1;
-      s.bitmap_words = (max_other + 31u) / 32u;
+      // Per-warp areas in whole 16-byte units (the bitmap is cleared with
+      // 16-byte stores).
+      s.table_words = (max_len + (kDelayGuide + 1) / 2 + 1 + 3u) & ~3u;
+      s.bitmap_words = ((max_other + 31u) / 32u + 3u) & ~3u;
       s.prim_offsets = d_prim_off;
       s.err = S.d_err;
       const size_t per_warp = static_cast<size_t>(s.bitmap_words + s.table_words) * sizeof(uint32_t);
