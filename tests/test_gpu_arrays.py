@@ -140,6 +140,36 @@ def test_batch_members_with_arrays(snc, oracle_mod):
         assert_network_equal(got[m], oracle_mod.build(spec), f"member {m}")
 
 
+def test_graph_rebuild_with_arrays(snc, oracle_mod):
+    """A graph-recorded batch whose members connect through id lists and
+    per-connection weight/delay arrays (with a Bernoulli and a no-multapse
+    total-number call): each rebuild with new seeds equals the oracle's
+    network for those seeds (the arrays are replayed from the recorded
+    copies)."""
+    from dataclasses import replace
+    rng = np.random.default_rng(12)
+    specs = []
+    for m in range(3):
+        perm = rng.permutation(900).astype(np.uint32)
+        specs.append(NetworkSpec(seed=70 + m, dt=0.1, populations=[900], projections=[
+            _proj("fixed_indegree", False, False, perm[:400], perm[200:700], rng, weights="numbers", k=25),
+            _proj("pairwise_bernoulli", False, True, perm[:300], perm[100:400], rng),
+            _proj("fixed_total_number", False, False, perm[:300], perm[300:600], rng, weights="random",
+                  delays="random", k=9_000)]))
+    nets = snc.Network.batch_graph(specs)
+    try:
+        for offset in (0, 500):
+            seeds = [sp.seed + offset for sp in specs]
+            if offset:
+                nets[0].rebuild(seeds)
+            for m, spec in enumerate(specs):
+                assert_network_equal(nets[m].to_host(), oracle_mod.build(replace(spec, seed=seeds[m])),
+                                     f"offset {offset} member {m}")
+    finally:
+        for n in reversed(nets):
+            n.close()
+
+
 def test_array_errors_match_the_oracle(snc, oracle_mod):
     """Connect refuses what the oracle's checks refuse, with the same status."""
     cases = [
