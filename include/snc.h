@@ -437,6 +437,19 @@ snc_status snc_radix_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t*
  * snc_set_wait_test(0, 0xFFFFFFFF). */
 snc_status snc_set_wait_test(uint32_t lookback_spin_limit, uint32_t withhold_tile);
 
+/* Test support for the bounds a graph-recorded build fixes when it is
+ * recorded (snc_batch_finalize_graph; no counterpart in the paper): the
+ * capacity of each pairwise_bernoulli projection is its Binomial mean +
+ * bernoulli_sd standard deviations + bernoulli_slack (defaults 10 and 32),
+ * and fixed_total_number without multapses runs redraw_rounds rounds (0 =
+ * the number computed from the density, the default).  Smaller values let a
+ * test make a replay exceed them: the replay then writes only inside its
+ * arrays and the next snc_synchronize reports UNSUPPORTED (a Bernoulli total
+ * above its capacity) or TIMEOUT (redraws still pending).  Process-wide, for
+ * graph builds recorded after the call.  INVALID_ARG: a negative value.
+ * Reset with snc_set_graph_test(10, 32, 0). */
+snc_status snc_set_graph_test(double bernoulli_sd, double bernoulli_slack, uint32_t redraw_rounds);
+
 /* Readable description of the last failure on ctx (or of the last
  * context-free failure when ctx is NULL).  Never NULL. */
 const char* snc_last_error(const snc_ctx* ctx);

@@ -595,12 +595,14 @@ __global__ void bern_pad_kernel(GenArgs g, const DevProj* projs, const uint32_t*
 }
 
 __global__ void member_real_kernel(const uint64_t* totals, const uint32_t* member, int n_list, const uint64_t* fixed,
-                                   const uint64_t* seg_begin, int n_members, uint64_t* real_end,
-                                   uint64_t* real_count) {
+                                   const uint64_t* seg_begin, const uint64_t* seg_end, int n_members,
+                                   uint64_t* real_end, uint64_t* real_count) {
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_members; m += gridDim.x * blockDim.x) {
     uint64_t cnt = fixed[m];
     for (int k = 0; k < n_list; ++k)
       if (member[k] == static_cast<uint32_t>(m)) cnt += totals[k];
+    const uint64_t cap = seg_end[m] - seg_begin[m];
+    if (cnt > cap) cnt = cap;
     real_count[m] = cnt;
     real_end[m] = seg_begin[m] + cnt;
   }

@@ -71,10 +71,12 @@ __global__ void bern_pad_kernel(GenArgs g, const DevProj* projs, const uint32_t*
                                 const uint64_t* totals, uint64_t pad_key);
 // Connections each network of the build really holds: fixed[m] plus the
 // drawn totals of its pairwise_bernoulli projections (member[k] owns
-// totals[k]); real_end[m] = seg_begin[m] + that count.
+// totals[k]), at most its segment [seg_begin[m], seg_end[m]) (a replay past
+// a capacity is reported, never read past); real_end[m] = seg_begin[m] +
+// that count.
 __global__ void member_real_kernel(const uint64_t* totals, const uint32_t* member, int n_list, const uint64_t* fixed,
-                                   const uint64_t* seg_begin, int n_members, uint64_t* real_end,
-                                   uint64_t* real_count);
+                                   const uint64_t* seg_begin, const uint64_t* seg_end, int n_members,
+                                   uint64_t* real_end, uint64_t* real_count);
 
 // fixed_total_number with autapses or multapses forbidden: the redraw
 // projections of a build, their slots concatenated.

@@ -43,6 +43,14 @@ struct DevBuf {
 // Page-locked host memory is recycled for the whole process: freeing it
 // (cudaFreeHost) would synchronize the device and stall builds running on
 // other streams when a context is destroyed.
+// Bounds a graph-recorded build fixes (snc_set_graph_test).
+struct GraphTest {
+  double bernoulli_sd = 10.0;
+  double bernoulli_slack = 32.0;
+  uint32_t redraw_rounds = 0;  // 0: computed from the density
+};
+GraphTest g_graph_test;
+
 class PinnedPool {
  public:
   static size_t round_size(size_t bytes) {
@@ -912,7 +920,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         const Projection& p = *ups[bern[bi]].p;
         const double pairs = static_cast<double>(p.src.n) * static_cast<double>(p.tgt.n);
         const double q = std::min(1.0, std::max(0.0, p.rule.p));
-        const double bound = std::ceil(pairs * q + 10.0 * std::sqrt(pairs * q * (1.0 - q)) + 32.0);
+        const double bound = std::ceil(pairs * q + g_graph_test.bernoulli_sd * std::sqrt(pairs * q * (1.0 - q)) +
+                                       g_graph_test.bernoulli_slack);
         cnt[bern[bi]] = static_cast<uint64_t>(std::min(bound, pairs));
       }
       d_bern_list = d_blist;
@@ -1055,7 +1064,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
     SNC_CUDA(c, upload(c, d_bern_member, bern_member.data(), bern_member.size() * sizeof(uint32_t)));
     member_real_kernel<<<(n_members + 255) / 256, 256, 0, st>>>(d_bern_totals, d_bern_member,
                                                                 static_cast<int>(bern.size()), d_fixed, d_seg_real,
-                                                                n_members, d_seg_real + n_members, d_real_count);
+                                                                d_seg + n_members, n_members, d_seg_real + n_members,
+                                                                d_real_count);
     ++c->stats.kernel_launches;
     SNC_CUDA(c, cudaGetLastError());
   }
@@ -1389,7 +1399,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         if (q >= 1.0 || need > 512.0)
           return fail(c, SNC_ERR_UNSUPPORTED,
                       "graph build: fixed_total_number without multapses at this density needs host-driven rounds");
-        const uint32_t rounds = static_cast<uint32_t>(std::max(2.0, std::ceil(need)));
+        const uint32_t rounds = g_graph_test.redraw_rounds ? g_graph_test.redraw_rounds
+                                                           : static_cast<uint32_t>(std::max(2.0, std::ceil(need)));
         unsigned long long* cur_n = a.n_next;  // round 0 filled pend_a and this counter
         unsigned long long* nxt_n = a.n_next + 1;
         for (uint32_t round = 1; round <= rounds; ++round) {
@@ -2188,6 +2199,17 @@ snc_status snc_set_wait_test(uint32_t lookback_spin_limit, uint32_t withhold_til
   return snc::abi_guard([&]() -> snc_status {
     g_wait_test.lookback_spin_limit = lookback_spin_limit ? lookback_spin_limit : kDefaultSpinLimit;
     g_wait_test.withhold_unit = withhold_tile;
+    return SNC_OK;
+  });
+}
+
+snc_status snc_set_graph_test(double bernoulli_sd, double bernoulli_slack, uint32_t redraw_rounds) {
+  return snc::abi_guard([&]() -> snc_status {
+    if (!(bernoulli_sd >= 0.0) || !(bernoulli_slack >= 0.0))
+      return fail(nullptr, SNC_ERR_INVALID_ARG, "graph test: negative capacity margin");
+    g_graph_test.bernoulli_sd = bernoulli_sd;
+    g_graph_test.bernoulli_slack = bernoulli_slack;
+    g_graph_test.redraw_rounds = redraw_rounds;
     return SNC_OK;
   });
 }

@@ -120,7 +120,7 @@ EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", 
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_block_sort_pairs", "snc_set_block_sort",
            "snc_get_stats",
            "snc_set_tuning", "snc_get_tuning", "snc_batch_finalize", "snc_batch_finalize_graph",
-           "snc_batch_rebuild", "snc_set_wait_test", "snc_last_error",
+           "snc_batch_rebuild", "snc_set_wait_test", "snc_set_graph_test", "snc_last_error",
            "snc_server_create", "snc_server_destroy", "snc_server_submit", "snc_server_poll",
            "snc_server_wait_any", "snc_server_context", "snc_server_times", "snc_server_release",
            "snc_server_get_stats", "snc_estimate_build")
@@ -167,6 +167,7 @@ def load(build: bool = True):
         "snc_set_tuning": ([ctypes.POINTER(snc_tuning)], I32),
         "snc_get_tuning": ([ctypes.POINTER(snc_tuning)], I32),
         "snc_set_wait_test": ([U32, U32], I32),
+        "snc_set_graph_test": ([ctypes.c_double, ctypes.c_double, U32], I32),
         "snc_last_error": ([P], ctypes.c_char_p),
         "snc_server_create": ([ctypes.POINTER(snc_server_config), ctypes.POINTER(P)], I32),
         "snc_server_destroy": ([P], I32),
@@ -350,6 +351,12 @@ def snc_block_sort_pairs(keys, vals, n, key_bits, block, stream=0):
 
 def snc_set_block_sort(ctx, block):
     _check(load().snc_set_block_sort(ctx, int(block)), ctx)
+
+
+def snc_set_graph_test(bernoulli_sd=10.0, bernoulli_slack=32.0, redraw_rounds=0):
+    """Test hook: the bounds graph-recorded builds fix (Bernoulli capacity
+    margin, redraw rounds); snc_set_graph_test() restores the defaults."""
+    _check(load().snc_set_graph_test(float(bernoulli_sd), float(bernoulli_slack), int(redraw_rounds)))
 
 
 def snc_set_wait_test(lookback_spin_limit=0, withhold_tile=0xFFFFFFFF):

@@ -236,3 +236,64 @@ def test_graph_built_networks_free_call_buffers(snc):
     finally:
         for net in reversed(nets):
             net.close()
+
+
+def test_graph_replay_past_its_bounds_is_reported(snc, oracle_mod):
+    """A replay that draws more Bernoulli connections than a projection's
+    recorded capacity, or that still has redraws pending after the recorded
+    rounds, is reported at the next synchronize (UNSUPPORTED, TIMEOUT) and
+    writes nothing outside the build's arrays; the replays that stay inside
+    their bounds give the single build's network.  The capacities are made
+    small (mean + 1 sd) with the test hook, and the oracle's per-projection
+    totals say in advance which seeds exceed them."""
+    import math
+    from dataclasses import replace
+    n, p = 300, 0.05
+    spec = W.two_population(n, "pairwise_bernoulli", p=p, autapses=False, seed=21)
+    pairs = n * n
+    cap = min(pairs, math.ceil(pairs * p + 1.0 * math.sqrt(pairs * p * (1.0 - p))))
+    fields = ("src", "tgt", "delay", "weight", "row_ptr", "group_ptr", "group_first")
+
+    def exceeds(seed):
+        ref = oracle_mod.build(replace(spec, seed=seed))
+        s, t = ref["src"].astype(np.int64), ref["tgt"].astype(np.int64)
+        counts = [int(np.sum((s // n == a) & (t // n == b))) for a in (0, 1) for b in (0, 1)]
+        return max(counts) > cap
+
+    try:
+        snc.snc_set_graph_test(1.0, 0.0, 0)
+        nets = snc.Network.batch_graph([spec])
+        outcomes = set()
+        for seed in range(100, 112):
+            nets[0].rebuild([seed])
+            over = exceeds(seed)
+            outcomes.add(over)
+            if over:
+                with pytest.raises(snc.SncError) as e:
+                    nets[0].synchronize()
+                assert e.value.name == "UNSUPPORTED", seed
+            else:
+                got = nets[0].to_host()
+                single = snc.Network(replace(spec, seed=seed)).finalize()
+                alone = single.to_host()
+                single.close()
+                for f in fields:
+                    np.testing.assert_array_equal(got[f], alone[f], err_msg=f"seed {seed} {f}")
+        assert outcomes == {True, False}  # both kinds of replay were exercised
+        nets[0].close()
+        # One redraw round for a total-number call that takes half of the pairs.
+        snc.snc_set_graph_test(10.0, 32.0, 1)
+        dense = W.two_population(100, "fixed_total_number", k=5_000, autapses=False, multapses=False, seed=23)
+        nets = snc.Network.batch_graph([dense])
+        with pytest.raises(snc.SncError) as e:
+            nets[0].synchronize()
+        assert e.value.name == "TIMEOUT"
+        nets[0].close()
+    finally:
+        snc.snc_set_graph_test()
+    # Back to the recorded defaults: the same networks build and replay correctly.
+    nets = snc.Network.batch_graph([spec])
+    nets[0].rebuild([101])
+    got = nets[0].to_host()
+    nets[0].close()
+    assert_network_equal(got, oracle_mod.build(replace(spec, seed=101)), "defaults again")
