@@ -757,13 +757,17 @@ def main():
     barrier()
     start.record(stream)
     n_total = 0
+    marks = []  # one event after each step (recorded in order; read after the final synchronize)
     for _ in range(args.steps):
         n_total += one_step(records)
+        marks.append(torch.cuda.Event(enable_timing=True))
+        marks[-1].record(stream)
     end.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     ms = start.elapsed_time(end)
+    step_ms = [start.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, len(marks))]
     ms, n_all = replicas.reduce_timing(ms, n_total, device="cuda")
     value = n_all / (ms / 1e3)
 
@@ -772,20 +776,30 @@ def main():
     # and the value ((target, weight): 8 B): 24 B (32 B) per connection.
     pass_bytes, pass_ms, pass_launches = 0.0, 0.0, 0
     gen_bytes, gen_ms, launches = 0.0, 0.0, 0
+    # Whole step: the bytes the method must move (generation writes the key
+    # and value; each radix pass reads and writes them, the last one writing
+    # the 2-byte delay array besides; the per-source sort reads them and
+    # writes key, target, weight and delay; the index reads the sorted keys
+    # once and writes the per-node and per-group offsets).
+    step_bytes = 0.0
     stage_sum = {}
-    for n_syn, times, npass, st, _, _ in records:
+    for n_syn, times, npass, st, n_groups, n_nodes in records:
         launches += int(st.kernel_launches)
-        pair = (4.0 if st.key_bits <= 32 else 8.0) + 8.0
+        key_b = 4.0 if st.key_bits <= 32 else 8.0
+        pair = key_b + 8.0
         if st.source_major:
             # One per-source counting sort by delay instead of radix passes
             # (every projection generated source by source): not a radix pass.
             names = ["count", "generate", "source_offsets", "source_sort", "index"]
+            step_bytes += (2.0 * pair + 2.0) * n_syn
         else:
             for k in range(npass):
                 pass_bytes += 2.0 * pair * n_syn
                 pass_ms += times[3 + k]
                 pass_launches += 1
             names = ["count", "generate", "histogram"] + ["pass%d" % k for k in range(npass)] + ["index"]
+            step_bytes += (2.0 * pair * npass + 2.0) * n_syn
+        step_bytes += pair * n_syn + key_b * n_syn + 8.0 * n_groups + 16.0 * (n_nodes + 1)
         gen_bytes += pair * n_syn
         gen_ms += times[1]
         for nm, t in zip(names, times):
@@ -904,6 +918,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "connections/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "step_ms": {"median": sorted(step_ms)[len(step_ms) // 2], "min": min(step_ms), "max": max(step_ms)},
         "dtype": "u32+f32", "data": "synthetic",
         "config": dict(config, connections_per_step=n_total // max(1, args.steps),
                        tuning={"sort_digit_bits": final_tuning.sort_digit_bits,
@@ -917,6 +932,14 @@ def main():
                      "unit": "GB/s", "frac": achieved / peak if peak else None, "traffic": traffic,
                      "launches": pass_launches, "avg_launch_ms": pass_ms / max(1, pass_launches),
                      "algorithmic_bytes_per_launch": pass_bytes / max(1, pass_launches)},
+        "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes / args.steps,
+                          "achieved": (step_bytes / args.steps) / (ms / args.steps / 1e3) / 1e9, "peak": peak,
+                          "unit": "GB/s",
+                          "frac": ((step_bytes / args.steps) / (ms / args.steps / 1e3) / 1e9) / peak if peak else None,
+                          "note": "whole step: generation, sort and index bytes the method must move (12 B "
+                                  "written per connection, 24 B per radix pass plus the 2-byte delay array, "
+                                  "the index's read of the sorted keys, per-node and per-group offsets), over "
+                                  "the step's CUDA-event time"},
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_sum.items()},
         "generate_GBps": (gen_bytes / (gen_ms / 1e3)) / 1e9 if gen_ms else None,
         "gpu_launches": launches,
