@@ -297,3 +297,19 @@ def test_graph_replay_past_its_bounds_is_reported(snc, oracle_mod):
     got = nets[0].to_host()
     nets[0].close()
     assert_network_equal(got, oracle_mod.build(replace(spec, seed=101)), "defaults again")
+
+
+def test_graph_rebuild_degenerate_members(snc, oracle_mod):
+    """Graph builds with members that test the capacity and padding edges: a
+    network with no projections, Bernoulli with p = 0 (a capacity of padding
+    only) and p = 1 (the capacity is every pair), a power-of-two node count,
+    one_to_one and a zero-count total-number call."""
+    specs = [
+        NetworkSpec(seed=51, dt=0.1, populations=[7], projections=[]),
+        W.two_population(64, "pairwise_bernoulli", p=0.0, autapses=False, seed=52),
+        W.two_population(32, "pairwise_bernoulli", p=1.0, autapses=False, seed=53),
+        W.two_population(128, "pairwise_bernoulli", p=0.1, autapses=True, seed=54),
+        W.two_population(40, "one_to_one", seed=55),
+        W.two_population(30, "fixed_total_number", k=0, autapses=False, multapses=False, seed=56),
+    ]
+    _graph_trials(snc, oracle_mod, specs, (700,), oracle_members=(1, 2, 3))
