@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_small_kernel(SrcMa
 // input order), stages it in shared memory in delay order and writes each
 // delay's run of the chunk with consecutive threads, after the runs of the
 // earlier chunks.
-__global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMajorArgs a) {
+__global__ void __launch_bounds__(kSrcMajorThreads, 4) src_major_sort_kernel(SrcMajorArgs a) {
   constexpr int TPB = kSrcMajorThreads, IPT = kSrcMajorItems, NW = TPB / 32, CH = kSrcMajorChunk;
   constexpr int RMAX = 1 << kSrcMajorMaxDelayBits;
   constexpr int DPT = RMAX / TPB;  // delays per thread in the per-delay loops
@@ -328,8 +328,13 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
     static_assert(sizeof(skey) >= sizeof(uint32_t) * NW * RMAX, "peer masks fit the key staging buffer");
     uint32_t* pmask = reinterpret_cast<uint32_t*>(skey) + warp * RMAX;
     for (uint64_t cb = 0; cb < c; cb += CH) {
-      for (uint32_t i = tid; i < NW * RMAX / 2; i += TPB) reinterpret_cast<uint32_t*>(&wcnt[0][0])[i] = 0u;
-      for (uint32_t i = tid; i < NW * RMAX; i += TPB) reinterpret_cast<uint32_t*>(skey)[i] = 0u;
+      // Only the build's R delay steps of each warp's counters and masks are
+      // used (R >= 2: a delay step takes at least one bit).
+      for (uint32_t i = tid; i < NW * R / 2; i += TPB) {
+        const uint32_t w = i / (R / 2), h = i % (R / 2);
+        reinterpret_cast<uint32_t*>(&wcnt[w][0])[h] = 0u;
+      }
+      for (uint32_t i = tid; i < NW * R; i += TPB) reinterpret_cast<uint32_t*>(skey)[(i / R) * RMAX + i % R] = 0u;
       __syncthreads();
       uint64_t key[IPT], val[IPT];
       uint32_t rank[IPT];
@@ -375,11 +380,13 @@ __global__ void __launch_bounds__(kSrcMajorThreads) src_major_sort_kernel(SrcMaj
       for (int q = 0; q < DPT; ++q) {
         const uint32_t d = tid * DPT + q;
         uint32_t r = 0;
+        if (d < R) {  // the counters of unused delay steps were not cleared
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const uint32_t cw = wcnt[w][d];
-          wcnt[w][d] = static_cast<uint16_t>(r);
-          r += cw;
+          for (int w = 0; w < NW; ++w) {
+            const uint32_t cw = wcnt[w][d];
+            wcnt[w][d] = static_cast<uint16_t>(r);
+            r += cw;
+          }
         }
         tot[q] = r;
       }

@@ -254,6 +254,22 @@ def test_source_major_sort(snc, oracle_mod, aut, mult):
     assert_network_equal(got, oracle_mod.build(spec), "source-major")
 
 
+@pytest.mark.parametrize("delay", [Dist("const", 0.1), Dist("normal", 25.0, 3.0)], ids=["one_step", "nine_bits"])
+def test_source_major_delay_widths(snc, oracle_mod, delay):
+    """The per-source sort at the narrowest delay field (a single delay step:
+    one bit) and at the widest it takes (nine bits), with sources of one chunk
+    and of several."""
+    WD = dict(weight=Dist("normal", 20.0, 1.0), delay=delay)
+    spec = NetworkSpec(seed=36, dt=0.1, populations=[700, 2600], projections=[
+        Projection(src=(0, 700), tgt=(700, 2600), rule="fixed_outdegree", k=300, **WD),
+        Projection(src=(0, 300), tgt=(700, 2600), rule="all_to_all", **WD)])
+    got, st = _build_with_stats(snc, spec)
+    assert st.source_major == 1 and st.n_passes == 0
+    if delay.kind == "normal":
+        assert int(got["delay"].max()) >= 256
+    assert_network_equal(got, oracle_mod.build(spec), "source-major delay width")
+
+
 def test_source_major_falls_back(snc, oracle_mod):
     """A fixed_indegree projection in the build, or delays beyond 9 bits, keep
     the radix sort."""
