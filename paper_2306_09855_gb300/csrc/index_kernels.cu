@@ -153,14 +153,20 @@ __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a
 }
 
 // group_first[g] = position of the g-th group start, from the bitmap and the
-// exclusive scan of the per-block counts.
+// exclusive scan of the per-block counts.  One bitmap word (32 positions)
+// per thread: a block of 256 threads covers four unpack blocks, two warps
+// each.
 __global__ void __launch_bounds__(kIndexThreads) index_groups_kernel(IndexArgs a) {
+  constexpr uint32_t kWords = kIndexTile / 32;  // bitmap words per unpack block
+  static_assert(kWords == 64 && kIndexThreads % kWords == 0, "two warps per unpack block");
   __shared__ uint32_t warp_tmp[kIndexThreads / 32];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const uint64_t n_blocks = (a.n + kIndexTile - 1) / kIndexTile;
-  for (uint64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
-    const uint32_t word = a.starts[blk * (kIndexTile / 32) + tid / 4];
-    uint32_t bits = (word >> (8u * (tid & 3u))) & 0xFFu;
+  const uint64_t n_words = n_blocks * kWords;
+  for (uint64_t w0 = static_cast<uint64_t>(blockIdx.x) * kIndexThreads; w0 < n_words;
+       w0 += static_cast<uint64_t>(gridDim.x) * kIndexThreads) {
+    const uint64_t w = w0 + tid;
+    uint32_t bits = w < n_words ? a.starts[w] : 0u;
     const uint32_t c = __popc(bits);
     uint32_t incl = c;
 #pragma unroll
@@ -170,16 +176,17 @@ __global__ void __launch_bounds__(kIndexThreads) index_groups_kernel(IndexArgs a
     }
     if (lane == 31) warp_tmp[warp] = incl;
     __syncthreads();
-    uint32_t before = 0;
-    for (uint32_t w = 0; w < warp; ++w) before += warp_tmp[w];
-    uint64_t g = a.block_offsets[blk] + before + incl - c;
-    const uint64_t q0 = blk * kIndexTile + static_cast<uint64_t>(tid) * kIndexItems;
-    while (bits) {
-      const uint32_t b = __ffs(bits) - 1;
-      bits &= bits - 1;
-      if (g < a.group_cap) a.group_first[g] = q0 + b;
-      else atomicOr(a.err, kErrBounds);
-      ++g;
+    if (bits) {
+      const uint32_t before = (warp & 1u) ? warp_tmp[warp - 1] : 0u;
+      uint64_t g = a.block_offsets[w / kWords] + before + incl - c;
+      const uint64_t q0 = w * 32u;
+      do {
+        const uint32_t b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if (g < a.group_cap) a.group_first[g] = q0 + b;
+        else atomicOr(a.err, kErrBounds);
+        ++g;
+      } while (bits);
     }
     __syncthreads();
   }
