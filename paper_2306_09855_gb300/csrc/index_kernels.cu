@@ -27,8 +27,10 @@ namespace snc {
 // `starts` (bit i of the bitmap <-> position i) and the number of group
 // starts of the block.  A group starts where the (source, delay) key
 // changes.
-template <typename K>
-__global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a) {
+// KEYS_ONLY: the sort's last pass wrote target, delay and weight, so only the
+// keys are read (at up to eight blocks per SM, for more loads in flight).
+template <typename K, bool KEYS_ONLY>
+__global__ void __launch_bounds__(kIndexThreads, KEYS_ONLY ? 8 : 1) index_unpack_kernel(IndexArgs a) {
   __shared__ uint32_t warp_cnt[kIndexThreads / 32];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const K* keys = static_cast<const K*>(a.keys);
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a
 #pragma unroll
         for (int j = 0; j < KPV; ++j) key[k * KPV + j] = kv[j];
       }
-      if (!a.unpacked) {
+      if (!KEYS_ONLY) {
         const ulonglong2* v2 = reinterpret_cast<const ulonglong2*>(a.vals + base);
 #pragma unroll
         for (int k = 0; k < kIndexItems / 2; ++k) {
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a
 #pragma unroll
       for (int k = 0; k < kIndexItems; ++k) {
         key[k] = base + k < a.n ? __ldg(keys + base + k) : K(0);
-        val[k] = base + k < a.n && !a.unpacked ? __ldg(a.vals + base + k) : 0ull;
+        val[k] = base + k < a.n && !KEYS_ONLY ? __ldg(a.vals + base + k) : 0ull;
       }
     }
     // Predecessor of this thread's first key: the previous lane's last key,
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(kIndexThreads) index_unpack_kernel(IndexArgs a
         bits |= (start ? 1u : 0u) << k;
       }
     }
-    if (a.unpacked) {
+    if (KEYS_ONLY) {
       // target, weight and delay were written by the sort's last pass
     } else if (full) {
       uint32_t tv[kIndexItems], wv[kIndexItems];
@@ -232,9 +234,11 @@ __global__ void member_index_kernel(MemberIndexArgs a) {
 
 cudaError_t launch_index_unpack(const IndexArgs& a, unsigned grid, cudaStream_t st) {
   if (a.key32)
-    index_unpack_kernel<uint32_t><<<grid, kIndexThreads, 0, st>>>(a);
+    a.unpacked ? index_unpack_kernel<uint32_t, true><<<grid, kIndexThreads, 0, st>>>(a)
+               : index_unpack_kernel<uint32_t, false><<<grid, kIndexThreads, 0, st>>>(a);
   else
-    index_unpack_kernel<uint64_t><<<grid, kIndexThreads, 0, st>>>(a);
+    a.unpacked ? index_unpack_kernel<uint64_t, true><<<grid, kIndexThreads, 0, st>>>(a)
+               : index_unpack_kernel<uint64_t, false><<<grid, kIndexThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
