@@ -823,7 +823,8 @@ def main():
     traffic = None
     tr = committed_traffic()
     if tr and pass_launches:
-        traffic = tr["dram_bytes_per_element"] * (sum(r[0] * r[2] for r in records)) / pass_launches
+        # Keys moved by radix passes only (a source-major record's sort is not one).
+        traffic = tr["dram_bytes_per_element"] * (sum(r[0] * r[2] for r in records if not r[3].source_major)) / pass_launches
 
     # End to end through the public API with host buffers: every step
     # plans on the host, copies the plans in, builds, and copies the whole
