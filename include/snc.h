@@ -277,6 +277,23 @@ snc_status snc_copy_connections(snc_ctx* ctx, uint32_t* src, uint32_t* tgt, uint
 snc_status snc_copy_index(snc_ctx* ctx, uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
                           uint64_t group_cap);
 
+/* The copies of snc_copy_connections (tgt, delay, weight; cap entries) and
+ * snc_copy_index (row_ptr, group_ptr, group_first; group_cap entries) of one
+ * finalized network, queued on the context's stream without waiting for
+ * them.  Each array may be NULL to skip it; the arrays are caller-owned host
+ * memory, page-locked for the copies to run while the host goes on (a
+ * pageable array makes the call wait for its copy).  The call waits for the
+ * build itself and reports its errors (as snc_synchronize); the arrays hold
+ * the network once a later snc_synchronize(ctx) has returned SNC_OK, and
+ * must not be read, written or freed before, nor the context destroyed
+ * (snc_destroy waits for the copies).  Lets a caller copy one network while
+ * the next one builds on another stream.  STATE before snc_finalize;
+ * INVALID_ARG when cap < n_syn or group_cap < n_groups with group_first
+ * given, before any copy is queued. */
+snc_status snc_copy_network_async(snc_ctx* ctx, uint32_t* tgt, uint16_t* delay, float* weight, uint64_t cap,
+                                  uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
+                                  uint64_t group_cap);
+
 /* Target shard (Sec. 4 names target-distributed construction as future
  * work): the build keeps only the connections whose target node is in
  * [first, first + n).  Every draw is keyed by (projection, node, slot), so a

@@ -2051,34 +2051,61 @@ snc_status snc_deliver(snc_ctx* c, const uint32_t* src, const uint32_t* grp, con
   });
 }
 
+namespace {
+// Host copies of a finalized network, queued on the context's stream; the
+// caller has synchronized (errors, counts of the views) and checked the
+// capacities.
+snc_status queue_connection_copies(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16_t* delay, float* weight) {
+  const uint64_t n = c->n_syn;
+  CallScope scope(c);
+  cudaStream_t st = c->store->stream;
+  if (src && n > 0) {
+    uint32_t* d_src = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
+    if (!d_src) return fail(c, SNC_ERR_OOM, "device allocation failed (source expansion)");
+    if (c->n_nodes > 0) {
+      const uint64_t blocks = std::min<uint64_t>((c->n_nodes + 7) / 8, static_cast<uint64_t>(c->sms) * 16);
+      expand_sources_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(c->row_ptr, c->n_nodes, d_src);
+      ++c->stats.kernel_launches;
+    }
+    SNC_CUDA(c, cudaGetLastError());
+    SNC_CUDA(c, cudaMemcpyAsync(src, d_src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    dev_free(c, d_src);  // stream-ordered: after the copy
+  }
+  if (tgt && n > 0) SNC_CUDA(c, cudaMemcpyAsync(tgt, c->target, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (delay && n > 0) SNC_CUDA(c, cudaMemcpyAsync(delay, c->delay, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
+  if (weight && n > 0) SNC_CUDA(c, cudaMemcpyAsync(weight, c->weight, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  c->stats.d2h_bytes += n * ((src ? 4 : 0) + (tgt ? 4 : 0) + (delay ? 2 : 0) + (weight ? 4 : 0));
+  return SNC_OK;
+}
+
+snc_status queue_index_copies(snc_ctx* c, uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first) {
+  cudaStream_t st = c->store->stream;
+  const size_t rows = (c->n_nodes + 1) * sizeof(uint64_t);
+  if (row_ptr) SNC_CUDA(c, cudaMemcpyAsync(row_ptr, c->row_ptr, rows, cudaMemcpyDeviceToHost, st));
+  if (group_ptr) SNC_CUDA(c, cudaMemcpyAsync(group_ptr, c->group_ptr, rows, cudaMemcpyDeviceToHost, st));
+  if (group_first && c->n_groups > 0)
+    SNC_CUDA(c, cudaMemcpyAsync(group_first, c->group_first, c->n_groups * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  c->stats.d2h_bytes += (row_ptr ? rows : 0) + (group_ptr ? rows : 0) + (group_first ? c->n_groups * sizeof(uint64_t) : 0);
+  return SNC_OK;
+}
+
+// The build done and its errors reported (snc_synchronize), before a copy.
+snc_status ready_for_copy(snc_ctx* c, const char* what) {
+  if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
+  if (!c->finalized) return fail(c, SNC_ERR_STATE, "%s before finalize", what);
+  return snc_synchronize(c);
+}
+}  // namespace
+
 snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16_t* delay, float* weight,
                                 uint64_t cap) {
   return snc::abi_guard([&]() -> snc_status {
-    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-    if (!c->finalized) return fail(c, SNC_ERR_STATE, "copy_connections before finalize");
-    snc_status s = snc_synchronize(c);
+    snc_status s = ready_for_copy(c, "copy_connections");
     if (s != SNC_OK) return s;
     if (cap < c->n_syn) return fail(c, SNC_ERR_INVALID_ARG, "capacity below the number of connections");
-    const uint64_t n = c->n_syn;
-    CallScope scope(c);
-    cudaStream_t st = c->store->stream;
-    if (src && n > 0) {
-      uint32_t* d_src = static_cast<uint32_t*>(dev_alloc(c, n * sizeof(uint32_t)));
-      if (!d_src) return fail(c, SNC_ERR_OOM, "device allocation failed (source expansion)");
-      if (c->n_nodes > 0) {
-        const uint64_t blocks = std::min<uint64_t>((c->n_nodes + 7) / 8, static_cast<uint64_t>(c->sms) * 16);
-        expand_sources_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(c->row_ptr, c->n_nodes, d_src);
-        ++c->stats.kernel_launches;
-      }
-      SNC_CUDA(c, cudaGetLastError());
-      SNC_CUDA(c, cudaMemcpyAsync(src, d_src, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-      dev_free(c, d_src);  // stream-ordered: after the copy
-    }
-    if (tgt && n > 0) SNC_CUDA(c, cudaMemcpyAsync(tgt, c->target, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    if (delay && n > 0) SNC_CUDA(c, cudaMemcpyAsync(delay, c->delay, n * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
-    if (weight && n > 0) SNC_CUDA(c, cudaMemcpyAsync(weight, c->weight, n * sizeof(float), cudaMemcpyDeviceToHost, st));
-    c->stats.d2h_bytes += n * ((src ? 4 : 0) + (tgt ? 4 : 0) + (delay ? 2 : 0) + (weight ? 4 : 0));
-    SNC_CUDA(c, cudaStreamSynchronize(st));
+    s = queue_connection_copies(c, src, tgt, delay, weight);
+    if (s != SNC_OK) return s;
+    SNC_CUDA(c, cudaStreamSynchronize(c->store->stream));
     return SNC_OK;
   });
 }
@@ -2086,20 +2113,29 @@ snc_status snc_copy_connections(snc_ctx* c, uint32_t* src, uint32_t* tgt, uint16
 snc_status snc_copy_index(snc_ctx* c, uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
                           uint64_t group_cap) {
   return snc::abi_guard([&]() -> snc_status {
-    if (!c) return fail(nullptr, SNC_ERR_INVALID_ARG, "null context");
-    if (!c->finalized) return fail(c, SNC_ERR_STATE, "copy_index before finalize");
-    snc_status s = snc_synchronize(c);
+    snc_status s = ready_for_copy(c, "copy_index");
     if (s != SNC_OK) return s;
     if (group_first && group_cap < c->n_groups) return fail(c, SNC_ERR_INVALID_ARG, "group capacity below n_groups");
-    cudaStream_t st = c->store->stream;
-    const size_t rows = (c->n_nodes + 1) * sizeof(uint64_t);
-    if (row_ptr) SNC_CUDA(c, cudaMemcpyAsync(row_ptr, c->row_ptr, rows, cudaMemcpyDeviceToHost, st));
-    if (group_ptr) SNC_CUDA(c, cudaMemcpyAsync(group_ptr, c->group_ptr, rows, cudaMemcpyDeviceToHost, st));
-    if (group_first && c->n_groups > 0)
-      SNC_CUDA(c, cudaMemcpyAsync(group_first, c->group_first, c->n_groups * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    c->stats.d2h_bytes += (row_ptr ? rows : 0) + (group_ptr ? rows : 0) + (group_first ? c->n_groups * sizeof(uint64_t) : 0);
-    SNC_CUDA(c, cudaStreamSynchronize(st));
+    s = queue_index_copies(c, row_ptr, group_ptr, group_first);
+    if (s != SNC_OK) return s;
+    SNC_CUDA(c, cudaStreamSynchronize(c->store->stream));
     return SNC_OK;
+  });
+}
+
+snc_status snc_copy_network_async(snc_ctx* c, uint32_t* tgt, uint16_t* delay, float* weight, uint64_t cap,
+                                  uint64_t* row_ptr, uint64_t* group_ptr, uint64_t* group_first,
+                                  uint64_t group_cap) {
+  return snc::abi_guard([&]() -> snc_status {
+    // The build's errors and counts first, so that nothing is queued when an
+    // argument is refused; then the copies, without waiting for them.
+    snc_status s = ready_for_copy(c, "copy_network_async");
+    if (s != SNC_OK) return s;
+    if (cap < c->n_syn) return fail(c, SNC_ERR_INVALID_ARG, "capacity below the number of connections");
+    if (group_first && group_cap < c->n_groups) return fail(c, SNC_ERR_INVALID_ARG, "group capacity below n_groups");
+    s = queue_connection_copies(c, nullptr, tgt, delay, weight);
+    if (s != SNC_OK) return s;
+    return queue_index_copies(c, row_ptr, group_ptr, group_first);
   });
 }
 

@@ -116,6 +116,7 @@ SNC_JOB_QUEUED, SNC_JOB_RUNNING, SNC_JOB_DONE, SNC_JOB_FAILED = range(4)
 EXPORTS = ("snc_create", "snc_destroy", "snc_create_population", "snc_connect", "snc_connect_arrays",
            "snc_finalize",
            "snc_synchronize", "snc_get_connections", "snc_copy_connections", "snc_copy_index",
+           "snc_copy_network_async",
            "snc_deliver", "snc_set_target_shard", "snc_stage_times",
            "snc_radix_sort_pairs", "snc_radix_sort_pairs_noalloc", "snc_block_sort_pairs", "snc_set_block_sort",
            "snc_get_stats",
@@ -155,6 +156,7 @@ def load(build: bool = True):
         "snc_get_connections": ([P, ctypes.POINTER(snc_conn_view)], I32),
         "snc_copy_connections": ([P, P, P, P, P, U64], I32),
         "snc_copy_index": ([P, P, P, P, U64], I32),
+        "snc_copy_network_async": ([P, P, P, P, U64, P, P, P, U64], I32),
         "snc_deliver": ([P, P, P, P, U64, P], I32),
         "snc_set_target_shard": ([P, U32, U32], I32),
         "snc_stage_times": ([P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(I32),
@@ -678,17 +680,32 @@ class Network:
         snc_copy_connections(self.ctx, n, out)
         return n
 
-    def to_host_network(self, out):
+    def to_host_network(self, out, wait=True):
         """Copy the network as it is kept on the device -- target, delay and
         weight arrays plus the CSR and group index (sources implicit in
         row_ptr) -- into caller-owned host arrays (keys "tgt", "delay",
         "weight", "row_ptr", "group_ptr", "group_first"); returns the
-        number of connections."""
+        number of connections.  wait=False queues the copies
+        (snc_copy_network_async; page-locked arrays) and returns: the arrays
+        hold the network after the next synchronize()."""
         v = self.view()
         n = int(v.n_syn)
+        cap = min(out[k].size for k in ("tgt", "delay", "weight"))
+        if not wait:
+            need = {"tgt": (np.uint32, n), "delay": (np.uint16, n), "weight": (np.float32, n),
+                    "row_ptr": (np.uint64, int(v.n_nodes) + 1), "group_ptr": (np.uint64, int(v.n_nodes) + 1),
+                    "group_first": (np.uint64, int(v.n_groups))}
+            for name, (dt, size) in need.items():
+                a = out[name]
+                if a.dtype != dt or a.size < size or not a.flags.c_contiguous:
+                    raise ValueError("output array %r: need %d contiguous %s" % (name, size, np.dtype(dt).name))
+            _check(load().snc_copy_network_async(self.ctx, out["tgt"].ctypes.data, out["delay"].ctypes.data,
+                                                 out["weight"].ctypes.data, cap, out["row_ptr"].ctypes.data,
+                                                 out["group_ptr"].ctypes.data, out["group_first"].ctypes.data,
+                                                 out["group_first"].size), self.ctx)
+            return n
         _check(load().snc_copy_connections(self.ctx, None, out["tgt"].ctypes.data, out["delay"].ctypes.data,
-                                           out["weight"].ctypes.data, min(out[k].size for k in ("tgt", "delay", "weight"))),
-               self.ctx)
+                                           out["weight"].ctypes.data, cap), self.ctx)
         snc_copy_index(self.ctx, int(v.n_nodes), int(v.n_groups), out)
         return n
 

@@ -207,6 +207,47 @@ def test_copy_index_and_network_copy_match_views(snc):
     net.close()
 
 
+def test_async_network_copy_while_another_builds(snc):
+    """snc_copy_network_async: network A's copies are queued into page-locked
+    arrays while network B is finalized on another stream; after A's
+    synchronize the arrays equal the synchronous copies, and a refused
+    capacity queues nothing."""
+    torch = pytest.importorskip("torch")
+    spec_a = W.two_population(3000, "fixed_indegree", k=50, autapses=False, seed=42)
+    spec_b = W.two_population(4000, "pairwise_bernoulli", p=0.02, seed=43)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    a = snc.Network(spec_a, stream=sa).finalize()
+    ref = a.to_host()
+    v = a.view()
+    n, nn, ng = int(v.n_syn), int(v.n_nodes), int(v.n_groups)
+
+    def pinned(count, dt):
+        return torch.empty(max(1, count), dtype=dt, pin_memory=True).numpy()
+
+    out = {"tgt": pinned(n, torch.int32).view(np.uint32), "delay": pinned(n, torch.int16).view(np.uint16),
+           "weight": pinned(n, torch.float32), "row_ptr": pinned(nn + 1, torch.int64).view(np.uint64),
+           "group_ptr": pinned(nn + 1, torch.int64).view(np.uint64),
+           "group_first": pinned(ng, torch.int64).view(np.uint64)}
+    for arr in out.values():
+        arr.fill(0xFF if arr.dtype != np.float32 else 0)
+    small = dict(out, group_first=out["group_first"][:max(0, ng - 1)])
+    with pytest.raises(Exception):
+        a.to_host_network(small, wait=False)
+    status = snc.load().snc_copy_network_async(a.ctx, out["tgt"].ctypes.data, out["delay"].ctypes.data,
+                                              out["weight"].ctypes.data, n - 1, 0, 0, 0, 0)
+    assert status == snc.SNC_ERR_INVALID_ARG
+    assert a.to_host_network(out, wait=False) == n
+    b = snc.Network(spec_b, stream=sb).finalize()
+    a.synchronize()
+    for f in ("tgt", "delay", "weight", "row_ptr", "group_ptr"):
+        np.testing.assert_array_equal(out[f].astype(ref[f].dtype), ref[f], err_msg=f)
+    np.testing.assert_array_equal(out["group_first"][:ng], ref["group_first"][:ng])
+    b.synchronize()
+    assert int(b.view().n_syn) > 0
+    b.close()
+    a.close()
+
+
 def test_redraw_super_buckets(snc, oracle_mod):
     """fixed_total_number without multapses above 2^19 slots: round-0 pairs
     pass through several super-buckets before their buckets (1.5e6 slots on
