@@ -202,9 +202,14 @@ snc_status snc_connect_arrays(snc_ctx* ctx, snc_range src, snc_range tgt, const 
  * sorts them stably by (source, delay step) and builds the CSR and group
  * index.
  * Work is queued on the context's stream; the call blocks only for the
- * small device->host reads that size variable-count rules.  After it,
- * snc_connect returns STATE.  UNSUPPORTED: packed key wider than 64 bits or
- * a sampler range beyond the shared-memory bitmap. */
+ * small device->host reads that size variable-count rules (pairwise_bernoulli
+ * counts; the pending counts of each redraw round of fixed_total_number
+ * without multapses or autapses when it needs more than 64 rounds: below
+ * that, the rounds are counted on the device and a redraw still pending
+ * after the last one, probability below 10^-15, is reported as TIMEOUT by
+ * snc_synchronize).  After it, snc_connect returns STATE.  UNSUPPORTED:
+ * packed key wider than 64 bits or a sampler range beyond the shared-memory
+ * bitmap. */
 snc_status snc_finalize(snc_ctx* ctx);
 
 /* Batched calibration (no counterpart in the paper, which builds one network

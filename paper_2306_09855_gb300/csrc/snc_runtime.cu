@@ -1384,28 +1384,33 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
       SNC_CUDA(c, cudaGetLastError());
       uint64_t* pending = pend_a;
       uint64_t* next = pend_b;
-      if (graph_build) {
-        // A pending slot redraws until its pair is free: it fails a round with
-        // probability at most q (the share of pairs already taken, or of
-        // pairs joining a node to itself), so after R rounds about
-        // n_slots * q^R remain; R is chosen for 10^-12.  Rounds with nothing
-        // pending cost a launch each; a replay with slots still pending after
-        // the last round reports TIMEOUT.
-        double q = 0.0;
-        for (const RedrawProj& r : rps) {
-          const Projection& p = *ups[r.proj].p;
-          const double pairs = std::max(1.0, static_cast<double>(p.src.n) * static_cast<double>(p.tgt.n));
-          double f = p.rule.allow_autapses ? 0.0 : 1.0 / std::max(1u, std::min(p.src.n, p.tgt.n));
-          if (!p.rule.allow_multapses) f += static_cast<double>(cnt[r.proj]) / pairs;
-          q = std::max(q, std::min(f, 1.0));
-        }
-        const double need = (std::log(static_cast<double>(n_slots) + 1.0) + 12.0 * std::log(10.0)) /
-                            std::max(1e-9, -std::log(std::max(q, 1e-300)));
+      // A pending slot redraws until its pair is free: it fails a round with
+      // probability at most q (the share of pairs already taken, or of pairs
+      // joining a node to itself), so after R rounds about n_slots * q^R
+      // remain.  A graph build records R rounds chosen for 10^-12 (a replay
+      // with slots still pending after the last one reports TIMEOUT); a plain
+      // build runs R rounds chosen for 10^-15 the same way when R <= 64, so
+      // that finalize does not wait on the host for the pending counts, and
+      // otherwise reads the count back after every round.
+      double q = 0.0;
+      for (const RedrawProj& r : rps) {
+        const Projection& p = *ups[r.proj].p;
+        const double pairs = std::max(1.0, static_cast<double>(p.src.n) * static_cast<double>(p.tgt.n));
+        double f = p.rule.allow_autapses ? 0.0 : 1.0 / std::max(1u, std::min(p.src.n, p.tgt.n));
+        if (!p.rule.allow_multapses) f += static_cast<double>(cnt[r.proj]) / pairs;
+        q = std::max(q, std::min(f, 1.0));
+      }
+      const double decades = graph_build ? 12.0 : 15.0;
+      const double need = (std::log(static_cast<double>(n_slots) + 1.0) + decades * std::log(10.0)) /
+                          std::max(1e-9, -std::log(std::max(q, 1e-300)));
+      const bool device_rounds = graph_build || (q < 1.0 && need <= 64.0);
+      if (device_rounds) {
         if (q >= 1.0 || need > 512.0)
           return fail(c, SNC_ERR_UNSUPPORTED,
                       "graph build: fixed_total_number without multapses at this density needs host-driven rounds");
-        const uint32_t rounds = g_graph_test.redraw_rounds ? g_graph_test.redraw_rounds
-                                                           : static_cast<uint32_t>(std::max(2.0, std::ceil(need)));
+        const uint32_t rounds = graph_build && g_graph_test.redraw_rounds
+                                    ? g_graph_test.redraw_rounds
+                                    : static_cast<uint32_t>(std::max(2.0, std::ceil(need)));
         unsigned long long* cur_n = a.n_next;  // round 0 filled pend_a and this counter
         unsigned long long* nxt_n = a.n_next + 1;
         for (uint32_t round = 1; round <= rounds; ++round) {
@@ -1424,7 +1429,7 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         ++c->stats.kernel_launches;
         SNC_CUDA(c, cudaGetLastError());
       }
-      for (uint32_t round = 1; !graph_build; ++round) {
+      for (uint32_t round = 1; !device_rounds; ++round) {
         SNC_CUDA(c, cudaMemcpyAsync(S.h_pinned, a.n_next, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         c->stats.d2h_bytes += sizeof(uint64_t);
         SNC_CUDA(c, cudaStreamSynchronize(st));
@@ -1957,7 +1962,7 @@ snc_status snc_synchronize(snc_ctx* c) {
     if (err & kErrLookbackTimeout) return fail(c, SNC_ERR_TIMEOUT, "a look-back wait expired on the device");
     if (err & kErrSamplerBound) return fail(c, SNC_ERR_TIMEOUT, "a sampler exceeded its attempt bound");
     if (err & kErrGraphRounds)
-      return fail(c, SNC_ERR_TIMEOUT, "graph replay: total-number redraws still pending after the recorded rounds");
+      return fail(c, SNC_ERR_TIMEOUT, "fixed_total_number: redraws still pending after the last device-counted round");
     if (err & kErrGraphCapacity)
       return fail(c, SNC_ERR_UNSUPPORTED, "graph replay: a pairwise_bernoulli projection drew past its capacity");
     if (err & kErrBounds) {
