@@ -468,7 +468,9 @@ snc_status snc_set_wait_test(uint32_t lookback_spin_limit, uint32_t withhold_til
  * test make a replay exceed them: the replay then writes only inside its
  * arrays and the next snc_synchronize reports UNSUPPORTED (a Bernoulli total
  * above its capacity) or TIMEOUT (redraws still pending).  Process-wide, for
- * graph builds recorded after the call.  INVALID_ARG: a negative value.
+ * graph builds recorded after the call; redraw_rounds also sets the rounds of
+ * plain builds that count their redraw rounds on the device (snc_finalize).
+ * INVALID_ARG: a negative value.
  * Reset with snc_set_graph_test(10, 32, 0). */
 snc_status snc_set_graph_test(double bernoulli_sd, double bernoulli_slack, uint32_t redraw_rounds);
 

@@ -1408,9 +1408,8 @@ snc_status finalize_build(snc_ctx* const* members, int n_members) {
         if (q >= 1.0 || need > 512.0)
           return fail(c, SNC_ERR_UNSUPPORTED,
                       "graph build: fixed_total_number without multapses at this density needs host-driven rounds");
-        const uint32_t rounds = graph_build && g_graph_test.redraw_rounds
-                                    ? g_graph_test.redraw_rounds
-                                    : static_cast<uint32_t>(std::max(2.0, std::ceil(need)));
+        const uint32_t rounds = g_graph_test.redraw_rounds ? g_graph_test.redraw_rounds
+                                                           : static_cast<uint32_t>(std::max(2.0, std::ceil(need)));
         unsigned long long* cur_n = a.n_next;  // round 0 filled pend_a and this counter
         unsigned long long* nxt_n = a.n_next + 1;
         for (uint32_t round = 1; round <= rounds; ++round) {

@@ -343,6 +343,32 @@ def test_sparse_samplers_wide_ranges(snc, oracle_mod):
     assert_network_equal(got, oracle_mod.build(spec), "sparse samplers")
 
 
+def test_device_counted_redraw_rounds(snc, oracle_mod):
+    """A plain fixed_total_number build without multapses that needs few
+    rounds counts them on the device: with the default number it equals the
+    oracle; held to one round by the test hook (about a fifth of the pairs
+    taken, so hundreds of slots still pending) it reports TIMEOUT at the next
+    synchronize instead of returning a wrong network; the build after the
+    reset is the oracle's again."""
+    spec = W.two_population(300, "fixed_total_number", k=20_000, autapses=False, multapses=False, seed=24)
+    got = snc.Network(spec).finalize()
+    assert_network_equal(got.to_host(), oracle_mod.build(spec), "device-counted rounds")
+    got.close()
+    try:
+        snc.snc_set_graph_test(10.0, 32.0, 1)
+        net = snc.Network(spec)
+        with pytest.raises(snc.SncError) as e:
+            net.finalize()
+            net.synchronize()
+        assert e.value.name == "TIMEOUT"
+        net.close()
+    finally:
+        snc.snc_set_graph_test(10.0, 32.0, 0)
+    again = snc.Network(spec).finalize()
+    assert_network_equal(again.to_host(), oracle_mod.build(spec), "after the reset")
+    again.close()
+
+
 def test_redraw_global_tables(snc, oracle_mod):
     """fixed_total_number without multapses on node ranges too wide for a
     packed (pair, slot) word (2 x 2.1e6 nodes, 1.1e6 slots: 68 bits) takes the
