@@ -773,7 +773,9 @@ def main():
 
     # Dominant kernel: the onesweep radix pass.  Algorithmic bytes per launch:
     # read and write the key ((source, delay): 4 B, or 8 B above 32 bits)
-    # and the value ((target, weight): 8 B): 24 B (32 B) per connection.
+    # and the value ((target, weight): 8 B): 24 B (32 B) per connection; the
+    # last pass of a sort also writes the 2-byte delay array (it unpacks the
+    # value into the target and weight arrays).
     pass_bytes, pass_ms, pass_launches = 0.0, 0.0, 0
     gen_bytes, gen_ms, launches = 0.0, 0.0, 0
     # Whole step: the bytes the method must move (generation writes the key
@@ -794,7 +796,7 @@ def main():
             step_bytes += (2.0 * pair + 2.0) * n_syn
         else:
             for k in range(npass):
-                pass_bytes += 2.0 * pair * n_syn
+                pass_bytes += (2.0 * pair + (2.0 if k == npass - 1 else 0.0)) * n_syn
                 pass_ms += times[3 + k]
                 pass_launches += 1
             names = ["count", "generate", "histogram"] + ["pass%d" % k for k in range(npass)] + ["index"]
